@@ -1,0 +1,111 @@
+"""Seeded synthetic workloads for the RAS-PML Helmholtz solver.
+
+This module is the one piece shared by the CPU oracle and the CUDA path. It
+holds problem parameters and seeded random draws only (wavenumber, domain,
+mesh size, subdomain grid, widths, Gaussian source centres); it contains none
+of the method's arithmetic (no stretching, quadrature, assembly or solve).
+
+Workloads (all with wave speed c = 1 and a Cartesian PML of width 0.1 around
+Omega_int, stretching profile g'(x) = 20 (3t^2 - 2t^3), t = min(x/0.05, 1)):
+
+  c0   k = 20*pi,  h = 1/160,  4 x 4 subdomains,    3 Gaussians, width 0.02
+  c1   k = 80*pi,  h = 1/640,  16 x 16 subdomains,  8 Gaussians, width 0.005
+  c2   k = 160*pi, h = 1/1280, 32 x 32 subdomains, 16 Gaussians, width 0.0025
+  c4   k = 320*pi, h = 1/2560, 64 x 64 subdomains, 32 Gaussians, width 0.00125
+
+Omega_int = (0,1)^2 in all four; overlap and local PML width are both
+0.5*ln(k)/k rounded half up to whole cells (at least one cell). Source centres
+are uniform in Omega_int from numpy's default_rng(seed); amplitudes are 1.
+Smaller "tiny*" workloads with the same construction serve the tests.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+__all__ = ["Workload", "get", "width_cells", "NAMES"]
+
+
+def width_cells(k: float, h: float) -> int:
+    """Cells in 0.5*ln(k)/k, rounded half up, at least 1 (workload recipe)."""
+    return max(1, int(math.floor(0.5 * math.log(k) / k / h + 0.5)))
+
+
+@dataclass
+class Workload:
+    name: str
+    k: float
+    x0: float
+    y0: float
+    x1: float
+    y1: float
+    kappa_g: float
+    h: float
+    px: int
+    py: int
+    ovlp_cells: int
+    pml_cells: int
+    g_amp: float = 20.0
+    g_ramp: float = 0.05
+    local_bc: int = 0          # 0 impedance (RAS-PML-Imp), 1 Dirichlet
+    centres: np.ndarray = field(default_factory=lambda: np.zeros((0, 2)))
+    amps: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    width: float = 0.02
+    seed: int = 0
+
+    @property
+    def cells_x(self) -> int:
+        return int(round((self.x1 - self.x0 + 2 * self.kappa_g) / self.h))
+
+    @property
+    def cells_y(self) -> int:
+        return int(round((self.y1 - self.y0 + 2 * self.kappa_g) / self.h))
+
+    @property
+    def n_unknowns(self) -> int:
+        return (self.cells_x - 1) * (self.cells_y - 1)
+
+    def params(self) -> dict:
+        """Scalar parameters, in the field order of the C parameter struct."""
+        return dict(k=self.k, x0=self.x0, y0=self.y0, x1=self.x1, y1=self.y1,
+                    kappa_g=self.kappa_g, h=self.h, px=self.px, py=self.py,
+                    ovlp_cells=self.ovlp_cells, pml_cells=self.pml_cells,
+                    g_amp=self.g_amp, g_ramp=self.g_ramp, local_bc=self.local_bc)
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+def _make(name, k, h, p, ns, width, seed, side=1.0, kappa_g=0.1, ovlp=None, pml=None):
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(0.0, side, size=(ns, 2))
+    w = width_cells(k, h)
+    return Workload(name=name, k=k, x0=0.0, y0=0.0, x1=side, y1=side,
+                    kappa_g=kappa_g, h=h, px=p, py=p,
+                    ovlp_cells=w if ovlp is None else ovlp,
+                    pml_cells=w if pml is None else pml,
+                    centres=centres, amps=np.ones(ns), width=width, seed=seed)
+
+
+def get(name: str) -> Workload:
+    """Return the named seeded workload."""
+    pi = math.pi
+    table = {
+        "c0": lambda: _make("c0", 20 * pi, 1 / 160, 4, 3, 0.02, 0),
+        "c1": lambda: _make("c1", 80 * pi, 1 / 640, 16, 8, 0.005, 1),
+        "c2": lambda: _make("c2", 160 * pi, 1 / 1280, 32, 16, 0.0025, 2),
+        "c4": lambda: _make("c4", 320 * pi, 1 / 2560, 64, 32, 0.00125, 4),
+        # small cases with the same construction (tests)
+        "tiny": lambda: _make("tiny", 4 * pi, 1 / 40, 2, 2, 0.08, 10, ovlp=2, pml=3),
+        "tiny3": lambda: _make("tiny3", 8 * pi, 1 / 50, 3, 3, 0.05, 11, ovlp=2, pml=3),
+        "small": lambda: _make("small", 10 * pi, 1 / 80, 4, 3, 0.04, 12),
+        "mid": lambda: _make("mid", 40 * pi, 1 / 320, 8, 5, 0.01, 13),
+    }
+    if name not in table:
+        raise KeyError(f"unknown workload {name!r}; known: {sorted(table)}")
+    return table[name]()
+
+
+NAMES = ("c0", "c1", "c2", "c4", "tiny", "tiny3", "small", "mid")
