@@ -1,0 +1,180 @@
+/*
+ * raspml.h -- C ABI of libraspml.so: the RAS-PML preconditioner and a
+ * device-side flexible GMRES for P1 discretisations of the 2D Helmholtz
+ * equation with a Cartesian PML, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Xie, Gong, Graham, Spence, Zhang, "Massively parallel Schwarz
+ * methods for the high frequency Helmholtz equation".
+ *   - Problem and PML truncation: Section 1 (eq. helmholtz0, the definitions
+ *     of g, g_i, gamma_i and eq. weak).
+ *   - Covering, local PML, local forms a_j, partition of unity: Section 2.
+ *   - Preconditioner B^-1 = sum_j R~_j^T A_j^-1 R_j: Section 2 (the equation
+ *     after eq. update1).
+ *   - Impedance closure of the local problems (RAS-PML-Imp): Section 3 (ii),
+ *     eq. impedance.
+ *   - GMRES with B^-1 as preconditioner: Section 4.1; Algorithm 1 for the
+ *     Richardson form.
+ *
+ * Discretisation (identical on every entry point):
+ *   Omega = [x0-kappa_g, x1+kappa_g] x [y0-kappa_g, y1+kappa_g], Mx x My square
+ *   cells of side h, each split along its (i,j)-(i+1,j+1) diagonal; P1
+ *   elements; the gamma_1*gamma_2-multiplied (complex-symmetric) form of
+ *   eq. weak; every element integral by the three-point edge-midpoint rule;
+ *   impedance edges by 2-point Gauss. Unknowns are the (Mx-1)*(My-1) nodes not
+ *   on the outer boundary, numbered x-fastest: node (i,j), 1<=i<=Mx-1,
+ *   1<=j<=My-1, has index (j-1)*(Mx-1) + (i-1).
+ *
+ * Conventions:
+ *   - Complex vectors are interleaved (re, im) doubles, i.e. the memory layout
+ *     of torch.complex128 / std::complex<double>.
+ *   - "_dev" pointers are device pointers on the handle's device; the caller
+ *     owns them. They must be 16-byte aligned and hold n elements.
+ *   - "_host" pointers are host pointers (pageable or pinned).
+ *   - The library owns everything it allocates (factors, index tables,
+ *     Krylov workspace) and frees it in ras_pml_destroy.
+ *   - Work is enqueued on the stream given to ras_pml_setup. Calls return
+ *     after enqueueing, except ras_pml_factor, helmholtz_solve and
+ *     helmholtz_solve_host, which return when their result is known.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *
+ * Status codes: 0 success; 1 not converged within maxit (outputs still
+ * valid); negative values are errors, see ras_pml_error_string().
+ */
+#ifndef RASPML_H
+#define RASPML_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RASPML_OK              0
+#define RASPML_NOT_CONVERGED   1
+#define RASPML_EBADARG        -1  /* invalid parameter or size            */
+#define RASPML_ENOMEM         -2  /* device allocation failed             */
+#define RASPML_ECUDA          -3  /* CUDA runtime error                   */
+#define RASPML_EPIVOT         -4  /* zero/tiny pivot in a local factor    */
+#define RASPML_ENAN           -5  /* NaN or Inf in a residual             */
+#define RASPML_ETIMEOUT       -6  /* a bounded device-side wait gave up   */
+#define RASPML_ESTATE         -7  /* call out of order (e.g. not factored)*/
+
+/* One complex128 element; same layout as torch.complex128. */
+typedef struct { double re, im; } rp_c128;
+
+/* Problem and method parameters (Section 1 and Section 2 of the paper). */
+typedef struct {
+  double k;               /* wavenumber (wave speed c = 1), k >= 0               */
+  double x0, y0, x1, y1;  /* Omega_int = (x0,x1) x (y0,y1)                       */
+  double kappa_g;         /* global PML width around Omega_int                   */
+  double h;               /* mesh size; (x1-x0+2 kappa_g)/h and (y1-y0+2
+                             kappa_g)/h must be whole numbers (to 1e-9 rel)    */
+  int    px, py;          /* subdomain grid over Omega (the non-overlapping
+                             Cartesian partition of Section 2)                 */
+  int    ovlp_cells;      /* overlap delta as a per-side extension in cells;
+                             -1: 0.5*ln(k)/k rounded half up, at least 1       */
+  int    pml_cells;       /* local PML width kappa in cells; -1: same law;
+                             0: no local PML (RAS-Imp)                         */
+  double g_amp, g_ramp;   /* stretching g'(d) = g_amp*(3t^2-2t^3),
+                             t = min(d/g_ramp, 1), d = distance beyond the box  */
+  int    local_bc;        /* 0: impedance closure (RAS-PML-Imp, Section 3 (ii));
+                             1: Dirichlet closure (RAS-PML-Drch, Section 2)    */
+  int    factor_prec;     /* local factors and solves: 0 complex128,
+                             1 complex64 (outer iteration stays complex128)    */
+} ras_pml_params;
+
+/* Sizes and statistics of a handle (filled by ras_pml_info). */
+typedef struct {
+  int64_t n;              /* global unknowns, (Mx-1)*(My-1)                     */
+  int32_t Mx, My;         /* cells per direction                                */
+  int32_t num_sub;        /* px*py                                              */
+  int32_t ovlp_cells, pml_cells;   /* resolved widths                           */
+  int32_t max_local_n;    /* largest local unknown count                        */
+  int32_t max_band;       /* largest local half-bandwidth b = nlx+1             */
+  int64_t sum_local_n;    /* sum_j n_j                                          */
+  int64_t sum_band_n;     /* sum_j b_j*n_j: entries of all L factors            */
+  int64_t factor_bytes;   /* device bytes of the stored factors (L and D^-1)    */
+  double  apply_bytes;    /* algorithmic bytes of one ras_pml_apply             */
+  double  min_pivot_ratio;/* min_j min_k |d_k| / max_k |d_k| after factor       */
+  int32_t factored;       /* 1 once ras_pml_factor succeeded                    */
+  int32_t factor_prec;
+  int32_t bad_subdomain;  /* subdomain of a RASPML_EPIVOT, else -1              */
+  int32_t last_iters;     /* iterations of the last solve                       */
+} ras_pml_info_t;
+
+typedef struct ras_pml_handle ras_pml_handle;
+
+/* Builds the mesh, the covering of Section 2 and the global matrix of
+ * eq. weak on the current device, on `cuda_stream` (a cudaStream_t, may be
+ * NULL for the legacy default stream). Validates params (RASPML_EBADARG when
+ * Omega is not whole cells, 2*ovlp exceeds a box, or a local band exceeds 127).
+ * On success *out owns all device memory of the handle. */
+int ras_pml_setup(const ras_pml_params* params, void* cuda_stream,
+                  ras_pml_handle** out);
+
+/* Fills *info (host struct). */
+int ras_pml_info(const ras_pml_handle* h, ras_pml_info_t* info);
+
+/* Load vector F_i = int f phi_i (Section 1) of
+ *   f(x) = sum_s amps[s] * exp(-|x - c_s|^2 / width^2) cut to Omega_int,
+ * with c_s = (centres[2s], centres[2s+1]); centres and amps are host arrays of
+ * ns entries (ns >= 0). Writes n complex values to b_dev. */
+int ras_pml_assemble_rhs(ras_pml_handle* h, const double* centres_host,
+                         const double* amps_host, int ns, double width,
+                         rp_c128* b_dev);
+
+/* Assembles every local operator A_j (Section 2; impedance term of
+ * Section 3 (ii) when local_bc = 0) and factors it as A_j = L_j D_j L_j^T
+ * (no pivoting; A_j is complex symmetric) in the handle's factor precision.
+ * Returns RASPML_EPIVOT if a pivot is zero or non-finite (see info.bad_subdomain).
+ * Synchronises the stream. */
+int ras_pml_factor(ras_pml_handle* h);
+
+/* z = B^-1 r = sum_j R_j^T ( chi_j .* A_j^-1 (R_j r) )  (Section 2).
+ * r_dev, z_dev: n complex128 on device; they must not overlap.
+ * RASPML_ESTATE if not factored. */
+int ras_pml_apply(ras_pml_handle* h, const rp_c128* r_dev, rp_c128* z_dev);
+
+/* y = A x with the global matrix of eq. weak; x_dev, y_dev n complex128,
+ * must not overlap. */
+int ras_pml_matvec(ras_pml_handle* h, const rp_c128* x_dev, rp_c128* y_dev);
+
+/* Flexible GMRES (Section 4.1) with B^-1 as right preconditioner, in
+ * complex128 (Arnoldi by classical Gram-Schmidt applied twice, complex Givens
+ * rotations), on the device. x_dev holds x0 on entry and the solution on exit.
+ * Stops when the residual estimate ||b-Ax||/||b|| <= rtol or after maxit
+ * preconditioned directions (restart = 0: no restart; else the Krylov space
+ * is rebuilt every `restart` directions). rtol = 0 runs exactly maxit
+ * directions. *iters gets the number of directions, *relres the final true
+ * relative residual ||b - A x||_2 / ||b||_2 (computed in complex128).
+ * Factors first if needed. Returns 0, RASPML_NOT_CONVERGED, or an error. */
+int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev,
+                    double rtol, int maxit, int restart,
+                    int* iters, double* relres);
+
+/* helmholtz_solve on host buffers: copies b_host (and x0 from x_host) to the
+ * device, solves, and copies the solution back into x_host. */
+int helmholtz_solve_host(ras_pml_handle* h, const rp_c128* b_host, rp_c128* x_host,
+                         double rtol, int maxit, int restart,
+                         int* iters, double* relres);
+
+/* Algorithm 1 (discrete form): u <- u + B^-1 (b - A u) until
+ * ||b - A u||/||b|| <= rtol or maxit sweeps. x_dev: u0 in, u out. */
+int ras_pml_richardson(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev,
+                       double rtol, int maxit, int* iters, double* relres);
+
+/* Copies up to `cap` entries of the last solve's residual-estimate history
+ * (relative to ||b||; entry 0 is the initial residual) to hist_host and
+ * returns the count through *count. */
+int ras_pml_history(const ras_pml_handle* h, double* hist_host, int cap, int* count);
+
+/* Human-readable text for a status code (static storage). */
+const char* ras_pml_error_string(int status);
+
+/* Releases every device allocation of the handle (NULL is allowed). */
+void ras_pml_destroy(ras_pml_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RASPML_H */

@@ -1,0 +1,571 @@
+// Host side of libraspml: parameter validation, the Cartesian covering of
+// Section 2, device memory, and the flexible GMRES driver of Section 4.1.
+// Every arithmetic step runs in the kernels of assembly.cu, factor.cu,
+// apply.cu and krylov.cu; this file only sizes, launches and synchronises.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/raspml.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using rp::c128;
+using rp::c64;
+using rp::KState;
+using rp::SubDesc;
+
+struct ras_pml_handle {
+  ras_pml_params p{};
+  cudaStream_t st = nullptr;
+  int dev = 0;
+  rp::Geo geo{};
+  std::vector<SubDesc> subs_h;
+  SubDesc* subs_d = nullptr;
+  int nsub = 0, max_b = 0, max_bp = 0, max_npad = 0, max_n = 0;
+  long long n = 0, sum_npad = 0, sum_l = 0, sum_n = 0, sum_bn = 0;
+  c128 *D = nullptr, *CW = nullptr, *CS = nullptr, *CSW = nullptr;
+  void *L = nullptr, *dinv = nullptr, *Y = nullptr;
+  double* pivstats = nullptr;
+  rp::DevStatus* status = nullptr;
+  bool factored = false;
+  double min_pivot_ratio = 0.0;
+  int bad_sub = -1;
+  // Krylov workspace (capacity kcap directions)
+  int kcap = 0;
+  c128 *V = nullptr, *Z = nullptr, *H = nullptr, *sn = nullptr, *gvec = nullptr, *yv = nullptr;
+  c128 *partial = nullptr, *hbuf = nullptr;
+  double *cs = nullptr, *hist = nullptr, *scal = nullptr;
+  int hist_cap = 0;
+  KState* kst = nullptr;
+  KState* kst_host = nullptr;   // pinned
+  c128 *tmp_b = nullptr, *tmp_x = nullptr, *tmp_r = nullptr;
+  int last_iters = 0;
+  std::vector<double> hist_host;
+};
+
+namespace {
+
+#define RP_CUDA(call)                                                          \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) {                                                   \
+      std::fprintf(stderr, "raspml: %s failed: %s\n", #call, cudaGetErrorString(e_)); \
+      return e_ == cudaErrorMemoryAllocation ? RASPML_ENOMEM : RASPML_ECUDA;    \
+    }                                                                          \
+  } while (0)
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? RASPML_ENOMEM : RASPML_ECUDA;
+  }
+  return RASPML_OK;
+}
+#define RP_ALLOC(ptr, cnt)            \
+  do {                                \
+    int s_ = dalloc(&(ptr), (cnt));   \
+    if (s_ != RASPML_OK) return s_;   \
+  } while (0)
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+int law_cells(double k, double h) {
+  if (!(k > 1.0)) return 1;
+  int c = (int)std::floor(0.5 * std::log(k) / k / h + 0.5);
+  return c < 1 ? 1 : c;
+}
+
+struct Range {
+  int box_lo, box_hi, int_lo, int_hi, ext_lo, ext_hi;
+  bool lo_in, hi_in;
+};
+
+std::vector<Range> ranges(int M, int P, int o, int pml, bool* ok) {
+  std::vector<Range> out;
+  *ok = true;
+  for (int q = 0; q < P; ++q) {
+    Range r;
+    r.box_lo = rp::box_start(q, M, P);
+    r.box_hi = rp::box_start(q + 1, M, P);
+    if (q + 1 == P) r.box_hi = M;
+    r.lo_in = q > 0;
+    r.hi_in = q < P - 1;
+    if (r.box_hi - r.box_lo < 2 * o) *ok = false;
+    r.int_lo = r.box_lo - (r.lo_in ? o : 0);
+    r.int_hi = r.box_hi + (r.hi_in ? o : 0);
+    r.ext_lo = std::max(0, r.int_lo - (r.lo_in ? pml : 0));
+    r.ext_hi = std::min(M, r.int_hi + (r.hi_in ? pml : 0));
+    out.push_back(r);
+  }
+  return out;
+}
+
+int ensure_krylov(ras_pml_handle* h, int m, int maxit) {
+  if (h->kcap < m) {
+    dfree(h->V); dfree(h->Z); dfree(h->H); dfree(h->sn); dfree(h->gvec); dfree(h->yv);
+    dfree(h->partial); dfree(h->hbuf); dfree(h->cs);
+    h->kcap = 0;
+    RP_ALLOC(h->V, (size_t)(m + 1) * h->n);
+    RP_ALLOC(h->Z, (size_t)m * h->n);
+    RP_ALLOC(h->H, (size_t)(m + 1) * m);
+    RP_ALLOC(h->sn, (size_t)m);
+    RP_ALLOC(h->gvec, (size_t)m + 1);
+    RP_ALLOC(h->yv, (size_t)m);
+    RP_ALLOC(h->hbuf, (size_t)m + 1);
+    RP_ALLOC(h->cs, (size_t)m);
+    RP_ALLOC(h->partial, (size_t)(m + 1) * rp::dot_blocks());
+    h->kcap = m;
+  }
+  if (h->hist_cap < maxit + 1) {
+    dfree(h->hist);
+    RP_ALLOC(h->hist, (size_t)maxit + 1);
+    h->hist_cap = maxit + 1;
+  }
+  if (!h->kst) {
+    RP_ALLOC(h->kst, 1);
+    RP_ALLOC(h->scal, 4);
+    RP_CUDA(cudaMallocHost((void**)&h->kst_host, sizeof(KState)));
+  }
+  return RASPML_OK;
+}
+
+// *out = ||v||_2 (device double), through the deterministic dot kernels
+int dev_norm(ras_pml_handle* h, const c128* v, double* out, c128* hslot, const KState* kst) {
+  RP_CUDA(rp::launch_dots(v, h->n, 1, v, h->n, h->partial, kst, h->st));
+  RP_CUDA(rp::launch_norm_finish(h->partial, out, hslot, kst, h->st));
+  return RASPML_OK;
+}
+
+int check_status(ras_pml_handle* h) {
+  rp::DevStatus s;
+  RP_CUDA(cudaMemcpyAsync(&s, h->status, sizeof(s), cudaMemcpyDeviceToHost, h->st));
+  RP_CUDA(cudaStreamSynchronize(h->st));
+  if (s.timeout) return RASPML_ETIMEOUT;
+  return RASPML_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ras_pml_error_string(int s) {
+  switch (s) {
+    case RASPML_OK: return "success";
+    case RASPML_NOT_CONVERGED: return "not converged within maxit";
+    case RASPML_EBADARG: return "invalid argument";
+    case RASPML_ENOMEM: return "device out of memory";
+    case RASPML_ECUDA: return "CUDA runtime error";
+    case RASPML_EPIVOT: return "zero or non-finite pivot in a local factor";
+    case RASPML_ENAN: return "NaN or Inf in the residual";
+    case RASPML_ETIMEOUT: return "a bounded device-side wait timed out";
+    case RASPML_ESTATE: return "call out of order (not factored)";
+    default: return "unknown status";
+  }
+}
+
+void ras_pml_destroy(ras_pml_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->dev);
+  if (h->st) cudaStreamSynchronize(h->st);
+  dfree(h->subs_d); dfree(h->D); dfree(h->CW); dfree(h->CS); dfree(h->CSW);
+  dfree(h->L); dfree(h->dinv); dfree(h->Y); dfree(h->pivstats); dfree(h->status);
+  dfree(h->V); dfree(h->Z); dfree(h->H); dfree(h->sn); dfree(h->gvec); dfree(h->yv);
+  dfree(h->partial); dfree(h->hbuf); dfree(h->cs); dfree(h->hist); dfree(h->scal); dfree(h->kst);
+  dfree(h->tmp_b); dfree(h->tmp_x); dfree(h->tmp_r);
+  if (h->kst_host) cudaFreeHost(h->kst_host);
+  delete h;
+}
+
+int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) {
+  if (!pp || !out) return RASPML_EBADARG;
+  *out = nullptr;
+  const ras_pml_params& p = *pp;
+  if (!(p.k >= 0.0) || !(p.h > 0.0) || !(p.kappa_g >= 0.0) || !(p.x1 > p.x0) || !(p.y1 > p.y0) || p.px < 1 ||
+      p.py < 1 || !(p.g_ramp > 0.0) || !(p.g_amp >= 0.0) || (p.local_bc != 0 && p.local_bc != 1) ||
+      (p.factor_prec != 0 && p.factor_prec != 1))
+    return RASPML_EBADARG;
+  const double lx = p.x1 - p.x0 + 2 * p.kappa_g, ly = p.y1 - p.y0 + 2 * p.kappa_g;
+  const long long Mx = std::llround(lx / p.h), My = std::llround(ly / p.h);
+  if (Mx < 2 || My < 2 || std::fabs(Mx * p.h - lx) > 1e-9 * lx || std::fabs(My * p.h - ly) > 1e-9 * ly ||
+      Mx > (1 << 20) || My > (1 << 20))
+    return RASPML_EBADARG;
+  const int o = p.ovlp_cells < 0 ? law_cells(p.k, p.h) : p.ovlp_cells;
+  const int pml = p.pml_cells < 0 ? law_cells(p.k, p.h) : p.pml_cells;
+  if (o < 1 || pml < 0 || p.px > Mx || p.py > My) return RASPML_EBADARG;
+  bool okx, oky;
+  auto rx = ranges((int)Mx, p.px, o, pml, &okx);
+  auto ry = ranges((int)My, p.py, o, pml, &oky);
+  if (!okx || !oky) return RASPML_EBADARG;
+
+  ras_pml_handle* h = new ras_pml_handle();
+  h->p = p;
+  h->p.ovlp_cells = o;
+  h->p.pml_cells = pml;
+  h->st = (cudaStream_t)stream;
+  cudaGetDevice(&h->dev);
+  rp::Geo& g = h->geo;
+  g.X0 = p.x0 - p.kappa_g;
+  g.Y0 = p.y0 - p.kappa_g;
+  g.h = p.h;
+  g.hh = 0.5 * p.h;
+  g.x0 = p.x0; g.x1 = p.x1; g.y0 = p.y0; g.y1 = p.y1;
+  g.k = p.k; g.g_amp = p.g_amp; g.g_ramp = p.g_ramp;
+  g.Mx = (int)Mx; g.My = (int)My; g.nx = (int)Mx - 1; g.ny = (int)My - 1;
+  g.px = p.px; g.py = p.py; g.ovlp = o; g.pml = pml; g.local_bc = p.local_bc;
+  h->n = (long long)g.nx * g.ny;
+
+  const bool imp = p.local_bc == 0;
+  long long l_off = 0, v_off = 0;
+  for (int qy = 0; qy < p.py; ++qy) {
+    for (int qx = 0; qx < p.px; ++qx) {
+      const Range& X = rx[qx];
+      const Range& Yr = ry[qy];
+      SubDesc d{};
+      d.ext_lo_x = X.ext_lo; d.ext_hi_x = X.ext_hi; d.ext_lo_y = Yr.ext_lo; d.ext_hi_y = Yr.ext_hi;
+      d.int_lo_x = X.int_lo; d.int_hi_x = X.int_hi; d.int_lo_y = Yr.int_lo; d.int_hi_y = Yr.int_hi;
+      d.box_lo_x = X.box_lo; d.box_hi_x = X.box_hi; d.box_lo_y = Yr.box_lo; d.box_hi_y = Yr.box_hi;
+      d.flags = (X.lo_in ? rp::LO_X : 0) | (X.hi_in ? rp::HI_X : 0) | (Yr.lo_in ? rp::LO_Y : 0) |
+                (Yr.hi_in ? rp::HI_Y : 0);
+      int ix0 = imp ? X.ext_lo : X.ext_lo + 1, ix1 = imp ? X.ext_hi : X.ext_hi - 1;
+      int iy0 = imp ? Yr.ext_lo : Yr.ext_lo + 1, iy1 = imp ? Yr.ext_hi : Yr.ext_hi - 1;
+      ix0 = std::max(ix0, 1); iy0 = std::max(iy0, 1);
+      ix1 = std::min(ix1, g.Mx - 1); iy1 = std::min(iy1, g.My - 1);
+      if (ix1 < ix0 || iy1 < iy0) { delete h; return RASPML_EBADARG; }
+      d.ix0 = ix0; d.iy0 = iy0; d.nlx = ix1 - ix0 + 1; d.nly = iy1 - iy0 + 1;
+      d.n = d.nlx * d.nly;
+      d.npad = (d.n + 31) / 32 * 32;
+      d.b = d.nlx + 1;
+      d.bp = d.b + (d.b & 1);
+      if (d.b > rp::kMaxBand) { delete h; return RASPML_EBADARG; }
+      d.l_off = l_off;
+      d.v_off = v_off;
+      l_off += (long long)d.npad * d.bp;
+      v_off += d.npad;
+      h->max_b = std::max(h->max_b, d.b);
+      h->max_bp = std::max(h->max_bp, d.bp);
+      h->max_npad = std::max(h->max_npad, d.npad);
+      h->max_n = std::max(h->max_n, d.n);
+      h->sum_n += d.n;
+      h->sum_bn += (long long)d.b * d.n;
+      h->subs_h.push_back(d);
+    }
+  }
+  h->nsub = p.px * p.py;
+  h->sum_npad = v_off;
+  h->sum_l = l_off;
+
+  int s;
+#define SETUP_ALLOC(ptr, cnt) \
+  if ((s = dalloc(&(ptr), (cnt))) != RASPML_OK) { ras_pml_destroy(h); return s; }
+  cudaSetDevice(h->dev);
+  SETUP_ALLOC(h->subs_d, (size_t)h->nsub);
+  SETUP_ALLOC(h->D, (size_t)h->n);
+  SETUP_ALLOC(h->CW, (size_t)h->n);
+  SETUP_ALLOC(h->CS, (size_t)h->n);
+  SETUP_ALLOC(h->CSW, (size_t)h->n);
+  SETUP_ALLOC(h->pivstats, (size_t)2 * h->nsub);
+  SETUP_ALLOC(h->status, (size_t)1);
+  cudaError_t e = cudaMemcpyAsync(h->subs_d, h->subs_h.data(), sizeof(SubDesc) * h->nsub, cudaMemcpyHostToDevice,
+                                  h->st);
+  rp::DevStatus s0{-1, 0, 0, 0};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->status, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess) e = rp::launch_global_stencil(g, h->D, h->CW, h->CS, h->CSW, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "raspml: setup: %s\n", cudaGetErrorString(e));
+    ras_pml_destroy(h);
+    return RASPML_ECUDA;
+  }
+  *out = h;
+  return RASPML_OK;
+}
+
+int ras_pml_info(const ras_pml_handle* h, ras_pml_info_t* info) {
+  if (!h || !info) return RASPML_EBADARG;
+  std::memset(info, 0, sizeof(*info));
+  const double es = h->p.factor_prec == 0 ? 16.0 : 8.0;
+  info->n = h->n;
+  info->Mx = h->geo.Mx;
+  info->My = h->geo.My;
+  info->num_sub = h->nsub;
+  info->ovlp_cells = h->geo.ovlp;
+  info->pml_cells = h->geo.pml;
+  info->max_local_n = h->max_n;
+  info->max_band = h->max_b;
+  info->sum_local_n = h->sum_n;
+  info->sum_band_n = h->sum_bn;
+  info->factor_bytes = (int64_t)((h->sum_l + h->sum_npad) * es);
+  // L read in the forward and in the backward sweep, D^-1 once, r read once, z written once
+  info->apply_bytes = 2.0 * es * (double)h->sum_bn + es * (double)h->sum_n + 32.0 * (double)h->n;
+  info->min_pivot_ratio = h->min_pivot_ratio;
+  info->factored = h->factored ? 1 : 0;
+  info->factor_prec = h->p.factor_prec;
+  info->bad_subdomain = h->bad_sub;
+  info->last_iters = h->last_iters;
+  return RASPML_OK;
+}
+
+int ras_pml_assemble_rhs(ras_pml_handle* h, const double* centres, const double* amps, int ns, double width,
+                         rp_c128* b_dev) {
+  if (!h || !b_dev || ns < 0 || (ns > 0 && (!centres || !amps)) || !(width > 0.0)) return RASPML_EBADARG;
+  cudaSetDevice(h->dev);
+  double* buf = nullptr;
+  RP_ALLOC(buf, (size_t)3 * (ns > 0 ? ns : 1));
+  cudaError_t e = cudaSuccess;
+  if (ns > 0) {
+    e = cudaMemcpyAsync(buf, centres, sizeof(double) * 2 * ns, cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(buf + 2 * ns, amps, sizeof(double) * ns, cudaMemcpyHostToDevice, h->st);
+  }
+  if (e == cudaSuccess) e = rp::launch_rhs(h->geo, buf, buf + 2 * ns, ns, width, (c128*)b_dev, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  cudaFree(buf);
+  if (e != cudaSuccess) return RASPML_ECUDA;
+  return RASPML_OK;
+}
+
+int ras_pml_factor(ras_pml_handle* h) {
+  if (!h) return RASPML_EBADARG;
+  cudaSetDevice(h->dev);
+  const size_t es = h->p.factor_prec == 0 ? sizeof(c128) : sizeof(c64);
+  if (!h->L) {
+    void* p;
+    cudaError_t e = cudaMalloc(&p, (size_t)h->sum_l * es);
+    if (e != cudaSuccess) return RASPML_ENOMEM;
+    h->L = p;
+    e = cudaMalloc(&p, (size_t)h->sum_npad * es);
+    if (e != cudaSuccess) return RASPML_ENOMEM;
+    h->dinv = p;
+    e = cudaMalloc(&p, (size_t)h->sum_npad * es);
+    if (e != cudaSuccess) return RASPML_ENOMEM;
+    h->Y = p;
+  }
+  c128* Aloc = nullptr;
+  RP_ALLOC(Aloc, (size_t)4 * h->sum_npad);
+  rp::DevStatus s0{-1, 0, 0, 0};
+  cudaError_t e = cudaMemcpyAsync(h->status, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess) e = rp::launch_local_rows(h->geo, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
+  if (e == cudaSuccess)
+    e = rp::launch_factor(h->p.factor_prec, h->subs_d, h->nsub, h->max_b, Aloc, h->L, h->dinv, h->pivstats,
+                          h->status, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  cudaFree(Aloc);
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "raspml: factor: %s\n", cudaGetErrorString(e));
+    return RASPML_ECUDA;
+  }
+  rp::DevStatus st;
+  std::vector<double> piv(2 * h->nsub);
+  RP_CUDA(cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
+  RP_CUDA(cudaMemcpy(piv.data(), h->pivstats, sizeof(double) * piv.size(), cudaMemcpyDeviceToHost));
+  double mr = 1e300;
+  for (int j = 0; j < h->nsub; ++j) mr = std::min(mr, piv[2 * j] / piv[2 * j + 1]);
+  h->min_pivot_ratio = mr;
+  h->bad_sub = st.pivot_bad_sub;
+  if (st.pivot_bad_sub >= 0) {
+    h->factored = false;
+    return RASPML_EPIVOT;
+  }
+  h->factored = true;
+  return RASPML_OK;
+}
+
+int ras_pml_apply(ras_pml_handle* h, const rp_c128* r, rp_c128* z) {
+  if (!h || !r || !z || (const void*)r == (const void*)z) return RASPML_EBADARG;
+  if (!h->factored) return RASPML_ESTATE;
+  cudaSetDevice(h->dev);
+  RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->dinv,
+                           (const c128*)r, h->Y, (c128*)z, nullptr, h->status, h->st));
+  return RASPML_OK;
+}
+
+int ras_pml_matvec(ras_pml_handle* h, const rp_c128* x, rp_c128* y) {
+  if (!h || !x || !y || (const void*)x == (const void*)y) return RASPML_EBADARG;
+  cudaSetDevice(h->dev);
+  RP_CUDA(rp::launch_spmv(h->n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, (const c128*)x, nullptr, (c128*)y,
+                          nullptr, h->st));
+  return RASPML_OK;
+}
+
+int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, double rtol, int maxit, int restart,
+                    int* iters, double* relres) {
+  if (!h || !b_dev || !x_dev || maxit < 1 || restart < 0 || !(rtol >= 0.0)) return RASPML_EBADARG;
+  cudaSetDevice(h->dev);
+  if (!h->factored) {
+    int s = ras_pml_factor(h);
+    if (s != RASPML_OK) return s;
+  }
+  const int m = (restart > 0 && restart < maxit) ? restart : maxit;
+  int s = ensure_krylov(h, m, maxit);
+  if (s != RASPML_OK) return s;
+  const long long n = h->n;
+  const c128* b = (const c128*)b_dev;
+  c128* x = (c128*)x_dev;
+  cudaStream_t st = h->st;
+  const int ldh = m + 1;
+  KState k0{};
+  RP_CUDA(cudaMemcpyAsync(h->kst, &k0, sizeof(k0), cudaMemcpyHostToDevice, st));
+  s = dev_norm(h, b, &h->kst->bnorm, nullptr, nullptr);
+  if (s) return s;
+  RP_CUDA(cudaMemcpyAsync(h->kst_host, h->kst, sizeof(KState), cudaMemcpyDeviceToHost, st));
+  RP_CUDA(cudaStreamSynchronize(st));
+  const double bnorm = h->kst_host->bnorm;
+  h->hist_host.clear();
+  if (!(bnorm > 0.0)) {
+    RP_CUDA(cudaMemsetAsync(x, 0, sizeof(c128) * n, st));
+    RP_CUDA(cudaStreamSynchronize(st));
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    h->last_iters = 0;
+    return std::isfinite(bnorm) ? RASPML_OK : RASPML_ENAN;
+  }
+  const int batch = 4;
+  int status = RASPML_NOT_CONVERGED;
+  double rel = NAN;
+  for (;;) {
+    // new cycle: V0 = b - A x, beta = ||V0||, g = beta e1, V0 /= beta
+    c128* V0 = h->V;
+    RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, x, b, V0, nullptr, st));
+    if ((s = dev_norm(h, V0, &h->kst->hnorm, nullptr, nullptr))) return s;
+    RP_CUDA(rp::launch_cycle_init(h->kst, h->gvec, m, rtol, h->hist, st));
+    RP_CUDA(rp::launch_scale_inv(V0, n, &h->kst->hnorm, h->kst, st));
+    for (int j = 0; j < m;) {
+      const int nb = std::min(batch, m - j);
+      for (int jj = j; jj < j + nb; ++jj) {
+        c128* vj = h->V + (size_t)jj * n;
+        c128* zj = h->Z + (size_t)jj * n;
+        c128* w = h->V + (size_t)(jj + 1) * n;
+        c128* hcol = h->H + (size_t)jj * ldh;
+        RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L,
+                                 h->dinv, vj, h->Y, zj, h->kst, h->status, st));
+        RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, nullptr, w, h->kst, st));
+        // classical Gram-Schmidt, twice
+        RP_CUDA(rp::launch_dots(h->V, n, jj + 1, w, n, h->partial, h->kst, st));
+        RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, hcol, 0, h->kst, st));
+        RP_CUDA(rp::launch_axpys(h->V, n, jj + 1, hcol, -1.0, w, n, h->kst, st));
+        RP_CUDA(rp::launch_dots(h->V, n, jj + 1, w, n, h->partial, h->kst, st));
+        RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, h->hbuf, 0, h->kst, st));
+        RP_CUDA(rp::launch_axpys(h->V, n, jj + 1, h->hbuf, -1.0, w, n, h->kst, st));
+        RP_CUDA(rp::launch_add(hcol, h->hbuf, jj + 1, h->kst, st));
+        if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst))) return s;
+        RP_CUDA(rp::launch_givens(h->kst, h->H, ldh, h->cs, h->sn, h->gvec, jj, rtol, m, maxit, h->hist, st));
+        RP_CUDA(rp::launch_scale_inv(w, n, &h->kst->hnorm, h->kst, st));
+      }
+      j += nb;
+      RP_CUDA(cudaMemcpyAsync(h->kst_host, h->kst, sizeof(KState), cudaMemcpyDeviceToHost, st));
+      RP_CUDA(cudaStreamSynchronize(st));
+      if (h->kst_host->stop) break;
+    }
+    const KState ks = *h->kst_host;
+    // x += Z y with y = H^-1 g
+    if (ks.jdone > 0) {
+      RP_CUDA(rp::launch_backsolve(h->H, ldh, h->gvec, h->kst, h->yv, st));
+      RP_CUDA(rp::launch_axpys(h->Z, n, ks.jdone, h->yv, 1.0, x, n, nullptr, st));
+    }
+    // true residual
+    RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, x, b, h->V, nullptr, st));
+    if ((s = dev_norm(h, h->V, h->scal, nullptr, nullptr))) return s;
+    double rn = 0.0;
+    RP_CUDA(cudaMemcpyAsync(&rn, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    RP_CUDA(cudaStreamSynchronize(st));
+    rel = rn / bnorm;
+    if (!std::isfinite(rel) || ks.nan) { status = RASPML_ENAN; break; }
+    if (rtol > 0.0 && rel <= rtol) { status = RASPML_OK; break; }
+    if (ks.total >= maxit) { status = RASPML_NOT_CONVERGED; break; }
+    if (ks.breakdown && ks.jdone == 0) { status = RASPML_NOT_CONVERGED; break; }
+  }
+  const int total = h->kst_host->total;
+  h->last_iters = total;
+  h->hist_host.resize(total + 1);
+  RP_CUDA(cudaMemcpy(h->hist_host.data(), h->hist, sizeof(double) * (total + 1), cudaMemcpyDeviceToHost));
+  if (iters) *iters = total;
+  if (relres) *relres = rel;
+  int ts = check_status(h);
+  if (ts != RASPML_OK) return ts;
+  return status;
+}
+
+int helmholtz_solve_host(ras_pml_handle* h, const rp_c128* b_host, rp_c128* x_host, double rtol, int maxit,
+                         int restart, int* iters, double* relres) {
+  if (!h || !b_host || !x_host) return RASPML_EBADARG;
+  cudaSetDevice(h->dev);
+  if (!h->tmp_b) {
+    RP_ALLOC(h->tmp_b, (size_t)h->n);
+    RP_ALLOC(h->tmp_x, (size_t)h->n);
+  }
+  const size_t bytes = sizeof(c128) * h->n;
+  RP_CUDA(cudaMemcpyAsync(h->tmp_b, b_host, bytes, cudaMemcpyHostToDevice, h->st));
+  RP_CUDA(cudaMemcpyAsync(h->tmp_x, x_host, bytes, cudaMemcpyHostToDevice, h->st));
+  int s = helmholtz_solve(h, (const rp_c128*)h->tmp_b, (rp_c128*)h->tmp_x, rtol, maxit, restart, iters, relres);
+  if (s < 0) return s;
+  RP_CUDA(cudaMemcpyAsync(x_host, h->tmp_x, bytes, cudaMemcpyDeviceToHost, h->st));
+  RP_CUDA(cudaStreamSynchronize(h->st));
+  return s;
+}
+
+int ras_pml_richardson(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, double rtol, int maxit, int* iters,
+                       double* relres) {
+  if (!h || !b_dev || !x_dev || maxit < 0 || !(rtol >= 0.0)) return RASPML_EBADARG;
+  cudaSetDevice(h->dev);
+  if (!h->factored) {
+    int s = ras_pml_factor(h);
+    if (s != RASPML_OK) return s;
+  }
+  int s = ensure_krylov(h, 1, maxit);
+  if (s) return s;
+  if (!h->tmp_r) RP_ALLOC(h->tmp_r, (size_t)h->n);
+  const long long n = h->n;
+  const c128* b = (const c128*)b_dev;
+  c128* x = (c128*)x_dev;
+  if ((s = dev_norm(h, b, h->scal, nullptr, nullptr))) return s;
+  double bn = 0.0;
+  RP_CUDA(cudaMemcpyAsync(&bn, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  RP_CUDA(cudaStreamSynchronize(h->st));
+  h->hist_host.clear();
+  int it = 0;
+  double rel = 0.0;
+  int status = RASPML_NOT_CONVERGED;
+  for (;; ++it) {
+    RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, x, b, h->tmp_r, nullptr, h->st));
+    if ((s = dev_norm(h, h->tmp_r, h->scal, nullptr, nullptr))) return s;
+    double rn = 0.0;
+    RP_CUDA(cudaMemcpyAsync(&rn, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    RP_CUDA(cudaStreamSynchronize(h->st));
+    rel = bn > 0.0 ? rn / bn : 0.0;
+    h->hist_host.push_back(rel);
+    if (!std::isfinite(rel)) { status = RASPML_ENAN; break; }
+    if (rel <= rtol) { status = RASPML_OK; break; }
+    if (it >= maxit) break;
+    RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->dinv,
+                             h->tmp_r, h->Y, h->V, nullptr, h->status, h->st));
+    RP_CUDA(rp::launch_axpy_state(x, h->V, n, h->st));
+  }
+  h->last_iters = it;
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  int ts = check_status(h);
+  if (ts != RASPML_OK) return ts;
+  return status;
+}
+
+int ras_pml_history(const ras_pml_handle* h, double* hist_host, int cap, int* count) {
+  if (!h || (!hist_host && cap > 0) || !count) return RASPML_EBADARG;
+  int c = (int)std::min<size_t>(h->hist_host.size(), (size_t)std::max(cap, 0));
+  if (c > 0) std::memcpy(hist_host, h->hist_host.data(), sizeof(double) * c);
+  *count = (int)h->hist_host.size();
+  return RASPML_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,229 @@
+// Assembly kernels (paper Section 1, eq. weak; Section 2, local forms a_j;
+// Section 3 (ii), impedance closure).
+//
+// The bilinear form is eq. weak multiplied by gamma_1 gamma_2 (complex
+// symmetric, same solution):
+//   a(u,v) = int (g2/g1) u_x v_x + (g1/g2) u_y v_y - k^2 g1 g2 u v
+// on P1 triangles (cells split along the (i,j)-(i+1,j+1) diagonal), every
+// element integral by the edge-midpoint rule. Rows are built node by node
+// from the four cells around the node, so every kernel writes its own
+// output with no atomics. Only the diagonal and the couplings to the W, S and
+// SW neighbours are produced; symmetry gives the rest.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rp {
+
+namespace {
+
+// Element quantities of the two triangles of one cell, from the stretching
+// at the cell's edge midpoints. K* are (1/h^2) int_T of the stiffness
+// coefficients, mu* = (h^2/6) g1 g2 at a midpoint (the midpoint-rule weight
+// of the mass term).
+struct CellTerms {
+  c128 KxL, KyL, KxU, KyU;
+  c128 m01, m12, m02, m23, m03;
+};
+
+template <class S>
+__device__ CellTerms cell_terms(const Geo& g, const S& st, int ci, int cj) {
+  // x positions: 2ci (left edge), 2ci+1 (middle), 2ci+2 (right edge)
+  c128 xa = st.gx(2.0 * ci + 1.0), xb = st.gx(2.0 * ci + 2.0), xc = st.gx(2.0 * ci);
+  c128 ya = st.gy(2.0 * cj), yb = st.gy(2.0 * cj + 1.0), yc = st.gy(2.0 * cj + 2.0);
+  const double sixth = 1.0 / 6.0;
+  const double w = g.h * g.h * sixth;
+  CellTerms t;
+  // lower triangle: m01 = (xa, ya), m12 = (xb, yb), m02 = (xa, yb)
+  t.KxL = sixth * (cdiv(ya, xa) + cdiv(yb, xb) + cdiv(yb, xa));
+  t.KyL = sixth * (cdiv(xa, ya) + cdiv(xb, yb) + cdiv(xa, yb));
+  // upper triangle: m02 = (xa, yb), m23 = (xa, yc), m03 = (xc, yb)
+  t.KxU = sixth * (cdiv(yb, xa) + cdiv(yc, xa) + cdiv(yb, xc));
+  t.KyU = sixth * (cdiv(xa, yb) + cdiv(xa, yc) + cdiv(xc, yb));
+  t.m01 = w * (xa * ya);
+  t.m12 = w * (xb * yb);
+  t.m02 = w * (xa * yb);
+  t.m23 = w * (xa * yc);
+  t.m03 = w * (xc * yb);
+  return t;
+}
+
+struct GlobalStretch {
+  Geo g;
+  __device__ c128 gx(double s) const { return gam_global_x(g, s); }
+  __device__ c128 gy(double s) const { return gam_global_y(g, s); }
+  __device__ bool cell_ok(int ci, int cj) const { return ci >= 0 && ci < g.Mx && cj >= 0 && cj < g.My; }
+};
+
+struct LocalStretch {
+  Geo g;
+  SubDesc sd;
+  __device__ c128 gx(double s) const { return gam_local_x(g, sd, s); }
+  __device__ c128 gy(double s) const { return gam_local_y(g, sd, s); }
+  __device__ bool cell_ok(int ci, int cj) const {
+    return ci >= sd.ext_lo_x && ci < sd.ext_hi_x && cj >= sd.ext_lo_y && cj < sd.ext_hi_y;
+  }
+};
+
+// Diagonal and lower couplings of node (i, j) from the cells around it.
+template <class S>
+__device__ void node_row(const Geo& g, const S& st, int i, int j, c128& D, c128& W, c128& Sx, c128& SW) {
+  const double q = 0.25 * g.k * g.k;  // k^2 * (hat product 1/2 * 1/2)
+  D = W = Sx = SW = mk(0.0, 0.0);
+  if (st.cell_ok(i, j)) {
+    CellTerms t = cell_terms(g, st, i, j);
+    D = D + t.KxL - q * (t.m01 + t.m02) + t.KyU - q * (t.m02 + t.m03);
+  }
+  if (st.cell_ok(i - 1, j)) {
+    CellTerms t = cell_terms(g, st, i - 1, j);
+    D = D + t.KxL + t.KyL - q * (t.m01 + t.m12);
+    W = W - t.KxL - q * t.m01;
+  }
+  if (st.cell_ok(i, j - 1)) {
+    CellTerms t = cell_terms(g, st, i, j - 1);
+    D = D + t.KxU + t.KyU - q * (t.m23 + t.m03);
+    Sx = Sx - t.KyU - q * t.m03;
+  }
+  if (st.cell_ok(i - 1, j - 1)) {
+    CellTerms t = cell_terms(g, st, i - 1, j - 1);
+    D = D + t.KyL - q * (t.m12 + t.m02) + t.KxU - q * (t.m02 + t.m23);
+    W = W - t.KxU - q * t.m23;
+    Sx = Sx - t.KyL - q * t.m12;
+    SW = SW - q * (t.m02 + t.m02);
+  }
+}
+
+// Impedance closure (Section 3 (ii)): -i k int gamma_t phi_a phi_b ds on the
+// edges of the artificial boundary of Omega_j, 2-point Gauss per edge.
+__device__ void impedance_terms(const Geo& g, const SubDesc& sd, const LocalStretch& st, int i, int j,
+                                c128& D, c128& W, c128& Sx) {
+  const double q1 = 0.5 - 0.5 / sqrt(3.0), q2 = 0.5 + 0.5 / sqrt(3.0);
+  const c128 mik = mk(0.0, -g.k * 0.5 * g.h);  // -i k * (h/2): Gauss weight h/2
+  // vertical sides x = const: tangential stretch gamma_2
+  bool left = sd.ext_lo_x > 0 && i == sd.ext_lo_x;
+  bool right = sd.ext_hi_x < g.Mx && i == sd.ext_hi_x;
+  if (left || right) {
+    if (j - 1 >= sd.ext_lo_y) {  // edge (i,j-1)-(i,j): node is its upper end
+      int jc = j - 1;
+      c128 a = st.gy(2.0 * (jc + q1)), b = st.gy(2.0 * (jc + q2));
+      D = D + mik * (q1 * q1 * a + q2 * q2 * b);
+      Sx = Sx + mik * ((q1 * (1.0 - q1)) * a + (q2 * (1.0 - q2)) * b);
+    }
+    if (j < sd.ext_hi_y) {       // edge (i,j)-(i,j+1): node is its lower end
+      c128 a = st.gy(2.0 * (j + q1)), b = st.gy(2.0 * (j + q2));
+      D = D + mik * ((1.0 - q1) * (1.0 - q1) * a + (1.0 - q2) * (1.0 - q2) * b);
+    }
+  }
+  // horizontal sides y = const: tangential stretch gamma_1
+  bool bottom = sd.ext_lo_y > 0 && j == sd.ext_lo_y;
+  bool top = sd.ext_hi_y < g.My && j == sd.ext_hi_y;
+  if (bottom || top) {
+    if (i - 1 >= sd.ext_lo_x) {
+      int ic = i - 1;
+      c128 a = st.gx(2.0 * (ic + q1)), b = st.gx(2.0 * (ic + q2));
+      D = D + mik * (q1 * q1 * a + q2 * q2 * b);
+      W = W + mik * ((q1 * (1.0 - q1)) * a + (q2 * (1.0 - q2)) * b);
+    }
+    if (i < sd.ext_hi_x) {
+      c128 a = st.gx(2.0 * (i + q1)), b = st.gx(2.0 * (i + q2));
+      D = D + mik * ((1.0 - q1) * (1.0 - q1) * a + (1.0 - q2) * (1.0 - q2) * b);
+    }
+  }
+}
+
+__global__ void k_global_stencil(Geo g, c128* __restrict__ D, c128* __restrict__ CW, c128* __restrict__ CS,
+                                 c128* __restrict__ CSW) {
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long n = (long long)g.nx * g.ny;
+  if (r >= n) return;
+  int i = (int)(r % g.nx) + 1, j = (int)(r / g.nx) + 1;
+  GlobalStretch st{g};
+  c128 d, w, s, sw;
+  node_row(g, st, i, j, d, w, s, sw);
+  const c128 z = mk(0.0, 0.0);
+  D[r] = d;
+  CW[r] = (i > 1) ? w : z;            // couplings to outer-boundary nodes drop out
+  CS[r] = (j > 1) ? s : z;
+  CSW[r] = (i > 1 && j > 1) ? sw : z;
+}
+
+// One thread per local row; blockIdx.y = subdomain. Output Aloc[v_off + r]
+// = {D, W, S, SW}; padding rows (r >= n) are identity rows.
+__global__ void k_local_rows(Geo g, const SubDesc* __restrict__ subs, c128* __restrict__ Aloc) {
+  const SubDesc sd = subs[blockIdx.y];
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= sd.npad) return;
+  c128* out = Aloc + 4 * (sd.v_off + r);
+  const c128 z = mk(0.0, 0.0);
+  if (r >= sd.n) {
+    out[0] = mk(1.0, 0.0);
+    out[1] = out[2] = out[3] = z;
+    return;
+  }
+  int i = sd.ix0 + r % sd.nlx, j = sd.iy0 + r / sd.nlx;
+  LocalStretch st{g, sd};
+  c128 d, w, s, sw;
+  node_row(g, st, i, j, d, w, s, sw);
+  if (g.local_bc == 0) impedance_terms(g, sd, st, i, j, d, w, s);
+  out[0] = d;
+  out[1] = (i > sd.ix0) ? w : z;
+  out[2] = (j > sd.iy0) ? s : z;
+  out[3] = (i > sd.ix0 && j > sd.iy0) ? sw : z;
+}
+
+// f at half-index (sx, sy): sum of Gaussians, cut to the closed Omega_int.
+__device__ double source_at(const Geo& g, const double* __restrict__ cen, const double* __restrict__ amp, int ns,
+                            double inv_w2, double sx, double sy) {
+  double x = xpos(g, sx), y = ypos(g, sy);
+  if (!(x >= g.x0 && x <= g.x1 && y >= g.y0 && y <= g.y1)) return 0.0;
+  double f = 0.0;
+  for (int s = 0; s < ns; ++s) {
+    double dx = x - cen[2 * s], dy = y - cen[2 * s + 1];
+    f += amp[s] * exp(-(dx * dx + dy * dy) * inv_w2);
+  }
+  return f;
+}
+
+// F_i = int f phi_i: each of the node's six edges has its midpoint in two
+// triangles with phi_i = 1/2 there, so F_i = (h^2/6) sum_edges f(midpoint).
+__global__ void k_rhs(Geo g, const double* __restrict__ cen, const double* __restrict__ amp, int ns, double width,
+                      c128* __restrict__ b) {
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long n = (long long)g.nx * g.ny;
+  if (r >= n) return;
+  int i = (int)(r % g.nx) + 1, j = (int)(r / g.nx) + 1;
+  double iw2 = 1.0 / (width * width);
+  double si = 2.0 * i, sj = 2.0 * j;
+  double f = source_at(g, cen, amp, ns, iw2, si + 1, sj) + source_at(g, cen, amp, ns, iw2, si - 1, sj) +
+             source_at(g, cen, amp, ns, iw2, si, sj + 1) + source_at(g, cen, amp, ns, iw2, si, sj - 1) +
+             source_at(g, cen, amp, ns, iw2, si + 1, sj + 1) + source_at(g, cen, amp, ns, iw2, si - 1, sj - 1);
+  b[r] = mk(f * (g.h * g.h / 6.0), 0.0);
+}
+
+}  // namespace
+
+cudaError_t launch_global_stencil(const Geo& g, c128* D, c128* CW, c128* CS, c128* CSW, cudaStream_t st) {
+  long long n = (long long)g.nx * g.ny;
+  int threads = 256;
+  unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  k_global_stencil<<<blocks, threads, 0, st>>>(g, D, CW, CS, CSW);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_local_rows(const Geo& g, const SubDesc* subs, int nsub, int max_npad, c128* Aloc,
+                              cudaStream_t st) {
+  int threads = 128;
+  dim3 grid((max_npad + threads - 1) / threads, nsub);
+  k_local_rows<<<grid, threads, 0, st>>>(g, subs, Aloc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs(const Geo& g, const double* cen, const double* amp, int ns, double width, c128* b,
+                       cudaStream_t st) {
+  long long n = (long long)g.nx * g.ny;
+  int threads = 256;
+  unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  k_rhs<<<blocks, threads, 0, st>>>(g, cen, amp, ns, width, b);
+  return cudaGetLastError();
+}
+
+}  // namespace rp

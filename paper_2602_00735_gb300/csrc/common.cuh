@@ -1,0 +1,233 @@
+// Shared device-side definitions of libraspml: complex arithmetic, the mesh
+// geometry, per-subdomain descriptors, the PML stretching and the PTX helpers
+// for bulk (TMA) copies with mbarrier completion.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rp {
+
+// ---------------------------------------------------------------------------
+// Complex numbers in interleaved (re, im) layout, float or double.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct __align__(2 * sizeof(R)) cx {
+  R re, im;
+};
+using c64 = cx<float>;
+using c128 = cx<double>;
+
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> mk(R a, R b) { return cx<R>{a, b}; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> conj(cx<R> a) { return {a.re, -a.im}; }
+template <typename R>
+__host__ __device__ __forceinline__ R abs2(cx<R> a) { return a.re * a.re + a.im * a.im; }
+// acc - a*b with fused multiply-adds
+template <typename R>
+__device__ __forceinline__ cx<R> fms(cx<R> acc, cx<R> a, cx<R> b) {
+  acc.re = fma(-a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(-a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+// acc + conj(a)*b
+template <typename R>
+__device__ __forceinline__ cx<R> fcma(cx<R> acc, cx<R> a, cx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> cdiv(cx<R> a, cx<R> b) {
+  R d = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> crecip(cx<R> b) {
+  R d = b.re * b.re + b.im * b.im;
+  return {b.re / d, -b.im / d};
+}
+template <typename To, typename From>
+__host__ __device__ __forceinline__ cx<To> cvt(cx<From> a) { return {(To)a.re, (To)a.im}; }
+
+template <typename R>
+__device__ __forceinline__ cx<R> shfl(cx<R> v, int src) {
+  return {__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
+}
+
+// ---------------------------------------------------------------------------
+// Geometry: Omega = [X0, X0 + Mx h] x [Y0, Y0 + My h]; positions in half-cell
+// index units s (x = X0 + s*hh, hh = h/2). Coordinates are formed with
+// explicitly rounded multiply and add (no contraction), so that a position
+// equals the one a plain two-step evaluation gives.
+// ---------------------------------------------------------------------------
+struct Geo {
+  double X0, Y0, h, hh;
+  double x0, x1, y0, y1;    // Omega_int
+  double k, g_amp, g_ramp;
+  int Mx, My, nx, ny;       // nx = Mx - 1 unknowns per grid row
+  int px, py, ovlp, pml;
+  int local_bc;
+};
+
+enum : int { LO_X = 1, HI_X = 2, LO_Y = 4, HI_Y = 8 };
+
+// One subdomain of the covering (Section 2). Cell ranges are half-open
+// [lo, hi) in cells, i.e. node ranges [lo, hi].
+struct SubDesc {
+  int ext_lo_x, ext_hi_x, ext_lo_y, ext_hi_y;   // Omega_j
+  int int_lo_x, int_hi_x, int_lo_y, int_hi_y;   // Omega_j,int
+  int box_lo_x, box_hi_x, box_lo_y, box_hi_y;   // non-overlapping box
+  int flags;                                    // LO_X|HI_X|LO_Y|HI_Y: interior sides
+  int ix0, iy0, nlx, nly;                       // local unknown nodes
+  int n;                                        // nlx*nly
+  int npad;                                     // n rounded up to 32
+  int b;                                        // half-bandwidth nlx + 1
+  int bp;                                       // L column stride (b rounded up to even)
+  long long l_off;                              // element offset of L_j
+  long long v_off;                              // element offset of per-row arrays
+};
+
+__device__ __forceinline__ double xpos(const Geo& g, double s) {
+  return __dadd_rn(g.X0, __dmul_rn(s, g.hh));
+}
+__device__ __forceinline__ double ypos(const Geo& g, double s) {
+  return __dadd_rn(g.Y0, __dmul_rn(s, g.hh));
+}
+
+// g'(d) = amp (3t^2 - 2t^3), t = min(d/ramp, 1), zero for d <= 0.
+__device__ __forceinline__ double gprime(double d, double amp, double ramp) {
+  if (!(d > 0.0)) return 0.0;
+  double t = fmin(d / ramp, 1.0);
+  return amp * t * t * (3.0 - 2.0 * t);
+}
+
+// Global stretching gamma_1(x) = 1 + i g'(distance of x beyond (x0, x1)).
+__device__ __forceinline__ c128 gam_global_x(const Geo& g, double s) {
+  double x = xpos(g, s);
+  double d = fmax(fmax(g.x0 - x, x - g.x1), 0.0);
+  return mk(1.0, gprime(d, g.g_amp, g.g_ramp));
+}
+__device__ __forceinline__ c128 gam_global_y(const Geo& g, double s) {
+  double y = ypos(g, s);
+  double d = fmax(fmax(g.y0 - y, y - g.y1), 0.0);
+  return mk(1.0, gprime(d, g.g_amp, g.g_ramp));
+}
+
+// Local stretching g_j (Section 2): restarts beyond an interior side of
+// Omega_j,int; the global stretching elsewhere.
+__device__ __forceinline__ c128 gam_local_x(const Geo& g, const SubDesc& sd, double s) {
+  if ((sd.flags & HI_X) && s >= 2.0 * sd.int_hi_x)
+    return mk(1.0, gprime((s - 2.0 * sd.int_hi_x) * g.hh, g.g_amp, g.g_ramp));
+  if ((sd.flags & LO_X) && s <= 2.0 * sd.int_lo_x)
+    return mk(1.0, gprime((2.0 * sd.int_lo_x - s) * g.hh, g.g_amp, g.g_ramp));
+  return gam_global_x(g, s);
+}
+__device__ __forceinline__ c128 gam_local_y(const Geo& g, const SubDesc& sd, double s) {
+  if ((sd.flags & HI_Y) && s >= 2.0 * sd.int_hi_y)
+    return mk(1.0, gprime((s - 2.0 * sd.int_hi_y) * g.hh, g.g_amp, g.g_ramp));
+  if ((sd.flags & LO_Y) && s <= 2.0 * sd.int_lo_y)
+    return mk(1.0, gprime((2.0 * sd.int_lo_y - s) * g.hh, g.g_amp, g.g_ramp));
+  return gam_global_y(g, s);
+}
+
+// Partition-of-unity weight chi_j at node (i, j) (Section 2, linear ramps
+// across the 2*ovlp-cell overlap strips, Section 4).
+__device__ __forceinline__ double pou_weight(const SubDesc& sd, int i, int j, int o) {
+  double inv = 1.0 / (2.0 * o);
+  double wx = 1.0, wy = 1.0;
+  if ((sd.flags & LO_X) && i < sd.box_lo_x + o) wx = (double)(i - (sd.box_lo_x - o)) * inv;
+  if ((sd.flags & HI_X) && i > sd.box_hi_x - o) wx = (double)((sd.box_hi_x + o) - i) * inv;
+  if ((sd.flags & LO_Y) && j < sd.box_lo_y + o) wy = (double)(j - (sd.box_lo_y - o)) * inv;
+  if ((sd.flags & HI_Y) && j > sd.box_hi_y - o) wy = (double)((sd.box_hi_y + o) - j) * inv;
+  wx = fmin(fmax(wx, 0.0), 1.0);
+  wy = fmin(fmax(wy, 0.0), 1.0);
+  return wx * wy;
+}
+
+// Box index of node i for M cells split into P boxes (first M mod P boxes
+// one cell wider); a node on a box edge belongs to the upper box.
+__host__ __device__ __forceinline__ int box_of_node(int i, int M, int P) {
+  int base = M / P, extra = M % P;
+  int split = extra * (base + 1);
+  int p = (i < split) ? i / (base + 1) : extra + (i - split) / base;
+  return p < P ? p : P - 1;
+}
+__host__ __device__ __forceinline__ int box_start(int p, int M, int P) {
+  int base = M / P, extra = M % P;
+  return p * base + (p < extra ? p : extra);
+}
+
+// Device status words shared by the kernels of one handle.
+struct DevStatus {
+  int pivot_bad_sub;    // first subdomain with a zero / non-finite pivot, else -1
+  int timeout;          // a bounded wait gave up
+  int nan;              // non-finite value seen
+  int pad;
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers: mbarrier and one-dimensional bulk copies (TMA engine).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after ~2^31 SM clock cycles (about a second at the
+// GB300 clock); returns false on time-out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Global -> shared bulk copy of `bytes` (multiple of 16, both addresses
+// 16-byte aligned), completion signalled on `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+}  // namespace rp

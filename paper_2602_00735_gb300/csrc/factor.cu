@@ -1,0 +1,156 @@
+// Batched band LDL^T factorisation of the local operators A_j (the local
+// solves A_j^-1 of the preconditioner, Section 2). A_j is complex symmetric
+// (the gamma_1 gamma_2 form), so A_j = L_j D_j L_j^T without pivoting; with
+// the x-fastest local numbering its half-bandwidth is b = nlx + 1.
+//
+// One CTA factors one subdomain, right-looking, holding the active
+// (b+1) x (b+1) window of the matrix in shared memory as a circular buffer:
+// row/column index i lives in slot i mod (b+1). Step k
+//   1. reads the pivot column c_i = W(k+i, k), d = c_0, l_i = c_i / d,
+//      and writes L(:, k) = l and D^-1(k) = 1/d to global memory;
+//   2. applies the rank-1 update W(k+i, k+j) -= c_i l_j, 1 <= j <= i <= b;
+//   3. moves row k+b+1 of A_j into the slot freed by row k.
+// Output layout: L_j column k at l_off + k*bp (bp >= b, entries b..bp-1 are
+// zero), rows k+1..k+b; D^-1 at v_off + k. Rows n..npad-1 are identity
+// padding, so their L columns are zero.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rp {
+
+namespace {
+
+constexpr int kFactorThreads = 256;
+
+template <typename R>
+__device__ __forceinline__ cx<R> aloc_val(const c128* __restrict__ A, const SubDesc& sd, int row, int t) {
+  // entry (row, row - t) of A_j, t in [0, b]; rows >= n are identity
+  if (row >= sd.n) return (t == 0) ? mk((R)1, (R)0) : mk((R)0, (R)0);
+  const c128* a = A + 4 * (sd.v_off + row);
+  c128 v = mk(0.0, 0.0);
+  if (t == 0) v = a[0];
+  if (t == 1) v = v + a[1];
+  if (t == sd.b - 1) v = v + a[2];
+  if (t == sd.b) v = v + a[3];
+  return cvt<R>(v);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kFactorThreads)
+    k_factor_ldlt(const SubDesc* __restrict__ subs, const c128* __restrict__ Aloc, cx<R>* __restrict__ Lall,
+                  cx<R>* __restrict__ dinv_all, double* __restrict__ pivstats, DevStatus* status) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const SubDesc sd = subs[blockIdx.x];
+  const int tid = threadIdx.x;
+  const int b = sd.b, Wc = b + 1, bp = sd.bp;
+  const int npairs = b * (b + 1) / 2;
+  cx<R>* W = reinterpret_cast<cx<R>*>(sm);          // W[colslot * Wc + rowslot]
+  cx<R>* cbuf = W + Wc * Wc;
+  cx<R>* lbuf = cbuf + Wc;
+  uint16_t* pairs = reinterpret_cast<uint16_t*>(lbuf + Wc);
+  cx<R>* L = Lall + sd.l_off;
+  cx<R>* dv = dinv_all + sd.v_off;
+
+  // (i', j') with 1 <= j' <= i' <= b, column by column
+  for (int e = tid; e < npairs; e += blockDim.x) {
+    int j = 1, start = 0;
+    while (start + (b - j + 1) <= e) {
+      start += b - j + 1;
+      ++j;
+    }
+    int i = j + (e - start);
+    pairs[e] = (uint16_t)((i << 8) | j);
+  }
+  for (int e = tid; e < Wc * Wc; e += blockDim.x) W[e] = mk((R)0, (R)0);
+  __syncthreads();
+  // rows 0..b of A_j: row r at slot r
+  if (tid <= b) {
+    const int r = tid;
+    for (int t = 0; t <= b && t <= r; ++t) {
+      cx<R> v = aloc_val<R>(Aloc, sd, r, t);
+      if (v.re != (R)0 || v.im != (R)0) W[(r - t) * Wc + r] = v;
+    }
+  }
+  __syncthreads();
+
+  double dmin = 1e300, dmax = 0.0;
+  bool bad = false;
+  int pk = 0;  // slot of row k
+  for (int k = 0; k < sd.npad; ++k) {
+    // 1. pivot column
+    if (tid <= b) {
+      int s = pk + tid;
+      if (s >= Wc) s -= Wc;
+      cx<R> c = W[pk * Wc + s];
+      cx<R> d = W[pk * Wc + pk];
+      cx<R> di = crecip(d);
+      cbuf[tid] = c;
+      if (tid == 0) {
+        double ad = sqrt((double)abs2(d));
+        if (!(ad > 0.0) || !isfinite(ad) || !isfinite((double)di.re) || !isfinite((double)di.im)) bad = true;
+        dmin = fmin(dmin, ad);
+        dmax = fmax(dmax, ad);
+        dv[k] = di;
+        if (bp > b) L[(long long)k * bp + b] = mk((R)0, (R)0);
+      } else {
+        cx<R> l = c * di;
+        lbuf[tid] = l;
+        L[(long long)k * bp + (tid - 1)] = l;
+      }
+    }
+    __syncthreads();
+    // 2. rank-1 update of the trailing window
+    for (int e = tid; e < npairs; e += blockDim.x) {
+      const int pr = pairs[e];
+      const int i = pr >> 8, j = pr & 255;
+      int si = pk + i;
+      if (si >= Wc) si -= Wc;
+      int sj = pk + j;
+      if (sj >= Wc) sj -= Wc;
+      cx<R>* w = &W[sj * Wc + si];
+      *w = fms(*w, cbuf[i], lbuf[j]);
+    }
+    // 3. row k+b+1 enters slot pk (disjoint from the slots updated above)
+    if (tid <= b) {
+      const int rn = k + b + 1;
+      const int t = tid;
+      int sc = pk + (b + 1 - t);  // slot of column rn - t
+      if (sc >= Wc) sc -= Wc;
+      W[sc * Wc + pk] = aloc_val<R>(Aloc, sd, rn, t);
+    }
+    __syncthreads();
+    pk = (pk + 1 == Wc) ? 0 : pk + 1;
+  }
+  if (tid == 0) {
+    pivstats[2 * blockIdx.x] = dmin;
+    pivstats[2 * blockIdx.x + 1] = dmax;
+    if (bad) atomicCAS(&status->pivot_bad_sub, -1, (int)blockIdx.x);
+  }
+}
+
+}  // namespace
+
+size_t factor_smem_bytes(int b, int prec) {
+  size_t es = prec == 0 ? sizeof(c128) : sizeof(c64);
+  size_t wc = (size_t)b + 1;
+  return wc * wc * es + 2 * wc * es + (size_t)b * (b + 1) / 2 * sizeof(uint16_t);
+}
+
+cudaError_t launch_factor(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
+                          void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
+  size_t smem = factor_smem_bytes(max_b, prec);
+  cudaError_t e;
+  if (prec == 0) {
+    e = cudaFuncSetAttribute(k_factor_ldlt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_factor_ldlt<double><<<nsub, kFactorThreads, smem, st>>>(subs, Aloc, (c128*)L, (c128*)dinv, pivstats,
+                                                               status);
+  } else {
+    e = cudaFuncSetAttribute(k_factor_ldlt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_factor_ldlt<float><<<nsub, kFactorThreads, smem, st>>>(subs, Aloc, (c64*)L, (c64*)dinv, pivstats, status);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rp

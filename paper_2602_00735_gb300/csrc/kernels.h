@@ -1,0 +1,67 @@
+// Host-side launchers of the libraspml kernels (internal interface).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace rp {
+
+constexpr int kMaxBand = 112;          // largest local half-bandwidth supported
+constexpr int kDotBlocksPerSM = 2;
+
+// Krylov control block in device memory.
+struct KState {
+  int stop;        // the current Arnoldi cycle has ended
+  int conv;        // residual estimate <= rtol
+  int total;       // directions taken over all cycles
+  int jdone;       // directions in the current cycle
+  int breakdown;   // ||w|| == 0
+  int nan;         // non-finite residual estimate
+  int pad0, pad1;
+  double bnorm;    // ||b||_2
+  double est;      // latest |g_{j+1}| / ||b||
+  double hnorm;    // latest ||w||_2
+  double pad2;
+};
+
+// assembly.cu
+cudaError_t launch_global_stencil(const Geo& g, c128* D, c128* CW, c128* CS, c128* CSW, cudaStream_t st);
+cudaError_t launch_local_rows(const Geo& g, const SubDesc* subs, int nsub, int max_npad, c128* Aloc,
+                              cudaStream_t st);
+cudaError_t launch_rhs(const Geo& g, const double* cen, const double* amp, int ns, double width, c128* b,
+                       cudaStream_t st);
+
+// factor.cu
+size_t factor_smem_bytes(int b, int prec);
+cudaError_t launch_factor(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
+                          void* dinv, double* pivstats, DevStatus* status, cudaStream_t st);
+
+// apply.cu
+size_t apply_smem_bytes(int max_bp, int prec);
+cudaError_t launch_apply(int prec, const Geo& g, const SubDesc* subs, int nsub, int max_b, int max_bp,
+                         const void* L, const void* dinv, const c128* r, void* Y, c128* z,
+                         const KState* kst, DevStatus* status, cudaStream_t st);
+
+// krylov.cu
+cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, const c128* CS, const c128* CSW,
+                        const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st);
+int dot_blocks();
+cudaError_t launch_dots(const c128* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
+                        const KState* kst, cudaStream_t st);
+cudaError_t launch_dots_finish(const c128* partial, int ncols, c128* out, int accumulate, const KState* kst,
+                               cudaStream_t st);
+cudaError_t launch_axpys(const c128* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
+                         long long n, const KState* kst, cudaStream_t st);
+cudaError_t launch_add(c128* dst, const c128* src, int cnt, const KState* kst, cudaStream_t st);
+cudaError_t launch_norm_finish(const c128* partial, double* out, c128* hslot, const KState* kst,
+                               cudaStream_t st);
+cudaError_t launch_scale_inv(c128* v, long long n, const double* nrm, const KState* kst, cudaStream_t st);
+cudaError_t launch_cycle_init(KState* kst, c128* gvec, int m, double rtol, double* hist, cudaStream_t st);
+cudaError_t launch_givens(KState* kst, c128* H, int ldh, double* cs, c128* sn, c128* gvec, int j, double rtol,
+                          int mcycle, int maxit, double* hist, cudaStream_t st);
+cudaError_t launch_backsolve(const c128* H, int ldh, const c128* gvec, const KState* kst, c128* y,
+                             cudaStream_t st);
+cudaError_t launch_axpy_state(c128* x, const c128* v, long long n, cudaStream_t st);
+
+}  // namespace rp

@@ -1,0 +1,330 @@
+// Global SpMV and the device-side flexible GMRES kernels (Section 4.1: GMRES
+// with B^-1 as preconditioner), all in complex128.
+//
+// The global matrix is stored as four arrays over unknowns: D (diagonal) and
+// the couplings of each node to its W, S and SW neighbours; the E, N and NE
+// couplings are the W, S, SW couplings of those neighbours (symmetry).
+//
+// Reductions are deterministic: fixed per-block trees, then a fixed-order
+// sum over blocks. Every kernel launched inside an Arnoldi cycle first reads
+// the cycle's stop flag and returns at once when it is set, so the host can
+// enqueue several iterations ahead and synchronise rarely.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rp {
+
+namespace {
+
+constexpr int kThreads = 256;
+int g_num_sms = 0;
+
+__device__ __forceinline__ c128 warp_sum(c128 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
+    v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
+  }
+  return v;
+}
+
+__device__ __forceinline__ c128 block_sum(c128 v) {
+  __shared__ c128 red[kThreads / 32];
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  c128 t = mk(0.0, 0.0);
+  if (threadIdx.x < 32) {
+    t = (l < kThreads / 32) ? red[l] : mk(0.0, 0.0);
+    t = warp_sum(t);
+  }
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+__global__ void k_spmv(long long n, int nx, const c128* __restrict__ D, const c128* __restrict__ CW,
+                       const c128* __restrict__ CS, const c128* __restrict__ CSW, const c128* __restrict__ x,
+                       const c128* __restrict__ bsub, c128* __restrict__ y, const KState* __restrict__ kst) {
+  if (kst != nullptr && kst->stop) return;
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  c128 acc = D[r] * x[r];
+  if (r >= 1) acc = acc + CW[r] * x[r - 1];
+  if (r + 1 < n) acc = acc + CW[r + 1] * x[r + 1];
+  if (r >= nx) acc = acc + CS[r] * x[r - nx];
+  if (r + nx < n) acc = acc + CS[r + nx] * x[r + nx];
+  if (r >= nx + 1) acc = acc + CSW[r] * x[r - nx - 1];
+  if (r + nx + 1 < n) acc = acc + CSW[r + nx + 1] * x[r + nx + 1];
+  y[r] = bsub ? bsub[r] - acc : acc;
+}
+
+// partial[c * gridDim.x + blk] = sum over the block's rows of conj(V_c) w
+__global__ void __launch_bounds__(kThreads)
+    k_dots(const c128* __restrict__ V, long long ldv, const c128* __restrict__ w, long long n,
+           c128* __restrict__ partial, const KState* __restrict__ kst) {
+  if (kst != nullptr && kst->stop) return;
+  const int c = blockIdx.y;
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long r0 = blockIdx.x * per;
+  const long long r1 = min(n, r0 + per);
+  const c128* v = V + c * ldv;
+  c128 a0 = mk(0.0, 0.0), a1 = mk(0.0, 0.0);
+  long long r = r0 + threadIdx.x;
+  for (; r + kThreads < r1; r += 2 * kThreads) {
+    a0 = fcma(a0, v[r], w[r]);
+    a1 = fcma(a1, v[r + kThreads], w[r + kThreads]);
+  }
+  if (r < r1) a0 = fcma(a0, v[r], w[r]);
+  c128 s = block_sum(a0 + a1);
+  if (threadIdx.x == 0) partial[(long long)c * gridDim.x + blockIdx.x] = s;
+}
+
+// out[c] (+)= sum_blk partial[c][blk], one warp per column
+__global__ void k_dots_finish(const c128* __restrict__ partial, int G, int ncols, c128* __restrict__ out,
+                              int accumulate, const KState* __restrict__ kst) {
+  if (kst != nullptr && kst->stop) return;
+  const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int l = threadIdx.x & 31;
+  if (c >= ncols) return;
+  c128 s = mk(0.0, 0.0);
+  for (int b = l; b < G; b += 32) s = s + partial[(long long)c * G + b];
+  s = warp_sum(s);
+  if (l == 0) out[c] = accumulate ? out[c] + s : s;
+}
+
+// w += sign * sum_c V_c h_c
+__global__ void __launch_bounds__(kThreads)
+    k_axpys(const c128* __restrict__ V, long long ldv, int ncols, const c128* __restrict__ h, double sign,
+            c128* __restrict__ w, long long n, const KState* __restrict__ kst) {
+  if (kst != nullptr && kst->stop) return;
+  extern __shared__ c128 hs[];
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = sign * h[c];
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
+    c128 acc = w[r];
+    int c = 0;
+    for (; c + 1 < ncols; c += 2) {
+      c128 v0 = V[c * ldv + r], v1 = V[(c + 1) * ldv + r];
+      acc = acc + v0 * hs[c];
+      acc = acc + v1 * hs[c + 1];
+    }
+    if (c < ncols) acc = acc + V[c * ldv + r] * hs[c];
+    w[r] = acc;
+  }
+}
+
+__global__ void k_add(c128* __restrict__ dst, const c128* __restrict__ src, int cnt,
+                      const KState* __restrict__ kst) {
+  if (kst != nullptr && kst->stop) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) dst[i] = dst[i] + src[i];
+}
+
+// ||w|| from the partial sums of conj(w) w
+__global__ void k_norm_finish(const c128* __restrict__ partial, int G, double* out, c128* hslot,
+                              const KState* __restrict__ kst) {
+  if (kst != nullptr && kst->stop) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < G; b += 32) s += partial[b].re;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) {
+    double nv = sqrt(s);
+    *out = nv;
+    if (hslot) *hslot = mk(nv, 0.0);
+  }
+}
+
+__global__ void k_scale_inv(c128* __restrict__ v, long long n, const double* __restrict__ nrm,
+                            const KState* __restrict__ kst) {
+  if (kst != nullptr && kst->stop) return;
+  const double d = *nrm;
+  if (!(d > 0.0)) return;
+  const double s = 1.0 / d;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) v[r] = s * v[r];
+}
+
+// Start of an Arnoldi cycle: beta = ||r0|| (in kst->hnorm), g = beta e_1.
+__global__ void k_cycle_init(KState* kst, c128* gvec, int m, double rtol, double* hist) {
+  const double beta = kst->hnorm;
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) gvec[i] = mk(i == 0 ? beta : 0.0, 0.0);
+  if (threadIdx.x == 0) {
+    kst->jdone = 0;
+    kst->stop = 0;
+    kst->conv = 0;
+    kst->breakdown = 0;
+    const double est = beta / kst->bnorm;
+    kst->est = est;
+    if (hist) hist[kst->total] = est;
+    if (!isfinite(est)) {
+      kst->nan = 1;
+      kst->stop = 1;
+    } else if (est <= rtol || beta == 0.0) {
+      kst->conv = 1;
+      kst->stop = 1;
+    }
+  }
+}
+
+// Givens step j of the cycle (one thread): rotate the new Hessenberg column,
+// build the new rotation, update g and the residual estimate, decide stop.
+__global__ void k_givens(KState* kst, c128* H, int ldh, double* cs, c128* sn, c128* gvec, int j, double rtol,
+                         int mcycle, int maxit, double* hist) {
+  if (threadIdx.x != 0 || kst->stop) return;
+  c128* col = H + (long long)j * ldh;
+  for (int i = 0; i < j; ++i) {
+    c128 a = col[i], b = col[i + 1];
+    c128 t = cs[i] * a + sn[i] * b;
+    col[i + 1] = cs[i] * b - conj(sn[i]) * a;
+    col[i] = t;
+  }
+  c128 a = col[j], b = col[j + 1];
+  double aa = sqrt(abs2(a)), bb = sqrt(abs2(b));
+  double c;
+  c128 s, r;
+  if (bb == 0.0) {
+    c = 1.0; s = mk(0.0, 0.0); r = a;
+  } else if (aa == 0.0) {
+    c = 0.0; s = mk(1.0, 0.0); r = b;
+  } else {
+    double nrm = hypot(aa, bb);
+    c128 ph = (1.0 / aa) * a;
+    c = aa / nrm;
+    s = (1.0 / nrm) * (ph * conj(b));
+    r = nrm * ph;
+  }
+  col[j] = r;
+  col[j + 1] = mk(0.0, 0.0);
+  cs[j] = c;
+  sn[j] = s;
+  c128 gj = gvec[j];
+  gvec[j + 1] = mk(0.0, 0.0) - conj(s) * gj;
+  gvec[j] = c * gj;
+  kst->total += 1;
+  kst->jdone = j + 1;
+  const double est = sqrt(abs2(gvec[j + 1])) / kst->bnorm;
+  kst->est = est;
+  if (hist) hist[kst->total] = est;
+  if (!isfinite(est)) { kst->nan = 1; kst->stop = 1; }
+  if (est <= rtol) { kst->conv = 1; kst->stop = 1; }
+  if (kst->hnorm == 0.0) { kst->breakdown = 1; kst->stop = 1; }
+  if (j + 1 >= mcycle || kst->total >= maxit) kst->stop = 1;
+}
+
+// y = H(0:m,0:m)^-1 g for the upper-triangular Hessenberg after rotations,
+// m = kst->jdone; one warp.
+__global__ void k_backsolve(const c128* __restrict__ H, int ldh, const c128* __restrict__ gvec,
+                            const KState* __restrict__ kst, c128* __restrict__ y) {
+  const int m = kst->jdone;
+  const int l = threadIdx.x;
+  for (int i = m - 1; i >= 0; --i) {
+    c128 s = mk(0.0, 0.0);
+    for (int c = i + 1 + l; c < m; c += 32) s = s + H[(long long)c * ldh + i] * y[c];
+    s = warp_sum(s);
+    if (l == 0) y[i] = cdiv(gvec[i] - s, H[(long long)i * ldh + i]);
+    __syncwarp();
+    __threadfence_block();
+  }
+}
+
+__global__ void k_axpy(c128* __restrict__ x, const c128* __restrict__ v, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) x[r] = x[r] + v[r];
+}
+
+unsigned grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  long long cap = (long long)(g_num_sms > 0 ? g_num_sms : 152) * 16;
+  return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+}  // namespace
+
+int dot_blocks() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 152;
+  }
+  return kDotBlocksPerSM * g_num_sms;
+}
+
+cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, const c128* CS, const c128* CSW,
+                        const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st) {
+  unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
+  k_spmv<<<blocks, kThreads, 0, st>>>(n, nx, D, CW, CS, CSW, x, bsub, y, kst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dots(const c128* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
+                        const KState* kst, cudaStream_t st) {
+  dim3 grid(dot_blocks(), ncols);
+  k_dots<<<grid, kThreads, 0, st>>>(V, ldv, w, n, partial, kst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dots_finish(const c128* partial, int ncols, c128* out, int accumulate, const KState* kst,
+                               cudaStream_t st) {
+  int per = kThreads / 32;
+  k_dots_finish<<<(ncols + per - 1) / per, kThreads, 0, st>>>(partial, dot_blocks(), ncols, out, accumulate,
+                                                              kst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpys(const c128* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
+                         long long n, const KState* kst, cudaStream_t st) {
+  dot_blocks();
+  size_t smem = (size_t)ncols * sizeof(c128);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_axpys, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_axpys<<<grid_for(n, kThreads), kThreads, smem, st>>>(V, ldv, ncols, h, sign, w, n, kst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add(c128* dst, const c128* src, int cnt, const KState* kst, cudaStream_t st) {
+  k_add<<<(cnt + 127) / 128, 128, 0, st>>>(dst, src, cnt, kst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm_finish(const c128* partial, double* out, c128* hslot, const KState* kst,
+                               cudaStream_t st) {
+  k_norm_finish<<<1, 32, 0, st>>>(partial, dot_blocks(), out, hslot, kst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_inv(c128* v, long long n, const double* nrm, const KState* kst, cudaStream_t st) {
+  dot_blocks();
+  k_scale_inv<<<grid_for(n, kThreads), kThreads, 0, st>>>(v, n, nrm, kst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cycle_init(KState* kst, c128* gvec, int m, double rtol, double* hist, cudaStream_t st) {
+  k_cycle_init<<<1, 128, 0, st>>>(kst, gvec, m, rtol, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_givens(KState* kst, c128* H, int ldh, double* cs, c128* sn, c128* gvec, int j, double rtol,
+                          int mcycle, int maxit, double* hist, cudaStream_t st) {
+  k_givens<<<1, 32, 0, st>>>(kst, H, ldh, cs, sn, gvec, j, rtol, mcycle, maxit, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backsolve(const c128* H, int ldh, const c128* gvec, const KState* kst, c128* y,
+                             cudaStream_t st) {
+  k_backsolve<<<1, 32, 0, st>>>(H, ldh, gvec, kst, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_state(c128* x, const c128* v, long long n, cudaStream_t st) {
+  dot_blocks();
+  k_axpy<<<grid_for(n, kThreads), kThreads, 0, st>>>(x, v, n);
+  return cudaGetLastError();
+}
+
+}  // namespace rp
