@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""RAS-PML Helmholtz benchmark on GB300.
+
+One step = the whole hot path on the workload "c2" (k = 160*pi, h = 1/1280,
+Omega_int = (0,1)^2 with a 0.1-wide PML, 32 x 32 subdomains, 16 seeded
+Gaussian sources, about 2.36M complex unknowns): mesh and global assembly,
+load vector, local assembly and LDL^T factorisation of all 1024 PML-extended
+subdomains, and flexible GMRES with the RAS-PML preconditioner to a relative
+residual of 1e-6.
+
+  value      time per step of the complex64-factor form (local factors and
+             solves in complex64, SpMV / Arnoldi / Givens / true residual in
+             complex128), seconds, lower is better
+  fp64       the same step with complex128 local factors
+  e2e        the complex64 form through helmholtz_solve_host: right-hand
+             side from pinned host memory in, solution back to the host
+  roofline   the apply of B^-1 (k_apply + k_prolong), timed with CUDA events
+             inside the timed steps on the handle's stream
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload,
+             scaled to a full solve (see cpu_sample below)
+
+--impl reference times the oracle alone (the reference arm of this repo).
+Multi-GPU (torchrun): every rank solves its own replica of the workload; no
+data-path collective. Inputs (factors of 4-17 GB) are far larger than L2.
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import math  # noqa: E402
+import re  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import threading  # noqa: E402
+import time  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "RAS-PML time to rtol 1e-6 at k=160*pi, complex64 local factors + complex128 FGMRES (s)"
+RTOL = 1e-6
+MAXIT = 1000
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_from_profile(kernel_src: str):
+    """DRAM bytes per launch of k_apply from the committed ncu summary, or None
+    when the summary is missing or was taken on a different apply.cu."""
+    path = os.path.join(ROOT, "profiles", "k_apply_c2.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_h = re.search(r"apply\.cu sha256: ([0-9a-f]{16})", txt)
+    m_t = re.search(r"dram bytes per full c2 launch: ([0-9.eE+]+)", txt)
+    if not m_h or not m_t:
+        return None
+    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    return float(m_t.group(1)) if cur == m_h.group(1) else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        if not self.rows:
+            return None
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline on a bounded sample
+# ---------------------------------------------------------------------------
+
+def cpu_sample(w, iters: int, n_local: int = 8):
+    """Times the oracle on a bounded sample of workload w and scales it to a
+    full solve of `iters` FGMRES directions:
+      full:   global assembly, load vector, one global SpMV, one vdot and one
+              axpy on a length-n vector;
+      sample: local assembly + SuperLU factor + one local solve on n_local of
+              the subdomains, scaled to all of them.
+    Estimated time = assembly + load + nsub*factor + iters*(nsub*solve + SpMV
+    + norm) + MGS work sum_{j<iters} (j+1)*(vdot + axpy)."""
+    from oracle import fem, ras
+    p = w.params()
+    t0 = time.perf_counter()
+    grid, A = fem.assemble_global(p)
+    t1 = time.perf_counter()
+    b = fem.assemble_rhs(p, w.centres, w.amps, w.width)
+    t2 = time.perf_counter()
+    x = b.copy()
+    y = A @ x
+    t3 = time.perf_counter()
+    s = np.vdot(x, y)
+    t4 = time.perf_counter()
+    y -= s * x
+    t5 = time.perf_counter()
+    rxs = ras.ranges_1d(grid.Mx, p["px"], p["ovlp_cells"], p["pml_cells"])
+    rys = ras.ranges_1d(grid.My, p["py"], p["ovlp_cells"], p["pml_cells"])
+    nsub = len(rxs) * len(rys)
+    picks = np.linspace(0, nsub - 1, n_local).astype(int)
+    import scipy.sparse.linalg as spla
+    tf = ts = 0.0
+    for j in picks:
+        a = time.perf_counter()
+        Aj, nodes, glob, _, _ = ras.local_operator(p, grid, rxs[j % len(rxs)], rys[j // len(rxs)])
+        lu = spla.splu(Aj.tocsc())
+        c = time.perf_counter()
+        lu.solve(b[glob])
+        d = time.perf_counter()
+        tf += c - a
+        ts += d - c
+    tf /= len(picks)
+    ts /= len(picks)
+    t_vec = (t4 - t3) + (t5 - t4)
+    est = (t1 - t0) + (t2 - t1) + nsub * tf + iters * (nsub * ts + (t3 - t2) + (t4 - t3)) \
+        + t_vec * iters * (iters + 1) / 2
+    sample_s = time.perf_counter() - t0
+    return est, sample_s, nsub
+
+
+def cpu_baseline_obj(w, iters):
+    est, sample_s, nsub = cpu_sample(w, iters)
+    return {"value": round(est, 3), "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle on {w.name}: global assembly, load vector, one SpMV and one vdot/axpy on the full "
+                       f"mesh; local assembly + SuperLU factor + one solve on 8 of {nsub} subdomains (scaled x"
+                       f"{nsub / 8:g}); scaled to {iters} FGMRES directions with modified Gram-Schmidt; "
+                       f"{sample_s:.1f} s of CPU work, one thread")}
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2602_00735_gb300 import RasPml
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = workloads.get(args.workload)
+    p = w.params()
+    stream = torch.cuda.current_stream(dev)
+
+    def one_step(prec, timing=False):
+        s = RasPml(p, factor_prec=prec)
+        if timing:
+            s.set_timing(True)
+        b = s.assemble_rhs(w.centres, w.amps, w.width)
+        s.factor()
+        x, it, rel, st = s.solve(b, rtol=RTOL, maxit=MAXIT)
+        return s, x, it, rel, st
+
+    def timed(prec, K, W, timing=True):
+        for _ in range(W):
+            s, x, it, rel, st = one_step(prec)
+            s.close()
+            del x
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        times, per = [], []
+        xs = None
+        for k in range(K):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s, x, it, rel, st = one_step(prec, timing)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            tm = s.timing()
+            per.append(dict(tm, iters=it, relres=rel, status=st, info=s.info()))
+            if k == K - 1:
+                xs = x
+            s.close()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        return times, per, xs
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t_c64, per_c64, x_c64 = timed(1, args.steps, args.warmup)
+    clk = clocks.stop()
+    fp64 = None
+    x_f64 = None
+    if not args.skip_fp64:
+        t_f64, per_f64, x_f64 = timed(0, max(1, min(args.steps, 2)), 1)
+        fp64 = {"time_s": round(float(np.mean(t_f64)), 4), "iters": per_f64[-1]["iters"],
+                "relres": per_f64[-1]["relres"], "factor_ms": round(per_f64[-1]["factor_ms"], 2),
+                "solve_ms": round(per_f64[-1]["solve_ms"], 2),
+                "apply_ms_avg": round(per_f64[-1]["apply_ms"] / max(1, per_f64[-1]["applies"]), 4),
+                "apply_bytes": per_f64[-1]["info"]["apply_bytes"]}
+    err = None
+    if x_f64 is not None:
+        err = float(torch.linalg.vector_norm(x_c64 - x_f64) / torch.linalg.vector_norm(x_f64))
+    del x_c64, x_f64
+
+    # end to end through host buffers
+    e2e = None
+    if not args.skip_e2e:
+        s0 = RasPml(p, factor_prec=1)
+        b_host = s0.assemble_rhs(w.centres, w.amps, w.width).cpu().pin_memory()
+        s0.close()
+        x_host = torch.zeros_like(b_host).pin_memory()
+        te = []
+        for k in range(args.warmup + args.steps):
+            x_host.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s = RasPml(p, factor_prec=1)
+            s.factor()
+            s.solve_host(b_host, rtol=RTOL, maxit=MAXIT, x_host=x_host)
+            t1 = time.perf_counter()
+            s.close()
+            if k >= args.warmup:
+                te.append(t1 - t0)
+        nb = b_host.numel() * b_host.element_size()
+        e2e = {"value": round(float(np.mean(te)), 4), "unit": "s", "h2d_bytes_per_step": 2 * nb,
+               "d2h_bytes_per_step": nb}
+
+    # max over ranks
+    mean_t = float(np.mean(t_c64))
+    if world > 1:
+        tt = torch.tensor([mean_t], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        mean_t = float(tt.item())
+    if rank != 0:
+        return
+
+    last = per_c64[-1]
+    info = last["info"]
+    applies = sum(q["applies"] for q in per_c64)
+    apply_ms = sum(q["apply_ms"] for q in per_c64)
+    avg_apply_s = apply_ms / max(1, applies) / 1e3
+    achieved = info["apply_bytes"] / avg_apply_s / 1e9
+    peak, peak_kind = peaks()
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2602_00735_gb300", "csrc", "apply.cu"))
+    launches_per_step = [q["launches"] + 4 for q in per_c64]   # + setup stencil, rhs, local rows, factor
+    out = {
+        "metric": METRIC, "value": round(mean_t, 4), "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(mean_t * 1e3, 2), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64+c128", "data": "synthetic",
+        "config": {"workload": f"{w.name}: k={p['k'] / math.pi:g}*pi, h=1/{round(1 / p['h'])}, "
+                               f"Omega_int=({p['x0']:g},{p['x1']:g})x({p['y0']:g},{p['y1']:g}), PML {p['kappa_g']:g}, "
+                               f"{p['px']}x{p['py']} subdomains, ovlp={p['ovlp_cells']} pml={p['pml_cells']} cells, "
+                               f"{len(w.amps)} Gaussians width {w.width}",
+                   "n_unknowns": info["n"], "rtol": RTOL, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (complex64 factors %.1f GB)" % (info["factor_bytes"] / 1e9)},
+        "iters": last["iters"], "relres": last["relres"],
+        "phases_ms": {"factor": round(last["factor_ms"], 2), "solve": round(last["solve_ms"], 2),
+                      "apply": round(last["apply_ms"], 2), "spmv": round(last["spmv_ms"], 2),
+                      "ortho": round(last["ortho_ms"], 2),
+                      "setup_and_rest": round(mean_t * 1e3 - last["factor_ms"] - last["solve_ms"], 2)},
+        "apply_gbs": round(achieved, 1),
+        "roofline": {"kernel": "ras_pml_apply (k_apply + k_prolong), complex64", "bound": "hbm",
+                     "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "algorithmic_bytes_per_launch": info["apply_bytes"]},
+        "fp64": fp64, "error_vs_fp64": err,
+        "gpu_launches": int(sum(launches_per_step)),
+        "gpu_launches_per_step": int(launches_per_step[-1]),
+        "clocks": clk, "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        it = fp64["iters"] if fp64 else last["iters"]
+        out["cpu_baseline"] = cpu_baseline_obj(w, it)
+    print(json.dumps(out), flush=True)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = workloads.get(args.workload)
+    gold = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
+    iters = json.load(open(gold))[w.name]["iters"]
+    vals = []
+    last = None
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        obj = cpu_baseline_obj(w, iters)
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            vals.append(obj["value"])
+            last = obj
+    v = float(np.mean(vals))
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 1),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+           "data": "synthetic", "config": {"workload": w.name, "rtol": RTOL, "iters": iters},
+           "cpu_baseline": dict(last, value=round(v, 3)),
+           "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

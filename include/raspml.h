@@ -107,7 +107,7 @@ typedef struct ras_pml_handle ras_pml_handle;
 /* Builds the mesh, the covering of Section 2 and the global matrix of
  * eq. weak on the current device, on `cuda_stream` (a cudaStream_t, may be
  * NULL for the legacy default stream). Validates params (RASPML_EBADARG when
- * Omega is not whole cells, 2*ovlp exceeds a box, or a local band exceeds 127).
+ * Omega is not whole cells, 2*ovlp exceeds a box, or a local half-bandwidth nlx+1 exceeds 112).
  * On success *out owns all device memory of the handle. */
 int ras_pml_setup(const ras_pml_params* params, void* cuda_stream,
                   ras_pml_handle** out);
@@ -167,6 +167,26 @@ int ras_pml_richardson(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev,
  * (relative to ||b||; entry 0 is the initial residual) to hist_host and
  * returns the count through *count. */
 int ras_pml_history(const ras_pml_handle* h, double* hist_host, int cap, int* count);
+
+/* Device-time breakdown of the last ras_pml_factor / helmholtz_solve, from
+ * CUDA events recorded on the handle's stream (recorded only while timing is
+ * enabled with ras_pml_set_timing; disabled by default). */
+typedef struct {
+  double factor_ms;       /* local assembly + LDL^T factorisation              */
+  double solve_ms;        /* whole helmholtz_solve, first launch to last       */
+  double apply_ms;        /* sum over the solve's applies of B^-1              */
+  double spmv_ms;         /* sum over the solve's A z products                 */
+  double ortho_ms;        /* Gram-Schmidt, norms, Givens, normalisation        */
+  int32_t applies;        /* directions (applies) the solve took               */
+  int32_t launches;       /* kernels the solve launched, including those that
+                             returned at once after convergence               */
+} ras_pml_timing_t;
+
+/* Enables (1) or disables (0) event timing on the handle. */
+int ras_pml_set_timing(ras_pml_handle* h, int enable);
+
+/* Fills *t (host struct) for the last factor and solve. */
+int ras_pml_get_timing(const ras_pml_handle* h, ras_pml_timing_t* t);
 
 /* Human-readable text for a status code (static storage). */
 const char* ras_pml_error_string(int status);

@@ -14,7 +14,8 @@ ERRORS = {-1: "EBADARG", -2: "ENOMEM", -3: "ECUDA", -4: "EPIVOT", -5: "ENAN", -6
 #: every entry point declared in include/raspml.h
 SYMBOLS = ("ras_pml_setup", "ras_pml_info", "ras_pml_assemble_rhs", "ras_pml_factor", "ras_pml_apply",
            "ras_pml_matvec", "helmholtz_solve", "helmholtz_solve_host", "ras_pml_richardson",
-           "ras_pml_history", "ras_pml_error_string", "ras_pml_destroy")
+           "ras_pml_history", "ras_pml_set_timing", "ras_pml_get_timing", "ras_pml_error_string",
+           "ras_pml_destroy")
 
 
 class Params(ctypes.Structure):
@@ -31,6 +32,11 @@ class Info(ctypes.Structure):
                 ("factor_bytes", c_int64), ("apply_bytes", c_double), ("min_pivot_ratio", c_double),
                 ("factored", c_int32), ("factor_prec", c_int32), ("bad_subdomain", c_int32),
                 ("last_iters", c_int32)]
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("factor_ms", c_double), ("solve_ms", c_double), ("apply_ms", c_double),
+                ("spmv_ms", c_double), ("ortho_ms", c_double), ("applies", c_int32), ("launches", c_int32)]
 
 
 _lib = None
@@ -57,6 +63,8 @@ def load() -> ctypes.CDLL:
     lib.helmholtz_solve_host.argtypes = lib.helmholtz_solve.argtypes
     lib.ras_pml_richardson.argtypes = [H, c_void_p, c_void_p, c_double, c_int, POINTER(c_int), POINTER(c_double)]
     lib.ras_pml_history.argtypes = [H, c_void_p, c_int, POINTER(c_int)]
+    lib.ras_pml_set_timing.argtypes = [H, c_int]
+    lib.ras_pml_get_timing.argtypes = [H, POINTER(Timing)]
     lib.ras_pml_error_string.argtypes = [c_int]
     lib.ras_pml_error_string.restype = ctypes.c_char_p
     lib.ras_pml_destroy.argtypes = [H]

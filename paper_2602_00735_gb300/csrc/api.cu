@@ -44,6 +44,10 @@ struct ras_pml_handle {
   c128 *tmp_b = nullptr, *tmp_x = nullptr, *tmp_r = nullptr;
   int last_iters = 0;
   std::vector<double> hist_host;
+  // event timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;     // 4 per iteration of a batch, + 2 spare
+  ras_pml_timing_t tm{};
 };
 
 namespace {
@@ -73,6 +77,21 @@ int dalloc(T** p, size_t count) {
     int s_ = dalloc(&(ptr), (cnt));   \
     if (s_ != RASPML_OK) return s_;   \
   } while (0)
+
+int ensure_events(ras_pml_handle* h, int count) {
+  while ((int)h->ev.size() < count) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return RASPML_ECUDA;
+    h->ev.push_back(e);
+  }
+  return RASPML_OK;
+}
+
+float ev_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.f;
+  return ms;
+}
 
 template <typename T>
 void dfree(T*& p) {
@@ -184,6 +203,7 @@ void ras_pml_destroy(ras_pml_handle* h) {
   dfree(h->partial); dfree(h->hbuf); dfree(h->cs); dfree(h->hist); dfree(h->scal); dfree(h->kst);
   dfree(h->tmp_b); dfree(h->tmp_x); dfree(h->tmp_r);
   if (h->kst_host) cudaFreeHost(h->kst_host);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
 }
 
@@ -354,13 +374,20 @@ int ras_pml_factor(ras_pml_handle* h) {
   }
   c128* Aloc = nullptr;
   RP_ALLOC(Aloc, (size_t)4 * h->sum_npad);
+  if (h->timing) {
+    int es_ = ensure_events(h, 2);
+    if (es_) return es_;
+  }
   rp::DevStatus s0{-1, 0, 0, 0};
   cudaError_t e = cudaMemcpyAsync(h->status, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[0], h->st);
   if (e == cudaSuccess) e = rp::launch_local_rows(h->geo, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
   if (e == cudaSuccess)
     e = rp::launch_factor(h->p.factor_prec, h->subs_d, h->nsub, h->max_b, Aloc, h->L, h->dinv, h->pivstats,
                           h->status, h->st);
+  if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[1], h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e == cudaSuccess && h->timing) h->tm.factor_ms = ev_ms(h->ev[0], h->ev[1]);
   cudaFree(Aloc);
   if (e != cudaSuccess) {
     std::fprintf(stderr, "raspml: factor: %s\n", cudaGetErrorString(e));
@@ -415,6 +442,11 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
   c128* x = (c128*)x_dev;
   cudaStream_t st = h->st;
   const int ldh = m + 1;
+  const int batch = 4;
+  if (h->timing && (s = ensure_events(h, 4 * batch + 2)) != RASPML_OK) return s;
+  double t_apply = 0.0, t_spmv = 0.0, t_ortho = 0.0;
+  long long launches = 2, issued = 0, cycles = 0;
+  if (h->timing) RP_CUDA(cudaEventRecord(h->ev[4 * batch], h->st));
   KState k0{};
   RP_CUDA(cudaMemcpyAsync(h->kst, &k0, sizeof(k0), cudaMemcpyHostToDevice, st));
   s = dev_norm(h, b, &h->kst->bnorm, nullptr, nullptr);
@@ -431,12 +463,12 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
     h->last_iters = 0;
     return std::isfinite(bnorm) ? RASPML_OK : RASPML_ENAN;
   }
-  const int batch = 4;
   int status = RASPML_NOT_CONVERGED;
   double rel = NAN;
   for (;;) {
     // new cycle: V0 = b - A x, beta = ||V0||, g = beta e1, V0 /= beta
     c128* V0 = h->V;
+    ++cycles;
     RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, x, b, V0, nullptr, st));
     if ((s = dev_norm(h, V0, &h->kst->hnorm, nullptr, nullptr))) return s;
     RP_CUDA(rp::launch_cycle_init(h->kst, h->gvec, m, rtol, h->hist, st));
@@ -448,9 +480,14 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
         c128* zj = h->Z + (size_t)jj * n;
         c128* w = h->V + (size_t)(jj + 1) * n;
         c128* hcol = h->H + (size_t)jj * ldh;
+        cudaEvent_t* evj = h->ev.data() + 4 * (jj - j);
+        ++issued;
+        if (h->timing) RP_CUDA(cudaEventRecord(evj[0], st));
         RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L,
                                  h->dinv, vj, h->Y, zj, h->kst, h->status, st));
+        if (h->timing) RP_CUDA(cudaEventRecord(evj[1], st));
         RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, nullptr, w, h->kst, st));
+        if (h->timing) RP_CUDA(cudaEventRecord(evj[2], st));
         // classical Gram-Schmidt, twice
         RP_CUDA(rp::launch_dots(h->V, n, jj + 1, w, n, h->partial, h->kst, st));
         RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, hcol, 0, h->kst, st));
@@ -462,10 +499,19 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
         if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst))) return s;
         RP_CUDA(rp::launch_givens(h->kst, h->H, ldh, h->cs, h->sn, h->gvec, jj, rtol, m, maxit, h->hist, st));
         RP_CUDA(rp::launch_scale_inv(w, n, &h->kst->hnorm, h->kst, st));
+        if (h->timing) RP_CUDA(cudaEventRecord(evj[3], st));
       }
-      j += nb;
       RP_CUDA(cudaMemcpyAsync(h->kst_host, h->kst, sizeof(KState), cudaMemcpyDeviceToHost, st));
       RP_CUDA(cudaStreamSynchronize(st));
+      if (h->timing) {
+        for (int jj = 0; jj < nb; ++jj) {
+          cudaEvent_t* evj = h->ev.data() + 4 * jj;
+          t_apply += ev_ms(evj[0], evj[1]);
+          t_spmv += ev_ms(evj[1], evj[2]);
+          t_ortho += ev_ms(evj[2], evj[3]);
+        }
+      }
+      j += nb;
       if (h->kst_host->stop) break;
     }
     const KState ks = *h->kst_host;
@@ -488,6 +534,19 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
   }
   const int total = h->kst_host->total;
   h->last_iters = total;
+  // launches: ||b|| (2); per cycle: residual, norm (2), init, scale, backsolve,
+  // update, true residual, norm (2) = 10; per issued direction: 13
+  launches += 10 * cycles + 13 * issued;
+  h->tm.launches = (int32_t)launches;
+  h->tm.applies = total;
+  if (h->timing) {
+    RP_CUDA(cudaEventRecord(h->ev[4 * batch + 1], st));
+    RP_CUDA(cudaEventSynchronize(h->ev[4 * batch + 1]));
+    h->tm.solve_ms = ev_ms(h->ev[4 * batch], h->ev[4 * batch + 1]);
+    h->tm.apply_ms = t_apply;
+    h->tm.spmv_ms = t_spmv;
+    h->tm.ortho_ms = t_ortho;
+  }
   h->hist_host.resize(total + 1);
   RP_CUDA(cudaMemcpy(h->hist_host.data(), h->hist, sizeof(double) * (total + 1), cudaMemcpyDeviceToHost));
   if (iters) *iters = total;
@@ -558,6 +617,20 @@ int ras_pml_richardson(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, 
   int ts = check_status(h);
   if (ts != RASPML_OK) return ts;
   return status;
+}
+
+int ras_pml_set_timing(ras_pml_handle* h, int enable) {
+  if (!h) return RASPML_EBADARG;
+  cudaSetDevice(h->dev);
+  h->timing = enable != 0;
+  if (h->timing && ensure_events(h, 18) != RASPML_OK) return RASPML_ECUDA;
+  return RASPML_OK;
+}
+
+int ras_pml_get_timing(const ras_pml_handle* h, ras_pml_timing_t* t) {
+  if (!h || !t) return RASPML_EBADARG;
+  *t = h->tm;
+  return RASPML_OK;
 }
 
 int ras_pml_history(const ras_pml_handle* h, double* hist_host, int cap, int* count) {

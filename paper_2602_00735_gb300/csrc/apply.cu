@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(32)
 #pragma unroll 4
     for (int i = 0; i < 31; ++i) {
       cx<R> yi = shfl(acc, i);
-      if (lane > i) acc = fms(acc, Lc[i * bp + (lane - i - 1)], yi);
+      if (lane > i && lane - i - 1 < b) acc = fms(acc, Lc[i * bp + (lane - i - 1)], yi);
     }
     const cx<R> y = acc;
     Yj[k0 + lane] = y * dv[k0 + lane];
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(32)
 #pragma unroll 4
     for (int r = 31; r > 0; --r) {
       cx<R> xv = shfl(acc2, r);
-      if (lane < r) acc2 = fms(acc2, Lc[lane * bp + (r - lane - 1)], xv);
+      if (lane < r && r - lane - 1 < b) acc2 = fms(acc2, Lc[lane * bp + (r - lane - 1)], xv);
     }
     xr[(k0 + lane) & (kRing - 1)] = acc2;
     const int row = k0 + lane;

@@ -47,6 +47,14 @@ class RasPml:
         _lib.check("ras_pml_info", self.lib.ras_pml_info(self._h, byref(inf)))
         return {name: getattr(inf, name) for name, _ in _lib.Info._fields_}
 
+    def set_timing(self, enable: bool = True) -> None:
+        _lib.check("ras_pml_set_timing", self.lib.ras_pml_set_timing(self._h, int(bool(enable))))
+
+    def timing(self) -> dict:
+        t = _lib.Timing()
+        _lib.check("ras_pml_get_timing", self.lib.ras_pml_get_timing(self._h, byref(t)))
+        return {name: getattr(t, name) for name, _ in _lib.Timing._fields_}
+
     def history(self) -> np.ndarray:
         cnt = c_int()
         self.lib.ras_pml_history(self._h, None, 0, byref(cnt))

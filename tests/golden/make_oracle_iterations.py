@@ -1,0 +1,41 @@
+"""Writes tests/golden/oracle_iterations.json: the CPU oracle's flexible GMRES
+iteration counts (rtol 1e-6, x0 = 0, no restart) with the RAS-PML
+preconditioner on the named workloads. Calls only oracle/ and workloads.
+
+    python tests/golden/make_oracle_iterations.py c0 c1 c2
+"""
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+from oracle import fem, krylov, ras  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_iterations.json")
+
+
+def run(name):
+    w = workloads.get(name)
+    p = w.params()
+    t0 = time.time()
+    grid, A = fem.assemble_global(p)
+    b = fem.assemble_rhs(p, w.centres, w.amps, w.width)
+    R = ras.RAS(p).factor()
+    t1 = time.time()
+    x, it, rel, hist = krylov.fgmres(A.dot, R.apply, b, rtol=1e-6, maxit=1000)
+    t2 = time.time()
+    return {"iters": int(it), "relres": float(rel), "rtol": 1e-6, "n": int(grid.n),
+            "subdomains": len(R.subs), "setup_factor_s": round(t1 - t0, 2), "solve_s": round(t2 - t1, 2)}
+
+
+if __name__ == "__main__":
+    data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    for name in sys.argv[1:]:
+        data[name] = run(name)
+        print(name, data[name], flush=True)
+        with open(OUT, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
