@@ -203,7 +203,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     def one_step(prec, timing=False):
-        s = RasPml(p, factor_prec=prec)
+        s = RasPml(p, factor_prec=prec, ortho=args.ortho)
         if timing:
             s.set_timing(True)
         b = s.assemble_rhs(w.centres, w.amps, w.width)
@@ -260,7 +260,7 @@ def run_ours(args, rank, world, local_rank):
     # end to end through host buffers
     e2e = None
     if not args.skip_e2e:
-        s0 = RasPml(p, factor_prec=1)
+        s0 = RasPml(p, factor_prec=1, ortho=args.ortho)
         b_host = s0.assemble_rhs(w.centres, w.amps, w.width).cpu().pin_memory()
         s0.close()
         x_host = torch.zeros_like(b_host).pin_memory()
@@ -269,7 +269,7 @@ def run_ours(args, rank, world, local_rank):
             x_host.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            s = RasPml(p, factor_prec=1)
+            s = RasPml(p, factor_prec=1, ortho=args.ortho)
             s.factor()
             s.solve_host(b_host, rtol=RTOL, maxit=MAXIT, x_host=x_host)
             t1 = time.perf_counter()
@@ -308,7 +308,7 @@ def run_ours(args, rank, world, local_rank):
                                f"{len(w.amps)} Gaussians width {w.width}",
                    "n_unknowns": info["n"], "rtol": RTOL, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (complex64 factors %.1f GB)" % (info["factor_bytes"] / 1e9)},
-        "iters": last["iters"], "relres": last["relres"],
+        "iters": last["iters"], "relres": last["relres"], "ortho": args.ortho, "reorths": last["reorths"],
         "phases_ms": {"factor": round(last["factor_ms"], 2), "solve": round(last["solve_ms"], 2),
                       "apply": round(last["apply_ms"], 2), "spmv": round(last["spmv_ms"], 2),
                       "ortho": round(last["ortho_ms"], 2),
@@ -361,6 +361,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c2")
+    ap.add_argument("--ortho", type=int, default=0, choices=[0, 1],
+                    help="0: classical Gram-Schmidt twice; 1: once plus the DGKS reorthogonalisation test")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -81,6 +81,10 @@ typedef struct {
                              1: Dirichlet closure (RAS-PML-Drch, Section 2)    */
   int    factor_prec;     /* local factors and solves: 0 complex128,
                              1 complex64 (outer iteration stays complex128)    */
+  int    ortho;           /* Arnoldi orthogonalisation, both in complex128:
+                             0 classical Gram-Schmidt applied twice;
+                             1 classical Gram-Schmidt once, repeated only when
+                             ||w'|| < ||w||/sqrt(2) (the DGKS test)            */
 } ras_pml_params;
 
 /* Sizes and statistics of a handle (filled by ras_pml_info). */
@@ -178,6 +182,7 @@ typedef struct {
   double spmv_ms;         /* sum over the solve's A z products                 */
   double ortho_ms;        /* Gram-Schmidt, norms, Givens, normalisation        */
   int32_t applies;        /* directions (applies) the solve took               */
+  int32_t reorths;        /* second Gram-Schmidt passes taken (ortho = 1)      */
   int32_t launches;       /* kernels the solve launched, including those that
                              returned at once after convergence               */
 } ras_pml_timing_t;

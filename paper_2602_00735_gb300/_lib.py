@@ -22,7 +22,7 @@ class Params(ctypes.Structure):
     _fields_ = [("k", c_double), ("x0", c_double), ("y0", c_double), ("x1", c_double), ("y1", c_double),
                 ("kappa_g", c_double), ("h", c_double), ("px", c_int), ("py", c_int),
                 ("ovlp_cells", c_int), ("pml_cells", c_int), ("g_amp", c_double), ("g_ramp", c_double),
-                ("local_bc", c_int), ("factor_prec", c_int)]
+                ("local_bc", c_int), ("factor_prec", c_int), ("ortho", c_int)]
 
 
 class Info(ctypes.Structure):
@@ -36,7 +36,8 @@ class Info(ctypes.Structure):
 
 class Timing(ctypes.Structure):
     _fields_ = [("factor_ms", c_double), ("solve_ms", c_double), ("apply_ms", c_double),
-                ("spmv_ms", c_double), ("ortho_ms", c_double), ("applies", c_int32), ("launches", c_int32)]
+                ("spmv_ms", c_double), ("ortho_ms", c_double), ("applies", c_int32), ("reorths", c_int32),
+                ("launches", c_int32)]
 
 
 _lib = None

@@ -27,7 +27,7 @@ struct ras_pml_handle {
   int nsub = 0, max_b = 0, max_bp = 0, max_npad = 0, max_n = 0;
   long long n = 0, sum_npad = 0, sum_l = 0, sum_n = 0, sum_bn = 0;
   c128 *D = nullptr, *CW = nullptr, *CS = nullptr, *CSW = nullptr;
-  void *L = nullptr, *dinv = nullptr, *Y = nullptr;
+  void *L = nullptr, *Lrev = nullptr, *dinv = nullptr, *Y = nullptr;
   double* pivstats = nullptr;
   rp::DevStatus* status = nullptr;
   bool factored = false;
@@ -160,9 +160,9 @@ int ensure_krylov(ras_pml_handle* h, int m, int maxit) {
 }
 
 // *out = ||v||_2 (device double), through the deterministic dot kernels
-int dev_norm(ras_pml_handle* h, const c128* v, double* out, c128* hslot, const KState* kst) {
-  RP_CUDA(rp::launch_dots(v, h->n, 1, v, h->n, h->partial, kst, h->st));
-  RP_CUDA(rp::launch_norm_finish(h->partial, out, hslot, kst, h->st));
+int dev_norm(ras_pml_handle* h, const c128* v, double* out, c128* hslot, const KState* kst, int gate = 0) {
+  RP_CUDA(rp::launch_dots(v, h->n, 1, v, h->n, h->partial, kst, gate, h->st));
+  RP_CUDA(rp::launch_norm_finish(h->partial, out, hslot, kst, gate, h->st));
   return RASPML_OK;
 }
 
@@ -198,7 +198,7 @@ void ras_pml_destroy(ras_pml_handle* h) {
   cudaSetDevice(h->dev);
   if (h->st) cudaStreamSynchronize(h->st);
   dfree(h->subs_d); dfree(h->D); dfree(h->CW); dfree(h->CS); dfree(h->CSW);
-  dfree(h->L); dfree(h->dinv); dfree(h->Y); dfree(h->pivstats); dfree(h->status);
+  dfree(h->L); dfree(h->Lrev); dfree(h->dinv); dfree(h->Y); dfree(h->pivstats); dfree(h->status);
   dfree(h->V); dfree(h->Z); dfree(h->H); dfree(h->sn); dfree(h->gvec); dfree(h->yv);
   dfree(h->partial); dfree(h->hbuf); dfree(h->cs); dfree(h->hist); dfree(h->scal); dfree(h->kst);
   dfree(h->tmp_b); dfree(h->tmp_x); dfree(h->tmp_r);
@@ -213,7 +213,7 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   const ras_pml_params& p = *pp;
   if (!(p.k >= 0.0) || !(p.h > 0.0) || !(p.kappa_g >= 0.0) || !(p.x1 > p.x0) || !(p.y1 > p.y0) || p.px < 1 ||
       p.py < 1 || !(p.g_ramp > 0.0) || !(p.g_amp >= 0.0) || (p.local_bc != 0 && p.local_bc != 1) ||
-      (p.factor_prec != 0 && p.factor_prec != 1))
+      (p.factor_prec != 0 && p.factor_prec != 1) || (p.ortho != 0 && p.ortho != 1))
     return RASPML_EBADARG;
   const double lx = p.x1 - p.x0 + 2 * p.kappa_g, ly = p.y1 - p.y0 + 2 * p.kappa_g;
   const long long Mx = std::llround(lx / p.h), My = std::llround(ly / p.h);
@@ -326,7 +326,7 @@ int ras_pml_info(const ras_pml_handle* h, ras_pml_info_t* info) {
   info->max_band = h->max_b;
   info->sum_local_n = h->sum_n;
   info->sum_band_n = h->sum_bn;
-  info->factor_bytes = (int64_t)((h->sum_l + h->sum_npad) * es);
+  info->factor_bytes = (int64_t)((2 * h->sum_l + h->sum_npad) * es);   // L, its reversed row copy, D^-1
   // L read in the forward and in the backward sweep, D^-1 once, r read once, z written once
   info->apply_bytes = 2.0 * es * (double)h->sum_bn + es * (double)h->sum_n + 32.0 * (double)h->n;
   info->min_pivot_ratio = h->min_pivot_ratio;
@@ -365,6 +365,9 @@ int ras_pml_factor(ras_pml_handle* h) {
     cudaError_t e = cudaMalloc(&p, (size_t)h->sum_l * es);
     if (e != cudaSuccess) return RASPML_ENOMEM;
     h->L = p;
+    e = cudaMalloc(&p, (size_t)h->sum_l * es);
+    if (e != cudaSuccess) return RASPML_ENOMEM;
+    h->Lrev = p;
     e = cudaMalloc(&p, (size_t)h->sum_npad * es);
     if (e != cudaSuccess) return RASPML_ENOMEM;
     h->dinv = p;
@@ -381,10 +384,11 @@ int ras_pml_factor(ras_pml_handle* h) {
   rp::DevStatus s0{-1, 0, 0, 0};
   cudaError_t e = cudaMemcpyAsync(h->status, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[0], h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Lrev, 0, (size_t)h->sum_l * es, h->st);
   if (e == cudaSuccess) e = rp::launch_local_rows(h->geo, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
   if (e == cudaSuccess)
-    e = rp::launch_factor(h->p.factor_prec, h->subs_d, h->nsub, h->max_b, Aloc, h->L, h->dinv, h->pivstats,
-                          h->status, h->st);
+    e = rp::launch_factor(h->p.factor_prec, h->subs_d, h->nsub, h->max_b, Aloc, h->L, h->Lrev, h->dinv,
+                          h->pivstats, h->status, h->st);
   if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[1], h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e == cudaSuccess && h->timing) h->tm.factor_ms = ev_ms(h->ev[0], h->ev[1]);
@@ -413,7 +417,7 @@ int ras_pml_apply(ras_pml_handle* h, const rp_c128* r, rp_c128* z) {
   if (!h || !r || !z || (const void*)r == (const void*)z) return RASPML_EBADARG;
   if (!h->factored) return RASPML_ESTATE;
   cudaSetDevice(h->dev);
-  RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->dinv,
+  RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev, h->dinv,
                            (const c128*)r, h->Y, (c128*)z, nullptr, h->status, h->st));
   return RASPML_OK;
 }
@@ -483,20 +487,35 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
         cudaEvent_t* evj = h->ev.data() + 4 * (jj - j);
         ++issued;
         if (h->timing) RP_CUDA(cudaEventRecord(evj[0], st));
-        RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L,
+        RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev,
                                  h->dinv, vj, h->Y, zj, h->kst, h->status, st));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[1], st));
         RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, nullptr, w, h->kst, st));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[2], st));
-        // classical Gram-Schmidt, twice
-        RP_CUDA(rp::launch_dots(h->V, n, jj + 1, w, n, h->partial, h->kst, st));
-        RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, hcol, 0, h->kst, st));
-        RP_CUDA(rp::launch_axpys(h->V, n, jj + 1, hcol, -1.0, w, n, h->kst, st));
-        RP_CUDA(rp::launch_dots(h->V, n, jj + 1, w, n, h->partial, h->kst, st));
-        RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, h->hbuf, 0, h->kst, st));
-        RP_CUDA(rp::launch_axpys(h->V, n, jj + 1, h->hbuf, -1.0, w, n, h->kst, st));
-        RP_CUDA(rp::launch_add(hcol, h->hbuf, jj + 1, h->kst, st));
-        if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst))) return s;
+        if (h->p.ortho == 0) {
+          // classical Gram-Schmidt, twice
+          RP_CUDA(rp::launch_dots(h->V, n, jj + 1, w, n, h->partial, h->kst, 0, st));
+          RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, hcol, 0, h->kst, 0, st));
+          RP_CUDA(rp::launch_axpys(h->V, n, jj + 1, hcol, -1.0, w, n, h->kst, 0, st));
+          RP_CUDA(rp::launch_dots(h->V, n, jj + 1, w, n, h->partial, h->kst, 0, st));
+          RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, h->hbuf, 0, h->kst, 0, st));
+          RP_CUDA(rp::launch_axpys(h->V, n, jj + 1, h->hbuf, -1.0, w, n, h->kst, 0, st));
+          RP_CUDA(rp::launch_add(hcol, h->hbuf, jj + 1, h->kst, 0, st));
+          if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst))) return s;
+        } else {
+          // one pass; the projection also returns ||w||^2 (w is column jj+1 of V)
+          RP_CUDA(rp::launch_dots(h->V, n, jj + 2, w, n, h->partial, h->kst, 0, st));
+          RP_CUDA(rp::launch_dots_finish(h->partial, jj + 2, hcol, 0, h->kst, 0, st));
+          RP_CUDA(rp::launch_axpys(h->V, n, jj + 1, hcol, -1.0, w, n, h->kst, 0, st));
+          if ((s = dev_norm(h, w, &h->kst->hnorm, nullptr, h->kst))) return s;
+          RP_CUDA(rp::launch_reorth_decide(h->kst, hcol, jj, st));
+          // second pass only where the DGKS test fired
+          RP_CUDA(rp::launch_dots(h->V, n, jj + 1, w, n, h->partial, h->kst, 1, st));
+          RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, h->hbuf, 0, h->kst, 1, st));
+          RP_CUDA(rp::launch_axpys(h->V, n, jj + 1, h->hbuf, -1.0, w, n, h->kst, 1, st));
+          RP_CUDA(rp::launch_add(hcol, h->hbuf, jj + 1, h->kst, 1, st));
+          if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst, 1))) return s;
+        }
         RP_CUDA(rp::launch_givens(h->kst, h->H, ldh, h->cs, h->sn, h->gvec, jj, rtol, m, maxit, h->hist, st));
         RP_CUDA(rp::launch_scale_inv(w, n, &h->kst->hnorm, h->kst, st));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[3], st));
@@ -518,7 +537,7 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
     // x += Z y with y = H^-1 g
     if (ks.jdone > 0) {
       RP_CUDA(rp::launch_backsolve(h->H, ldh, h->gvec, h->kst, h->yv, st));
-      RP_CUDA(rp::launch_axpys(h->Z, n, ks.jdone, h->yv, 1.0, x, n, nullptr, st));
+      RP_CUDA(rp::launch_axpys(h->Z, n, ks.jdone, h->yv, 1.0, x, n, nullptr, 0, st));
     }
     // true residual
     RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, x, b, h->V, nullptr, st));
@@ -535,10 +554,12 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
   const int total = h->kst_host->total;
   h->last_iters = total;
   // launches: ||b|| (2); per cycle: residual, norm (2), init, scale, backsolve,
-  // update, true residual, norm (2) = 10; per issued direction: 13
-  launches += 10 * cycles + 13 * issued;
+  // update, true residual, norm (2) = 10; per issued direction: 13 (CGS twice)
+  // or 17 (one pass, test, gated second pass)
+  launches += 10 * cycles + (h->p.ortho == 0 ? 13 : 17) * issued;
   h->tm.launches = (int32_t)launches;
   h->tm.applies = total;
+  h->tm.reorths = h->p.ortho == 0 ? total : h->kst_host->reorths;
   if (h->timing) {
     RP_CUDA(cudaEventRecord(h->ev[4 * batch + 1], st));
     RP_CUDA(cudaEventSynchronize(h->ev[4 * batch + 1]));
@@ -607,7 +628,7 @@ int ras_pml_richardson(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, 
     if (!std::isfinite(rel)) { status = RASPML_ENAN; break; }
     if (rel <= rtol) { status = RASPML_OK; break; }
     if (it >= maxit) break;
-    RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->dinv,
+    RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev, h->dinv,
                              h->tmp_r, h->Y, h->V, nullptr, h->status, h->st));
     RP_CUDA(rp::launch_axpy_state(x, h->V, n, h->st));
   }

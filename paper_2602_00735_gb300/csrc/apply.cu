@@ -2,15 +2,22 @@
 // (Section 2, the equation defining B^-1; restriction as in
 // eq. local-ras-discrete, weighted prolongation as in eq. update1).
 //
-// k_apply: one warp per subdomain runs the restriction R_j r (a gather of the
-//   global residual), the forward solve L y = R_j r, z = D^-1 y, the backward
-//   solve L^T x = z, and writes chi_j .* x to the subdomain's slice of Y.
-//   The factor L_j is streamed from HBM in chunks of 32 columns by the bulk
-//   copy (TMA) engine into a two-stage shared-memory ring, first in
-//   ascending then in descending chunk order. Both sweeps work in blocks of
-//   32 rows: a 32x32 triangular solve carried by warp shuffles, and a
-//   band-panel update (rows below the block in the forward sweep, rows
-//   below the block as known values in the backward sweep).
+// k_apply: one warp per subdomain computes R_j r (a gather of the global
+//   residual), y = L^-1 R_j r, z = D^-1 y, x = L^-T z, and writes chi_j .* x
+//   to the subdomain's slice of Y. Both triangular solves run as the same
+//   column sweep on a unit lower band matrix stored by columns: the forward
+//   sweep reads L by columns, the backward sweep reads the row-band copy of
+//   L stored in reversed row order (column k' of that copy is row npad-1-k'
+//   of L read leftwards), so that L^T x = z becomes a forward sweep on
+//   reversed vectors.
+//   Sweep: the rows k..k+32S-1 of the right-hand side live in a register
+//   window, row r in lane r mod 32, slot (r/32) mod S, S = ceil((b+1)/32).
+//   Step k broadcasts the finished row k from its lane, subtracts
+//   column k times y_k from the rows below (one complex FMA per slot and
+//   lane), and refills row k's slot with row k+32S.
+//   The band columns stream from HBM through a 4-stage shared-memory ring of
+//   8-column chunks filled by the bulk-copy (TMA) engine; both sweeps use one
+//   continuous chunk sequence.
 // k_prolong: one thread per global unknown sums the (at most four) weighted
 //   local values that cover it, in a fixed order (bit-reproducible).
 #include "common.cuh"
@@ -20,7 +27,8 @@ namespace rp {
 
 namespace {
 
-constexpr int kRing = 256;   // backward-sweep ring of solved values (>= b + 32)
+constexpr int kCol = 8;       // columns per bulk copy
+constexpr int kStages = 4;    // ring depth
 
 template <typename R>
 __device__ __forceinline__ cx<R> gather_row(const SubDesc& sd, const Geo& g, const c128* __restrict__ r, int row) {
@@ -30,131 +38,149 @@ __device__ __forceinline__ cx<R> gather_row(const SubDesc& sd, const Geo& g, con
   return cvt<R>(v);
 }
 
-template <typename R, int NS>
+template <typename R>
+struct Pipe {
+  uint64_t* bar;
+  cx<R>* stg;
+  const cx<R>* src0;   // forward band (columns of L)
+  const cx<R>* src1;   // reversed row band of L
+  int stage_elems, Q, bp;
+  uint32_t bytes;
+  __device__ void issue(int s) const {
+    const cx<R>* src = s < Q ? src0 + (long long)s * kCol * bp : src1 + (long long)(s - Q) * kCol * bp;
+    const int st = s % kStages;
+    mbar_arrive_expect_tx(&bar[st], bytes);
+    bulk_g2s(stg + st * stage_elems, src, bytes, &bar[st]);
+  }
+  __device__ const cx<R>* wait(int s, bool& ok) const {
+    const int st = s % kStages;
+    ok = mbar_wait_bounded(&bar[st], (uint32_t)((s / kStages) & 1));
+    return stg + st * stage_elems;
+  }
+};
+
+// The 32 steps of one row group with window phase PH (= group mod S).
+template <typename R, int S, int PH>
+__device__ __forceinline__ bool group_steps(const Pipe<R>& pp, int s0, int b, int lane, cx<R> (&win)[S],
+                                            const cx<R>& nxt, cx<R>& outv) {
+  const int bp = pp.bp;
+#pragma unroll 1
+  for (int c4 = 0; c4 < 32 / kCol; ++c4) {
+    const int s = s0 + c4;
+    bool ok;
+    const cx<R>* Lc = pp.wait(s, ok);
+    if (!__all_sync(0xffffffffu, ok)) return false;
+#pragma unroll 2
+    for (int ii = 0; ii < kCol; ++ii) {
+      const int i = c4 * kCol + ii;
+      const cx<R>* col = Lc + ii * bp;
+      const cx<R> y = shfl(win[PH], i);
+      if (lane == i) {
+        outv = y;
+        win[PH] = nxt;
+      }
+      const int base = lane - i - 1;
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl) {
+        const int t = (sl == PH) ? ((lane > i) ? base : base + 32 * S) : base + 32 * ((sl - PH + S) % S);
+        if (t < b) win[sl] = fms(win[sl], col[t], y);
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && s + kStages < 2 * pp.Q) {
+      fence_proxy_async_smem();
+      pp.issue(s + kStages);
+    }
+  }
+  return true;
+}
+
+template <typename R, int S>
+__device__ __forceinline__ bool group_dispatch(int ph, const Pipe<R>& pp, int s0, int b, int lane, cx<R> (&win)[S],
+                                               const cx<R>& nxt, cx<R>& outv) {
+  switch (ph) {
+    case 0: return group_steps<R, S, 0>(pp, s0, b, lane, win, nxt, outv);
+    case 1: if constexpr (S > 1) return group_steps<R, S, 1>(pp, s0, b, lane, win, nxt, outv); break;
+    case 2: if constexpr (S > 2) return group_steps<R, S, 2>(pp, s0, b, lane, win, nxt, outv); break;
+    case 3: if constexpr (S > 3) return group_steps<R, S, 3>(pp, s0, b, lane, win, nxt, outv); break;
+  }
+  return false;
+}
+
+template <typename R, int S>
 __global__ void __launch_bounds__(32)
-    k_apply(Geo g, const SubDesc* __restrict__ subs, const cx<R>* __restrict__ Lall,
+    k_apply(Geo g, const SubDesc* __restrict__ subs, const cx<R>* __restrict__ Lf, const cx<R>* __restrict__ Lb,
             const cx<R>* __restrict__ dinv_all, const c128* __restrict__ rglob, cx<R>* __restrict__ Y,
             int stage_elems, const KState* __restrict__ kst, DevStatus* status) {
   extern __shared__ __align__(128) unsigned char sm[];
   if (kst != nullptr && kst->stop) return;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm);
-  cx<R>* xr = reinterpret_cast<cx<R>*>(sm + 128);
-  cx<R>* stg = xr + kRing;
   const SubDesc sd = subs[blockIdx.x];
   const int lane = threadIdx.x;
-  const int b = sd.b, bp = sd.bp, Q = sd.npad / 32, S = 2 * Q;
-  const cx<R>* L = Lall + sd.l_off;
+  const int b = sd.b, npad = sd.npad, G = npad / 32;
+  Pipe<R> pp;
+  pp.bar = reinterpret_cast<uint64_t*>(sm);
+  pp.stg = reinterpret_cast<cx<R>*>(sm + 128);
+  pp.src0 = Lf + sd.l_off;
+  pp.src1 = Lb + sd.l_off;
+  pp.stage_elems = stage_elems;
+  pp.Q = npad / kCol;
+  pp.bp = sd.bp;
+  pp.bytes = (uint32_t)(kCol * sd.bp * sizeof(cx<R>));
   const cx<R>* dv = dinv_all + sd.v_off;
   cx<R>* Yj = Y + sd.v_off;
-  const uint32_t chunk_bytes = 32u * (uint32_t)bp * (uint32_t)sizeof(cx<R>);
-
-  // load sequence s = 0..2Q-1: chunks 0..Q-1, then Q-1..0
-  auto issue = [&](int s) {
-    const int q = s < Q ? s : S - 1 - s;
-    mbar_arrive_expect_tx(&bar[s & 1], chunk_bytes);
-    bulk_g2s(stg + (s & 1) * stage_elems, L + (long long)q * 32 * bp, chunk_bytes, &bar[s & 1]);
-  };
+  const int nseq = 2 * pp.Q;
+  if (lane == 0) {
+    for (int t = 0; t < kStages; ++t) mbar_init(&pp.bar[t], 1);
+    mbar_fence_init();
+    for (int t = 0; t < kStages && t < nseq; ++t) pp.issue(t);
+  }
+  __syncwarp();
   auto fail = [&](int s) {
-    // a wait gave up: record it, drain the copies still in flight, leave
+    // a bounded wait gave up: record it, drain this warp's copies in flight, leave
     if (lane == 0) {
       atomicExch(&status->timeout, 1);
-      for (int t = s; t < s + 2 && t < S; ++t) mbar_wait_bounded(&bar[t & 1], (t >> 1) & 1);
+      for (int t = s; t < s + kStages && t < nseq; ++t) mbar_wait_bounded(&pp.bar[t % kStages], (t / kStages) & 1);
     }
     __syncwarp();
   };
-  if (lane == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    mbar_fence_init();
-    issue(0);
-    if (S > 1) issue(1);
+
+  // ---------------- forward: L y = R_j r, z = D^-1 y ----------------
+  cx<R> win[S];
+#pragma unroll
+  for (int sl = 0; sl < S; ++sl) win[sl] = gather_row<R>(sd, g, rglob, 32 * sl + lane);
+  cx<R> nxt = gather_row<R>(sd, g, rglob, 32 * S + lane);
+  for (int gi = 0; gi < G; ++gi) {
+    const cx<R> nxt2 = gather_row<R>(sd, g, rglob, 32 * (gi + S + 1) + lane);
+    const cx<R> d = dv[32 * gi + lane];
+    cx<R> outv;
+    if (!group_dispatch<R, S>(gi % S, pp, 4 * gi, b, lane, win, nxt, outv)) { fail(4 * gi); return; }
+    Yj[32 * gi + lane] = outv * d;
+    nxt = nxt2;
   }
+  __threadfence_block();
   __syncwarp();
 
-  // ---------------- forward sweep: L y = R_j r, z = D^-1 y ----------------
-  cx<R> acc = gather_row<R>(sd, g, rglob, lane);
-  cx<R> win[NS];
+  // ---------------- backward: L^T x = z on reversed rows ----------------
+  auto zrow = [&](int q) -> cx<R> { return q < npad ? Yj[npad - 1 - q] : mk((R)0, (R)0); };
 #pragma unroll
-  for (int m = 0; m < NS; ++m) win[m] = gather_row<R>(sd, g, rglob, 32 * (m + 1) + lane);
-
-  for (int s = 0; s < Q; ++s) {
-    const int k0 = 32 * s;
-    const bool ok = mbar_wait_bounded(&bar[s & 1], (s >> 1) & 1);
-    if (!__all_sync(0xffffffffu, ok)) { fail(s); return; }
-    const cx<R>* Lc = stg + (s & 1) * stage_elems;
-    // 32x32 unit lower triangle of the block
-#pragma unroll 4
-    for (int i = 0; i < 31; ++i) {
-      cx<R> yi = shfl(acc, i);
-      if (lane > i && lane - i - 1 < b) acc = fms(acc, Lc[i * bp + (lane - i - 1)], yi);
+  for (int sl = 0; sl < S; ++sl) win[sl] = zrow(32 * sl + lane);
+  nxt = zrow(32 * S + lane);
+  const int o = g.ovlp;
+  for (int gi = 0; gi < G; ++gi) {
+    const cx<R> nxt2 = zrow(32 * (gi + S + 1) + lane);
+    cx<R> outv;
+    if (!group_dispatch<R, S>(gi % S, pp, pp.Q + 4 * gi, b, lane, win, nxt, outv)) {
+      fail(pp.Q + 4 * gi);
+      return;
     }
-    const cx<R> y = acc;
-    Yj[k0 + lane] = y * dv[k0 + lane];
-    // band-panel update of the next b rows
-#pragma unroll 2
-    for (int i = 0; i < 32; ++i) {
-      cx<R> yi = shfl(y, i);
-#pragma unroll
-      for (int m = 0; m < NS; ++m) {
-        const int t = 32 * m + lane + 31 - i;
-        if (t < b) win[m] = fms(win[m], Lc[i * bp + t], yi);
-      }
-    }
-    acc = win[0];
-#pragma unroll
-    for (int m = 0; m + 1 < NS; ++m) win[m] = win[m + 1];
-    win[NS - 1] = gather_row<R>(sd, g, rglob, k0 + 32 * (NS + 1) + lane);
-    __syncwarp();
-    if (lane == 0 && s + 2 < S) {
-      fence_proxy_async_smem();
-      issue(s + 2);
-    }
-  }
-
-  // ---------------- backward sweep: L^T x = z ----------------
-  for (int t = lane; t < kRing; t += 32) xr[t] = mk((R)0, (R)0);
-  __syncwarp();
-  const double o = g.ovlp;
-  for (int s = Q; s < S; ++s) {
-    const int k0 = 32 * (S - 1 - s);
-    const bool ok = mbar_wait_bounded(&bar[s & 1], (s >> 1) & 1);
-    if (!__all_sync(0xffffffffu, ok)) { fail(s); return; }
-    const cx<R>* Lc = stg + (s & 1) * stage_elems;
-    cx<R> a0 = Yj[k0 + lane], a1 = mk((R)0, (R)0);
-    // known values below the block: rows k0+32+u, coefficient L(k0+32+u, k0+lane)
-    const cx<R>* col = Lc + lane * bp + 31 - lane;
-    int u = 0;
-    for (; u + 1 < b; u += 2) {
-      const cx<R> x0 = xr[(k0 + 32 + u) & (kRing - 1)];
-      const cx<R> x1 = xr[(k0 + 33 + u) & (kRing - 1)];
-      if (31 + u - lane < b) a0 = fms(a0, col[u], x0);
-      if (32 + u - lane < b) a1 = fms(a1, col[u + 1], x1);
-    }
-    if (u < b) {
-      const cx<R> x0 = xr[(k0 + 32 + u) & (kRing - 1)];
-      if (31 + u - lane < b) a0 = fms(a0, col[u], x0);
-    }
-    cx<R> acc2 = a0 + a1;
-    // 32x32 unit upper triangle (L^T) of the block, bottom-up
-#pragma unroll 4
-    for (int r = 31; r > 0; --r) {
-      cx<R> xv = shfl(acc2, r);
-      if (lane < r && r - lane - 1 < b) acc2 = fms(acc2, Lc[lane * bp + (r - lane - 1)], xv);
-    }
-    xr[(k0 + lane) & (kRing - 1)] = acc2;
-    const int row = k0 + lane;
-    cx<R> outv = mk((R)0, (R)0);
+    const int row = npad - 1 - (32 * gi + lane);
+    cx<R> v = mk((R)0, (R)0);
     if (row < sd.n) {
       const int i = sd.ix0 + row % sd.nlx, j = sd.iy0 + row / sd.nlx;
-      const R chi = (R)pou_weight(sd, i, j, (int)o);
-      outv = chi * acc2;
+      v = (R)pou_weight(sd, i, j, o) * outv;
     }
-    Yj[row] = outv;
-    __syncwarp();
-    if (lane == 0 && s + 2 < S) {
-      fence_proxy_async_smem();
-      issue(s + 2);
-    }
+    Yj[row] = v;
+    nxt = nxt2;
   }
 }
 
@@ -187,16 +213,16 @@ __global__ void k_prolong(Geo g, const SubDesc* __restrict__ subs, const cx<R>* 
   z[r] = mk(re, im);
 }
 
-template <typename R, int NS>
-cudaError_t launch_apply_t(const Geo& g, const SubDesc* subs, int nsub, int max_bp, const void* L,
+template <typename R, int S>
+cudaError_t launch_apply_t(const Geo& g, const SubDesc* subs, int nsub, int max_bp, const void* Lf, const void* Lb,
                            const void* dinv, const c128* r, void* Y, const KState* kst, DevStatus* status,
                            cudaStream_t st) {
-  const int stage_elems = 32 * max_bp;
+  const int stage_elems = kCol * max_bp;
   const size_t smem = apply_smem_bytes(max_bp, sizeof(R) == 8 ? 0 : 1);
-  cudaError_t e = cudaFuncSetAttribute(k_apply<R, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_apply<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_apply<R, NS><<<nsub, 32, smem, st>>>(g, subs, (const cx<R>*)L, (const cx<R>*)dinv, r, (cx<R>*)Y,
-                                         stage_elems, kst, status);
+  k_apply<R, S><<<nsub, 32, smem, st>>>(g, subs, (const cx<R>*)Lf, (const cx<R>*)Lb, (const cx<R>*)dinv, r,
+                                        (cx<R>*)Y, stage_elems, kst, status);
   return cudaGetLastError();
 }
 
@@ -204,27 +230,27 @@ cudaError_t launch_apply_t(const Geo& g, const SubDesc* subs, int nsub, int max_
 
 size_t apply_smem_bytes(int max_bp, int prec) {
   size_t es = prec == 0 ? sizeof(c128) : sizeof(c64);
-  return 128 + kRing * es + 2 * (size_t)32 * max_bp * es;
+  return 128 + (size_t)kStages * kCol * max_bp * es;
 }
 
 cudaError_t launch_apply(int prec, const Geo& g, const SubDesc* subs, int nsub, int max_b, int max_bp,
-                         const void* L, const void* dinv, const c128* r, void* Y, c128* z, const KState* kst,
-                         DevStatus* status, cudaStream_t st) {
-  const int ns = (max_b + 31) / 32;
+                         const void* Lf, const void* Lb, const void* dinv, const c128* r, void* Y, c128* z,
+                         const KState* kst, DevStatus* status, cudaStream_t st) {
+  const int S = (max_b + 1 + 31) / 32;
   cudaError_t e;
   if (prec == 0) {
-    switch (ns) {
-      case 1: e = launch_apply_t<double, 1>(g, subs, nsub, max_bp, L, dinv, r, Y, kst, status, st); break;
-      case 2: e = launch_apply_t<double, 2>(g, subs, nsub, max_bp, L, dinv, r, Y, kst, status, st); break;
-      case 3: e = launch_apply_t<double, 3>(g, subs, nsub, max_bp, L, dinv, r, Y, kst, status, st); break;
-      default: e = launch_apply_t<double, 4>(g, subs, nsub, max_bp, L, dinv, r, Y, kst, status, st); break;
+    switch (S) {
+      case 1: e = launch_apply_t<double, 1>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
+      case 2: e = launch_apply_t<double, 2>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
+      case 3: e = launch_apply_t<double, 3>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
+      default: e = launch_apply_t<double, 4>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
     }
   } else {
-    switch (ns) {
-      case 1: e = launch_apply_t<float, 1>(g, subs, nsub, max_bp, L, dinv, r, Y, kst, status, st); break;
-      case 2: e = launch_apply_t<float, 2>(g, subs, nsub, max_bp, L, dinv, r, Y, kst, status, st); break;
-      case 3: e = launch_apply_t<float, 3>(g, subs, nsub, max_bp, L, dinv, r, Y, kst, status, st); break;
-      default: e = launch_apply_t<float, 4>(g, subs, nsub, max_bp, L, dinv, r, Y, kst, status, st); break;
+    switch (S) {
+      case 1: e = launch_apply_t<float, 1>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
+      case 2: e = launch_apply_t<float, 2>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
+      case 3: e = launch_apply_t<float, 3>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
+      default: e = launch_apply_t<float, 4>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
     }
   }
   if (e != cudaSuccess) return e;

@@ -43,6 +43,15 @@ __device__ __forceinline__ cx<R> fms(cx<R> acc, cx<R> a, cx<R> b) {
   acc.im = fma(-a.im, b.re, acc.im);
   return acc;
 }
+// acc + a*b with fused multiply-adds
+template <typename R>
+__device__ __forceinline__ cx<R> fmac(cx<R> acc, cx<R> a, cx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
 // acc + conj(a)*b
 template <typename R>
 __device__ __forceinline__ cx<R> fcma(cx<R> acc, cx<R> a, cx<R> b) {

@@ -12,7 +12,11 @@
 //   3. moves row k+b+1 of A_j into the slot freed by row k.
 // Output layout: L_j column k at l_off + k*bp (bp >= b, entries b..bp-1 are
 // zero), rows k+1..k+b; D^-1 at v_off + k. Rows n..npad-1 are identity
-// padding, so their L columns are zero.
+// padding, so their L columns are zero. A second copy holds the rows of L_j
+// in reversed order: row i of L, read leftwards (L(i,i-1), L(i,i-2), ...),
+// at l_off + (npad-1-i)*bp; this is the column band of L^T in reversed
+// index order, which the backward sweep of the apply streams. The caller
+// zero-fills that copy first (entries left of column 0 stay zero).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -38,7 +42,8 @@ __device__ __forceinline__ cx<R> aloc_val(const c128* __restrict__ A, const SubD
 template <typename R>
 __global__ void __launch_bounds__(kFactorThreads)
     k_factor_ldlt(const SubDesc* __restrict__ subs, const c128* __restrict__ Aloc, cx<R>* __restrict__ Lall,
-                  cx<R>* __restrict__ dinv_all, double* __restrict__ pivstats, DevStatus* status) {
+                  cx<R>* __restrict__ Lrev_all, cx<R>* __restrict__ dinv_all, double* __restrict__ pivstats,
+                  DevStatus* status) {
   extern __shared__ __align__(16) unsigned char sm[];
   const SubDesc sd = subs[blockIdx.x];
   const int tid = threadIdx.x;
@@ -49,6 +54,7 @@ __global__ void __launch_bounds__(kFactorThreads)
   cx<R>* lbuf = cbuf + Wc;
   uint16_t* pairs = reinterpret_cast<uint16_t*>(lbuf + Wc);
   cx<R>* L = Lall + sd.l_off;
+  cx<R>* Lr = Lrev_all + sd.l_off;
   cx<R>* dv = dinv_all + sd.v_off;
 
   // (i', j') with 1 <= j' <= i' <= b, column by column
@@ -96,6 +102,7 @@ __global__ void __launch_bounds__(kFactorThreads)
         cx<R> l = c * di;
         lbuf[tid] = l;
         L[(long long)k * bp + (tid - 1)] = l;
+        if (k + tid < sd.npad) Lr[(long long)(sd.npad - 1 - (k + tid)) * bp + (tid - 1)] = l;
       }
     }
     __syncthreads();
@@ -137,18 +144,19 @@ size_t factor_smem_bytes(int b, int prec) {
 }
 
 cudaError_t launch_factor(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
-                          void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
+                          void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
   size_t smem = factor_smem_bytes(max_b, prec);
   cudaError_t e;
   if (prec == 0) {
     e = cudaFuncSetAttribute(k_factor_ldlt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_factor_ldlt<double><<<nsub, kFactorThreads, smem, st>>>(subs, Aloc, (c128*)L, (c128*)dinv, pivstats,
-                                                               status);
+    k_factor_ldlt<double><<<nsub, kFactorThreads, smem, st>>>(subs, Aloc, (c128*)L, (c128*)Lrev, (c128*)dinv,
+                                                               pivstats, status);
   } else {
     e = cudaFuncSetAttribute(k_factor_ldlt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_factor_ldlt<float><<<nsub, kFactorThreads, smem, st>>>(subs, Aloc, (c64*)L, (c64*)dinv, pivstats, status);
+    k_factor_ldlt<float><<<nsub, kFactorThreads, smem, st>>>(subs, Aloc, (c64*)L, (c64*)Lrev, (c64*)dinv, pivstats,
+                                                             status);
   }
   return cudaGetLastError();
 }

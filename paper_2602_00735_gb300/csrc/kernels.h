@@ -18,7 +18,8 @@ struct KState {
   int jdone;       // directions in the current cycle
   int breakdown;   // ||w|| == 0
   int nan;         // non-finite residual estimate
-  int pad0, pad1;
+  int reorth;      // the current direction needs a second Gram-Schmidt pass
+  int reorths;     // second passes taken over the solve
   double bnorm;    // ||b||_2
   double est;      // latest |g_{j+1}| / ||b||
   double hnorm;    // latest ||w||_2
@@ -35,12 +36,12 @@ cudaError_t launch_rhs(const Geo& g, const double* cen, const double* amp, int n
 // factor.cu
 size_t factor_smem_bytes(int b, int prec);
 cudaError_t launch_factor(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
-                          void* dinv, double* pivstats, DevStatus* status, cudaStream_t st);
+                          void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st);
 
 // apply.cu
 size_t apply_smem_bytes(int max_bp, int prec);
 cudaError_t launch_apply(int prec, const Geo& g, const SubDesc* subs, int nsub, int max_b, int max_bp,
-                         const void* L, const void* dinv, const c128* r, void* Y, c128* z,
+                         const void* Lf, const void* Lb, const void* dinv, const c128* r, void* Y, c128* z,
                          const KState* kst, DevStatus* status, cudaStream_t st);
 
 // krylov.cu
@@ -48,18 +49,19 @@ cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, cons
                         const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st);
 int dot_blocks();
 cudaError_t launch_dots(const c128* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
-                        const KState* kst, cudaStream_t st);
-cudaError_t launch_dots_finish(const c128* partial, int ncols, c128* out, int accumulate, const KState* kst,
+                        const KState* kst, int gate, cudaStream_t st);
+cudaError_t launch_dots_finish(const c128* partial, int ncols, c128* out, int accumulate, const KState* kst, int gate,
                                cudaStream_t st);
 cudaError_t launch_axpys(const c128* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
-                         long long n, const KState* kst, cudaStream_t st);
-cudaError_t launch_add(c128* dst, const c128* src, int cnt, const KState* kst, cudaStream_t st);
-cudaError_t launch_norm_finish(const c128* partial, double* out, c128* hslot, const KState* kst,
+                         long long n, const KState* kst, int gate, cudaStream_t st);
+cudaError_t launch_add(c128* dst, const c128* src, int cnt, const KState* kst, int gate, cudaStream_t st);
+cudaError_t launch_norm_finish(const c128* partial, double* out, c128* hslot, const KState* kst, int gate,
                                cudaStream_t st);
 cudaError_t launch_scale_inv(c128* v, long long n, const double* nrm, const KState* kst, cudaStream_t st);
 cudaError_t launch_cycle_init(KState* kst, c128* gvec, int m, double rtol, double* hist, cudaStream_t st);
 cudaError_t launch_givens(KState* kst, c128* H, int ldh, double* cs, c128* sn, c128* gvec, int j, double rtol,
                           int mcycle, int maxit, double* hist, cudaStream_t st);
+cudaError_t launch_reorth_decide(KState* kst, c128* hcol, int j, cudaStream_t st);
 cudaError_t launch_backsolve(const c128* H, int ldh, const c128* gvec, const KState* kst, c128* y,
                              cudaStream_t st);
 cudaError_t launch_axpy_state(c128* x, const c128* v, long long n, cudaStream_t st);

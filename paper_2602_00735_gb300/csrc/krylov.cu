@@ -19,6 +19,12 @@ namespace {
 constexpr int kThreads = 256;
 int g_num_sms = 0;
 
+// Kernels of a cycle return at once after the stop flag is set; gated ones
+// (the second Gram-Schmidt pass) also when no reorthogonalisation is due.
+__device__ __forceinline__ bool skip(const KState* kst, int gate) {
+  return kst != nullptr && (kst->stop || (gate && !kst->reorth));
+}
+
 __device__ __forceinline__ c128 warp_sum(c128 v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -49,21 +55,23 @@ __global__ void k_spmv(long long n, int nx, const c128* __restrict__ D, const c1
   if (kst != nullptr && kst->stop) return;
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (r >= n) return;
-  c128 acc = D[r] * x[r];
-  if (r >= 1) acc = acc + CW[r] * x[r - 1];
-  if (r + 1 < n) acc = acc + CW[r + 1] * x[r + 1];
-  if (r >= nx) acc = acc + CS[r] * x[r - nx];
-  if (r + nx < n) acc = acc + CS[r + nx] * x[r + nx];
-  if (r >= nx + 1) acc = acc + CSW[r] * x[r - nx - 1];
-  if (r + nx + 1 < n) acc = acc + CSW[r + nx + 1] * x[r + nx + 1];
+  c128 a0 = mk(0.0, 0.0), a1 = mk(0.0, 0.0);
+  a0 = fmac(a0, D[r], x[r]);
+  if (r >= 1) a1 = fmac(a1, CW[r], x[r - 1]);
+  if (r + 1 < n) a0 = fmac(a0, CW[r + 1], x[r + 1]);
+  if (r >= nx) a1 = fmac(a1, CS[r], x[r - nx]);
+  if (r + nx < n) a0 = fmac(a0, CS[r + nx], x[r + nx]);
+  if (r >= nx + 1) a1 = fmac(a1, CSW[r], x[r - nx - 1]);
+  if (r + nx + 1 < n) a0 = fmac(a0, CSW[r + nx + 1], x[r + nx + 1]);
+  const c128 acc = a0 + a1;
   y[r] = bsub ? bsub[r] - acc : acc;
 }
 
 // partial[c * gridDim.x + blk] = sum over the block's rows of conj(V_c) w
 __global__ void __launch_bounds__(kThreads)
     k_dots(const c128* __restrict__ V, long long ldv, const c128* __restrict__ w, long long n,
-           c128* __restrict__ partial, const KState* __restrict__ kst) {
-  if (kst != nullptr && kst->stop) return;
+           c128* __restrict__ partial, const KState* __restrict__ kst, int gate) {
+  if (skip(kst, gate)) return;
   const int c = blockIdx.y;
   const long long per = (n + gridDim.x - 1) / gridDim.x;
   const long long r0 = blockIdx.x * per;
@@ -82,8 +90,8 @@ __global__ void __launch_bounds__(kThreads)
 
 // out[c] (+)= sum_blk partial[c][blk], one warp per column
 __global__ void k_dots_finish(const c128* __restrict__ partial, int G, int ncols, c128* __restrict__ out,
-                              int accumulate, const KState* __restrict__ kst) {
-  if (kst != nullptr && kst->stop) return;
+                              int accumulate, const KState* __restrict__ kst, int gate) {
+  if (skip(kst, gate)) return;
   const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int l = threadIdx.x & 31;
   if (c >= ncols) return;
@@ -96,36 +104,36 @@ __global__ void k_dots_finish(const c128* __restrict__ partial, int G, int ncols
 // w += sign * sum_c V_c h_c
 __global__ void __launch_bounds__(kThreads)
     k_axpys(const c128* __restrict__ V, long long ldv, int ncols, const c128* __restrict__ h, double sign,
-            c128* __restrict__ w, long long n, const KState* __restrict__ kst) {
-  if (kst != nullptr && kst->stop) return;
+            c128* __restrict__ w, long long n, const KState* __restrict__ kst, int gate) {
+  if (skip(kst, gate)) return;
   extern __shared__ c128 hs[];
   for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = sign * h[c];
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
-    c128 acc = w[r];
+    c128 a0 = w[r], a1 = mk(0.0, 0.0);
     int c = 0;
     for (; c + 1 < ncols; c += 2) {
-      c128 v0 = V[c * ldv + r], v1 = V[(c + 1) * ldv + r];
-      acc = acc + v0 * hs[c];
-      acc = acc + v1 * hs[c + 1];
+      const c128 v0 = V[c * ldv + r], v1 = V[(c + 1) * ldv + r];
+      a0 = fmac(a0, v0, hs[c]);
+      a1 = fmac(a1, v1, hs[c + 1]);
     }
-    if (c < ncols) acc = acc + V[c * ldv + r] * hs[c];
-    w[r] = acc;
+    if (c < ncols) a0 = fmac(a0, V[c * ldv + r], hs[c]);
+    w[r] = a0 + a1;
   }
 }
 
 __global__ void k_add(c128* __restrict__ dst, const c128* __restrict__ src, int cnt,
-                      const KState* __restrict__ kst) {
-  if (kst != nullptr && kst->stop) return;
+                      const KState* __restrict__ kst, int gate) {
+  if (skip(kst, gate)) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < cnt) dst[i] = dst[i] + src[i];
 }
 
 // ||w|| from the partial sums of conj(w) w
 __global__ void k_norm_finish(const c128* __restrict__ partial, int G, double* out, c128* hslot,
-                              const KState* __restrict__ kst) {
-  if (kst != nullptr && kst->stop) return;
+                              const KState* __restrict__ kst, int gate) {
+  if (skip(kst, gate)) return;
   double s = 0.0;
   for (int b = threadIdx.x; b < G; b += 32) s += partial[b].re;
 #pragma unroll
@@ -145,6 +153,19 @@ __global__ void k_scale_inv(c128* __restrict__ v, long long n, const double* __r
   const double s = 1.0 / d;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) v[r] = s * v[r];
+}
+
+// DGKS test after one classical Gram-Schmidt pass: hcol[j+1] holds ||w||^2
+// from before the projection, kst->hnorm = ||w'|| after it. A second pass is
+// due when ||w'|| < ||w|| / sqrt(2); otherwise ||w'|| is the new subdiagonal.
+__global__ void k_reorth_decide(KState* kst, c128* hcol, int j) {
+  if (threadIdx.x != 0 || kst->stop) return;
+  const double w2 = hcol[j + 1].re;
+  const double nu = kst->hnorm;
+  const int need = (nu * nu < 0.5 * w2) ? 1 : 0;
+  kst->reorth = need;
+  kst->reorths += need;
+  if (!need) hcol[j + 1] = mk(nu, 0.0);
 }
 
 // Start of an Arnoldi cycle: beta = ||r0|| (in kst->hnorm), g = beta e_1.
@@ -261,40 +282,40 @@ cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, cons
 }
 
 cudaError_t launch_dots(const c128* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
-                        const KState* kst, cudaStream_t st) {
+                        const KState* kst, int gate, cudaStream_t st) {
   dim3 grid(dot_blocks(), ncols);
-  k_dots<<<grid, kThreads, 0, st>>>(V, ldv, w, n, partial, kst);
+  k_dots<<<grid, kThreads, 0, st>>>(V, ldv, w, n, partial, kst, gate);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dots_finish(const c128* partial, int ncols, c128* out, int accumulate, const KState* kst,
-                               cudaStream_t st) {
+                               int gate, cudaStream_t st) {
   int per = kThreads / 32;
   k_dots_finish<<<(ncols + per - 1) / per, kThreads, 0, st>>>(partial, dot_blocks(), ncols, out, accumulate,
-                                                              kst);
+                                                              kst, gate);
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpys(const c128* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
-                         long long n, const KState* kst, cudaStream_t st) {
+                         long long n, const KState* kst, int gate, cudaStream_t st) {
   dot_blocks();
   size_t smem = (size_t)ncols * sizeof(c128);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_axpys, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_axpys<<<grid_for(n, kThreads), kThreads, smem, st>>>(V, ldv, ncols, h, sign, w, n, kst);
+  k_axpys<<<grid_for(n, kThreads), kThreads, smem, st>>>(V, ldv, ncols, h, sign, w, n, kst, gate);
   return cudaGetLastError();
 }
 
-cudaError_t launch_add(c128* dst, const c128* src, int cnt, const KState* kst, cudaStream_t st) {
-  k_add<<<(cnt + 127) / 128, 128, 0, st>>>(dst, src, cnt, kst);
+cudaError_t launch_add(c128* dst, const c128* src, int cnt, const KState* kst, int gate, cudaStream_t st) {
+  k_add<<<(cnt + 127) / 128, 128, 0, st>>>(dst, src, cnt, kst, gate);
   return cudaGetLastError();
 }
 
-cudaError_t launch_norm_finish(const c128* partial, double* out, c128* hslot, const KState* kst,
+cudaError_t launch_norm_finish(const c128* partial, double* out, c128* hslot, const KState* kst, int gate,
                                cudaStream_t st) {
-  k_norm_finish<<<1, 32, 0, st>>>(partial, dot_blocks(), out, hslot, kst);
+  k_norm_finish<<<1, 32, 0, st>>>(partial, dot_blocks(), out, hslot, kst, gate);
   return cudaGetLastError();
 }
 
@@ -312,6 +333,11 @@ cudaError_t launch_cycle_init(KState* kst, c128* gvec, int m, double rtol, doubl
 cudaError_t launch_givens(KState* kst, c128* H, int ldh, double* cs, c128* sn, c128* gvec, int j, double rtol,
                           int mcycle, int maxit, double* hist, cudaStream_t st) {
   k_givens<<<1, 32, 0, st>>>(kst, H, ldh, cs, sn, gvec, j, rtol, mcycle, maxit, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reorth_decide(KState* kst, c128* hcol, int j, cudaStream_t st) {
+  k_reorth_decide<<<1, 32, 0, st>>>(kst, hcol, j);
   return cudaGetLastError();
 }
 

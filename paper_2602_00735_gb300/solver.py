@@ -26,7 +26,8 @@ def _dev_ptr(t: torch.Tensor, n: int) -> int:
 class RasPml:
     """Handle on a set-up problem: global matrix, covering, local factors."""
 
-    def __init__(self, params: dict, factor_prec: int = 0, device=None, stream: torch.cuda.Stream | None = None):
+    def __init__(self, params: dict, factor_prec: int = 0, ortho: int = 0, device=None,
+                 stream: torch.cuda.Stream | None = None):
         self.lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
@@ -35,6 +36,7 @@ class RasPml:
         for key in PARAM_KEYS:
             setattr(p, key, params[key])
         p.factor_prec = int(factor_prec)
+        p.ortho = int(ortho)
         self._h = c_void_p()
         with torch.cuda.device(self.device):
             _lib.check("ras_pml_setup", self.lib.ras_pml_setup(byref(p), c_void_p(self.stream.cuda_stream),

@@ -63,8 +63,9 @@ def test_apply_fp64_matches_oracle(solver_cls, name, kw):
         assert s.info()["min_pivot_ratio"] > 0
 
 
+@pytest.mark.parametrize("ortho", [0, 1])
 @pytest.mark.parametrize("name", ["tiny3", "small", "c0"])
-def test_fgmres_fixed_iterations_match_oracle(solver_cls, name):
+def test_fgmres_fixed_iterations_match_oracle(solver_cls, name, ortho):
     """Same m directions from x0 = 0: the iterates agree to 1e-10 (CGS2 on the
     GPU vs modified Gram-Schmidt in the oracle: equal in exact arithmetic)."""
     w = variant(name)
@@ -73,7 +74,7 @@ def test_fgmres_fixed_iterations_match_oracle(solver_cls, name):
     bo = fem.assemble_rhs(p, w.centres, w.amps, w.width)
     m = 7
     xo, _, _, ho = krylov.fgmres(A.dot, R.apply, bo, rtol=0.0, maxit=m)
-    with solver_cls(p) as s:
+    with solver_cls(p, ortho=ortho) as s:
         b = s.assemble_rhs(w.centres, w.amps, w.width)
         x, it, relres, st = s.solve(b, rtol=0.0, maxit=m)
         assert it == m and st == 1
@@ -83,14 +84,15 @@ def test_fgmres_fixed_iterations_match_oracle(solver_cls, name):
         assert np.max(np.abs(h - np.array(ho)) / np.array(ho)) <= 1e-8
 
 
+@pytest.mark.parametrize("ortho", [0, 1])
 @pytest.mark.parametrize("name,kw", CASES[:6], ids=IDS[:6])
-def test_converged_solve_matches_direct_solve(solver_cls, name, kw):
+def test_converged_solve_matches_direct_solve(solver_cls, name, kw, ortho):
     w = variant(name, **kw)
     p = w.params()
     grid, A, _ = oracle_problem(w)
     bo = fem.assemble_rhs(p, w.centres, w.amps, w.width)
     u = fem.direct_solve(A, bo)
-    with solver_cls(p) as s:
+    with solver_cls(p, ortho=ortho) as s:
         b = s.assemble_rhs(w.centres, w.amps, w.width)
         x, it, relres, st = s.solve(b, rtol=1e-12, maxit=400)
         assert st == 0 and relres <= 1e-12
