@@ -361,8 +361,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c2")
-    ap.add_argument("--ortho", type=int, default=0, choices=[0, 1],
-                    help="0: classical Gram-Schmidt twice; 1: once plus the DGKS reorthogonalisation test")
+    ap.add_argument("--ortho", type=int, default=2, choices=[0, 1, 2],
+                    help="0: classical Gram-Schmidt twice; 1: once plus the DGKS reorthogonalisation test; "
+                         "2: once")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -81,10 +81,11 @@ typedef struct {
                              1: Dirichlet closure (RAS-PML-Drch, Section 2)    */
   int    factor_prec;     /* local factors and solves: 0 complex128,
                              1 complex64 (outer iteration stays complex128)    */
-  int    ortho;           /* Arnoldi orthogonalisation, both in complex128:
+  int    ortho;           /* Arnoldi orthogonalisation, all in complex128:
                              0 classical Gram-Schmidt applied twice;
                              1 classical Gram-Schmidt once, repeated only when
-                             ||w'|| < ||w||/sqrt(2) (the DGKS test)            */
+                             ||w'|| < ||w||/sqrt(2) (the DGKS test);
+                             2 classical Gram-Schmidt once                     */
 } ras_pml_params;
 
 /* Sizes and statistics of a handle (filled by ras_pml_info). */

@@ -213,7 +213,7 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   const ras_pml_params& p = *pp;
   if (!(p.k >= 0.0) || !(p.h > 0.0) || !(p.kappa_g >= 0.0) || !(p.x1 > p.x0) || !(p.y1 > p.y0) || p.px < 1 ||
       p.py < 1 || !(p.g_ramp > 0.0) || !(p.g_amp >= 0.0) || (p.local_bc != 0 && p.local_bc != 1) ||
-      (p.factor_prec != 0 && p.factor_prec != 1) || (p.ortho != 0 && p.ortho != 1))
+      (p.factor_prec != 0 && p.factor_prec != 1) || (p.ortho < 0 || p.ortho > 2))
     return RASPML_EBADARG;
   const double lx = p.x1 - p.x0 + 2 * p.kappa_g, ly = p.y1 - p.y0 + 2 * p.kappa_g;
   const long long Mx = std::llround(lx / p.h), My = std::llround(ly / p.h);
@@ -508,7 +508,7 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
           RP_CUDA(rp::launch_dots_finish(h->partial, jj + 2, hcol, 0, h->kst, 0, st));
           RP_CUDA(rp::launch_axpys(h->V, n, jj + 1, hcol, -1.0, w, n, h->kst, 0, st));
           if ((s = dev_norm(h, w, &h->kst->hnorm, nullptr, h->kst))) return s;
-          RP_CUDA(rp::launch_reorth_decide(h->kst, hcol, jj, st));
+          RP_CUDA(rp::launch_reorth_decide(h->kst, hcol, jj, h->p.ortho == 1 ? 0.5 : 0.0, st));
           // second pass only where the DGKS test fired
           RP_CUDA(rp::launch_dots(h->V, n, jj + 1, w, n, h->partial, h->kst, 1, st));
           RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, h->hbuf, 0, h->kst, 1, st));
@@ -663,3 +663,4 @@ int ras_pml_history(const ras_pml_handle* h, double* hist_host, int cap, int* co
 }
 
 }  // extern "C"
+

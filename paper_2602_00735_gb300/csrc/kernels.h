@@ -61,7 +61,7 @@ cudaError_t launch_scale_inv(c128* v, long long n, const double* nrm, const KSta
 cudaError_t launch_cycle_init(KState* kst, c128* gvec, int m, double rtol, double* hist, cudaStream_t st);
 cudaError_t launch_givens(KState* kst, c128* H, int ldh, double* cs, c128* sn, c128* gvec, int j, double rtol,
                           int mcycle, int maxit, double* hist, cudaStream_t st);
-cudaError_t launch_reorth_decide(KState* kst, c128* hcol, int j, cudaStream_t st);
+cudaError_t launch_reorth_decide(KState* kst, c128* hcol, int j, double eta2, cudaStream_t st);
 cudaError_t launch_backsolve(const c128* H, int ldh, const c128* gvec, const KState* kst, c128* y,
                              cudaStream_t st);
 cudaError_t launch_axpy_state(c128* x, const c128* v, long long n, cudaStream_t st);

@@ -158,11 +158,12 @@ __global__ void k_scale_inv(c128* __restrict__ v, long long n, const double* __r
 // DGKS test after one classical Gram-Schmidt pass: hcol[j+1] holds ||w||^2
 // from before the projection, kst->hnorm = ||w'|| after it. A second pass is
 // due when ||w'|| < ||w|| / sqrt(2); otherwise ||w'|| is the new subdiagonal.
-__global__ void k_reorth_decide(KState* kst, c128* hcol, int j) {
+// eta2 = 0 disables the second pass (classical Gram-Schmidt once).
+__global__ void k_reorth_decide(KState* kst, c128* hcol, int j, double eta2) {
   if (threadIdx.x != 0 || kst->stop) return;
   const double w2 = hcol[j + 1].re;
   const double nu = kst->hnorm;
-  const int need = (nu * nu < 0.5 * w2) ? 1 : 0;
+  const int need = (nu * nu < eta2 * w2) ? 1 : 0;
   kst->reorth = need;
   kst->reorths += need;
   if (!need) hcol[j + 1] = mk(nu, 0.0);
@@ -336,8 +337,8 @@ cudaError_t launch_givens(KState* kst, c128* H, int ldh, double* cs, c128* sn, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_reorth_decide(KState* kst, c128* hcol, int j, cudaStream_t st) {
-  k_reorth_decide<<<1, 32, 0, st>>>(kst, hcol, j);
+cudaError_t launch_reorth_decide(KState* kst, c128* hcol, int j, double eta2, cudaStream_t st) {
+  k_reorth_decide<<<1, 32, 0, st>>>(kst, hcol, j, eta2);
   return cudaGetLastError();
 }
 
