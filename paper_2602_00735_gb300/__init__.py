@@ -12,7 +12,7 @@ __all__ = ["RasPml", "load", "RasPmlError", "SYMBOLS", "build"]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    from .build import build as _build
+    from .buildlib import build as _build
     return _build(force=force, verbose=verbose)
 
 
