@@ -128,6 +128,29 @@ int ras_pml_assemble_rhs(ras_pml_handle* h, const double* centres_host,
                          const double* amps_host, int ns, double width,
                          rp_c128* b_dev);
 
+/* ras_pml_assemble_rhs without any device allocation. The paper has no
+ * counterpart: this is a service for callers that cannot call cudaMalloc or
+ * cudaFree at this point, e.g. applications whose caching allocator has
+ * already reserved the device's memory (so cudaMalloc fails), or loops that
+ * must not stall on the device-wide synchronisation cudaFree implies.
+ * ras_pml_assemble_rhs allocates and frees a small device table of the
+ * sources on every call; this variant copies the sources into a fixed
+ * device array of the library instead (24 KB per device, held until the
+ * process exits) and then runs the same kernel, so b_dev is identical.
+ *   - At most 1024 sources; larger ns returns RASPML_EBADARG with a message.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls on a device share the array, and each call overwrites the
+ *     entries it uses (nothing needs clearing). Calls whose work overlaps on
+ *     the GPU (different streams, not ordered) race on it.
+ *   - Returns after enqueueing on the handle's stream. Pageable host arrays
+ *     may be reused on return; pinned ones only after the stream has run
+ *     the copy. */
+int ras_pml_assemble_rhs_noalloc(ras_pml_handle* h, const double* centres_host,
+                                 const double* amps_host, int ns, double width,
+                                 rp_c128* b_dev);
+
 /* Assembles every local operator A_j (Section 2; impedance term of
  * Section 3 (ii) when local_bc = 0) and factors it as A_j = L_j D_j L_j^T
  * (no pivoting; A_j is complex symmetric) in the handle's factor precision.

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -664,3 +665,63 @@ int ras_pml_history(const ras_pml_handle* h, double* hist_host, int cap, int* co
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// ras_pml_assemble_rhs_noalloc: the load-vector kernel with its source table
+// in a fixed device array instead of a per-call cudaMalloc/cudaFree.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxSources = 1024;
+constexpr int kNoAllocMaxDevices = 256;
+
+// Source table shared by every call on a device: centres (x, y) of up to
+// kNoAllocMaxSources sources, then their amplitudes. 24 KB per device that
+// loads the library, held until the process exits.
+__device__ __align__(256) double g_noalloc_sources[3 * kNoAllocMaxSources];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_table[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_sources on the current device. The host-side
+// name of the array is only a stand-in; the address must come from the
+// runtime, once per device, with that device current.
+int noalloc_table(int dev, double** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return RASPML_EBADARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_table[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_sources);
+    if (e != cudaSuccess || p == nullptr) {
+      std::fprintf(stderr, "raspml: cudaGetSymbolAddress of the source table failed: %s\n",
+                   cudaGetErrorString(e));
+      return RASPML_ECUDA;
+    }
+    g_noalloc_table[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_table[dev];
+  return RASPML_OK;
+}
+
+}  // namespace
+
+extern "C" int ras_pml_assemble_rhs_noalloc(ras_pml_handle* h, const double* centres_host, const double* amps_host,
+                                            int ns, double width, rp_c128* b_dev) {
+  if (!h || !b_dev || ns < 0 || (ns > 0 && (!centres_host || !amps_host)) || !(width > 0.0)) return RASPML_EBADARG;
+  if (ns > kNoAllocMaxSources) {
+    std::fprintf(stderr, "raspml: ras_pml_assemble_rhs_noalloc takes at most %d sources (got %d)\n",
+                 kNoAllocMaxSources, ns);
+    return RASPML_EBADARG;
+  }
+  cudaSetDevice(h->dev);
+  double* table = nullptr;
+  int s = noalloc_table(h->dev, &table);
+  if (s != RASPML_OK) return s;
+  double* cen = table;
+  double* amp = table + 2 * kNoAllocMaxSources;
+  if (ns > 0) {
+    RP_CUDA(cudaMemcpyAsync(cen, centres_host, sizeof(double) * 2 * ns, cudaMemcpyHostToDevice, h->st));
+    RP_CUDA(cudaMemcpyAsync(amp, amps_host, sizeof(double) * ns, cudaMemcpyHostToDevice, h->st));
+  }
+  RP_CUDA(rp::launch_rhs(h->geo, cen, amp, ns, width, (c128*)b_dev, h->st));
+  return RASPML_OK;
+}
