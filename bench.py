@@ -63,7 +63,7 @@ def peaks():
 def traffic_from_profile(kernel_src: str):
     """DRAM bytes per launch of k_apply from the committed ncu summary, or None
     when the summary is missing or was taken on a different apply.cu."""
-    path = os.path.join(ROOT, "profiles", "k_apply_c2.md")
+    path = os.path.join(ROOT, "profiles", "k_apply_sweep_c1.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -130,13 +130,16 @@ class ClockSampler:
 
 def cpu_sample(w, iters: int, n_local: int = 8):
     """Times the oracle on a bounded sample of workload w and scales it to a
-    full solve of `iters` FGMRES directions:
-      full:   global assembly, load vector, one global SpMV, one vdot and one
-              axpy on a length-n vector;
-      sample: local assembly + SuperLU factor + one local solve on n_local of
-              the subdomains, scaled to all of them.
-    Estimated time = assembly + load + nsub*factor + iters*(nsub*solve + SpMV
-    + norm) + MGS work sum_{j<iters} (j+1)*(vdot + axpy)."""
+    full solve of `iters` FGMRES directions, with the oracle's own code:
+      full:   global assembly, load vector, one global SpMV, one norm, and one
+              modified Gram-Schmidt step (vdot + w - h v) on length-n vectors;
+      sample: for n_local of the subdomains, local assembly + SuperLU factor
+              (ras.build_subdomain, splu) and one local apply (gather, solve,
+              weighted scatter: ras.local_apply), scaled to all subdomains.
+    Estimate = assembly + load + nsub*factor + iters*(nsub*apply + SpMV + norm)
+               + MGS steps sum_{j<iters} (j+1) + the final update (iters axpys)."""
+    import scipy.sparse.linalg as spla
+
     from oracle import fem, ras
     p = w.params()
     t0 = time.perf_counter()
@@ -144,44 +147,44 @@ def cpu_sample(w, iters: int, n_local: int = 8):
     t1 = time.perf_counter()
     b = fem.assemble_rhs(p, w.centres, w.amps, w.width)
     t2 = time.perf_counter()
-    x = b.copy()
-    y = A @ x
+    x = b / np.linalg.norm(b)
+    y = A.dot(x)
     t3 = time.perf_counter()
-    s = np.vdot(x, y)
+    nrm = np.linalg.norm(y)
     t4 = time.perf_counter()
-    y -= s * x
+    hij = np.vdot(x, y)
+    y = y - hij * x
     t5 = time.perf_counter()
-    rxs = ras.ranges_1d(grid.Mx, p["px"], p["ovlp_cells"], p["pml_cells"])
-    rys = ras.ranges_1d(grid.My, p["py"], p["ovlp_cells"], p["pml_cells"])
+    grid, rxs, rys = ras.covering(p)
     nsub = len(rxs) * len(rys)
     picks = np.linspace(0, nsub - 1, n_local).astype(int)
-    import scipy.sparse.linalg as spla
-    tf = ts = 0.0
+    tf = ta = 0.0
+    z = np.zeros(grid.n, dtype=np.complex128)
     for j in picks:
         a = time.perf_counter()
-        Aj, nodes, glob, _, _ = ras.local_operator(p, grid, rxs[j % len(rxs)], rys[j // len(rxs)])
-        lu = spla.splu(Aj.tocsc())
+        s = ras.build_subdomain(p, grid, rxs[j % len(rxs)], rys[j // len(rxs)])
+        lu = spla.splu(s.A.tocsc())
         c = time.perf_counter()
-        lu.solve(b[glob])
+        ras.local_apply(s, lu, b, z)
         d = time.perf_counter()
         tf += c - a
-        ts += d - c
+        ta += d - c
     tf /= len(picks)
-    ts /= len(picks)
-    t_vec = (t4 - t3) + (t5 - t4)
-    est = (t1 - t0) + (t2 - t1) + nsub * tf + iters * (nsub * ts + (t3 - t2) + (t4 - t3)) \
-        + t_vec * iters * (iters + 1) / 2
+    ta /= len(picks)
+    t_mgs = t5 - t4
+    est = (t1 - t0) + (t2 - t1) + nsub * tf + iters * (nsub * ta + (t3 - t2) + (t4 - t3)) \
+        + t_mgs * iters * (iters + 1) / 2 + iters * t_mgs
     sample_s = time.perf_counter() - t0
-    return est, sample_s, nsub
+    return est, sample_s, nsub, nrm
 
 
 def cpu_baseline_obj(w, iters):
-    est, sample_s, nsub = cpu_sample(w, iters)
+    est, sample_s, nsub, _ = cpu_sample(w, iters)
     return {"value": round(est, 3), "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle on {w.name}: global assembly, load vector, one SpMV and one vdot/axpy on the full "
-                       f"mesh; local assembly + SuperLU factor + one solve on 8 of {nsub} subdomains (scaled x"
-                       f"{nsub / 8:g}); scaled to {iters} FGMRES directions with modified Gram-Schmidt; "
-                       f"{sample_s:.1f} s of CPU work, one thread")}
+            "sample": (f"oracle on {w.name}: global assembly, load vector, one SpMV, one norm and one modified "
+                       f"Gram-Schmidt step on the full mesh; local assembly + SuperLU factor + one local apply "
+                       f"(gather, solve, weighted scatter) on 8 of {nsub} subdomains (scaled x{nsub / 8:g}); "
+                       f"scaled to {iters} FGMRES directions; {sample_s:.1f} s of CPU work, one thread")}
 
 
 # ---------------------------------------------------------------------------

@@ -204,24 +204,37 @@ def local_operator(p: dict, grid: fem.Grid, rx: Range1D, ry: Range1D):
     return A, nodes, glob, ix.size, iy.size
 
 
-def build_subdomains(p: dict):
-    """All subdomains of the covering with their local operators and weights."""
+def build_subdomain(p: dict, grid: fem.Grid, rx: Range1D, ry: Range1D) -> Subdomain:
+    """One subdomain: local operator, R_j and chi_j."""
+    ovlp = p["ovlp_cells"]
+    wx = pou_1d(rx, ovlp, grid.Mx)
+    wy = pou_1d(ry, ovlp, grid.My)
+    A, nodes, glob, nlx, nly = local_operator(p, grid, rx, ry)
+    ii = nodes % (grid.Mx + 1)
+    jj = nodes // (grid.Mx + 1)
+    return Subdomain(rx, ry, nodes, glob, wx[ii] * wy[jj], A, nlx, nly)
+
+
+def covering(p: dict):
+    """Grid and the per-direction ranges of the covering (Section 2)."""
     grid = fem.make_grid(p)
     ovlp, pml = p["ovlp_cells"], p["pml_cells"]
     if ovlp < 1:
         raise ValueError("overlap must be at least one cell")
-    rxs = ranges_1d(grid.Mx, p["px"], ovlp, pml)
-    rys = ranges_1d(grid.My, p["py"], ovlp, pml)
-    subs = []
-    for ry in rys:
-        wy = pou_1d(ry, ovlp, grid.My)
-        for rx in rxs:
-            wx = pou_1d(rx, ovlp, grid.Mx)
-            A, nodes, glob, nlx, nly = local_operator(p, grid, rx, ry)
-            ii = nodes % (grid.Mx + 1)
-            jj = nodes // (grid.Mx + 1)
-            subs.append(Subdomain(rx, ry, nodes, glob, wx[ii] * wy[jj], A, nlx, nly))
+    return grid, ranges_1d(grid.Mx, p["px"], ovlp, pml), ranges_1d(grid.My, p["py"], ovlp, pml)
+
+
+def build_subdomains(p: dict):
+    """All subdomains of the covering with their local operators and weights."""
+    grid, rxs, rys = covering(p)
+    subs = [build_subdomain(p, grid, rx, ry) for ry in rys for rx in rxs]
     return grid, subs
+
+
+def local_apply(s: Subdomain, lu, r, z):
+    """z += R_j^T (chi_j * A_j^-1 (R_j r)) for one subdomain."""
+    c = lu.solve(r[s.glob])
+    np.add.at(z, s.glob, s.chi * c)
 
 
 class RAS:
@@ -242,8 +255,7 @@ class RAS:
         r = np.asarray(r, dtype=np.complex128)
         z = np.zeros(self.n, dtype=np.complex128)
         for s, lu in zip(self.subs, self.lu):
-            c = lu.solve(r[s.glob])
-            np.add.at(z, s.glob, s.chi * c)
+            local_apply(s, lu, r, z)
         return z
 
     def chi_sum(self):
