@@ -386,7 +386,7 @@ int ras_pml_factor(ras_pml_handle* h) {
   cudaError_t e = cudaMemcpyAsync(h->status, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[0], h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->Lrev, 0, (size_t)h->sum_l * es, h->st);
-  if (e == cudaSuccess) e = rp::launch_local_rows(h->geo, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
+  if (e == cudaSuccess) e = rp::launch_local_rows(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
   if (e == cudaSuccess)
     e = rp::launch_factor(h->p.factor_prec, h->subs_d, h->nsub, h->max_b, Aloc, h->L, h->Lrev, h->dinv,
                           h->pivstats, h->status, h->st);

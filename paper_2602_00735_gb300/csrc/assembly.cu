@@ -20,19 +20,20 @@ namespace {
 // at the cell's edge midpoints. K* are (1/h^2) int_T of the stiffness
 // coefficients, mu* = (h^2/6) g1 g2 at a midpoint (the midpoint-rule weight
 // of the mass term).
+template <typename T>
 struct CellTerms {
-  c128 KxL, KyL, KxU, KyU;
-  c128 m01, m12, m02, m23, m03;
+  cx<T> KxL, KyL, KxU, KyU;
+  cx<T> m01, m12, m02, m23, m03;
 };
 
-template <class S>
-__device__ CellTerms cell_terms(const Geo& g, const S& st, int ci, int cj) {
+template <typename T, class S>
+__device__ CellTerms<T> cell_terms(const Geo& g, const S& st, int ci, int cj) {
   // x positions: 2ci (left edge), 2ci+1 (middle), 2ci+2 (right edge)
-  c128 xa = st.gx(2.0 * ci + 1.0), xb = st.gx(2.0 * ci + 2.0), xc = st.gx(2.0 * ci);
-  c128 ya = st.gy(2.0 * cj), yb = st.gy(2.0 * cj + 1.0), yc = st.gy(2.0 * cj + 2.0);
-  const double sixth = 1.0 / 6.0;
-  const double w = g.h * g.h * sixth;
-  CellTerms t;
+  cx<T> xa = st.gx(2.0 * ci + 1.0), xb = st.gx(2.0 * ci + 2.0), xc = st.gx(2.0 * ci);
+  cx<T> ya = st.gy(2.0 * cj), yb = st.gy(2.0 * cj + 1.0), yc = st.gy(2.0 * cj + 2.0);
+  const T sixth = (T)(1.0 / 6.0);
+  const T w = (T)(g.h * g.h * (1.0 / 6.0));
+  CellTerms<T> t;
   // lower triangle: m01 = (xa, ya), m12 = (xb, yb), m02 = (xa, yb)
   t.KxL = sixth * (cdiv(ya, xa) + cdiv(yb, xb) + cdiv(yb, xa));
   t.KyL = sixth * (cdiv(xa, ya) + cdiv(xb, yb) + cdiv(xa, yb));
@@ -47,6 +48,14 @@ __device__ CellTerms cell_terms(const Geo& g, const S& st, int ci, int cj) {
   return t;
 }
 
+// g'(d) in arithmetic type T; for T = double it is gprime() of common.cuh.
+template <typename T>
+__device__ __forceinline__ T gprime_t(double d, double amp, double ramp) {
+  if (!(d > 0.0)) return (T)0;
+  const T t = fmin((T)d / (T)ramp, (T)1);
+  return (T)amp * t * t * ((T)3 - (T)2 * t);
+}
+
 struct GlobalStretch {
   Geo g;
   __device__ c128 gx(double s) const { return gam_global_x(g, s); }
@@ -54,37 +63,47 @@ struct GlobalStretch {
   __device__ bool cell_ok(int ci, int cj) const { return ci >= 0 && ci < g.Mx && cj >= 0 && cj < g.My; }
 };
 
+// Local stretching g_j (Section 2) evaluated in arithmetic type T. Positions
+// and branch decisions are in double (half-index units), as for the global one.
+template <typename T>
 struct LocalStretch {
   Geo g;
   SubDesc sd;
-  __device__ c128 gx(double s) const { return gam_local_x(g, sd, s); }
-  __device__ c128 gy(double s) const { return gam_local_y(g, sd, s); }
+  __device__ cx<T> gam(double s, double x0, double x1, int lo, int hi, int flo, int fhi, double X0) const {
+    if ((sd.flags & fhi) && s >= 2.0 * hi) return mk((T)1, gprime_t<T>((s - 2.0 * hi) * g.hh, g.g_amp, g.g_ramp));
+    if ((sd.flags & flo) && s <= 2.0 * lo) return mk((T)1, gprime_t<T>((2.0 * lo - s) * g.hh, g.g_amp, g.g_ramp));
+    const double x = __dadd_rn(X0, __dmul_rn(s, g.hh));
+    const double d = fmax(fmax(x0 - x, x - x1), 0.0);
+    return mk((T)1, gprime_t<T>(d, g.g_amp, g.g_ramp));
+  }
+  __device__ cx<T> gx(double s) const { return gam(s, g.x0, g.x1, sd.int_lo_x, sd.int_hi_x, LO_X, HI_X, g.X0); }
+  __device__ cx<T> gy(double s) const { return gam(s, g.y0, g.y1, sd.int_lo_y, sd.int_hi_y, LO_Y, HI_Y, g.Y0); }
   __device__ bool cell_ok(int ci, int cj) const {
     return ci >= sd.ext_lo_x && ci < sd.ext_hi_x && cj >= sd.ext_lo_y && cj < sd.ext_hi_y;
   }
 };
 
 // Diagonal and lower couplings of node (i, j) from the cells around it.
-template <class S>
-__device__ void node_row(const Geo& g, const S& st, int i, int j, c128& D, c128& W, c128& Sx, c128& SW) {
-  const double q = 0.25 * g.k * g.k;  // k^2 * (hat product 1/2 * 1/2)
-  D = W = Sx = SW = mk(0.0, 0.0);
+template <typename T, class S>
+__device__ void node_row(const Geo& g, const S& st, int i, int j, cx<T>& D, cx<T>& W, cx<T>& Sx, cx<T>& SW) {
+  const T q = (T)(0.25 * g.k * g.k);  // k^2 * (hat product 1/2 * 1/2)
+  D = W = Sx = SW = mk((T)0, (T)0);
   if (st.cell_ok(i, j)) {
-    CellTerms t = cell_terms(g, st, i, j);
+    CellTerms<T> t = cell_terms<T>(g, st, i, j);
     D = D + t.KxL - q * (t.m01 + t.m02) + t.KyU - q * (t.m02 + t.m03);
   }
   if (st.cell_ok(i - 1, j)) {
-    CellTerms t = cell_terms(g, st, i - 1, j);
+    CellTerms<T> t = cell_terms<T>(g, st, i - 1, j);
     D = D + t.KxL + t.KyL - q * (t.m01 + t.m12);
     W = W - t.KxL - q * t.m01;
   }
   if (st.cell_ok(i, j - 1)) {
-    CellTerms t = cell_terms(g, st, i, j - 1);
+    CellTerms<T> t = cell_terms<T>(g, st, i, j - 1);
     D = D + t.KxU + t.KyU - q * (t.m23 + t.m03);
     Sx = Sx - t.KyU - q * t.m03;
   }
   if (st.cell_ok(i - 1, j - 1)) {
-    CellTerms t = cell_terms(g, st, i - 1, j - 1);
+    CellTerms<T> t = cell_terms<T>(g, st, i - 1, j - 1);
     D = D + t.KyL - q * (t.m12 + t.m02) + t.KxU - q * (t.m02 + t.m23);
     W = W - t.KxU - q * t.m23;
     Sx = Sx - t.KyL - q * t.m12;
@@ -94,23 +113,25 @@ __device__ void node_row(const Geo& g, const S& st, int i, int j, c128& D, c128&
 
 // Impedance closure (Section 3 (ii)): -i k int gamma_t phi_a phi_b ds on the
 // edges of the artificial boundary of Omega_j, 2-point Gauss per edge.
-__device__ void impedance_terms(const Geo& g, const SubDesc& sd, const LocalStretch& st, int i, int j,
-                                c128& D, c128& W, c128& Sx) {
-  const double q1 = 0.5 - 0.5 / sqrt(3.0), q2 = 0.5 + 0.5 / sqrt(3.0);
-  const c128 mik = mk(0.0, -g.k * 0.5 * g.h);  // -i k * (h/2): Gauss weight h/2
+template <typename T>
+__device__ void impedance_terms(const Geo& g, const SubDesc& sd, const LocalStretch<T>& st, int i, int j,
+                                cx<T>& D, cx<T>& W, cx<T>& Sx) {
+  const double q1d = 0.5 - 0.5 / sqrt(3.0), q2d = 0.5 + 0.5 / sqrt(3.0);
+  const T q1 = (T)q1d, q2 = (T)q2d, one = (T)1;
+  const cx<T> mik = mk((T)0, (T)(-g.k * 0.5 * g.h));  // -i k * (h/2): Gauss weight h/2
   // vertical sides x = const: tangential stretch gamma_2
   bool left = sd.ext_lo_x > 0 && i == sd.ext_lo_x;
   bool right = sd.ext_hi_x < g.Mx && i == sd.ext_hi_x;
   if (left || right) {
     if (j - 1 >= sd.ext_lo_y) {  // edge (i,j-1)-(i,j): node is its upper end
       int jc = j - 1;
-      c128 a = st.gy(2.0 * (jc + q1)), b = st.gy(2.0 * (jc + q2));
+      cx<T> a = st.gy(2.0 * (jc + q1d)), b = st.gy(2.0 * (jc + q2d));
       D = D + mik * (q1 * q1 * a + q2 * q2 * b);
-      Sx = Sx + mik * ((q1 * (1.0 - q1)) * a + (q2 * (1.0 - q2)) * b);
+      Sx = Sx + mik * ((q1 * (one - q1)) * a + (q2 * (one - q2)) * b);
     }
     if (j < sd.ext_hi_y) {       // edge (i,j)-(i,j+1): node is its lower end
-      c128 a = st.gy(2.0 * (j + q1)), b = st.gy(2.0 * (j + q2));
-      D = D + mik * ((1.0 - q1) * (1.0 - q1) * a + (1.0 - q2) * (1.0 - q2) * b);
+      cx<T> a = st.gy(2.0 * (j + q1d)), b = st.gy(2.0 * (j + q2d));
+      D = D + mik * ((one - q1) * (one - q1) * a + (one - q2) * (one - q2) * b);
     }
   }
   // horizontal sides y = const: tangential stretch gamma_1
@@ -119,13 +140,13 @@ __device__ void impedance_terms(const Geo& g, const SubDesc& sd, const LocalStre
   if (bottom || top) {
     if (i - 1 >= sd.ext_lo_x) {
       int ic = i - 1;
-      c128 a = st.gx(2.0 * (ic + q1)), b = st.gx(2.0 * (ic + q2));
+      cx<T> a = st.gx(2.0 * (ic + q1d)), b = st.gx(2.0 * (ic + q2d));
       D = D + mik * (q1 * q1 * a + q2 * q2 * b);
-      W = W + mik * ((q1 * (1.0 - q1)) * a + (q2 * (1.0 - q2)) * b);
+      W = W + mik * ((q1 * (one - q1)) * a + (q2 * (one - q2)) * b);
     }
     if (i < sd.ext_hi_x) {
-      c128 a = st.gx(2.0 * (i + q1)), b = st.gx(2.0 * (i + q2));
-      D = D + mik * ((1.0 - q1) * (1.0 - q1) * a + (1.0 - q2) * (1.0 - q2) * b);
+      cx<T> a = st.gx(2.0 * (i + q1d)), b = st.gx(2.0 * (i + q2d));
+      D = D + mik * ((one - q1) * (one - q1) * a + (one - q2) * (one - q2) * b);
     }
   }
 }
@@ -138,7 +159,7 @@ __global__ void k_global_stencil(Geo g, c128* __restrict__ D, c128* __restrict__
   int i = (int)(r % g.nx) + 1, j = (int)(r / g.nx) + 1;
   GlobalStretch st{g};
   c128 d, w, s, sw;
-  node_row(g, st, i, j, d, w, s, sw);
+  node_row<double>(g, st, i, j, d, w, s, sw);
   const c128 z = mk(0.0, 0.0);
   D[r] = d;
   CW[r] = (i > 1) ? w : z;            // couplings to outer-boundary nodes drop out
@@ -147,7 +168,10 @@ __global__ void k_global_stencil(Geo g, c128* __restrict__ D, c128* __restrict__
 }
 
 // One thread per local row; blockIdx.y = subdomain. Output Aloc[v_off + r]
-// = {D, W, S, SW}; padding rows (r >= n) are identity rows.
+// = {D, W, S, SW}; padding rows (r >= n) are identity rows. T is the
+// arithmetic type: double for complex128 factors, float for complex64 ones
+// (those entries are rounded to complex64 before the factorisation anyway).
+template <typename T>
 __global__ void k_local_rows(Geo g, const SubDesc* __restrict__ subs, c128* __restrict__ Aloc) {
   const SubDesc sd = subs[blockIdx.y];
   int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -160,14 +184,14 @@ __global__ void k_local_rows(Geo g, const SubDesc* __restrict__ subs, c128* __re
     return;
   }
   int i = sd.ix0 + r % sd.nlx, j = sd.iy0 + r / sd.nlx;
-  LocalStretch st{g, sd};
-  c128 d, w, s, sw;
-  node_row(g, st, i, j, d, w, s, sw);
-  if (g.local_bc == 0) impedance_terms(g, sd, st, i, j, d, w, s);
-  out[0] = d;
-  out[1] = (i > sd.ix0) ? w : z;
-  out[2] = (j > sd.iy0) ? s : z;
-  out[3] = (i > sd.ix0 && j > sd.iy0) ? sw : z;
+  LocalStretch<T> st{g, sd};
+  cx<T> d, w, s, sw;
+  node_row<T>(g, st, i, j, d, w, s, sw);
+  if (g.local_bc == 0) impedance_terms<T>(g, sd, st, i, j, d, w, s);
+  out[0] = cvt<double>(d);
+  out[1] = (i > sd.ix0) ? cvt<double>(w) : z;
+  out[2] = (j > sd.iy0) ? cvt<double>(s) : z;
+  out[3] = (i > sd.ix0 && j > sd.iy0) ? cvt<double>(sw) : z;
 }
 
 // f at half-index (sx, sy): sum of Gaussians, cut to the closed Omega_int.
@@ -177,8 +201,9 @@ __device__ double source_at(const Geo& g, const double* __restrict__ cen, const 
   if (!(x >= g.x0 && x <= g.x1 && y >= g.y0 && y <= g.y1)) return 0.0;
   double f = 0.0;
   for (int s = 0; s < ns; ++s) {
-    double dx = x - cen[2 * s], dy = y - cen[2 * s + 1];
-    f += amp[s] * exp(-(dx * dx + dy * dy) * inv_w2);
+    const double dx = x - cen[2 * s], dy = y - cen[2 * s + 1];
+    const double e = (dx * dx + dy * dy) * inv_w2;
+    if (e < 700.0) f += amp[s] * exp(-e);  // beyond: below 1e-304, skipped
   }
   return f;
 }
@@ -209,11 +234,14 @@ cudaError_t launch_global_stencil(const Geo& g, c128* D, c128* CW, c128* CS, c12
   return cudaGetLastError();
 }
 
-cudaError_t launch_local_rows(const Geo& g, const SubDesc* subs, int nsub, int max_npad, c128* Aloc,
+cudaError_t launch_local_rows(int prec, const Geo& g, const SubDesc* subs, int nsub, int max_npad, c128* Aloc,
                               cudaStream_t st) {
   int threads = 128;
   dim3 grid((max_npad + threads - 1) / threads, nsub);
-  k_local_rows<<<grid, threads, 0, st>>>(g, subs, Aloc);
+  if (prec == 0)
+    k_local_rows<double><<<grid, threads, 0, st>>>(g, subs, Aloc);
+  else
+    k_local_rows<float><<<grid, threads, 0, st>>>(g, subs, Aloc);
   return cudaGetLastError();
 }
 

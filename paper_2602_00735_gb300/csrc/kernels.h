@@ -28,7 +28,7 @@ struct KState {
 
 // assembly.cu
 cudaError_t launch_global_stencil(const Geo& g, c128* D, c128* CW, c128* CS, c128* CSW, cudaStream_t st);
-cudaError_t launch_local_rows(const Geo& g, const SubDesc* subs, int nsub, int max_npad, c128* Aloc,
+cudaError_t launch_local_rows(int prec, const Geo& g, const SubDesc* subs, int nsub, int max_npad, c128* Aloc,
                               cudaStream_t st);
 cudaError_t launch_rhs(const Geo& g, const double* cen, const double* amp, int ns, double width, c128* b,
                        cudaStream_t st);

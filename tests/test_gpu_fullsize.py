@@ -1,0 +1,132 @@
+"""Parity at the benchmark's full size (workload c2: k = 160*pi, 2.36M
+unknowns, 1024 subdomains), in the configuration bench.py times, on outputs
+the oracle computes one by one:
+
+- rows of A x and of the load vector at sampled nodes (the oracle assembles
+  the four cells around each node);
+- B^-1 r at nodes where a single subdomain carries the whole partition of
+  unity: there z = (A_j^-1 R_j r) at that node, and the oracle factors only
+  that A_j;
+- the solve: true residual, and the iteration count equal to the oracle's own
+  FGMRES count on c2 (tests/golden/oracle_iterations.json).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+import torch
+
+import workloads
+from gpu_util import random_vector, to_dev
+from oracle import fem, ras
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "oracle_iterations.json")
+
+
+@pytest.fixture(scope="module")
+def c2():
+    import __graft_entry__
+    __graft_entry__.build()
+    w = workloads.get("c2")
+    return w, w.params(), fem.make_grid(w.params())
+
+
+def _sample_nodes(grid, count, seed):
+    rng = np.random.default_rng(seed)
+    i = rng.integers(1, grid.Mx, size=count)
+    j = rng.integers(1, grid.My, size=count)
+    i[:4] = [1, grid.Mx - 1, 1, grid.Mx - 1]       # corners next to the outer boundary
+    j[:4] = [1, 1, grid.My - 1, grid.My - 1]
+    return i, j
+
+
+def _oracle_rows(p, grid, i, j):
+    """Rows of the global matrix and load vector at nodes (i, j), from the
+    four cells around each node (all of the node's triangles)."""
+    amp, ramp = p["g_amp"], p["g_ramp"]
+    gx = lambda s: fem.global_gamma_x(grid, s, amp, ramp)  # noqa: E731
+    gy = lambda s: fem.global_gamma_y(grid, s, amp, ramp)  # noqa: E731
+    num = fem.interior_numbering(grid)
+    rows = {}
+    for node in zip(i, j):
+        ci = np.array([node[0] - 1, node[0], node[0] - 1, node[0]])
+        cj = np.array([node[1] - 1, node[1] - 1, node[1], node[1]])
+        r, c, v = fem.assemble_cells(grid, ci, cj, gx, gy, p["k"])
+        nid = node[1] * (grid.Mx + 1) + node[0]
+        m = (r == nid) & (num[c] >= 0)
+        cols, vals = num[c[m]], v[m]
+        u, inv = np.unique(cols, return_inverse=True)
+        rows[node] = (u, np.bincount(inv, weights=vals.real) + 1j * np.bincount(inv, weights=vals.imag))
+    return rows
+
+
+def test_c2_matvec_and_rhs_rows(c2):
+    from paper_2602_00735_gb300 import RasPml
+    w, p, grid = c2
+    i, j = _sample_nodes(grid, 64, 0)
+    rows = _oracle_rows(p, grid, i, j)
+    f = fem.source_function(grid, w.centres, w.amps, w.width)
+    with RasPml(p, factor_prec=1, ortho=2) as s:
+        x = random_vector(grid.n, 11)
+        y = s.matvec(to_dev(x)).cpu().numpy()
+        b = s.assemble_rhs(w.centres, w.amps, w.width).cpu().numpy()
+    for (ii, jj) in zip(i, j):
+        g = (jj - 1) * grid.nx + (ii - 1)
+        cols, vals = rows[(ii, jj)]
+        ref = vals @ x[cols]
+        assert abs(y[g] - ref) <= 1e-13 * max(1.0, np.abs(vals).sum() * np.abs(x[cols]).max())
+        ci = np.array([ii - 1, ii, ii - 1, ii])
+        cj = np.array([jj - 1, jj - 1, jj, jj])
+        rr, vv = fem.load_cells(grid, ci, cj, f)
+        bref = vv[rr == jj * (grid.Mx + 1) + ii].sum()
+        assert abs(b[g] - bref) <= 1e-13 * max(1e-300, np.abs(b).max())
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-4), (0, 1e-10)])
+def test_c2_apply_on_single_cover_nodes(c2, prec, tol):
+    from paper_2602_00735_gb300 import RasPml
+    w, p, grid = c2
+    gr, rxs, rys = ras.covering(p)
+    r = random_vector(grid.n, 12)
+    with RasPml(p, factor_prec=prec, ortho=2) as s:
+        s.factor()
+        z = s.apply(to_dev(r)).cpu().numpy()
+    o = p["ovlp_cells"]
+    for (qx, qy) in ((0, 0), (31, 0), (13, 17), (31, 31), (0, 22)):
+        sub = ras.build_subdomain(p, grid, rxs[qx], rys[qy])
+        c = spla.splu(sub.A.tocsc()).solve(r[sub.glob])
+        ii = sub.nodes % (grid.Mx + 1)
+        jj = sub.nodes // (grid.Mx + 1)
+        # nodes whose covering is this subdomain alone: chi_j = 1 there
+        single = sub.chi == 1.0
+        single &= (ii >= sub.rx.box_lo + o) | ~np.array(sub.rx.lo_interior)
+        single &= (ii <= sub.rx.box_hi - o) | ~np.array(sub.rx.hi_interior)
+        single &= (jj >= sub.ry.box_lo + o) | ~np.array(sub.ry.lo_interior)
+        single &= (jj <= sub.ry.box_hi - o) | ~np.array(sub.ry.hi_interior)
+        assert single.sum() > 1000
+        zs = z[sub.glob[single]]
+        assert np.linalg.norm(zs - c[single]) <= tol * np.linalg.norm(c[single])
+
+
+def test_c2_solve_in_bench_configuration(c2):
+    from paper_2602_00735_gb300 import RasPml
+    w, p, grid = c2
+    gold = json.load(open(GOLD))["c2"]
+    with RasPml(p, factor_prec=1, ortho=2) as s:
+        b = s.assemble_rhs(w.centres, w.amps, w.width)
+        x, it, rel, st = s.solve(b, rtol=1e-6, maxit=1000)
+        assert st == 0 and rel <= 1e-6
+        r = b - s.matvec(x)
+        assert float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(b)) <= 1e-6
+        assert abs(it - gold["iters"]) <= 1
+        x64 = None
+    with RasPml(p, factor_prec=0, ortho=2) as s:
+        b = s.assemble_rhs(w.centres, w.amps, w.width)
+        x64, it64, rel64, st64 = s.solve(b, rtol=1e-6, maxit=1000)
+        assert st64 == 0 and it64 == gold["iters"]
+        assert abs(rel64 - gold["relres"]) <= 1e-3 * gold["relres"]
+    # the complex64-factor form lands within 1e-5 of the complex128 form
+    assert float(torch.linalg.vector_norm(x - x64) / torch.linalg.vector_norm(x64)) <= 1e-5
