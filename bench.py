@@ -205,8 +205,8 @@ def run_ours(args, rank, world, local_rank):
     p = w.params()
     stream = torch.cuda.current_stream(dev)
 
-    def one_step(prec, timing=False):
-        s = RasPml(p, factor_prec=prec, ortho=args.ortho)
+    def one_step(prec, timing=False, ortho=None):
+        s = RasPml(p, factor_prec=prec, ortho=args.ortho if ortho is None else ortho)
         if timing:
             s.set_timing(True)
         b = s.assemble_rhs(w.centres, w.amps, w.width)
@@ -214,9 +214,9 @@ def run_ours(args, rank, world, local_rank):
         x, it, rel, st = s.solve(b, rtol=RTOL, maxit=MAXIT)
         return s, x, it, rel, st
 
-    def timed(prec, K, W, timing=True):
+    def timed(prec, K, W, timing=True, ortho=None):
         for _ in range(W):
-            s, x, it, rel, st = one_step(prec)
+            s, x, it, rel, st = one_step(prec, ortho=ortho)
             s.close()
             del x
         if world > 1:
@@ -228,7 +228,7 @@ def run_ours(args, rank, world, local_rank):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            s, x, it, rel, st = one_step(prec, timing)
+            s, x, it, rel, st = one_step(prec, timing, ortho=ortho)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
@@ -248,8 +248,15 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     fp64 = None
     x_f64 = None
+    gs64 = None
+    if not args.skip_fp64 and args.ortho == 3:
+        t_g, per_g, x_g = timed(1, max(1, min(args.steps, 2)), 1, ortho=2)
+        gs64 = {"time_s": round(float(np.mean(t_g)), 4), "iters": per_g[-1]["iters"],
+                "ortho_ms": round(per_g[-1]["ortho_ms"], 2),
+                "error_vs_df": float(torch.linalg.vector_norm(x_g - x_c64) / torch.linalg.vector_norm(x_g))}
+        del x_g
     if not args.skip_fp64:
-        t_f64, per_f64, x_f64 = timed(0, max(1, min(args.steps, 2)), 1)
+        t_f64, per_f64, x_f64 = timed(0, max(1, min(args.steps, 2)), 1, ortho=2)
         fp64 = {"time_s": round(float(np.mean(t_f64)), 4), "iters": per_f64[-1]["iters"],
                 "relres": per_f64[-1]["relres"], "factor_ms": round(per_f64[-1]["factor_ms"], 2),
                 "solve_ms": round(per_f64[-1]["solve_ms"], 2),
@@ -321,7 +328,7 @@ def run_ours(args, rank, world, local_rank):
                      "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "algorithmic_bytes_per_launch": info["apply_bytes"]},
-        "fp64": fp64, "error_vs_fp64": err,
+        "fp64": fp64, "error_vs_fp64": err, "c64_fp64_gram_schmidt": gs64,
         "gpu_launches": int(sum(launches_per_step)),
         "gpu_launches_per_step": int(launches_per_step[-1]),
         "clocks": clk, "e2e": e2e,
@@ -364,9 +371,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c2")
-    ap.add_argument("--ortho", type=int, default=2, choices=[0, 1, 2],
+    ap.add_argument("--ortho", type=int, default=3, choices=[0, 1, 2, 3],
                     help="0: classical Gram-Schmidt twice; 1: once plus the DGKS reorthogonalisation test; "
-                         "2: once")
+                         "2: once; 3: once in double-float arithmetic")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -85,7 +85,11 @@ typedef struct {
                              0 classical Gram-Schmidt applied twice;
                              1 classical Gram-Schmidt once, repeated only when
                              ||w'|| < ||w||/sqrt(2) (the DGKS test);
-                             2 classical Gram-Schmidt once                     */
+                             2 classical Gram-Schmidt once;
+                             3 classical Gram-Schmidt once with the basis kept in
+                               complex128 and its products and sums in
+                               double-float arithmetic (two floats, about 46
+                               bits) on the FP32 pipe                          */
 } ras_pml_params;
 
 /* Sizes and statistics of a handle (filled by ras_pml_info). */

@@ -214,7 +214,7 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   const ras_pml_params& p = *pp;
   if (!(p.k >= 0.0) || !(p.h > 0.0) || !(p.kappa_g >= 0.0) || !(p.x1 > p.x0) || !(p.y1 > p.y0) || p.px < 1 ||
       p.py < 1 || !(p.g_ramp > 0.0) || !(p.g_amp >= 0.0) || (p.local_bc != 0 && p.local_bc != 1) ||
-      (p.factor_prec != 0 && p.factor_prec != 1) || (p.ortho < 0 || p.ortho > 2))
+      (p.factor_prec != 0 && p.factor_prec != 1) || (p.ortho < 0 || p.ortho > 3))
     return RASPML_EBADARG;
   const double lx = p.x1 - p.x0 + 2 * p.kappa_g, ly = p.y1 - p.y0 + 2 * p.kappa_g;
   const long long Mx = std::llround(lx / p.h), My = std::llround(ly / p.h);
@@ -503,6 +503,12 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
           RP_CUDA(rp::launch_axpys(h->V, n, jj + 1, h->hbuf, -1.0, w, n, h->kst, 0, st));
           RP_CUDA(rp::launch_add(hcol, h->hbuf, jj + 1, h->kst, 0, st));
           if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst))) return s;
+        } else if (h->p.ortho == 3) {
+          // one pass, products and sums in double-float arithmetic on the FP32 pipe
+          RP_CUDA(rp::launch_dots_df(h->V, n, jj + 1, w, n, h->partial, h->kst, 0, st));
+          RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, hcol, 0, h->kst, 0, st));
+          RP_CUDA(rp::launch_axpys_df(h->V, n, jj + 1, hcol, -1.0, w, n, h->kst, 0, st));
+          if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst))) return s;
         } else {
           // one pass; the projection also returns ||w||^2 (w is column jj+1 of V)
           RP_CUDA(rp::launch_dots(h->V, n, jj + 2, w, n, h->partial, h->kst, 0, st));
@@ -557,10 +563,10 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
   // launches: ||b|| (2); per cycle: residual, norm (2), init, scale, backsolve,
   // update, true residual, norm (2) = 10; per issued direction: 13 (CGS twice)
   // or 17 (one pass, test, gated second pass)
-  launches += 10 * cycles + (h->p.ortho == 0 ? 13 : 17) * issued;
+  launches += 10 * cycles + (h->p.ortho == 0 ? 13 : h->p.ortho == 3 ? 11 : 17) * issued;
   h->tm.launches = (int32_t)launches;
   h->tm.applies = total;
-  h->tm.reorths = h->p.ortho == 0 ? total : h->kst_host->reorths;
+  h->tm.reorths = h->p.ortho == 0 ? total : (h->p.ortho == 3 ? 0 : h->kst_host->reorths);
   if (h->timing) {
     RP_CUDA(cudaEventRecord(h->ev[4 * batch + 1], st));
     RP_CUDA(cudaEventSynchronize(h->ev[4 * batch + 1]));

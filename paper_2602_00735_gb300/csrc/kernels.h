@@ -54,6 +54,10 @@ cudaError_t launch_dots_finish(const c128* partial, int ncols, c128* out, int ac
                                cudaStream_t st);
 cudaError_t launch_axpys(const c128* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
                          long long n, const KState* kst, int gate, cudaStream_t st);
+cudaError_t launch_dots_df(const c128* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
+                           const KState* kst, int gate, cudaStream_t st);
+cudaError_t launch_axpys_df(const c128* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
+                            long long n, const KState* kst, int gate, cudaStream_t st);
 cudaError_t launch_add(c128* dst, const c128* src, int cnt, const KState* kst, int gate, cudaStream_t st);
 cudaError_t launch_norm_finish(const c128* partial, double* out, c128* hslot, const KState* kst, int gate,
                                cudaStream_t st);

@@ -123,6 +123,126 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Gram-Schmidt in double-float arithmetic on the FP32 pipe (ortho = 3).
+// A double x is split with integer operations into floats hi + lo: hi holds
+// the sign, exponent and top 23 mantissa bits, lo the next 24 of the remaining
+// 29 bits (|x - hi - lo| <= 2^-47 |x|; magnitudes below 2^-74 keep hi only,
+// below 2^-126 become 0). Products use the exact FMA residual, sums the
+// TwoSum transformation, so a product-sum carries about 46 correct bits.
+// ---------------------------------------------------------------------------
+struct dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfl split_d(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hw = (unsigned int)(u >> 32), lw = (unsigned int)u;
+  const unsigned int sign = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7FFu);
+  const int ef = e - 896;                          // float biased exponent of hi
+  dfl r;
+  if (ef <= 0) {
+    r.hi = 0.f;
+    r.lo = 0.f;
+    return r;
+  }
+  if (ef >= 255) {                                  // beyond float range: poison
+    r.hi = __int_as_float(0x7fc00000);
+    r.lo = 0.f;
+    return r;
+  }
+  const unsigned int mh = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+  r.hi = __uint_as_float(sign | ((unsigned int)ef << 23) | mh);
+  const int es = e - 948;                           // biased exponent of 2^(e-1075)
+  float lo = 0.f;
+  if (es > 0) lo = __uint2float_rn(lw & 0x1FFFFFFFu) * __uint_as_float((unsigned int)es << 23);
+  r.lo = __uint_as_float(__float_as_uint(lo) | sign);
+  return r;
+}
+
+// a*b as p + t with p = fl(a_hi*b_hi) and t the remaining terms
+__device__ __forceinline__ void df_prod(const dfl& a, const dfl& b, float& p, float& t) {
+  p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p);
+  t = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+}
+
+// (hi, lo) += p + t, TwoSum on the leading part
+__device__ __forceinline__ void df_acc(float& hi, float& lo, float p, float t) {
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (p - bb);
+  hi = s;
+  lo += err + t;
+}
+
+__device__ __forceinline__ double df_to_d(float hi, float lo) { return (double)hi + (double)lo; }
+
+// partial[c * gridDim.x + blk] = sum over the block's rows of conj(V_c) w
+__global__ void __launch_bounds__(kThreads)
+    k_dots_df(const c128* __restrict__ V, long long ldv, const c128* __restrict__ w, long long n,
+              c128* __restrict__ partial, const KState* __restrict__ kst, int gate) {
+  if (skip(kst, gate)) return;
+  const int c = blockIdx.y;
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long r0 = blockIdx.x * per;
+  const long long r1 = min(n, r0 + per);
+  const c128* v = V + c * ldv;
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  for (long long r = r0 + threadIdx.x; r < r1; r += kThreads) {
+    const c128 a = v[r], b = w[r];
+    const dfl ar = split_d(a.re), ai = split_d(a.im), br = split_d(b.re), bi = split_d(b.im);
+    float p, t;
+    // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
+    df_prod(ar, br, p, t);
+    df_acc(rh, rl, p, t);
+    df_prod(ai, bi, p, t);
+    df_acc(rh, rl, p, t);
+    df_prod(ar, bi, p, t);
+    df_acc(ih, il, p, t);
+    df_prod(ai, br, p, t);
+    df_acc(ih, il, -p, -t);
+  }
+  c128 s = block_sum(mk(df_to_d(rh, rl), df_to_d(ih, il)));
+  if (threadIdx.x == 0) partial[(long long)c * gridDim.x + blockIdx.x] = s;
+}
+
+// w += sign * sum_c V_c h_c with double-float accumulation
+__global__ void __launch_bounds__(kThreads)
+    k_axpys_df(const c128* __restrict__ V, long long ldv, int ncols, const c128* __restrict__ h, double sign,
+               c128* __restrict__ w, long long n, const KState* __restrict__ kst, int gate) {
+  if (skip(kst, gate)) return;
+  extern __shared__ dfl hsd[];                     // 2*ncols entries: (re, im) per column
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+    hsd[2 * c] = split_d(sign * h[c].re);
+    hsd[2 * c + 1] = split_d(sign * h[c].im);
+  }
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
+    const c128 w0 = w[r];
+    const dfl wr = split_d(w0.re), wi = split_d(w0.im);
+    float rh = wr.hi, rl = wr.lo, ih = wi.hi, il = wi.lo;
+    for (int c = 0; c < ncols; ++c) {
+      const c128 a = V[c * ldv + r];
+      const dfl ar = split_d(a.re), ai = split_d(a.im);
+      const dfl hr = hsd[2 * c], hi_ = hsd[2 * c + 1];
+      float p, t;
+      // a h = (ar hr - ai hi) + i (ar hi + ai hr)
+      df_prod(ar, hr, p, t);
+      df_acc(rh, rl, p, t);
+      df_prod(ai, hi_, p, t);
+      df_acc(rh, rl, -p, -t);
+      df_prod(ar, hi_, p, t);
+      df_acc(ih, il, p, t);
+      df_prod(ai, hr, p, t);
+      df_acc(ih, il, p, t);
+    }
+    w[r] = mk(df_to_d(rh, rl), df_to_d(ih, il));
+  }
+}
+
 __global__ void k_add(c128* __restrict__ dst, const c128* __restrict__ src, int cnt,
                       const KState* __restrict__ kst, int gate) {
   if (skip(kst, gate)) return;
@@ -306,6 +426,25 @@ cudaError_t launch_axpys(const c128* V, long long ldv, int ncols, const c128* h,
     if (e != cudaSuccess) return e;
   }
   k_axpys<<<grid_for(n, kThreads), kThreads, smem, st>>>(V, ldv, ncols, h, sign, w, n, kst, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dots_df(const c128* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
+                           const KState* kst, int gate, cudaStream_t st) {
+  dim3 grid(dot_blocks(), ncols);
+  k_dots_df<<<grid, kThreads, 0, st>>>(V, ldv, w, n, partial, kst, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpys_df(const c128* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
+                            long long n, const KState* kst, int gate, cudaStream_t st) {
+  dot_blocks();
+  size_t smem = (size_t)ncols * 2 * sizeof(dfl);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_axpys_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_axpys_df<<<grid_for(n, kThreads), kThreads, smem, st>>>(V, ldv, ncols, h, sign, w, n, kst, gate);
   return cudaGetLastError();
 }
 

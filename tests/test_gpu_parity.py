@@ -63,7 +63,7 @@ def test_apply_fp64_matches_oracle(solver_cls, name, kw):
         assert s.info()["min_pivot_ratio"] > 0
 
 
-@pytest.mark.parametrize("ortho", [0, 1, 2])
+@pytest.mark.parametrize("ortho", [0, 1, 2, 3])
 @pytest.mark.parametrize("name", ["tiny3", "small", "c0"])
 def test_fgmres_fixed_iterations_match_oracle(solver_cls, name, ortho):
     """Same m directions from x0 = 0: the iterates agree to 1e-10 (CGS2 on the
@@ -84,7 +84,7 @@ def test_fgmres_fixed_iterations_match_oracle(solver_cls, name, ortho):
         assert np.max(np.abs(h - np.array(ho)) / np.array(ho)) <= 1e-8
 
 
-@pytest.mark.parametrize("ortho", [0, 1, 2])
+@pytest.mark.parametrize("ortho", [0, 1, 2, 3])
 @pytest.mark.parametrize("name,kw", CASES[:6], ids=IDS[:6])
 def test_converged_solve_matches_direct_solve(solver_cls, name, kw, ortho):
     w = variant(name, **kw)
