@@ -9,7 +9,9 @@
 //   1. reads the pivot column c_i = W(k+i, k), d = c_0, l_i = c_i / d,
 //      and writes L(:, k) = l and D^-1(k) = 1/d to global memory;
 //   2. applies the rank-1 update W(k+i, k+j) -= c_i l_j, 1 <= j <= i <= b;
-//   3. moves row k+b+1 of A_j into the slot freed by row k.
+//   3. moves row k+b+1 of A_j into the slot freed by row k; those rows are
+//      staged in shared memory 32 steps ahead, so no global load sits on a
+//      step's critical path.
 // Output layout: L_j column k at l_off + k*bp (bp >= b, entries b..bp-1 are
 // zero), rows k+1..k+b; D^-1 at v_off + k. Rows n..npad-1 are identity
 // padding, so their L columns are zero. A second copy holds the rows of L_j
@@ -37,6 +39,31 @@ __device__ __forceinline__ cx<R> aloc_val(const c128* __restrict__ A, const SubD
   if (t == sd.b - 1) v = v + a[2];
   if (t == sd.b) v = v + a[3];
   return cvt<R>(v);
+}
+
+// The four stored entries of row `row` of A_j (D, W, S, SW couplings);
+// identity for padding rows.
+template <typename R>
+__device__ __forceinline__ void aloc_row(const c128* __restrict__ A, const SubDesc& sd, int row, cx<R> (&v)[4]) {
+  if (row >= sd.n) {
+    v[0] = mk((R)1, (R)0);
+    v[1] = v[2] = v[3] = mk((R)0, (R)0);
+    return;
+  }
+  const c128* a = A + 4 * (sd.v_off + row);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = cvt<R>(a[i]);
+}
+
+// Entry (row, row - t) from a row's four stored entries.
+template <typename R>
+__device__ __forceinline__ cx<R> row_entry(const cx<R> (&v)[4], int t, int b) {
+  cx<R> r = mk((R)0, (R)0);
+  if (t == 0) r = v[0];
+  if (t == 1) r = r + v[1];
+  if (t == b - 1) r = r + v[2];
+  if (t == b) r = r + v[3];
+  return r;
 }
 
 template <typename R>
@@ -79,10 +106,26 @@ __global__ void __launch_bounds__(kFactorThreads)
   }
   __syncthreads();
 
-  double dmin = 1e300, dmax = 0.0;
+  R dmin2 = (R)3e38, dmax2 = (R)0;
   bool bad = false;
   int pk = 0;  // slot of row k
+  __shared__ cx<R> rows[2][32][4];   // rows entering at the next steps, double-buffered
+  if (tid < 128) {
+    const int s = tid >> 2, e = tid & 3;
+    cx<R> v[4];
+    aloc_row<R>(Aloc, sd, b + 1 + s, v);
+    rows[0][s][e] = v[e];
+  }
+  __syncthreads();
   for (int k = 0; k < sd.npad; ++k) {
+    if ((k & 31) == 0 && tid < 128) {
+      // rows entering at steps k+32..k+63; that buffer's last reader was
+      // step k-1, which ended at the barrier before this point
+      const int s = tid >> 2, e = tid & 3;
+      cx<R> v[4];
+      aloc_row<R>(Aloc, sd, k + 32 + b + 1 + s, v);
+      rows[((k >> 5) + 1) & 1][s][e] = v[e];
+    }
     // 1. pivot column
     if (tid <= b) {
       int s = pk + tid;
@@ -92,10 +135,10 @@ __global__ void __launch_bounds__(kFactorThreads)
       cx<R> di = crecip(d);
       cbuf[tid] = c;
       if (tid == 0) {
-        double ad = sqrt((double)abs2(d));
-        if (!(ad > 0.0) || !isfinite(ad) || !isfinite((double)di.re) || !isfinite((double)di.im)) bad = true;
-        dmin = fmin(dmin, ad);
-        dmax = fmax(dmax, ad);
+        const R ad2 = abs2(d);
+        if (!(ad2 > (R)0) || !isfinite(ad2) || !isfinite(di.re) || !isfinite(di.im)) bad = true;
+        dmin2 = fmin(dmin2, ad2);
+        dmax2 = fmax(dmax2, ad2);
         dv[k] = di;
         if (bp > b) L[(long long)k * bp + b] = mk((R)0, (R)0);
       } else {
@@ -119,18 +162,20 @@ __global__ void __launch_bounds__(kFactorThreads)
     }
     // 3. row k+b+1 enters slot pk (disjoint from the slots updated above)
     if (tid <= b) {
-      const int rn = k + b + 1;
       const int t = tid;
-      int sc = pk + (b + 1 - t);  // slot of column rn - t
+      int sc = pk + (b + 1 - t);  // slot of column k+b+1-t
       if (sc >= Wc) sc -= Wc;
-      W[sc * Wc + pk] = aloc_val<R>(Aloc, sd, rn, t);
+      cx<R> v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] = rows[(k >> 5) & 1][k & 31][i];
+      W[sc * Wc + pk] = row_entry<R>(v, t, b);
     }
     __syncthreads();
     pk = (pk + 1 == Wc) ? 0 : pk + 1;
   }
   if (tid == 0) {
-    pivstats[2 * blockIdx.x] = dmin;
-    pivstats[2 * blockIdx.x + 1] = dmax;
+    pivstats[2 * blockIdx.x] = sqrt((double)dmin2);
+    pivstats[2 * blockIdx.x + 1] = sqrt((double)dmax2);
     if (bad) atomicCAS(&status->pivot_bad_sub, -1, (int)blockIdx.x);
   }
 }
