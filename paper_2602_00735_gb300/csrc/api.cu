@@ -38,6 +38,7 @@ struct ras_pml_handle {
   int kcap = 0;
   c128 *V = nullptr, *Z = nullptr, *H = nullptr, *sn = nullptr, *gvec = nullptr, *yv = nullptr;
   c128 *partial = nullptr, *hbuf = nullptr;
+  c128* wdf = nullptr;   // w split into double-float form (ortho = 3)
   double *cs = nullptr, *hist = nullptr, *scal = nullptr;
   int hist_cap = 0;
   KState* kst = nullptr;
@@ -134,8 +135,9 @@ std::vector<Range> ranges(int M, int P, int o, int pml, bool* ok) {
 int ensure_krylov(ras_pml_handle* h, int m, int maxit) {
   if (h->kcap < m) {
     dfree(h->V); dfree(h->Z); dfree(h->H); dfree(h->sn); dfree(h->gvec); dfree(h->yv);
-    dfree(h->partial); dfree(h->hbuf); dfree(h->cs);
+    dfree(h->partial); dfree(h->hbuf); dfree(h->cs); dfree(h->wdf);
     h->kcap = 0;
+    RP_ALLOC(h->wdf, (size_t)h->n);
     RP_ALLOC(h->V, (size_t)(m + 1) * h->n);
     RP_ALLOC(h->Z, (size_t)m * h->n);
     RP_ALLOC(h->H, (size_t)(m + 1) * m);
@@ -202,6 +204,7 @@ void ras_pml_destroy(ras_pml_handle* h) {
   dfree(h->L); dfree(h->Lrev); dfree(h->dinv); dfree(h->Y); dfree(h->pivstats); dfree(h->status);
   dfree(h->V); dfree(h->Z); dfree(h->H); dfree(h->sn); dfree(h->gvec); dfree(h->yv);
   dfree(h->partial); dfree(h->hbuf); dfree(h->cs); dfree(h->hist); dfree(h->scal); dfree(h->kst);
+  dfree(h->wdf);
   dfree(h->tmp_b); dfree(h->tmp_x); dfree(h->tmp_r);
   if (h->kst_host) cudaFreeHost(h->kst_host);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -470,6 +473,7 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
   }
   int status = RASPML_NOT_CONVERGED;
   double rel = NAN;
+  const bool dfbasis = h->p.ortho == 3;   // V stored in double-float form
   for (;;) {
     // new cycle: V0 = b - A x, beta = ||V0||, g = beta e1, V0 /= beta
     c128* V0 = h->V;
@@ -477,7 +481,10 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
     RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, x, b, V0, nullptr, st));
     if ((s = dev_norm(h, V0, &h->kst->hnorm, nullptr, nullptr))) return s;
     RP_CUDA(rp::launch_cycle_init(h->kst, h->gvec, m, rtol, h->hist, st));
-    RP_CUDA(rp::launch_scale_inv(V0, n, &h->kst->hnorm, h->kst, st));
+    if (dfbasis)
+      RP_CUDA(rp::launch_scale_to_df(V0, n, &h->kst->hnorm, h->kst, st));
+    else
+      RP_CUDA(rp::launch_scale_inv(V0, n, &h->kst->hnorm, h->kst, st));
     for (int j = 0; j < m;) {
       const int nb = std::min(batch, m - j);
       for (int jj = j; jj < j + nb; ++jj) {
@@ -489,7 +496,7 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
         ++issued;
         if (h->timing) RP_CUDA(cudaEventRecord(evj[0], st));
         RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev,
-                                 h->dinv, vj, h->Y, zj, h->kst, h->status, st));
+                                 h->dinv, vj, h->Y, zj, h->kst, h->status, st, dfbasis));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[1], st));
         RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, nullptr, w, h->kst, st));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[2], st));
@@ -504,8 +511,9 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
           RP_CUDA(rp::launch_add(hcol, h->hbuf, jj + 1, h->kst, 0, st));
           if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst))) return s;
         } else if (h->p.ortho == 3) {
-          // one pass, products and sums in double-float arithmetic on the FP32 pipe
-          RP_CUDA(rp::launch_dots_df(h->V, n, jj + 1, w, n, h->partial, h->kst, 0, st));
+          // one pass against the double-float basis, products and sums on the FP32 pipe
+          RP_CUDA(rp::launch_split(w, h->wdf, n, h->kst, st));
+          RP_CUDA(rp::launch_dots_df(h->V, n, jj + 1, h->wdf, n, h->partial, h->kst, 0, st));
           RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, hcol, 0, h->kst, 0, st));
           RP_CUDA(rp::launch_axpys_df(h->V, n, jj + 1, hcol, -1.0, w, n, h->kst, 0, st));
           if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst))) return s;
@@ -524,7 +532,10 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
           if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst, 1))) return s;
         }
         RP_CUDA(rp::launch_givens(h->kst, h->H, ldh, h->cs, h->sn, h->gvec, jj, rtol, m, maxit, h->hist, st));
-        RP_CUDA(rp::launch_scale_inv(w, n, &h->kst->hnorm, h->kst, st));
+        if (dfbasis)
+          RP_CUDA(rp::launch_scale_to_df(w, n, &h->kst->hnorm, h->kst, st));
+        else
+          RP_CUDA(rp::launch_scale_inv(w, n, &h->kst->hnorm, h->kst, st));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[3], st));
       }
       RP_CUDA(cudaMemcpyAsync(h->kst_host, h->kst, sizeof(KState), cudaMemcpyDeviceToHost, st));
@@ -563,7 +574,7 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
   // launches: ||b|| (2); per cycle: residual, norm (2), init, scale, backsolve,
   // update, true residual, norm (2) = 10; per issued direction: 13 (CGS twice)
   // or 17 (one pass, test, gated second pass)
-  launches += 10 * cycles + (h->p.ortho == 0 ? 13 : h->p.ortho == 3 ? 11 : 17) * issued;
+  launches += 10 * cycles + (h->p.ortho == 0 ? 13 : h->p.ortho == 3 ? 12 : 17) * issued;
   h->tm.launches = (int32_t)launches;
   h->tm.applies = total;
   h->tm.reorths = h->p.ortho == 0 ? total : (h->p.ortho == 3 ? 0 : h->kst_host->reorths);

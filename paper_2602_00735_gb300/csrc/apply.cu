@@ -30,12 +30,18 @@ namespace {
 constexpr int kCol = 8;       // columns per bulk copy
 constexpr int kStages = 4;    // ring depth
 
+// R_j r at local row `row`: r is complex128, or double-float (dfc) when rdf
 template <typename R>
-__device__ __forceinline__ cx<R> gather_row(const SubDesc& sd, const Geo& g, const c128* __restrict__ r, int row) {
+__device__ __forceinline__ cx<R> gather_row(const SubDesc& sd, const Geo& g, const c128* __restrict__ r, int rdf,
+                                            int row) {
   if (row >= sd.n) return mk((R)0, (R)0);
   int i = sd.ix0 + row % sd.nlx, j = sd.iy0 + row / sd.nlx;
-  c128 v = r[(long long)(j - 1) * g.nx + (i - 1)];
-  return cvt<R>(v);
+  const long long idx = (long long)(j - 1) * g.nx + (i - 1);
+  if (rdf) {
+    const dfc v = reinterpret_cast<const dfc*>(r)[idx];
+    return mk((R)((R)v.rh + (R)v.rl), (R)((R)v.ih + (R)v.il));
+  }
+  return cvt<R>(r[idx]);
 }
 
 template <typename R>
@@ -110,7 +116,7 @@ __device__ __forceinline__ bool group_dispatch(int ph, const Pipe<R>& pp, int s0
 template <typename R, int S>
 __global__ void __launch_bounds__(32)
     k_apply(Geo g, const SubDesc* __restrict__ subs, const cx<R>* __restrict__ Lf, const cx<R>* __restrict__ Lb,
-            const cx<R>* __restrict__ dinv_all, const c128* __restrict__ rglob, cx<R>* __restrict__ Y,
+            const cx<R>* __restrict__ dinv_all, const c128* __restrict__ rglob, int rdf, cx<R>* __restrict__ Y,
             int stage_elems, const KState* __restrict__ kst, DevStatus* status) {
   extern __shared__ __align__(128) unsigned char sm[];
   if (kst != nullptr && kst->stop) return;
@@ -147,10 +153,10 @@ __global__ void __launch_bounds__(32)
   // ---------------- forward: L y = R_j r, z = D^-1 y ----------------
   cx<R> win[S];
 #pragma unroll
-  for (int sl = 0; sl < S; ++sl) win[sl] = gather_row<R>(sd, g, rglob, 32 * sl + lane);
-  cx<R> nxt = gather_row<R>(sd, g, rglob, 32 * S + lane);
+  for (int sl = 0; sl < S; ++sl) win[sl] = gather_row<R>(sd, g, rglob, rdf, 32 * sl + lane);
+  cx<R> nxt = gather_row<R>(sd, g, rglob, rdf, 32 * S + lane);
   for (int gi = 0; gi < G; ++gi) {
-    const cx<R> nxt2 = gather_row<R>(sd, g, rglob, 32 * (gi + S + 1) + lane);
+    const cx<R> nxt2 = gather_row<R>(sd, g, rglob, rdf, 32 * (gi + S + 1) + lane);
     const cx<R> d = dv[32 * gi + lane];
     cx<R> outv;
     if (!group_dispatch<R, S>(gi % S, pp, 4 * gi, b, lane, win, nxt, outv)) { fail(4 * gi); return; }
@@ -215,13 +221,13 @@ __global__ void k_prolong(Geo g, const SubDesc* __restrict__ subs, const cx<R>* 
 
 template <typename R, int S>
 cudaError_t launch_apply_t(const Geo& g, const SubDesc* subs, int nsub, int max_bp, const void* Lf, const void* Lb,
-                           const void* dinv, const c128* r, void* Y, const KState* kst, DevStatus* status,
+                           const void* dinv, const c128* r, int rdf, void* Y, const KState* kst, DevStatus* status,
                            cudaStream_t st) {
   const int stage_elems = kCol * max_bp;
   const size_t smem = apply_smem_bytes(max_bp, sizeof(R) == 8 ? 0 : 1);
   cudaError_t e = cudaFuncSetAttribute(k_apply<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_apply<R, S><<<nsub, 32, smem, st>>>(g, subs, (const cx<R>*)Lf, (const cx<R>*)Lb, (const cx<R>*)dinv, r,
+  k_apply<R, S><<<nsub, 32, smem, st>>>(g, subs, (const cx<R>*)Lf, (const cx<R>*)Lb, (const cx<R>*)dinv, r, rdf,
                                         (cx<R>*)Y, stage_elems, kst, status);
   return cudaGetLastError();
 }
@@ -235,22 +241,23 @@ size_t apply_smem_bytes(int max_bp, int prec) {
 
 cudaError_t launch_apply(int prec, const Geo& g, const SubDesc* subs, int nsub, int max_b, int max_bp,
                          const void* Lf, const void* Lb, const void* dinv, const c128* r, void* Y, c128* z,
-                         const KState* kst, DevStatus* status, cudaStream_t st) {
+                         const KState* kst, DevStatus* status, cudaStream_t st, bool r_is_df) {
+  const int rdf = r_is_df ? 1 : 0;
   const int S = (max_b + 1 + 31) / 32;
   cudaError_t e;
   if (prec == 0) {
     switch (S) {
-      case 1: e = launch_apply_t<double, 1>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
-      case 2: e = launch_apply_t<double, 2>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
-      case 3: e = launch_apply_t<double, 3>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
-      default: e = launch_apply_t<double, 4>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
+      case 1: e = launch_apply_t<double, 1>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
+      case 2: e = launch_apply_t<double, 2>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
+      case 3: e = launch_apply_t<double, 3>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
+      default: e = launch_apply_t<double, 4>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
     }
   } else {
     switch (S) {
-      case 1: e = launch_apply_t<float, 1>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
-      case 2: e = launch_apply_t<float, 2>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
-      case 3: e = launch_apply_t<float, 3>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
-      default: e = launch_apply_t<float, 4>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, Y, kst, status, st); break;
+      case 1: e = launch_apply_t<float, 1>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
+      case 2: e = launch_apply_t<float, 2>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
+      case 3: e = launch_apply_t<float, 3>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
+      default: e = launch_apply_t<float, 4>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
     }
   }
   if (e != cudaSuccess) return e;

@@ -182,6 +182,63 @@ __host__ __device__ __forceinline__ int box_start(int p, int M, int P) {
   return p * base + (p < extra ? p : extra);
 }
 
+// ---------------------------------------------------------------------------
+// Double-float numbers: a double x held as floats hi + lo, split with integer
+// operations and one exact float subtraction. hi keeps the sign, exponent and
+// top 23 mantissa bits; lo the next 23 bits, so |x - hi - lo| < 2^-46 |x|.
+// Magnitudes below 2^-103 keep hi only, below 2^-126 become 0; magnitudes
+// beyond the float range become NaN (there is no such value in a normalised
+// Krylov basis; a NaN is caught by the residual checks).
+// ---------------------------------------------------------------------------
+struct dfl {
+  float hi, lo;
+};
+// a complex128 value in double-float form (16 bytes, like the double pair)
+struct __align__(16) dfc {
+  float rh, rl, ih, il;
+};
+
+__device__ __forceinline__ dfl split_d(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hw = (unsigned int)(u >> 32), lw = (unsigned int)u;
+  const unsigned int sign = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7FFu);
+  const int ef = e - 896;                              // biased float exponent of hi
+  dfl r;
+  if (ef <= 0) {
+    r.hi = 0.f;
+    r.lo = 0.f;
+    return r;
+  }
+  if (ef >= 255) {
+    r.hi = __int_as_float(0x7fc00000);
+    r.lo = 0.f;
+    return r;
+  }
+  const unsigned int mh = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+  r.hi = __uint_as_float(sign | ((unsigned int)ef << 23) | mh);
+  // the 29 remaining bits rem weigh 2^(e-1075); with E = ef - 23,
+  // (1 + (rem>>6)/2^23) 2^(E-127) - 2^(E-127) = (rem>>6) 2^(e-1069), exactly
+  float lo = 0.f;
+  const int E = ef - 23;
+  if (E > 0) {
+    const unsigned int base = (unsigned int)E << 23;
+    lo = __uint_as_float(base | ((lw & 0x1FFFFFFFu) >> 6)) - __uint_as_float(base);
+  }
+  r.lo = __uint_as_float(__float_as_uint(lo) | sign);
+  return r;
+}
+
+__device__ __forceinline__ dfc split_c(c128 v) {
+  const dfl a = split_d(v.re), b = split_d(v.im);
+  dfc r;
+  r.rh = a.hi;
+  r.rl = a.lo;
+  r.ih = b.hi;
+  r.il = b.lo;
+  return r;
+}
+
 // Device status words shared by the kernels of one handle.
 struct DevStatus {
   int pivot_bad_sub;    // first subdomain with a zero / non-finite pivot, else -1

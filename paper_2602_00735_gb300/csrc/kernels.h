@@ -40,9 +40,10 @@ cudaError_t launch_factor(int prec, const SubDesc* subs, int nsub, int max_b, co
 
 // apply.cu
 size_t apply_smem_bytes(int max_bp, int prec);
+// r is complex128, or double-float (dfc) when r_is_df
 cudaError_t launch_apply(int prec, const Geo& g, const SubDesc* subs, int nsub, int max_b, int max_bp,
                          const void* Lf, const void* Lb, const void* dinv, const c128* r, void* Y, c128* z,
-                         const KState* kst, DevStatus* status, cudaStream_t st);
+                         const KState* kst, DevStatus* status, cudaStream_t st, bool r_is_df = false);
 
 // krylov.cu
 cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, const c128* CS, const c128* CSW,
@@ -54,9 +55,12 @@ cudaError_t launch_dots_finish(const c128* partial, int ncols, c128* out, int ac
                                cudaStream_t st);
 cudaError_t launch_axpys(const c128* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
                          long long n, const KState* kst, int gate, cudaStream_t st);
-cudaError_t launch_dots_df(const c128* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
+// double-float Gram-Schmidt: V and wdf hold dfc values (16 bytes each)
+cudaError_t launch_split(const c128* w, void* wdf, long long n, const KState* kst, cudaStream_t st);
+cudaError_t launch_scale_to_df(c128* v, long long n, const double* nrm, const KState* kst, cudaStream_t st);
+cudaError_t launch_dots_df(const void* V, long long ldv, int ncols, const void* wdf, long long n, c128* partial,
                            const KState* kst, int gate, cudaStream_t st);
-cudaError_t launch_axpys_df(const c128* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
+cudaError_t launch_axpys_df(const void* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
                             long long n, const KState* kst, int gate, cudaStream_t st);
 cudaError_t launch_add(c128* dst, const c128* src, int cnt, const KState* kst, int gate, cudaStream_t st);
 cudaError_t launch_norm_finish(const c128* partial, double* out, c128* hslot, const KState* kst, int gate,

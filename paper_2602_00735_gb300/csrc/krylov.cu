@@ -124,43 +124,12 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------------------
-// Gram-Schmidt in double-float arithmetic on the FP32 pipe (ortho = 3).
-// A double x is split with integer operations into floats hi + lo: hi holds
-// the sign, exponent and top 23 mantissa bits, lo the next 24 of the remaining
-// 29 bits (|x - hi - lo| <= 2^-47 |x|; magnitudes below 2^-74 keep hi only,
-// below 2^-126 become 0). Products use the exact FMA residual, sums the
-// TwoSum transformation, so a product-sum carries about 46 correct bits.
+// Gram-Schmidt in double-float arithmetic on the FP32 pipe (ortho = 3). The
+// Krylov basis V is stored in double-float form (dfc, split once when a
+// vector is normalised) and w is split once per projection, so the
+// projection and the update read pre-split operands. Products use the exact
+// FMA residual, sums the TwoSum transformation: about 46 correct bits.
 // ---------------------------------------------------------------------------
-struct dfl {
-  float hi, lo;
-};
-
-__device__ __forceinline__ dfl split_d(double x) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const unsigned int hw = (unsigned int)(u >> 32), lw = (unsigned int)u;
-  const unsigned int sign = hw & 0x80000000u;
-  const int e = (int)((hw >> 20) & 0x7FFu);
-  const int ef = e - 896;                          // float biased exponent of hi
-  dfl r;
-  if (ef <= 0) {
-    r.hi = 0.f;
-    r.lo = 0.f;
-    return r;
-  }
-  if (ef >= 255) {                                  // beyond float range: poison
-    r.hi = __int_as_float(0x7fc00000);
-    r.lo = 0.f;
-    return r;
-  }
-  const unsigned int mh = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
-  r.hi = __uint_as_float(sign | ((unsigned int)ef << 23) | mh);
-  const int es = e - 948;                           // biased exponent of 2^(e-1075)
-  float lo = 0.f;
-  if (es > 0) lo = __uint2float_rn(lw & 0x1FFFFFFFu) * __uint_as_float((unsigned int)es << 23);
-  r.lo = __uint_as_float(__float_as_uint(lo) | sign);
-  return r;
-}
-
 // a*b as p + t with p = fl(a_hi*b_hi) and t the remaining terms
 __device__ __forceinline__ void df_prod(const dfl& a, const dfl& b, float& p, float& t) {
   p = a.hi * b.hi;
@@ -179,20 +148,51 @@ __device__ __forceinline__ void df_acc(float& hi, float& lo, float p, float t) {
 
 __device__ __forceinline__ double df_to_d(float hi, float lo) { return (double)hi + (double)lo; }
 
+__device__ __forceinline__ dfl dfl_of(float hi, float lo) {
+  dfl r;
+  r.hi = hi;
+  r.lo = lo;
+  return r;
+}
+
+// wdf = split(w)
+__global__ void k_split(const c128* __restrict__ w, dfc* __restrict__ wdf, long long n,
+                        const KState* __restrict__ kst) {
+  if (skip(kst, 0)) return;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) wdf[r] = split_c(w[r]);
+}
+
+// v (in place) = split(w / nrm): the new basis vector in double-float form
+__global__ void k_scale_to_df(c128* __restrict__ v, long long n, const double* __restrict__ nrm,
+                              const KState* __restrict__ kst) {
+  if (skip(kst, 0)) return;
+  const double d = *nrm;
+  if (!(d > 0.0)) return;
+  const double s = 1.0 / d;
+  dfc* out = reinterpret_cast<dfc*>(v);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
+    const c128 x = v[r];
+    out[r] = split_c(mk(s * x.re, s * x.im));
+  }
+}
+
 // partial[c * gridDim.x + blk] = sum over the block's rows of conj(V_c) w
 __global__ void __launch_bounds__(kThreads)
-    k_dots_df(const c128* __restrict__ V, long long ldv, const c128* __restrict__ w, long long n,
+    k_dots_df(const dfc* __restrict__ V, long long ldv, const dfc* __restrict__ w, long long n,
               c128* __restrict__ partial, const KState* __restrict__ kst, int gate) {
   if (skip(kst, gate)) return;
   const int c = blockIdx.y;
   const long long per = (n + gridDim.x - 1) / gridDim.x;
   const long long r0 = blockIdx.x * per;
   const long long r1 = min(n, r0 + per);
-  const c128* v = V + c * ldv;
+  const dfc* v = V + c * ldv;
   float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
   for (long long r = r0 + threadIdx.x; r < r1; r += kThreads) {
-    const c128 a = v[r], b = w[r];
-    const dfl ar = split_d(a.re), ai = split_d(a.im), br = split_d(b.re), bi = split_d(b.im);
+    const dfc a = v[r], b = w[r];
+    const dfl ar = dfl_of(a.rh, a.rl), ai = dfl_of(a.ih, a.il);
+    const dfl br = dfl_of(b.rh, b.rl), bi = dfl_of(b.ih, b.il);
     float p, t;
     // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
     df_prod(ar, br, p, t);
@@ -210,24 +210,21 @@ __global__ void __launch_bounds__(kThreads)
 
 // w += sign * sum_c V_c h_c with double-float accumulation
 __global__ void __launch_bounds__(kThreads)
-    k_axpys_df(const c128* __restrict__ V, long long ldv, int ncols, const c128* __restrict__ h, double sign,
+    k_axpys_df(const dfc* __restrict__ V, long long ldv, int ncols, const c128* __restrict__ h, double sign,
                c128* __restrict__ w, long long n, const KState* __restrict__ kst, int gate) {
   if (skip(kst, gate)) return;
-  extern __shared__ dfl hsd[];                     // 2*ncols entries: (re, im) per column
-  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
-    hsd[2 * c] = split_d(sign * h[c].re);
-    hsd[2 * c + 1] = split_d(sign * h[c].im);
-  }
+  extern __shared__ dfc hsd[];
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) hsd[c] = split_c(mk(sign * h[c].re, sign * h[c].im));
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
-    const c128 w0 = w[r];
-    const dfl wr = split_d(w0.re), wi = split_d(w0.im);
-    float rh = wr.hi, rl = wr.lo, ih = wi.hi, il = wi.lo;
+    const dfc w0 = split_c(w[r]);
+    float rh = w0.rh, rl = w0.rl, ih = w0.ih, il = w0.il;
     for (int c = 0; c < ncols; ++c) {
-      const c128 a = V[c * ldv + r];
-      const dfl ar = split_d(a.re), ai = split_d(a.im);
-      const dfl hr = hsd[2 * c], hi_ = hsd[2 * c + 1];
+      const dfc a = V[c * ldv + r];
+      const dfc hc = hsd[c];
+      const dfl ar = dfl_of(a.rh, a.rl), ai = dfl_of(a.ih, a.il);
+      const dfl hr = dfl_of(hc.rh, hc.rl), hi_ = dfl_of(hc.ih, hc.il);
       float p, t;
       // a h = (ar hr - ai hi) + i (ar hi + ai hr)
       df_prod(ar, hr, p, t);
@@ -429,22 +426,34 @@ cudaError_t launch_axpys(const c128* V, long long ldv, int ncols, const c128* h,
   return cudaGetLastError();
 }
 
-cudaError_t launch_dots_df(const c128* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
-                           const KState* kst, int gate, cudaStream_t st) {
-  dim3 grid(dot_blocks(), ncols);
-  k_dots_df<<<grid, kThreads, 0, st>>>(V, ldv, w, n, partial, kst, gate);
+cudaError_t launch_split(const c128* w, void* wdf, long long n, const KState* kst, cudaStream_t st) {
+  dot_blocks();
+  k_split<<<grid_for(n, kThreads), kThreads, 0, st>>>(w, (dfc*)wdf, n, kst);
   return cudaGetLastError();
 }
 
-cudaError_t launch_axpys_df(const c128* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
+cudaError_t launch_scale_to_df(c128* v, long long n, const double* nrm, const KState* kst, cudaStream_t st) {
+  dot_blocks();
+  k_scale_to_df<<<grid_for(n, kThreads), kThreads, 0, st>>>(v, n, nrm, kst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dots_df(const void* V, long long ldv, int ncols, const void* wdf, long long n, c128* partial,
+                           const KState* kst, int gate, cudaStream_t st) {
+  dim3 grid(dot_blocks(), ncols);
+  k_dots_df<<<grid, kThreads, 0, st>>>((const dfc*)V, ldv, (const dfc*)wdf, n, partial, kst, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpys_df(const void* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
                             long long n, const KState* kst, int gate, cudaStream_t st) {
   dot_blocks();
-  size_t smem = (size_t)ncols * 2 * sizeof(dfl);
+  size_t smem = (size_t)ncols * sizeof(dfc);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_axpys_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_axpys_df<<<grid_for(n, kThreads), kThreads, smem, st>>>(V, ldv, ncols, h, sign, w, n, kst, gate);
+  k_axpys_df<<<grid_for(n, kThreads), kThreads, smem, st>>>((const dfc*)V, ldv, ncols, h, sign, w, n, kst, gate);
   return cudaGetLastError();
 }
 
