@@ -48,7 +48,7 @@ struct ras_pml_handle {
   std::vector<double> hist_host;
   // event timing
   bool timing = false;
-  std::vector<cudaEvent_t> ev;     // 4 per iteration of a batch, + 2 spare
+  std::vector<cudaEvent_t> ev;     // per-direction events (2 batch slots), solve and batch marks
   ras_pml_timing_t tm{};
 };
 
@@ -157,7 +157,7 @@ int ensure_krylov(ras_pml_handle* h, int m, int maxit) {
   if (!h->kst) {
     RP_ALLOC(h->kst, 1);
     RP_ALLOC(h->scal, 4);
-    RP_CUDA(cudaMallocHost((void**)&h->kst_host, sizeof(KState)));
+    RP_CUDA(cudaMallocHost((void**)&h->kst_host, 2 * sizeof(KState)));
   }
   return RASPML_OK;
 }
@@ -451,10 +451,11 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
   cudaStream_t st = h->st;
   const int ldh = m + 1;
   const int batch = 4;
-  if (h->timing && (s = ensure_events(h, 4 * batch + 2)) != RASPML_OK) return s;
+  // events: 4 per direction for two batch slots, solve start/end, batch-done x2
+  if ((s = ensure_events(h, 8 * batch + 4)) != RASPML_OK) return s;
   double t_apply = 0.0, t_spmv = 0.0, t_ortho = 0.0;
   long long launches = 2, issued = 0, cycles = 0;
-  if (h->timing) RP_CUDA(cudaEventRecord(h->ev[4 * batch], h->st));
+  if (h->timing) RP_CUDA(cudaEventRecord(h->ev[8 * batch], h->st));
   KState k0{};
   RP_CUDA(cudaMemcpyAsync(h->kst, &k0, sizeof(k0), cudaMemcpyHostToDevice, st));
   s = dev_norm(h, b, &h->kst->bnorm, nullptr, nullptr);
@@ -485,14 +486,31 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
       RP_CUDA(rp::launch_scale_to_df(V0, n, &h->kst->hnorm, h->kst, st));
     else
       RP_CUDA(rp::launch_scale_inv(V0, n, &h->kst->hnorm, h->kst, st));
-    for (int j = 0; j < m;) {
+    // Batches of `batch` directions; batch b+1 is enqueued before the stop flag
+    // of batch b is read back, so the device always has queued work while the
+    // host waits. Kernels after a stop return at once.
+    int slot = 0, pending = -1, pending_nb = 0;
+    bool stopped = false;
+    auto drain = [&](int sl, int cnt) -> int {
+      RP_CUDA(cudaEventSynchronize(h->ev[8 * batch + 2 + sl]));
+      if (h->timing) {
+        for (int q = 0; q < cnt; ++q) {
+          cudaEvent_t* evj = h->ev.data() + sl * 4 * batch + 4 * q;
+          t_apply += ev_ms(evj[0], evj[1]);
+          t_spmv += ev_ms(evj[1], evj[2]);
+          t_ortho += ev_ms(evj[2], evj[3]);
+        }
+      }
+      return RASPML_OK;
+    };
+    for (int j = 0; j < m && !stopped;) {
       const int nb = std::min(batch, m - j);
       for (int jj = j; jj < j + nb; ++jj) {
         c128* vj = h->V + (size_t)jj * n;
         c128* zj = h->Z + (size_t)jj * n;
         c128* w = h->V + (size_t)(jj + 1) * n;
         c128* hcol = h->H + (size_t)jj * ldh;
-        cudaEvent_t* evj = h->ev.data() + 4 * (jj - j);
+        cudaEvent_t* evj = h->ev.data() + slot * 4 * batch + 4 * (jj - j);
         ++issued;
         if (h->timing) RP_CUDA(cudaEventRecord(evj[0], st));
         RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev,
@@ -538,19 +556,19 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
           RP_CUDA(rp::launch_scale_inv(w, n, &h->kst->hnorm, h->kst, st));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[3], st));
       }
-      RP_CUDA(cudaMemcpyAsync(h->kst_host, h->kst, sizeof(KState), cudaMemcpyDeviceToHost, st));
-      RP_CUDA(cudaStreamSynchronize(st));
-      if (h->timing) {
-        for (int jj = 0; jj < nb; ++jj) {
-          cudaEvent_t* evj = h->ev.data() + 4 * jj;
-          t_apply += ev_ms(evj[0], evj[1]);
-          t_spmv += ev_ms(evj[1], evj[2]);
-          t_ortho += ev_ms(evj[2], evj[3]);
-        }
+      RP_CUDA(cudaMemcpyAsync(h->kst_host + slot, h->kst, sizeof(KState), cudaMemcpyDeviceToHost, st));
+      RP_CUDA(cudaEventRecord(h->ev[8 * batch + 2 + slot], st));
+      if (pending >= 0) {
+        if ((s = drain(pending, pending_nb))) return s;
+        if (h->kst_host[pending].stop) stopped = true;
       }
+      pending = slot;
+      pending_nb = nb;
+      slot ^= 1;
       j += nb;
-      if (h->kst_host->stop) break;
     }
+    if ((s = drain(pending, pending_nb))) return s;
+    *h->kst_host = h->kst_host[pending];
     const KState ks = *h->kst_host;
     // x += Z y with y = H^-1 g
     if (ks.jdone > 0) {
@@ -579,9 +597,9 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
   h->tm.applies = total;
   h->tm.reorths = h->p.ortho == 0 ? total : (h->p.ortho == 3 ? 0 : h->kst_host->reorths);
   if (h->timing) {
-    RP_CUDA(cudaEventRecord(h->ev[4 * batch + 1], st));
-    RP_CUDA(cudaEventSynchronize(h->ev[4 * batch + 1]));
-    h->tm.solve_ms = ev_ms(h->ev[4 * batch], h->ev[4 * batch + 1]);
+    RP_CUDA(cudaEventRecord(h->ev[8 * batch + 1], st));
+    RP_CUDA(cudaEventSynchronize(h->ev[8 * batch + 1]));
+    h->tm.solve_ms = ev_ms(h->ev[8 * batch], h->ev[8 * batch + 1]);
     h->tm.apply_ms = t_apply;
     h->tm.spmv_ms = t_spmv;
     h->tm.ortho_ms = t_ortho;
@@ -662,7 +680,7 @@ int ras_pml_set_timing(ras_pml_handle* h, int enable) {
   if (!h) return RASPML_EBADARG;
   cudaSetDevice(h->dev);
   h->timing = enable != 0;
-  if (h->timing && ensure_events(h, 18) != RASPML_OK) return RASPML_ECUDA;
+  if (h->timing && ensure_events(h, 36) != RASPML_OK) return RASPML_ECUDA;
   return RASPML_OK;
 }
 

@@ -178,34 +178,52 @@ __global__ void k_scale_to_df(c128* __restrict__ v, long long n, const double* _
   }
 }
 
-// partial[c * gridDim.x + blk] = sum over the block's rows of conj(V_c) w
+// Four columns per block: partial[c * gridDim.x + blk] = sum over the
+// block's rows of conj(V_c) w for c = 4*blockIdx.y + 0..3 (< ncols); w is
+// read once for the four.
+constexpr int kDfCols = 4;
+
 __global__ void __launch_bounds__(kThreads)
-    k_dots_df(const dfc* __restrict__ V, long long ldv, const dfc* __restrict__ w, long long n,
+    k_dots_df(const dfc* __restrict__ V, long long ldv, int ncols, const dfc* __restrict__ w, long long n,
               c128* __restrict__ partial, const KState* __restrict__ kst, int gate) {
   if (skip(kst, gate)) return;
-  const int c = blockIdx.y;
+  const int c0 = blockIdx.y * kDfCols;
+  const int nc = min(kDfCols, ncols - c0);
   const long long per = (n + gridDim.x - 1) / gridDim.x;
   const long long r0 = blockIdx.x * per;
   const long long r1 = min(n, r0 + per);
-  const dfc* v = V + c * ldv;
-  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  float rh[kDfCols], rl[kDfCols], ih[kDfCols], il[kDfCols];
+#pragma unroll
+  for (int q = 0; q < kDfCols; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.f;
   for (long long r = r0 + threadIdx.x; r < r1; r += kThreads) {
-    const dfc a = v[r], b = w[r];
-    const dfl ar = dfl_of(a.rh, a.rl), ai = dfl_of(a.ih, a.il);
+    const dfc b = w[r];
     const dfl br = dfl_of(b.rh, b.rl), bi = dfl_of(b.ih, b.il);
-    float p, t;
-    // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
-    df_prod(ar, br, p, t);
-    df_acc(rh, rl, p, t);
-    df_prod(ai, bi, p, t);
-    df_acc(rh, rl, p, t);
-    df_prod(ar, bi, p, t);
-    df_acc(ih, il, p, t);
-    df_prod(ai, br, p, t);
-    df_acc(ih, il, -p, -t);
+    dfc a[kDfCols];
+#pragma unroll
+    for (int q = 0; q < kDfCols; ++q)
+      if (q < nc) a[q] = V[(long long)(c0 + q) * ldv + r];
+#pragma unroll
+    for (int q = 0; q < kDfCols; ++q) {
+      if (q >= nc) continue;
+      const dfl ar = dfl_of(a[q].rh, a[q].rl), ai = dfl_of(a[q].ih, a[q].il);
+      float p, t;
+      // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
+      df_prod(ar, br, p, t);
+      df_acc(rh[q], rl[q], p, t);
+      df_prod(ai, bi, p, t);
+      df_acc(rh[q], rl[q], p, t);
+      df_prod(ar, bi, p, t);
+      df_acc(ih[q], il[q], p, t);
+      df_prod(ai, br, p, t);
+      df_acc(ih[q], il[q], -p, -t);
+    }
   }
-  c128 s = block_sum(mk(df_to_d(rh, rl), df_to_d(ih, il)));
-  if (threadIdx.x == 0) partial[(long long)c * gridDim.x + blockIdx.x] = s;
+#pragma unroll
+  for (int q = 0; q < kDfCols; ++q) {
+    if (q >= nc) break;
+    c128 s = block_sum(mk(df_to_d(rh[q], rl[q]), df_to_d(ih[q], il[q])));
+    if (threadIdx.x == 0) partial[(long long)(c0 + q) * gridDim.x + blockIdx.x] = s;
+  }
 }
 
 // w += sign * sum_c V_c h_c with double-float accumulation
@@ -220,21 +238,28 @@ __global__ void __launch_bounds__(kThreads)
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
     const dfc w0 = split_c(w[r]);
     float rh = w0.rh, rl = w0.rl, ih = w0.ih, il = w0.il;
-    for (int c = 0; c < ncols; ++c) {
-      const dfc a = V[c * ldv + r];
-      const dfc hc = hsd[c];
-      const dfl ar = dfl_of(a.rh, a.rl), ai = dfl_of(a.ih, a.il);
-      const dfl hr = dfl_of(hc.rh, hc.rl), hi_ = dfl_of(hc.ih, hc.il);
-      float p, t;
-      // a h = (ar hr - ai hi) + i (ar hi + ai hr)
-      df_prod(ar, hr, p, t);
-      df_acc(rh, rl, p, t);
-      df_prod(ai, hi_, p, t);
-      df_acc(rh, rl, -p, -t);
-      df_prod(ar, hi_, p, t);
-      df_acc(ih, il, p, t);
-      df_prod(ai, hr, p, t);
-      df_acc(ih, il, p, t);
+    for (int c0 = 0; c0 < ncols; c0 += kDfCols) {
+      dfc a[kDfCols];
+#pragma unroll
+      for (int q = 0; q < kDfCols; ++q)
+        if (c0 + q < ncols) a[q] = V[(long long)(c0 + q) * ldv + r];   // loads first
+#pragma unroll
+      for (int q = 0; q < kDfCols; ++q) {
+        if (c0 + q >= ncols) continue;
+        const dfc hc = hsd[c0 + q];
+        const dfl ar = dfl_of(a[q].rh, a[q].rl), ai = dfl_of(a[q].ih, a[q].il);
+        const dfl hr = dfl_of(hc.rh, hc.rl), hi_ = dfl_of(hc.ih, hc.il);
+        float p, t;
+        // a h = (ar hr - ai hi) + i (ar hi + ai hr)
+        df_prod(ar, hr, p, t);
+        df_acc(rh, rl, p, t);
+        df_prod(ai, hi_, p, t);
+        df_acc(rh, rl, -p, -t);
+        df_prod(ar, hi_, p, t);
+        df_acc(ih, il, p, t);
+        df_prod(ai, hr, p, t);
+        df_acc(ih, il, p, t);
+      }
     }
     w[r] = mk(df_to_d(rh, rl), df_to_d(ih, il));
   }
@@ -440,8 +465,8 @@ cudaError_t launch_scale_to_df(c128* v, long long n, const double* nrm, const KS
 
 cudaError_t launch_dots_df(const void* V, long long ldv, int ncols, const void* wdf, long long n, c128* partial,
                            const KState* kst, int gate, cudaStream_t st) {
-  dim3 grid(dot_blocks(), ncols);
-  k_dots_df<<<grid, kThreads, 0, st>>>((const dfc*)V, ldv, (const dfc*)wdf, n, partial, kst, gate);
+  dim3 grid(dot_blocks(), (ncols + kDfCols - 1) / kDfCols);
+  k_dots_df<<<grid, kThreads, 0, st>>>((const dfc*)V, ldv, ncols, (const dfc*)wdf, n, partial, kst, gate);
   return cudaGetLastError();
 }
 
