@@ -75,7 +75,7 @@ typedef struct {
                              -1: 0.5*ln(k)/k rounded half up, at least 1       */
   int    pml_cells;       /* local PML width kappa in cells; -1: same law;
                              0: no local PML (RAS-Imp)                         */
-  double g_amp, g_ramp;   /* stretching g'(d) = g_amp*(3t^2-2t^3),
+  double g_amp, g_ramp;   /* stretching (g_profile 0): g'(d) = g_amp*(3t^2-2t^3),
                              t = min(d/g_ramp, 1), d = distance beyond the box  */
   int    local_bc;        /* 0: impedance closure (RAS-PML-Imp, Section 3 (ii));
                              1: Dirichlet closure (RAS-PML-Drch, Section 2)    */
@@ -90,6 +90,9 @@ typedef struct {
                                complex128 and its products and sums in
                                double-float arithmetic (two floats, about 46
                                bits) on the FP32 pipe                          */
+  int    g_profile;       /* stretching: 0 g'(d) as above; 1 g(d) = g_amp d^3,
+                             i.e. g'(d) = 3 g_amp d^2 (the paper's experiments
+                             use g_amp = 10k, Section 4); g_ramp unused        */
 } ras_pml_params;
 
 /* Sizes and statistics of a handle (filled by ras_pml_info). */

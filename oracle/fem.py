@@ -37,13 +37,19 @@ import scipy.sparse.linalg as spla
 # Stretching function (Section 1: conditions on g; profile fixed by workload)
 # ----------------------------------------------------------------------------
 
-def gprime(d, amp: float, ramp: float):
-    """g'(d) = amp*(3t^2 - 2t^3), t = min(d/ramp, 1) for d > 0; 0 for d <= 0.
+def gprime(d, amp: float, ramp: float, profile: int = 0):
+    """Derivative of the stretching function g at distance d beyond the box.
 
-    Satisfies the paper's conditions on g (Section 1): g = g' = 0 for d <= 0,
+    profile 0: g'(d) = amp*(3t^2 - 2t^3), t = min(d/ramp, 1) for d > 0. It
+    satisfies the paper's conditions on g (Section 1): g = g' = 0 for d <= 0,
     g' > 0 for d > 0, g'' = 0 beyond kappa_inf = ramp.
+    profile 1: g(d) = amp*d^3, so g'(d) = 3 amp d^2 (the function of the
+    paper's experiments, Section 4, with amp = 10k).
+    Both are 0 for d <= 0.
     """
     d = np.asarray(d, dtype=np.float64)
+    if profile == 1:
+        return np.where(d > 0.0, 3.0 * amp * d * d, 0.0)
     t = np.clip(d / ramp, 0.0, 1.0)
     return np.where(d > 0.0, amp * (3.0 * t * t - 2.0 * t ** 3), 0.0)
 
@@ -107,17 +113,17 @@ def make_grid(p: dict) -> Grid:
     return Grid(X0, Y0, p["h"], Mx, My, p["x0"], p["x1"], p["y0"], p["y1"])
 
 
-def global_gamma_x(grid: Grid, s, amp, ramp):
+def global_gamma_x(grid: Grid, s, amp, ramp, profile: int = 0):
     """gamma_1 = 1 + i g_1'(x): g_1' = g'(distance of x beyond Omega_int in x)."""
     x = grid.xs(s)
     d = np.maximum(np.maximum(grid.x0 - x, x - grid.x1), 0.0)
-    return 1.0 + 1j * gprime(d, amp, ramp)
+    return 1.0 + 1j * gprime(d, amp, ramp, profile)
 
 
-def global_gamma_y(grid: Grid, s, amp, ramp):
+def global_gamma_y(grid: Grid, s, amp, ramp, profile: int = 0):
     y = grid.ys(s)
     d = np.maximum(np.maximum(grid.y0 - y, y - grid.y1), 0.0)
-    return 1.0 + 1j * gprime(d, amp, ramp)
+    return 1.0 + 1j * gprime(d, amp, ramp, profile)
 
 
 # ----------------------------------------------------------------------------
@@ -217,11 +223,11 @@ def assemble_global(p: dict, gx_fn=None, gy_fn=None):
     Returns (grid, A) with A a CSR complex128 matrix of size n x n.
     """
     grid = make_grid(p)
-    amp, ramp = p["g_amp"], p["g_ramp"]
+    amp, ramp, prof = p["g_amp"], p["g_ramp"], p.get("g_profile", 0)
     if gx_fn is None:
-        gx_fn = lambda s: global_gamma_x(grid, s, amp, ramp)  # noqa: E731
+        gx_fn = lambda s: global_gamma_x(grid, s, amp, ramp, prof)  # noqa: E731
     if gy_fn is None:
-        gy_fn = lambda s: global_gamma_y(grid, s, amp, ramp)  # noqa: E731
+        gy_fn = lambda s: global_gamma_y(grid, s, amp, ramp, prof)  # noqa: E731
     cj, ci = np.meshgrid(np.arange(grid.My), np.arange(grid.Mx), indexing="ij")
     r, c, v = assemble_cells(grid, ci, cj, gx_fn, gy_fn, p["k"])
     return grid, _to_matrix(r, c, v, interior_numbering(grid), grid.n)

@@ -99,7 +99,7 @@ def pou_1d(r: Range1D, ovlp: int, M: int):
     return w
 
 
-def local_gamma_fn(grid: fem.Grid, r: Range1D, axis: int, amp: float, ramp: float):
+def local_gamma_fn(grid: fem.Grid, r: Range1D, axis: int, amp: float, ramp: float, profile: int = 0):
     """gamma_j along one axis as a function of half-index s (Section 2, g_j).
 
     Beyond an interior side of Omega_j,int (s >= 2*int_hi, resp. s <= 2*int_lo)
@@ -110,13 +110,13 @@ def local_gamma_fn(grid: fem.Grid, r: Range1D, axis: int, amp: float, ramp: floa
 
     def fn(s):
         s = np.asarray(s, dtype=np.float64)
-        val = glob(grid, s, amp, ramp)
+        val = glob(grid, s, amp, ramp, profile)
         if r.hi_interior:
             d = (s - 2 * r.int_hi) * hh
-            val = np.where(s >= 2 * r.int_hi, 1.0 + 1j * fem.gprime(d, amp, ramp), val)
+            val = np.where(s >= 2 * r.int_hi, 1.0 + 1j * fem.gprime(d, amp, ramp, profile), val)
         if r.lo_interior:
             d = (2 * r.int_lo - s) * hh
-            val = np.where(s <= 2 * r.int_lo, 1.0 + 1j * fem.gprime(d, amp, ramp), val)
+            val = np.where(s <= 2 * r.int_lo, 1.0 + 1j * fem.gprime(d, amp, ramp, profile), val)
         return val
     return fn
 
@@ -139,9 +139,10 @@ class Subdomain:
 def local_operator(p: dict, grid: fem.Grid, rx: Range1D, ry: Range1D):
     """Local matrix A_j, its unknowns, and R_j, chi_j (Section 2 and Section 3 (ii))."""
     amp, ramp, k = p["g_amp"], p["g_ramp"], p["k"]
+    prof = p.get("g_profile", 0)
     imp = p.get("local_bc", 0) == 0
-    gx = local_gamma_fn(grid, rx, 0, amp, ramp)
-    gy = local_gamma_fn(grid, ry, 1, amp, ramp)
+    gx = local_gamma_fn(grid, rx, 0, amp, ramp, prof)
+    gy = local_gamma_fn(grid, ry, 1, amp, ramp, prof)
     cj, ci = np.meshgrid(np.arange(ry.ext_lo, ry.ext_hi),
                          np.arange(rx.ext_lo, rx.ext_hi), indexing="ij")
     rows, cols, vals = fem.assemble_cells(grid, ci, cj, gx, gy, k)

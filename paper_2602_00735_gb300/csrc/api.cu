@@ -217,7 +217,7 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   const ras_pml_params& p = *pp;
   if (!(p.k >= 0.0) || !(p.h > 0.0) || !(p.kappa_g >= 0.0) || !(p.x1 > p.x0) || !(p.y1 > p.y0) || p.px < 1 ||
       p.py < 1 || !(p.g_ramp > 0.0) || !(p.g_amp >= 0.0) || (p.local_bc != 0 && p.local_bc != 1) ||
-      (p.factor_prec != 0 && p.factor_prec != 1) || (p.ortho < 0 || p.ortho > 3))
+      (p.factor_prec != 0 && p.factor_prec != 1) || (p.ortho < 0 || p.ortho > 3) || (p.g_profile != 0 && p.g_profile != 1))
     return RASPML_EBADARG;
   const double lx = p.x1 - p.x0 + 2 * p.kappa_g, ly = p.y1 - p.y0 + 2 * p.kappa_g;
   const long long Mx = std::llround(lx / p.h), My = std::llround(ly / p.h);
@@ -247,6 +247,7 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   g.k = p.k; g.g_amp = p.g_amp; g.g_ramp = p.g_ramp;
   g.Mx = (int)Mx; g.My = (int)My; g.nx = (int)Mx - 1; g.ny = (int)My - 1;
   g.px = p.px; g.py = p.py; g.ovlp = o; g.pml = pml; g.local_bc = p.local_bc;
+  g.g_profile = p.g_profile;
   h->n = (long long)g.nx * g.ny;
 
   const bool imp = p.local_bc == 0;

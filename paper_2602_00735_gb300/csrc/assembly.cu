@@ -50,8 +50,9 @@ __device__ CellTerms<T> cell_terms(const Geo& g, const S& st, int ci, int cj) {
 
 // g'(d) in arithmetic type T; for T = double it is gprime() of common.cuh.
 template <typename T>
-__device__ __forceinline__ T gprime_t(double d, double amp, double ramp) {
+__device__ __forceinline__ T gprime_t(double d, double amp, double ramp, int profile) {
   if (!(d > 0.0)) return (T)0;
+  if (profile == 1) return (T)3 * (T)amp * (T)d * (T)d;
   const T t = fmin((T)d / (T)ramp, (T)1);
   return (T)amp * t * t * ((T)3 - (T)2 * t);
 }
@@ -70,11 +71,11 @@ struct LocalStretch {
   Geo g;
   SubDesc sd;
   __device__ cx<T> gam(double s, double x0, double x1, int lo, int hi, int flo, int fhi, double X0) const {
-    if ((sd.flags & fhi) && s >= 2.0 * hi) return mk((T)1, gprime_t<T>((s - 2.0 * hi) * g.hh, g.g_amp, g.g_ramp));
-    if ((sd.flags & flo) && s <= 2.0 * lo) return mk((T)1, gprime_t<T>((2.0 * lo - s) * g.hh, g.g_amp, g.g_ramp));
+    if ((sd.flags & fhi) && s >= 2.0 * hi) return mk((T)1, gprime_t<T>((s - 2.0 * hi) * g.hh, g.g_amp, g.g_ramp, g.g_profile));
+    if ((sd.flags & flo) && s <= 2.0 * lo) return mk((T)1, gprime_t<T>((2.0 * lo - s) * g.hh, g.g_amp, g.g_ramp, g.g_profile));
     const double x = __dadd_rn(X0, __dmul_rn(s, g.hh));
     const double d = fmax(fmax(x0 - x, x - x1), 0.0);
-    return mk((T)1, gprime_t<T>(d, g.g_amp, g.g_ramp));
+    return mk((T)1, gprime_t<T>(d, g.g_amp, g.g_ramp, g.g_profile));
   }
   __device__ cx<T> gx(double s) const { return gam(s, g.x0, g.x1, sd.int_lo_x, sd.int_hi_x, LO_X, HI_X, g.X0); }
   __device__ cx<T> gy(double s) const { return gam(s, g.y0, g.y1, sd.int_lo_y, sd.int_hi_y, LO_Y, HI_Y, g.Y0); }

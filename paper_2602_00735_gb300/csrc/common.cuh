@@ -92,6 +92,7 @@ struct Geo {
   int Mx, My, nx, ny;       // nx = Mx - 1 unknowns per grid row
   int px, py, ovlp, pml;
   int local_bc;
+  int g_profile;            // 0 smoothstep ramp, 1 g(d) = g_amp d^3
 };
 
 enum : int { LO_X = 1, HI_X = 2, LO_Y = 4, HI_Y = 8 };
@@ -119,9 +120,11 @@ __device__ __forceinline__ double ypos(const Geo& g, double s) {
   return __dadd_rn(g.Y0, __dmul_rn(s, g.hh));
 }
 
-// g'(d) = amp (3t^2 - 2t^3), t = min(d/ramp, 1), zero for d <= 0.
-__device__ __forceinline__ double gprime(double d, double amp, double ramp) {
+// g'(d), zero for d <= 0. profile 0: amp (3t^2 - 2t^3), t = min(d/ramp, 1);
+// profile 1: 3 amp d^2 (g(d) = amp d^3).
+__device__ __forceinline__ double gprime(double d, double amp, double ramp, int profile) {
   if (!(d > 0.0)) return 0.0;
+  if (profile == 1) return 3.0 * amp * d * d;
   double t = fmin(d / ramp, 1.0);
   return amp * t * t * (3.0 - 2.0 * t);
 }
@@ -130,28 +133,28 @@ __device__ __forceinline__ double gprime(double d, double amp, double ramp) {
 __device__ __forceinline__ c128 gam_global_x(const Geo& g, double s) {
   double x = xpos(g, s);
   double d = fmax(fmax(g.x0 - x, x - g.x1), 0.0);
-  return mk(1.0, gprime(d, g.g_amp, g.g_ramp));
+  return mk(1.0, gprime(d, g.g_amp, g.g_ramp, g.g_profile));
 }
 __device__ __forceinline__ c128 gam_global_y(const Geo& g, double s) {
   double y = ypos(g, s);
   double d = fmax(fmax(g.y0 - y, y - g.y1), 0.0);
-  return mk(1.0, gprime(d, g.g_amp, g.g_ramp));
+  return mk(1.0, gprime(d, g.g_amp, g.g_ramp, g.g_profile));
 }
 
 // Local stretching g_j (Section 2): restarts beyond an interior side of
 // Omega_j,int; the global stretching elsewhere.
 __device__ __forceinline__ c128 gam_local_x(const Geo& g, const SubDesc& sd, double s) {
   if ((sd.flags & HI_X) && s >= 2.0 * sd.int_hi_x)
-    return mk(1.0, gprime((s - 2.0 * sd.int_hi_x) * g.hh, g.g_amp, g.g_ramp));
+    return mk(1.0, gprime((s - 2.0 * sd.int_hi_x) * g.hh, g.g_amp, g.g_ramp, g.g_profile));
   if ((sd.flags & LO_X) && s <= 2.0 * sd.int_lo_x)
-    return mk(1.0, gprime((2.0 * sd.int_lo_x - s) * g.hh, g.g_amp, g.g_ramp));
+    return mk(1.0, gprime((2.0 * sd.int_lo_x - s) * g.hh, g.g_amp, g.g_ramp, g.g_profile));
   return gam_global_x(g, s);
 }
 __device__ __forceinline__ c128 gam_local_y(const Geo& g, const SubDesc& sd, double s) {
   if ((sd.flags & HI_Y) && s >= 2.0 * sd.int_hi_y)
-    return mk(1.0, gprime((s - 2.0 * sd.int_hi_y) * g.hh, g.g_amp, g.g_ramp));
+    return mk(1.0, gprime((s - 2.0 * sd.int_hi_y) * g.hh, g.g_amp, g.g_ramp, g.g_profile));
   if ((sd.flags & LO_Y) && s <= 2.0 * sd.int_lo_y)
-    return mk(1.0, gprime((2.0 * sd.int_lo_y - s) * g.hh, g.g_amp, g.g_ramp));
+    return mk(1.0, gprime((2.0 * sd.int_lo_y - s) * g.hh, g.g_amp, g.g_ramp, g.g_profile));
   return gam_global_y(g, s);
 }
 

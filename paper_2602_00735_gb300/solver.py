@@ -37,6 +37,7 @@ class RasPml:
             setattr(p, key, params[key])
         p.factor_prec = int(factor_prec)
         p.ortho = int(ortho)
+        p.g_profile = int(params.get("g_profile", 0))
         self._h = c_void_p()
         with torch.cuda.device(self.device):
             _lib.check("ras_pml_setup", self.lib.ras_pml_setup(byref(p), c_void_p(self.stream.cuda_stream),

@@ -46,9 +46,9 @@ def _sample_nodes(grid, count, seed):
 def _oracle_rows(p, grid, i, j):
     """Rows of the global matrix and load vector at nodes (i, j), from the
     four cells around each node (all of the node's triangles)."""
-    amp, ramp = p["g_amp"], p["g_ramp"]
-    gx = lambda s: fem.global_gamma_x(grid, s, amp, ramp)  # noqa: E731
-    gy = lambda s: fem.global_gamma_y(grid, s, amp, ramp)  # noqa: E731
+    amp, ramp, prof = p["g_amp"], p["g_ramp"], p.get("g_profile", 0)
+    gx = lambda s: fem.global_gamma_x(grid, s, amp, ramp, prof)  # noqa: E731
+    gy = lambda s: fem.global_gamma_y(grid, s, amp, ramp, prof)  # noqa: E731
     num = fem.interior_numbering(grid)
     rows = {}
     for node in zip(i, j):

@@ -155,3 +155,31 @@ def test_point_source_converges_to_hankel_with_pml():
     assert e80 < 0.05
     assert e40 / e80 > 3.0
     assert err(80, 0.0) > 0.5
+
+
+def test_cubic_profile_of_the_papers_experiments():
+    """Section 4: g(x) = 10 k x^3, so g'(d) = 30 k d^2 (profile 1), zero for d <= 0;
+    its numerical integral is g."""
+    k = 300.0
+    amp = 10.0 * k
+    d = np.array([-0.01, 0.0, 0.001, 0.01, 0.05])
+    gp = fem.gprime(d, amp, 1.0, profile=1)
+    assert np.all(gp[:2] == 0.0)
+    assert np.allclose(gp[2:], 3.0 * amp * d[2:] ** 2, rtol=1e-15)
+    for x in (0.003, 0.02, 0.06):
+        val, _ = quad(lambda t: float(fem.gprime(t, amp, 1.0, profile=1)), 0.0, x)
+        assert abs(val - amp * x ** 3) < 1e-12 * max(1.0, amp * x ** 3)
+
+
+def test_paper_setup_geometry():
+    """Section 4: Omega = (0,1)^2 with a three-wavelength PML, h = 1/(2k), the
+    smoothed-delta source of unit mass, widths from the law of Section 3 (iii)."""
+    w = workloads.paper_setup(300, 75, C_delta=1 / 6, C_kappa=3 / 8)
+    p = w.params()
+    grid = fem.make_grid(p)
+    assert grid.Mx == grid.My == 600 and abs(grid.X0) < 1e-15
+    assert abs(p["kappa_g"] - 3 * 2 * math.pi / 300) <= 0.5 * grid.h
+    # l(300) = 2: delta = lambda/3 -> 4 cells, kappa = 0.75 lambda -> 9 cells
+    assert (p["ovlp_cells"], p["pml_cells"]) == (4, 9)
+    b = fem.assemble_rhs(p, w.centres, w.amps, w.width)
+    assert abs(b.sum().real - 1.0) < 1e-3                    # unit mass (16k^2/pi^3 * pi w^2 = 1)

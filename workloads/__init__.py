@@ -17,6 +17,10 @@ Omega_int = (0,1)^2 in all four; overlap and local PML width are both
 0.5*ln(k)/k rounded half up to whole cells (at least one cell). Source centres
 are uniform in Omega_int from numpy's default_rng(seed); amplitudes are 1.
 Smaller "tiny*" workloads with the same construction serve the tests.
+
+paper_setup(k, cells_per_box, ...) builds the set-up of the paper's own
+experiments (Omega = (0,1)^2 with a three-wavelength PML, h = 1/(2k),
+g(x) = 10 k x^3, smoothed-delta source, the paper's width law).
 """
 from __future__ import annotations
 
@@ -50,6 +54,7 @@ class Workload:
     g_amp: float = 20.0
     g_ramp: float = 0.05
     local_bc: int = 0          # 0 impedance (RAS-PML-Imp), 1 Dirichlet
+    g_profile: int = 0         # 0 smoothstep ramp; 1 g(d) = g_amp d^3
     centres: np.ndarray = field(default_factory=lambda: np.zeros((0, 2)))
     amps: np.ndarray = field(default_factory=lambda: np.zeros(0))
     width: float = 0.02
@@ -72,7 +77,8 @@ class Workload:
         return dict(k=self.k, x0=self.x0, y0=self.y0, x1=self.x1, y1=self.y1,
                     kappa_g=self.kappa_g, h=self.h, px=self.px, py=self.py,
                     ovlp_cells=self.ovlp_cells, pml_cells=self.pml_cells,
-                    g_amp=self.g_amp, g_ramp=self.g_ramp, local_bc=self.local_bc)
+                    g_amp=self.g_amp, g_ramp=self.g_ramp, local_bc=self.local_bc,
+                    g_profile=self.g_profile)
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
@@ -87,6 +93,44 @@ def _make(name, k, h, p, ns, width, seed, side=1.0, kappa_g=0.1, ovlp=None, pml=
                     ovlp_cells=w if ovlp is None else ovlp,
                     pml_cells=w if pml is None else pml,
                     centres=centres, amps=np.ones(ns), width=width, seed=seed)
+
+
+def paper_width_cells(k: float, h: float, C: float, k0: float = 150.0) -> int:
+    """C * l(k) * 2*pi/k in whole cells (rounded half up, at least 1), with
+    l(k) = k/(k - k0) * log2(k/k0): the overlap / PML width law the paper
+    proposes for k > k0 (Section 3 (iii))."""
+    if not k > k0:
+        raise ValueError("the width law needs k > k0")
+    ell = k / (k - k0) * math.log2(k / k0)
+    return max(1, int(math.floor(C * ell * 2 * math.pi / k / h + 0.5)))
+
+
+def paper_setup(k: int, cells_per_box: int, C_delta: float = 1.0 / 6, C_kappa: float = 0.5,
+                local_bc: int = 0, pml: bool = True) -> Workload:
+    """The set-up of the paper's experiments (Section 4) on P1 triangles:
+    Omega = (0,1)^2 holds Omega_int and a global PML of three wavelengths
+    (kappa_g rounded to whole cells), h = 1/(2k) (12 points per wavelength),
+    stretching g(x) = 10 k x^3, the smoothed-delta source
+    f = 16k^2/pi^3 exp(-16 k^2 |x - (0.5,0.5)|^2 / pi^2) (a Gaussian of width
+    pi/(4k) and unit integral), overlap and local PML widths from the paper's
+    law. The number of boxes is chosen so that boxes have about
+    `cells_per_box` cells (the paper's boxes have ~300; the GPU kernels here
+    take subdomains up to ~110 cells across). pml=False gives RAS-Imp."""
+    if int(k) != k:
+        raise ValueError("k must be an integer (h = 1/(2k))")
+    M = 2 * int(k)
+    h = 1.0 / M
+    lam = 2 * math.pi / k
+    kg_cells = max(1, int(math.floor(3 * lam / h + 0.5)))
+    kappa_g = kg_cells * h
+    P = max(1, int(round(M / cells_per_box)))
+    ovlp = paper_width_cells(k, h, C_delta)
+    pml_cells = paper_width_cells(k, h, C_kappa) if pml else 0
+    w = math.pi / (4 * k)
+    return Workload(name=f"paper-k{k}", k=float(k), x0=kappa_g, y0=kappa_g, x1=1 - kappa_g, y1=1 - kappa_g,
+                    kappa_g=kappa_g, h=h, px=P, py=P, ovlp_cells=ovlp, pml_cells=pml_cells,
+                    g_amp=10.0 * k, g_ramp=1.0, local_bc=local_bc, g_profile=1,
+                    centres=np.array([[0.5, 0.5]]), amps=np.array([16 * k * k / math.pi ** 3]), width=w, seed=0)
 
 
 def get(name: str) -> Workload:
