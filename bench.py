@@ -49,7 +49,7 @@ import workloads  # noqa: E402
 
 METRIC = "RAS-PML time to rtol 1e-6 at k=160*pi, complex64 local factors + complex128 FGMRES (s)"
 RTOL = 1e-6
-MAXIT = 1000
+MAXIT = 400
 
 
 def peaks():

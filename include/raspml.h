@@ -179,7 +179,9 @@ int ras_pml_matvec(ras_pml_handle* h, const rp_c128* x_dev, rp_c128* y_dev);
  * rotations), on the device. x_dev holds x0 on entry and the solution on exit.
  * Stops when the residual estimate ||b-Ax||/||b|| <= rtol or after maxit
  * preconditioned directions (restart = 0: no restart; else the Krylov space
- * is rebuilt every `restart` directions). rtol = 0 runs exactly maxit
+ * is rebuilt every `restart` directions). The Krylov space takes
+ * (2m+1)*n*16 bytes for a cycle of m directions; if that does not fit in
+ * the free device memory, the cycle is shortened to what fits. rtol = 0 runs exactly maxit
  * directions. *iters gets the number of directions, *relres the final true
  * relative residual ||b - A x||_2 / ||b||_2 (computed in complex128).
  * Factors first if needed. Returns 0, RASPML_NOT_CONVERGED, or an error. */

@@ -443,7 +443,20 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
     int s = ras_pml_factor(h);
     if (s != RASPML_OK) return s;
   }
-  const int m = (restart > 0 && restart < maxit) ? restart : maxit;
+  int m = (restart > 0 && restart < maxit) ? restart : maxit;
+  // The Krylov space (V: m+1 and Z: m vectors of n complex128) must fit in
+  // the free device memory; beyond that the cycle is shortened (restarted
+  // FGMRES) rather than failing.
+  if (m > h->kcap) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+      const double per_vec = 16.0 * (double)h->n;
+      const double held = h->kcap > 0 ? (2.0 * h->kcap + 2.0) * per_vec : 0.0;   // freed on regrowth
+      const double avail = (double)free_b + held - 0.05 * (double)total_b - 512.0 * 1048576.0;
+      const int fit = (int)std::max(1.0, std::floor(avail / (2.0 * per_vec) - 2.0));
+      if (fit < m) m = fit;
+    }
+  }
   int s = ensure_krylov(h, m, maxit);
   if (s != RASPML_OK) return s;
   const long long n = h->n;
