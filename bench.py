@@ -271,7 +271,7 @@ def run_ours(args, rank, world, local_rank):
 
     clocks = ClockSampler(local_rank)
     clocks.start()
-    t_c64, per_c64, x_c64 = timed(1, args.steps, args.warmup)
+    t_c64, per_c64, x_c64 = timed(args.prec, args.steps, args.warmup)
     clk = clocks.stop()
     fp64 = None
     x_f64 = None
@@ -297,7 +297,7 @@ def run_ours(args, rank, world, local_rank):
     # end to end through host buffers
     e2e = None
     if not args.skip_e2e:
-        s0 = RasPml(p, factor_prec=1, ortho=args.ortho)
+        s0 = RasPml(p, factor_prec=args.prec, ortho=args.ortho)
         b_host = s0.assemble_rhs(w.centres, w.amps, w.width).cpu().pin_memory()
         s0.close()
         x_host = torch.zeros_like(b_host).pin_memory()
@@ -306,7 +306,7 @@ def run_ours(args, rank, world, local_rank):
             x_host.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            s = RasPml(p, factor_prec=1, ortho=args.ortho)
+            s = RasPml(p, factor_prec=args.prec, ortho=args.ortho)
             s.factor()
             s.solve_host(b_host, rtol=RTOL, maxit=MAXIT, x_host=x_host)
             t1 = time.perf_counter()
@@ -396,6 +396,8 @@ def main():
     ap.add_argument("--ortho", type=int, default=3, choices=[0, 1, 2, 3],
                     help="0: classical Gram-Schmidt twice; 1: once plus the DGKS reorthogonalisation test; "
                          "2: once; 3: once in double-float arithmetic")
+    ap.add_argument("--prec", type=int, default=1, choices=[1, 2],
+                    help="local factors of the headline form: 1 complex64, 2 complex64 with half-precision storage")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

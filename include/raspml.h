@@ -80,7 +80,9 @@ typedef struct {
   int    local_bc;        /* 0: impedance closure (RAS-PML-Imp, Section 3 (ii));
                              1: Dirichlet closure (RAS-PML-Drch, Section 2)    */
   int    factor_prec;     /* local factors and solves: 0 complex128,
-                             1 complex64 (outer iteration stays complex128)    */
+                             1 complex64, 2 complex64 arithmetic with the L
+                             entries stored as pairs of IEEE halves (4 bytes);
+                             the outer iteration stays complex128              */
   int    ortho;           /* Arnoldi orthogonalisation, all in complex128:
                              0 classical Gram-Schmidt applied twice;
                              1 classical Gram-Schmidt once, repeated only when

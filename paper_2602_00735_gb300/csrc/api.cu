@@ -217,7 +217,7 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   const ras_pml_params& p = *pp;
   if (!(p.k >= 0.0) || !(p.h > 0.0) || !(p.kappa_g >= 0.0) || !(p.x1 > p.x0) || !(p.y1 > p.y0) || p.px < 1 ||
       p.py < 1 || !(p.g_ramp > 0.0) || !(p.g_amp >= 0.0) || (p.local_bc != 0 && p.local_bc != 1) ||
-      (p.factor_prec != 0 && p.factor_prec != 1) || (p.ortho < 0 || p.ortho > 3) || (p.g_profile != 0 && p.g_profile != 1))
+      (p.factor_prec < 0 || p.factor_prec > 2) || (p.ortho < 0 || p.ortho > 3) || (p.g_profile != 0 && p.g_profile != 1))
     return RASPML_EBADARG;
   const double lx = p.x1 - p.x0 + 2 * p.kappa_g, ly = p.y1 - p.y0 + 2 * p.kappa_g;
   const long long Mx = std::llround(lx / p.h), My = std::llround(ly / p.h);
@@ -320,7 +320,8 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
 int ras_pml_info(const ras_pml_handle* h, ras_pml_info_t* info) {
   if (!h || !info) return RASPML_EBADARG;
   std::memset(info, 0, sizeof(*info));
-  const double es = h->p.factor_prec == 0 ? 16.0 : 8.0;
+  const double es = h->p.factor_prec == 0 ? 16.0 : 8.0;          // D^-1 and work vector
+  const double esl = h->p.factor_prec == 0 ? 16.0 : h->p.factor_prec == 1 ? 8.0 : 4.0;   // L entries
   info->n = h->n;
   info->Mx = h->geo.Mx;
   info->My = h->geo.My;
@@ -331,9 +332,9 @@ int ras_pml_info(const ras_pml_handle* h, ras_pml_info_t* info) {
   info->max_band = h->max_b;
   info->sum_local_n = h->sum_n;
   info->sum_band_n = h->sum_bn;
-  info->factor_bytes = (int64_t)((2 * h->sum_l + h->sum_npad) * es);   // L, its reversed row copy, D^-1
+  info->factor_bytes = (int64_t)(2 * h->sum_l * esl + h->sum_npad * es);   // L, its reversed row copy, D^-1
   // L read in the forward and in the backward sweep, D^-1 once, r read once, z written once
-  info->apply_bytes = 2.0 * es * (double)h->sum_bn + es * (double)h->sum_n + 32.0 * (double)h->n;
+  info->apply_bytes = 2.0 * esl * (double)h->sum_bn + es * (double)h->sum_n + 32.0 * (double)h->n;
   info->min_pivot_ratio = h->min_pivot_ratio;
   info->factored = h->factored ? 1 : 0;
   info->factor_prec = h->p.factor_prec;
@@ -365,12 +366,13 @@ int ras_pml_factor(ras_pml_handle* h) {
   if (!h) return RASPML_EBADARG;
   cudaSetDevice(h->dev);
   const size_t es = h->p.factor_prec == 0 ? sizeof(c128) : sizeof(c64);
+  const size_t esl = h->p.factor_prec == 0 ? 16 : h->p.factor_prec == 1 ? 8 : 4;   // L entry storage
   if (!h->L) {
     void* p;
-    cudaError_t e = cudaMalloc(&p, (size_t)h->sum_l * es);
+    cudaError_t e = cudaMalloc(&p, (size_t)h->sum_l * esl);
     if (e != cudaSuccess) return RASPML_ENOMEM;
     h->L = p;
-    e = cudaMalloc(&p, (size_t)h->sum_l * es);
+    e = cudaMalloc(&p, (size_t)h->sum_l * esl);
     if (e != cudaSuccess) return RASPML_ENOMEM;
     h->Lrev = p;
     e = cudaMalloc(&p, (size_t)h->sum_npad * es);
@@ -389,7 +391,7 @@ int ras_pml_factor(ras_pml_handle* h) {
   rp::DevStatus s0{-1, 0, 0, 0};
   cudaError_t e = cudaMemcpyAsync(h->status, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[0], h->st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->Lrev, 0, (size_t)h->sum_l * es, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Lrev, 0, (size_t)h->sum_l * esl, h->st);
   if (e == cudaSuccess) e = rp::launch_local_rows(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
   if (e == cudaSuccess)
     e = rp::launch_factor(h->p.factor_prec, h->subs_d, h->nsub, h->max_b, Aloc, h->L, h->Lrev, h->dinv,

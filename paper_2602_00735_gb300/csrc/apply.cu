@@ -28,7 +28,10 @@ namespace rp {
 namespace {
 
 constexpr int kCol = 8;       // columns per bulk copy
-constexpr int kStages = 4;    // ring depth
+// ring depth: 4 stages of 8 columns (a deeper ring for half-pair entries was
+// measured: no gain on c2, slower on c4)
+template <typename ST>
+constexpr int stages_for() { return 4; }
 
 // R_j r at local row `row`: r is complex128, or double-float (dfc) when rdf
 template <typename R>
@@ -44,42 +47,43 @@ __device__ __forceinline__ cx<R> gather_row(const SubDesc& sd, const Geo& g, con
   return cvt<R>(r[idx]);
 }
 
-template <typename R>
+template <typename S>
 struct Pipe {
   uint64_t* bar;
-  cx<R>* stg;
-  const cx<R>* src0;   // forward band (columns of L)
-  const cx<R>* src1;   // reversed row band of L
+  S* stg;
+  const S* src0;       // forward band (columns of L)
+  const S* src1;       // reversed row band of L
   int stage_elems, Q, bp;
   uint32_t bytes;
   __device__ void issue(int s) const {
-    const cx<R>* src = s < Q ? src0 + (long long)s * kCol * bp : src1 + (long long)(s - Q) * kCol * bp;
-    const int st = s % kStages;
+    const S* src = s < Q ? src0 + (long long)s * kCol * bp : src1 + (long long)(s - Q) * kCol * bp;
+    const int st = s % stages_for<S>();
     mbar_arrive_expect_tx(&bar[st], bytes);
     bulk_g2s(stg + st * stage_elems, src, bytes, &bar[st]);
   }
-  __device__ const cx<R>* wait(int s, bool& ok) const {
-    const int st = s % kStages;
-    ok = mbar_wait_bounded(&bar[st], (uint32_t)((s / kStages) & 1));
+  __device__ const S* wait(int s, bool& ok) const {
+    const int st = s % stages_for<S>();
+    ok = mbar_wait_bounded(&bar[st], (uint32_t)((s / stages_for<S>()) & 1));
     return stg + st * stage_elems;
   }
 };
 
-// The 32 steps of one row group with window phase PH (= group mod S).
-template <typename R, int S, int PH>
-__device__ __forceinline__ bool group_steps(const Pipe<R>& pp, int s0, int b, int lane, cx<R> (&win)[S],
+// The 32 steps of one row group with window phase PH (= group mod S);
+// ST is the storage type of the factor entries.
+template <typename R, typename ST, int S, int PH>
+__device__ __forceinline__ bool group_steps(const Pipe<ST>& pp, int s0, int b, int lane, cx<R> (&win)[S],
                                             const cx<R>& nxt, cx<R>& outv) {
   const int bp = pp.bp;
 #pragma unroll 1
   for (int c4 = 0; c4 < 32 / kCol; ++c4) {
     const int s = s0 + c4;
     bool ok;
-    const cx<R>* Lc = pp.wait(s, ok);
+    const ST* Lc = pp.wait(s, ok);
     if (!__all_sync(0xffffffffu, ok)) return false;
 #pragma unroll 2
     for (int ii = 0; ii < kCol; ++ii) {
       const int i = c4 * kCol + ii;
-      const cx<R>* col = Lc + ii * bp;
+      const ST* col = Lc + ii * bp;
       const cx<R> y = shfl(win[PH], i);
       if (lane == i) {
         outv = y;
@@ -89,33 +93,33 @@ __device__ __forceinline__ bool group_steps(const Pipe<R>& pp, int s0, int b, in
 #pragma unroll
       for (int sl = 0; sl < S; ++sl) {
         const int t = (sl == PH) ? ((lane > i) ? base : base + 32 * S) : base + 32 * ((sl - PH + S) % S);
-        if (t < b) win[sl] = fms(win[sl], col[t], y);
+        if (t < b) win[sl] = fms(win[sl], ld_entry(col[t]), y);
       }
     }
     __syncwarp();
-    if (lane == 0 && s + kStages < 2 * pp.Q) {
+    if (lane == 0 && s + stages_for<ST>() < 2 * pp.Q) {
       fence_proxy_async_smem();
-      pp.issue(s + kStages);
+      pp.issue(s + stages_for<ST>());
     }
   }
   return true;
 }
 
-template <typename R, int S>
-__device__ __forceinline__ bool group_dispatch(int ph, const Pipe<R>& pp, int s0, int b, int lane, cx<R> (&win)[S],
+template <typename R, typename ST, int S>
+__device__ __forceinline__ bool group_dispatch(int ph, const Pipe<ST>& pp, int s0, int b, int lane, cx<R> (&win)[S],
                                                const cx<R>& nxt, cx<R>& outv) {
   switch (ph) {
-    case 0: return group_steps<R, S, 0>(pp, s0, b, lane, win, nxt, outv);
-    case 1: if constexpr (S > 1) return group_steps<R, S, 1>(pp, s0, b, lane, win, nxt, outv); break;
-    case 2: if constexpr (S > 2) return group_steps<R, S, 2>(pp, s0, b, lane, win, nxt, outv); break;
-    case 3: if constexpr (S > 3) return group_steps<R, S, 3>(pp, s0, b, lane, win, nxt, outv); break;
+    case 0: return group_steps<R, ST, S, 0>(pp, s0, b, lane, win, nxt, outv);
+    case 1: if constexpr (S > 1) return group_steps<R, ST, S, 1>(pp, s0, b, lane, win, nxt, outv); break;
+    case 2: if constexpr (S > 2) return group_steps<R, ST, S, 2>(pp, s0, b, lane, win, nxt, outv); break;
+    case 3: if constexpr (S > 3) return group_steps<R, ST, S, 3>(pp, s0, b, lane, win, nxt, outv); break;
   }
   return false;
 }
 
-template <typename R, int S>
+template <typename R, typename ST, int S>
 __global__ void __launch_bounds__(32)
-    k_apply(Geo g, const SubDesc* __restrict__ subs, const cx<R>* __restrict__ Lf, const cx<R>* __restrict__ Lb,
+    k_apply(Geo g, const SubDesc* __restrict__ subs, const ST* __restrict__ Lf, const ST* __restrict__ Lb,
             const cx<R>* __restrict__ dinv_all, const c128* __restrict__ rglob, int rdf, cx<R>* __restrict__ Y,
             int stage_elems, const KState* __restrict__ kst, DevStatus* status) {
   extern __shared__ __align__(128) unsigned char sm[];
@@ -123,29 +127,30 @@ __global__ void __launch_bounds__(32)
   const SubDesc sd = subs[blockIdx.x];
   const int lane = threadIdx.x;
   const int b = sd.b, npad = sd.npad, G = npad / 32;
-  Pipe<R> pp;
+  Pipe<ST> pp;
   pp.bar = reinterpret_cast<uint64_t*>(sm);
-  pp.stg = reinterpret_cast<cx<R>*>(sm + 128);
+  pp.stg = reinterpret_cast<ST*>(sm + 128);
   pp.src0 = Lf + sd.l_off;
   pp.src1 = Lb + sd.l_off;
   pp.stage_elems = stage_elems;
   pp.Q = npad / kCol;
   pp.bp = sd.bp;
-  pp.bytes = (uint32_t)(kCol * sd.bp * sizeof(cx<R>));
+  pp.bytes = (uint32_t)(kCol * sd.bp * sizeof(ST));
   const cx<R>* dv = dinv_all + sd.v_off;
   cx<R>* Yj = Y + sd.v_off;
   const int nseq = 2 * pp.Q;
+  constexpr int NST = stages_for<ST>();
   if (lane == 0) {
-    for (int t = 0; t < kStages; ++t) mbar_init(&pp.bar[t], 1);
+    for (int t = 0; t < NST; ++t) mbar_init(&pp.bar[t], 1);
     mbar_fence_init();
-    for (int t = 0; t < kStages && t < nseq; ++t) pp.issue(t);
+    for (int t = 0; t < NST && t < nseq; ++t) pp.issue(t);
   }
   __syncwarp();
   auto fail = [&](int s) {
     // a bounded wait gave up: record it, drain this warp's copies in flight, leave
     if (lane == 0) {
       atomicExch(&status->timeout, 1);
-      for (int t = s; t < s + kStages && t < nseq; ++t) mbar_wait_bounded(&pp.bar[t % kStages], (t / kStages) & 1);
+      for (int t = s; t < s + NST && t < nseq; ++t) mbar_wait_bounded(&pp.bar[t % NST], (t / NST) & 1);
     }
     __syncwarp();
   };
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(32)
     const cx<R> nxt2 = gather_row<R>(sd, g, rglob, rdf, 32 * (gi + S + 1) + lane);
     const cx<R> d = dv[32 * gi + lane];
     cx<R> outv;
-    if (!group_dispatch<R, S>(gi % S, pp, 4 * gi, b, lane, win, nxt, outv)) { fail(4 * gi); return; }
+    if (!group_dispatch<R, ST, S>(gi % S, pp, 4 * gi, b, lane, win, nxt, outv)) { fail(4 * gi); return; }
     Yj[32 * gi + lane] = outv * d;
     nxt = nxt2;
   }
@@ -175,7 +180,7 @@ __global__ void __launch_bounds__(32)
   for (int gi = 0; gi < G; ++gi) {
     const cx<R> nxt2 = zrow(32 * (gi + S + 1) + lane);
     cx<R> outv;
-    if (!group_dispatch<R, S>(gi % S, pp, pp.Q + 4 * gi, b, lane, win, nxt, outv)) {
+    if (!group_dispatch<R, ST, S>(gi % S, pp, pp.Q + 4 * gi, b, lane, win, nxt, outv)) {
       fail(pp.Q + 4 * gi);
       return;
     }
@@ -219,24 +224,37 @@ __global__ void k_prolong(Geo g, const SubDesc* __restrict__ subs, const cx<R>* 
   z[r] = mk(re, im);
 }
 
-template <typename R, int S>
+template <typename R, typename ST, int S>
 cudaError_t launch_apply_t(const Geo& g, const SubDesc* subs, int nsub, int max_bp, const void* Lf, const void* Lb,
                            const void* dinv, const c128* r, int rdf, void* Y, const KState* kst, DevStatus* status,
                            cudaStream_t st) {
   const int stage_elems = kCol * max_bp;
-  const size_t smem = apply_smem_bytes(max_bp, sizeof(R) == 8 ? 0 : 1);
-  cudaError_t e = cudaFuncSetAttribute(k_apply<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = 128 + (size_t)stages_for<ST>() * kCol * max_bp * sizeof(ST);
+  cudaError_t e = cudaFuncSetAttribute(k_apply<R, ST, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_apply<R, S><<<nsub, 32, smem, st>>>(g, subs, (const cx<R>*)Lf, (const cx<R>*)Lb, (const cx<R>*)dinv, r, rdf,
-                                        (cx<R>*)Y, stage_elems, kst, status);
+  k_apply<R, ST, S><<<nsub, 32, smem, st>>>(g, subs, (const ST*)Lf, (const ST*)Lb, (const cx<R>*)dinv, r, rdf,
+                                            (cx<R>*)Y, stage_elems, kst, status);
   return cudaGetLastError();
+}
+
+template <typename R, typename ST>
+cudaError_t launch_apply_s(int S, const Geo& g, const SubDesc* subs, int nsub, int max_bp, const void* Lf,
+                           const void* Lb, const void* dinv, const c128* r, int rdf, void* Y, const KState* kst,
+                           DevStatus* status, cudaStream_t st) {
+  switch (S) {
+    case 1: return launch_apply_t<R, ST, 1>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
+    case 2: return launch_apply_t<R, ST, 2>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
+    case 3: return launch_apply_t<R, ST, 3>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
+    default: return launch_apply_t<R, ST, 4>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
+  }
 }
 
 }  // namespace
 
 size_t apply_smem_bytes(int max_bp, int prec) {
-  size_t es = prec == 0 ? sizeof(c128) : sizeof(c64);
-  return 128 + (size_t)kStages * kCol * max_bp * es;
+  if (prec == 0) return 128 + (size_t)stages_for<c128>() * kCol * max_bp * sizeof(c128);
+  if (prec == 1) return 128 + (size_t)stages_for<c64>() * kCol * max_bp * sizeof(c64);
+  return 128 + (size_t)stages_for<h2c>() * kCol * max_bp * sizeof(h2c);
 }
 
 cudaError_t launch_apply(int prec, const Geo& g, const SubDesc* subs, int nsub, int max_b, int max_bp,
@@ -245,21 +263,12 @@ cudaError_t launch_apply(int prec, const Geo& g, const SubDesc* subs, int nsub, 
   const int rdf = r_is_df ? 1 : 0;
   const int S = (max_b + 1 + 31) / 32;
   cudaError_t e;
-  if (prec == 0) {
-    switch (S) {
-      case 1: e = launch_apply_t<double, 1>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
-      case 2: e = launch_apply_t<double, 2>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
-      case 3: e = launch_apply_t<double, 3>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
-      default: e = launch_apply_t<double, 4>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
-    }
-  } else {
-    switch (S) {
-      case 1: e = launch_apply_t<float, 1>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
-      case 2: e = launch_apply_t<float, 2>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
-      case 3: e = launch_apply_t<float, 3>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
-      default: e = launch_apply_t<float, 4>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st); break;
-    }
-  }
+  if (prec == 0)
+    e = launch_apply_s<double, c128>(S, g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
+  else if (prec == 1)
+    e = launch_apply_s<float, c64>(S, g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
+  else
+    e = launch_apply_s<float, h2c>(S, g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
   if (e != cudaSuccess) return e;
   long long n = (long long)g.nx * g.ny;
   int threads = 256;

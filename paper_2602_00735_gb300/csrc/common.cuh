@@ -3,6 +3,7 @@
 // for bulk (TMA) copies with mbarrier completion.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -73,6 +74,23 @@ __host__ __device__ __forceinline__ cx<R> crecip(cx<R> b) {
 }
 template <typename To, typename From>
 __host__ __device__ __forceinline__ cx<To> cvt(cx<From> a) { return {(To)a.re, (To)a.im}; }
+
+// Storage of factor entries: the arithmetic type itself, or (for complex64
+// arithmetic) a pair of IEEE halves, 4 bytes per complex entry.
+struct __align__(4) h2c {
+  __half re, im;
+};
+template <typename R>
+__device__ __forceinline__ cx<R> ld_entry(const cx<R>& v) { return v; }
+__device__ __forceinline__ c64 ld_entry(const h2c& v) { return {__half2float(v.re), __half2float(v.im)}; }
+template <typename S, typename R>
+__device__ __forceinline__ S st_entry(cx<R> v);
+template <>
+__device__ __forceinline__ c64 st_entry<c64, float>(c64 v) { return v; }
+template <>
+__device__ __forceinline__ c128 st_entry<c128, double>(c128 v) { return v; }
+template <>
+__device__ __forceinline__ h2c st_entry<h2c, float>(c64 v) { return {__float2half_rn(v.re), __float2half_rn(v.im)}; }
 
 template <typename R>
 __device__ __forceinline__ cx<R> shfl(cx<R> v, int src) {

@@ -66,10 +66,11 @@ __device__ __forceinline__ cx<R> row_entry(const cx<R> (&v)[4], int t, int b) {
   return r;
 }
 
-template <typename R>
+// R: arithmetic; S: storage of the L entries (cx<R>, or h2c halves).
+template <typename R, typename S>
 __global__ void __launch_bounds__(kFactorThreads)
-    k_factor_ldlt(const SubDesc* __restrict__ subs, const c128* __restrict__ Aloc, cx<R>* __restrict__ Lall,
-                  cx<R>* __restrict__ Lrev_all, cx<R>* __restrict__ dinv_all, double* __restrict__ pivstats,
+    k_factor_ldlt(const SubDesc* __restrict__ subs, const c128* __restrict__ Aloc, S* __restrict__ Lall,
+                  S* __restrict__ Lrev_all, cx<R>* __restrict__ dinv_all, double* __restrict__ pivstats,
                   DevStatus* status) {
   extern __shared__ __align__(16) unsigned char sm[];
   const SubDesc sd = subs[blockIdx.x];
@@ -80,8 +81,8 @@ __global__ void __launch_bounds__(kFactorThreads)
   cx<R>* cbuf = W + Wc * Wc;
   cx<R>* lbuf = cbuf + Wc;
   uint16_t* pairs = reinterpret_cast<uint16_t*>(lbuf + Wc);
-  cx<R>* L = Lall + sd.l_off;
-  cx<R>* Lr = Lrev_all + sd.l_off;
+  S* L = Lall + sd.l_off;
+  S* Lr = Lrev_all + sd.l_off;
   cx<R>* dv = dinv_all + sd.v_off;
 
   // (i', j') with 1 <= j' <= i' <= b, column by column
@@ -140,12 +141,13 @@ __global__ void __launch_bounds__(kFactorThreads)
         dmin2 = fmin(dmin2, ad2);
         dmax2 = fmax(dmax2, ad2);
         dv[k] = di;
-        if (bp > b) L[(long long)k * bp + b] = mk((R)0, (R)0);
+        if (bp > b) L[(long long)k * bp + b] = st_entry<S, R>(mk((R)0, (R)0));
       } else {
         cx<R> l = c * di;
         lbuf[tid] = l;
-        L[(long long)k * bp + (tid - 1)] = l;
-        if (k + tid < sd.npad) Lr[(long long)(sd.npad - 1 - (k + tid)) * bp + (tid - 1)] = l;
+        const S ls = st_entry<S, R>(l);
+        L[(long long)k * bp + (tid - 1)] = ls;
+        if (k + tid < sd.npad) Lr[(long long)(sd.npad - 1 - (k + tid)) * bp + (tid - 1)] = ls;
       }
     }
     __syncthreads();
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(kFactorThreads)
 }  // namespace
 
 size_t factor_smem_bytes(int b, int prec) {
-  size_t es = prec == 0 ? sizeof(c128) : sizeof(c64);
+  size_t es = prec == 0 ? sizeof(c128) : sizeof(c64);   // window in the arithmetic type
   size_t wc = (size_t)b + 1;
   return wc * wc * es + 2 * wc * es + (size_t)b * (b + 1) / 2 * sizeof(uint16_t);
 }
@@ -193,15 +195,20 @@ cudaError_t launch_factor(int prec, const SubDesc* subs, int nsub, int max_b, co
   size_t smem = factor_smem_bytes(max_b, prec);
   cudaError_t e;
   if (prec == 0) {
-    e = cudaFuncSetAttribute(k_factor_ldlt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_factor_ldlt<double, c128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_factor_ldlt<double><<<nsub, kFactorThreads, smem, st>>>(subs, Aloc, (c128*)L, (c128*)Lrev, (c128*)dinv,
-                                                               pivstats, status);
+    k_factor_ldlt<double, c128><<<nsub, kFactorThreads, smem, st>>>(subs, Aloc, (c128*)L, (c128*)Lrev,
+                                                                     (c128*)dinv, pivstats, status);
+  } else if (prec == 1) {
+    e = cudaFuncSetAttribute(k_factor_ldlt<float, c64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_factor_ldlt<float, c64><<<nsub, kFactorThreads, smem, st>>>(subs, Aloc, (c64*)L, (c64*)Lrev, (c64*)dinv,
+                                                                   pivstats, status);
   } else {
-    e = cudaFuncSetAttribute(k_factor_ldlt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_factor_ldlt<float, h2c>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_factor_ldlt<float><<<nsub, kFactorThreads, smem, st>>>(subs, Aloc, (c64*)L, (c64*)Lrev, (c64*)dinv, pivstats,
-                                                             status);
+    k_factor_ldlt<float, h2c><<<nsub, kFactorThreads, smem, st>>>(subs, Aloc, (h2c*)L, (h2c*)Lrev, (c64*)dinv,
+                                                                   pivstats, status);
   }
   return cudaGetLastError();
 }

@@ -185,13 +185,28 @@ def test_c64_apply_close_to_oracle(solver_cls, name, kw):
         assert rel(z, R.apply(r)) <= 1e-4
 
 
+@pytest.mark.parametrize("name,kw", CASES[:6], ids=IDS[:6])
+def test_half_storage_apply_close_to_oracle(solver_cls, name, kw):
+    """factor_prec = 2: complex64 factorisation, L entries stored as IEEE half
+    pairs (relative rounding 2^-11 per entry), sweeps in FP32. The apply then
+    differs from the exact B^-1 by about 1e-3; bounded here by 2e-2."""
+    w = variant(name, **kw)
+    grid, A, R = oracle_problem(w)
+    with solver_cls(w.params(), factor_prec=2) as s:
+        s.factor()
+        r = random_vector(grid.n, 2)
+        z = s.apply(to_dev(r)).cpu().numpy()
+        assert rel(z, R.apply(r)) <= 2e-2
+
+
+@pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("name", ["tiny3", "small", "c0"])
-def test_c64_fgmres_converges_to_fp64_solution(solver_cls, name):
+def test_c64_fgmres_converges_to_fp64_solution(solver_cls, name, prec):
     w = variant(name)
     p = w.params()
     grid, A, _ = oracle_problem(w)
     u = fem.direct_solve(A, fem.assemble_rhs(p, w.centres, w.amps, w.width))
-    with solver_cls(p, factor_prec=1) as s:
+    with solver_cls(p, factor_prec=prec) as s:
         b = s.assemble_rhs(w.centres, w.amps, w.width)
         x, it, relres, st = s.solve(b, rtol=1e-11, maxit=400)
         assert st == 0 and relres <= 1e-11
