@@ -121,7 +121,8 @@ typedef struct ras_pml_handle ras_pml_handle;
 /* Builds the mesh, the covering of Section 2 and the global matrix of
  * eq. weak on the current device, on `cuda_stream` (a cudaStream_t, may be
  * NULL for the legacy default stream). Validates params (RASPML_EBADARG when
- * Omega is not whole cells, 2*ovlp exceeds a box, or a local half-bandwidth nlx+1 exceeds 112).
+ * Omega is not whole cells, 2*ovlp exceeds a box, or a local half-bandwidth nlx+1 exceeds
+ * 160 for factor_prec 0 or 232 for factor_prec 1 and 2).
  * On success *out owns all device memory of the handle. */
 int ras_pml_setup(const ras_pml_params* params, void* cuda_stream,
                   ras_pml_handle** out);

@@ -272,7 +272,7 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
       d.npad = (d.n + 31) / 32 * 32;
       d.b = d.nlx + 1;
       d.bp = d.b + (d.b & 1);
-      if (d.b > rp::kMaxBand) { delete h; return RASPML_EBADARG; }
+      if (d.b > rp::max_band(p.factor_prec)) { delete h; return RASPML_EBADARG; }
       d.l_off = l_off;
       d.v_off = v_off;
       l_off += (long long)d.npad * d.bp;

@@ -113,6 +113,10 @@ __device__ __forceinline__ bool group_dispatch(int ph, const Pipe<ST>& pp, int s
     case 1: if constexpr (S > 1) return group_steps<R, ST, S, 1>(pp, s0, b, lane, win, nxt, outv); break;
     case 2: if constexpr (S > 2) return group_steps<R, ST, S, 2>(pp, s0, b, lane, win, nxt, outv); break;
     case 3: if constexpr (S > 3) return group_steps<R, ST, S, 3>(pp, s0, b, lane, win, nxt, outv); break;
+    case 4: if constexpr (S > 4) return group_steps<R, ST, S, 4>(pp, s0, b, lane, win, nxt, outv); break;
+    case 5: if constexpr (S > 5) return group_steps<R, ST, S, 5>(pp, s0, b, lane, win, nxt, outv); break;
+    case 6: if constexpr (S > 6) return group_steps<R, ST, S, 6>(pp, s0, b, lane, win, nxt, outv); break;
+    case 7: if constexpr (S > 7) return group_steps<R, ST, S, 7>(pp, s0, b, lane, win, nxt, outv); break;
   }
   return false;
 }
@@ -245,8 +249,16 @@ cudaError_t launch_apply_s(int S, const Geo& g, const SubDesc* subs, int nsub, i
     case 1: return launch_apply_t<R, ST, 1>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
     case 2: return launch_apply_t<R, ST, 2>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
     case 3: return launch_apply_t<R, ST, 3>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
-    default: return launch_apply_t<R, ST, 4>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
+    case 4: return launch_apply_t<R, ST, 4>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
+    case 5: return launch_apply_t<R, ST, 5>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
+    case 6: return launch_apply_t<R, ST, 6>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
   }
+  if constexpr (sizeof(R) == 4) {
+    // complex64 factors allow bands up to 232 (b + 1 <= 256)
+    if (S == 7) return launch_apply_t<R, ST, 7>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
+    if (S == 8) return launch_apply_t<R, ST, 8>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace

@@ -4,14 +4,23 @@
 // the x-fastest local numbering its half-bandwidth is b = nlx + 1.
 //
 // One CTA factors one subdomain, right-looking, holding the active
-// (b+1) x (b+1) window of the matrix in shared memory as a circular buffer:
-// row/column index i lives in slot i mod (b+1). Step k
-//   1. reads the pivot column c_i = W(k+i, k), d = c_0, l_i = c_i / d,
+// window of the matrix (rows and columns k..k+b, lower triangle) in shared
+// memory. The window is stored by diagonals: entry (c+t, c), 0 <= t <= b,
+// lives on diagonal t, a circular buffer of m_t = b+1-t slots at offset
+// off_t = t(b+1) - t(t-1)/2, column c in slot c mod m_t. At step k diagonal
+// t holds columns k..k+b-t (exactly m_t of them), so the window needs
+// (b+1)(b+2)/2 entries, half of a square window, and the row entering at
+// step k meets diagonal t at column k+b+1-t = k (mod m_t): it takes the slot
+// that the pivot column frees. Step k
+//   1. reads the pivot column c_t = W(k+t, k), d = c_0, l_t = c_t / d,
 //      and writes L(:, k) = l and D^-1(k) = 1/d to global memory;
 //   2. applies the rank-1 update W(k+i, k+j) -= c_i l_j, 1 <= j <= i <= b;
-//   3. moves row k+b+1 of A_j into the slot freed by row k; those rows are
-//      staged in shared memory 32 steps ahead, so no global load sits on a
-//      step's critical path.
+//      diagonals t and b-1-t are paired (b+1 entries per pair), so the
+//      flattened work is spread evenly over the block and consecutive
+//      threads touch consecutive slots of one diagonal;
+//   3. moves row k+b+1 of A_j into the freed slots; those rows are staged in
+//      shared memory 32 steps ahead, so no global load sits on a step's
+//      critical path.
 // Output layout: L_j column k at l_off + k*bp (bp >= b, entries b..bp-1 are
 // zero), rows k+1..k+b; D^-1 at v_off + k. Rows n..npad-1 are identity
 // padding, so their L columns are zero. A second copy holds the rows of L_j
@@ -27,19 +36,6 @@ namespace rp {
 namespace {
 
 constexpr int kFactorThreads = 256;
-
-template <typename R>
-__device__ __forceinline__ cx<R> aloc_val(const c128* __restrict__ A, const SubDesc& sd, int row, int t) {
-  // entry (row, row - t) of A_j, t in [0, b]; rows >= n are identity
-  if (row >= sd.n) return (t == 0) ? mk((R)1, (R)0) : mk((R)0, (R)0);
-  const c128* a = A + 4 * (sd.v_off + row);
-  c128 v = mk(0.0, 0.0);
-  if (t == 0) v = a[0];
-  if (t == 1) v = v + a[1];
-  if (t == sd.b - 1) v = v + a[2];
-  if (t == sd.b) v = v + a[3];
-  return cvt<R>(v);
-}
 
 // The four stored entries of row `row` of A_j (D, W, S, SW couplings);
 // identity for padding rows.
@@ -75,41 +71,45 @@ __global__ void __launch_bounds__(kFactorThreads)
   extern __shared__ __align__(16) unsigned char sm[];
   const SubDesc sd = subs[blockIdx.x];
   const int tid = threadIdx.x;
-  const int b = sd.b, Wc = b + 1, bp = sd.bp;
+  const int b = sd.b, bp = sd.bp, Wc = b + 1;
+  const int nwin = Wc * (b + 2) / 2;
   const int npairs = b * (b + 1) / 2;
-  cx<R>* W = reinterpret_cast<cx<R>*>(sm);          // W[colslot * Wc + rowslot]
-  cx<R>* cbuf = W + Wc * Wc;
+  cx<R>* W = reinterpret_cast<cx<R>*>(sm);
+  cx<R>* cbuf = W + nwin;
   cx<R>* lbuf = cbuf + Wc;
-  uint16_t* pairs = reinterpret_cast<uint16_t*>(lbuf + Wc);
+  // pos[2][Wc]: {slot of column k on diagonal t, end of diagonal t}, one
+  // copy read during step k, the other written for step k+1
+  int2* pos = reinterpret_cast<int2*>(lbuf + Wc);
   S* L = Lall + sd.l_off;
   S* Lr = Lrev_all + sd.l_off;
   cx<R>* dv = dinv_all + sd.v_off;
 
-  // (i', j') with 1 <= j' <= i' <= b, column by column
-  for (int e = tid; e < npairs; e += blockDim.x) {
-    int j = 1, start = 0;
-    while (start + (b - j + 1) <= e) {
-      start += b - j + 1;
-      ++j;
-    }
-    int i = j + (e - start);
-    pairs[e] = (uint16_t)((i << 8) | j);
+  for (int e = tid; e < nwin; e += blockDim.x) W[e] = mk((R)0, (R)0);
+  if (tid <= b) {
+    const int t = tid, off = t * Wc - t * (t - 1) / 2;
+    pos[t] = make_int2(off, off + Wc - t);
   }
-  for (int e = tid; e < Wc * Wc; e += blockDim.x) W[e] = mk((R)0, (R)0);
   __syncthreads();
-  // rows 0..b of A_j: row r at slot r
+  // rows 0..b of A_j: entry (r, r-t) on diagonal t, column r-t < m_t
   if (tid <= b) {
     const int r = tid;
-    for (int t = 0; t <= b && t <= r; ++t) {
-      cx<R> v = aloc_val<R>(Aloc, sd, r, t);
-      if (v.re != (R)0 || v.im != (R)0) W[(r - t) * Wc + r] = v;
+    cx<R> v[4];
+    aloc_row<R>(Aloc, sd, r, v);
+    const int ts[4] = {0, 1, b - 1, b};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = ts[q];
+      if (t <= r) W[t * Wc - t * (t - 1) / 2 + (r - t)] = row_entry<R>(v, t, b);
     }
   }
-  __syncthreads();
+
+  // this thread's first update entry e = tid: pair p = e / Wc, offset q = e % Wc;
+  // e advances by the block size, (p, q) by (dp, dq) with one carry
+  const int dp = kFactorThreads / Wc, dq = kFactorThreads % Wc;
+  const int p0 = tid / Wc, q0 = tid % Wc;
 
   R dmin2 = (R)3e38, dmax2 = (R)0;
   bool bad = false;
-  int pk = 0;  // slot of row k
   __shared__ cx<R> rows[2][32][4];   // rows entering at the next steps, double-buffered
   if (tid < 128) {
     const int s = tid >> 2, e = tid & 3;
@@ -119,6 +119,8 @@ __global__ void __launch_bounds__(kFactorThreads)
   }
   __syncthreads();
   for (int k = 0; k < sd.npad; ++k) {
+    const int2* pc = pos + (k & 1) * Wc;
+    int2* pn = pos + ((k + 1) & 1) * Wc;
     if ((k & 31) == 0 && tid < 128) {
       // rows entering at steps k+32..k+63; that buffer's last reader was
       // step k-1, which ended at the barrier before this point
@@ -129,10 +131,8 @@ __global__ void __launch_bounds__(kFactorThreads)
     }
     // 1. pivot column
     if (tid <= b) {
-      int s = pk + tid;
-      if (s >= Wc) s -= Wc;
-      cx<R> c = W[pk * Wc + s];
-      cx<R> d = W[pk * Wc + pk];
+      cx<R> c = W[pc[tid].x];
+      cx<R> d = W[pc[0].x];
       cx<R> di = crecip(d);
       cbuf[tid] = c;
       if (tid == 0) {
@@ -151,29 +151,36 @@ __global__ void __launch_bounds__(kFactorThreads)
       }
     }
     __syncthreads();
-    // 2. rank-1 update of the trailing window
-    for (int e = tid; e < npairs; e += blockDim.x) {
-      const int pr = pairs[e];
-      const int i = pr >> 8, j = pr & 255;
-      int si = pk + i;
-      if (si >= Wc) si -= Wc;
-      int sj = pk + j;
-      if (sj >= Wc) sj -= Wc;
-      cx<R>* w = &W[sj * Wc + si];
-      *w = fms(*w, cbuf[i], lbuf[j]);
+    // 2. rank-1 update: pair p covers diagonal p (entries j = 1..b-p) then
+    //    diagonal b-1-p (j = 1..p+1); for odd b the last pair is the middle
+    //    diagonal alone, and e < npairs ends it there
+    {
+      int p = p0, q = q0;
+      for (int e = tid; e < npairs; e += kFactorThreads) {
+        const int l1 = b - p;
+        int t, j;
+        if (q < l1) { t = p; j = q + 1; } else { t = b - 1 - p; j = q - l1 + 1; }
+        const int2 ps = pc[t];
+        int a = ps.x + j;
+        if (a >= ps.y) a -= Wc - t;
+        cx<R>* w = &W[a];
+        *w = fms(*w, cbuf[j + t], lbuf[j]);
+        p += dp;
+        q += dq;
+        if (q >= Wc) { q -= Wc; ++p; }
+      }
     }
-    // 3. row k+b+1 enters slot pk (disjoint from the slots updated above)
+    // 3. row k+b+1 enters the slots of column k (untouched by the update above)
     if (tid <= b) {
       const int t = tid;
-      int sc = pk + (b + 1 - t);  // slot of column k+b+1-t
-      if (sc >= Wc) sc -= Wc;
       cx<R> v[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) v[i] = rows[(k >> 5) & 1][k & 31][i];
-      W[sc * Wc + pk] = row_entry<R>(v, t, b);
+      const int2 ps = pc[t];
+      W[ps.x] = row_entry<R>(v, t, b);
+      pn[t] = make_int2(ps.x + 1 == ps.y ? ps.y - (Wc - t) : ps.x + 1, ps.y);
     }
     __syncthreads();
-    pk = (pk + 1 == Wc) ? 0 : pk + 1;
   }
   if (tid == 0) {
     pivstats[2 * blockIdx.x] = sqrt((double)dmin2);
@@ -184,10 +191,12 @@ __global__ void __launch_bounds__(kFactorThreads)
 
 }  // namespace
 
+int max_band(int prec) { return prec == 0 ? kMaxBandC128 : kMaxBandC64; }
+
 size_t factor_smem_bytes(int b, int prec) {
   size_t es = prec == 0 ? sizeof(c128) : sizeof(c64);   // window in the arithmetic type
   size_t wc = (size_t)b + 1;
-  return wc * wc * es + 2 * wc * es + (size_t)b * (b + 1) / 2 * sizeof(uint16_t);
+  return (wc * (wc + 1) / 2 + 2 * wc) * es + 2 * wc * sizeof(int2);
 }
 
 cudaError_t launch_factor(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,

@@ -7,7 +7,11 @@
 
 namespace rp {
 
-constexpr int kMaxBand = 112;          // largest local half-bandwidth supported
+// largest local half-bandwidth b: the factor window, (b+1)(b+2)/2 entries in
+// the arithmetic type, must fit in shared memory with its buffers
+constexpr int kMaxBandC128 = 160;
+constexpr int kMaxBandC64 = 232;
+int max_band(int prec);
 constexpr int kDotBlocksPerSM = 2;
 
 // Krylov control block in device memory.
