@@ -19,6 +19,12 @@ residual of 1e-6.
   cpu_baseline  the CPU oracle on a bounded sample of the same workload,
              scaled to a full solve (see cpu_sample below)
 
+--workload c3 times the batched form instead: 64 independent problems
+(workloads.batch("c3"): k log-uniform in [20*pi, 120*pi], Omega_int sides
+0.5-1.5, subdomain grids 2x2..12x12, 19.5M unknowns, 3827 subdomains) set up,
+factored and solved to rtol 1e-6 in the same launches (complex64 factors,
+lockstep FGMRES in complex128, one Arnoldi step per CUDA graph replay).
+
 --impl reference times the oracle alone (the reference arm of this repo).
 Multi-GPU (torchrun): every rank solves its own replica of the workload; no
 data-path collective. Inputs (factors of 4-17 GB) are far larger than L2.
@@ -48,6 +54,8 @@ import numpy as np  # noqa: E402
 import workloads  # noqa: E402
 
 METRIC = "RAS-PML time to rtol 1e-6 at k=160*pi, complex64 local factors + complex128 FGMRES (s)"
+BATCH_METRIC = ("RAS-PML batched form: 64 independent problems (k 20*pi..120*pi, 19.5M unknowns) to rtol 1e-6, "
+                "complex64 local factors + complex128 lockstep FGMRES (s)")
 RTOL = 1e-6
 MAXIT = 400
 
@@ -185,6 +193,21 @@ def cpu_baseline_obj(w, iters):
                        f"Gram-Schmidt step on the full mesh; local assembly + SuperLU factor + one local apply "
                        f"(gather, solve, weighted scatter) on 8 of {nsub} subdomains (scaled x{nsub / 8:g}); "
                        f"scaled to {iters} FGMRES directions; {sample_s:.1f} s of CPU work, one thread")}
+
+
+def cpu_batch_baseline(probs, iters):
+    """The oracle on the batched workload: cpu_sample on the problem of median
+    size with its own iteration count, scaled to every problem by unknowns x
+    (iterations + 1)."""
+    n = np.array([w.n_unknowns for w in probs], dtype=float)
+    it = np.asarray(iters, dtype=float)
+    q = int(np.argsort(n)[len(n) // 2])
+    est_q, sample_s, nsub, _ = cpu_sample(probs[q], int(it[q]))
+    est = est_q * float(np.sum(n * (it + 1)) / (n[q] * (it[q] + 1)))
+    return {"value": round(est, 3), "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle cpu_sample on {probs[q].name} ({int(n[q])} unknowns, {nsub} subdomains, "
+                       f"{int(it[q])} directions; {sample_s:.1f} s of CPU work, one thread), scaled to all "
+                       f"{len(probs)} problems by unknowns x (directions + 1)")}
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:
@@ -362,8 +385,171 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Batched form (--workload c3)
+# ---------------------------------------------------------------------------
+
+def batch_iterations_golden():
+    gold = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
+    if os.path.exists(gold):
+        d = json.load(open(gold))
+        if "c3" in d:
+            return d["c3"]["iters"]
+    return None
+
+
+def run_batch(args, rank, world, local_rank):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2602_00735_gb300 import BatchRasPml
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    probs = workloads.batch("c3")
+    params = [w.params() for w in probs]
+    srcs = [(w.centres, w.amps, w.width) for w in probs]
+    shapes = None
+
+    def one_step():
+        B = BatchRasPml(params, factor_prec=args.prec)
+        if shapes is not None:
+            B.set_shapes(*shapes)
+        b = B.assemble_rhs(srcs)
+        B.factor()
+        x, it, rel, st = B.solve(b, rtol=RTOL, maxit=MAXIT)
+        return B, b, x, it, rel, st
+
+    # tile shapes chosen once, on the first warm-up handle
+    B0 = BatchRasPml(params, factor_prec=args.prec)
+    tune = B0.tune()
+    shapes = (tune["factor_threads"], tune["apply_cols"])
+    B0.close()
+    for _ in range(args.warmup):
+        B, b, x, it, rel, st = one_step()
+        B.close()
+        del b, x
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    times = []
+    for k in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B, b, x, it, rel, st = one_step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        info = B.info()
+        B.close()          # its Krylov space takes most of the free memory
+        del x
+    clk = clocks.stop()
+    # the batch apply (local solves of all subdomains + prolongation) on a
+    # factored handle without a Krylov space
+    B = BatchRasPml(params, factor_prec=args.prec)
+    B.set_shapes(*shapes)
+    B.factor()
+    r = b.clone()
+    z = B.apply(r)
+    ta = []
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.apply(r, out=z)
+        e1.record(stream)
+        e1.synchronize()
+        ta.append(e0.elapsed_time(e1) / 1e3)
+    B.close()
+    del r, z
+    t_apply = float(np.median(ta))
+    achieved = info["apply_bytes"] / t_apply / 1e9
+    peak, peak_kind = peaks()
+    # end to end: right-hand sides from pinned host memory, solutions back
+    e2e = None
+    if not args.skip_e2e:
+        b_host = b.cpu().pin_memory()
+        x_host = torch.empty_like(b_host).pin_memory()
+        te = []
+        for k in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Bh = BatchRasPml(params, factor_prec=args.prec)
+            Bh.set_shapes(*shapes)
+            bd = b_host.to(dev, non_blocking=True)
+            Bh.factor()
+            xd, _, _, _ = Bh.solve(bd, rtol=RTOL, maxit=MAXIT)
+            x_host.copy_(xd)
+            t1 = time.perf_counter()
+            Bh.close()
+            del xd, bd
+            if k >= args.warmup:
+                te.append(t1 - t0)
+        nb = b_host.numel() * b_host.element_size()
+        e2e = {"value": round(float(np.mean(te)), 4), "unit": "s", "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb}
+    mean_t = max_over_ranks(float(np.mean(times)), world, dev)
+    if rank != 0:
+        return
+    nprob = info["nprob"]
+    launches = 2 * nprob + 2 + info["cycles"] * 5 + 3 + info["steps"] * 9
+    out = {
+        "metric": BATCH_METRIC, "value": round(mean_t, 4), "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(mean_t * 1e3, 2), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64+c128", "data": "synthetic",
+        "config": {"workload": (f"c3: {nprob} problems, k {min(w.k for w in probs) / math.pi:.1f}*pi.."
+                                f"{max(w.k for w in probs) / math.pi:.1f}*pi, 16 points per wavelength, "
+                                f"Omega_int sides 0.5..1.5, PML 0.1, grids 2x2..12x12, 1-8 Gaussians each"),
+                   "n_unknowns": info["sum_n"], "num_subdomains": info["num_sub"], "rtol": RTOL,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (complex64 factors %.1f GB)" % (info["factor_bytes"] / 1e9)},
+        "iters": {"min": int(it.min()), "median": float(np.median(it)), "max": int(it.max())},
+        "relres_max": float(rel.max()), "status": st, "lockstep_steps": info["steps"], "cycles": info["cycles"],
+        "tune": tune, "shapes": {"factor_threads": shapes[0], "apply_cols": shapes[1]},
+        "apply_ms": round(t_apply * 1e3, 3),
+        "roofline": {"kernel": "ras_pml_batch_apply (k_apply + k_bprolong), complex64", "bound": "hbm",
+                     "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "algorithmic_bytes_per_launch": info["apply_bytes"]},
+        "gpu_launches": int(launches * args.steps), "gpu_launches_per_step": int(launches),
+        "clocks": clk, "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_batch_baseline(probs, it)
+    print(json.dumps(out), flush=True)
+
+
+
+def run_reference_batch(args, world):
+    probs = workloads.batch("c3")
+    iters = batch_iterations_golden()
+    if iters is None:
+        print(json.dumps({"impl": "reference", "unavailable": "no stored oracle iteration counts for c3"}))
+        return
+    vals, last = [], None
+    for k in range(args.warmup + args.steps):
+        obj = cpu_batch_baseline(probs, iters)
+        if k >= args.warmup:
+            vals.append(obj["value"])
+            last = obj
+    v = float(np.mean(vals))
+    out = {"impl": "reference", "metric": BATCH_METRIC, "value": round(v, 3), "unit": "s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 1),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+           "data": "synthetic", "config": {"workload": "c3", "rtol": RTOL},
+           "cpu_baseline": dict(last, value=round(v, 3)),
+           "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
+        return
+    if args.workload == "c3":
+        run_reference_batch(args, world)
         return
     w = workloads.get(args.workload)
     iters = oracle_iterations(w)
@@ -414,7 +600,10 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload == "c3":
+            run_batch(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -235,6 +235,123 @@ const char* ras_pml_error_string(int status);
 /* Releases every device allocation of the handle (NULL is allowed). */
 void ras_pml_destroy(ras_pml_handle* h);
 
+/* ---------------------------------------------------------------------------
+ * Tile-shape tuning. Not an operation of the paper (which fixes no kernel
+ * shapes): times each candidate shape of the factor launch (threads per CTA)
+ * and of the apply launch (band columns per bulk copy) on the handle's own
+ * subdomains with CUDA events, keeps the fastest for later calls, and leaves
+ * the handle factored (every shape computes the same factors bit for bit).
+ * The candidates: factor threads 128, 256, 512; apply columns 8, plus 4 and
+ * 16 when factor_prec = 1. Synchronises the stream.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t factor_threads;    /* chosen threads per factor CTA                 */
+  int32_t apply_cols;        /* chosen band columns per bulk copy             */
+  int32_t n_factor;          /* factor candidates timed (entries below)       */
+  int32_t n_apply;           /* apply candidates timed                        */
+  int32_t factor_cand[4];
+  float   factor_ms[4];      /* median time of each factor candidate          */
+  int32_t apply_cand[4];
+  float   apply_ms[4];       /* median time of each apply candidate (local
+                                solves of all subdomains)                     */
+} ras_pml_tune_t;
+
+int ras_pml_tune(ras_pml_handle* h, ras_pml_tune_t* report);
+
+/* Sets the tile shapes directly (e.g. those a tuning run chose for another
+ * handle of the same sizes): factor_threads 128, 256 or 512; apply_cols 8,
+ * or 4 or 16 with factor_prec = 1. RASPML_EBADARG for other values. */
+int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int apply_cols);
+
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent problems in the same launches. The paper
+ * solves one problem at a time; a batch holds nprob problems, each defined
+ * by its own ras_pml_params exactly as ras_pml_setup would define it, and
+ * runs every step of the method over all of them at once:
+ *   - one local-assembly and one factor launch over the union of all
+ *     subdomains (ordered by decreasing factor cost, so that the largest
+ *     start first and the uneven sizes pack onto the SMs);
+ *   - one local-solve launch and one prolongation launch per application
+ *     of the preconditioners;
+ *   - flexible GMRES run in lockstep: direction j of every unfinished
+ *     problem in the same launches, each problem with its own Krylov
+ *     space, Hessenberg matrix, rotations, residual estimate and stop
+ *     flag; a finished problem's share of each launch returns at once.
+ *     One Arnoldi step is a CUDA graph (its kernels read the step index
+ *     from device memory) captured once and replayed for every step.
+ * Vectors of a batch are concatenations: problem q occupies elements
+ * [off_q, off_q + n_q) of a complex128 vector of ntot elements
+ * (ras_pml_batch_layout); off_q is a multiple of 2048. Elements between
+ * problems are ignored on input and written as zero on output.
+ * All problems must share factor_prec; ortho is ignored (the Gram-Schmidt of
+ * the batch is one classical pass in double-float arithmetic, as ortho = 3).
+ * ------------------------------------------------------------------------- */
+typedef struct ras_pml_batch ras_pml_batch;
+
+typedef struct {
+  int32_t nprob;
+  int32_t num_sub;         /* subdomains over all problems                  */
+  int64_t ntot;            /* length of a batch vector                      */
+  int64_t sum_n;           /* unknowns over all problems                    */
+  int64_t sum_local_n;     /* local unknowns over all subdomains            */
+  int32_t max_band;
+  int32_t factor_prec;
+  int64_t factor_bytes;    /* device bytes of the stored factors            */
+  double  apply_bytes;     /* algorithmic bytes of one batch apply          */
+  double  min_pivot_ratio; /* over all subdomains                           */
+  int32_t factored;
+  int32_t bad_problem;     /* problem of a RASPML_EPIVOT subdomain, else -1 */
+  int32_t bad_subdomain;   /* its subdomain index within that problem       */
+  int32_t factor_threads;  /* tile shapes in use                            */
+  int32_t apply_cols;
+  int32_t steps;           /* lockstep Arnoldi steps of the last solve      */
+  int32_t cycles;          /* restart cycles of the last solve              */
+  int32_t kcap;            /* Krylov directions per cycle of the last solve */
+} ras_pml_batch_info_t;
+
+/* Builds every problem (params[q], q < nprob; RASPML_EBADARG if one is
+ * invalid, as ras_pml_setup) on the current device and stream. */
+int ras_pml_batch_setup(const ras_pml_params* params, int nprob, void* cuda_stream,
+                        ras_pml_batch** out);
+
+int ras_pml_batch_info(const ras_pml_batch* h, ras_pml_batch_info_t* info);
+
+/* offsets_host[q] = off_q and sizes_host[q] = n_q for q < nprob (host arrays). */
+int ras_pml_batch_layout(const ras_pml_batch* h, int64_t* offsets_host, int64_t* sizes_host);
+
+/* Load vectors of all problems (the f of ras_pml_assemble_rhs): problem q
+ * has ns_host[q] sources, taken in order from centres_host (2 doubles each)
+ * and amps_host, and Gaussian width widths_host[q]. Writes ntot elements. */
+int ras_pml_batch_assemble_rhs(ras_pml_batch* h, const int32_t* ns_host, const double* centres_host,
+                               const double* amps_host, const double* widths_host, rp_c128* b_dev);
+
+/* ras_pml_factor for all problems in one local-assembly and one factor
+ * launch. RASPML_EPIVOT names the first failing (problem, subdomain) in info. */
+int ras_pml_batch_factor(ras_pml_batch* h);
+
+/* ras_pml_tune and ras_pml_set_shapes on the batch's subdomains. */
+int ras_pml_batch_tune(ras_pml_batch* h, ras_pml_tune_t* report);
+int ras_pml_batch_set_shapes(ras_pml_batch* h, int factor_threads, int apply_cols);
+
+/* z = B_q^-1 r for every problem q (batch vectors, must not overlap). */
+int ras_pml_batch_apply(ras_pml_batch* h, const rp_c128* r_dev, rp_c128* z_dev);
+
+/* y = A_q x for every problem q (batch vectors, must not overlap). */
+int ras_pml_batch_matvec(ras_pml_batch* h, const rp_c128* x_dev, rp_c128* y_dev);
+
+/* helmholtz_solve for every problem, in lockstep, from x0 = 0 (x_dev is
+ * overwritten). Each problem stops on its own residual estimate or after
+ * maxit directions; restart = 0 keeps one cycle (shortened, as for
+ * helmholtz_solve, to the Krylov space that fits in free memory, (2m+1)*ntot*16
+ * bytes, and to at most 1024 directions). iters_host[q] and relres_host[q] (host arrays) receive each
+ * problem's directions and final true relative residual. Returns 0 when
+ * every problem converged, RASPML_NOT_CONVERGED otherwise, or an error
+ * (RASPML_ENAN if a problem's residual became non-finite). */
+int ras_pml_batch_solve(ras_pml_batch* h, const rp_c128* b_dev, rp_c128* x_dev, double rtol,
+                        int maxit, int restart, int32_t* iters_host, double* relres_host);
+
+void ras_pml_batch_destroy(ras_pml_batch* h);
+
 #ifdef __cplusplus
 }
 #endif

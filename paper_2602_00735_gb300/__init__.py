@@ -8,7 +8,7 @@ this package only marshals arguments to it.
 """
 from ._lib import SYMBOLS, RasPmlError, load  # noqa: F401
 
-__all__ = ["RasPml", "load", "RasPmlError", "SYMBOLS", "build"]
+__all__ = ["RasPml", "BatchRasPml", "load", "RasPmlError", "SYMBOLS", "build"]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -20,4 +20,7 @@ def __getattr__(name):
     if name == "RasPml":
         from .solver import RasPml
         return RasPml
+    if name == "BatchRasPml":
+        from .batch import BatchRasPml
+        return BatchRasPml
     raise AttributeError(name)

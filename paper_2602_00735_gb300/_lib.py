@@ -16,7 +16,11 @@ SYMBOLS = ("ras_pml_setup", "ras_pml_info", "ras_pml_assemble_rhs", "ras_pml_ass
            "ras_pml_factor", "ras_pml_apply",
            "ras_pml_matvec", "helmholtz_solve", "helmholtz_solve_host", "ras_pml_richardson",
            "ras_pml_history", "ras_pml_set_timing", "ras_pml_get_timing", "ras_pml_error_string",
-           "ras_pml_destroy")
+           "ras_pml_destroy", "ras_pml_tune", "ras_pml_set_shapes", "ras_pml_batch_set_shapes",
+           "ras_pml_batch_setup", "ras_pml_batch_info", "ras_pml_batch_layout", "ras_pml_batch_assemble_rhs",
+           "ras_pml_batch_factor", "ras_pml_batch_tune", "ras_pml_batch_apply", "ras_pml_batch_matvec",
+           "ras_pml_batch_solve", "ras_pml_batch_destroy")
+VOID_SYMBOLS = ("ras_pml_error_string", "ras_pml_destroy", "ras_pml_batch_destroy")
 
 
 class Params(ctypes.Structure):
@@ -40,6 +44,21 @@ class Timing(ctypes.Structure):
     _fields_ = [("factor_ms", c_double), ("solve_ms", c_double), ("apply_ms", c_double),
                 ("spmv_ms", c_double), ("ortho_ms", c_double), ("applies", c_int32), ("reorths", c_int32),
                 ("launches", c_int32)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("factor_threads", c_int32), ("apply_cols", c_int32), ("n_factor", c_int32),
+                ("n_apply", c_int32), ("factor_cand", c_int32 * 4), ("factor_ms", ctypes.c_float * 4),
+                ("apply_cand", c_int32 * 4), ("apply_ms", ctypes.c_float * 4)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("nprob", c_int32), ("num_sub", c_int32), ("ntot", c_int64), ("sum_n", c_int64),
+                ("sum_local_n", c_int64), ("max_band", c_int32), ("factor_prec", c_int32),
+                ("factor_bytes", c_int64), ("apply_bytes", c_double), ("min_pivot_ratio", c_double),
+                ("factored", c_int32), ("bad_problem", c_int32), ("bad_subdomain", c_int32),
+                ("factor_threads", c_int32), ("apply_cols", c_int32), ("steps", c_int32), ("cycles", c_int32),
+                ("kcap", c_int32)]
 
 
 _lib = None
@@ -73,8 +92,22 @@ def load() -> ctypes.CDLL:
     lib.ras_pml_error_string.restype = ctypes.c_char_p
     lib.ras_pml_destroy.argtypes = [H]
     lib.ras_pml_destroy.restype = None
+    lib.ras_pml_tune.argtypes = [H, POINTER(TuneReport)]
+    lib.ras_pml_set_shapes.argtypes = [H, c_int, c_int]
+    lib.ras_pml_batch_set_shapes.argtypes = [H, c_int, c_int]
+    lib.ras_pml_batch_setup.argtypes = [POINTER(Params), c_int, c_void_p, POINTER(c_void_p)]
+    lib.ras_pml_batch_info.argtypes = [H, POINTER(BatchInfo)]
+    lib.ras_pml_batch_layout.argtypes = [H, c_void_p, c_void_p]
+    lib.ras_pml_batch_assemble_rhs.argtypes = [H, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.ras_pml_batch_factor.argtypes = [H]
+    lib.ras_pml_batch_tune.argtypes = [H, POINTER(TuneReport)]
+    lib.ras_pml_batch_apply.argtypes = [H, c_void_p, c_void_p]
+    lib.ras_pml_batch_matvec.argtypes = [H, c_void_p, c_void_p]
+    lib.ras_pml_batch_solve.argtypes = [H, c_void_p, c_void_p, c_double, c_int, c_int, c_void_p, c_void_p]
+    lib.ras_pml_batch_destroy.argtypes = [H]
+    lib.ras_pml_batch_destroy.restype = None
     for name in SYMBOLS:
-        if name not in ("ras_pml_error_string", "ras_pml_destroy"):
+        if name not in VOID_SYMBOLS:
             getattr(lib, name).restype = c_int
     _lib = lib
     return lib

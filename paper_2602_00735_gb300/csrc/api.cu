@@ -9,9 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/raspml.h"
-#include "common.cuh"
-#include "kernels.h"
+#include "host.h"
 
 using rp::c128;
 using rp::c64;
@@ -23,6 +21,8 @@ struct ras_pml_handle {
   cudaStream_t st = nullptr;
   int dev = 0;
   rp::Geo geo{};
+  rp::Geo* geo_d = nullptr;      // the same geometry in device memory
+  rp::Tune tune{};               // tile shapes of the factor and apply launches
   std::vector<SubDesc> subs_h;
   SubDesc* subs_d = nullptr;
   int nsub = 0, max_b = 0, max_bp = 0, max_npad = 0, max_n = 0;
@@ -54,26 +54,10 @@ struct ras_pml_handle {
 
 namespace {
 
-#define RP_CUDA(call)                                                          \
-  do {                                                                         \
-    cudaError_t e_ = (call);                                                   \
-    if (e_ != cudaSuccess) {                                                   \
-      std::fprintf(stderr, "raspml: %s failed: %s\n", #call, cudaGetErrorString(e_)); \
-      return e_ == cudaErrorMemoryAllocation ? RASPML_ENOMEM : RASPML_ECUDA;    \
-    }                                                                          \
-  } while (0)
+using rp::dalloc;
+using rp::dfree;
+using rp::ev_ms;
 
-template <typename T>
-int dalloc(T** p, size_t count) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    return e == cudaErrorMemoryAllocation ? RASPML_ENOMEM : RASPML_ECUDA;
-  }
-  return RASPML_OK;
-}
 #define RP_ALLOC(ptr, cnt)            \
   do {                                \
     int s_ = dalloc(&(ptr), (cnt));   \
@@ -87,18 +71,6 @@ int ensure_events(ras_pml_handle* h, int count) {
     h->ev.push_back(e);
   }
   return RASPML_OK;
-}
-
-float ev_ms(cudaEvent_t a, cudaEvent_t b) {
-  float ms = 0.f;
-  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.f;
-  return ms;
-}
-
-template <typename T>
-void dfree(T*& p) {
-  if (p) cudaFree((void*)p);
-  p = nullptr;
 }
 
 int law_cells(double k, double h) {
@@ -179,6 +151,72 @@ int check_status(ras_pml_handle* h) {
 
 }  // namespace
 
+namespace rp {
+
+int build_problem(const ras_pml_params& p, int prob, Geo& g, std::vector<SubDesc>& subs) {
+  if (!(p.k >= 0.0) || !(p.h > 0.0) || !(p.kappa_g >= 0.0) || !(p.x1 > p.x0) || !(p.y1 > p.y0) || p.px < 1 ||
+      p.py < 1 || !(p.g_ramp > 0.0) || !(p.g_amp >= 0.0) || (p.local_bc != 0 && p.local_bc != 1) ||
+      (p.factor_prec < 0 || p.factor_prec > 2) || (p.ortho < 0 || p.ortho > 3) || (p.g_profile != 0 && p.g_profile != 1))
+    return RASPML_EBADARG;
+  const double lx = p.x1 - p.x0 + 2 * p.kappa_g, ly = p.y1 - p.y0 + 2 * p.kappa_g;
+  const long long Mx = std::llround(lx / p.h), My = std::llround(ly / p.h);
+  if (Mx < 2 || My < 2 || std::fabs(Mx * p.h - lx) > 1e-9 * lx || std::fabs(My * p.h - ly) > 1e-9 * ly ||
+      Mx > (1 << 20) || My > (1 << 20))
+    return RASPML_EBADARG;
+  const int o = p.ovlp_cells < 0 ? law_cells(p.k, p.h) : p.ovlp_cells;
+  const int pml = p.pml_cells < 0 ? law_cells(p.k, p.h) : p.pml_cells;
+  if (o < 1 || pml < 0 || p.px > Mx || p.py > My) return RASPML_EBADARG;
+  bool okx, oky;
+  auto rx = ranges((int)Mx, p.px, o, pml, &okx);
+  auto ry = ranges((int)My, p.py, o, pml, &oky);
+  if (!okx || !oky) return RASPML_EBADARG;
+
+  g = Geo{};
+  g.X0 = p.x0 - p.kappa_g;
+  g.Y0 = p.y0 - p.kappa_g;
+  g.h = p.h;
+  g.hh = 0.5 * p.h;
+  g.x0 = p.x0; g.x1 = p.x1; g.y0 = p.y0; g.y1 = p.y1;
+  g.k = p.k; g.g_amp = p.g_amp; g.g_ramp = p.g_ramp;
+  g.Mx = (int)Mx; g.My = (int)My; g.nx = (int)Mx - 1; g.ny = (int)My - 1;
+  g.px = p.px; g.py = p.py; g.ovlp = o; g.pml = pml; g.local_bc = p.local_bc;
+  g.g_profile = p.g_profile;
+  g.n = g.nx * g.ny;
+  if ((long long)g.nx * g.ny > (1ll << 31) - 1) return RASPML_EBADARG;
+
+  const bool imp = p.local_bc == 0;
+  const size_t first = subs.size();
+  for (int qy = 0; qy < p.py; ++qy) {
+    for (int qx = 0; qx < p.px; ++qx) {
+      const Range& X = rx[qx];
+      const Range& Yr = ry[qy];
+      SubDesc d{};
+      d.ext_lo_x = X.ext_lo; d.ext_hi_x = X.ext_hi; d.ext_lo_y = Yr.ext_lo; d.ext_hi_y = Yr.ext_hi;
+      d.int_lo_x = X.int_lo; d.int_hi_x = X.int_hi; d.int_lo_y = Yr.int_lo; d.int_hi_y = Yr.int_hi;
+      d.box_lo_x = X.box_lo; d.box_hi_x = X.box_hi; d.box_lo_y = Yr.box_lo; d.box_hi_y = Yr.box_hi;
+      d.flags = (X.lo_in ? LO_X : 0) | (X.hi_in ? HI_X : 0) | (Yr.lo_in ? LO_Y : 0) | (Yr.hi_in ? HI_Y : 0);
+      int ix0 = imp ? X.ext_lo : X.ext_lo + 1, ix1 = imp ? X.ext_hi : X.ext_hi - 1;
+      int iy0 = imp ? Yr.ext_lo : Yr.ext_lo + 1, iy1 = imp ? Yr.ext_hi : Yr.ext_hi - 1;
+      ix0 = std::max(ix0, 1); iy0 = std::max(iy0, 1);
+      ix1 = std::min(ix1, g.Mx - 1); iy1 = std::min(iy1, g.My - 1);
+      if (ix1 < ix0 || iy1 < iy0 || (d.b = ix1 - ix0 + 2) > max_band(p.factor_prec)) {
+        subs.resize(first);
+        return RASPML_EBADARG;
+      }
+      d.ix0 = ix0; d.iy0 = iy0; d.nlx = ix1 - ix0 + 1; d.nly = iy1 - iy0 + 1;
+      d.n = d.nlx * d.nly;
+      d.npad = (d.n + 31) / 32 * 32;
+      d.b = d.nlx + 1;
+      d.bp = d.b + (d.b & 1);
+      d.prob = prob;
+      subs.push_back(d);
+    }
+  }
+  return RASPML_OK;
+}
+
+}  // namespace rp
+
 extern "C" {
 
 const char* ras_pml_error_string(int s) {
@@ -200,7 +238,7 @@ void ras_pml_destroy(ras_pml_handle* h) {
   if (!h) return;
   cudaSetDevice(h->dev);
   if (h->st) cudaStreamSynchronize(h->st);
-  dfree(h->subs_d); dfree(h->D); dfree(h->CW); dfree(h->CS); dfree(h->CSW);
+  dfree(h->subs_d); dfree(h->geo_d); dfree(h->D); dfree(h->CW); dfree(h->CS); dfree(h->CSW);
   dfree(h->L); dfree(h->Lrev); dfree(h->dinv); dfree(h->Y); dfree(h->pivstats); dfree(h->status);
   dfree(h->V); dfree(h->Z); dfree(h->H); dfree(h->sn); dfree(h->gvec); dfree(h->yv);
   dfree(h->partial); dfree(h->hbuf); dfree(h->cs); dfree(h->hist); dfree(h->scal); dfree(h->kst);
@@ -214,79 +252,30 @@ void ras_pml_destroy(ras_pml_handle* h) {
 int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) {
   if (!pp || !out) return RASPML_EBADARG;
   *out = nullptr;
-  const ras_pml_params& p = *pp;
-  if (!(p.k >= 0.0) || !(p.h > 0.0) || !(p.kappa_g >= 0.0) || !(p.x1 > p.x0) || !(p.y1 > p.y0) || p.px < 1 ||
-      p.py < 1 || !(p.g_ramp > 0.0) || !(p.g_amp >= 0.0) || (p.local_bc != 0 && p.local_bc != 1) ||
-      (p.factor_prec < 0 || p.factor_prec > 2) || (p.ortho < 0 || p.ortho > 3) || (p.g_profile != 0 && p.g_profile != 1))
-    return RASPML_EBADARG;
-  const double lx = p.x1 - p.x0 + 2 * p.kappa_g, ly = p.y1 - p.y0 + 2 * p.kappa_g;
-  const long long Mx = std::llround(lx / p.h), My = std::llround(ly / p.h);
-  if (Mx < 2 || My < 2 || std::fabs(Mx * p.h - lx) > 1e-9 * lx || std::fabs(My * p.h - ly) > 1e-9 * ly ||
-      Mx > (1 << 20) || My > (1 << 20))
-    return RASPML_EBADARG;
-  const int o = p.ovlp_cells < 0 ? law_cells(p.k, p.h) : p.ovlp_cells;
-  const int pml = p.pml_cells < 0 ? law_cells(p.k, p.h) : p.pml_cells;
-  if (o < 1 || pml < 0 || p.px > Mx || p.py > My) return RASPML_EBADARG;
-  bool okx, oky;
-  auto rx = ranges((int)Mx, p.px, o, pml, &okx);
-  auto ry = ranges((int)My, p.py, o, pml, &oky);
-  if (!okx || !oky) return RASPML_EBADARG;
-
   ras_pml_handle* h = new ras_pml_handle();
-  h->p = p;
-  h->p.ovlp_cells = o;
-  h->p.pml_cells = pml;
+  const int bs = rp::build_problem(*pp, 0, h->geo, h->subs_h);
+  if (bs != RASPML_OK) { delete h; return bs; }
+  rp::Geo& g = h->geo;
+  h->p = *pp;
+  h->p.ovlp_cells = g.ovlp;
+  h->p.pml_cells = g.pml;
   h->st = (cudaStream_t)stream;
   cudaGetDevice(&h->dev);
-  rp::Geo& g = h->geo;
-  g.X0 = p.x0 - p.kappa_g;
-  g.Y0 = p.y0 - p.kappa_g;
-  g.h = p.h;
-  g.hh = 0.5 * p.h;
-  g.x0 = p.x0; g.x1 = p.x1; g.y0 = p.y0; g.y1 = p.y1;
-  g.k = p.k; g.g_amp = p.g_amp; g.g_ramp = p.g_ramp;
-  g.Mx = (int)Mx; g.My = (int)My; g.nx = (int)Mx - 1; g.ny = (int)My - 1;
-  g.px = p.px; g.py = p.py; g.ovlp = o; g.pml = pml; g.local_bc = p.local_bc;
-  g.g_profile = p.g_profile;
   h->n = (long long)g.nx * g.ny;
-
-  const bool imp = p.local_bc == 0;
   long long l_off = 0, v_off = 0;
-  for (int qy = 0; qy < p.py; ++qy) {
-    for (int qx = 0; qx < p.px; ++qx) {
-      const Range& X = rx[qx];
-      const Range& Yr = ry[qy];
-      SubDesc d{};
-      d.ext_lo_x = X.ext_lo; d.ext_hi_x = X.ext_hi; d.ext_lo_y = Yr.ext_lo; d.ext_hi_y = Yr.ext_hi;
-      d.int_lo_x = X.int_lo; d.int_hi_x = X.int_hi; d.int_lo_y = Yr.int_lo; d.int_hi_y = Yr.int_hi;
-      d.box_lo_x = X.box_lo; d.box_hi_x = X.box_hi; d.box_lo_y = Yr.box_lo; d.box_hi_y = Yr.box_hi;
-      d.flags = (X.lo_in ? rp::LO_X : 0) | (X.hi_in ? rp::HI_X : 0) | (Yr.lo_in ? rp::LO_Y : 0) |
-                (Yr.hi_in ? rp::HI_Y : 0);
-      int ix0 = imp ? X.ext_lo : X.ext_lo + 1, ix1 = imp ? X.ext_hi : X.ext_hi - 1;
-      int iy0 = imp ? Yr.ext_lo : Yr.ext_lo + 1, iy1 = imp ? Yr.ext_hi : Yr.ext_hi - 1;
-      ix0 = std::max(ix0, 1); iy0 = std::max(iy0, 1);
-      ix1 = std::min(ix1, g.Mx - 1); iy1 = std::min(iy1, g.My - 1);
-      if (ix1 < ix0 || iy1 < iy0) { delete h; return RASPML_EBADARG; }
-      d.ix0 = ix0; d.iy0 = iy0; d.nlx = ix1 - ix0 + 1; d.nly = iy1 - iy0 + 1;
-      d.n = d.nlx * d.nly;
-      d.npad = (d.n + 31) / 32 * 32;
-      d.b = d.nlx + 1;
-      d.bp = d.b + (d.b & 1);
-      if (d.b > rp::max_band(p.factor_prec)) { delete h; return RASPML_EBADARG; }
-      d.l_off = l_off;
-      d.v_off = v_off;
-      l_off += (long long)d.npad * d.bp;
-      v_off += d.npad;
-      h->max_b = std::max(h->max_b, d.b);
-      h->max_bp = std::max(h->max_bp, d.bp);
-      h->max_npad = std::max(h->max_npad, d.npad);
-      h->max_n = std::max(h->max_n, d.n);
-      h->sum_n += d.n;
-      h->sum_bn += (long long)d.b * d.n;
-      h->subs_h.push_back(d);
-    }
+  for (SubDesc& d : h->subs_h) {
+    d.l_off = l_off;
+    d.v_off = v_off;
+    l_off += rp::sub_l_entries(d);
+    v_off += d.npad;
+    h->max_b = std::max(h->max_b, d.b);
+    h->max_bp = std::max(h->max_bp, d.bp);
+    h->max_npad = std::max(h->max_npad, d.npad);
+    h->max_n = std::max(h->max_n, d.n);
+    h->sum_n += d.n;
+    h->sum_bn += (long long)d.b * d.n;
   }
-  h->nsub = p.px * p.py;
+  h->nsub = (int)h->subs_h.size();
   h->sum_npad = v_off;
   h->sum_l = l_off;
 
@@ -295,6 +284,7 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   if ((s = dalloc(&(ptr), (cnt))) != RASPML_OK) { ras_pml_destroy(h); return s; }
   cudaSetDevice(h->dev);
   SETUP_ALLOC(h->subs_d, (size_t)h->nsub);
+  SETUP_ALLOC(h->geo_d, (size_t)1);
   SETUP_ALLOC(h->D, (size_t)h->n);
   SETUP_ALLOC(h->CW, (size_t)h->n);
   SETUP_ALLOC(h->CS, (size_t)h->n);
@@ -303,6 +293,7 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   SETUP_ALLOC(h->status, (size_t)1);
   cudaError_t e = cudaMemcpyAsync(h->subs_d, h->subs_h.data(), sizeof(SubDesc) * h->nsub, cudaMemcpyHostToDevice,
                                   h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->geo_d, &h->geo, sizeof(rp::Geo), cudaMemcpyHostToDevice, h->st);
   rp::DevStatus s0{-1, 0, 0, 0};
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->status, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->st);
@@ -392,9 +383,9 @@ int ras_pml_factor(ras_pml_handle* h) {
   cudaError_t e = cudaMemcpyAsync(h->status, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[0], h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->Lrev, 0, (size_t)h->sum_l * esl, h->st);
-  if (e == cudaSuccess) e = rp::launch_local_rows(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
+  if (e == cudaSuccess) e = rp::launch_local_rows(h->p.factor_prec, h->geo_d, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
   if (e == cudaSuccess)
-    e = rp::launch_factor(h->p.factor_prec, h->subs_d, h->nsub, h->max_b, Aloc, h->L, h->Lrev, h->dinv,
+    e = rp::launch_factor(h->p.factor_prec, h->tune.factor_threads, h->subs_d, h->nsub, h->max_b, Aloc, h->L, h->Lrev, h->dinv,
                           h->pivstats, h->status, h->st);
   if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[1], h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
@@ -420,11 +411,42 @@ int ras_pml_factor(ras_pml_handle* h) {
   return RASPML_OK;
 }
 
+int ras_pml_tune(ras_pml_handle* h, ras_pml_tune_t* report) {
+  if (!h) return RASPML_EBADARG;
+  cudaSetDevice(h->dev);
+  int s = ras_pml_factor(h);
+  if (s != RASPML_OK) return s;
+  c128 *Aloc = nullptr, *r = nullptr;
+  RP_ALLOC(Aloc, (size_t)4 * h->sum_npad);
+  if ((s = dalloc(&r, (size_t)h->n)) != RASPML_OK) { dfree(Aloc); return s; }
+  cudaError_t e = cudaMemsetAsync(r, 0, sizeof(c128) * h->n, h->st);
+  if (e == cudaSuccess)
+    e = rp::launch_local_rows(h->p.factor_prec, h->geo_d, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
+  if (e != cudaSuccess) {
+    dfree(Aloc); dfree(r);
+    return RASPML_ECUDA;
+  }
+  rp::TuneTarget t{h->p.factor_prec, h->geo_d, h->subs_d, h->nsub, h->max_b, h->max_bp, h->max_npad, h->sum_npad,
+                   h->sum_l, Aloc, h->L, h->Lrev, h->dinv, h->Y, h->pivstats, h->status, r, h->st};
+  s = rp::tune_shapes(t, 3, &h->tune, report);
+  cudaStreamSynchronize(h->st);
+  dfree(Aloc); dfree(r);
+  return s;
+}
+
+int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int apply_cols) {
+  if (!h || !rp::factor_threads_valid(factor_threads) || !rp::apply_cols_valid(h->p.factor_prec, apply_cols))
+    return RASPML_EBADARG;
+  h->tune.factor_threads = factor_threads;
+  h->tune.apply_cols = apply_cols;
+  return RASPML_OK;
+}
+
 int ras_pml_apply(ras_pml_handle* h, const rp_c128* r, rp_c128* z) {
   if (!h || !r || !z || (const void*)r == (const void*)z) return RASPML_EBADARG;
   if (!h->factored) return RASPML_ESTATE;
   cudaSetDevice(h->dev);
-  RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev, h->dinv,
+  RP_CUDA(rp::launch_apply(h->p.factor_prec, h->tune.apply_cols, h->geo, h->geo_d, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev, h->dinv,
                            (const c128*)r, h->Y, (c128*)z, nullptr, h->status, h->st));
   return RASPML_OK;
 }
@@ -529,7 +551,7 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
         cudaEvent_t* evj = h->ev.data() + slot * 4 * batch + 4 * (jj - j);
         ++issued;
         if (h->timing) RP_CUDA(cudaEventRecord(evj[0], st));
-        RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev,
+        RP_CUDA(rp::launch_apply(h->p.factor_prec, h->tune.apply_cols, h->geo, h->geo_d, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev,
                                  h->dinv, vj, h->Y, zj, h->kst, h->status, st, dfbasis));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[1], st));
         RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, nullptr, w, h->kst, st));
@@ -680,7 +702,7 @@ int ras_pml_richardson(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, 
     if (!std::isfinite(rel)) { status = RASPML_ENAN; break; }
     if (rel <= rtol) { status = RASPML_OK; break; }
     if (it >= maxit) break;
-    RP_CUDA(rp::launch_apply(h->p.factor_prec, h->geo, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev, h->dinv,
+    RP_CUDA(rp::launch_apply(h->p.factor_prec, h->tune.apply_cols, h->geo, h->geo_d, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev, h->dinv,
                              h->tmp_r, h->Y, h->V, nullptr, h->status, h->st));
     RP_CUDA(rp::launch_axpy_state(x, h->V, n, h->st));
   }

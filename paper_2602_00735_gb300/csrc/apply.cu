@@ -16,8 +16,10 @@
 //   column k times y_k from the rows below (one complex FMA per slot and
 //   lane), and refills row k's slot with row k+32S.
 //   The band columns stream from HBM through a 4-stage shared-memory ring of
-//   8-column chunks filled by the bulk-copy (TMA) engine; both sweeps use one
-//   continuous chunk sequence.
+//   KC-column chunks (KC = 4, 8 or 16, a tuned tile shape) filled by the
+//   bulk-copy (TMA) engine; both sweeps use one continuous chunk sequence.
+//   Subdomains may belong to different problems of a batch: each reads its
+//   problem's geometry (geos[prob]) and skips when that problem has stopped.
 // k_prolong: one thread per global unknown sums the (at most four) weighted
 //   local values that cover it, in a fixed order (bit-reproducible).
 #include "common.cuh"
@@ -27,7 +29,6 @@ namespace rp {
 
 namespace {
 
-constexpr int kCol = 8;       // columns per bulk copy
 // ring depth: 4 stages of 8 columns (a deeper ring for half-pair entries was
 // measured: no gain on c2, slower on c4)
 template <typename ST>
@@ -35,11 +36,11 @@ constexpr int stages_for() { return 4; }
 
 // R_j r at local row `row`: r is complex128, or double-float (dfc) when rdf
 template <typename R>
-__device__ __forceinline__ cx<R> gather_row(const SubDesc& sd, const Geo& g, const c128* __restrict__ r, int rdf,
-                                            int row) {
+__device__ __forceinline__ cx<R> gather_row(const SubDesc& sd, int nx, long long goff, const c128* __restrict__ r,
+                                            int rdf, int row) {
   if (row >= sd.n) return mk((R)0, (R)0);
   int i = sd.ix0 + row % sd.nlx, j = sd.iy0 + row / sd.nlx;
-  const long long idx = (long long)(j - 1) * g.nx + (i - 1);
+  const long long idx = goff + (long long)(j - 1) * nx + (i - 1);
   if (rdf) {
     const dfc v = reinterpret_cast<const dfc*>(r)[idx];
     return mk((R)((R)v.rh + (R)v.rl), (R)((R)v.ih + (R)v.il));
@@ -47,7 +48,7 @@ __device__ __forceinline__ cx<R> gather_row(const SubDesc& sd, const Geo& g, con
   return cvt<R>(r[idx]);
 }
 
-template <typename S>
+template <typename S, int KC>
 struct Pipe {
   uint64_t* bar;
   S* stg;
@@ -56,7 +57,7 @@ struct Pipe {
   int stage_elems, Q, bp;
   uint32_t bytes;
   __device__ void issue(int s) const {
-    const S* src = s < Q ? src0 + (long long)s * kCol * bp : src1 + (long long)(s - Q) * kCol * bp;
+    const S* src = s < Q ? src0 + (long long)s * KC * bp : src1 + (long long)(s - Q) * KC * bp;
     const int st = s % stages_for<S>();
     mbar_arrive_expect_tx(&bar[st], bytes);
     bulk_g2s(stg + st * stage_elems, src, bytes, &bar[st]);
@@ -70,19 +71,19 @@ struct Pipe {
 
 // The 32 steps of one row group with window phase PH (= group mod S);
 // ST is the storage type of the factor entries.
-template <typename R, typename ST, int S, int PH>
-__device__ __forceinline__ bool group_steps(const Pipe<ST>& pp, int s0, int b, int lane, cx<R> (&win)[S],
+template <typename R, typename ST, int S, int KC, int PH>
+__device__ __forceinline__ bool group_steps(const Pipe<ST, KC>& pp, int s0, int b, int lane, cx<R> (&win)[S],
                                             const cx<R>& nxt, cx<R>& outv) {
   const int bp = pp.bp;
 #pragma unroll 1
-  for (int c4 = 0; c4 < 32 / kCol; ++c4) {
+  for (int c4 = 0; c4 < 32 / KC; ++c4) {
     const int s = s0 + c4;
     bool ok;
     const ST* Lc = pp.wait(s, ok);
     if (!__all_sync(0xffffffffu, ok)) return false;
 #pragma unroll 2
-    for (int ii = 0; ii < kCol; ++ii) {
-      const int i = c4 * kCol + ii;
+    for (int ii = 0; ii < KC; ++ii) {
+      const int i = c4 * KC + ii;
       const ST* col = Lc + ii * bp;
       const cx<R> y = shfl(win[PH], i);
       if (lane == i) {
@@ -105,51 +106,32 @@ __device__ __forceinline__ bool group_steps(const Pipe<ST>& pp, int s0, int b, i
   return true;
 }
 
-template <typename R, typename ST, int S>
-__device__ __forceinline__ bool group_dispatch(int ph, const Pipe<ST>& pp, int s0, int b, int lane, cx<R> (&win)[S],
-                                               const cx<R>& nxt, cx<R>& outv) {
+template <typename R, typename ST, int S, int KC>
+__device__ __forceinline__ bool group_dispatch(int ph, const Pipe<ST, KC>& pp, int s0, int b, int lane,
+                                               cx<R> (&win)[S], const cx<R>& nxt, cx<R>& outv) {
   switch (ph) {
-    case 0: return group_steps<R, ST, S, 0>(pp, s0, b, lane, win, nxt, outv);
-    case 1: if constexpr (S > 1) return group_steps<R, ST, S, 1>(pp, s0, b, lane, win, nxt, outv); break;
-    case 2: if constexpr (S > 2) return group_steps<R, ST, S, 2>(pp, s0, b, lane, win, nxt, outv); break;
-    case 3: if constexpr (S > 3) return group_steps<R, ST, S, 3>(pp, s0, b, lane, win, nxt, outv); break;
-    case 4: if constexpr (S > 4) return group_steps<R, ST, S, 4>(pp, s0, b, lane, win, nxt, outv); break;
-    case 5: if constexpr (S > 5) return group_steps<R, ST, S, 5>(pp, s0, b, lane, win, nxt, outv); break;
-    case 6: if constexpr (S > 6) return group_steps<R, ST, S, 6>(pp, s0, b, lane, win, nxt, outv); break;
-    case 7: if constexpr (S > 7) return group_steps<R, ST, S, 7>(pp, s0, b, lane, win, nxt, outv); break;
+    case 0: return group_steps<R, ST, S, KC, 0>(pp, s0, b, lane, win, nxt, outv);
+    case 1: if constexpr (S > 1) return group_steps<R, ST, S, KC, 1>(pp, s0, b, lane, win, nxt, outv); break;
+    case 2: if constexpr (S > 2) return group_steps<R, ST, S, KC, 2>(pp, s0, b, lane, win, nxt, outv); break;
+    case 3: if constexpr (S > 3) return group_steps<R, ST, S, KC, 3>(pp, s0, b, lane, win, nxt, outv); break;
+    case 4: if constexpr (S > 4) return group_steps<R, ST, S, KC, 4>(pp, s0, b, lane, win, nxt, outv); break;
+    case 5: if constexpr (S > 5) return group_steps<R, ST, S, KC, 5>(pp, s0, b, lane, win, nxt, outv); break;
+    case 6: if constexpr (S > 6) return group_steps<R, ST, S, KC, 6>(pp, s0, b, lane, win, nxt, outv); break;
+    case 7: if constexpr (S > 7) return group_steps<R, ST, S, KC, 7>(pp, s0, b, lane, win, nxt, outv); break;
   }
   return false;
 }
 
-template <typename R, typename ST, int S>
-__global__ void __launch_bounds__(32)
-    k_apply(Geo g, const SubDesc* __restrict__ subs, const ST* __restrict__ Lf, const ST* __restrict__ Lb,
-            const cx<R>* __restrict__ dinv_all, const c128* __restrict__ rglob, int rdf, cx<R>* __restrict__ Y,
-            int stage_elems, const KState* __restrict__ kst, DevStatus* status) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  if (kst != nullptr && kst->stop) return;
-  const SubDesc sd = subs[blockIdx.x];
+// The two sweeps of one subdomain with an S-slot register window (S >= the
+// subdomain's ceil((b+1)/32)); the bulk-copy ring is already started.
+template <typename R, typename ST, int S, int KC>
+__device__ __forceinline__ void sweeps(const SubDesc& sd, const Pipe<ST, KC>& pp, int nx, long long goff, int o,
+                                       const c128* __restrict__ rglob, int rdf, const cx<R>* __restrict__ dv,
+                                       cx<R>* __restrict__ Yj, DevStatus* status) {
   const int lane = threadIdx.x;
   const int b = sd.b, npad = sd.npad, G = npad / 32;
-  Pipe<ST> pp;
-  pp.bar = reinterpret_cast<uint64_t*>(sm);
-  pp.stg = reinterpret_cast<ST*>(sm + 128);
-  pp.src0 = Lf + sd.l_off;
-  pp.src1 = Lb + sd.l_off;
-  pp.stage_elems = stage_elems;
-  pp.Q = npad / kCol;
-  pp.bp = sd.bp;
-  pp.bytes = (uint32_t)(kCol * sd.bp * sizeof(ST));
-  const cx<R>* dv = dinv_all + sd.v_off;
-  cx<R>* Yj = Y + sd.v_off;
   const int nseq = 2 * pp.Q;
   constexpr int NST = stages_for<ST>();
-  if (lane == 0) {
-    for (int t = 0; t < NST; ++t) mbar_init(&pp.bar[t], 1);
-    mbar_fence_init();
-    for (int t = 0; t < NST && t < nseq; ++t) pp.issue(t);
-  }
-  __syncwarp();
   auto fail = [&](int s) {
     // a bounded wait gave up: record it, drain this warp's copies in flight, leave
     if (lane == 0) {
@@ -162,13 +144,16 @@ __global__ void __launch_bounds__(32)
   // ---------------- forward: L y = R_j r, z = D^-1 y ----------------
   cx<R> win[S];
 #pragma unroll
-  for (int sl = 0; sl < S; ++sl) win[sl] = gather_row<R>(sd, g, rglob, rdf, 32 * sl + lane);
-  cx<R> nxt = gather_row<R>(sd, g, rglob, rdf, 32 * S + lane);
+  for (int sl = 0; sl < S; ++sl) win[sl] = gather_row<R>(sd, nx, goff, rglob, rdf, 32 * sl + lane);
+  cx<R> nxt = gather_row<R>(sd, nx, goff, rglob, rdf, 32 * S + lane);
   for (int gi = 0; gi < G; ++gi) {
-    const cx<R> nxt2 = gather_row<R>(sd, g, rglob, rdf, 32 * (gi + S + 1) + lane);
+    const cx<R> nxt2 = gather_row<R>(sd, nx, goff, rglob, rdf, 32 * (gi + S + 1) + lane);
     const cx<R> d = dv[32 * gi + lane];
     cx<R> outv;
-    if (!group_dispatch<R, ST, S>(gi % S, pp, 4 * gi, b, lane, win, nxt, outv)) { fail(4 * gi); return; }
+    if (!group_dispatch<R, ST, S, KC>(gi % S, pp, (32 / KC) * gi, b, lane, win, nxt, outv)) {
+      fail((32 / KC) * gi);
+      return;
+    }
     Yj[32 * gi + lane] = outv * d;
     nxt = nxt2;
   }
@@ -180,12 +165,11 @@ __global__ void __launch_bounds__(32)
 #pragma unroll
   for (int sl = 0; sl < S; ++sl) win[sl] = zrow(32 * sl + lane);
   nxt = zrow(32 * S + lane);
-  const int o = g.ovlp;
   for (int gi = 0; gi < G; ++gi) {
     const cx<R> nxt2 = zrow(32 * (gi + S + 1) + lane);
     cx<R> outv;
-    if (!group_dispatch<R, ST, S>(gi % S, pp, pp.Q + 4 * gi, b, lane, win, nxt, outv)) {
-      fail(pp.Q + 4 * gi);
+    if (!group_dispatch<R, ST, S, KC>(gi % S, pp, pp.Q + (32 / KC) * gi, b, lane, win, nxt, outv)) {
+      fail(pp.Q + (32 / KC) * gi);
       return;
     }
     const int row = npad - 1 - (32 * gi + lane);
@@ -197,6 +181,58 @@ __global__ void __launch_bounds__(32)
     Yj[row] = v;
     nxt = nxt2;
   }
+}
+
+// One warp per subdomain; the register window is sized per subdomain
+// (S = ceil((b+1)/32), at most SMAX), so subdomains of different bands share
+// one launch without the small ones paying for the largest window.
+// rbase + (*jptr) * r_ld is the input vector when jptr is set (a step of a
+// captured Arnoldi graph reads its column index from device memory).
+template <typename R, typename ST, int SMAX, int KC>
+__global__ void __launch_bounds__(32)
+    k_apply(const Geo* __restrict__ geos, const SubDesc* __restrict__ subs, const ST* __restrict__ Lf,
+            const ST* __restrict__ Lb, const cx<R>* __restrict__ dinv_all, const c128* __restrict__ rbase,
+            long long r_ld, const int* __restrict__ jptr, int rdf, cx<R>* __restrict__ Y, int stage_elems,
+            const KState* __restrict__ kst, DevStatus* status) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const SubDesc sd = subs[blockIdx.x];
+  if (kst != nullptr && kst[sd.prob].stop) return;
+  const int nx = geos[sd.prob].nx, o = geos[sd.prob].ovlp;
+  const long long goff = geos[sd.prob].goff;
+  const c128* rglob = rbase;
+  if (jptr != nullptr) rglob = (const c128*)((const dfc*)rbase + (long long)(*jptr) * r_ld);
+  const int lane = threadIdx.x;
+  Pipe<ST, KC> pp;
+  pp.bar = reinterpret_cast<uint64_t*>(sm);
+  pp.stg = reinterpret_cast<ST*>(sm + 128);
+  pp.src0 = Lf + sd.l_off;
+  pp.src1 = Lb + sd.l_off;
+  pp.stage_elems = stage_elems;
+  pp.Q = sd.npad / KC;
+  pp.bp = sd.bp;
+  pp.bytes = (uint32_t)(KC * sd.bp * sizeof(ST));
+  const int nseq = 2 * pp.Q;
+  constexpr int NST = stages_for<ST>();
+  if (lane == 0) {
+    for (int t = 0; t < NST; ++t) mbar_init(&pp.bar[t], 1);
+    mbar_fence_init();
+    for (int t = 0; t < NST && t < nseq; ++t) pp.issue(t);
+  }
+  __syncwarp();
+  const cx<R>* dv = dinv_all + sd.v_off;
+  cx<R>* Yj = Y + sd.v_off;
+#define RP_SWEEPS(S_) sweeps<R, ST, S_, KC>(sd, pp, nx, goff, o, rglob, rdf, dv, Yj, status)
+  switch ((sd.b + 32) / 32) {
+    case 1: RP_SWEEPS(1); break;
+    case 2: if constexpr (SMAX >= 2) RP_SWEEPS(2); break;
+    case 3: if constexpr (SMAX >= 3) RP_SWEEPS(3); break;
+    case 4: if constexpr (SMAX >= 4) RP_SWEEPS(4); break;
+    case 5: if constexpr (SMAX >= 5) RP_SWEEPS(5); break;
+    case 6: if constexpr (SMAX >= 6) RP_SWEEPS(6); break;
+    case 7: if constexpr (SMAX >= 7) RP_SWEEPS(7); break;
+    case 8: if constexpr (SMAX >= 8) RP_SWEEPS(8); break;
+  }
+#undef RP_SWEEPS
 }
 
 template <typename R>
@@ -228,60 +264,49 @@ __global__ void k_prolong(Geo g, const SubDesc* __restrict__ subs, const cx<R>* 
   z[r] = mk(re, im);
 }
 
-template <typename R, typename ST, int S>
-cudaError_t launch_apply_t(const Geo& g, const SubDesc* subs, int nsub, int max_bp, const void* Lf, const void* Lb,
-                           const void* dinv, const c128* r, int rdf, void* Y, const KState* kst, DevStatus* status,
-                           cudaStream_t st) {
-  const int stage_elems = kCol * max_bp;
-  const size_t smem = 128 + (size_t)stages_for<ST>() * kCol * max_bp * sizeof(ST);
-  cudaError_t e = cudaFuncSetAttribute(k_apply<R, ST, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// SMAX: 6 slots for complex128 (b <= 160), 8 for complex64 (b <= 232)
+template <typename R, typename ST, int KC>
+cudaError_t launch_apply_t(int max_b, const Geo* geos, const SubDesc* subs, int nsub, int max_bp, const void* Lf,
+                           const void* Lb, const void* dinv, const c128* r, long long r_ld, const int* jptr, int rdf,
+                           void* Y, const KState* kst, DevStatus* status, cudaStream_t st) {
+  constexpr int SMAX = sizeof(R) == 8 ? 6 : 8;
+  if ((max_b + 32) / 32 > SMAX) return cudaErrorInvalidValue;
+  const int stage_elems = KC * max_bp;
+  const size_t smem = 128 + (size_t)stages_for<ST>() * KC * max_bp * sizeof(ST);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_apply<R, ST, SMAX, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_apply<R, ST, S><<<nsub, 32, smem, st>>>(g, subs, (const ST*)Lf, (const ST*)Lb, (const cx<R>*)dinv, r, rdf,
-                                            (cx<R>*)Y, stage_elems, kst, status);
+  k_apply<R, ST, SMAX, KC><<<nsub, 32, smem, st>>>(geos, subs, (const ST*)Lf, (const ST*)Lb, (const cx<R>*)dinv, r,
+                                                   r_ld, jptr, rdf, (cx<R>*)Y, stage_elems, kst, status);
   return cudaGetLastError();
-}
-
-template <typename R, typename ST>
-cudaError_t launch_apply_s(int S, const Geo& g, const SubDesc* subs, int nsub, int max_bp, const void* Lf,
-                           const void* Lb, const void* dinv, const c128* r, int rdf, void* Y, const KState* kst,
-                           DevStatus* status, cudaStream_t st) {
-  switch (S) {
-    case 1: return launch_apply_t<R, ST, 1>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
-    case 2: return launch_apply_t<R, ST, 2>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
-    case 3: return launch_apply_t<R, ST, 3>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
-    case 4: return launch_apply_t<R, ST, 4>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
-    case 5: return launch_apply_t<R, ST, 5>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
-    case 6: return launch_apply_t<R, ST, 6>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
-  }
-  if constexpr (sizeof(R) == 4) {
-    // complex64 factors allow bands up to 232 (b + 1 <= 256)
-    if (S == 7) return launch_apply_t<R, ST, 7>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
-    if (S == 8) return launch_apply_t<R, ST, 8>(g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
-  }
-  return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-size_t apply_smem_bytes(int max_bp, int prec) {
-  if (prec == 0) return 128 + (size_t)stages_for<c128>() * kCol * max_bp * sizeof(c128);
-  if (prec == 1) return 128 + (size_t)stages_for<c64>() * kCol * max_bp * sizeof(c64);
-  return 128 + (size_t)stages_for<h2c>() * kCol * max_bp * sizeof(h2c);
+bool apply_cols_valid(int prec, int cols) { return cols == 8 || (prec == 1 && (cols == 4 || cols == 16)); }
+
+size_t apply_smem_bytes(int max_bp, int prec, int cols) {
+  const size_t es = prec == 0 ? sizeof(c128) : prec == 1 ? sizeof(c64) : sizeof(h2c);
+  return 128 + (size_t)4 * cols * max_bp * es;
 }
 
-cudaError_t launch_apply(int prec, const Geo& g, const SubDesc* subs, int nsub, int max_b, int max_bp,
-                         const void* Lf, const void* Lb, const void* dinv, const c128* r, void* Y, c128* z,
-                         const KState* kst, DevStatus* status, cudaStream_t st, bool r_is_df) {
+cudaError_t launch_local_solves(int prec, int cols, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
+                                int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r,
+                                long long r_ld, const int* jptr, void* Y, const KState* kst, DevStatus* status,
+                                cudaStream_t st, bool r_is_df) {
   const int rdf = r_is_df ? 1 : 0;
-  const int S = (max_b + 1 + 31) / 32;
-  cudaError_t e;
-  if (prec == 0)
-    e = launch_apply_s<double, c128>(S, g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
-  else if (prec == 1)
-    e = launch_apply_s<float, c64>(S, g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
-  else
-    e = launch_apply_s<float, h2c>(S, g, subs, nsub, max_bp, Lf, Lb, dinv, r, rdf, Y, kst, status, st);
-  if (e != cudaSuccess) return e;
+  if (!apply_cols_valid(prec, cols)) return cudaErrorInvalidValue;
+#define RP_APPLY_ARGS max_b, geos, subs, nsub, max_bp, Lf, Lb, dinv, r, r_ld, jptr, rdf, Y, kst, status, st
+  if (prec == 0) return launch_apply_t<double, c128, 8>(RP_APPLY_ARGS);
+  if (prec == 2) return launch_apply_t<float, h2c, 8>(RP_APPLY_ARGS);
+  if (cols == 4) return launch_apply_t<float, c64, 4>(RP_APPLY_ARGS);
+  if (cols == 16) return launch_apply_t<float, c64, 16>(RP_APPLY_ARGS);
+  return launch_apply_t<float, c64, 8>(RP_APPLY_ARGS);
+}
+#undef RP_APPLY_ARGS
+
+cudaError_t launch_prolong(int prec, const Geo& g, const SubDesc* subs, const void* Y, c128* z, const KState* kst,
+                           cudaStream_t st) {
   long long n = (long long)g.nx * g.ny;
   int threads = 256;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
@@ -290,6 +315,15 @@ cudaError_t launch_apply(int prec, const Geo& g, const SubDesc* subs, int nsub, 
   else
     k_prolong<float><<<blocks, threads, 0, st>>>(g, subs, (const c64*)Y, z, kst);
   return cudaGetLastError();
+}
+
+cudaError_t launch_apply(int prec, int cols, const Geo& g, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
+                         int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r, void* Y,
+                         c128* z, const KState* kst, DevStatus* status, cudaStream_t st, bool r_is_df) {
+  cudaError_t e = launch_local_solves(prec, cols, geos, subs, nsub, max_b, max_bp, Lf, Lb, dinv, r, 0, nullptr, Y,
+                                      kst, status, st, r_is_df);
+  if (e != cudaSuccess) return e;
+  return launch_prolong(prec, g, subs, Y, z, kst, st);
 }
 
 }  // namespace rp

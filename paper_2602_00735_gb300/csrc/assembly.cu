@@ -173,10 +173,11 @@ __global__ void k_global_stencil(Geo g, c128* __restrict__ D, c128* __restrict__
 // arithmetic type: double for complex128 factors, float for complex64 ones
 // (those entries are rounded to complex64 before the factorisation anyway).
 template <typename T>
-__global__ void k_local_rows(Geo g, const SubDesc* __restrict__ subs, c128* __restrict__ Aloc) {
+__global__ void k_local_rows(const Geo* __restrict__ geos, const SubDesc* __restrict__ subs, c128* __restrict__ Aloc) {
   const SubDesc sd = subs[blockIdx.y];
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= sd.npad) return;
+  const Geo g = geos[sd.prob];
   c128* out = Aloc + 4 * (sd.v_off + r);
   const c128 z = mk(0.0, 0.0);
   if (r >= sd.n) {
@@ -235,14 +236,14 @@ cudaError_t launch_global_stencil(const Geo& g, c128* D, c128* CW, c128* CS, c12
   return cudaGetLastError();
 }
 
-cudaError_t launch_local_rows(int prec, const Geo& g, const SubDesc* subs, int nsub, int max_npad, c128* Aloc,
+cudaError_t launch_local_rows(int prec, const Geo* geos, const SubDesc* subs, int nsub, int max_npad, c128* Aloc,
                               cudaStream_t st) {
   int threads = 128;
   dim3 grid((max_npad + threads - 1) / threads, nsub);
   if (prec == 0)
-    k_local_rows<double><<<grid, threads, 0, st>>>(g, subs, Aloc);
+    k_local_rows<double><<<grid, threads, 0, st>>>(geos, subs, Aloc);
   else
-    k_local_rows<float><<<grid, threads, 0, st>>>(g, subs, Aloc);
+    k_local_rows<float><<<grid, threads, 0, st>>>(geos, subs, Aloc);
   return cudaGetLastError();
 }
 

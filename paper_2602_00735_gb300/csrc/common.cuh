@@ -111,6 +111,9 @@ struct Geo {
   int px, py, ovlp, pml;
   int local_bc;
   int g_profile;            // 0 smoothstep ramp, 1 g(d) = g_amp d^3
+  long long goff;           // first element of this problem in a concatenated vector
+  int sub0;                 // index of its first subdomain (natural order)
+  int n;                    // nx * ny
 };
 
 enum : int { LO_X = 1, HI_X = 2, LO_Y = 4, HI_Y = 8 };
@@ -129,6 +132,8 @@ struct SubDesc {
   int bp;                                       // L column stride (b rounded up to even)
   long long l_off;                              // element offset of L_j
   long long v_off;                              // element offset of per-row arrays
+  int prob;                                     // problem of a batch (0 for one problem)
+  int pad0;
 };
 
 __device__ __forceinline__ double xpos(const Geo& g, double s) {
@@ -257,6 +262,32 @@ __device__ __forceinline__ dfc split_c(c128 v) {
   r.rl = a.lo;
   r.ih = b.hi;
   r.il = b.lo;
+  return r;
+}
+
+// Double-float arithmetic on the FP32 pipe: a*b as p + t with p = fl(a_hi*b_hi)
+// and t the remaining terms (exact FMA residual of the leading product)
+__device__ __forceinline__ void df_prod(const dfl& a, const dfl& b, float& p, float& t) {
+  p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p);
+  t = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+}
+
+// (hi, lo) += p + t, TwoSum on the leading part
+__device__ __forceinline__ void df_acc(float& hi, float& lo, float p, float t) {
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (p - bb);
+  hi = s;
+  lo += err + t;
+}
+
+__device__ __forceinline__ double df_to_d(float hi, float lo) { return (double)hi + (double)lo; }
+
+__device__ __forceinline__ dfl dfl_of(float hi, float lo) {
+  dfl r;
+  r.hi = hi;
+  r.lo = lo;
   return r;
 }
 

@@ -35,8 +35,6 @@ namespace rp {
 
 namespace {
 
-constexpr int kFactorThreads = 256;
-
 // The four stored entries of row `row` of A_j (D, W, S, SW couplings);
 // identity for padding rows.
 template <typename R>
@@ -62,9 +60,10 @@ __device__ __forceinline__ cx<R> row_entry(const cx<R> (&v)[4], int t, int b) {
   return r;
 }
 
-// R: arithmetic; S: storage of the L entries (cx<R>, or h2c halves).
-template <typename R, typename S>
-__global__ void __launch_bounds__(kFactorThreads)
+// R: arithmetic; S: storage of the L entries (cx<R>, or h2c halves);
+// NT: threads per CTA (128, 256 or 512, a tuned tile shape).
+template <typename R, typename S, int NT>
+__global__ void __launch_bounds__(NT)
     k_factor_ldlt(const SubDesc* __restrict__ subs, const c128* __restrict__ Aloc, S* __restrict__ Lall,
                   S* __restrict__ Lrev_all, cx<R>* __restrict__ dinv_all, double* __restrict__ pivstats,
                   DevStatus* status) {
@@ -105,7 +104,7 @@ __global__ void __launch_bounds__(kFactorThreads)
 
   // this thread's first update entry e = tid: pair p = e / Wc, offset q = e % Wc;
   // e advances by the block size, (p, q) by (dp, dq) with one carry
-  const int dp = kFactorThreads / Wc, dq = kFactorThreads % Wc;
+  const int dp = NT / Wc, dq = NT % Wc;
   const int p0 = tid / Wc, q0 = tid % Wc;
 
   R dmin2 = (R)3e38, dmax2 = (R)0;
@@ -156,7 +155,7 @@ __global__ void __launch_bounds__(kFactorThreads)
     //    diagonal alone, and e < npairs ends it there
     {
       int p = p0, q = q0;
-      for (int e = tid; e < npairs; e += kFactorThreads) {
+      for (int e = tid; e < npairs; e += NT) {
         const int l1 = b - p;
         int t, j;
         if (q < l1) { t = p; j = q + 1; } else { t = b - 1 - p; j = q - l1 + 1; }
@@ -199,27 +198,40 @@ size_t factor_smem_bytes(int b, int prec) {
   return (wc * (wc + 1) / 2 + 2 * wc) * es + 2 * wc * sizeof(int2);
 }
 
-cudaError_t launch_factor(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
-                          void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
-  size_t smem = factor_smem_bytes(max_b, prec);
-  cudaError_t e;
-  if (prec == 0) {
-    e = cudaFuncSetAttribute(k_factor_ldlt<double, c128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_factor_ldlt<double, c128><<<nsub, kFactorThreads, smem, st>>>(subs, Aloc, (c128*)L, (c128*)Lrev,
-                                                                     (c128*)dinv, pivstats, status);
-  } else if (prec == 1) {
-    e = cudaFuncSetAttribute(k_factor_ldlt<float, c64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_factor_ldlt<float, c64><<<nsub, kFactorThreads, smem, st>>>(subs, Aloc, (c64*)L, (c64*)Lrev, (c64*)dinv,
-                                                                   pivstats, status);
-  } else {
-    e = cudaFuncSetAttribute(k_factor_ldlt<float, h2c>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_factor_ldlt<float, h2c><<<nsub, kFactorThreads, smem, st>>>(subs, Aloc, (h2c*)L, (h2c*)Lrev, (c64*)dinv,
-                                                                   pivstats, status);
-  }
+namespace {
+
+template <typename R, typename S, int NT>
+cudaError_t launch_factor_t(size_t smem, const SubDesc* subs, int nsub, const c128* Aloc, void* L, void* Lrev,
+                            void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_factor_ldlt<R, S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_factor_ldlt<R, S, NT><<<nsub, NT, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (cx<R>*)dinv, pivstats, status);
   return cudaGetLastError();
+}
+
+template <typename R, typename S>
+cudaError_t launch_factor_s(int threads, size_t smem, const SubDesc* subs, int nsub, const c128* Aloc, void* L,
+                            void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
+  switch (threads) {
+    case 128: return launch_factor_t<R, S, 128>(smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+    case 256: return launch_factor_t<R, S, 256>(smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+    case 512: return launch_factor_t<R, S, 512>(smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+bool factor_threads_valid(int threads) { return threads == 128 || threads == 256 || threads == 512; }
+
+cudaError_t launch_factor(int prec, int threads, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
+                          void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
+  const size_t smem = factor_smem_bytes(max_b, prec);
+  if (prec == 0)
+    return launch_factor_s<double, c128>(threads, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+  if (prec == 1)
+    return launch_factor_s<float, c64>(threads, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+  return launch_factor_s<float, h2c>(threads, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
 }
 
 }  // namespace rp

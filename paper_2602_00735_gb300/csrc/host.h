@@ -1,0 +1,74 @@
+// Host-side helpers shared by the one-problem and the batched handles:
+// CUDA error mapping, device allocation, and the construction of one
+// problem's geometry and covering (Section 2).
+#pragma once
+
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/raspml.h"
+#include "common.cuh"
+#include "kernels.h"
+
+#define RP_CUDA(call)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      std::fprintf(stderr, "raspml: %s failed: %s\n", #call, cudaGetErrorString(e_)); \
+      return e_ == cudaErrorMemoryAllocation ? RASPML_ENOMEM : RASPML_ECUDA;           \
+    }                                                                                 \
+  } while (0)
+
+namespace rp {
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? RASPML_ENOMEM : RASPML_ECUDA;
+  }
+  return RASPML_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+inline float ev_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.f;
+  return ms;
+}
+
+// Validates p (the rules of ras_pml_setup), fills g (goff and sub0 left 0)
+// and appends the descriptors of its subdomains in natural order (x fastest)
+// with prob set; l_off and v_off are left for the caller. Returns a status.
+int build_problem(const ras_pml_params& p, int prob, Geo& g, std::vector<SubDesc>& subs);
+
+// Entry counts of one subdomain's factor (L: npad*bp) and per-row arrays (npad).
+inline long long sub_l_entries(const SubDesc& d) { return (long long)d.npad * d.bp; }
+
+// Times each tile shape of the factor and the apply on the given problem
+// set (CUDA events, median of `reps`) and returns the fastest in *best.
+struct TuneTarget {
+  int prec;
+  const Geo* geos;
+  const SubDesc* subs;
+  int nsub, max_b, max_bp, max_npad;
+  long long sum_npad, sum_l;
+  c128* Aloc;          // local rows, already assembled
+  void *L, *Lrev, *dinv, *Y;
+  double* pivstats;
+  DevStatus* status;
+  const c128* r;       // any input vector of the problems' layout
+  cudaStream_t st;
+};
+int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* report);
+
+}  // namespace rp

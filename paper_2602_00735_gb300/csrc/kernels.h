@@ -27,27 +27,45 @@ struct KState {
   double bnorm;    // ||b||_2
   double est;      // latest |g_{j+1}| / ||b||
   double hnorm;    // latest ||w||_2
-  double pad2;
+  double relres;   // true relative residual at the last cycle start (batch)
+  int live;        // batch: not yet finished (converged or out of iterations)
+  int pad;
 };
+
+// Tile shapes of the factor and apply launches (chosen by the tuner).
+struct Tune {
+  int factor_threads = 256;   // threads per factor CTA: 128, 256, 512
+  int apply_cols = 8;         // band columns per bulk copy: 8 (4 or 16 with complex64 storage)
+};
+bool factor_threads_valid(int threads);
+bool apply_cols_valid(int prec, int cols);
 
 // assembly.cu
 cudaError_t launch_global_stencil(const Geo& g, c128* D, c128* CW, c128* CS, c128* CSW, cudaStream_t st);
-cudaError_t launch_local_rows(int prec, const Geo& g, const SubDesc* subs, int nsub, int max_npad, c128* Aloc,
+cudaError_t launch_local_rows(int prec, const Geo* geos, const SubDesc* subs, int nsub, int max_npad, c128* Aloc,
                               cudaStream_t st);
 cudaError_t launch_rhs(const Geo& g, const double* cen, const double* amp, int ns, double width, c128* b,
                        cudaStream_t st);
 
 // factor.cu
 size_t factor_smem_bytes(int b, int prec);
-cudaError_t launch_factor(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
+cudaError_t launch_factor(int prec, int threads, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
                           void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st);
 
 // apply.cu
-size_t apply_smem_bytes(int max_bp, int prec);
-// r is complex128, or double-float (dfc) when r_is_df
-cudaError_t launch_apply(int prec, const Geo& g, const SubDesc* subs, int nsub, int max_b, int max_bp,
-                         const void* Lf, const void* Lb, const void* dinv, const c128* r, void* Y, c128* z,
-                         const KState* kst, DevStatus* status, cudaStream_t st, bool r_is_df = false);
+size_t apply_smem_bytes(int max_bp, int prec, int cols);
+// Local solves of all subdomains into Y. The input is r (complex128, or
+// double-float dfc when r_is_df), or r + (*jptr) * r_ld when jptr is set.
+cudaError_t launch_local_solves(int prec, int cols, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
+                                int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r,
+                                long long r_ld, const int* jptr, void* Y, const KState* kst, DevStatus* status,
+                                cudaStream_t st, bool r_is_df);
+cudaError_t launch_prolong(int prec, const Geo& g, const SubDesc* subs, const void* Y, c128* z, const KState* kst,
+                           cudaStream_t st);
+// one problem: local solves + prolongation
+cudaError_t launch_apply(int prec, int cols, const Geo& g, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
+                         int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r, void* Y,
+                         c128* z, const KState* kst, DevStatus* status, cudaStream_t st, bool r_is_df = false);
 
 // krylov.cu
 cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, const c128* CS, const c128* CSW,
@@ -77,5 +95,64 @@ cudaError_t launch_reorth_decide(KState* kst, c128* hcol, int j, double eta2, cu
 cudaError_t launch_backsolve(const c128* H, int ldh, const c128* gvec, const KState* kst, c128* y,
                              cudaStream_t st);
 cudaError_t launch_axpy_state(c128* x, const c128* v, long long n, cudaStream_t st);
+
+}  // namespace rp
+
+namespace rp {
+
+// ---------------------------------------------------------------------------
+// Batched form (batch.cu): vectors of many problems concatenated, each
+// problem starting at a multiple of kBatchTile elements.
+// ---------------------------------------------------------------------------
+constexpr int kBatchTile = 2048;
+
+// Lockstep control in device memory: the current Arnoldi step j and the
+// number of problems whose cycle is still running.
+struct BCtl {
+  int j;
+  int active;
+  int pad0, pad1;
+};
+
+// Everything one lockstep Arnoldi step touches (device pointers).
+struct BStep {
+  int prec, cols, nprob, nsub, ntiles, max_b, max_bp, m, maxit;
+  double rtol;
+  const Geo* geos;
+  const SubDesc* subs;
+  const int* sub_index;   // natural subdomain index -> launch position
+  const int* tile_prob;   // tile -> problem
+  const int* tile0;       // problem -> first tile
+  const int* tile1;       // problem -> one past its last tile
+  const void *L, *Lrev, *dinv;
+  void* Y;
+  const c128 *D, *CW, *CS, *CSW;
+  void* V;                // (m+1) x ld double-float basis
+  c128* Z;                // m x ld preconditioned directions
+  long long ld;           // batch vector length
+  c128* w;
+  c128* partial;          // (m+1) x ntiles
+  double* pnorm;          // ntiles
+  c128* H;                // per problem (m+1) x m, column-major
+  long long hstride;
+  double* cs;
+  c128 *sn, *gvec, *yv;
+  KState* kst;            // per problem
+  BCtl* ctl;
+  DevStatus* status;
+};
+
+cudaError_t launch_bprolong(int prec, int ntiles, const int* tile_prob, const Geo* geos, const SubDesc* subs,
+                            const int* sub_index, const void* Y, c128* z, long long ldz, const int* jptr,
+                            const KState* kst, int gate, cudaStream_t st);
+cudaError_t launch_bspmv(int ntiles, const int* tile_prob, const Geo* geos, const c128* D, const c128* CW,
+                         const c128* CS, const c128* CSW, const c128* x, long long ldx, const int* jptr,
+                         const c128* bsub, c128* y, double* pnorm, const KState* kst, int gate, cudaStream_t st);
+// one Arnoldi step of every running problem (j read from ctl->j, then advanced)
+cudaError_t launch_bstep(const BStep& a, cudaStream_t st);
+// r = b - A x, beta, stop/start decisions, v_0 (problems still being solved)
+cudaError_t launch_bcycle_start(const BStep& a, const c128* b, const c128* x, int first, cudaStream_t st);
+// y = R^-1 g and x += Z y for the problems of the cycle
+cudaError_t launch_bcycle_end(const BStep& a, c128* x, cudaStream_t st);
 
 }  // namespace rp

@@ -130,31 +130,6 @@ __global__ void __launch_bounds__(kThreads)
 // projection and the update read pre-split operands. Products use the exact
 // FMA residual, sums the TwoSum transformation: about 46 correct bits.
 // ---------------------------------------------------------------------------
-// a*b as p + t with p = fl(a_hi*b_hi) and t the remaining terms
-__device__ __forceinline__ void df_prod(const dfl& a, const dfl& b, float& p, float& t) {
-  p = a.hi * b.hi;
-  const float e = fmaf(a.hi, b.hi, -p);
-  t = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
-}
-
-// (hi, lo) += p + t, TwoSum on the leading part
-__device__ __forceinline__ void df_acc(float& hi, float& lo, float p, float t) {
-  const float s = hi + p;
-  const float bb = s - hi;
-  const float err = (hi - (s - bb)) + (p - bb);
-  hi = s;
-  lo += err + t;
-}
-
-__device__ __forceinline__ double df_to_d(float hi, float lo) { return (double)hi + (double)lo; }
-
-__device__ __forceinline__ dfl dfl_of(float hi, float lo) {
-  dfl r;
-  r.hi = hi;
-  r.lo = lo;
-  return r;
-}
-
 // wdf = split(w)
 __global__ void k_split(const c128* __restrict__ w, dfc* __restrict__ wdf, long long n,
                         const KState* __restrict__ kst) {

@@ -1,0 +1,83 @@
+// Tile-shape tuner: times each candidate shape of the factor launch (threads
+// per CTA) and of the local-solve launch (band columns per bulk copy) on the
+// caller's own subdomains with CUDA events on its stream, and returns the
+// fastest. Every factor shape performs the same operations on every window
+// entry in the same order, so the factors it leaves are those of any shape.
+#include <algorithm>
+
+#include "host.h"
+
+namespace rp {
+
+namespace {
+
+float median(std::vector<float> v) {
+  std::sort(v.begin(), v.end());
+  return v.empty() ? 0.f : v[v.size() / 2];
+}
+
+}  // namespace
+
+int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* report) {
+  if (reps < 1) reps = 1;
+  ras_pml_tune_t rep{};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RP_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return RASPML_ECUDA;
+  }
+  cudaError_t e = cudaSuccess;
+  const int fcand[3] = {128, 256, 512};
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+    std::vector<float> ms;
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+      e = cudaEventRecord(e0, t.st);
+      if (e == cudaSuccess)
+        e = launch_factor(t.prec, fcand[c], t.subs, t.nsub, t.max_b, t.Aloc, t.L, t.Lrev, t.dinv, t.pivstats,
+                          t.status, t.st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, t.st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) ms.push_back(ev_ms(e0, e1));
+    }
+    rep.factor_cand[rep.n_factor] = fcand[c];
+    rep.factor_ms[rep.n_factor++] = median(ms);
+  }
+  std::vector<int> acand{8};
+  if (t.prec == 1) { acand.push_back(4); acand.push_back(16); }
+  for (int cols : acand) {
+    if (e != cudaSuccess) break;
+    if (apply_smem_bytes(t.max_bp, t.prec, cols) > 227 * 1024) continue;
+    std::vector<float> ms;
+    for (int r = 0; r <= reps && e == cudaSuccess; ++r) {   // the first run warms up
+      e = cudaEventRecord(e0, t.st);
+      if (e == cudaSuccess)
+        e = launch_local_solves(t.prec, cols, t.geos, t.subs, t.nsub, t.max_b, t.max_bp, t.L, t.Lrev, t.dinv, t.r, 0,
+                                nullptr, t.Y, nullptr, t.status, t.st, false);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, t.st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess && r > 0) ms.push_back(ev_ms(e0, e1));
+    }
+    rep.apply_cand[rep.n_apply] = cols;
+    rep.apply_ms[rep.n_apply++] = median(ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "raspml: tune: %s\n", cudaGetErrorString(e));
+    return RASPML_ECUDA;
+  }
+  int bf = 0, ba = 0;
+  for (int i = 1; i < rep.n_factor; ++i)
+    if (rep.factor_ms[i] < rep.factor_ms[bf]) bf = i;
+  for (int i = 1; i < rep.n_apply; ++i)
+    if (rep.apply_ms[i] < rep.apply_ms[ba]) ba = i;
+  best->factor_threads = rep.factor_cand[bf];
+  best->apply_cols = rep.n_apply > 0 ? rep.apply_cand[ba] : 8;
+  rep.factor_threads = best->factor_threads;
+  rep.apply_cols = best->apply_cols;
+  if (report) *report = rep;
+  return RASPML_OK;
+}
+
+}  // namespace rp

@@ -17,6 +17,22 @@ PARAM_KEYS = ("k", "x0", "y0", "x1", "y1", "kappa_g", "h", "px", "py", "ovlp_cel
               "g_amp", "g_ramp", "local_bc")
 
 
+def make_params(params: dict, factor_prec: int = 0, ortho: int = 0) -> _lib.Params:
+    p = _lib.Params()
+    for key in PARAM_KEYS:
+        setattr(p, key, params[key])
+    p.factor_prec = int(factor_prec)
+    p.ortho = int(ortho)
+    p.g_profile = int(params.get("g_profile", 0))
+    return p
+
+
+def tune_dict(rep: _lib.TuneReport) -> dict:
+    return {"factor_threads": rep.factor_threads, "apply_cols": rep.apply_cols,
+            "factor_ms": {rep.factor_cand[i]: rep.factor_ms[i] for i in range(rep.n_factor)},
+            "apply_ms": {rep.apply_cand[i]: rep.apply_ms[i] for i in range(rep.n_apply)}}
+
+
 def _dev_ptr(t: torch.Tensor, n: int) -> int:
     if not (t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous() and t.numel() == n):
         raise ValueError(f"expected a contiguous cuda complex128 tensor of {n} elements")
@@ -32,12 +48,7 @@ class RasPml:
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        p = _lib.Params()
-        for key in PARAM_KEYS:
-            setattr(p, key, params[key])
-        p.factor_prec = int(factor_prec)
-        p.ortho = int(ortho)
-        p.g_profile = int(params.get("g_profile", 0))
+        p = make_params(params, factor_prec, ortho)
         self._h = c_void_p()
         with torch.cuda.device(self.device):
             _lib.check("ras_pml_setup", self.lib.ras_pml_setup(byref(p), c_void_p(self.stream.cuda_stream),
@@ -81,6 +92,15 @@ class RasPml:
 
     def factor(self) -> None:
         _lib.check("ras_pml_factor", self.lib.ras_pml_factor(self._h))
+
+    def tune(self) -> dict:
+        """Time the factor and apply tile shapes, keep the fastest (leaves the handle factored)."""
+        rep = _lib.TuneReport()
+        _lib.check("ras_pml_tune", self.lib.ras_pml_tune(self._h, byref(rep)))
+        return tune_dict(rep)
+
+    def set_shapes(self, factor_threads: int, apply_cols: int) -> None:
+        _lib.check("ras_pml_set_shapes", self.lib.ras_pml_set_shapes(self._h, int(factor_threads), int(apply_cols)))
 
     # -- operators -------------------------------------------------------------
     def apply(self, r: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:

@@ -3,6 +3,10 @@ iteration counts (rtol 1e-6, x0 = 0, no restart) with the RAS-PML
 preconditioner on the named workloads. Calls only oracle/ and workloads.
 
     python tests/golden/make_oracle_iterations.py c0 c1 c2
+    python tests/golden/make_oracle_iterations.py c3     # every problem of the batch
+
+For a batch the counts are stored per problem, in the batch's order; the
+problems run in a pool of processes started with "spawn".
 """
 import json
 import os
@@ -19,7 +23,10 @@ OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_iteration
 
 
 def run(name):
-    w = workloads.get(name)
+    return run_workload(workloads.get(name))
+
+
+def run_workload(w):
     p = w.params()
     t0 = time.time()
     grid, A = fem.assemble_global(p)
@@ -32,10 +39,20 @@ def run(name):
             "subdomains": len(R.subs), "setup_factor_s": round(t1 - t0, 2), "solve_s": round(t2 - t1, 2)}
 
 
+def run_batch(name):
+    import multiprocessing as mp
+    probs = workloads.batch(name)
+    order = sorted(range(len(probs)), key=lambda q: -probs[q].n_unknowns)   # largest first
+    with mp.get_context("spawn").Pool(min(len(probs), os.cpu_count() or 1)) as pool:
+        res = dict(zip(order, pool.map(run_workload, [probs[q] for q in order], chunksize=1)))
+    return {key: [res[q][key] for q in range(len(probs))] for key in ("iters", "relres", "n", "subdomains")} | \
+        {"rtol": 1e-6, "solve_s_total": round(sum(res[q]["solve_s"] + res[q]["setup_factor_s"] for q in res), 1)}
+
+
 if __name__ == "__main__":
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for name in sys.argv[1:]:
-        data[name] = run(name)
+        data[name] = run_batch(name) if name in workloads.BATCH_NAMES else run(name)
         print(name, data[name], flush=True)
         with open(OUT, "w") as f:
             json.dump(data, f, indent=1, sort_keys=True)

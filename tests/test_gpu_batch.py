@@ -1,0 +1,141 @@
+"""Batched form: eight independent problems of uneven size, subdomain grids
+and wavenumbers (workloads.batch("c3small")) set up, factored, applied and
+solved in the same launches. Each problem is compared with the CPU FP64
+oracle on its own, at the tolerances of the one-problem path; the batch
+apply is also compared bit for bit with the one-problem handle (the same
+kernels run the same arithmetic on every subdomain)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from gpu_util import oracle_problem, rel, random_vector
+from oracle import fem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2602_00735_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def probs():
+    return workloads.batch("c3small")
+
+
+def _sources(ws):
+    return [(w.centres, w.amps, w.width) for w in ws]
+
+
+def test_layout_matvec_and_rhs(pkg, probs):
+    with pkg.BatchRasPml([w.params() for w in probs], factor_prec=1) as B:
+        assert B.nprob == len(probs)
+        assert np.all(B.offsets % 2048 == 0)
+        assert list(B.sizes) == [w.n_unknowns for w in probs]
+        xs = [random_vector(int(n), 10 + q) for q, n in enumerate(B.sizes)]
+        x = B.join(xs)
+        y = B.matvec(x)
+        b = B.assemble_rhs(_sources(probs))
+        mask = torch.ones(B.ntot, dtype=torch.bool, device=y.device)
+        for q, (w, yq, bq) in enumerate(zip(probs, B.split(y), B.split(b))):
+            grid, A, _ = oracle_problem(w)
+            assert rel(yq.cpu().numpy(), A @ xs[q]) <= 1e-13
+            bo = fem.assemble_rhs(w.params(), w.centres, w.amps, w.width)
+            assert np.max(np.abs(bq.cpu().numpy() - bo)) <= 1e-13 * np.max(np.abs(bo))
+            mask[int(B.offsets[q]):int(B.offsets[q]) + int(B.sizes[q])] = False
+        assert torch.count_nonzero(y[mask]) == 0 and torch.count_nonzero(b[mask]) == 0
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
+def test_apply_matches_oracle(pkg, probs, prec, tol):
+    with pkg.BatchRasPml([w.params() for w in probs], factor_prec=prec) as B:
+        B.factor()
+        inf = B.info()
+        assert inf["factored"] == 1 and inf["num_sub"] == sum(w.px * w.py for w in probs)
+        rs = [random_vector(int(n), 20 + q) for q, n in enumerate(B.sizes)]
+        z = B.apply(B.join(rs))
+        for q, (w, zq) in enumerate(zip(probs, B.split(z))):
+            _, _, R = oracle_problem(w)
+            assert rel(zq.cpu().numpy(), R.apply(rs[q])) <= tol, q
+
+
+def test_apply_equals_one_problem_handle_bitwise(pkg, probs):
+    with pkg.BatchRasPml([w.params() for w in probs], factor_prec=1) as B:
+        B.factor()
+        rs = [random_vector(int(n), 30 + q) for q, n in enumerate(B.sizes)]
+        z = B.apply(B.join(rs))
+        for q, w in enumerate(probs[:4]):
+            with pkg.RasPml(w.params(), factor_prec=1) as s:
+                s.factor()
+                zs = s.apply(torch.from_numpy(rs[q]).cuda())
+                assert torch.equal(zs, B.split(z)[q])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lockstep_solve_matches_direct_solves(pkg, probs, prec):
+    with pkg.BatchRasPml([w.params() for w in probs], factor_prec=prec) as B:
+        b = B.assemble_rhs(_sources(probs))
+        x, it, relres, st = B.solve(b, rtol=1e-10, maxit=400)
+        assert st == 0 and np.all(relres <= 1e-10)
+        assert len(set(it.tolist())) > 1            # problems stopped at different steps
+        assert B.info()["steps"] >= it.max()
+        for q, (w, xq) in enumerate(zip(probs, B.split(x))):
+            grid, A, _ = oracle_problem(w)
+            p = w.params()
+            u = fem.direct_solve(A, fem.assemble_rhs(p, w.centres, w.amps, w.width))
+            assert rel(xq.cpu().numpy(), u) <= 1e-8, q
+
+
+def test_iterations_match_one_problem_solves(pkg, probs):
+    """Lockstep FGMRES takes, per problem, the iterations of the one-problem
+    solver with the same Gram-Schmidt (double-float CGS, ortho = 3); sums in
+    a different order may move the stopping step by one."""
+    with pkg.BatchRasPml([w.params() for w in probs], factor_prec=1) as B:
+        b = B.assemble_rhs(_sources(probs))
+        _, it, _, st = B.solve(b, rtol=1e-6, maxit=400)
+        assert st == 0
+        for q, w in enumerate(probs):
+            with pkg.RasPml(w.params(), factor_prec=1, ortho=3) as s:
+                bq = s.assemble_rhs(w.centres, w.amps, w.width)
+                _, its, _, _ = s.solve(bq, rtol=1e-6, maxit=400)
+            assert abs(int(it[q]) - its) <= 1, (q, it[q], its)
+
+
+def test_restarted_and_tuned_solve(pkg, probs):
+    with pkg.BatchRasPml([w.params() for w in probs], factor_prec=1) as B:
+        rep = B.tune()
+        assert rep["factor_threads"] in (128, 256, 512) and rep["apply_cols"] in (4, 8, 16)
+        assert set(rep["factor_ms"]) == {128, 256, 512} and all(v > 0 for v in rep["factor_ms"].values())
+        inf = B.info()
+        assert (inf["factor_threads"], inf["apply_cols"]) == (rep["factor_threads"], rep["apply_cols"])
+        b = B.assemble_rhs(_sources(probs))
+        x, it, relres, st = B.solve(b, rtol=1e-8, maxit=600, restart=15)
+        assert st == 0 and np.all(relres <= 1e-8)
+        assert B.info()["cycles"] >= 2
+        w = probs[0]
+        grid, A, _ = oracle_problem(w)
+        u = fem.direct_solve(A, fem.assemble_rhs(w.params(), w.centres, w.amps, w.width))
+        assert rel(B.split(x)[0].cpu().numpy(), u) <= 1e-6
+
+
+def test_not_converged_and_errors(pkg, probs):
+    from paper_2602_00735_gb300 import RasPmlError
+    ps = [w.params() for w in probs[:3]]
+    with pkg.BatchRasPml(ps, factor_prec=1) as B:
+        with pytest.raises(RasPmlError):
+            B.apply(B.empty())                    # not factored
+        b = B.assemble_rhs(_sources(probs[:3]))
+        x, it, relres, st = B.solve(b, rtol=1e-12, maxit=3)
+        assert st == 1 and np.all(it == 3) and np.all(relres > 1e-12)
+        zero = torch.zeros_like(b)
+        x, it, relres, st = B.solve(zero, rtol=1e-6, maxit=10)
+        assert st == 0 and np.all(it == 0) and torch.count_nonzero(x) == 0
+        bn = b.clone()
+        bn[int(B.offsets[1]) + 5] = float("nan")
+        with pytest.raises(RasPmlError):
+            B.solve(bn, rtol=1e-6, maxit=10)

@@ -53,6 +53,22 @@ def test_struct_layout_matches_header(lib):
     assert names == [n for n, _ in _lib.Info._fields_]
 
 
+def _fields(src, start, end):
+    body = src[src.index(start):]
+    body = body[:body.index(end)]
+    fields = re.findall(r"\b(?:double|float|int64_t|int32_t)\s+([\w\s,\[\]]+);", body)
+    return [re.sub(r"\[\d+\]", "", f).strip() for grp in fields for f in grp.split(",")]
+
+
+def test_tune_and_batch_struct_layouts(lib):
+    from paper_2602_00735_gb300 import _lib
+    src = open(HEADER).read()
+    assert _fields(src, "typedef struct {\n  int32_t factor_threads;", "} ras_pml_tune_t;") == \
+        [n for n, _ in _lib.TuneReport._fields_]
+    assert _fields(src, "typedef struct {\n  int32_t nprob;", "} ras_pml_batch_info_t;") == \
+        [n for n, _ in _lib.BatchInfo._fields_]
+
+
 def test_error_strings_and_null_handling(lib):
     import ctypes
     assert lib.ras_pml_error_string(0) == b"success"
@@ -60,7 +76,12 @@ def test_error_strings_and_null_handling(lib):
     # argument validation happens before any device call
     assert lib.ras_pml_setup(None, None, None) == -1
     assert lib.ras_pml_apply(None, None, None) == -1
+    assert lib.ras_pml_tune(None, None) == -1
+    assert lib.ras_pml_batch_setup(None, 1, None, None) == -1
+    assert lib.ras_pml_batch_solve(None, None, None, 1e-6, 10, 0, None, None) == -1
+    assert lib.ras_pml_batch_apply(None, None, None) == -1
     lib.ras_pml_destroy(None)
+    lib.ras_pml_batch_destroy(None)
     from paper_2602_00735_gb300 import _lib
     p = _lib.Params(k=10.0, x0=0, y0=0, x1=1, y1=1, kappa_g=0.1, h=0.013, px=2, py=2, ovlp_cells=2,
                     pml_cells=2, g_amp=20, g_ramp=0.05, local_bc=0, factor_prec=0)

@@ -21,6 +21,16 @@ Smaller "tiny*" workloads with the same construction serve the tests.
 paper_setup(k, cells_per_box, ...) builds the set-up of the paper's own
 experiments (Omega = (0,1)^2 with a three-wavelength PML, h = 1/(2k),
 g(x) = 10 k x^3, smoothed-delta source, the paper's width law).
+
+batch(name) returns a list of independent problems for the batched form:
+  c3   64 problems; k log-uniform in [20*pi, 120*pi]; Omega_int = (0, s)^2
+       with s uniform in [0.5, 1.5] and the same PML of width 0.1; about 16
+       points per wavelength (h = (s + 0.2)/M, M = round((s + 0.2) 16 k / 2 pi));
+       overlap and local PML width 0.5*ln(k)/k in cells; px and py drawn
+       independently from 2..12, within the range where a subdomain's
+       half-bandwidth stays <= 232 and a box holds at least two overlaps;
+       1..8 Gaussian sources (width 0.4*pi/k, amplitude 1) uniform in
+       Omega_int. All draws from numpy's default_rng(seed).
 """
 from __future__ import annotations
 
@@ -29,7 +39,7 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-__all__ = ["Workload", "get", "width_cells", "NAMES"]
+__all__ = ["Workload", "get", "batch", "width_cells", "NAMES", "BATCH_NAMES"]
 
 
 def width_cells(k: float, h: float) -> int:
@@ -153,3 +163,71 @@ def get(name: str) -> Workload:
 
 
 NAMES = ("c0", "c1", "c2", "c4", "tiny", "tiny3", "small", "mid")
+
+#: largest local half-bandwidth of the complex64 factor window
+BAND_LIMIT = 232
+
+
+def _grid_range(M: int, w: int) -> tuple[int, int]:
+    """Subdomain counts P in 2..12 for M cells with overlap and PML width w:
+    every box holds at least 2w cells (floor(M/P) >= 2w) and the widest
+    subdomain, ceil(M/P) + 4w + 1 nodes, keeps b <= BAND_LIMIT."""
+    lo = 2
+    while lo <= 12 and -(-M // lo) + 4 * w + 2 > BAND_LIMIT:
+        lo += 1
+    hi = 12
+    while hi >= 2 and M // hi < 2 * w:
+        hi -= 1
+    if lo > hi:
+        raise ValueError(f"no subdomain grid in 2..12 fits M={M}, w={w}")
+    return lo, hi
+
+
+def _batch_c3(count=64, seed=3, name="c3") -> list:
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(count):
+        k = float(np.exp(rng.uniform(math.log(20 * math.pi), math.log(120 * math.pi))))
+        side = float(rng.uniform(0.5, 1.5))
+        L = side + 0.2
+        M = int(round(L * 16 * k / (2 * math.pi)))
+        h = L / M
+        w = width_cells(k, h)
+        lo, hi = _grid_range(M, w)
+        px, py = (int(v) for v in rng.integers(lo, hi + 1, size=2))
+        ns = int(rng.integers(1, 9))
+        centres = rng.uniform(0.0, side, size=(ns, 2))
+        out.append(Workload(name=f"{name}-{q}", k=k, x0=0.0, y0=0.0, x1=side, y1=side, kappa_g=0.1, h=h,
+                            px=px, py=py, ovlp_cells=w, pml_cells=w, centres=centres, amps=np.ones(ns),
+                            width=0.4 * math.pi / k, seed=seed))
+    return out
+
+
+def batch(name: str) -> list:
+    """Return the named seeded list of problems for the batched form:
+    c3 (the 64-problem set), c3small (8 problems of the same construction at
+    k in [8*pi, 24*pi], for tests)."""
+    if name == "c3":
+        return _batch_c3()
+    if name == "c3small":
+        rng = np.random.default_rng(5)
+        out = []
+        for q in range(8):
+            k = float(np.exp(rng.uniform(math.log(8 * math.pi), math.log(24 * math.pi))))
+            side = float(rng.uniform(0.5, 1.5))
+            L = side + 0.2
+            M = int(round(L * 16 * k / (2 * math.pi)))
+            h = L / M
+            w = width_cells(k, h)
+            lo, hi = _grid_range(M, w)
+            px, py = (int(v) for v in rng.integers(lo, hi + 1, size=2))
+            ns = int(rng.integers(1, 9))
+            out.append(Workload(name=f"c3small-{q}", k=k, x0=0.0, y0=0.0, x1=side, y1=side, kappa_g=0.1, h=h,
+                                px=px, py=py, ovlp_cells=w, pml_cells=w,
+                                centres=rng.uniform(0.0, side, size=(ns, 2)), amps=np.ones(ns),
+                                width=0.4 * math.pi / k, seed=5))
+        return out
+    raise KeyError(f"unknown batch {name!r}; known: {BATCH_NAMES}")
+
+
+BATCH_NAMES = ("c3", "c3small")
