@@ -255,8 +255,14 @@ def run_ours(args, rank, world, local_rank):
     p = w.params()
     stream = torch.cuda.current_stream(dev)
 
+    shapes = {}   # tile shapes per factor precision, tuned once on a warm-up handle
+
     def one_step(prec, timing=False, ortho=None):
         s = RasPml(p, factor_prec=prec, ortho=args.ortho if ortho is None else ortho)
+        if prec not in shapes:
+            rep = s.tune()
+            shapes[prec] = (rep["factor_threads"], rep["factor_rank"], rep["apply_cols"], rep)
+        s.set_shapes(*shapes[prec][:3])
         if timing:
             s.set_timing(True)
         b = s.assemble_rhs(w.centres, w.amps, w.width)
@@ -330,6 +336,7 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             s = RasPml(p, factor_prec=args.prec, ortho=args.ortho)
+            s.set_shapes(*shapes[args.prec][:3])
             s.factor()
             s.solve_host(b_host, rtol=RTOL, maxit=MAXIT, x_host=x_host)
             t1 = time.perf_counter()
@@ -375,6 +382,7 @@ def run_ours(args, rank, world, local_rank):
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "algorithmic_bytes_per_launch": info["apply_bytes"]},
         "fp64": fp64, "error_vs_fp64": err, "c64_fp64_gram_schmidt": gs64,
+        "tune": shapes[args.prec][3],
         "gpu_launches": int(sum(launches_per_step)),
         "gpu_launches_per_step": int(launches_per_step[-1]),
         "clocks": clk, "e2e": e2e,
@@ -425,7 +433,7 @@ def run_batch(args, rank, world, local_rank):
     # tile shapes chosen once, on the first warm-up handle
     B0 = BatchRasPml(params, factor_prec=args.prec)
     tune = B0.tune()
-    shapes = (tune["factor_threads"], tune["apply_cols"])
+    shapes = (tune["factor_threads"], tune["factor_rank"], tune["apply_cols"])
     B0.close()
     for _ in range(args.warmup):
         B, b, x, it, rel, st = one_step()
@@ -508,7 +516,7 @@ def run_batch(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (complex64 factors %.1f GB)" % (info["factor_bytes"] / 1e9)},
         "iters": {"min": int(it.min()), "median": float(np.median(it)), "max": int(it.max())},
         "relres_max": float(rel.max()), "status": st, "lockstep_steps": info["steps"], "cycles": info["cycles"],
-        "tune": tune, "shapes": {"factor_threads": shapes[0], "apply_cols": shapes[1]},
+        "tune": tune, "shapes": {"factor_threads": shapes[0], "factor_rank": shapes[1], "apply_cols": shapes[2]},
         "apply_ms": round(t_apply * 1e3, 3),
         "roofline": {"kernel": "ras_pml_batch_apply (k_apply + k_bprolong), complex64", "bound": "hbm",
                      "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",

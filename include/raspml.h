@@ -237,20 +237,24 @@ void ras_pml_destroy(ras_pml_handle* h);
 
 /* ---------------------------------------------------------------------------
  * Tile-shape tuning. Not an operation of the paper (which fixes no kernel
- * shapes): times each candidate shape of the factor launch (threads per CTA)
- * and of the apply launch (band columns per bulk copy) on the handle's own
- * subdomains with CUDA events, keeps the fastest for later calls, and leaves
- * the handle factored (every shape computes the same factors bit for bit).
- * The candidates: factor threads 128, 256, 512; apply columns 8, plus 4 and
- * 16 when factor_prec = 1. Synchronises the stream.
+ * shapes): times each candidate shape of the factor launch (threads per CTA
+ * and pivots per pass over the window) and of the apply launch (band columns
+ * per bulk copy) on the handle's own subdomains with CUDA events, keeps the
+ * fastest for later calls, and leaves the handle factored (every shape
+ * computes the same factors up to the rounding order of the rank-2 update).
+ * Factor candidates: 128, 256, 512 threads with one pivot per pass, 256 and
+ * 512 threads with two; apply columns 8, plus 4 and 16 when factor_prec = 1.
+ * Synchronises the stream.
  * ------------------------------------------------------------------------- */
 typedef struct {
   int32_t factor_threads;    /* chosen threads per factor CTA                 */
+  int32_t factor_rank;       /* chosen pivots per pass (1 or 2)               */
   int32_t apply_cols;        /* chosen band columns per bulk copy             */
   int32_t n_factor;          /* factor candidates timed (entries below)       */
   int32_t n_apply;           /* apply candidates timed                        */
-  int32_t factor_cand[4];
-  float   factor_ms[4];      /* median time of each factor candidate          */
+  int32_t factor_cand_threads[6];
+  int32_t factor_cand_rank[6];
+  float   factor_ms[6];      /* median time of each factor candidate          */
   int32_t apply_cand[4];
   float   apply_ms[4];       /* median time of each apply candidate (local
                                 solves of all subdomains)                     */
@@ -259,9 +263,10 @@ typedef struct {
 int ras_pml_tune(ras_pml_handle* h, ras_pml_tune_t* report);
 
 /* Sets the tile shapes directly (e.g. those a tuning run chose for another
- * handle of the same sizes): factor_threads 128, 256 or 512; apply_cols 8,
- * or 4 or 16 with factor_prec = 1. RASPML_EBADARG for other values. */
-int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int apply_cols);
+ * handle of the same sizes): factor_threads 128, 256 or 512; factor_rank 1
+ * or 2; apply_cols 8, or 4 or 16 with factor_prec = 1. RASPML_EBADARG for
+ * other values. */
+int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, int apply_cols);
 
 /* ---------------------------------------------------------------------------
  * Batched form: many independent problems in the same launches. The paper
@@ -303,6 +308,7 @@ typedef struct {
   int32_t bad_problem;     /* problem of a RASPML_EPIVOT subdomain, else -1 */
   int32_t bad_subdomain;   /* its subdomain index within that problem       */
   int32_t factor_threads;  /* tile shapes in use                            */
+  int32_t factor_rank;
   int32_t apply_cols;
   int32_t steps;           /* lockstep Arnoldi steps of the last solve      */
   int32_t cycles;          /* restart cycles of the last solve              */
@@ -331,7 +337,7 @@ int ras_pml_batch_factor(ras_pml_batch* h);
 
 /* ras_pml_tune and ras_pml_set_shapes on the batch's subdomains. */
 int ras_pml_batch_tune(ras_pml_batch* h, ras_pml_tune_t* report);
-int ras_pml_batch_set_shapes(ras_pml_batch* h, int factor_threads, int apply_cols);
+int ras_pml_batch_set_shapes(ras_pml_batch* h, int factor_threads, int factor_rank, int apply_cols);
 
 /* z = B_q^-1 r for every problem q (batch vectors, must not overlap). */
 int ras_pml_batch_apply(ras_pml_batch* h, const rp_c128* r_dev, rp_c128* z_dev);

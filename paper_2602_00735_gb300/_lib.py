@@ -47,8 +47,9 @@ class Timing(ctypes.Structure):
 
 
 class TuneReport(ctypes.Structure):
-    _fields_ = [("factor_threads", c_int32), ("apply_cols", c_int32), ("n_factor", c_int32),
-                ("n_apply", c_int32), ("factor_cand", c_int32 * 4), ("factor_ms", ctypes.c_float * 4),
+    _fields_ = [("factor_threads", c_int32), ("factor_rank", c_int32), ("apply_cols", c_int32),
+                ("n_factor", c_int32), ("n_apply", c_int32), ("factor_cand_threads", c_int32 * 6),
+                ("factor_cand_rank", c_int32 * 6), ("factor_ms", ctypes.c_float * 6),
                 ("apply_cand", c_int32 * 4), ("apply_ms", ctypes.c_float * 4)]
 
 
@@ -57,7 +58,8 @@ class BatchInfo(ctypes.Structure):
                 ("sum_local_n", c_int64), ("max_band", c_int32), ("factor_prec", c_int32),
                 ("factor_bytes", c_int64), ("apply_bytes", c_double), ("min_pivot_ratio", c_double),
                 ("factored", c_int32), ("bad_problem", c_int32), ("bad_subdomain", c_int32),
-                ("factor_threads", c_int32), ("apply_cols", c_int32), ("steps", c_int32), ("cycles", c_int32),
+                ("factor_threads", c_int32), ("factor_rank", c_int32), ("apply_cols", c_int32), ("steps", c_int32),
+                ("cycles", c_int32),
                 ("kcap", c_int32)]
 
 
@@ -93,8 +95,8 @@ def load() -> ctypes.CDLL:
     lib.ras_pml_destroy.argtypes = [H]
     lib.ras_pml_destroy.restype = None
     lib.ras_pml_tune.argtypes = [H, POINTER(TuneReport)]
-    lib.ras_pml_set_shapes.argtypes = [H, c_int, c_int]
-    lib.ras_pml_batch_set_shapes.argtypes = [H, c_int, c_int]
+    lib.ras_pml_set_shapes.argtypes = [H, c_int, c_int, c_int]
+    lib.ras_pml_batch_set_shapes.argtypes = [H, c_int, c_int, c_int]
     lib.ras_pml_batch_setup.argtypes = [POINTER(Params), c_int, c_void_p, POINTER(c_void_p)]
     lib.ras_pml_batch_info.argtypes = [H, POINTER(BatchInfo)]
     lib.ras_pml_batch_layout.argtypes = [H, c_void_p, c_void_p]

@@ -385,7 +385,7 @@ int ras_pml_factor(ras_pml_handle* h) {
   if (e == cudaSuccess) e = cudaMemsetAsync(h->Lrev, 0, (size_t)h->sum_l * esl, h->st);
   if (e == cudaSuccess) e = rp::launch_local_rows(h->p.factor_prec, h->geo_d, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
   if (e == cudaSuccess)
-    e = rp::launch_factor(h->p.factor_prec, h->tune.factor_threads, h->subs_d, h->nsub, h->max_b, Aloc, h->L, h->Lrev, h->dinv,
+    e = rp::launch_factor(h->p.factor_prec, h->tune.factor_threads, h->tune.factor_rank, h->subs_d, h->nsub, h->max_b, Aloc, h->L, h->Lrev, h->dinv,
                           h->pivstats, h->status, h->st);
   if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[1], h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
@@ -434,10 +434,11 @@ int ras_pml_tune(ras_pml_handle* h, ras_pml_tune_t* report) {
   return s;
 }
 
-int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int apply_cols) {
-  if (!h || !rp::factor_threads_valid(factor_threads) || !rp::apply_cols_valid(h->p.factor_prec, apply_cols))
+int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, int apply_cols) {
+  if (!h || !rp::factor_shape_valid(factor_threads, factor_rank) || !rp::apply_cols_valid(h->p.factor_prec, apply_cols))
     return RASPML_EBADARG;
   h->tune.factor_threads = factor_threads;
+  h->tune.factor_rank = factor_rank;
   h->tune.apply_cols = apply_cols;
   return RASPML_OK;
 }

@@ -316,6 +316,7 @@ int ras_pml_batch_info(const ras_pml_batch* h, ras_pml_batch_info_t* info) {
   info->bad_problem = h->bad_prob;
   info->bad_subdomain = h->bad_sub;
   info->factor_threads = h->tune.factor_threads;
+  info->factor_rank = h->tune.factor_rank;
   info->apply_cols = h->tune.apply_cols;
   info->steps = h->steps;
   info->cycles = h->cycles;
@@ -405,7 +406,7 @@ int ras_pml_batch_factor(ras_pml_batch* h) {
   c128* Aloc = nullptr;
   s = batch_local_rows(h, &Aloc);
   if (s != RASPML_OK) { dfree(Aloc); return s; }
-  cudaError_t e = rp::launch_factor(h->prec, h->tune.factor_threads, h->subs_d, h->nsub, h->max_b, Aloc, h->L,
+  cudaError_t e = rp::launch_factor(h->prec, h->tune.factor_threads, h->tune.factor_rank, h->subs_d, h->nsub, h->max_b, Aloc, h->L,
                                     h->Lrev, h->dinv, h->pivstats, h->status, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   dfree(Aloc);
@@ -451,10 +452,11 @@ int ras_pml_batch_tune(ras_pml_batch* h, ras_pml_tune_t* report) {
   return s;
 }
 
-int ras_pml_batch_set_shapes(ras_pml_batch* h, int factor_threads, int apply_cols) {
-  if (!h || !rp::factor_threads_valid(factor_threads) || !rp::apply_cols_valid(h->prec, apply_cols))
+int ras_pml_batch_set_shapes(ras_pml_batch* h, int factor_threads, int factor_rank, int apply_cols) {
+  if (!h || !rp::factor_shape_valid(factor_threads, factor_rank) || !rp::apply_cols_valid(h->prec, apply_cols))
     return RASPML_EBADARG;
   h->tune.factor_threads = factor_threads;
+  h->tune.factor_rank = factor_rank;
   h->tune.apply_cols = apply_cols;
   return RASPML_OK;
 }

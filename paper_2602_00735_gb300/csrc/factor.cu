@@ -188,50 +188,249 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
+// Two pivots per pass (rank-2 update), same window storage. Pass k (k even):
+//   A. thread t reads c_t = W(k+t, k) and forms column k+1 after step k,
+//      e_t = W(k+1+t, k+1) - c_{t+1} l_1 (e_b from the entering row k+b+1),
+//      then l_t = c_t / c_0 and l2_t = e_t / e_0, and writes both L columns;
+//      it stores c_i, e_{i-1} and l_j, l2_{j-1} side by side for phase B;
+//   B. W(k+i, k+j) -= c_i l_j + e_{i-1} l2_{j-1}, 2 <= j <= i <= b+1, where
+//      row k+b+1 (i = b+1, c_{b+1} = 0) is taken from the staged rows and
+//      lands in the slots of column k;
+//   C. row k+b+2 enters the slots of column k+1.
+// Each window entry is read and written once per two pivots, and a pass has
+// two barriers instead of four.
+template <typename R>
+struct __align__(4 * sizeof(R)) cx2 {
+  cx<R> a, b;
+};
+
+template <typename R, typename S, int NT>
+__global__ void __launch_bounds__(NT)
+    k_factor_ldlt2(const SubDesc* __restrict__ subs, const c128* __restrict__ Aloc, S* __restrict__ Lall,
+                   S* __restrict__ Lrev_all, cx<R>* __restrict__ dinv_all, double* __restrict__ pivstats,
+                   DevStatus* status) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const SubDesc sd = subs[blockIdx.x];
+  const int tid = threadIdx.x;
+  const int b = sd.b, bp = sd.bp, Wc = b + 1, npad = sd.npad;
+  const int nwin = Wc * (b + 2) / 2;
+  const int npairs = b * (b + 1) / 2;
+  cx<R>* W = reinterpret_cast<cx<R>*>(sm);
+  cx2<R>* CE = reinterpret_cast<cx2<R>*>(W + nwin + (nwin & 1));   // [Wc + 1], 2x aligned
+  cx2<R>* LL = CE + Wc + 1;
+  int2* pos = reinterpret_cast<int2*>(LL + Wc + 1);
+  S* L = Lall + sd.l_off;
+  S* Lr = Lrev_all + sd.l_off;
+  cx<R>* dv = dinv_all + sd.v_off;
+  const cx<R> zero = mk((R)0, (R)0);
+
+  for (int e = tid; e < nwin; e += NT) W[e] = zero;
+  if (tid <= b) {
+    const int t = tid, off = t * Wc - t * (t - 1) / 2;
+    pos[t] = make_int2(off, off + Wc - t);
+  }
+  __syncthreads();
+  if (tid <= b) {
+    const int r = tid;
+    cx<R> v[4];
+    aloc_row<R>(Aloc, sd, r, v);
+    const int ts[4] = {0, 1, b - 1, b};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = ts[q];
+      if (t <= r) W[t * Wc - t * (t - 1) / 2 + (r - t)] = row_entry<R>(v, t, b);
+    }
+  }
+  const int dp = NT / Wc, dq = NT % Wc;
+  const int p0 = tid / Wc, q0 = tid % Wc;
+
+  R dmin2 = (R)3e38, dmax2 = (R)0;
+  bool bad = false;
+  __shared__ cx<R> rows[2][32][4];   // rows k+b+1.. entering in the next steps, double-buffered
+  if (tid < 128) {
+    const int s = tid >> 2, e = tid & 3;
+    cx<R> v[4];
+    aloc_row<R>(Aloc, sd, b + 1 + s, v);
+    rows[0][s][e] = v[e];
+  }
+  __syncthreads();
+  for (int k = 0; k < npad; k += 2) {
+    const int2* pc = pos + ((k >> 1) & 1) * Wc;
+    int2* pn = pos + (((k >> 1) + 1) & 1) * Wc;
+    if ((k & 31) == 0 && tid < 128) {
+      // rows entering at steps k+32..k+63; that buffer's last readers were
+      // the passes before, which ended at the barrier before this point
+      const int s = tid >> 2, e = tid & 3;
+      cx<R> v[4];
+      aloc_row<R>(Aloc, sd, k + 32 + b + 1 + s, v);
+      rows[((k >> 5) + 1) & 1][s][e] = v[e];
+    }
+    const cx<R>(&raw1)[4] = rows[(k >> 5) & 1][k & 31];         // row k+b+1
+    const cx<R>(&raw2)[4] = rows[(k >> 5) & 1][(k & 31) + 1];   // row k+b+2
+    // A. both pivot columns
+    if (tid <= b) {
+      const int t = tid;
+      auto slot1 = [&](int tt) {   // slot of column k+1 on diagonal tt
+        const int2 ps = pc[tt];
+        return ps.x + 1 >= ps.y ? ps.x + 1 - (Wc - tt) : ps.x + 1;
+      };
+      const cx<R> d1 = W[pc[0].x];
+      const cx<R> c1 = W[pc[1].x];
+      const cx<R> di1 = crecip(d1);
+      const cx<R> l1 = c1 * di1;
+      const cx<R> d2 = fms(W[slot1(0)], c1, l1);
+      const cx<R> di2 = crecip(d2);
+      const cx<R> ct = W[pc[t].x];
+      cx<R> et;
+      if (t < b) {
+        et = fms(W[slot1(t)], W[pc[t + 1].x], l1);
+      } else {
+        cx<R> v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = raw1[i];
+        et = row_entry<R>(v, b, b);
+      }
+      if (t == 0) {
+        const R a1 = abs2(d1), a2 = abs2(d2);
+        if (!(a1 > (R)0) || !isfinite(a1) || !isfinite(di1.re) || !isfinite(di1.im)) bad = true;
+        if (!(a2 > (R)0) || !isfinite(a2) || !isfinite(di2.re) || !isfinite(di2.im)) bad = true;
+        dmin2 = fmin(dmin2, fmin(a1, a2));
+        dmax2 = fmax(dmax2, fmax(a1, a2));
+        dv[k] = di1;
+        dv[k + 1] = di2;
+        if (bp > b) {
+          L[(long long)k * bp + b] = st_entry<S, R>(zero);
+          L[(long long)(k + 1) * bp + b] = st_entry<S, R>(zero);
+        }
+      } else {
+        const cx<R> lt = ct * di1, l2t = et * di2;
+        const S ls = st_entry<S, R>(lt), l2s = st_entry<S, R>(l2t);
+        L[(long long)k * bp + (t - 1)] = ls;
+        if (k + t < npad) Lr[(long long)(npad - 1 - (k + t)) * bp + (t - 1)] = ls;
+        L[(long long)(k + 1) * bp + (t - 1)] = l2s;
+        if (k + 1 + t < npad) Lr[(long long)(npad - 2 - (k + t)) * bp + (t - 1)] = l2s;
+        if (t >= 2) {
+          CE[t].a = ct;
+          LL[t].a = lt;
+        }
+        CE[t + 1].b = et;
+        LL[t + 1].b = l2t;
+      }
+      if (t == b) {
+        CE[b + 1].a = zero;
+        LL[b + 1].a = zero;
+      }
+    }
+    __syncthreads();
+    // B. rank-2 update; pair p covers diagonal p (j' = 1..b-p) then diagonal
+    //    b-1-p (j' = 1..p+1), column offset j = j' + 1
+    {
+      int p = p0, q = q0;
+      for (int e = tid; e < npairs; e += NT) {
+        const int l1n = b - p;
+        int t, j;
+        if (q < l1n) { t = p; j = q + 2; } else { t = b - 1 - p; j = q - l1n + 2; }
+        const int i = j + t;
+        const int2 ps = pc[t];
+        int a = ps.x + j;
+        if (a >= ps.y) a -= Wc - t;
+        cx<R> w;
+        if (i <= b) {
+          w = W[a];
+        } else {
+          cx<R> v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = raw1[u];
+          w = row_entry<R>(v, b + 1 - j, b);
+        }
+        const cx2<R> ce = CE[i], ll = LL[j];
+        w = fms(w, ce.a, ll.a);
+        w = fms(w, ce.b, ll.b);
+        W[a] = w;
+        p += dp;
+        q += dq;
+        if (q >= Wc) { q -= Wc; ++p; }
+      }
+    }
+    // C. row k+b+2 enters the slots of column k+1 (untouched by B)
+    if (tid <= b) {
+      const int t = tid;
+      const int2 ps = pc[t];
+      const int m = Wc - t;
+      const int a = ps.x + 1 >= ps.y ? ps.x + 1 - m : ps.x + 1;
+      cx<R> v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = raw2[u];
+      W[a] = row_entry<R>(v, t, b);
+      int x = ps.x + 2;
+      while (x >= ps.y) x -= m;
+      pn[t] = make_int2(x, ps.y);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    pivstats[2 * blockIdx.x] = sqrt((double)dmin2);
+    pivstats[2 * blockIdx.x + 1] = sqrt((double)dmax2);
+    if (bad) atomicCAS(&status->pivot_bad_sub, -1, (int)blockIdx.x);
+  }
+}
+
 }  // namespace
 
 int max_band(int prec) { return prec == 0 ? kMaxBandC128 : kMaxBandC64; }
 
-size_t factor_smem_bytes(int b, int prec) {
-  size_t es = prec == 0 ? sizeof(c128) : sizeof(c64);   // window in the arithmetic type
-  size_t wc = (size_t)b + 1;
-  return (wc * (wc + 1) / 2 + 2 * wc) * es + 2 * wc * sizeof(int2);
+size_t factor_smem_bytes(int b, int prec, int rank) {
+  const size_t es = prec == 0 ? sizeof(c128) : sizeof(c64);   // window in the arithmetic type
+  const size_t wc = (size_t)b + 1, nwin = wc * (wc + 1) / 2;
+  if (rank == 2) return (nwin + (nwin & 1) + 4 * (wc + 1)) * es + 2 * wc * sizeof(int2);
+  return (nwin + 2 * wc) * es + 2 * wc * sizeof(int2);
 }
 
 namespace {
 
 template <typename R, typename S, int NT>
-cudaError_t launch_factor_t(size_t smem, const SubDesc* subs, int nsub, const c128* Aloc, void* L, void* Lrev,
-                            void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_factor_ldlt<R, S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_factor_ldlt<R, S, NT><<<nsub, NT, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (cx<R>*)dinv, pivstats, status);
+cudaError_t launch_factor_t(int rank, size_t smem, const SubDesc* subs, int nsub, const c128* Aloc, void* L,
+                            void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
+  cudaError_t e;
+  if (rank == 2) {
+    e = cudaFuncSetAttribute(k_factor_ldlt2<R, S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_factor_ldlt2<R, S, NT><<<nsub, NT, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (cx<R>*)dinv, pivstats, status);
+  } else {
+    e = cudaFuncSetAttribute(k_factor_ldlt<R, S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_factor_ldlt<R, S, NT><<<nsub, NT, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (cx<R>*)dinv, pivstats, status);
+  }
   return cudaGetLastError();
 }
 
 template <typename R, typename S>
-cudaError_t launch_factor_s(int threads, size_t smem, const SubDesc* subs, int nsub, const c128* Aloc, void* L,
-                            void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
+cudaError_t launch_factor_s(int threads, int rank, size_t smem, const SubDesc* subs, int nsub, const c128* Aloc,
+                            void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
   switch (threads) {
-    case 128: return launch_factor_t<R, S, 128>(smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
-    case 256: return launch_factor_t<R, S, 256>(smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
-    case 512: return launch_factor_t<R, S, 512>(smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+    case 128: return launch_factor_t<R, S, 128>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+    case 256: return launch_factor_t<R, S, 256>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+    case 512: return launch_factor_t<R, S, 512>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
   }
   return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-bool factor_threads_valid(int threads) { return threads == 128 || threads == 256 || threads == 512; }
+bool factor_shape_valid(int threads, int rank) {
+  return (threads == 128 || threads == 256 || threads == 512) && (rank == 1 || rank == 2);
+}
 
-cudaError_t launch_factor(int prec, int threads, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
-                          void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
-  const size_t smem = factor_smem_bytes(max_b, prec);
+cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, int nsub, int max_b,
+                          const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status,
+                          cudaStream_t st) {
+  if (!factor_shape_valid(threads, rank)) return cudaErrorInvalidValue;
+  const size_t smem = factor_smem_bytes(max_b, prec, rank);
   if (prec == 0)
-    return launch_factor_s<double, c128>(threads, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+    return launch_factor_s<double, c128>(threads, rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
   if (prec == 1)
-    return launch_factor_s<float, c64>(threads, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
-  return launch_factor_s<float, h2c>(threads, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+    return launch_factor_s<float, c64>(threads, rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+  return launch_factor_s<float, h2c>(threads, rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
 }
 
 }  // namespace rp

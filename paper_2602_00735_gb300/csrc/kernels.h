@@ -35,9 +35,10 @@ struct KState {
 // Tile shapes of the factor and apply launches (chosen by the tuner).
 struct Tune {
   int factor_threads = 256;   // threads per factor CTA: 128, 256, 512
+  int factor_rank = 2;        // pivots per pass over the window: 1 or 2
   int apply_cols = 8;         // band columns per bulk copy: 8 (4 or 16 with complex64 storage)
 };
-bool factor_threads_valid(int threads);
+bool factor_shape_valid(int threads, int rank);
 bool apply_cols_valid(int prec, int cols);
 
 // assembly.cu
@@ -48,9 +49,10 @@ cudaError_t launch_rhs(const Geo& g, const double* cen, const double* amp, int n
                        cudaStream_t st);
 
 // factor.cu
-size_t factor_smem_bytes(int b, int prec);
-cudaError_t launch_factor(int prec, int threads, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
-                          void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st);
+size_t factor_smem_bytes(int b, int prec, int rank);
+cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, int nsub, int max_b,
+                          const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status,
+                          cudaStream_t st);
 
 // apply.cu
 size_t apply_smem_bytes(int max_bp, int prec, int cols);

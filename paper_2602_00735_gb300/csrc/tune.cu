@@ -1,8 +1,8 @@
 // Tile-shape tuner: times each candidate shape of the factor launch (threads
-// per CTA) and of the local-solve launch (band columns per bulk copy) on the
-// caller's own subdomains with CUDA events on its stream, and returns the
-// fastest. Every factor shape performs the same operations on every window
-// entry in the same order, so the factors it leaves are those of any shape.
+// per CTA, pivots per pass) and of the local-solve launch (band columns per
+// bulk copy) on the caller's own subdomains with CUDA events on its stream,
+// and returns the fastest. The factor runs last with the chosen shape, so
+// the factors left behind are that shape's.
 #include <algorithm>
 
 #include "host.h"
@@ -28,19 +28,21 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
     return RASPML_ECUDA;
   }
   cudaError_t e = cudaSuccess;
-  const int fcand[3] = {128, 256, 512};
-  for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+  const int fthreads[5] = {128, 256, 512, 256, 512};
+  const int franks[5] = {1, 1, 1, 2, 2};
+  for (int c = 0; c < 5 && e == cudaSuccess; ++c) {
     std::vector<float> ms;
     for (int r = 0; r < reps && e == cudaSuccess; ++r) {
       e = cudaEventRecord(e0, t.st);
       if (e == cudaSuccess)
-        e = launch_factor(t.prec, fcand[c], t.subs, t.nsub, t.max_b, t.Aloc, t.L, t.Lrev, t.dinv, t.pivstats,
-                          t.status, t.st);
+        e = launch_factor(t.prec, fthreads[c], franks[c], t.subs, t.nsub, t.max_b, t.Aloc, t.L, t.Lrev, t.dinv,
+                          t.pivstats, t.status, t.st);
       if (e == cudaSuccess) e = cudaEventRecord(e1, t.st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       if (e == cudaSuccess) ms.push_back(ev_ms(e0, e1));
     }
-    rep.factor_cand[rep.n_factor] = fcand[c];
+    rep.factor_cand_threads[rep.n_factor] = fthreads[c];
+    rep.factor_cand_rank[rep.n_factor] = franks[c];
     rep.factor_ms[rep.n_factor++] = median(ms);
   }
   std::vector<int> acand{8};
@@ -72,9 +74,19 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
     if (rep.factor_ms[i] < rep.factor_ms[bf]) bf = i;
   for (int i = 1; i < rep.n_apply; ++i)
     if (rep.apply_ms[i] < rep.apply_ms[ba]) ba = i;
-  best->factor_threads = rep.factor_cand[bf];
+  // leave the factors of the chosen shape
+  cudaError_t e3 = launch_factor(t.prec, rep.factor_cand_threads[bf], rep.factor_cand_rank[bf], t.subs, t.nsub,
+                                 t.max_b, t.Aloc, t.L, t.Lrev, t.dinv, t.pivstats, t.status, t.st);
+  if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(t.st);
+  if (e3 != cudaSuccess) {
+    std::fprintf(stderr, "raspml: tune: %s\n", cudaGetErrorString(e3));
+    return RASPML_ECUDA;
+  }
+  best->factor_threads = rep.factor_cand_threads[bf];
+  best->factor_rank = rep.factor_cand_rank[bf];
   best->apply_cols = rep.n_apply > 0 ? rep.apply_cand[ba] : 8;
   rep.factor_threads = best->factor_threads;
+  rep.factor_rank = best->factor_rank;
   rep.apply_cols = best->apply_cols;
   if (report) *report = rep;
   return RASPML_OK;

@@ -28,8 +28,10 @@ def make_params(params: dict, factor_prec: int = 0, ortho: int = 0) -> _lib.Para
 
 
 def tune_dict(rep: _lib.TuneReport) -> dict:
-    return {"factor_threads": rep.factor_threads, "apply_cols": rep.apply_cols,
-            "factor_ms": {rep.factor_cand[i]: rep.factor_ms[i] for i in range(rep.n_factor)},
+    """The tuner's report; factor candidates keyed "<threads>x<rank>"."""
+    return {"factor_threads": rep.factor_threads, "factor_rank": rep.factor_rank, "apply_cols": rep.apply_cols,
+            "factor_ms": {f"{rep.factor_cand_threads[i]}x{rep.factor_cand_rank[i]}": rep.factor_ms[i]
+                          for i in range(rep.n_factor)},
             "apply_ms": {rep.apply_cand[i]: rep.apply_ms[i] for i in range(rep.n_apply)}}
 
 
@@ -99,8 +101,9 @@ class RasPml:
         _lib.check("ras_pml_tune", self.lib.ras_pml_tune(self._h, byref(rep)))
         return tune_dict(rep)
 
-    def set_shapes(self, factor_threads: int, apply_cols: int) -> None:
-        _lib.check("ras_pml_set_shapes", self.lib.ras_pml_set_shapes(self._h, int(factor_threads), int(apply_cols)))
+    def set_shapes(self, factor_threads: int, factor_rank: int, apply_cols: int) -> None:
+        _lib.check("ras_pml_set_shapes", self.lib.ras_pml_set_shapes(self._h, int(factor_threads), int(factor_rank),
+                                                                     int(apply_cols)))
 
     # -- operators -------------------------------------------------------------
     def apply(self, r: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:

@@ -110,9 +110,11 @@ def test_restarted_and_tuned_solve(pkg, probs):
     with pkg.BatchRasPml([w.params() for w in probs], factor_prec=1) as B:
         rep = B.tune()
         assert rep["factor_threads"] in (128, 256, 512) and rep["apply_cols"] in (4, 8, 16)
-        assert set(rep["factor_ms"]) == {128, 256, 512} and all(v > 0 for v in rep["factor_ms"].values())
+        assert set(rep["factor_ms"]) == {"128x1", "256x1", "512x1", "256x2", "512x2"}
+        assert all(v > 0 for v in rep["factor_ms"].values())
         inf = B.info()
-        assert (inf["factor_threads"], inf["apply_cols"]) == (rep["factor_threads"], rep["apply_cols"])
+        assert (inf["factor_threads"], inf["factor_rank"], inf["apply_cols"]) == \
+            (rep["factor_threads"], rep["factor_rank"], rep["apply_cols"])
         b = B.assemble_rhs(_sources(probs))
         x, it, relres, st = B.solve(b, rtol=1e-8, maxit=600, restart=15)
         assert st == 0 and np.all(relres <= 1e-8)

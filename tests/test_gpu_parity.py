@@ -211,3 +211,21 @@ def test_c64_fgmres_converges_to_fp64_solution(solver_cls, name, prec):
         x, it, relres, st = s.solve(b, rtol=1e-11, maxit=400)
         assert st == 0 and relres <= 1e-11
         assert rel(x.cpu().numpy(), u) <= 1e-9
+
+
+# ------------------------------------------------------------- tile shapes --
+# Every factor shape (threads per CTA, one or two pivots per pass) gives the
+# oracle's B^-1 at the precision's tolerance; two widths of subdomain (odd
+# and even half-bandwidths) on uneven boxes.
+
+@pytest.mark.parametrize("threads,rank", [(128, 1), (256, 1), (512, 1), (256, 2), (512, 2)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4), (2, 2e-2)])
+@pytest.mark.parametrize("name,kw", [("small", {"px": 3, "py": 5}), ("tiny3", {})])
+def test_factor_shapes_match_oracle(solver_cls, name, kw, prec, tol, threads, rank):
+    w = variant(name, **kw)
+    grid, A, R = oracle_problem(w)
+    with solver_cls(w.params(), factor_prec=prec) as s:
+        s.set_shapes(threads, rank, 8)
+        s.factor()
+        r = random_vector(grid.n, 4)
+        assert rel(s.apply(to_dev(r)).cpu().numpy(), R.apply(r)) <= tol
