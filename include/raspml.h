@@ -358,6 +358,33 @@ int ras_pml_batch_solve(ras_pml_batch* h, const rp_c128* b_dev, rp_c128* x_dev, 
 
 void ras_pml_batch_destroy(ras_pml_batch* h);
 
+/* ---------------------------------------------------------------------------
+ * Learned coarse correction. The paper has no learned component; this is an
+ * extra stage of the flexible GMRES: after z = B^-1 r, the residual it
+ * leaves, r1 = r - A z, is averaged onto an Nc x Nc coarse grid (pixel means
+ * in index space, two real channels), normalised to norm Nc, mapped by a
+ * 6-layer 3x3 convolutional network (channels 2-32-32-32-32-32-2, ReLU after
+ * the first five, zero padding; BF16 weights and activations, FP32
+ * accumulation, tensor cores), scaled back by gamma * ||R r1|| / Nc and
+ * interpolated bilinearly to the fine grid, where it is added to z.
+ * Parameters (FP32, ras_pml_net_param_count of them) are stored layer by
+ * layer as W[co][ci][3][3] followed by b[co].
+ * ------------------------------------------------------------------------- */
+typedef struct ras_pml_net ras_pml_net;
+
+/* Network for an Nc x Nc grid and batches of up to `cap` images, He-normal
+ * weights from `seed`, zero biases; work on `cuda_stream`. */
+int ras_pml_net_create(int Nc, int cap, uint64_t seed, void* cuda_stream, ras_pml_net** out);
+int ras_pml_net_param_count(const ras_pml_net* net);
+/* Host copies of all parameters (count = ras_pml_net_param_count). Setting
+ * them also resets the optimiser state. */
+int ras_pml_net_set_params(ras_pml_net* net, const float* params_host, int count);
+int ras_pml_net_get_params(const ras_pml_net* net, float* params_host, int count);
+/* y = net(x) for nimg <= cap images; x_dev and y_dev hold nimg x 2 x Nc x Nc
+ * FP32 values (image, channel, row, column). */
+int ras_pml_net_forward(ras_pml_net* net, const float* x_dev, float* y_dev, int nimg);
+void ras_pml_net_destroy(ras_pml_net* net);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,8 +19,10 @@ SYMBOLS = ("ras_pml_setup", "ras_pml_info", "ras_pml_assemble_rhs", "ras_pml_ass
            "ras_pml_destroy", "ras_pml_tune", "ras_pml_set_shapes", "ras_pml_batch_set_shapes",
            "ras_pml_batch_setup", "ras_pml_batch_info", "ras_pml_batch_layout", "ras_pml_batch_assemble_rhs",
            "ras_pml_batch_factor", "ras_pml_batch_tune", "ras_pml_batch_apply", "ras_pml_batch_matvec",
-           "ras_pml_batch_solve", "ras_pml_batch_destroy")
-VOID_SYMBOLS = ("ras_pml_error_string", "ras_pml_destroy", "ras_pml_batch_destroy")
+           "ras_pml_batch_solve", "ras_pml_batch_destroy",
+           "ras_pml_net_create", "ras_pml_net_param_count", "ras_pml_net_set_params", "ras_pml_net_get_params",
+           "ras_pml_net_forward", "ras_pml_net_destroy")
+VOID_SYMBOLS = ("ras_pml_error_string", "ras_pml_destroy", "ras_pml_batch_destroy", "ras_pml_net_destroy")
 
 
 class Params(ctypes.Structure):
@@ -108,6 +110,13 @@ def load() -> ctypes.CDLL:
     lib.ras_pml_batch_solve.argtypes = [H, c_void_p, c_void_p, c_double, c_int, c_int, c_void_p, c_void_p]
     lib.ras_pml_batch_destroy.argtypes = [H]
     lib.ras_pml_batch_destroy.restype = None
+    lib.ras_pml_net_create.argtypes = [c_int, c_int, ctypes.c_uint64, c_void_p, POINTER(c_void_p)]
+    lib.ras_pml_net_param_count.argtypes = [H]
+    lib.ras_pml_net_set_params.argtypes = [H, c_void_p, c_int]
+    lib.ras_pml_net_get_params.argtypes = [H, c_void_p, c_int]
+    lib.ras_pml_net_forward.argtypes = [H, c_void_p, c_void_p, c_int]
+    lib.ras_pml_net_destroy.argtypes = [H]
+    lib.ras_pml_net_destroy.restype = None
     for name in SYMBOLS:
         if name not in VOID_SYMBOLS:
             getattr(lib, name).restype = c_int

@@ -1,0 +1,330 @@
+// Learned coarse correction (an extra stage of the flexible GMRES; the paper
+// has no learned component): a 6-layer 3x3 convolutional network on an
+// Nc x Nc coarse grid, BF16 activations and weights with FP32 accumulation.
+//
+// k_conv_tc: one 3x3 convolution (zero padding) as an implicit GEMM on the
+//   5th-generation tensor cores. A CTA of 128 threads takes 128 consecutive
+//   pixels: D[128 x CO] = A[128 x 9CI] B[9CI x CO] with A the im2col rows of
+//   those pixels (K index = tap * CI + ci) and B the weights. A and B are
+//   staged in shared memory in the no-swizzle K-major core-matrix layout
+//   (8 rows x 16 bytes per core matrix; core matrices adjacent in K are
+//   LBO bytes apart, adjacent 8-row groups SBO bytes apart), one thread
+//   issues the K/16 tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulator in
+//   TMEM), tcgen05.commit signals an mbarrier, and each warp reads its 32
+//   accumulator rows back with tcgen05.ld for the epilogue (bias, ReLU or a
+//   ReLU mask, BF16 and/or FP32 store). The same kernel runs the backward
+//   data gradient with the transposed, tap-flipped weights.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rp {
+
+namespace {
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: no swizzle, LBO/SBO in bytes
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version of this architecture
+  return d;                 // base offset 0, layout type 0 (no swizzle)
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N and M as given
+constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 lanes x 16 columns of FP32 from TMEM (one row per thread)
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int kConvPix = 128;     // pixels per CTA (the MMA's M)
+constexpr int kTmemCols = 32;     // accumulator columns allocated (CO <= 32)
+
+template <int CI, int CO>
+struct ConvSmem {
+  static constexpr int K = 9 * CI;
+  static constexpr int A_BYTES = kConvPix * K * 2;
+  static constexpr int B_BYTES = CO * K * 2;
+  // room after A and B so that a descriptor read with LBO and SBO in either
+  // order stays inside the allocation
+  static constexpr int SLACK = 32 * 1024;
+  static constexpr int BYTES = A_BYTES + B_BYTES + SLACK + 64;
+};
+
+}  // namespace
+
+// in: NHWC BF16 [H*X][CI]; wt: B in core-matrix order ([K/8][CO/8][8][8]
+// BF16); bias: CO floats or null; mask: NHWC BF16 [H*X][CO] or null (output
+// multiplied by (mask > 0)); relu: apply max(., 0); outputs NHWC (BF16
+// and/or FP32, [H*X][CO]). blockIdx.y selects the image of a batch: every
+// pointer is offset by blockIdx.y times its per-image size.
+template <int CI, int CO>
+__global__ void __launch_bounds__(128)
+    k_conv_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wt,
+              const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask, int relu, int H, int X,
+              __nv_bfloat16* __restrict__ out_bf, float* __restrict__ out_f, DevStatus* status) {
+  using SM = ConvSmem<CI, CO>;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* A = sm;
+  unsigned char* B = sm + SM::A_BYTES;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + SM::A_BYTES + SM::B_BYTES + SM::SLACK);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long npix = (long long)H * X;
+  const long long img = blockIdx.y;
+  in += img * npix * CI;
+  if (mask) mask += img * npix * CO;
+  if (out_bf) out_bf += img * npix * CO;
+  if (out_f) out_f += img * npix * CO;
+  const long long p0 = (long long)blockIdx.x * kConvPix;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  // B: the weights are stored in core-matrix order already
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(wt);
+    uint4* dst = reinterpret_cast<uint4*>(B);
+    for (int i = tid; i < SM::B_BYTES / 16; i += 128) dst[i] = src[i];
+  }
+  // A: im2col of pixel p0 + tid, one 16-byte chunk (8 channels) at a time
+  {
+    const int m = tid;
+    const long long p = p0 + m;
+    const int y = (int)(p / X), x = (int)(p % X);
+    const bool live = p < npix;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+      const int sy = y + tap / 3 - 1, sx = x + tap % 3 - 1;
+      const bool ok = live && sy >= 0 && sy < H && sx >= 0 && sx < X;
+      const uint4* src = reinterpret_cast<const uint4*>(in + ((long long)sy * X + sx) * CI);
+#pragma unroll
+      for (int q = 0; q < CI / 8; ++q) {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (ok) v = src[q];
+        const int c = tap * (CI / 8) + q;   // K chunk
+        *reinterpret_cast<uint4*>(A + ((c * (kConvPix / 8) + (m >> 3)) * 128 + (m & 7) * 16)) = v;
+      }
+    }
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+    const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+    constexpr uint32_t lbo_a = (kConvPix / 8) * 128, lbo_b = (CO / 8) * 128;
+    constexpr uint32_t idesc = idesc_bf16(kConvPix, CO);
+#pragma unroll 1
+    for (int s = 0; s < SM::K / 16; ++s) {
+      const uint64_t ad = smem_desc(a0 + 2 * s * lbo_a, lbo_a, 128);
+      const uint64_t bd = smem_desc(b0 + 2 * s * lbo_b, lbo_b, 128);
+      tc_mma(tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
+    }
+    tc_commit(bar);
+  }
+  __syncwarp();
+  bool ok = mbar_wait_bounded(bar, 0);
+  if (!ok) {
+    // record the time-out; wait once more (bounded) for the MMAs in flight
+    if (tid == 0) atomicExch(&status->timeout, 1);
+    ok = mbar_wait_bounded(bar, 0);
+  }
+  tc_fence_after();
+  if (ok) {
+    const int m = warp * 32 + lane;
+    const long long p = p0 + m;
+#pragma unroll
+    for (int h = 0; h < CO / 16; ++h) {
+      float v[16];
+      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * 16), v);
+      if (p < npix) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int co = h * 16 + i;
+          float t = v[i] + (bias ? bias[co] : 0.f);
+          if (relu) t = fmaxf(t, 0.f);
+          if (mask && !(__bfloat162float(mask[p * CO + co]) > 0.f)) t = 0.f;
+          v[i] = t;
+        }
+        if (out_f) {
+          float4* o = reinterpret_cast<float4*>(out_f + p * CO + h * 16);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        }
+        if (out_bf) {
+          __nv_bfloat162 pk[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) pk[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+          uint4* o = reinterpret_cast<uint4*>(out_bf + p * CO + h * 16);
+          o[0] = *reinterpret_cast<uint4*>(&pk[0]);
+          o[1] = *reinterpret_cast<uint4*>(&pk[4]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Layout helpers
+// ---------------------------------------------------------------------------
+// Master parameters (FP32), layer by layer: W[co][ci][3][3] then b[co], the
+// real channel counts (2, 32, 32, 32, 32, 32, 2).
+constexpr int kLayers = 6;
+__host__ __device__ constexpr int ch_real(int i) { return (i == 0 || i == kLayers) ? 2 : 32; }
+__host__ __device__ constexpr int ch_pad(int i) { return (i == 0 || i == kLayers) ? 16 : 32; }
+
+// B tile (core-matrix order) of layer l, forward: n = co, k = tap*CI + ci.
+// Transposed (data gradient): n = ci, k = tap'*CO + co with tap' = 8 - tap.
+__global__ void k_prep_weights(const float* __restrict__ W, int cir, int cor, int cip, int cop, int transposed,
+                               __nv_bfloat16* __restrict__ tile) {
+  const int N = transposed ? cip : cop, CIk = transposed ? cop : cip, K = 9 * CIk;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * K) return;
+  // element e of the tile: chunk c, n-group g, row r, column q
+  const int q = e & 7, r = (e >> 3) & 7, rest = e >> 6;
+  const int g = rest % (N / 8), c = rest / (N / 8);
+  const int n = g * 8 + r, k = c * 8 + q;
+  const int tap = k / CIk, kc = k % CIk;
+  float v = 0.f;
+  if (!transposed) {
+    const int co = n, ci = kc;
+    if (co < cor && ci < cir) v = W[(co * cir + ci) * 9 + tap];
+  } else {
+    const int ci = n, co = kc;
+    if (co < cor && ci < cir) v = W[(co * cir + ci) * 9 + (8 - tap)];
+  }
+  tile[e] = __float2bfloat16_rn(v);
+}
+
+__global__ void k_pad_bias(const float* __restrict__ b, int cor, int cop, float* __restrict__ bp) {
+  const int i = threadIdx.x;
+  if (i < cop) bp[i] = i < cor ? b[i] : 0.f;
+}
+
+// NCHW FP32 (2 channels) -> NHWC BF16 with 16 channels (zeros beyond 2)
+__global__ void k_to_nhwc16(const float* __restrict__ x, long long npix, __nv_bfloat16* __restrict__ a) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long img = blockIdx.y;
+  if (p >= npix) return;
+  __nv_bfloat16* o = a + (img * npix + p) * 16;
+  const float* xi = x + img * 2 * npix;
+  o[0] = __float2bfloat16_rn(xi[p]);
+  o[1] = __float2bfloat16_rn(xi[npix + p]);
+#pragma unroll
+  for (int c = 2; c < 16; ++c) o[c] = __float2bfloat16_rn(0.f);
+}
+
+// NHWC FP32 (16 channels, first 2 used) -> NCHW FP32 (2 channels)
+__global__ void k_from_nhwc16(const float* __restrict__ y, long long npix, float* __restrict__ x) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long img = blockIdx.y;
+  if (p >= npix) return;
+  x[img * 2 * npix + p] = y[(img * npix + p) * 16];
+  x[img * 2 * npix + npix + p] = y[(img * npix + p) * 16 + 1];
+}
+
+template <int CI, int CO>
+cudaError_t conv_t(const __nv_bfloat16* in, const __nv_bfloat16* wt, const float* bias, const __nv_bfloat16* mask,
+                   int relu, int H, int X, int nimg, __nv_bfloat16* out_bf, float* out_f, DevStatus* status,
+                   cudaStream_t st) {
+  using SM = ConvSmem<CI, CO>;
+  cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::BYTES);
+  if (e != cudaSuccess) return e;
+  const long long npix = (long long)H * X;
+  dim3 grid((unsigned)((npix + kConvPix - 1) / kConvPix), (unsigned)nimg);
+  k_conv_tc<CI, CO><<<grid, 128, SM::BYTES, st>>>(in, wt, bias, mask, relu, H, X, out_bf, out_f, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_conv(int ci, int co, const void* in, const void* wt, const float* bias, const void* mask, int relu,
+                        int H, int X, int nimg, void* out_bf, float* out_f, DevStatus* status, cudaStream_t st) {
+  using bf = __nv_bfloat16;
+  if (ci == 16 && co == 32)
+    return conv_t<16, 32>((const bf*)in, (const bf*)wt, bias, (const bf*)mask, relu, H, X, nimg, (bf*)out_bf, out_f,
+                          status, st);
+  if (ci == 32 && co == 32)
+    return conv_t<32, 32>((const bf*)in, (const bf*)wt, bias, (const bf*)mask, relu, H, X, nimg, (bf*)out_bf, out_f,
+                          status, st);
+  if (ci == 32 && co == 16)
+    return conv_t<32, 16>((const bf*)in, (const bf*)wt, bias, (const bf*)mask, relu, H, X, nimg, (bf*)out_bf, out_f,
+                          status, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_prep_weights(const float* W, int l, int transposed, void* tile, cudaStream_t st) {
+  const int cip = ch_pad(l), cop = ch_pad(l + 1);
+  const int n = 9 * cip * cop;
+  k_prep_weights<<<(n + 255) / 256, 256, 0, st>>>(W, ch_real(l), ch_real(l + 1), cip, cop, transposed,
+                                                 (__nv_bfloat16*)tile);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pad_bias(const float* b, int l, float* bp, cudaStream_t st) {
+  k_pad_bias<<<1, 32, 0, st>>>(b, ch_real(l + 1), ch_pad(l + 1), bp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_nhwc16(const float* x, long long npix, int nimg, void* a, cudaStream_t st) {
+  dim3 grid((unsigned)((npix + 255) / 256), (unsigned)nimg);
+  k_to_nhwc16<<<grid, 256, 0, st>>>(x, npix, (__nv_bfloat16*)a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_nhwc16(const float* y, long long npix, int nimg, float* x, cudaStream_t st) {
+  dim3 grid((unsigned)((npix + 255) / 256), (unsigned)nimg);
+  k_from_nhwc16<<<grid, 256, 0, st>>>(y, npix, x);
+  return cudaGetLastError();
+}
+
+}  // namespace rp

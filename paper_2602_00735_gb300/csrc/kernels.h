@@ -158,3 +158,21 @@ cudaError_t launch_bcycle_start(const BStep& a, const c128* b, const c128* x, in
 cudaError_t launch_bcycle_end(const BStep& a, c128* x, cudaStream_t st);
 
 }  // namespace rp
+
+namespace rp {
+
+// ---------------------------------------------------------------------------
+// Learned coarse correction (cnn.cu): 3x3 convolutions on tensor cores
+// ---------------------------------------------------------------------------
+// in: NHWC BF16 [nimg][H*X][ci]; wt: B tile (core-matrix order); bias ci/co
+// padded channels; mask (NHWC BF16, co channels) multiplies the output by
+// (mask > 0); relu: max(., 0); outputs NHWC BF16 and/or FP32 with co channels.
+cudaError_t launch_conv(int ci, int co, const void* in, const void* wt, const float* bias, const void* mask, int relu,
+                        int H, int X, int nimg, void* out_bf, float* out_f, DevStatus* status, cudaStream_t st);
+// B tile of layer l from the FP32 master weights (transposed: data gradient)
+cudaError_t launch_prep_weights(const float* W, int l, int transposed, void* tile, cudaStream_t st);
+cudaError_t launch_pad_bias(const float* b, int l, float* bp, cudaStream_t st);
+cudaError_t launch_to_nhwc16(const float* x, long long npix, int nimg, void* a, cudaStream_t st);
+cudaError_t launch_from_nhwc16(const float* y, long long npix, int nimg, float* x, cudaStream_t st);
+
+}  // namespace rp
