@@ -383,6 +383,18 @@ int ras_pml_net_get_params(const ras_pml_net* net, float* params_host, int count
 /* y = net(x) for nimg <= cap images; x_dev and y_dev hold nimg x 2 x Nc x Nc
  * FP32 values (image, channel, row, column). */
 int ras_pml_net_forward(ras_pml_net* net, const float* x_dev, float* y_dev, int nimg);
+/* Loss L = (1/nimg) sum over images of mean over pixels and the two
+ * channels of (net(x) - t)^2 / 2 into *loss_host, and its gradient with
+ * respect to every parameter (kept on the device for
+ * ras_pml_net_adam_step; copied to grad_host, in the parameter layout, when
+ * that is not NULL). The backward pass: data gradients on the tensor cores
+ * (transposed, tap-flipped weights; the ReLU mask applied in the epilogue),
+ * weight gradients as FP32 sums over pixels. */
+int ras_pml_net_loss_grad(ras_pml_net* net, const float* x_dev, const float* t_dev, int nimg,
+                          double* loss_host, float* grad_host);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected) with the last
+ * gradients and learning rate lr. */
+int ras_pml_net_adam_step(ras_pml_net* net, float lr);
 void ras_pml_net_destroy(ras_pml_net* net);
 
 #ifdef __cplusplus

@@ -69,6 +69,52 @@ int net_forward_dev(ras_pml_net* n, int nimg) {
   return RASPML_OK;
 }
 
+// gradients of the mean loss over nimg images whose forward pass has run;
+// the output gradient is in g0 (16 channels)
+int net_backward_dev(ras_pml_net* n, int nimg) {
+  const int need = rp::wgrad_blocks(n->Nc, n->cap) * (32 * 32 * 9 + 32);
+  if (n->part_blocks < need) {
+    dfree(n->part);
+    int s = dalloc(&n->part, (size_t)need);
+    if (s != RASPML_OK) return s;
+    n->part_blocks = need;
+  }
+  void* g = n->g0;
+  void* gn = n->g1;
+  for (int l = kL - 1; l >= 0; --l) {
+    RP_CUDA(rp::launch_wgrad(l, n->act[l], g, n->Nc, n->Nc, nimg, n->part, n->grads + n->w_off[l], n->st));
+    if (l > 0) {
+      // gradient of layer l's input, masked by the ReLU that produced it
+      RP_CUDA(rp::launch_conv(cp(l + 1), cp(l), g, n->wd[l], nullptr, n->act[l], 0, n->Nc, n->Nc, nimg, gn, nullptr,
+                              n->status, n->st));
+      void* t = g;
+      g = gn;
+      gn = t;
+    }
+  }
+  return RASPML_OK;
+}
+
+// loss and gradients for x (NCHW FP32, device) against t; loss on the host
+int net_loss_grad_dev(ras_pml_net* n, const float* x, const float* t, int nimg, double* loss) {
+  RP_CUDA(rp::launch_to_nhwc16(x, n->npix, nimg, n->act[0], n->st));
+  int s = net_forward_dev(n, nimg);
+  if (s != RASPML_OK) return s;
+  int nparts = 0;
+  RP_CUDA(rp::launch_loss_grad(n->out, t, n->npix, nimg, n->g0, n->lossbuf, &nparts, n->st));
+  s = net_backward_dev(n, nimg);
+  if (s != RASPML_OK) return s;
+  if (loss) {
+    std::vector<double> lp(nparts);
+    RP_CUDA(cudaMemcpyAsync(lp.data(), n->lossbuf, sizeof(double) * nparts, cudaMemcpyDeviceToHost, n->st));
+    RP_CUDA(cudaStreamSynchronize(n->st));
+    double sum = 0.0;
+    for (double v : lp) sum += v;
+    *loss = sum;
+  }
+  return RASPML_OK;
+}
+
 // splitmix64 + Box-Muller: He-normal initial weights (host side)
 uint64_t splitmix(uint64_t& x) {
   uint64_t z = (x += 0x9E3779B97F4A7C15ull);
@@ -141,7 +187,7 @@ int ras_pml_net_create(int Nc, int cap, uint64_t seed, void* stream, ras_pml_net
   n->g1 = g1;
   NA(n->xin, (size_t)np * 2);
   NA(n->tgt, (size_t)np * 2);
-  NA(n->lossbuf, (size_t)1024);
+  NA(n->lossbuf, (size_t)((n->npix + 255) / 256 * cap));
   NA(n->status, (size_t)1);
 #undef NA
   // He-normal weights, zero biases
@@ -202,6 +248,30 @@ int ras_pml_net_forward(ras_pml_net* n, const float* x_dev, float* y_dev, int ni
   RP_CUDA(cudaMemcpyAsync(&stt, n->status, sizeof(stt), cudaMemcpyDeviceToHost, n->st));
   RP_CUDA(cudaStreamSynchronize(n->st));
   return stt.timeout ? RASPML_ETIMEOUT : RASPML_OK;
+}
+
+int ras_pml_net_loss_grad(ras_pml_net* n, const float* x_dev, const float* t_dev, int nimg, double* loss_host,
+                          float* grad_host) {
+  if (!n || !x_dev || !t_dev || nimg < 1 || nimg > n->cap || !loss_host) return RASPML_EBADARG;
+  cudaSetDevice(n->dev);
+  int s = net_loss_grad_dev(n, x_dev, t_dev, nimg, loss_host);
+  if (s != RASPML_OK) return s;
+  if (grad_host) {
+    RP_CUDA(cudaMemcpyAsync(grad_host, n->grads, sizeof(float) * n->nparam, cudaMemcpyDeviceToHost, n->st));
+  }
+  rp::DevStatus stt;
+  RP_CUDA(cudaMemcpyAsync(&stt, n->status, sizeof(stt), cudaMemcpyDeviceToHost, n->st));
+  RP_CUDA(cudaStreamSynchronize(n->st));
+  return stt.timeout ? RASPML_ETIMEOUT : RASPML_OK;
+}
+
+int ras_pml_net_adam_step(ras_pml_net* n, float lr) {
+  if (!n || !(lr > 0.f)) return RASPML_EBADARG;
+  cudaSetDevice(n->dev);
+  n->adam_t += 1;
+  RP_CUDA(rp::launch_adam(n->params, n->grads, n->m1, n->m2, n->nparam, lr, n->adam_t, n->st));
+  n->tiles_ok = false;
+  return RASPML_OK;
 }
 
 }  // extern "C"

@@ -327,4 +327,183 @@ cudaError_t launch_from_nhwc16(const float* y, long long npix, int nimg, float* 
   return cudaGetLastError();
 }
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Backward pieces
+// ---------------------------------------------------------------------------
+// Loss L = (1/nimg) sum_images mean_{pixel, channel<2} (out - t)^2 / 2 and its
+// gradient g = (out - t) / (2 npix nimg) on the first two of 16 channels
+// (BF16 NHWC); per-block partial sums of L in lossp.
+__global__ void k_loss_grad(const float* __restrict__ out, const float* __restrict__ t, long long npix, int nimg,
+                            __nv_bfloat16* __restrict__ g, double* __restrict__ lossp) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long img = blockIdx.y;
+  const double inv = 1.0 / (2.0 * (double)npix * nimg);
+  double l = 0.0;
+  if (p < npix) {
+    const float* o = out + (img * npix + p) * 16;
+    const float* ti = t + img * 2 * npix;
+    const float d0 = o[0] - ti[p], d1 = o[1] - ti[npix + p];
+    l = 0.5 * ((double)d0 * d0 + (double)d1 * d1) * inv;
+    __nv_bfloat16* go = g + (img * npix + p) * 16;
+    go[0] = __float2bfloat16_rn((float)(d0 * inv));
+    go[1] = __float2bfloat16_rn((float)(d1 * inv));
+#pragma unroll
+    for (int c = 2; c < 16; ++c) go[c] = __float2bfloat16_rn(0.f);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    lossp[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+constexpr int kWgRows = 8;   // image rows per weight-gradient block
+
+// Partial weight and bias gradients of one layer over kWgRows image rows:
+// dW[co][ci][tap] = sum_p g[p][co] a[p + tap - 4][ci], db[co] = sum_p g[p][co],
+// FP32. Thread (ci, group of four co) keeps 4 x 9 sums; the three input
+// rows around the current one and the gradient row are staged in shared
+// memory. Only the real channels are written, in the master layout.
+template <int CI, int CO>
+__global__ void __launch_bounds__(256)
+    k_wgrad(const __nv_bfloat16* __restrict__ a, const __nv_bfloat16* __restrict__ g, int H, int X, int cir,
+            int cor, float* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smw[];
+  __nv_bfloat16* as = reinterpret_cast<__nv_bfloat16*>(smw);   // [3][X + 2][CI]
+  __nv_bfloat16* gs = as + 3 * (X + 2) * CI;                    // [X][CO]
+  const int tid = threadIdx.x;
+  const int ci = tid % CI, cg = tid / CI;
+  const bool act = cg < CO / 4;
+  const long long npix = (long long)H * X;
+  const long long img = blockIdx.y;
+  a += img * npix * CI;
+  g += img * npix * CO;
+  float acc[4][9], bacc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    bacc[u] = 0.f;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[u][t] = 0.f;
+  }
+  const int y0 = blockIdx.x * kWgRows;
+  for (int y = y0; y < y0 + kWgRows && y < H; ++y) {
+    __syncthreads();
+    for (int e = tid; e < 3 * (X + 2) * CI; e += blockDim.x) {
+      const int c = e % CI, xx = (e / CI) % (X + 2) - 1, dy = e / (CI * (X + 2));
+      const int sy = y + dy - 1;
+      __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+      if (sy >= 0 && sy < H && xx >= 0 && xx < X) v = a[((long long)sy * X + xx) * CI + c];
+      as[e] = v;
+    }
+    for (int e = tid; e < X * CO; e += blockDim.x) gs[e] = g[(long long)y * X * CO + e];
+    __syncthreads();
+    if (act) {
+      for (int x = 0; x < X; ++x) {
+        float gv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) gv[u] = __bfloat162float(gs[x * CO + cg * 4 + u]);
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) {
+            const float av = __bfloat162float(as[(dy * (X + 2) + x + dx) * CI + ci]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u][dy * 3 + dx] = fmaf(gv[u], av, acc[u][dy * 3 + dx]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) bacc[u] += gv[u];
+      }
+    }
+  }
+  const int nw = cor * cir * 9;
+  float* out = part + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * (nw + cor);
+  if (act) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int co = cg * 4 + u;
+      if (co < cor && ci < cir) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) out[(co * cir + ci) * 9 + t] = acc[u][t];
+      }
+      if (co < cor && ci == 0) out[nw + co] = bacc[u];
+    }
+  }
+}
+
+// grad[i] = sum over blocks of part[b][i], i < count
+__global__ void k_sum_parts(const float* __restrict__ part, int nblocks, int count, float* __restrict__ grad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float s = 0.f;
+  for (int b = 0; b < nblocks; ++b) s += part[(long long)b * count + i];
+  grad[i] = s;
+}
+
+// Adam (bias-corrected moments) on the FP32 master parameters
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int n, float lr, float b1, float b2, float c1, float c2, float eps) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+template <int CI, int CO>
+cudaError_t wgrad_t(const void* a, const void* g, int H, int X, int nimg, int cir, int cor, float* part,
+                    cudaStream_t st) {
+  const size_t smem = (size_t)(3 * (X + 2) * CI + X * CO) * sizeof(__nv_bfloat16);
+  cudaError_t e = cudaFuncSetAttribute(k_wgrad<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((H + kWgRows - 1) / kWgRows), (unsigned)nimg);
+  k_wgrad<CI, CO><<<grid, 256, smem, st>>>((const __nv_bfloat16*)a, (const __nv_bfloat16*)g, H, X, cir, cor, part);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int wgrad_blocks(int H, int nimg) { return ((H + kWgRows - 1) / kWgRows) * nimg; }
+
+cudaError_t launch_loss_grad(const float* out, const float* t, long long npix, int nimg, void* g, double* lossp,
+                             int* nparts, cudaStream_t st) {
+  dim3 grid((unsigned)((npix + 255) / 256), (unsigned)nimg);
+  *nparts = (int)(grid.x * grid.y);
+  k_loss_grad<<<grid, 256, 0, st>>>(out, t, npix, nimg, (__nv_bfloat16*)g, lossp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wgrad(int l, const void* a, const void* g, int H, int X, int nimg, float* part, float* grad,
+                         cudaStream_t st) {
+  const int cir = ch_real(l), cor = ch_real(l + 1);
+  cudaError_t e;
+  if (l == 0)
+    e = wgrad_t<16, 32>(a, g, H, X, nimg, cir, cor, part, st);
+  else if (l == kLayers - 1)
+    e = wgrad_t<32, 16>(a, g, H, X, nimg, cir, cor, part, st);
+  else
+    e = wgrad_t<32, 32>(a, g, H, X, nimg, cir, cor, part, st);
+  if (e != cudaSuccess) return e;
+  const int count = cor * cir * 9 + cor;
+  k_sum_parts<<<(count + 255) / 256, 256, 0, st>>>(part, wgrad_blocks(H, nimg), count, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, long long t, cudaStream_t st) {
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+  k_adam<<<(n + 255) / 256, 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, c1, c2, 1e-8f);
+  return cudaGetLastError();
+}
+
 }  // namespace rp

@@ -174,5 +174,14 @@ cudaError_t launch_prep_weights(const float* W, int l, int transposed, void* til
 cudaError_t launch_pad_bias(const float* b, int l, float* bp, cudaStream_t st);
 cudaError_t launch_to_nhwc16(const float* x, long long npix, int nimg, void* a, cudaStream_t st);
 cudaError_t launch_from_nhwc16(const float* y, long long npix, int nimg, float* x, cudaStream_t st);
+// loss of the last layer's output against t (NCHW, 2 channels), its gradient
+// (BF16 NHWC, 16 channels); *nparts partial sums written to lossp
+cudaError_t launch_loss_grad(const float* out, const float* t, long long npix, int nimg, void* g, double* lossp,
+                             int* nparts, cudaStream_t st);
+int wgrad_blocks(int H, int nimg);
+// weight and bias gradients of layer l (master layout) from its input a and output gradient g
+cudaError_t launch_wgrad(int l, const void* a, const void* g, int H, int X, int nimg, float* part, float* grad,
+                         cudaStream_t st);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, long long t, cudaStream_t st);
 
 }  // namespace rp

@@ -8,7 +8,7 @@ from a list of (W, b) arrays.
 """
 from __future__ import annotations
 
-from ctypes import byref, c_void_p
+from ctypes import byref, c_double, c_void_p
 
 import numpy as np
 import torch
@@ -70,6 +70,22 @@ class Net:
         _lib.check("ras_pml_net_forward", self.lib.ras_pml_net_forward(
             self._h, c_void_p(x.data_ptr()), c_void_p(y.data_ptr()), int(x.shape[0])))
         return y
+
+    def loss_grad(self, x: torch.Tensor, t: torch.Tensor, want_grad: bool = True):
+        """(loss, gradient vector or None) of the mean loss over the images of x against t."""
+        for a in (x, t):
+            if not (a.is_cuda and a.dtype == torch.float32 and a.is_contiguous()
+                    and tuple(a.shape[1:]) == (2, self.Nc, self.Nc)):
+                raise ValueError("expected contiguous cuda float32 tensors (nimg, 2, Nc, Nc)")
+        loss = c_double()
+        g = np.zeros(self.nparam, dtype=np.float32) if want_grad else None
+        _lib.check("ras_pml_net_loss_grad", self.lib.ras_pml_net_loss_grad(
+            self._h, c_void_p(x.data_ptr()), c_void_p(t.data_ptr()), int(x.shape[0]), byref(loss),
+            g.ctypes.data_as(c_void_p) if want_grad else None))
+        return loss.value, g
+
+    def adam_step(self, lr: float) -> None:
+        _lib.check("ras_pml_net_adam_step", self.lib.ras_pml_net_adam_step(self._h, float(lr)))
 
     def close(self) -> None:
         if getattr(self, "_h", None) and self._h.value:
