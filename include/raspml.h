@@ -395,7 +395,38 @@ int ras_pml_net_loss_grad(ras_pml_net* net, const float* x_dev, const float* t_d
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected) with the last
  * gradients and learning rate lr. */
 int ras_pml_net_adam_step(ras_pml_net* net, float lr);
+/* Output scale gamma of the correction (set by ras_pml_net_train). */
+int ras_pml_net_set_gamma(ras_pml_net* net, double gamma);
+double ras_pml_net_get_gamma(const ras_pml_net* net);
+/* Trains the network on residual/error pairs the method itself generates on
+ * the handle's problem: for each of nrhs load vectors (1-8 Gaussian sources
+ * of width 0.4 pi / k at random points of Omega_int, from `seed`) the
+ * converged solution x* (FGMRES, rtol 1e-9) and, for every m in m_list, the
+ * FGMRES iterate x_m after m directions give the pair (r_m = b - A x_m,
+ * e_m = x* - x_m). Inputs restrict(r_m) Nc / ||restrict(r_m)||, targets
+ * restrict(e_m) Nc / (gamma ||restrict(r_m)||) with gamma the median of
+ * ||restrict(e_m)|| / ||restrict(r_m)||; then `epochs` passes of Adam (rate lr)
+ * over shuffled minibatches of up to `cap` pairs. loss_hist_host receives the
+ * mean loss of every epoch, *gamma_out (may be NULL) gamma. Detaches any
+ * network from the handle while generating pairs. Synchronises. */
+int ras_pml_net_train(ras_pml_net* net, ras_pml_handle* h, int nrhs, const int32_t* m_list, int nm, int epochs,
+                      float lr, uint64_t seed, float* loss_hist_host, double* gamma_out);
 void ras_pml_net_destroy(ras_pml_net* net);
+
+/* Attaches a network as the learned stage of helmholtz_solve on this handle
+ * (NULL detaches): every preconditioned direction becomes
+ * z_j = z1 + alpha c, z1 = B^-1 v_j, c = c(r1) the correction of the
+ * residual r1 = v_j - A z1 described above, and alpha = <A c, r1> / ||A c||^2
+ * the step that minimises ||r1 - alpha A c|| (so the stage never increases
+ * that residual); the flexible GMRES absorbs the nonlinearity. Costs two
+ * more SpMVs and two inner products per direction. The net must live as long as it is attached; Nc must not
+ * exceed the unknowns per grid row or column. */
+int ras_pml_attach_net(ras_pml_handle* h, ras_pml_net* net);
+/* z += c(r): the learned correction of a fine residual r on the handle's
+ * grid (n complex128 each, device, not overlapping). Synchronises. */
+int ras_pml_net_correct(ras_pml_handle* h, ras_pml_net* net, const rp_c128* r_dev, rp_c128* z_dev);
+/* The handle's parameters (ovlp_cells and pml_cells as resolved). */
+int ras_pml_get_params(const ras_pml_handle* h, ras_pml_params* out);
 
 #ifdef __cplusplus
 }

@@ -21,8 +21,11 @@ SYMBOLS = ("ras_pml_setup", "ras_pml_info", "ras_pml_assemble_rhs", "ras_pml_ass
            "ras_pml_batch_factor", "ras_pml_batch_tune", "ras_pml_batch_apply", "ras_pml_batch_matvec",
            "ras_pml_batch_solve", "ras_pml_batch_destroy",
            "ras_pml_net_create", "ras_pml_net_param_count", "ras_pml_net_set_params", "ras_pml_net_get_params",
-           "ras_pml_net_forward", "ras_pml_net_loss_grad", "ras_pml_net_adam_step", "ras_pml_net_destroy")
-VOID_SYMBOLS = ("ras_pml_error_string", "ras_pml_destroy", "ras_pml_batch_destroy", "ras_pml_net_destroy")
+           "ras_pml_net_forward", "ras_pml_net_loss_grad", "ras_pml_net_adam_step", "ras_pml_net_set_gamma",
+           "ras_pml_net_get_gamma", "ras_pml_net_train", "ras_pml_net_destroy", "ras_pml_attach_net",
+           "ras_pml_get_params", "ras_pml_net_correct")
+VOID_SYMBOLS = ("ras_pml_error_string", "ras_pml_destroy", "ras_pml_batch_destroy", "ras_pml_net_destroy",
+                "ras_pml_net_get_gamma")
 
 
 class Params(ctypes.Structure):
@@ -117,6 +120,14 @@ def load() -> ctypes.CDLL:
     lib.ras_pml_net_forward.argtypes = [H, c_void_p, c_void_p, c_int]
     lib.ras_pml_net_loss_grad.argtypes = [H, c_void_p, c_void_p, c_int, POINTER(c_double), c_void_p]
     lib.ras_pml_net_adam_step.argtypes = [H, ctypes.c_float]
+    lib.ras_pml_net_set_gamma.argtypes = [H, c_double]
+    lib.ras_pml_net_get_gamma.argtypes = [H]
+    lib.ras_pml_net_get_gamma.restype = c_double
+    lib.ras_pml_net_train.argtypes = [H, H, c_int, c_void_p, c_int, c_int, ctypes.c_float, ctypes.c_uint64, c_void_p,
+                                      POINTER(c_double)]
+    lib.ras_pml_attach_net.argtypes = [H, H]
+    lib.ras_pml_get_params.argtypes = [H, POINTER(Params)]
+    lib.ras_pml_net_correct.argtypes = [H, H, c_void_p, c_void_p]
     lib.ras_pml_net_destroy.argtypes = [H]
     lib.ras_pml_net_destroy.restype = None
     for name in SYMBOLS:

@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "host.h"
+#include "net_internal.h"
 
 using rp::c128;
 using rp::c64;
@@ -23,6 +23,8 @@ struct ras_pml_handle {
   rp::Geo geo{};
   rp::Geo* geo_d = nullptr;      // the same geometry in device memory
   rp::Tune tune{};               // tile shapes of the factor and apply launches
+  ras_pml_net* net = nullptr;    // learned coarse-correction stage (optional)
+  c128 *lc = nullptr, *lac = nullptr, *lhv = nullptr;   // its correction, A times it, two inner products
   std::vector<SubDesc> subs_h;
   SubDesc* subs_d = nullptr;
   int nsub = 0, max_b = 0, max_bp = 0, max_npad = 0, max_n = 0;
@@ -244,6 +246,7 @@ void ras_pml_destroy(ras_pml_handle* h) {
   dfree(h->partial); dfree(h->hbuf); dfree(h->cs); dfree(h->hist); dfree(h->scal); dfree(h->kst);
   dfree(h->wdf);
   dfree(h->tmp_b); dfree(h->tmp_x); dfree(h->tmp_r);
+  dfree(h->lc); dfree(h->lac); dfree(h->lhv);
   if (h->kst_host) cudaFreeHost(h->kst_host);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
@@ -443,6 +446,35 @@ int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, i
   return RASPML_OK;
 }
 
+int ras_pml_attach_net(ras_pml_handle* h, ras_pml_net* net) {
+  if (!h) return RASPML_EBADARG;
+  if (net && (rp::net_grid(net) > h->geo.nx || rp::net_grid(net) > h->geo.ny)) return RASPML_EBADARG;
+  if (net && !h->lc) {
+    cudaSetDevice(h->dev);
+    RP_ALLOC(h->lc, (size_t)h->n);
+    RP_ALLOC(h->lac, (size_t)h->n);
+    RP_ALLOC(h->lhv, (size_t)2);
+  }
+  h->net = net;
+  return RASPML_OK;
+}
+
+int ras_pml_net_correct(ras_pml_handle* h, ras_pml_net* net, const rp_c128* r, rp_c128* z) {
+  if (!h || !net || !r || !z || (const void*)r == (const void*)z) return RASPML_EBADARG;
+  if (rp::net_grid(net) > h->geo.nx || rp::net_grid(net) > h->geo.ny) return RASPML_EBADARG;
+  cudaSetDevice(h->dev);
+  const int s = rp::net_correct(net, (const c128*)r, (c128*)z, h->geo.nx, h->geo.ny, nullptr, h->st);
+  if (s != RASPML_OK) return s;
+  RP_CUDA(cudaStreamSynchronize(h->st));
+  return RASPML_OK;
+}
+
+int ras_pml_get_params(const ras_pml_handle* h, ras_pml_params* out) {
+  if (!h || !out) return RASPML_EBADARG;
+  *out = h->p;
+  return RASPML_OK;
+}
+
 int ras_pml_apply(ras_pml_handle* h, const rp_c128* r, rp_c128* z) {
   if (!h || !r || !z || (const void*)r == (const void*)z) return RASPML_EBADARG;
   if (!h->factored) return RASPML_ESTATE;
@@ -554,6 +586,20 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
         if (h->timing) RP_CUDA(cudaEventRecord(evj[0], st));
         RP_CUDA(rp::launch_apply(h->p.factor_prec, h->tune.apply_cols, h->geo, h->geo_d, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev,
                                  h->dinv, vj, h->Y, zj, h->kst, h->status, st, dfbasis));
+        if (h->net) {
+          // learned stage: c = correction of r1 = v_j - A z_j (r1 held in w), then
+          // z_j += alpha c with the alpha minimising ||r1 - alpha A c||
+          RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, vj, w, h->kst, st, dfbasis));
+          RP_CUDA(cudaMemsetAsync(h->lc, 0, sizeof(c128) * n, st));
+          const int cs = rp::net_correct(h->net, w, h->lc, h->geo.nx, h->geo.ny, h->kst, st);
+          if (cs != RASPML_OK) return cs;
+          RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, h->lc, nullptr, h->lac, h->kst, st));
+          RP_CUDA(rp::launch_dots(h->lac, n, 1, w, n, h->partial, h->kst, 0, st));
+          RP_CUDA(rp::launch_dots_finish(h->partial, 1, h->lhv, 0, h->kst, 0, st));
+          RP_CUDA(rp::launch_dots(h->lac, n, 1, h->lac, n, h->partial, h->kst, 0, st));
+          RP_CUDA(rp::launch_dots_finish(h->partial, 1, h->lhv + 1, 0, h->kst, 0, st));
+          RP_CUDA(rp::launch_mr_axpy(zj, h->lc, h->lhv, n, h->kst, st));
+        }
         if (h->timing) RP_CUDA(cudaEventRecord(evj[1], st));
         RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, nullptr, w, h->kst, st));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[2], st));

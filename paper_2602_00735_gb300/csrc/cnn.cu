@@ -506,4 +506,137 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, flo
   return cudaGetLastError();
 }
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Coarse grid transfers (fine unknowns nx x ny, x fastest; pixel (I, J) owns
+// the nodes with floor(i Nc / nx) = I, floor(j Nc / ny) = J)
+// ---------------------------------------------------------------------------
+constexpr int kRT = 256;
+
+__global__ void k_restrict(const c128* __restrict__ r, int nx, int ny, int Nc, float* __restrict__ out,
+                           double* __restrict__ partial, const KState* __restrict__ kst) {
+  if (kst != nullptr && kst->stop) return;
+  const int pix = blockIdx.x * kRT + threadIdx.x;
+  const int npix = Nc * Nc;
+  double ss = 0.0;
+  if (pix < npix) {
+    const int I = pix % Nc, J = pix / Nc;
+    const int i0 = (int)(((long long)I * nx + Nc - 1) / Nc), i1 = (int)(((long long)(I + 1) * nx + Nc - 1) / Nc);
+    const int j0 = (int)(((long long)J * ny + Nc - 1) / Nc), j1 = (int)(((long long)(J + 1) * ny + Nc - 1) / Nc);
+    double re = 0.0, im = 0.0;
+    for (int j = j0; j < j1; ++j)
+      for (int i = i0; i < i1; ++i) {
+        const c128 v = r[(long long)j * nx + i];
+        re += v.re;
+        im += v.im;
+      }
+    const double inv = 1.0 / ((double)(i1 - i0) * (j1 - j0));
+    re *= inv;
+    im *= inv;
+    out[pix] = (float)re;
+    out[npix + pix] = (float)im;
+    ss = re * re + im * im;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  __shared__ double red[kRT / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kRT / 32; ++w) t += red[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_normalise(float* __restrict__ out, int Nc, const double* __restrict__ partial, int nparts,
+                            double* __restrict__ s_dev, const KState* __restrict__ kst) {
+  if (kst != nullptr && kst->stop) return;
+  __shared__ double sh;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < nparts; ++b) t += partial[b];
+    sh = sqrt(t);
+    if (blockIdx.x == 0) *s_dev = sh;
+  }
+  __syncthreads();
+  const double s = sh;
+  const float f = s > 0.0 ? (float)((double)Nc / s) : 0.f;
+  const int n = 2 * Nc * Nc;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] *= f;
+}
+
+__device__ __forceinline__ void bilin_1d(int i, int n, int Nc, int& i0, float& w) {
+  float u = ((float)i + 0.5f) * (float)Nc / (float)n - 0.5f;
+  u = fminf(fmaxf(u, 0.f), (float)(Nc - 1));
+  i0 = min((int)floorf(u), Nc - 2);
+  w = u - (float)i0;
+}
+
+__global__ void k_prolong_add(const float* __restrict__ out16, int Nc, int nx, int ny, const double* __restrict__ s_dev,
+                              double gamma, c128* __restrict__ z, const KState* __restrict__ kst) {
+  if (kst != nullptr && kst->stop) return;
+  const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= (long long)nx * ny) return;
+  const double s = *s_dev;
+  if (!(s > 0.0)) return;
+  const int i = (int)(r % nx), j = (int)(r / nx);
+  int I0, J0;
+  float wx, wy;
+  bilin_1d(i, nx, Nc, I0, wx);
+  bilin_1d(j, ny, Nc, J0, wy);
+  const float* a = out16 + ((long long)J0 * Nc + I0) * 16;
+  const float* b = a + 16;
+  const float* c = a + (long long)Nc * 16;
+  const float* d = c + 16;
+  const float v0 = (1.f - wy) * ((1.f - wx) * a[0] + wx * b[0]) + wy * ((1.f - wx) * c[0] + wx * d[0]);
+  const float v1 = (1.f - wy) * ((1.f - wx) * a[1] + wx * b[1]) + wy * ((1.f - wx) * c[1] + wx * d[1]);
+  const double f = gamma * s / Nc;
+  z[r] = z[r] + mk(f * v0, f * v1);
+}
+
+__global__ void k_scale_f32(float* __restrict__ v, long long n, float f) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) v[i] *= f;
+}
+
+__global__ void k_csub(const c128* __restrict__ a, const c128* __restrict__ b, c128* __restrict__ o, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) o[i] = a[i] - b[i];
+}
+
+}  // namespace
+
+int restrict_blocks(int Nc) { return (Nc * Nc + kRT - 1) / kRT; }
+
+cudaError_t launch_restrict(const c128* r, int nx, int ny, int Nc, float* out, double* partial, const KState* kst,
+                            cudaStream_t st) {
+  k_restrict<<<restrict_blocks(Nc), kRT, 0, st>>>(r, nx, ny, Nc, out, partial, kst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalise(float* out, int Nc, const double* partial, double* s_dev, const KState* kst,
+                             cudaStream_t st) {
+  k_normalise<<<64, 256, 0, st>>>(out, Nc, partial, restrict_blocks(Nc), s_dev, kst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(const float* out16, int Nc, int nx, int ny, const double* s_dev, double gamma, c128* z,
+                               const KState* kst, cudaStream_t st) {
+  const long long n = (long long)nx * ny;
+  k_prolong_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out16, Nc, nx, ny, s_dev, gamma, z, kst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_f32(float* v, long long n, float f, cudaStream_t st) {
+  k_scale_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, n, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_csub(const c128* a, const c128* b, c128* out, long long n, cudaStream_t st) {
+  k_csub<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, out, n);
+  return cudaGetLastError();
+}
+
 }  // namespace rp

@@ -71,7 +71,8 @@ cudaError_t launch_apply(int prec, int cols, const Geo& g, const Geo* geos, cons
 
 // krylov.cu
 cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, const c128* CS, const c128* CSW,
-                        const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st);
+                        const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st,
+                        bool bsub_df = false);
 int dot_blocks();
 cudaError_t launch_dots(const c128* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
                         const KState* kst, int gate, cudaStream_t st);
@@ -97,6 +98,8 @@ cudaError_t launch_reorth_decide(KState* kst, c128* hcol, int j, double eta2, cu
 cudaError_t launch_backsolve(const c128* H, int ldh, const c128* gvec, const KState* kst, c128* y,
                              cudaStream_t st);
 cudaError_t launch_axpy_state(c128* x, const c128* v, long long n, cudaStream_t st);
+// z += (hv[0] / hv[1]) c, skipped when hv[1] = 0 or kst->stop
+cudaError_t launch_mr_axpy(c128* z, const c128* c, const c128* hv, long long n, const KState* kst, cudaStream_t st);
 
 }  // namespace rp
 
@@ -183,5 +186,18 @@ int wgrad_blocks(int H, int nimg);
 cudaError_t launch_wgrad(int l, const void* a, const void* g, int H, int X, int nimg, float* part, float* grad,
                          cudaStream_t st);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, long long t, cudaStream_t st);
+// coarse grid transfers of the learned stage (kernels skip when kst->stop)
+int restrict_blocks(int Nc);
+// out (NCHW FP32, 2 channels) = pixel means of r; partial sums of their squares
+cudaError_t launch_restrict(const c128* r, int nx, int ny, int Nc, float* out, double* partial, const KState* kst,
+                            cudaStream_t st);
+// s = ||out|| from the partials into *s_dev; out *= Nc / s (zero when s = 0)
+cudaError_t launch_normalise(float* out, int Nc, const double* partial, double* s_dev, const KState* kst,
+                             cudaStream_t st);
+// z += gamma * s / Nc * bilinear(first two channels of out16 (NHWC, 16 channels))
+cudaError_t launch_prolong_add(const float* out16, int Nc, int nx, int ny, const double* s_dev, double gamma, c128* z,
+                               const KState* kst, cudaStream_t st);
+cudaError_t launch_scale_f32(float* v, long long n, float f, cudaStream_t st);
+cudaError_t launch_csub(const c128* a, const c128* b, c128* out, long long n, cudaStream_t st);
 
 }  // namespace rp

@@ -49,9 +49,10 @@ __device__ __forceinline__ c128 block_sum(c128 v) {
   return t;  // valid in thread 0
 }
 
+// y = A x, or y = bsub - A x (bsub complex128, or double-float when bdf)
 __global__ void k_spmv(long long n, int nx, const c128* __restrict__ D, const c128* __restrict__ CW,
                        const c128* __restrict__ CS, const c128* __restrict__ CSW, const c128* __restrict__ x,
-                       const c128* __restrict__ bsub, c128* __restrict__ y, const KState* __restrict__ kst) {
+                       const c128* __restrict__ bsub, int bdf, c128* __restrict__ y, const KState* __restrict__ kst) {
   if (kst != nullptr && kst->stop) return;
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (r >= n) return;
@@ -64,7 +65,18 @@ __global__ void k_spmv(long long n, int nx, const c128* __restrict__ D, const c1
   if (r >= nx + 1) a1 = fmac(a1, CSW[r], x[r - nx - 1]);
   if (r + nx + 1 < n) a0 = fmac(a0, CSW[r + nx + 1], x[r + nx + 1]);
   const c128 acc = a0 + a1;
-  y[r] = bsub ? bsub[r] - acc : acc;
+  if (bsub) {
+    c128 bv;
+    if (bdf) {
+      const dfc d = reinterpret_cast<const dfc*>(bsub)[r];
+      bv = mk(df_to_d(d.rh, d.rl), df_to_d(d.ih, d.il));
+    } else {
+      bv = bsub[r];
+    }
+    y[r] = bv - acc;
+  } else {
+    y[r] = acc;
+  }
 }
 
 // partial[c * gridDim.x + blk] = sum over the block's rows of conj(V_c) w
@@ -374,6 +386,18 @@ __global__ void k_axpy(c128* __restrict__ x, const c128* __restrict__ v, long lo
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) x[r] = x[r] + v[r];
 }
 
+// z += alpha c with alpha = hv[0] / hv[1] (the minimal-residual step of a
+// correction c: hv[0] = <A c, r1>, hv[1] = <A c, A c>); nothing when hv[1] = 0
+__global__ void k_mr_axpy(c128* __restrict__ z, const c128* __restrict__ c, const c128* __restrict__ hv,
+                          long long n, const KState* __restrict__ kst) {
+  if (kst != nullptr && kst->stop) return;
+  const double d = hv[1].re;
+  if (!(d > 0.0)) return;
+  const c128 a = mk(hv[0].re / d, hv[0].im / d);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) z[r] = fmac(z[r], a, c[r]);
+}
+
 unsigned grid_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   long long cap = (long long)(g_num_sms > 0 ? g_num_sms : 152) * 16;
@@ -393,9 +417,9 @@ int dot_blocks() {
 }
 
 cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, const c128* CS, const c128* CSW,
-                        const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st) {
+                        const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st, bool bsub_df) {
   unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
-  k_spmv<<<blocks, kThreads, 0, st>>>(n, nx, D, CW, CS, CSW, x, bsub, y, kst);
+  k_spmv<<<blocks, kThreads, 0, st>>>(n, nx, D, CW, CS, CSW, x, bsub, bsub_df ? 1 : 0, y, kst);
   return cudaGetLastError();
 }
 
@@ -493,6 +517,12 @@ cudaError_t launch_reorth_decide(KState* kst, c128* hcol, int j, double eta2, cu
 cudaError_t launch_backsolve(const c128* H, int ldh, const c128* gvec, const KState* kst, c128* y,
                              cudaStream_t st) {
   k_backsolve<<<1, 32, 0, st>>>(H, ldh, gvec, kst, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mr_axpy(c128* z, const c128* c, const c128* hv, long long n, const KState* kst, cudaStream_t st) {
+  dot_blocks();
+  k_mr_axpy<<<grid_for(n, kThreads), kThreads, 0, st>>>(z, c, hv, n, kst);
   return cudaGetLastError();
 }
 

@@ -87,6 +87,26 @@ class Net:
     def adam_step(self, lr: float) -> None:
         _lib.check("ras_pml_net_adam_step", self.lib.ras_pml_net_adam_step(self._h, float(lr)))
 
+    @property
+    def gamma(self) -> float:
+        return float(self.lib.ras_pml_net_get_gamma(self._h))
+
+    @gamma.setter
+    def gamma(self, value: float) -> None:
+        _lib.check("ras_pml_net_set_gamma", self.lib.ras_pml_net_set_gamma(self._h, float(value)))
+
+    def train(self, solver, nrhs: int = 4, m_list=(1, 2, 3, 4, 6, 8, 12, 16), epochs: int = 100,
+              lr: float = 1e-3, seed: int = 0):
+        """Train on residual/error pairs of the solver's own problem; returns
+        (loss per epoch, gamma)."""
+        ms = np.ascontiguousarray(m_list, dtype=np.int32)
+        hist = np.zeros(int(epochs), dtype=np.float32)
+        g = c_double()
+        _lib.check("ras_pml_net_train", self.lib.ras_pml_net_train(
+            self._h, solver._h, int(nrhs), ms.ctypes.data_as(c_void_p), int(ms.size), int(epochs), float(lr),
+            int(seed), hist.ctypes.data_as(c_void_p), byref(g)))
+        return hist, g.value
+
     def close(self) -> None:
         if getattr(self, "_h", None) and self._h.value:
             self.lib.ras_pml_net_destroy(self._h)

@@ -101,6 +101,17 @@ class RasPml:
         _lib.check("ras_pml_tune", self.lib.ras_pml_tune(self._h, byref(rep)))
         return tune_dict(rep)
 
+    def attach_net(self, net) -> None:
+        """Use net (a paper_2602_00735_gb300.net.Net, or None) as the learned FGMRES stage."""
+        self._net = net
+        _lib.check("ras_pml_attach_net", self.lib.ras_pml_attach_net(self._h, net._h if net is not None else None))
+
+    def net_correct(self, net, r: torch.Tensor, z: torch.Tensor) -> torch.Tensor:
+        """z += the learned correction of r (in place; returns z)."""
+        _lib.check("ras_pml_net_correct", self.lib.ras_pml_net_correct(
+            self._h, net._h, c_void_p(_dev_ptr(r, self.n)), c_void_p(_dev_ptr(z, self.n))))
+        return z
+
     def set_shapes(self, factor_threads: int, factor_rank: int, apply_cols: int) -> None:
         _lib.check("ras_pml_set_shapes", self.lib.ras_pml_set_shapes(self._h, int(factor_threads), int(factor_rank),
                                                                      int(apply_cols)))
