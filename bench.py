@@ -16,6 +16,10 @@ residual of 1e-6.
              side from pinned host memory in, solution back to the host
   roofline   the apply of B^-1 (k_apply + k_prolong), timed with CUDA events
              inside the timed steps on the handle's stream
+  learned    the same step with the learned coarse correction attached (a
+             6-layer CNN on a 256^2 grid, tensor-core kernels), trained first
+             on this problem's own residual/error pairs (training reported
+             apart), and the network's forward / training-step times
   cpu_baseline  the CPU oracle on a bounded sample of the same workload,
              scaled to a full solve (see cpu_sample below)
 
@@ -58,6 +62,10 @@ BATCH_METRIC = ("RAS-PML batched form: 64 independent problems (k 20*pi..120*pi,
                 "complex64 local factors + complex128 lockstep FGMRES (s)")
 RTOL = 1e-6
 MAXIT = 400
+
+
+def net_channels():
+    return (2, 32, 32, 32, 32, 32, 2)
 
 
 def peaks():
@@ -350,6 +358,68 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": round(float(np.mean(te)), 4), "unit": "s", "h2d_bytes_per_step": 2 * nb,
                "d2h_bytes_per_step": nb}
 
+    # learned coarse correction (NEXT-2): trained on this problem's own
+    # residual/error pairs (training time reported apart), then the same step
+    # with the stage attached
+    learned = None
+    if not args.skip_learned:
+        from paper_2602_00735_gb300.net import Net
+        net = Net(Nc=256, cap=8, seed=0)
+        s0 = RasPml(p, factor_prec=args.prec, ortho=args.ortho)
+        s0.set_shapes(*shapes[args.prec][:3])
+        s0.factor()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist, gamma = net.train(s0, nrhs=2, m_list=(1, 2, 4, 8, 16, 32), epochs=40, lr=1e-3, seed=7)
+        t_train = time.perf_counter() - t0
+        s0.close()
+        tl, itl, rell = [], None, None
+        for k in range(1 + args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s = RasPml(p, factor_prec=args.prec, ortho=args.ortho)
+            s.set_shapes(*shapes[args.prec][:3])
+            b = s.assemble_rhs(w.centres, w.amps, w.width)
+            s.factor()
+            s.attach_net(net)
+            x, itl, rell, stl = s.solve(b, rtol=RTOL, maxit=MAXIT)
+            e1.record(stream)
+            e1.synchronize()
+            if k > 0:
+                tl.append(e0.elapsed_time(e1) / 1e3)
+            s.attach_net(None)
+            s.close()
+            del x, b
+        # the network alone: one forward on one 256^2 image; one training step on 8
+        xin = torch.randn(8, 2, 256, 256, device=dev, dtype=torch.float32)
+        tin = torch.randn(8, 2, 256, 256, device=dev, dtype=torch.float32)
+        net.forward(xin[:1])
+        net.loss_grad(xin, tin, want_grad=False)
+        tf, tb = [], []
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            net.forward(xin[:1])
+            e1.record(stream)
+            net.loss_grad(xin, tin, want_grad=False)
+            e2.record(stream)
+            e2.synchronize()
+            tf.append(e0.elapsed_time(e1) / 1e3)
+            tb.append(e1.elapsed_time(e2) / 1e3)
+        flop_img = 2 * 256 * 256 * 9 * sum(a * b for a, b in zip(net_channels(), net_channels()[1:]))
+        learned = {"time_s": round(float(np.mean(tl)), 4), "iters": int(itl), "relres": float(rell),
+                   "iters_plain": int(per_c64[-1]["iters"]), "train_s": round(t_train, 2), "gamma": gamma,
+                   "loss_first_epoch": float(hist[0]), "loss_last_epoch": float(hist[-1]),
+                   "coarse_grid": 256, "forward_ms_1img": round(1e3 * float(np.median(tf)), 4),
+                   "forward_tflops": round(flop_img / float(np.median(tf)) / 1e12, 2),
+                   "train_step_ms_8img": round(1e3 * float(np.median(tb)), 3),
+                   "note": "complex64 form with the learned stage attached (minimal-residual scaled); "
+                           "time excludes training"}
+        net.close()
+
     # max over ranks
     mean_t = max_over_ranks(float(np.mean(t_c64)), world, dev)
     if rank != 0:
@@ -386,6 +456,7 @@ def run_ours(args, rank, world, local_rank):
                      "algorithmic_bytes_per_launch": info["apply_bytes"]},
         "fp64": fp64, "error_vs_fp64": err, "c64_fp64_gram_schmidt": gs64,
         "tune": shapes[args.prec][3],
+        "learned": learned,
         "gpu_launches": int(sum(launches_per_step)),
         "gpu_launches_per_step": int(launches_per_step[-1]),
         "clocks": clk, "e2e": e2e,
@@ -602,6 +673,7 @@ def main():
                     help="local factors of the headline form: 1 complex64, 2 complex64 with half-precision storage")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-learned", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shapes", default="",
                     help="fixed tile shapes 'threads,rank,cols' instead of tuning (profiling runs)")
