@@ -229,3 +229,20 @@ def test_factor_shapes_match_oracle(solver_cls, name, kw, prec, tol, threads, ra
         s.factor()
         r = random_vector(grid.n, 4)
         assert rel(s.apply(to_dev(r)).cpu().numpy(), R.apply(r)) <= tol
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
+def test_residual_after_one_sweep_lives_in_the_overlaps(solver_cls, prec, tol):
+    """Section 3, practical point (i), on the GPU: b - A B^-1 b vanishes away
+    from the overlaps (to the local solves' precision)."""
+    from test_oracle_ras import deep_core_mask
+    w = variant("c0")
+    p = w.params()
+    with solver_cls(p, factor_prec=prec) as s:
+        s.factor()
+        b = random_vector(s.n, 9)
+        bd = to_dev(b)
+        r = (bd - s.matvec(s.apply(bd))).cpu().numpy()
+    m = deep_core_mask(p)
+    assert np.max(np.abs(r[m])) <= tol * np.max(np.abs(b))
+    assert np.linalg.norm(r[~m]) >= 0.1 * np.linalg.norm(b)

@@ -247,3 +247,38 @@ def test_iterations_grow_with_k_at_fixed_resolution():
         its.append(it)
     assert its[0] < its[1] < its[2]
     assert its[2] < 4 * 4 * its[0]                 # far below quadratic growth
+
+
+def deep_core_mask(p):
+    """Unknowns whose whole 7-point stencil lies where exactly one subdomain
+    carries the partition of unity (chi_j = 1 away from every overlap strip)."""
+    grid, rxs, rys = ras.covering(p)
+    o = p["ovlp_cells"]
+    ok_x = np.zeros(grid.Mx + 1, bool)
+    ok_y = np.zeros(grid.My + 1, bool)
+    for r, ok in ((rxs, ok_x), (rys, ok_y)):
+        for q in r:
+            lo = q.box_lo + o + 1 if q.lo_interior else 1
+            hi = q.box_hi - o - 1 if q.hi_interior else len(ok) - 2
+            ok[lo:hi + 1] = True
+    ii = np.arange(1, grid.Mx)
+    jj = np.arange(1, grid.My)
+    return (ok_y[jj][:, None] & ok_x[ii][None, :]).ravel()
+
+
+@pytest.mark.parametrize("name", ["small", "c0"])
+def test_residual_after_one_sweep_lives_in_the_overlaps(name):
+    """Section 3, practical point (i): after one RAS sweep from u = 0 the
+    residual b - A B^-1 b vanishes wherever a single subdomain's local solve
+    is exact for the global equations, i.e. away from the overlaps."""
+    w = _w(name)
+    p = w.params()
+    grid, A = fem.assemble_global(p)
+    R = ras.RAS(p).factor()
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(grid.n) + 1j * rng.standard_normal(grid.n)
+    r = b - A @ R.apply(b)
+    m = deep_core_mask(p)
+    assert m.sum() > 0.3 * grid.n
+    assert np.max(np.abs(r[m])) <= 1e-11 * np.max(np.abs(b))
+    assert np.linalg.norm(r[~m]) >= 0.1 * np.linalg.norm(b)    # but not in the overlaps
