@@ -300,8 +300,11 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   rp::DevStatus s0{-1, 0, 0, 0};
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->status, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->st);
-  if (e == cudaSuccess) e = rp::launch_global_stencil(g, h->D, h->CW, h->CS, h->CSW, h->st);
+  c128* tab = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc((void**)&tab, sizeof(c128) * rp::stretch_table_elems(g));
+  if (e == cudaSuccess) e = rp::launch_global_stencil(g, tab, h->D, h->CW, h->CS, h->CSW, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (tab) cudaFree(tab);
   if (e != cudaSuccess) {
     std::fprintf(stderr, "raspml: setup: %s\n", cudaGetErrorString(e));
     ras_pml_destroy(h);

@@ -281,11 +281,16 @@ int ras_pml_batch_setup(const ras_pml_params* params, int nprob, void* stream, r
   up(h->status, &s0, sizeof(s0));
   for (c128* a : {h->D, h->CW, h->CS, h->CSW})
     if (e == cudaSuccess) e = cudaMemsetAsync(a, 0, sizeof(c128) * h->ntot, h->st);
+  size_t tabn = 0;
+  for (int q = 0; q < nprob; ++q) tabn = std::max(tabn, rp::stretch_table_elems(h->geos_h[q]));
+  c128* tab = nullptr;   // one problem's stretching tables at a time (stream-ordered reuse)
+  if (e == cudaSuccess) e = cudaMalloc((void**)&tab, sizeof(c128) * tabn);
   for (int q = 0; q < nprob && e == cudaSuccess; ++q) {
     const long long o = h->geos_h[q].goff;
-    e = rp::launch_global_stencil(h->geos_h[q], h->D + o, h->CW + o, h->CS + o, h->CSW + o, h->st);
+    e = rp::launch_global_stencil(h->geos_h[q], tab, h->D + o, h->CW + o, h->CS + o, h->CSW + o, h->st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (tab) cudaFree(tab);
   if (e != cudaSuccess) {
     std::fprintf(stderr, "raspml: batch setup: %s\n", cudaGetErrorString(e));
     ras_pml_batch_destroy(h);

@@ -57,13 +57,6 @@ __device__ __forceinline__ T gprime_t(double d, double amp, double ramp, int pro
   return (T)amp * t * t * ((T)3 - (T)2 * t);
 }
 
-struct GlobalStretch {
-  Geo g;
-  __device__ c128 gx(double s) const { return gam_global_x(g, s); }
-  __device__ c128 gy(double s) const { return gam_global_y(g, s); }
-  __device__ bool cell_ok(int ci, int cj) const { return ci >= 0 && ci < g.Mx && cj >= 0 && cj < g.My; }
-};
-
 // Local stretching g_j (Section 2) evaluated in arithmetic type T. Positions
 // and branch decisions are in double (half-index units), as for the global one.
 template <typename T>
@@ -84,27 +77,32 @@ struct LocalStretch {
   }
 };
 
+template <typename T, class S>
+__device__ __forceinline__ CellTerms<T> cell_of(const Geo& g, const S& st, int ci, int cj) {
+  return cell_terms<T>(g, st, ci, cj);
+}
+
 // Diagonal and lower couplings of node (i, j) from the cells around it.
 template <typename T, class S>
 __device__ void node_row(const Geo& g, const S& st, int i, int j, cx<T>& D, cx<T>& W, cx<T>& Sx, cx<T>& SW) {
   const T q = (T)(0.25 * g.k * g.k);  // k^2 * (hat product 1/2 * 1/2)
   D = W = Sx = SW = mk((T)0, (T)0);
   if (st.cell_ok(i, j)) {
-    CellTerms<T> t = cell_terms<T>(g, st, i, j);
+    CellTerms<T> t = cell_of<T>(g, st, i, j);
     D = D + t.KxL - q * (t.m01 + t.m02) + t.KyU - q * (t.m02 + t.m03);
   }
   if (st.cell_ok(i - 1, j)) {
-    CellTerms<T> t = cell_terms<T>(g, st, i - 1, j);
+    CellTerms<T> t = cell_of<T>(g, st, i - 1, j);
     D = D + t.KxL + t.KyL - q * (t.m01 + t.m12);
     W = W - t.KxL - q * t.m01;
   }
   if (st.cell_ok(i, j - 1)) {
-    CellTerms<T> t = cell_terms<T>(g, st, i, j - 1);
+    CellTerms<T> t = cell_of<T>(g, st, i, j - 1);
     D = D + t.KxU + t.KyU - q * (t.m23 + t.m03);
     Sx = Sx - t.KyU - q * t.m03;
   }
   if (st.cell_ok(i - 1, j - 1)) {
-    CellTerms<T> t = cell_terms<T>(g, st, i - 1, j - 1);
+    CellTerms<T> t = cell_of<T>(g, st, i - 1, j - 1);
     D = D + t.KyL - q * (t.m12 + t.m02) + t.KxU - q * (t.m02 + t.m23);
     W = W - t.KxU - q * t.m23;
     Sx = Sx - t.KyL - q * t.m12;
@@ -152,13 +150,70 @@ __device__ void impedance_terms(const Geo& g, const SubDesc& sd, const LocalStre
   }
 }
 
-__global__ void k_global_stencil(Geo g, c128* __restrict__ D, c128* __restrict__ CW, c128* __restrict__ CS,
-                                 c128* __restrict__ CSW) {
+// The global stretching is Cartesian: gamma_1 depends on x alone, gamma_2
+// on y alone. tab holds, at every half-index position s, gamma_1(s) and
+// 1/gamma_1(s) (first 2Mx+1 pairs), then gamma_2 and 1/gamma_2 (2My+1 pairs).
+__global__ void k_stretch_tables(Geo g, c128* __restrict__ tab) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nxs = 2 * g.Mx + 1, nys = 2 * g.My + 1;
+  if (e >= nxs + nys) return;
+  const c128 v = e < nxs ? gam_global_x(g, (double)e) : gam_global_y(g, (double)(e - nxs));
+  tab[2 * e] = v;
+  tab[2 * e + 1] = crecip(v);
+}
+
+// Global stretching read from the tables; quotients become products with
+// the tabulated reciprocals.
+struct TabStretch {
+  const c128* tx;   // (gamma_1, 1/gamma_1) at half-index s
+  const c128* ty;
+  __device__ c128 gx(double s) const { return tx[2 * (int)s]; }
+  __device__ c128 gy(double s) const { return ty[2 * (int)s]; }
+  __device__ c128 rgx(double s) const { return tx[2 * (int)s + 1]; }
+  __device__ c128 rgy(double s) const { return ty[2 * (int)s + 1]; }
+};
+
+__device__ CellTerms<double> cell_terms_tab(const Geo& g, const TabStretch& st, int ci, int cj) {
+  const double sa = 2.0 * ci + 1.0, sb = 2.0 * ci + 2.0, sc = 2.0 * ci;
+  const double ta = 2.0 * cj, tb = 2.0 * cj + 1.0, tc = 2.0 * cj + 2.0;
+  const c128 xa = st.gx(sa), xb = st.gx(sb), xc = st.gx(sc);
+  const c128 ya = st.gy(ta), yb = st.gy(tb), yc = st.gy(tc);
+  const c128 ixa = st.rgx(sa), ixb = st.rgx(sb), ixc = st.rgx(sc);
+  const c128 iya = st.rgy(ta), iyb = st.rgy(tb), iyc = st.rgy(tc);
+  const double sixth = 1.0 / 6.0;
+  const double w = g.h * g.h * (1.0 / 6.0);
+  CellTerms<double> t;
+  t.KxL = sixth * (ya * ixa + yb * ixb + yb * ixa);
+  t.KyL = sixth * (xa * iya + xb * iyb + xa * iyb);
+  t.KxU = sixth * (yb * ixa + yc * ixa + yb * ixc);
+  t.KyU = sixth * (xa * iyb + xa * iyc + xc * iyb);
+  t.m01 = w * (xa * ya);
+  t.m12 = w * (xb * yb);
+  t.m02 = w * (xa * yb);
+  t.m23 = w * (xa * yc);
+  t.m03 = w * (xc * yb);
+  return t;
+}
+
+struct TabCells {
+  Geo g;
+  TabStretch st;
+  __device__ bool cell_ok(int ci, int cj) const { return ci >= 0 && ci < g.Mx && cj >= 0 && cj < g.My; }
+  __device__ CellTerms<double> cell(int ci, int cj) const { return cell_terms_tab(g, st, ci, cj); }
+};
+
+template <typename T>
+__device__ __forceinline__ CellTerms<T> cell_of(const Geo& g, const TabCells& st, int ci, int cj) {
+  return st.cell(ci, cj);
+}
+
+__global__ void k_global_stencil(Geo g, const c128* __restrict__ tab, c128* __restrict__ D, c128* __restrict__ CW,
+                                 c128* __restrict__ CS, c128* __restrict__ CSW) {
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long n = (long long)g.nx * g.ny;
   if (r >= n) return;
   int i = (int)(r % g.nx) + 1, j = (int)(r / g.nx) + 1;
-  GlobalStretch st{g};
+  TabCells st{g, TabStretch{tab, tab + 2 * (2 * g.Mx + 1)}};
   c128 d, w, s, sw;
   node_row<double>(g, st, i, j, d, w, s, sw);
   const c128 z = mk(0.0, 0.0);
@@ -228,11 +283,15 @@ __global__ void k_rhs(Geo g, const double* __restrict__ cen, const double* __res
 
 }  // namespace
 
-cudaError_t launch_global_stencil(const Geo& g, c128* D, c128* CW, c128* CS, c128* CSW, cudaStream_t st) {
+size_t stretch_table_elems(const Geo& g) { return (size_t)2 * (2 * g.Mx + 1 + 2 * g.My + 1); }
+
+cudaError_t launch_global_stencil(const Geo& g, c128* tab, c128* D, c128* CW, c128* CS, c128* CSW, cudaStream_t st) {
+  const int ne = 2 * g.Mx + 1 + 2 * g.My + 1;
+  k_stretch_tables<<<(ne + 255) / 256, 256, 0, st>>>(g, tab);
   long long n = (long long)g.nx * g.ny;
   int threads = 256;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
-  k_global_stencil<<<blocks, threads, 0, st>>>(g, D, CW, CS, CSW);
+  k_global_stencil<<<blocks, threads, 0, st>>>(g, tab, D, CW, CS, CSW);
   return cudaGetLastError();
 }
 

@@ -42,7 +42,9 @@ bool factor_shape_valid(int threads, int rank);
 bool apply_cols_valid(int prec, int cols);
 
 // assembly.cu
-cudaError_t launch_global_stencil(const Geo& g, c128* D, c128* CW, c128* CS, c128* CSW, cudaStream_t st);
+// tab: scratch of stretch_table_elems(g) complex128 values (stretching tables)
+size_t stretch_table_elems(const Geo& g);
+cudaError_t launch_global_stencil(const Geo& g, c128* tab, c128* D, c128* CW, c128* CS, c128* CSW, cudaStream_t st);
 cudaError_t launch_local_rows(int prec, const Geo* geos, const SubDesc* subs, int nsub, int max_npad, c128* Aloc,
                               cudaStream_t st);
 cudaError_t launch_rhs(const Geo& g, const double* cen, const double* amp, int ns, double width, c128* b,
