@@ -91,7 +91,13 @@ typedef struct {
                              3 classical Gram-Schmidt once with the basis kept in
                                complex128 and its products and sums in
                                double-float arithmetic (two floats, about 46
-                               bits) on the FP32 pipe                          */
+                               bits) on the FP32 pipe;
+                             4 as 3 with the basis vectors stored as their
+                               complex64 roundings (8 bytes per entry; the
+                               projections use those values exactly; the
+                               rounding perturbs the Arnoldi relation by
+                               ~1e-7 relative, which the true-residual check
+                               at the end of each cycle catches)               */
   int    g_profile;       /* stretching: 0 g'(d) as above; 1 g(d) = g_amp d^3,
                              i.e. g'(d) = 3 g_amp d^2 (the paper's experiments
                              use g_amp = 10k, Section 4); g_ramp unused        */

@@ -60,6 +60,11 @@ using rp::dalloc;
 using rp::dfree;
 using rp::ev_ms;
 
+// Reduction of the residual estimate after which a cycle on a complex64
+// Krylov basis ends and restarts from the true residual: the basis
+// rounding (2^-24) bounds what one cycle's estimate can be trusted to.
+constexpr double kC64BasisFloor = 1e-6;
+
 #define RP_ALLOC(ptr, cnt)            \
   do {                                \
     int s_ = dalloc(&(ptr), (cnt));   \
@@ -158,7 +163,7 @@ namespace rp {
 int build_problem(const ras_pml_params& p, int prob, Geo& g, std::vector<SubDesc>& subs) {
   if (!(p.k >= 0.0) || !(p.h > 0.0) || !(p.kappa_g >= 0.0) || !(p.x1 > p.x0) || !(p.y1 > p.y0) || p.px < 1 ||
       p.py < 1 || !(p.g_ramp > 0.0) || !(p.g_amp >= 0.0) || (p.local_bc != 0 && p.local_bc != 1) ||
-      (p.factor_prec < 0 || p.factor_prec > 2) || (p.ortho < 0 || p.ortho > 3) || (p.g_profile != 0 && p.g_profile != 1))
+      (p.factor_prec < 0 || p.factor_prec > 2) || (p.ortho < 0 || p.ortho > 4) || (p.g_profile != 0 && p.g_profile != 1))
     return RASPML_EBADARG;
   const double lx = p.x1 - p.x0 + 2 * p.kappa_g, ly = p.y1 - p.y0 + 2 * p.kappa_g;
   const long long Mx = std::llround(lx / p.h), My = std::llround(ly / p.h);
@@ -549,15 +554,20 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
   int status = RASPML_NOT_CONVERGED;
   double rel = NAN;
   const bool dfbasis = h->p.ortho == 3;   // V stored in double-float form
+  const bool c64basis = h->p.ortho == 4;  // V stored as complex64, w in its own buffer
+  const int bkind = dfbasis ? rp::RK_DF : c64basis ? rp::RK_C64 : rp::RK_C128;
+  c64* V64 = reinterpret_cast<c64*>(h->V);
   for (;;) {
     // new cycle: V0 = b - A x, beta = ||V0||, g = beta e1, V0 /= beta
-    c128* V0 = h->V;
+    c128* V0 = c64basis ? h->wdf : h->V;
     ++cycles;
     RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, x, b, V0, nullptr, st));
     if ((s = dev_norm(h, V0, &h->kst->hnorm, nullptr, nullptr))) return s;
     RP_CUDA(rp::launch_cycle_init(h->kst, h->gvec, m, rtol, h->hist, st));
     if (dfbasis)
       RP_CUDA(rp::launch_scale_to_df(V0, n, &h->kst->hnorm, h->kst, st));
+    else if (c64basis)
+      RP_CUDA(rp::launch_scale_to_c64(V0, V64, n, &h->kst->hnorm, h->kst, st));
     else
       RP_CUDA(rp::launch_scale_inv(V0, n, &h->kst->hnorm, h->kst, st));
     // Batches of `batch` directions; batch b+1 is enqueued before the stop flag
@@ -580,19 +590,19 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
     for (int j = 0; j < m && !stopped;) {
       const int nb = std::min(batch, m - j);
       for (int jj = j; jj < j + nb; ++jj) {
-        c128* vj = h->V + (size_t)jj * n;
+        c128* vj = c64basis ? reinterpret_cast<c128*>(V64 + (size_t)jj * n) : h->V + (size_t)jj * n;
         c128* zj = h->Z + (size_t)jj * n;
-        c128* w = h->V + (size_t)(jj + 1) * n;
+        c128* w = c64basis ? h->wdf : h->V + (size_t)(jj + 1) * n;
         c128* hcol = h->H + (size_t)jj * ldh;
         cudaEvent_t* evj = h->ev.data() + slot * 4 * batch + 4 * (jj - j);
         ++issued;
         if (h->timing) RP_CUDA(cudaEventRecord(evj[0], st));
         RP_CUDA(rp::launch_apply(h->p.factor_prec, h->tune.apply_cols, h->geo, h->geo_d, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev,
-                                 h->dinv, vj, h->Y, zj, h->kst, h->status, st, dfbasis));
+                                 h->dinv, vj, h->Y, zj, h->kst, h->status, st, bkind));
         if (h->net) {
           // learned stage: c = correction of r1 = v_j - A z_j (r1 held in w), then
           // z_j += alpha c with the alpha minimising ||r1 - alpha A c||
-          RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, vj, w, h->kst, st, dfbasis));
+          RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, vj, w, h->kst, st, bkind));
           RP_CUDA(cudaMemsetAsync(h->lc, 0, sizeof(c128) * n, st));
           const int cs = rp::net_correct(h->net, w, h->lc, h->geo.nx, h->geo.ny, h->kst, st);
           if (cs != RASPML_OK) return cs;
@@ -616,6 +626,12 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
           RP_CUDA(rp::launch_axpys(h->V, n, jj + 1, h->hbuf, -1.0, w, n, h->kst, 0, st));
           RP_CUDA(rp::launch_add(hcol, h->hbuf, jj + 1, h->kst, 0, st));
           if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst))) return s;
+        } else if (c64basis) {
+          // one pass against the complex64 basis, double-float products and sums
+          RP_CUDA(rp::launch_dots_c64b(V64, n, jj + 1, w, n, h->partial, h->kst, st));
+          RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, hcol, 0, h->kst, 0, st));
+          RP_CUDA(rp::launch_axpys_c64b(V64, n, jj + 1, hcol, -1.0, w, n, h->kst, st));
+          if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst))) return s;
         } else if (h->p.ortho == 3) {
           // one pass against the double-float basis, products and sums on the FP32 pipe
           RP_CUDA(rp::launch_split(w, h->wdf, n, h->kst, st));
@@ -637,9 +653,12 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
           RP_CUDA(rp::launch_add(hcol, h->hbuf, jj + 1, h->kst, 1, st));
           if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst, 1))) return s;
         }
-        RP_CUDA(rp::launch_givens(h->kst, h->H, ldh, h->cs, h->sn, h->gvec, jj, rtol, m, maxit, h->hist, st));
+        RP_CUDA(rp::launch_givens(h->kst, h->H, ldh, h->cs, h->sn, h->gvec, jj, rtol, m, maxit, h->hist, st,
+                                  c64basis ? kC64BasisFloor : 0.0));
         if (dfbasis)
           RP_CUDA(rp::launch_scale_to_df(w, n, &h->kst->hnorm, h->kst, st));
+        else if (c64basis)
+          RP_CUDA(rp::launch_scale_to_c64(w, V64 + (size_t)(jj + 1) * n, n, &h->kst->hnorm, h->kst, st));
         else
           RP_CUDA(rp::launch_scale_inv(w, n, &h->kst->hnorm, h->kst, st));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[3], st));
@@ -680,10 +699,10 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
   // launches: ||b|| (2); per cycle: residual, norm (2), init, scale, backsolve,
   // update, true residual, norm (2) = 10; per issued direction: 13 (CGS twice)
   // or 17 (one pass, test, gated second pass)
-  launches += 10 * cycles + (h->p.ortho == 0 ? 13 : h->p.ortho == 3 ? 12 : 17) * issued;
+  launches += 10 * cycles + (h->p.ortho == 0 ? 13 : h->p.ortho == 3 ? 12 : h->p.ortho == 4 ? 11 : 17) * issued;
   h->tm.launches = (int32_t)launches;
   h->tm.applies = total;
-  h->tm.reorths = h->p.ortho == 0 ? total : (h->p.ortho == 3 ? 0 : h->kst_host->reorths);
+  h->tm.reorths = h->p.ortho == 0 ? total : (h->p.ortho >= 3 ? 0 : h->kst_host->reorths);
   if (h->timing) {
     RP_CUDA(cudaEventRecord(h->ev[8 * batch + 1], st));
     RP_CUDA(cudaEventSynchronize(h->ev[8 * batch + 1]));

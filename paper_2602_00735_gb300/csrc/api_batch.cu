@@ -472,7 +472,7 @@ int ras_pml_batch_apply(ras_pml_batch* h, const rp_c128* r, rp_c128* z) {
   cudaSetDevice(h->dev);
   RP_CUDA(rp::launch_local_solves(h->prec, h->tune.apply_cols, h->geos_d, h->subs_d, h->nsub, h->max_b, h->max_bp,
                                   h->L, h->Lrev, h->dinv, (const c128*)r, 0, nullptr, h->Y, nullptr, h->status,
-                                  h->st, false));
+                                  h->st, rp::RK_C128));
   RP_CUDA(rp::launch_bprolong(h->prec, h->ntiles, h->tile_prob_d, h->geos_d, h->subs_d, h->sub_index_d, h->Y,
                               (c128*)z, 0, nullptr, nullptr, 0, h->st));
   return RASPML_OK;

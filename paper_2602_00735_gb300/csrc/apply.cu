@@ -34,17 +34,19 @@ namespace {
 template <typename ST>
 constexpr int stages_for() { return 4; }
 
-// R_j r at local row `row`: r is complex128, or double-float (dfc) when rdf
+// R_j r at local row `row`: r is complex128 (rdf 0), double-float dfc
+// (rdf 1) or complex64 (rdf 2)
 template <typename R>
 __device__ __forceinline__ cx<R> gather_row(const SubDesc& sd, int nx, long long goff, const c128* __restrict__ r,
                                             int rdf, int row) {
   if (row >= sd.n) return mk((R)0, (R)0);
   int i = sd.ix0 + row % sd.nlx, j = sd.iy0 + row / sd.nlx;
   const long long idx = goff + (long long)(j - 1) * nx + (i - 1);
-  if (rdf) {
+  if (rdf == 1) {
     const dfc v = reinterpret_cast<const dfc*>(r)[idx];
     return mk((R)((R)v.rh + (R)v.rl), (R)((R)v.ih + (R)v.il));
   }
+  if (rdf == 2) return cvt<R>(reinterpret_cast<const c64*>(r)[idx]);
   return cvt<R>(r[idx]);
 }
 
@@ -200,7 +202,9 @@ __global__ void __launch_bounds__(32)
   const int nx = geos[sd.prob].nx, o = geos[sd.prob].ovlp;
   const long long goff = geos[sd.prob].goff;
   const c128* rglob = rbase;
-  if (jptr != nullptr) rglob = (const c128*)((const dfc*)rbase + (long long)(*jptr) * r_ld);
+  if (jptr != nullptr)
+    rglob = rdf == 2 ? (const c128*)((const c64*)rbase + (long long)(*jptr) * r_ld)
+                     : (const c128*)((const dfc*)rbase + (long long)(*jptr) * r_ld);
   const int lane = threadIdx.x;
   Pipe<ST, KC> pp;
   pp.bar = reinterpret_cast<uint64_t*>(sm);
@@ -293,8 +297,8 @@ size_t apply_smem_bytes(int max_bp, int prec, int cols) {
 cudaError_t launch_local_solves(int prec, int cols, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
                                 int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r,
                                 long long r_ld, const int* jptr, void* Y, const KState* kst, DevStatus* status,
-                                cudaStream_t st, bool r_is_df) {
-  const int rdf = r_is_df ? 1 : 0;
+                                cudaStream_t st, int rkind) {
+  const int rdf = rkind;
   if (!apply_cols_valid(prec, cols)) return cudaErrorInvalidValue;
 #define RP_APPLY_ARGS max_b, geos, subs, nsub, max_bp, Lf, Lb, dinv, r, r_ld, jptr, rdf, Y, kst, status, st
   if (prec == 0) return launch_apply_t<double, c128, 8>(RP_APPLY_ARGS);
@@ -319,9 +323,9 @@ cudaError_t launch_prolong(int prec, const Geo& g, const SubDesc* subs, const vo
 
 cudaError_t launch_apply(int prec, int cols, const Geo& g, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
                          int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r, void* Y,
-                         c128* z, const KState* kst, DevStatus* status, cudaStream_t st, bool r_is_df) {
+                         c128* z, const KState* kst, DevStatus* status, cudaStream_t st, int rkind) {
   cudaError_t e = launch_local_solves(prec, cols, geos, subs, nsub, max_b, max_bp, Lf, Lb, dinv, r, 0, nullptr, Y,
-                                      kst, status, st, r_is_df);
+                                      kst, status, st, rkind);
   if (e != cudaSuccess) return e;
   return launch_prolong(prec, g, subs, Y, z, kst, st);
 }

@@ -497,7 +497,7 @@ cudaError_t launch_bstep(const BStep& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
   }
   e = launch_local_solves(a.prec, a.cols, a.geos, a.subs, a.nsub, a.max_b, a.max_bp, a.L, a.Lrev, a.dinv,
-                          (const c128*)a.V, a.ld, jp, a.Y, a.kst, a.status, st, true);
+                          (const c128*)a.V, a.ld, jp, a.Y, a.kst, a.status, st, RK_DF);
   if (e != cudaSuccess) return e;
   e = launch_bprolong(a.prec, a.ntiles, a.tile_prob, a.geos, a.subs, a.sub_index, a.Y, a.Z, a.ld, jp, a.kst, 1, st);
   if (e != cudaSuccess) return e;

@@ -28,6 +28,7 @@ struct KState {
   double est;      // latest |g_{j+1}| / ||b||
   double hnorm;    // latest ||w||_2
   double relres;   // true relative residual at the last cycle start (batch)
+  double beta0;    // ||r|| at the start of the current cycle
   int live;        // batch: not yet finished (converged or out of iterations)
   int pad;
 };
@@ -58,23 +59,25 @@ cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, 
 
 // apply.cu
 size_t apply_smem_bytes(int max_bp, int prec, int cols);
-// Local solves of all subdomains into Y. The input is r (complex128, or
-// double-float dfc when r_is_df), or r + (*jptr) * r_ld when jptr is set.
+// Input kinds of r: complex128, double-float (dfc) or complex64
+enum : int { RK_C128 = 0, RK_DF = 1, RK_C64 = 2 };
+// Local solves of all subdomains into Y. The input is r of kind rkind, or
+// r + (*jptr) * r_ld when jptr is set.
 cudaError_t launch_local_solves(int prec, int cols, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
                                 int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r,
                                 long long r_ld, const int* jptr, void* Y, const KState* kst, DevStatus* status,
-                                cudaStream_t st, bool r_is_df);
+                                cudaStream_t st, int rkind);
 cudaError_t launch_prolong(int prec, const Geo& g, const SubDesc* subs, const void* Y, c128* z, const KState* kst,
                            cudaStream_t st);
 // one problem: local solves + prolongation
 cudaError_t launch_apply(int prec, int cols, const Geo& g, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
                          int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r, void* Y,
-                         c128* z, const KState* kst, DevStatus* status, cudaStream_t st, bool r_is_df = false);
+                         c128* z, const KState* kst, DevStatus* status, cudaStream_t st, int rkind = RK_C128);
 
 // krylov.cu
 cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, const c128* CS, const c128* CSW,
                         const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st,
-                        bool bsub_df = false);
+                        int bsub_kind = RK_C128);
 int dot_blocks();
 cudaError_t launch_dots(const c128* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
                         const KState* kst, int gate, cudaStream_t st);
@@ -90,12 +93,21 @@ cudaError_t launch_dots_df(const void* V, long long ldv, int ncols, const void* 
 cudaError_t launch_axpys_df(const void* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
                             long long n, const KState* kst, int gate, cudaStream_t st);
 cudaError_t launch_add(c128* dst, const c128* src, int cnt, const KState* kst, int gate, cudaStream_t st);
+// complex64 Krylov basis (ortho = 4): v = fl32(w / nrm); projections of w
+// (complex128, split in the kernel) on the basis and the update, double-float
+cudaError_t launch_scale_to_c64(const c128* w, void* v, long long n, const double* nrm, const KState* kst,
+                                cudaStream_t st);
+cudaError_t launch_dots_c64b(const void* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
+                             const KState* kst, cudaStream_t st);
+cudaError_t launch_axpys_c64b(const void* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
+                              long long n, const KState* kst, cudaStream_t st);
 cudaError_t launch_norm_finish(const c128* partial, double* out, c128* hslot, const KState* kst, int gate,
                                cudaStream_t st);
 cudaError_t launch_scale_inv(c128* v, long long n, const double* nrm, const KState* kst, cudaStream_t st);
 cudaError_t launch_cycle_init(KState* kst, c128* gvec, int m, double rtol, double* hist, cudaStream_t st);
+// the cycle also ends (without convergence) once |g_{j+1}| <= cfloor * beta0
 cudaError_t launch_givens(KState* kst, c128* H, int ldh, double* cs, c128* sn, c128* gvec, int j, double rtol,
-                          int mcycle, int maxit, double* hist, cudaStream_t st);
+                          int mcycle, int maxit, double* hist, cudaStream_t st, double cfloor = 0.0);
 cudaError_t launch_reorth_decide(KState* kst, c128* hcol, int j, double eta2, cudaStream_t st);
 cudaError_t launch_backsolve(const c128* H, int ldh, const c128* gvec, const KState* kst, c128* y,
                              cudaStream_t st);

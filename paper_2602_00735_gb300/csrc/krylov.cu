@@ -49,7 +49,8 @@ __device__ __forceinline__ c128 block_sum(c128 v) {
   return t;  // valid in thread 0
 }
 
-// y = A x, or y = bsub - A x (bsub complex128, or double-float when bdf)
+// y = A x, or y = bsub - A x (bsub complex128 (bdf 0), double-float (1) or
+// complex64 (2))
 __global__ void k_spmv(long long n, int nx, const c128* __restrict__ D, const c128* __restrict__ CW,
                        const c128* __restrict__ CS, const c128* __restrict__ CSW, const c128* __restrict__ x,
                        const c128* __restrict__ bsub, int bdf, c128* __restrict__ y, const KState* __restrict__ kst) {
@@ -67,9 +68,11 @@ __global__ void k_spmv(long long n, int nx, const c128* __restrict__ D, const c1
   const c128 acc = a0 + a1;
   if (bsub) {
     c128 bv;
-    if (bdf) {
+    if (bdf == 1) {
       const dfc d = reinterpret_cast<const dfc*>(bsub)[r];
       bv = mk(df_to_d(d.rh, d.rl), df_to_d(d.ih, d.il));
+    } else if (bdf == 2) {
+      bv = cvt<double>(reinterpret_cast<const c64*>(bsub)[r]);
     } else {
       bv = bsub[r];
     }
@@ -252,6 +255,118 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Complex64 Krylov basis (ortho = 4). The basis vectors are the complex64
+// roundings of the normalised w; the projection and the update use those
+// values exactly (products of a float by a double-float as FMA residual
+// pairs, double-float sums), so V takes 8 bytes per entry.
+// ---------------------------------------------------------------------------
+// a * b for a float a and a double-float b, as p + t
+__device__ __forceinline__ void fdf_prod(float a, const dfl& b, float& p, float& t) {
+  p = a * b.hi;
+  const float e = fmaf(a, b.hi, -p);
+  t = fmaf(a, b.lo, e);
+}
+
+__global__ void k_scale_to_c64(const c128* __restrict__ w, c64* __restrict__ v, long long n,
+                               const double* __restrict__ nrm, const KState* __restrict__ kst) {
+  if (skip(kst, 0)) return;
+  const double d = *nrm;
+  if (!(d > 0.0)) return;
+  const double s = 1.0 / d;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
+    const c128 x = w[r];
+    v[r] = mk((float)(s * x.re), (float)(s * x.im));
+  }
+}
+
+// partial[c * gridDim.x + blk] = sum over the block's rows of conj(V_c) w,
+// four columns per block, w read and split once per row of the block (eight
+// columns were measured: 105 registers per thread, slower on c2 and c4)
+constexpr int kC64Cols = 4;
+
+__global__ void __launch_bounds__(kThreads)
+    k_dots_c64b(const c64* __restrict__ V, long long ldv, int ncols, const c128* __restrict__ w, long long n,
+                c128* __restrict__ partial, const KState* __restrict__ kst) {
+  if (skip(kst, 0)) return;
+  constexpr int kDfCols = kC64Cols;
+  const int c0 = blockIdx.y * kDfCols;
+  const int nc = min(kDfCols, ncols - c0);
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long r0 = blockIdx.x * per;
+  const long long r1 = min(n, r0 + per);
+  float rh[kDfCols], rl[kDfCols], ih[kDfCols], il[kDfCols];
+#pragma unroll
+  for (int q = 0; q < kDfCols; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.f;
+  for (long long r = r0 + threadIdx.x; r < r1; r += kThreads) {
+    const dfc b = split_c(w[r]);
+    const dfl br = dfl_of(b.rh, b.rl), bi = dfl_of(b.ih, b.il);
+    c64 a[kDfCols];
+#pragma unroll
+    for (int q = 0; q < kDfCols; ++q)
+      if (q < nc) a[q] = V[(long long)(c0 + q) * ldv + r];
+#pragma unroll
+    for (int q = 0; q < kDfCols; ++q) {
+      if (q >= nc) continue;
+      float p, t;
+      // conj(a) w = (ar wr + ai wi) + i (ar wi - ai wr)
+      fdf_prod(a[q].re, br, p, t);
+      df_acc(rh[q], rl[q], p, t);
+      fdf_prod(a[q].im, bi, p, t);
+      df_acc(rh[q], rl[q], p, t);
+      fdf_prod(a[q].re, bi, p, t);
+      df_acc(ih[q], il[q], p, t);
+      fdf_prod(a[q].im, br, p, t);
+      df_acc(ih[q], il[q], -p, -t);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kDfCols; ++q) {
+    if (q >= nc) break;
+    c128 s = block_sum(mk(df_to_d(rh[q], rl[q]), df_to_d(ih[q], il[q])));
+    if (threadIdx.x == 0) partial[(long long)(c0 + q) * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// w += sign * sum_c V_c h_c, double-float accumulation
+__global__ void __launch_bounds__(kThreads)
+    k_axpys_c64b(const c64* __restrict__ V, long long ldv, int ncols, const c128* __restrict__ h, double sign,
+                 c128* __restrict__ w, long long n, const KState* __restrict__ kst) {
+  if (skip(kst, 0)) return;
+  extern __shared__ dfc hsc[];
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) hsc[c] = split_c(mk(sign * h[c].re, sign * h[c].im));
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
+    const dfc w0 = split_c(w[r]);
+    float rh = w0.rh, rl = w0.rl, ih = w0.ih, il = w0.il;
+    for (int c0 = 0; c0 < ncols; c0 += kDfCols) {
+      c64 a[kDfCols];
+#pragma unroll
+      for (int q = 0; q < kDfCols; ++q)
+        if (c0 + q < ncols) a[q] = V[(long long)(c0 + q) * ldv + r];   // loads first
+#pragma unroll
+      for (int q = 0; q < kDfCols; ++q) {
+        if (c0 + q >= ncols) continue;
+        const dfc hc = hsc[c0 + q];
+        const dfl hr = dfl_of(hc.rh, hc.rl), hi_ = dfl_of(hc.ih, hc.il);
+        float p, t;
+        // a h = (ar hr - ai hi) + i (ar hi + ai hr)
+        fdf_prod(a[q].re, hr, p, t);
+        df_acc(rh, rl, p, t);
+        fdf_prod(a[q].im, hi_, p, t);
+        df_acc(rh, rl, -p, -t);
+        fdf_prod(a[q].re, hi_, p, t);
+        df_acc(ih, il, p, t);
+        fdf_prod(a[q].im, hr, p, t);
+        df_acc(ih, il, p, t);
+      }
+    }
+    w[r] = mk(df_to_d(rh, rl), df_to_d(ih, il));
+  }
+}
+
 __global__ void k_add(c128* __restrict__ dst, const c128* __restrict__ src, int cnt,
                       const KState* __restrict__ kst, int gate) {
   if (skip(kst, gate)) return;
@@ -307,6 +422,7 @@ __global__ void k_cycle_init(KState* kst, c128* gvec, int m, double rtol, double
     kst->stop = 0;
     kst->conv = 0;
     kst->breakdown = 0;
+    kst->beta0 = beta;
     const double est = beta / kst->bnorm;
     kst->est = est;
     if (hist) hist[kst->total] = est;
@@ -323,7 +439,7 @@ __global__ void k_cycle_init(KState* kst, c128* gvec, int m, double rtol, double
 // Givens step j of the cycle (one thread): rotate the new Hessenberg column,
 // build the new rotation, update g and the residual estimate, decide stop.
 __global__ void k_givens(KState* kst, c128* H, int ldh, double* cs, c128* sn, c128* gvec, int j, double rtol,
-                         int mcycle, int maxit, double* hist) {
+                         int mcycle, int maxit, double* hist, double cfloor) {
   if (threadIdx.x != 0 || kst->stop) return;
   c128* col = H + (long long)j * ldh;
   for (int i = 0; i < j; ++i) {
@@ -363,6 +479,9 @@ __global__ void k_givens(KState* kst, c128* H, int ldh, double* cs, c128* sn, c1
   if (est <= rtol) { kst->conv = 1; kst->stop = 1; }
   if (kst->hnorm == 0.0) { kst->breakdown = 1; kst->stop = 1; }
   if (j + 1 >= mcycle || kst->total >= maxit) kst->stop = 1;
+  // the attainable reduction of one cycle (complex64 basis): restart from the
+  // true residual instead of iterating on a stagnating estimate
+  if (sqrt(abs2(gvec[j + 1])) <= cfloor * kst->beta0) kst->stop = 1;
 }
 
 // y = H(0:m,0:m)^-1 g for the upper-triangular Hessenberg after rotations,
@@ -417,9 +536,9 @@ int dot_blocks() {
 }
 
 cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, const c128* CS, const c128* CSW,
-                        const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st, bool bsub_df) {
+                        const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st, int bsub_kind) {
   unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
-  k_spmv<<<blocks, kThreads, 0, st>>>(n, nx, D, CW, CS, CSW, x, bsub, bsub_df ? 1 : 0, y, kst);
+  k_spmv<<<blocks, kThreads, 0, st>>>(n, nx, D, CW, CS, CSW, x, bsub, bsub_kind, y, kst);
   return cudaGetLastError();
 }
 
@@ -504,8 +623,8 @@ cudaError_t launch_cycle_init(KState* kst, c128* gvec, int m, double rtol, doubl
 }
 
 cudaError_t launch_givens(KState* kst, c128* H, int ldh, double* cs, c128* sn, c128* gvec, int j, double rtol,
-                          int mcycle, int maxit, double* hist, cudaStream_t st) {
-  k_givens<<<1, 32, 0, st>>>(kst, H, ldh, cs, sn, gvec, j, rtol, mcycle, maxit, hist);
+                          int mcycle, int maxit, double* hist, cudaStream_t st, double cfloor) {
+  k_givens<<<1, 32, 0, st>>>(kst, H, ldh, cs, sn, gvec, j, rtol, mcycle, maxit, hist, cfloor);
   return cudaGetLastError();
 }
 
@@ -517,6 +636,32 @@ cudaError_t launch_reorth_decide(KState* kst, c128* hcol, int j, double eta2, cu
 cudaError_t launch_backsolve(const c128* H, int ldh, const c128* gvec, const KState* kst, c128* y,
                              cudaStream_t st) {
   k_backsolve<<<1, 32, 0, st>>>(H, ldh, gvec, kst, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_to_c64(const c128* w, void* v, long long n, const double* nrm, const KState* kst,
+                                cudaStream_t st) {
+  dot_blocks();
+  k_scale_to_c64<<<grid_for(n, kThreads), kThreads, 0, st>>>(w, (c64*)v, n, nrm, kst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dots_c64b(const void* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
+                             const KState* kst, cudaStream_t st) {
+  dim3 grid(dot_blocks(), (ncols + kC64Cols - 1) / kC64Cols);
+  k_dots_c64b<<<grid, kThreads, 0, st>>>((const c64*)V, ldv, ncols, w, n, partial, kst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpys_c64b(const void* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
+                              long long n, const KState* kst, cudaStream_t st) {
+  dot_blocks();
+  const size_t smem = (size_t)ncols * sizeof(dfc);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_axpys_c64b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_axpys_c64b<<<grid_for(n, kThreads), kThreads, smem, st>>>((const c64*)V, ldv, ncols, h, sign, w, n, kst);
   return cudaGetLastError();
 }
 

@@ -55,7 +55,7 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
       e = cudaEventRecord(e0, t.st);
       if (e == cudaSuccess)
         e = launch_local_solves(t.prec, cols, t.geos, t.subs, t.nsub, t.max_b, t.max_bp, t.L, t.Lrev, t.dinv, t.r, 0,
-                                nullptr, t.Y, nullptr, t.status, t.st, false);
+                                nullptr, t.Y, nullptr, t.status, t.st, RK_C128);
       if (e == cudaSuccess) e = cudaEventRecord(e1, t.st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       if (e == cudaSuccess && r > 0) ms.push_back(ev_ms(e0, e1));

@@ -84,7 +84,28 @@ def test_fgmres_fixed_iterations_match_oracle(solver_cls, name, ortho):
         assert np.max(np.abs(h - np.array(ho)) / np.array(ho)) <= 1e-8
 
 
-@pytest.mark.parametrize("ortho", [0, 1, 2, 3])
+@pytest.mark.parametrize("name", ["tiny3", "small", "c0"])
+def test_fgmres_fixed_iterations_complex64_basis(solver_cls, name):
+    """ortho = 4 keeps the basis vectors as complex64 roundings: the first m
+    iterates then differ from exact-arithmetic FGMRES by the basis rounding
+    (2^-24 relative per vector, amplified by the conditioning of the small
+    least-squares problem): bounded by 1e-5 here."""
+    w = variant(name)
+    p = w.params()
+    grid, A, R = oracle_problem(w)
+    bo = fem.assemble_rhs(p, w.centres, w.amps, w.width)
+    m = 7
+    xo, _, _, ho = krylov.fgmres(A.dot, R.apply, bo, rtol=0.0, maxit=m)
+    with solver_cls(p, ortho=4) as s:
+        b = s.assemble_rhs(w.centres, w.amps, w.width)
+        x, it, relres, st = s.solve(b, rtol=0.0, maxit=m)
+        assert it == m and st == 1
+        assert rel(x.cpu().numpy(), xo) <= 1e-5
+        h = s.history()
+        assert np.max(np.abs(h - np.array(ho)) / np.array(ho)) <= 1e-5
+
+
+@pytest.mark.parametrize("ortho", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("name,kw", CASES[:6], ids=IDS[:6])
 def test_converged_solve_matches_direct_solve(solver_cls, name, kw, ortho):
     w = variant(name, **kw)
