@@ -299,26 +299,36 @@ __global__ void __launch_bounds__(kThreads)
   float rh[kDfCols], rl[kDfCols], ih[kDfCols], il[kDfCols];
 #pragma unroll
   for (int q = 0; q < kDfCols; ++q) rh[q] = rl[q] = ih[q] = il[q] = 0.f;
-  for (long long r = r0 + threadIdx.x; r < r1; r += kThreads) {
-    const dfc b = split_c(w[r]);
-    const dfl br = dfl_of(b.rh, b.rl), bi = dfl_of(b.ih, b.il);
-    c64 a[kDfCols];
+  // two rows per iteration, all loads issued before the arithmetic
+  for (long long r = r0 + threadIdx.x; r < r1; r += 2 * kThreads) {
+    const bool two = r + kThreads < r1;
+    c128 wv[2];
+    c64 a[2][kDfCols];
+    wv[0] = w[r];
+    wv[1] = two ? w[r + kThreads] : mk(0.0, 0.0);
 #pragma unroll
-    for (int q = 0; q < kDfCols; ++q)
-      if (q < nc) a[q] = V[(long long)(c0 + q) * ldv + r];
+    for (int u = 0; u < 2; ++u)
 #pragma unroll
-    for (int q = 0; q < kDfCols; ++q) {
-      if (q >= nc) continue;
-      float p, t;
-      // conj(a) w = (ar wr + ai wi) + i (ar wi - ai wr)
-      fdf_prod(a[q].re, br, p, t);
-      df_acc(rh[q], rl[q], p, t);
-      fdf_prod(a[q].im, bi, p, t);
-      df_acc(rh[q], rl[q], p, t);
-      fdf_prod(a[q].re, bi, p, t);
-      df_acc(ih[q], il[q], p, t);
-      fdf_prod(a[q].im, br, p, t);
-      df_acc(ih[q], il[q], -p, -t);
+      for (int q = 0; q < kDfCols; ++q)
+        a[u][q] = (q < nc && (u == 0 || two)) ? V[(long long)(c0 + q) * ldv + r + u * kThreads] : mk(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const dfc b = split_c(wv[u]);
+      const dfl br = dfl_of(b.rh, b.rl), bi = dfl_of(b.ih, b.il);
+#pragma unroll
+      for (int q = 0; q < kDfCols; ++q) {
+        if (q >= nc) continue;
+        float p, t;
+        // conj(a) w = (ar wr + ai wi) + i (ar wi - ai wr)
+        fdf_prod(a[u][q].re, br, p, t);
+        df_acc(rh[q], rl[q], p, t);
+        fdf_prod(a[u][q].im, bi, p, t);
+        df_acc(rh[q], rl[q], p, t);
+        fdf_prod(a[u][q].re, bi, p, t);
+        df_acc(ih[q], il[q], p, t);
+        fdf_prod(a[u][q].im, br, p, t);
+        df_acc(ih[q], il[q], -p, -t);
+      }
     }
   }
 #pragma unroll
@@ -341,13 +351,14 @@ __global__ void __launch_bounds__(kThreads)
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
     const dfc w0 = split_c(w[r]);
     float rh = w0.rh, rl = w0.rl, ih = w0.ih, il = w0.il;
-    for (int c0 = 0; c0 < ncols; c0 += kDfCols) {
-      c64 a[kDfCols];
+    constexpr int kU = 2 * kDfCols;   // basis entries loaded ahead of the arithmetic
+    for (int c0 = 0; c0 < ncols; c0 += kU) {
+      c64 a[kU];
 #pragma unroll
-      for (int q = 0; q < kDfCols; ++q)
+      for (int q = 0; q < kU; ++q)
         if (c0 + q < ncols) a[q] = V[(long long)(c0 + q) * ldv + r];   // loads first
 #pragma unroll
-      for (int q = 0; q < kDfCols; ++q) {
+      for (int q = 0; q < kU; ++q) {
         if (c0 + q >= ncols) continue;
         const dfc hc = hsc[c0 + q];
         const dfl hr = dfl_of(hc.rh, hc.rl), hi_ = dfl_of(hc.ih, hc.il);

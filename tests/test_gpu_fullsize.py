@@ -111,11 +111,15 @@ def test_c2_apply_on_single_cover_nodes(c2, prec, tol):
         assert np.linalg.norm(zs - c[single]) <= tol * np.linalg.norm(c[single])
 
 
-def test_c2_solve_in_bench_configuration(c2):
+@pytest.mark.parametrize("ortho", [4, 2])
+def test_c2_solve_in_bench_configuration(c2, ortho):
+    """The bench's headline form (complex64 factors, ortho = 4) and the
+    complex128 Gram-Schmidt form, each against the oracle's iteration count
+    and the complex128-factor solution."""
     from paper_2602_00735_gb300 import RasPml
     w, p, grid = c2
     gold = json.load(open(GOLD))["c2"]
-    with RasPml(p, factor_prec=1, ortho=2) as s:
+    with RasPml(p, factor_prec=1, ortho=ortho) as s:
         b = s.assemble_rhs(w.centres, w.amps, w.width)
         x, it, rel, st = s.solve(b, rtol=1e-6, maxit=1000)
         assert st == 0 and rel <= 1e-6
