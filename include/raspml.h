@@ -248,8 +248,9 @@ void ras_pml_destroy(ras_pml_handle* h);
  * per bulk copy) on the handle's own subdomains with CUDA events, keeps the
  * fastest for later calls, and leaves the handle factored (every shape
  * computes the same factors up to the rounding order of the rank-2 update).
- * Factor candidates: 128, 256, 512 threads with one pivot per pass, 256 and
- * 512 threads with two; apply columns 8, plus 4 and 16 when factor_prec = 1.
+ * Factor candidates: 128, 256, 512 threads with one pivot per pass, 256,
+ * 512 and 1024 threads with two; apply columns 8, plus 4 and 16 when
+ * factor_prec = 1.
  * Synchronises the stream.
  * ------------------------------------------------------------------------- */
 typedef struct {
@@ -269,9 +270,9 @@ typedef struct {
 int ras_pml_tune(ras_pml_handle* h, ras_pml_tune_t* report);
 
 /* Sets the tile shapes directly (e.g. those a tuning run chose for another
- * handle of the same sizes): factor_threads 128, 256 or 512; factor_rank 1
- * or 2; apply_cols 8, or 4 or 16 with factor_prec = 1. RASPML_EBADARG for
- * other values. */
+ * handle of the same sizes): factor_threads 128, 256 or 512 with
+ * factor_rank 1 or 2, or 1024 with factor_rank 2; apply_cols 8, or 4 or 16
+ * with factor_prec = 1. RASPML_EBADARG for other values. */
 int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, int apply_cols);
 
 /* ---------------------------------------------------------------------------

@@ -392,11 +392,11 @@ template <typename R, typename S, int NT>
 cudaError_t launch_factor_t(int rank, size_t smem, const SubDesc* subs, int nsub, const c128* Aloc, void* L,
                             void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
   cudaError_t e;
-  if (rank == 2) {
+  if (NT == 1024 || rank == 2) {
     e = cudaFuncSetAttribute(k_factor_ldlt2<R, S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_factor_ldlt2<R, S, NT><<<nsub, NT, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (cx<R>*)dinv, pivstats, status);
-  } else {
+  } else if constexpr (NT < 1024) {
     e = cudaFuncSetAttribute(k_factor_ldlt<R, S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_factor_ldlt<R, S, NT><<<nsub, NT, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (cx<R>*)dinv, pivstats, status);
@@ -411,6 +411,10 @@ cudaError_t launch_factor_s(int threads, int rank, size_t smem, const SubDesc* s
     case 128: return launch_factor_t<R, S, 128>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
     case 256: return launch_factor_t<R, S, 256>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
     case 512: return launch_factor_t<R, S, 512>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+    case 1024:
+      if (rank == 2)
+        return launch_factor_t<R, S, 1024>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+      break;
   }
   return cudaErrorInvalidValue;
 }
@@ -418,7 +422,8 @@ cudaError_t launch_factor_s(int threads, int rank, size_t smem, const SubDesc* s
 }  // namespace
 
 bool factor_shape_valid(int threads, int rank) {
-  return (threads == 128 || threads == 256 || threads == 512) && (rank == 1 || rank == 2);
+  return ((threads == 128 || threads == 256 || threads == 512) && (rank == 1 || rank == 2)) ||
+         (threads == 1024 && rank == 2);
 }
 
 cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, int nsub, int max_b,

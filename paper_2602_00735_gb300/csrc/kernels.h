@@ -35,7 +35,7 @@ struct KState {
 
 // Tile shapes of the factor and apply launches (chosen by the tuner).
 struct Tune {
-  int factor_threads = 256;   // threads per factor CTA: 128, 256, 512
+  int factor_threads = 256;   // threads per factor CTA: 128, 256, 512 (1024 with rank 2)
   int factor_rank = 2;        // pivots per pass over the window: 1 or 2
   int apply_cols = 8;         // band columns per bulk copy: 8 (4 or 16 with complex64 storage)
 };

@@ -28,9 +28,9 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
     return RASPML_ECUDA;
   }
   cudaError_t e = cudaSuccess;
-  const int fthreads[5] = {128, 256, 512, 256, 512};
-  const int franks[5] = {1, 1, 1, 2, 2};
-  for (int c = 0; c < 5 && e == cudaSuccess; ++c) {
+  const int fthreads[6] = {128, 256, 512, 256, 512, 1024};
+  const int franks[6] = {1, 1, 1, 2, 2, 2};
+  for (int c = 0; c < 6 && e == cudaSuccess; ++c) {
     std::vector<float> ms;
     for (int r = 0; r < reps && e == cudaSuccess; ++r) {
       e = cudaEventRecord(e0, t.st);

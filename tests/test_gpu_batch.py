@@ -109,8 +109,8 @@ def test_iterations_match_one_problem_solves(pkg, probs):
 def test_restarted_and_tuned_solve(pkg, probs):
     with pkg.BatchRasPml([w.params() for w in probs], factor_prec=1) as B:
         rep = B.tune()
-        assert rep["factor_threads"] in (128, 256, 512) and rep["apply_cols"] in (4, 8, 16)
-        assert set(rep["factor_ms"]) == {"128x1", "256x1", "512x1", "256x2", "512x2"}
+        assert rep["factor_threads"] in (128, 256, 512, 1024) and rep["apply_cols"] in (4, 8, 16)
+        assert set(rep["factor_ms"]) == {"128x1", "256x1", "512x1", "256x2", "512x2", "1024x2"}
         assert all(v > 0 for v in rep["factor_ms"].values())
         inf = B.info()
         assert (inf["factor_threads"], inf["factor_rank"], inf["apply_cols"]) == \

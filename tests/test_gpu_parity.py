@@ -239,7 +239,7 @@ def test_c64_fgmres_converges_to_fp64_solution(solver_cls, name, prec):
 # oracle's B^-1 at the precision's tolerance; two widths of subdomain (odd
 # and even half-bandwidths) on uneven boxes.
 
-@pytest.mark.parametrize("threads,rank", [(128, 1), (256, 1), (512, 1), (256, 2), (512, 2)])
+@pytest.mark.parametrize("threads,rank", [(128, 1), (256, 1), (512, 1), (256, 2), (512, 2), (1024, 2)])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4), (2, 2e-2)])
 @pytest.mark.parametrize("name,kw", [("small", {"px": 3, "py": 5}), ("tiny3", {})])
 def test_factor_shapes_match_oracle(solver_cls, name, kw, prec, tol, threads, rank):
