@@ -296,7 +296,8 @@ int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, i
  * (ras_pml_batch_layout); off_q is a multiple of 2048. Elements between
  * problems are ignored on input and written as zero on output.
  * All problems must share factor_prec; ortho is ignored (the Gram-Schmidt of
- * the batch is one classical pass in double-float arithmetic, as ortho = 3).
+ * the batch is one classical pass in double-float arithmetic on a complex64
+ * basis, as ortho = 4).
  * ------------------------------------------------------------------------- */
 typedef struct ras_pml_batch ras_pml_batch;
 
@@ -355,8 +356,8 @@ int ras_pml_batch_matvec(ras_pml_batch* h, const rp_c128* x_dev, rp_c128* y_dev)
 /* helmholtz_solve for every problem, in lockstep, from x0 = 0 (x_dev is
  * overwritten). Each problem stops on its own residual estimate or after
  * maxit directions; restart = 0 keeps one cycle (shortened, as for
- * helmholtz_solve, to the Krylov space that fits in free memory, (2m+1)*ntot*16
- * bytes, and to at most 1024 directions). iters_host[q] and relres_host[q] (host arrays) receive each
+ * helmholtz_solve, to the Krylov space that fits in free memory, about
+ * 24*m*ntot bytes, and to at most 1024 directions). iters_host[q] and relres_host[q] (host arrays) receive each
  * problem's directions and final true relative residual. Returns 0 when
  * every problem converged, RASPML_NOT_CONVERGED otherwise, or an error
  * (RASPML_ENAN if a problem's residual became non-finite). */

@@ -80,7 +80,7 @@ int ensure_krylov(ras_pml_batch* h, int m) {
   int s;
 #define BK_ALLOC(ptr, cnt) \
   if ((s = dalloc(&(ptr), (cnt))) != RASPML_OK) { free_krylov(h); return s; }
-  c128* v = nullptr;
+  rp::c64* v = nullptr;   // complex64 basis
   BK_ALLOC(v, (size_t)(m + 1) * h->ntot);
   h->V = v;
   BK_ALLOC(h->Z, (size_t)m * h->ntot);
@@ -498,13 +498,13 @@ int ras_pml_batch_solve(ras_pml_batch* h, const rp_c128* b, rp_c128* x, double r
   // every column in shared memory)
   int m = std::min(restart > 0 ? std::min(restart, maxit) : maxit, 1024);
   // cap the cycle at the Krylov space that fits in free memory (V and Z
-  // take 32 bytes per element and direction)
+  // take 8 + 16 bytes per element and direction)
   if (h->kcap < m) {
     free_krylov(h);
     size_t fr = 0, tot = 0;
     RP_CUDA(cudaMemGetInfo(&fr, &tot));
     const double reserve = 512.0 * (1 << 20) + 32.0 * (double)h->ntot;
-    const double per = 32.0 * (double)h->ntot + 16.0 * h->ntiles + 80.0 * h->nprob;
+    const double per = 24.0 * (double)h->ntot + 16.0 * h->ntiles + 80.0 * h->nprob;
     const double fit = ((double)fr - reserve) / per - 1.0;
     if (fit < 1.0) return RASPML_ENOMEM;
     m = std::min(m, (int)fit);

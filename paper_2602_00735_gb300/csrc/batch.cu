@@ -18,6 +18,7 @@ namespace rp {
 namespace {
 
 constexpr int kBT = 256;                   // threads per tile block
+constexpr double kBasisFloor = 1e-6;       // per-cycle reduction trusted on a complex64 basis
 constexpr int kRows = kBatchTile / kBT;    // rows per thread
 
 __device__ __forceinline__ bool gated(const KState* kst, int q, int gate) {
@@ -149,7 +150,10 @@ __global__ void __launch_bounds__(kBT)
 }
 
 // ---------------------------------------------------------------------------
-// Gram-Schmidt of step j in double-float arithmetic (see krylov.cu):
+// Gram-Schmidt of step j in double-float arithmetic on a complex64 basis
+// (the basis vectors are the complex64 roundings of w/||w||, used exactly as
+// stored; products of a float by the double-float split of w or h are FMA
+// residual pairs, sums are double-float):
 // k_bdots_df: partial[c * ntiles + t] = sum over tile t of conj(V_c) w,
 //   c = 0..j; the tile's rows of w are split once and held in registers,
 //   the columns are read four at a time; per-warp sums are kept in shared
@@ -157,8 +161,15 @@ __global__ void __launch_bounds__(kBT)
 // ---------------------------------------------------------------------------
 constexpr int kBCols = 4;
 
+// a * b for a float a and a double-float b, as p + t
+__device__ __forceinline__ void fdf_mul(float a, const dfl& b, float& p, float& t) {
+  p = a * b.hi;
+  const float e = fmaf(a, b.hi, -p);
+  t = fmaf(a, b.lo, e);
+}
+
 __global__ void __launch_bounds__(kBT)
-    k_bdots_df(const int* __restrict__ tile_prob, const dfc* __restrict__ V, long long ldv,
+    k_bdots_df(const int* __restrict__ tile_prob, const c64* __restrict__ V, long long ldv,
                const c128* __restrict__ w, const int* __restrict__ jptr, c128* __restrict__ partial, int ntiles,
                const KState* __restrict__ kst) {
   extern __shared__ c128 wsum[];   // [ncols][kBT / 32]
@@ -181,23 +192,22 @@ __global__ void __launch_bounds__(kBT)
     for (int u = 0; u < kBCols; ++u) rh[u] = rl[u] = ih[u] = il[u] = 0.f;
 #pragma unroll
     for (int s = 0; s < kRows; ++s) {
-      dfc a[kBCols];
+      c64 a[kBCols];
 #pragma unroll
       for (int u = 0; u < kBCols; ++u)
         if (c0 + u < ncols) a[u] = V[(long long)(c0 + u) * ldv + r0 + s * kBT];
 #pragma unroll
       for (int u = 0; u < kBCols; ++u) {
         if (c0 + u >= ncols) continue;
-        const dfl ar = dfl_of(a[u].rh, a[u].rl), ai = dfl_of(a[u].ih, a[u].il);
         float p, e;
         // conj(a) w = (ar wr + ai wi) + i (ar wi - ai wr)
-        df_prod(ar, wr[s], p, e);
+        fdf_mul(a[u].re, wr[s], p, e);
         df_acc(rh[u], rl[u], p, e);
-        df_prod(ai, wi[s], p, e);
+        fdf_mul(a[u].im, wi[s], p, e);
         df_acc(rh[u], rl[u], p, e);
-        df_prod(ar, wi[s], p, e);
+        fdf_mul(a[u].re, wi[s], p, e);
         df_acc(ih[u], il[u], p, e);
-        df_prod(ai, wr[s], p, e);
+        fdf_mul(a[u].im, wr[s], p, e);
         df_acc(ih[u], il[u], -p, -e);
       }
     }
@@ -240,7 +250,7 @@ __global__ void __launch_bounds__(kBT)
 // w -= sum_{c<=j} V_c H_q(c, j) with double-float accumulation; then
 // pnorm[t] = sum over the tile of |w|^2 (FP64).
 __global__ void __launch_bounds__(kBT)
-    k_baxpys_df(const int* __restrict__ tile_prob, const dfc* __restrict__ V, long long ldv,
+    k_baxpys_df(const int* __restrict__ tile_prob, const c64* __restrict__ V, long long ldv,
                 const c128* __restrict__ H, int ldh, long long hstride, const int* __restrict__ jptr,
                 c128* __restrict__ w, double* __restrict__ pnorm, const KState* __restrict__ kst) {
   extern __shared__ dfc hsd[];
@@ -258,26 +268,25 @@ __global__ void __launch_bounds__(kBT)
     const long long r = r0 + s * kBT;
     const dfc w0 = split_c(w[r]);
     float rh = w0.rh, rl = w0.rl, ih = w0.ih, il = w0.il;
-    for (int c0 = 0; c0 < ncols; c0 += kBCols) {
-      dfc a[kBCols];
+    for (int c0 = 0; c0 < ncols; c0 += 2 * kBCols) {
+      c64 a[2 * kBCols];
 #pragma unroll
-      for (int u = 0; u < kBCols; ++u)
-        if (c0 + u < ncols) a[u] = V[(long long)(c0 + u) * ldv + r];
+      for (int u = 0; u < 2 * kBCols; ++u)
+        if (c0 + u < ncols) a[u] = V[(long long)(c0 + u) * ldv + r];   // loads first
 #pragma unroll
-      for (int u = 0; u < kBCols; ++u) {
+      for (int u = 0; u < 2 * kBCols; ++u) {
         if (c0 + u >= ncols) continue;
         const dfc hc = hsd[c0 + u];
-        const dfl ar = dfl_of(a[u].rh, a[u].rl), ai = dfl_of(a[u].ih, a[u].il);
         const dfl hr = dfl_of(hc.rh, hc.rl), hi_ = dfl_of(hc.ih, hc.il);
         float p, e;
         // a h = (ar hr - ai hi) + i (ar hi + ai hr)
-        df_prod(ar, hr, p, e);
+        fdf_mul(a[u].re, hr, p, e);
         df_acc(rh, rl, p, e);
-        df_prod(ai, hi_, p, e);
+        fdf_mul(a[u].im, hi_, p, e);
         df_acc(rh, rl, -p, -e);
-        df_prod(ar, hi_, p, e);
+        fdf_mul(a[u].re, hi_, p, e);
         df_acc(ih, il, p, e);
-        df_prod(ai, hr, p, e);
+        fdf_mul(a[u].im, hr, p, e);
         df_acc(ih, il, p, e);
       }
     }
@@ -350,16 +359,19 @@ __global__ void k_bnorm_givens(const int* __restrict__ tile0, const int* __restr
   if (est <= rtol) { k.conv = 1; stop = 1; }
   if (hn == 0.0) { k.breakdown = 1; stop = 1; }
   if (j + 1 >= m || k.total >= maxit) stop = 1;
+  // one cycle on the complex64 basis is trusted down to 1e-6 of its start;
+  // below that the next cycle starts from the true residual
+  if (sqrt(abs2(gq[j + 1])) <= kBasisFloor * k.beta0) stop = 1;
   if (stop) {
     k.stop = 1;
     atomicSub(&ctl->active, 1);
   }
 }
 
-// v_{j+1} = split(w / h_{j+1,j}) for problems whose cycle continues; with
-// jptr == nullptr, v_0 = split(w / beta) at a cycle start (beta in hnorm).
+// v_{j+1} = fl32(w / h_{j+1,j}) for problems whose cycle continues; with
+// jptr == nullptr, v_0 = fl32(w / beta) at a cycle start (beta in hnorm).
 __global__ void __launch_bounds__(kBT)
-    k_bscale_df(const int* __restrict__ tile_prob, const c128* __restrict__ w, dfc* __restrict__ V, long long ldv,
+    k_bscale_df(const int* __restrict__ tile_prob, const c128* __restrict__ w, c64* __restrict__ V, long long ldv,
                 const int* __restrict__ jptr, const KState* __restrict__ kst) {
   const int t = blockIdx.x;
   const int q = tile_prob[t];
@@ -367,12 +379,12 @@ __global__ void __launch_bounds__(kBT)
   const double d = kst[q].hnorm;
   if (!(d > 0.0)) return;
   const double sc = 1.0 / d;
-  dfc* v = V + (jptr ? (long long)(*jptr + 1) * ldv : 0);
+  c64* v = V + (jptr ? (long long)(*jptr + 1) * ldv : 0);
 #pragma unroll 2
   for (int s = 0; s < kRows; ++s) {
     const long long r = (long long)t * kBatchTile + s * kBT + threadIdx.x;
     const c128 x = w[r];
-    v[r] = split_c(mk(sc * x.re, sc * x.im));
+    v[r] = mk((float)(sc * x.re), (float)(sc * x.im));
   }
 }
 
@@ -400,6 +412,7 @@ __global__ void k_bcycle_init(const int* __restrict__ tile0, const int* __restri
   k.relres = rel;
   k.jdone = 0;
   k.hnorm = beta;
+  k.beta0 = beta;
   if (!isfinite(beta) || !isfinite(rel)) {
     k.nan = 1;
     k.live = 0;
@@ -487,7 +500,7 @@ cudaError_t launch_bstep(const BStep& a, cudaStream_t st) {
   const int* jp = &a.ctl->j;
   cudaError_t e = cudaSuccess;
   const size_t dsm = (size_t)(a.m + 1) * (kBT / 32) * sizeof(c128);
-  const size_t hsm = (size_t)(a.m + 1) * sizeof(dfc);
+  const size_t hsm = (size_t)(a.m + 1) * sizeof(dfc);   // h column split, double-float
   if (dsm > 48 * 1024) {
     e = cudaFuncSetAttribute(k_bdots_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
     if (e != cudaSuccess) return e;
@@ -497,21 +510,21 @@ cudaError_t launch_bstep(const BStep& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
   }
   e = launch_local_solves(a.prec, a.cols, a.geos, a.subs, a.nsub, a.max_b, a.max_bp, a.L, a.Lrev, a.dinv,
-                          (const c128*)a.V, a.ld, jp, a.Y, a.kst, a.status, st, RK_DF);
+                          (const c128*)a.V, a.ld, jp, a.Y, a.kst, a.status, st, RK_C64);
   if (e != cudaSuccess) return e;
   e = launch_bprolong(a.prec, a.ntiles, a.tile_prob, a.geos, a.subs, a.sub_index, a.Y, a.Z, a.ld, jp, a.kst, 1, st);
   if (e != cudaSuccess) return e;
   e = launch_bspmv(a.ntiles, a.tile_prob, a.geos, a.D, a.CW, a.CS, a.CSW, a.Z, a.ld, jp, nullptr, a.w, nullptr,
                    a.kst, 1, st);
   if (e != cudaSuccess) return e;
-  k_bdots_df<<<a.ntiles, kBT, dsm, st>>>(a.tile_prob, (const dfc*)a.V, a.ld, a.w, jp, a.partial, a.ntiles, a.kst);
+  k_bdots_df<<<a.ntiles, kBT, dsm, st>>>(a.tile_prob, (const c64*)a.V, a.ld, a.w, jp, a.partial, a.ntiles, a.kst);
   k_bdots_finish<<<a.nprob, kBT, 0, st>>>(a.tile0, a.tile1, a.partial, a.ntiles, jp, a.H, a.m + 1, a.hstride,
                                           a.kst);
-  k_baxpys_df<<<a.ntiles, kBT, hsm, st>>>(a.tile_prob, (const dfc*)a.V, a.ld, a.H, a.m + 1, a.hstride, jp, a.w,
+  k_baxpys_df<<<a.ntiles, kBT, hsm, st>>>(a.tile_prob, (const c64*)a.V, a.ld, a.H, a.m + 1, a.hstride, jp, a.w,
                                           a.pnorm, a.kst);
   k_bnorm_givens<<<a.nprob, 32, 0, st>>>(a.tile0, a.tile1, a.pnorm, jp, a.ctl, a.H, a.m + 1, a.hstride, a.cs, a.sn,
                                          a.gvec, a.m, a.rtol, a.maxit, a.kst);
-  k_bscale_df<<<a.ntiles, kBT, 0, st>>>(a.tile_prob, a.w, (dfc*)a.V, a.ld, jp, a.kst);
+  k_bscale_df<<<a.ntiles, kBT, 0, st>>>(a.tile_prob, a.w, (c64*)a.V, a.ld, jp, a.kst);
   k_bnext<<<1, 1, 0, st>>>(a.ctl);
   return cudaGetLastError();
 }
@@ -521,7 +534,7 @@ cudaError_t launch_bcycle_start(const BStep& a, const c128* b, const c128* x, in
                                a.pnorm, a.kst, 2, st);
   if (e != cudaSuccess) return e;
   k_bcycle_init<<<a.nprob, 32, 0, st>>>(a.tile0, a.tile1, a.pnorm, a.ctl, a.gvec, a.m, a.rtol, a.maxit, first, a.kst);
-  k_bscale_df<<<a.ntiles, kBT, 0, st>>>(a.tile_prob, a.w, (dfc*)a.V, a.ld, nullptr, a.kst);
+  k_bscale_df<<<a.ntiles, kBT, 0, st>>>(a.tile_prob, a.w, (c64*)a.V, a.ld, nullptr, a.kst);
   return cudaGetLastError();
 }
 

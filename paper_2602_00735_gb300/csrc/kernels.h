@@ -146,7 +146,7 @@ struct BStep {
   const void *L, *Lrev, *dinv;
   void* Y;
   const c128 *D, *CW, *CS, *CSW;
-  void* V;                // (m+1) x ld double-float basis
+  void* V;                // (m+1) x ld complex64 basis
   c128* Z;                // m x ld preconditioned directions
   long long ld;           // batch vector length
   c128* w;

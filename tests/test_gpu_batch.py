@@ -93,14 +93,14 @@ def test_lockstep_solve_matches_direct_solves(pkg, probs, prec):
 
 def test_iterations_match_one_problem_solves(pkg, probs):
     """Lockstep FGMRES takes, per problem, the iterations of the one-problem
-    solver with the same Gram-Schmidt (double-float CGS, ortho = 3); sums in
-    a different order may move the stopping step by one."""
+    solver with the same Gram-Schmidt (double-float CGS on a complex64 basis,
+    ortho = 4); sums in a different order may move the stopping step by one."""
     with pkg.BatchRasPml([w.params() for w in probs], factor_prec=1) as B:
         b = B.assemble_rhs(_sources(probs))
         _, it, _, st = B.solve(b, rtol=1e-6, maxit=400)
         assert st == 0
         for q, w in enumerate(probs):
-            with pkg.RasPml(w.params(), factor_prec=1, ortho=3) as s:
+            with pkg.RasPml(w.params(), factor_prec=1, ortho=4) as s:
                 bq = s.assemble_rhs(w.centres, w.amps, w.width)
                 _, its, _, _ = s.solve(bq, rtol=1e-6, maxit=400)
             assert abs(int(it[q]) - its) <= 1, (q, it[q], its)
