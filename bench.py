@@ -30,6 +30,9 @@ residual of 1e-6.
 factored and solved to rtol 1e-6 in the same launches (complex64 factors,
 lockstep FGMRES in complex128, one Arnoldi step per CUDA graph replay).
 
+--workload net times the learned correction's network alone (forward pass on
+one 256^2 image, training steps on 8), against the bf16 tensor peak.
+
 --impl reference times the oracle alone (the reference arm of this repo).
 Multi-GPU (torchrun): every rank solves its own replica of the workload; no
 data-path collective. Inputs (factors of 4-17 GB) are far larger than L2.
@@ -611,6 +614,68 @@ def run_batch(args, rank, world, local_rank):
 
 
 
+def run_net(args, rank, world, local_rank):
+    """The learned correction's network alone (tensor-core 3x3 convolutions):
+    forward passes on one 256^2 image and training steps (forward, backward,
+    Adam) on batches of 8, random inputs; the roofline object is the forward
+    pass against the measured bf16 tensor peak."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2602_00735_gb300.net import Net
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    Nc, B = 256, 8
+    net = Net(Nc=Nc, cap=B, seed=0)
+    x = torch.randn(B, 2, Nc, Nc, device=dev, dtype=torch.float32)
+    t = torch.randn(B, 2, Nc, Nc, device=dev, dtype=torch.float32)
+    for _ in range(args.warmup):
+        net.forward(x[:1])
+        net.loss_grad(x, t, want_grad=False)
+        net.adam_step(1e-4)
+    torch.cuda.synchronize()
+    tf, tt = [], []
+    for _ in range(args.steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        net.forward(x[:1])
+        e1.record(stream)
+        net.loss_grad(x, t, want_grad=False)
+        net.adam_step(1e-4)
+        e2.record(stream)
+        e2.synchronize()
+        tf.append(e0.elapsed_time(e1) / 1e3)
+        tt.append(e1.elapsed_time(e2) / 1e3)
+    net.close()
+    ch = net_channels()
+    flop_real = 2 * Nc * Nc * 9 * sum(a * b for a, b in zip(ch, ch[1:]))
+    pad = (16, 32, 32, 32, 32, 32, 16)   # channels as the tensor cores run them
+    flop_tc = 2 * Nc * Nc * 9 * sum(a * b for a, b in zip(pad, pad[1:]))
+    tfw = float(np.median(tf))
+    mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(mp.get("bf16_tflops", 1900.0))
+    if rank != 0:
+        return
+    out = {"metric": "learned-correction network: one forward pass on a 256^2 image (ms)",
+           "value": round(1e3 * tfw, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(1e3 * tfw, 4), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+           "config": {"workload": "net: 6 layers 3x3, channels 2-32-32-32-32-32-2, 256^2 grid, batch 8 for training",
+                      "l2": "activations resident in L2 (4 MB per layer)"},
+           "train_step_ms_8img": round(1e3 * float(np.median(tt)), 3),
+           "roofline": {"kernel": "k_conv_tc (forward, 6 launches)", "bound": "tensor",
+                        "achieved": round(flop_tc / tfw / 1e12, 2), "peak": peak,
+                        "peak_kind": "measured" if mp else "fallback", "unit": "TFLOP/s",
+                        "frac": round(flop_tc / tfw / 1e12 / peak, 4), "traffic": None,
+                        "flop_per_launch_set": flop_tc, "flop_real_channels": flop_real},
+           "gpu_launches": 6 * args.steps, "e2e": None}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference_batch(args, world):
     probs = workloads.batch("c3")
     iters = batch_iterations_golden()
@@ -638,6 +703,10 @@ def run_reference(args, rank, world):
         return
     if args.workload == "c3":
         run_reference_batch(args, world)
+        return
+    if args.workload == "net":
+        print(json.dumps({"impl": "reference", "unavailable": "the network has no timed reference arm "
+                                                             "(the paper has no learned component)"}))
         return
     w = workloads.get(args.workload)
     iters = oracle_iterations(w)
@@ -693,6 +762,8 @@ def main():
     try:
         if args.workload in workloads.BATCH_NAMES:
             run_batch(args, rank, world, local_rank)
+        elif args.workload == "net":
+            run_net(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

@@ -77,10 +77,7 @@ struct ConvSmem {
   static constexpr int K = 9 * CI;
   static constexpr int A_BYTES = kConvPix * K * 2;
   static constexpr int B_BYTES = CO * K * 2;
-  // room after A and B so that a descriptor read with LBO and SBO in either
-  // order stays inside the allocation
-  static constexpr int SLACK = 32 * 1024;
-  static constexpr int BYTES = A_BYTES + B_BYTES + SLACK + 64;
+  static constexpr int BYTES = A_BYTES + B_BYTES + 64;
 };
 
 }  // namespace
@@ -99,7 +96,7 @@ __global__ void __launch_bounds__(128)
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* A = sm;
   unsigned char* B = sm + SM::A_BYTES;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + SM::A_BYTES + SM::B_BYTES + SM::SLACK);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + SM::A_BYTES + SM::B_BYTES);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long npix = (long long)H * X;
@@ -132,7 +129,7 @@ __global__ void __launch_bounds__(128)
     const long long p = p0 + m;
     const int y = (int)(p / X), x = (int)(p % X);
     const bool live = p < npix;
-#pragma unroll 1
+#pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
       const int sy = y + tap / 3 - 1, sx = x + tap % 3 - 1;
       const bool ok = live && sy >= 0 && sy < H && sx >= 0 && sx < X;

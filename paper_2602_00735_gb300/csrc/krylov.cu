@@ -331,11 +331,21 @@ __global__ void __launch_bounds__(kThreads)
       }
     }
   }
+  // the kDfCols sums of the block in one pass: shuffles within each warp,
+  // one barrier, then the first warp adds the warps' values
+  __shared__ c128 red[kThreads / 32][kDfCols];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < kDfCols; ++q) {
-    if (q >= nc) break;
-    c128 s = block_sum(mk(df_to_d(rh[q], rl[q]), df_to_d(ih[q], il[q])));
-    if (threadIdx.x == 0) partial[(long long)(c0 + q) * gridDim.x + blockIdx.x] = s;
+    const c128 v = warp_sum(mk(df_to_d(rh[q], rl[q]), df_to_d(ih[q], il[q])));
+    if (lane == 0) red[wid][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nc) {
+    c128 s = mk(0.0, 0.0);
+#pragma unroll
+    for (int u = 0; u < kThreads / 32; ++u) s = s + red[u][threadIdx.x];
+    partial[(long long)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
   }
 }
 
