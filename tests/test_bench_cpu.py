@@ -29,6 +29,16 @@ def test_reference_arm_prints_one_json_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0
 
 
+def test_reference_arm_for_the_batched_workload():
+    """--workload c3: the oracle's bounded sample on the median problem, scaled
+    by the oracle's own per-problem iteration counts (tests/golden)."""
+    r = _run(["--impl", "reference", "--workload", "c3", "--steps", "1", "--warmup", "0"], {})
+    assert r.returncode == 0, r.stderr
+    d = json.loads([ln for ln in r.stdout.splitlines() if ln.strip()][0])
+    assert d["impl"] == "reference" and d["value"] > 0 and "64 independent problems" in d["metric"]
+    assert "scaled to all 64 problems" in d["cpu_baseline"]["sample"]
+
+
 def test_reference_arm_runs_on_rank_zero_only():
     r = _run(["--impl", "reference", "--workload", "tiny3", "--steps", "1", "--warmup", "0"],
              {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})

@@ -9,6 +9,9 @@ bench.py times (complex64 factors, tuned tile shapes, rtol 1e-6):
 - rows of A x of the largest problem at sampled nodes (oracle assembly of
   the cells around each node).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -18,6 +21,7 @@ from gpu_util import random_vector
 from oracle import fem
 
 pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "oracle_iterations.json")
 
 
 @pytest.fixture(scope="module")
@@ -38,6 +42,9 @@ def test_c3_solve_in_bench_configuration(c3):
     x, it, relres, st = B.solve(b, rtol=1e-6, maxit=400)
     assert st == 0 and np.all(relres <= 1e-6)
     assert it.min() >= 1 and it.max() <= 400
+    # every problem takes the oracle's own FGMRES count (tests/golden/oracle_iterations.json)
+    gold = np.array(json.load(open(GOLD))["c3"]["iters"])
+    assert np.max(np.abs(it - gold)) <= 1, np.abs(it - gold).max()
     order = np.argsort([w.n_unknowns for w in probs])
     for q in order[:3]:
         w = probs[q]
