@@ -454,6 +454,10 @@ def run_ours(args, rank, world, local_rank):
                       "ortho": round(last["ortho_ms"], 2),
                       "setup_and_rest": round(mean_t * 1e3 - last["factor_ms"] - last["solve_ms"], 2)},
         "apply_gbs": round(achieved, 1),
+        "applies_per_s": round(1.0 / avg_apply_s, 1),
+        # one timed SpMV per direction: 4 coefficient arrays, x and y (96 bytes per row)
+        "spmv_gbs": round(96.0 * info["n"] * sum(q["applies"] for q in per_c64)
+                          / max(1e-9, sum(q["spmv_ms"] for q in per_c64) / 1e3) / 1e9, 1),
         "roofline": {"kernel": "ras_pml_apply (k_apply + k_prolong), complex64", "bound": "hbm",
                      "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
