@@ -97,7 +97,10 @@ typedef struct {
                                projections use those values exactly; the
                                rounding perturbs the Arnoldi relation by
                                ~1e-7 relative, which the true-residual check
-                               at the end of each cycle catches)               */
+                               at the end of each cycle catches).
+                             With 3 and 4 the Arnoldi products w = A z_j are
+                             double-float too (coefficients split once at
+                             set-up); the true residual stays complex128.     */
   int    g_profile;       /* stretching: 0 g'(d) as above; 1 g(d) = g_amp d^3,
                              i.e. g'(d) = 3 g_amp d^2 (the paper's experiments
                              use g_amp = 10k, Section 4); g_ramp unused        */

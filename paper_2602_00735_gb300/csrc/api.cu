@@ -30,6 +30,7 @@ struct ras_pml_handle {
   int nsub = 0, max_b = 0, max_bp = 0, max_npad = 0, max_n = 0;
   long long n = 0, sum_npad = 0, sum_l = 0, sum_n = 0, sum_bn = 0;
   c128 *D = nullptr, *CW = nullptr, *CS = nullptr, *CSW = nullptr;
+  c128 *Ddf = nullptr, *CWdf = nullptr, *CSdf = nullptr, *CSWdf = nullptr;   // the same, split (ortho >= 3)
   void *L = nullptr, *Lrev = nullptr, *dinv = nullptr, *Y = nullptr;
   double* pivstats = nullptr;
   rp::DevStatus* status = nullptr;
@@ -245,6 +246,7 @@ void ras_pml_destroy(ras_pml_handle* h) {
   if (!h) return;
   cudaSetDevice(h->dev);
   if (h->st) cudaStreamSynchronize(h->st);
+  dfree(h->Ddf); dfree(h->CWdf); dfree(h->CSdf); dfree(h->CSWdf);
   dfree(h->subs_d); dfree(h->geo_d); dfree(h->D); dfree(h->CW); dfree(h->CS); dfree(h->CSW);
   dfree(h->L); dfree(h->Lrev); dfree(h->dinv); dfree(h->Y); dfree(h->pivstats); dfree(h->status);
   dfree(h->V); dfree(h->Z); dfree(h->H); dfree(h->sn); dfree(h->gvec); dfree(h->yv);
@@ -308,6 +310,15 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   c128* tab = nullptr;
   if (e == cudaSuccess) e = cudaMalloc((void**)&tab, sizeof(c128) * rp::stretch_table_elems(g));
   if (e == cudaSuccess) e = rp::launch_global_stencil(g, tab, h->D, h->CW, h->CS, h->CSW, h->st);
+  if (e == cudaSuccess && h->p.ortho >= 3) {
+    // the Arnoldi products of the double-float forms use the split coefficients
+    c128* src[4] = {h->D, h->CW, h->CS, h->CSW};
+    c128** dst[4] = {&h->Ddf, &h->CWdf, &h->CSdf, &h->CSWdf};
+    for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
+      e = cudaMalloc((void**)dst[q], sizeof(c128) * h->n);
+      if (e == cudaSuccess) e = rp::launch_split(src[q], *dst[q], h->n, nullptr, h->st);
+    }
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (tab) cudaFree(tab);
   if (e != cudaSuccess) {
@@ -614,7 +625,10 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
           RP_CUDA(rp::launch_mr_axpy(zj, h->lc, h->lhv, n, h->kst, st));
         }
         if (h->timing) RP_CUDA(cudaEventRecord(evj[1], st));
-        RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, nullptr, w, h->kst, st));
+        if (h->Ddf)
+          RP_CUDA(rp::launch_spmv_df(n, h->geo.nx, h->Ddf, h->CWdf, h->CSdf, h->CSWdf, zj, w, h->kst, st));
+        else
+          RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, nullptr, w, h->kst, st));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[2], st));
         if (h->p.ortho == 0) {
           // classical Gram-Schmidt, twice

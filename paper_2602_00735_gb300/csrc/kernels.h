@@ -78,6 +78,9 @@ cudaError_t launch_apply(int prec, int cols, const Geo& g, const Geo* geos, cons
 cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, const c128* CS, const c128* CSW,
                         const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st,
                         int bsub_kind = RK_C128);
+// y = A x with double-float coefficients (dfc arrays from launch_split)
+cudaError_t launch_spmv_df(long long n, int nx, const void* D, const void* CW, const void* CS, const void* CSW,
+                           const c128* x, c128* y, const KState* kst, cudaStream_t st);
 int dot_blocks();
 cudaError_t launch_dots(const c128* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
                         const KState* kst, int gate, cudaStream_t st);

@@ -82,6 +82,43 @@ __global__ void k_spmv(long long n, int nx, const c128* __restrict__ D, const c1
   }
 }
 
+// y = A x with the coefficients in double-float form (split once at set-up)
+// and the products and sums in double-float arithmetic on the FP32 pipe
+// (about 46 bits): the Arnoldi products w = A z_j. The true residual keeps
+// the FP64 k_spmv.
+__device__ __forceinline__ void cmac_df(float& rh, float& rl, float& ih, float& il, const dfc& a, const dfc& x) {
+  const dfl ar = dfl_of(a.rh, a.rl), ai = dfl_of(a.ih, a.il);
+  const dfl xr = dfl_of(x.rh, x.rl), xi = dfl_of(x.ih, x.il);
+  float p, t;
+  // a x = (ar xr - ai xi) + i (ar xi + ai xr)
+  df_prod(ar, xr, p, t);
+  df_acc(rh, rl, p, t);
+  df_prod(ai, xi, p, t);
+  df_acc(rh, rl, -p, -t);
+  df_prod(ar, xi, p, t);
+  df_acc(ih, il, p, t);
+  df_prod(ai, xr, p, t);
+  df_acc(ih, il, p, t);
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_spmv_df(long long n, int nx, const dfc* __restrict__ D, const dfc* __restrict__ CW,
+              const dfc* __restrict__ CS, const dfc* __restrict__ CSW, const c128* __restrict__ x,
+              c128* __restrict__ y, const KState* __restrict__ kst) {
+  if (kst != nullptr && kst->stop) return;
+  const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  cmac_df(rh, rl, ih, il, D[r], split_c(x[r]));
+  if (r >= 1) cmac_df(rh, rl, ih, il, CW[r], split_c(x[r - 1]));
+  if (r + 1 < n) cmac_df(rh, rl, ih, il, CW[r + 1], split_c(x[r + 1]));
+  if (r >= nx) cmac_df(rh, rl, ih, il, CS[r], split_c(x[r - nx]));
+  if (r + nx < n) cmac_df(rh, rl, ih, il, CS[r + nx], split_c(x[r + nx]));
+  if (r >= nx + 1) cmac_df(rh, rl, ih, il, CSW[r], split_c(x[r - nx - 1]));
+  if (r + nx + 1 < n) cmac_df(rh, rl, ih, il, CSW[r + nx + 1], split_c(x[r + nx + 1]));
+  y[r] = mk(df_to_d(rh, rl), df_to_d(ih, il));
+}
+
 // partial[c * gridDim.x + blk] = sum over the block's rows of conj(V_c) w
 __global__ void __launch_bounds__(kThreads)
     k_dots(const c128* __restrict__ V, long long ldv, const c128* __restrict__ w, long long n,
@@ -560,6 +597,14 @@ cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, cons
                         const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st, int bsub_kind) {
   unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
   k_spmv<<<blocks, kThreads, 0, st>>>(n, nx, D, CW, CS, CSW, x, bsub, bsub_kind, y, kst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_df(long long n, int nx, const void* D, const void* CW, const void* CS, const void* CSW,
+                           const c128* x, c128* y, const KState* kst, cudaStream_t st) {
+  unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
+  k_spmv_df<<<blocks, kThreads, 0, st>>>(n, nx, (const dfc*)D, (const dfc*)CW, (const dfc*)CS, (const dfc*)CSW, x, y,
+                                         kst);
   return cudaGetLastError();
 }
 
