@@ -34,6 +34,7 @@ struct ras_pml_batch {
   SubDesc* subs_d = nullptr;
   int *sub_index_d = nullptr, *tile_prob_d = nullptr, *tile0_d = nullptr, *tile1_d = nullptr;
   c128 *D = nullptr, *CW = nullptr, *CS = nullptr, *CSW = nullptr;
+  c128 *Ddf = nullptr, *CWdf = nullptr, *CSdf = nullptr, *CSWdf = nullptr;   // split, for the Arnoldi SpMV
   void *L = nullptr, *Lrev = nullptr, *dinv = nullptr, *Y = nullptr;
   double* pivstats = nullptr;
   rp::DevStatus* status = nullptr;
@@ -123,6 +124,10 @@ rp::BStep step_args(ras_pml_batch* h, int m, double rtol, int maxit) {
   a.CW = h->CW;
   a.CS = h->CS;
   a.CSW = h->CSW;
+  a.Ddf = h->Ddf;
+  a.CWdf = h->CWdf;
+  a.CSdf = h->CSdf;
+  a.CSWdf = h->CSWdf;
   a.V = h->V;
   a.Z = h->Z;
   a.ld = h->ntot;
@@ -184,6 +189,7 @@ void ras_pml_batch_destroy(ras_pml_batch* h) {
   free_krylov(h);
   dfree(h->geos_d); dfree(h->subs_d); dfree(h->sub_index_d); dfree(h->tile_prob_d); dfree(h->tile0_d);
   dfree(h->tile1_d); dfree(h->D); dfree(h->CW); dfree(h->CS); dfree(h->CSW); dfree(h->L); dfree(h->Lrev);
+  dfree(h->Ddf); dfree(h->CWdf); dfree(h->CSdf); dfree(h->CSWdf);
   dfree(h->dinv); dfree(h->Y); dfree(h->pivstats); dfree(h->status); dfree(h->kst); dfree(h->ctl);
   if (h->kst_host) cudaFreeHost(h->kst_host);
   if (h->active_host) cudaFreeHost(h->active_host);
@@ -258,6 +264,10 @@ int ras_pml_batch_setup(const ras_pml_params* params, int nprob, void* stream, r
   BS_ALLOC(h->CW, (size_t)h->ntot);
   BS_ALLOC(h->CS, (size_t)h->ntot);
   BS_ALLOC(h->CSW, (size_t)h->ntot);
+  BS_ALLOC(h->Ddf, (size_t)h->ntot);
+  BS_ALLOC(h->CWdf, (size_t)h->ntot);
+  BS_ALLOC(h->CSdf, (size_t)h->ntot);
+  BS_ALLOC(h->CSWdf, (size_t)h->ntot);
   BS_ALLOC(h->pivstats, (size_t)2 * h->nsub);
   BS_ALLOC(h->status, (size_t)1);
   BS_ALLOC(h->kst, (size_t)nprob);
@@ -289,6 +299,10 @@ int ras_pml_batch_setup(const ras_pml_params* params, int nprob, void* stream, r
     const long long o = h->geos_h[q].goff;
     e = rp::launch_global_stencil(h->geos_h[q], tab, h->D + o, h->CW + o, h->CS + o, h->CSW + o, h->st);
   }
+  if (e == cudaSuccess) e = rp::launch_split(h->D, h->Ddf, h->ntot, nullptr, h->st);
+  if (e == cudaSuccess) e = rp::launch_split(h->CW, h->CWdf, h->ntot, nullptr, h->st);
+  if (e == cudaSuccess) e = rp::launch_split(h->CS, h->CSdf, h->ntot, nullptr, h->st);
+  if (e == cudaSuccess) e = rp::launch_split(h->CSW, h->CSWdf, h->ntot, nullptr, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (tab) cudaFree(tab);
   if (e != cudaSuccess) {

@@ -149,6 +149,55 @@ __global__ void __launch_bounds__(kBT)
   }
 }
 
+// The Arnoldi product w = A z_j of step j with the coefficients in
+// double-float form (split once at set-up) and double-float products and
+// sums; the cycle-start residual b - A x keeps the FP64 k_bspmv.
+__device__ __forceinline__ void bcmac_df(float& rh, float& rl, float& ih, float& il, const dfc& a, const c128& xv) {
+  const dfc x = split_c(xv);
+  const dfl ar = dfl_of(a.rh, a.rl), ai = dfl_of(a.ih, a.il);
+  const dfl xr = dfl_of(x.rh, x.rl), xi = dfl_of(x.ih, x.il);
+  float p, t;
+  df_prod(ar, xr, p, t);
+  df_acc(rh, rl, p, t);
+  df_prod(ai, xi, p, t);
+  df_acc(rh, rl, -p, -t);
+  df_prod(ar, xi, p, t);
+  df_acc(ih, il, p, t);
+  df_prod(ai, xr, p, t);
+  df_acc(ih, il, p, t);
+}
+
+__global__ void __launch_bounds__(kBT)
+    k_bspmv_df(const int* __restrict__ tile_prob, const Geo* __restrict__ geos, const dfc* __restrict__ D,
+               const dfc* __restrict__ CW, const dfc* __restrict__ CS, const dfc* __restrict__ CSW,
+               const c128* __restrict__ xbase, long long ldx, const int* __restrict__ jptr, c128* __restrict__ y,
+               const KState* __restrict__ kst) {
+  const int t = blockIdx.x;
+  const int q = tile_prob[t];
+  if (kst[q].stop) return;
+  const long long goff = geos[q].goff;
+  const int nx = geos[q].nx, n = geos[q].n;
+  const c128* x = xbase + (long long)(*jptr) * ldx;
+#pragma unroll 2
+  for (int s = 0; s < kRows; ++s) {
+    const long long r = (long long)t * kBatchTile + s * kBT + threadIdx.x;
+    const int lr = (int)(r - goff);
+    if (lr >= n) {
+      y[r] = mk(0.0, 0.0);
+      continue;
+    }
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    bcmac_df(rh, rl, ih, il, D[r], x[r]);
+    if (lr >= 1) bcmac_df(rh, rl, ih, il, CW[r], x[r - 1]);
+    if (lr + 1 < n) bcmac_df(rh, rl, ih, il, CW[r + 1], x[r + 1]);
+    if (lr >= nx) bcmac_df(rh, rl, ih, il, CS[r], x[r - nx]);
+    if (lr + nx < n) bcmac_df(rh, rl, ih, il, CS[r + nx], x[r + nx]);
+    if (lr >= nx + 1) bcmac_df(rh, rl, ih, il, CSW[r], x[r - nx - 1]);
+    if (lr + nx + 1 < n) bcmac_df(rh, rl, ih, il, CSW[r + nx + 1], x[r + nx + 1]);
+    y[r] = mk(df_to_d(rh, rl), df_to_d(ih, il));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Gram-Schmidt of step j in double-float arithmetic on a complex64 basis
 // (the basis vectors are the complex64 roundings of w/||w||, used exactly as
@@ -514,9 +563,8 @@ cudaError_t launch_bstep(const BStep& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   e = launch_bprolong(a.prec, a.ntiles, a.tile_prob, a.geos, a.subs, a.sub_index, a.Y, a.Z, a.ld, jp, a.kst, 1, st);
   if (e != cudaSuccess) return e;
-  e = launch_bspmv(a.ntiles, a.tile_prob, a.geos, a.D, a.CW, a.CS, a.CSW, a.Z, a.ld, jp, nullptr, a.w, nullptr,
-                   a.kst, 1, st);
-  if (e != cudaSuccess) return e;
+  k_bspmv_df<<<a.ntiles, kBT, 0, st>>>(a.tile_prob, a.geos, (const dfc*)a.Ddf, (const dfc*)a.CWdf,
+                                       (const dfc*)a.CSdf, (const dfc*)a.CSWdf, a.Z, a.ld, jp, a.w, a.kst);
   k_bdots_df<<<a.ntiles, kBT, dsm, st>>>(a.tile_prob, (const c64*)a.V, a.ld, a.w, jp, a.partial, a.ntiles, a.kst);
   k_bdots_finish<<<a.nprob, kBT, 0, st>>>(a.tile0, a.tile1, a.partial, a.ntiles, jp, a.H, a.m + 1, a.hstride,
                                           a.kst);

@@ -149,6 +149,7 @@ struct BStep {
   const void *L, *Lrev, *dinv;
   void* Y;
   const c128 *D, *CW, *CS, *CSW;
+  const void *Ddf, *CWdf, *CSdf, *CSWdf;   // the same, split into double-float form
   void* V;                // (m+1) x ld complex64 basis
   c128* Z;                // m x ld preconditioned directions
   long long ld;           // batch vector length
