@@ -243,10 +243,10 @@ template <typename R>
 __global__ void k_prolong(Geo g, const SubDesc* __restrict__ subs, const cx<R>* __restrict__ Y,
                           c128* __restrict__ z, const KState* __restrict__ kst) {
   if (kst != nullptr && kst->stop) return;
-  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long n = (long long)g.nx * g.ny;
-  if (r >= n) return;
-  const int i = (int)(r % g.nx) + 1, j = (int)(r / g.nx) + 1;
+  // n < 2^31 (checked at set-up): 32-bit index arithmetic
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= g.nx * g.ny) return;
+  const int j = r / g.nx + 1, i = r - (j - 1) * g.nx + 1;
   const int o = g.ovlp;
   int bx = box_of_node(i, g.Mx, g.px), by = box_of_node(j, g.My, g.py);
   int qx0 = bx, qx1 = bx, qy0 = by, qy1 = by;

@@ -77,12 +77,12 @@ __global__ void __launch_bounds__(kBT)
 #pragma unroll 1
   for (int s = 0; s < kRows; ++s) {
     const long long r = (long long)t * kBatchTile + s * kBT + threadIdx.x;
-    const long long lr = r - goff;
+    const int lr = (int)(r - goff);   // < 2^31 within a problem
     if (lr >= n) {
       z[r] = mk(0.0, 0.0);
       continue;
     }
-    const int i = (int)(lr % nx) + 1, j = (int)(lr / nx) + 1;
+    const int j = lr / nx + 1, i = lr - (j - 1) * nx + 1;
     const int bx = box_of_node(i, Mx, px), by = box_of_node(j, My, py);
     int qx0 = bx, qx1 = bx, qy0 = by, qy1 = by;
     if (bx > 0 && i < box_start(bx, Mx, px) + o) qx0 = bx - 1;

@@ -578,7 +578,7 @@ __global__ void k_prolong_add(const float* __restrict__ out16, int Nc, int nx, i
   if (r >= (long long)nx * ny) return;
   const double s = *s_dev;
   if (!(s > 0.0)) return;
-  const int i = (int)(r % nx), j = (int)(r / nx);
+  const int j = (int)r / nx, i = (int)r - j * nx;   // n < 2^31
   int I0, J0;
   float wx, wy;
   bilin_1d(i, nx, Nc, I0, wx);
