@@ -212,7 +212,7 @@ __global__ void k_global_stencil(Geo g, const c128* __restrict__ tab, c128* __re
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long n = (long long)g.nx * g.ny;
   if (r >= n) return;
-  int i = (int)(r % g.nx) + 1, j = (int)(r / g.nx) + 1;
+  const int jq = (int)r / g.nx, i = (int)r - jq * g.nx + 1, j = jq + 1;   // n < 2^31
   TabCells st{g, TabStretch{tab, tab + 2 * (2 * g.Mx + 1)}};
   c128 d, w, s, sw;
   node_row<double>(g, st, i, j, d, w, s, sw);
@@ -272,7 +272,7 @@ __global__ void k_rhs(Geo g, const double* __restrict__ cen, const double* __res
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long n = (long long)g.nx * g.ny;
   if (r >= n) return;
-  int i = (int)(r % g.nx) + 1, j = (int)(r / g.nx) + 1;
+  const int jq = (int)r / g.nx, i = (int)r - jq * g.nx + 1, j = jq + 1;   // n < 2^31
   double iw2 = 1.0 / (width * width);
   double si = 2.0 * i, sj = 2.0 * j;
   double f = source_at(g, cen, amp, ns, iw2, si + 1, sj) + source_at(g, cen, amp, ns, iw2, si - 1, sj) +
