@@ -223,7 +223,7 @@ def cpu_batch_baseline(probs, iters):
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:
-    """Largest value of x over the ranks (the step time the job is judged by)."""
+    """Largest value of x over the ranks (the step time of the slowest rank)."""
     if world <= 1:
         return x
     import torch
