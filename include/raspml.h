@@ -173,7 +173,8 @@ int ras_pml_assemble_rhs_noalloc(ras_pml_handle* h, const double* centres_host,
 /* Assembles every local operator A_j (Section 2; impedance term of
  * Section 3 (ii) when local_bc = 0) and factors it as A_j = L_j D_j L_j^T
  * (no pivoting; A_j is complex symmetric) in the handle's factor precision.
- * Returns RASPML_EPIVOT if a pivot is zero or non-finite (see info.bad_subdomain).
+ * Returns RASPML_EPIVOT if a pivot is zero or non-finite (see info.bad_subdomain),
+ * RASPML_ETIMEOUT if the tensor-core form's bounded wait for its MMAs gave up.
  * Synchronises the stream. */
 int ras_pml_factor(ras_pml_handle* h);
 
@@ -252,19 +253,22 @@ void ras_pml_destroy(ras_pml_handle* h);
  * fastest for later calls, and leaves the handle factored (every shape
  * computes the same factors up to the rounding order of the rank-2 update).
  * Factor candidates: 128, 256, 512 threads with one pivot per pass, 256,
- * 512 and 1024 threads with two; apply columns 8, plus 4 and 16 when
- * factor_prec = 1.
+ * 512 and 1024 threads with two, and, when factor_prec >= 1 and every
+ * half-bandwidth is <= 127, the blocked form on the tensor cores (128
+ * threads, factor_rank 8 or 16: that many pivots per panel, the trailing
+ * update as TF32 MMAs with a three-term split of each FP32 operand); apply
+ * columns 8, plus 4 and 16 when factor_prec = 1.
  * Synchronises the stream.
  * ------------------------------------------------------------------------- */
 typedef struct {
   int32_t factor_threads;    /* chosen threads per factor CTA                 */
-  int32_t factor_rank;       /* chosen pivots per pass (1 or 2)               */
+  int32_t factor_rank;       /* chosen pivots per pass (1, 2; 8, 16: tensor cores) */
   int32_t apply_cols;        /* chosen band columns per bulk copy             */
   int32_t n_factor;          /* factor candidates timed (entries below)       */
   int32_t n_apply;           /* apply candidates timed                        */
-  int32_t factor_cand_threads[6];
-  int32_t factor_cand_rank[6];
-  float   factor_ms[6];      /* median time of each factor candidate          */
+  int32_t factor_cand_threads[8];
+  int32_t factor_cand_rank[8];
+  float   factor_ms[8];      /* median time of each factor candidate          */
   int32_t apply_cand[4];
   float   apply_ms[4];       /* median time of each apply candidate (local
                                 solves of all subdomains)                     */
@@ -274,8 +278,11 @@ int ras_pml_tune(ras_pml_handle* h, ras_pml_tune_t* report);
 
 /* Sets the tile shapes directly (e.g. those a tuning run chose for another
  * handle of the same sizes): factor_threads 128, 256 or 512 with
- * factor_rank 1 or 2, or 1024 with factor_rank 2; apply_cols 8, or 4 or 16
- * with factor_prec = 1. RASPML_EBADARG for other values. */
+ * factor_rank 1 or 2, 1024 with factor_rank 2, or 128 with factor_rank 8
+ * or 16 (the tensor-core form: factor_prec >= 1 and every half-bandwidth
+ * <= 127);
+ * apply_cols 8, or 4 or 16 with factor_prec = 1. RASPML_EBADARG for other
+ * values. */
 int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, int apply_cols);
 
 /* ---------------------------------------------------------------------------

@@ -425,6 +425,10 @@ int ras_pml_factor(ras_pml_handle* h) {
   for (int j = 0; j < h->nsub; ++j) mr = std::min(mr, piv[2 * j] / piv[2 * j + 1]);
   h->min_pivot_ratio = mr;
   h->bad_sub = st.pivot_bad_sub;
+  if (st.timeout) {
+    h->factored = false;
+    return RASPML_ETIMEOUT;
+  }
   if (st.pivot_bad_sub >= 0) {
     h->factored = false;
     return RASPML_EPIVOT;
@@ -457,7 +461,7 @@ int ras_pml_tune(ras_pml_handle* h, ras_pml_tune_t* report) {
 }
 
 int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, int apply_cols) {
-  if (!h || !rp::factor_shape_valid(factor_threads, factor_rank) || !rp::apply_cols_valid(h->p.factor_prec, apply_cols))
+  if (!h || !rp::factor_shape_valid(h->p.factor_prec, h->max_b, factor_threads, factor_rank) || !rp::apply_cols_valid(h->p.factor_prec, apply_cols))
     return RASPML_EBADARG;
   h->tune.factor_threads = factor_threads;
   h->tune.factor_rank = factor_rank;

@@ -441,6 +441,7 @@ int ras_pml_batch_factor(ras_pml_batch* h) {
   for (int j = 0; j < h->nsub; ++j) mr = std::min(mr, piv[2 * j] / piv[2 * j + 1]);
   h->min_pivot_ratio = mr;
   h->bad_prob = h->bad_sub = -1;
+  if (stt.timeout) return RASPML_ETIMEOUT;
   if (stt.pivot_bad_sub >= 0) {
     const SubDesc& d = h->subs_h[stt.pivot_bad_sub];
     h->bad_prob = d.prob;
@@ -472,7 +473,7 @@ int ras_pml_batch_tune(ras_pml_batch* h, ras_pml_tune_t* report) {
 }
 
 int ras_pml_batch_set_shapes(ras_pml_batch* h, int factor_threads, int factor_rank, int apply_cols) {
-  if (!h || !rp::factor_shape_valid(factor_threads, factor_rank) || !rp::apply_cols_valid(h->prec, apply_cols))
+  if (!h || !rp::factor_shape_valid(h->prec, h->max_b, factor_threads, factor_rank) || !rp::apply_cols_valid(h->prec, apply_cols))
     return RASPML_EBADARG;
   h->tune.factor_threads = factor_threads;
   h->tune.factor_rank = factor_rank;

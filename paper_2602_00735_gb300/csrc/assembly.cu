@@ -223,16 +223,78 @@ __global__ void k_global_stencil(Geo g, const c128* __restrict__ tab, c128* __re
   CSW[r] = (i > 1 && j > 1) ? sw : z;
 }
 
-// One thread per local row; blockIdx.y = subdomain. Output Aloc[v_off + r]
-// = {D, W, S, SW}; padding rows (r >= n) are identity rows. T is the
-// arithmetic type: double for complex128 factors, float for complex64 ones
-// (those entries are rounded to complex64 before the factorisation anyway).
+// Local stretching read from per-CTA tables: gamma_1 and 1/gamma_1 at the
+// half-indices sx0..sx0+nxs-1 of the subdomain's x range, gamma_2 and
+// 1/gamma_2 at sy0..sy0+nys-1 (the rows one CTA covers); quotients become
+// products with the tabulated reciprocals.
 template <typename T>
-__global__ void k_local_rows(const Geo* __restrict__ geos, const SubDesc* __restrict__ subs, c128* __restrict__ Aloc) {
+struct LocalTab {
+  const cx<T>* tx;   // (gamma_1, 1/gamma_1) pairs
+  const cx<T>* ty;
+  int sx0, sy0;
+  SubDesc sd;
+  __device__ bool cell_ok(int ci, int cj) const {
+    return ci >= sd.ext_lo_x && ci < sd.ext_hi_x && cj >= sd.ext_lo_y && cj < sd.ext_hi_y;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ CellTerms<T> cell_of(const Geo& g, const LocalTab<T>& st, int ci, int cj) {
+  const int sa = 2 * ci + 1 - st.sx0, sb = sa + 1, sc = sa - 1;
+  const int ta = 2 * cj - st.sy0, tb = ta + 1, tc = ta + 2;
+  const cx<T> xa = st.tx[2 * sa], xb = st.tx[2 * sb], xc = st.tx[2 * sc];
+  const cx<T> ixa = st.tx[2 * sa + 1], ixb = st.tx[2 * sb + 1], ixc = st.tx[2 * sc + 1];
+  const cx<T> ya = st.ty[2 * ta], yb = st.ty[2 * tb], yc = st.ty[2 * tc];
+  const cx<T> iya = st.ty[2 * ta + 1], iyb = st.ty[2 * tb + 1], iyc = st.ty[2 * tc + 1];
+  const T sixth = (T)(1.0 / 6.0);
+  const T w = (T)(g.h * g.h * (1.0 / 6.0));
+  CellTerms<T> t;
+  t.KxL = sixth * (ya * ixa + yb * ixb + yb * ixa);
+  t.KyL = sixth * (xa * iya + xb * iyb + xa * iyb);
+  t.KxU = sixth * (yb * ixa + yc * ixa + yb * ixc);
+  t.KyU = sixth * (xa * iyb + xa * iyc + xc * iyb);
+  t.m01 = w * (xa * ya);
+  t.m12 = w * (xb * yb);
+  t.m02 = w * (xa * yb);
+  t.m23 = w * (xa * yc);
+  t.m03 = w * (xc * yb);
+  return t;
+}
+
+// table sizes of k_local_rows: x half-indices of a subdomain of up to
+// kMaxBandC64 + 1 nodes per line, y half-indices of the lines of 128 rows
+constexpr int kLrThreads = 128;
+constexpr int kLrTabX = 2 * (kMaxBandC64 + 1) + 4;
+constexpr int kLrTabY = 2 * (kLrThreads + 1) + 4;
+
+// kLrThreads local rows per CTA; blockIdx.y = subdomain. Output
+// Aloc[v_off + r] = {D, W, S, SW}; padding rows (r >= n) are identity rows.
+// T is the arithmetic type: double for complex128 factors, float for
+// complex64 ones (those entries are rounded to complex64 before the
+// factorisation anyway). The stretching of the CTA's cells is tabulated
+// first (one evaluation per half-index instead of six per cell).
+template <typename T>
+__global__ void __launch_bounds__(kLrThreads)
+    k_local_rows(const Geo* __restrict__ geos, const SubDesc* __restrict__ subs, c128* __restrict__ Aloc) {
+  __shared__ cx<T> tabx[2 * kLrTabX], taby[2 * kLrTabY];
   const SubDesc sd = subs[blockIdx.y];
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= sd.npad) return;
+  const int r0 = blockIdx.x * kLrThreads;
+  if (r0 >= sd.npad) return;   // whole CTA
+  const int r = r0 + threadIdx.x;
   const Geo g = geos[sd.prob];
+  const LocalStretch<T> ls{g, sd};
+  // half-indices: x from 2(ix0-1) to 2(ix0+nlx); y over the lines of rows r0..r0+127
+  const int sx0 = 2 * (sd.ix0 - 1), nxs = 2 * sd.nlx + 3;
+  const int jlo = sd.iy0 + min(r0, sd.n - 1) / sd.nlx, jhi = sd.iy0 + min(r0 + kLrThreads - 1, sd.n - 1) / sd.nlx;
+  const int sy0 = 2 * (jlo - 1), nys = 2 * (jhi - jlo) + 5;
+  for (int e = threadIdx.x; e < nxs + nys; e += kLrThreads) {
+    const cx<T> v = e < nxs ? ls.gx((double)(sx0 + e)) : ls.gy((double)(sy0 + e - nxs));
+    cx<T>* d = e < nxs ? tabx + 2 * e : taby + 2 * (e - nxs);
+    d[0] = v;
+    d[1] = crecip(v);
+  }
+  __syncthreads();
+  if (r >= sd.npad) return;
   c128* out = Aloc + 4 * (sd.v_off + r);
   const c128 z = mk(0.0, 0.0);
   if (r >= sd.n) {
@@ -241,10 +303,10 @@ __global__ void k_local_rows(const Geo* __restrict__ geos, const SubDesc* __rest
     return;
   }
   int i = sd.ix0 + r % sd.nlx, j = sd.iy0 + r / sd.nlx;
-  LocalStretch<T> st{g, sd};
+  const LocalTab<T> st{tabx, taby, sx0, sy0, sd};
   cx<T> d, w, s, sw;
   node_row<T>(g, st, i, j, d, w, s, sw);
-  if (g.local_bc == 0) impedance_terms<T>(g, sd, st, i, j, d, w, s);
+  if (g.local_bc == 0) impedance_terms<T>(g, sd, ls, i, j, d, w, s);
   out[0] = cvt<double>(d);
   out[1] = (i > sd.ix0) ? cvt<double>(w) : z;
   out[2] = (j > sd.iy0) ? cvt<double>(s) : z;
@@ -252,15 +314,29 @@ __global__ void k_local_rows(const Geo* __restrict__ geos, const SubDesc* __rest
 }
 
 // f at half-index (sx, sy): sum of Gaussians, cut to the closed Omega_int.
+// Terms with exponent e >= 700 (below 1e-304) are skipped. With a source
+// width above 5e-6 the decision is screened in FP32 first (centres cf, the
+// first kRhsScreen sources): the FP32 exponent is within 3% of e for
+// positions of magnitude below 4, so a term it puts at or above 720 has
+// e > 700 and is skipped either way; the others take the FP64 test and
+// value, so the result is the same bits as without the screen.
+constexpr int kRhsScreen = 64;
+
 __device__ double source_at(const Geo& g, const double* __restrict__ cen, const double* __restrict__ amp, int ns,
-                            double inv_w2, double sx, double sy) {
+                            const float2* cf, double inv_w2, double sx, double sy) {
   double x = xpos(g, sx), y = ypos(g, sy);
   if (!(x >= g.x0 && x <= g.x1 && y >= g.y0 && y <= g.y1)) return 0.0;
+  const bool screen = inv_w2 < 4e10 && fabs(x) < 4.0 && fabs(y) < 4.0;
+  const float xf = (float)x, yf = (float)y, iwf = (float)inv_w2;
   double f = 0.0;
   for (int s = 0; s < ns; ++s) {
+    if (screen && s < kRhsScreen) {
+      const float dxf = xf - cf[s].x, dyf = yf - cf[s].y;
+      if ((dxf * dxf + dyf * dyf) * iwf >= 720.f) continue;
+    }
     const double dx = x - cen[2 * s], dy = y - cen[2 * s + 1];
     const double e = (dx * dx + dy * dy) * inv_w2;
-    if (e < 700.0) f += amp[s] * exp(-e);  // beyond: below 1e-304, skipped
+    if (e < 700.0) f += amp[s] * exp(-e);
   }
   return f;
 }
@@ -269,15 +345,19 @@ __device__ double source_at(const Geo& g, const double* __restrict__ cen, const 
 // triangles with phi_i = 1/2 there, so F_i = (h^2/6) sum_edges f(midpoint).
 __global__ void k_rhs(Geo g, const double* __restrict__ cen, const double* __restrict__ amp, int ns, double width,
                       c128* __restrict__ b) {
+  __shared__ float2 cf[kRhsScreen];
+  for (int s = threadIdx.x; s < min(ns, kRhsScreen); s += blockDim.x)
+    cf[s] = make_float2((float)cen[2 * s], (float)cen[2 * s + 1]);
+  __syncthreads();
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long n = (long long)g.nx * g.ny;
   if (r >= n) return;
   const int jq = (int)r / g.nx, i = (int)r - jq * g.nx + 1, j = jq + 1;   // n < 2^31
   double iw2 = 1.0 / (width * width);
   double si = 2.0 * i, sj = 2.0 * j;
-  double f = source_at(g, cen, amp, ns, iw2, si + 1, sj) + source_at(g, cen, amp, ns, iw2, si - 1, sj) +
-             source_at(g, cen, amp, ns, iw2, si, sj + 1) + source_at(g, cen, amp, ns, iw2, si, sj - 1) +
-             source_at(g, cen, amp, ns, iw2, si + 1, sj + 1) + source_at(g, cen, amp, ns, iw2, si - 1, sj - 1);
+  double f = source_at(g, cen, amp, ns, cf, iw2, si + 1, sj) + source_at(g, cen, amp, ns, cf, iw2, si - 1, sj) +
+             source_at(g, cen, amp, ns, cf, iw2, si, sj + 1) + source_at(g, cen, amp, ns, cf, iw2, si, sj - 1) +
+             source_at(g, cen, amp, ns, cf, iw2, si + 1, sj + 1) + source_at(g, cen, amp, ns, cf, iw2, si - 1, sj - 1);
   b[r] = mk(f * (g.h * g.h / 6.0), 0.0);
 }
 
@@ -297,7 +377,7 @@ cudaError_t launch_global_stencil(const Geo& g, c128* tab, c128* D, c128* CW, c1
 
 cudaError_t launch_local_rows(int prec, const Geo* geos, const SubDesc* subs, int nsub, int max_npad, c128* Aloc,
                               cudaStream_t st) {
-  int threads = 128;
+  const int threads = kLrThreads;
   dim3 grid((max_npad + threads - 1) / threads, nsub);
   if (prec == 0)
     k_local_rows<double><<<grid, threads, 0, st>>>(geos, subs, Aloc);

@@ -30,6 +30,7 @@
 // zero-fills that copy first (entries left of column 0 stay zero).
 #include "common.cuh"
 #include "kernels.h"
+#include "tc.cuh"
 
 namespace rp {
 
@@ -375,6 +376,377 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Blocked form on the tensor cores (complex64 arithmetic, b <= 127), the
+// same factorisation with NB = 8 or 16 pivots per panel (a tuned shape: the
+// narrower panel needs less shared memory, so that two subdomains share an
+// SM and hide each other's latencies). One CTA of 128 threads
+// per subdomain. Rows k..k+NB+b-1 live in a ring of R = NB + b row slots
+// (row i in slot i mod R), each holding the band part of the row, columns
+// i-b..i, at position c - i + b. Panel k (columns k..k+NB-1):
+//   1. warp 0 factors the NB x NB diagonal block in registers (lane a holds
+//      row k+a; pivot j broadcasts d_j and the multipliers by shuffles) and
+//      writes L11 and 1/d to shared memory;
+//   2. thread t < b takes row i = k+NB+t and eliminates its panel part with
+//      the diagonal block: c_ij = A(i, k+j) as pivot j reaches it and
+//      l_ij = c_ij / d_j;
+//   3. the trailing update A(i, c) -= sum_j c_ij l_cj, k+NB <= c <= i <
+//      k+NB+b, is the product P Q^T of P = (c_ij) and Q = (l_cj), both
+//      b x NB. It runs as tcgen05.mma kind::tf32 (M = 128 rows, N = b
+//      rounded up to 16, FP32 accumulators in TMEM): complex products as
+//      real ones (Re = Pr Qr^T - Pi Qi^T, Im = Pr Qi^T + Pi Qr^T) and every
+//      FP32 operand as a TF32 head plus tail (x = xh + xl, xh = x with the 13
+//      low mantissa bits cleared, exact in TF32), of which the three products
+//      xh yh + xh yl + xl yh are kept: about 2^-21 relative rounding per
+//      product, next to FP32's 2^-24;
+//   4. while the MMAs run, the NB rows entering the window (read from global
+//      memory during step 2) fill the slots of rows k..k+NB-1;
+//   5. each warp reads its 32 accumulator rows back (tcgen05.ld) and
+//      subtracts them from the ring; warp 0 then factors the next diagonal
+//      block (its rows are the first NB of this trailing block), while the
+//      other warps finish their rows.
+// Output layout and pivot statistics as k_factor_ldlt.
+// ---------------------------------------------------------------------------
+constexpr int kTcM = 128;
+__host__ __device__ constexpr uint32_t tc_ab(int NB) { return kTcM * NB * 4; }   // bytes of one A operand array
+
+__host__ __device__ inline int tc_ldw(int b) { return (b & 1) ? b + 1 : b + 2; }   // even: conflict-free columns
+__host__ __device__ inline int tc_n(int b) { return (b + 15) & ~15; }
+
+__device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// Row `r` (K = NB values) of an operand array with `rows` rows in the
+// core-matrix layout: element (r, k) at (k/4)*rows*16 + (r/8)*128 + (r%8)*16 + (k%4)*4.
+template <int NB>
+__device__ __forceinline__ void tc_put_row(unsigned char* arr, int rows, int r, const float (&v)[NB]) {
+#pragma unroll
+  for (int q = 0; q < NB / 4; ++q)
+    *reinterpret_cast<float4*>(arr + q * rows * 16 + (r >> 3) * 128 + (r & 7) * 16) =
+        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+// head and tail arrays of the real and imaginary parts of z[0..15]
+template <int NB>
+__device__ __forceinline__ void tc_put_split(unsigned char* base, uint32_t stride, int rows, int r,
+                                             const c64 (&z)[NB]) {
+  float h[NB], l[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    h[j] = tf32_head(z[j].re);
+    l[j] = z[j].re - h[j];
+  }
+  tc_put_row<NB>(base, rows, r, h);
+  tc_put_row<NB>(base + stride, rows, r, l);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    h[j] = tf32_head(z[j].im);
+    l[j] = z[j].im - h[j];
+  }
+  tc_put_row<NB>(base + 2 * stride, rows, r, h);
+  tc_put_row<NB>(base + 3 * stride, rows, r, l);
+}
+
+// 32 lanes x 16 columns from each of two TMEM addresses, one wait
+__device__ __forceinline__ void tc_ld16x2(uint32_t ta, uint32_t tb, float (&va)[16], float (&vb)[16]) {
+  uint32_t a[16], c[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
+        "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15])
+      : "r"(ta));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7]),
+        "=r"(c[8]), "=r"(c[9]), "=r"(c[10]), "=r"(c[11]), "=r"(c[12]), "=r"(c[13]), "=r"(c[14]), "=r"(c[15])
+      : "r"(tb));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    va[i] = __uint_as_float(a[i]);
+    vb[i] = __uint_as_float(c[i]);
+  }
+}
+
+// Fills positions sub, sub+step, ... of ring slot `slot` with row r of A_j,
+// whose four stored entries are v (position p holds column r - b + p).
+__device__ __forceinline__ void tc_fill_row(c64* ring, int LDW, int slot, int r, int b, const c64 (&v)[4],
+                                            int sub, int step) {
+  for (int p = sub; p < LDW; p += step) {
+    c64 x = mk(0.f, 0.f);
+    if (p <= b && r - (b - p) >= 0) x = row_entry<float>(v, b - p, b);
+    ring[slot * LDW + p] = x;
+  }
+}
+
+// 1. the NB x NB diagonal block of the panel at k (one warp; lane a < NB
+// holds row k+a, the other lanes mirror lanes 0..NB-1 without writing).
+// Pivot j broadcasts d_j and the multipliers by shuffles (a shared-memory
+// broadcast with a warp barrier per pivot measured twice as slow); the
+// multipliers also go to L11[j*NB + a] = L(k+a, k+j) for step 2. Lane a
+// keeps its own pivot and takes its statistics after the loop, so the loop
+// has no divergent branch. The block's global outputs are written
+// afterwards by the whole CTA (tc_diag_out).
+template <int NB>
+__device__ __forceinline__ void tc_diag_block(int k, int lane, const c64* ring, int R, int LDW, int b, c64* L11,
+                                              c64* dis, float& dmin2, float& dmax2, bool& bad) {
+  const c64 zero = mk(0.f, 0.f);
+  const int a = lane & (NB - 1);
+  const c64* row = ring + ((k + a) % R) * LDW;
+  c64 x[NB];
+#pragma unroll
+  for (int jj = 0; jj < NB; ++jj) {
+    const int p = jj - a + b;
+    x[jj] = (jj <= a && p >= 0) ? row[p] : zero;
+  }
+  c64 mydi = zero;
+  float myd2 = 0.f;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    const c64 d = shfl(x[j], j);
+    const float ad2 = abs2(d);
+    const float inv = __frcp_rn(ad2);
+    const c64 di = mk(d.re * inv, -d.im * inv);
+    const c64 l = x[j] * di;
+    if (a == j) {
+      mydi = di;
+      myd2 = ad2;
+    }
+    // entries jj > a are never read back: updated without a predicate
+#pragma unroll
+    for (int jj = j + 1; jj < NB; ++jj) x[jj] = fms(x[jj], x[j], shfl(l, jj));
+    if (lane < NB) L11[j * NB + a] = l;   // entries a <= j are never read
+  }
+  if (lane < NB) {
+    dis[a] = mydi;
+    if (!(myd2 > 0.f) || !isfinite(myd2) || !isfinite(mydi.re) || !isfinite(mydi.im)) bad = true;
+    dmin2 = fminf(dmin2, myd2);
+    dmax2 = fmaxf(dmax2, myd2);
+  }
+}
+
+// Global outputs of the diagonal block at k: 1/d, the zero entry b of each
+// column (bp > b), and L(k+a, k+j) for j < a in both copies of L.
+template <typename S, int NB>
+__device__ __forceinline__ void tc_diag_out(int k, int tid, int b, int bp, int npad, const c64* L11,
+                                            const c64* dis, c64* dv, S* L, S* Lr) {
+  if (tid < NB) {
+    dv[k + tid] = dis[tid];
+    if (bp > b) L[(long long)(k + tid) * bp + b] = st_entry<S, float>(mk(0.f, 0.f));
+  }
+  for (int e = tid; e < NB * NB; e += kTcM) {
+    const int j = e / NB, a = e % NB;
+    if (a > j && a - j <= b) {
+      const S ls = st_entry<S, float>(L11[j * NB + a]);
+      L[(long long)(k + j) * bp + (a - j - 1)] = ls;
+      Lr[(long long)(npad - 1 - (k + a)) * bp + (a - j - 1)] = ls;
+    }
+  }
+}
+
+template <typename S, int NB>
+__global__ void __launch_bounds__(kTcM)
+    k_factor_tc(const SubDesc* __restrict__ subs, const c128* __restrict__ Aloc, S* __restrict__ Lall,
+                S* __restrict__ Lrev_all, c64* __restrict__ dinv_all, double* __restrict__ pivstats,
+                DevStatus* status, int Nmax, int ring_elems, int tcols) {
+  extern __shared__ __align__(1024) unsigned char smt[];
+  unsigned char* sm = smt;
+  const SubDesc sd = subs[blockIdx.x];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = sd.b, bp = sd.bp, npad = sd.npad;
+  const int R = NB + b, LDW = tc_ldw(b), N = tc_n(b);
+  constexpr uint32_t AB = tc_ab(NB);              // bytes of one A operand array
+  const uint32_t BB = (uint32_t)Nmax * NB * 4;   // bytes of one B operand array
+  unsigned char* Aop = sm;                          // Prh, Prl, Pih, Pil
+  unsigned char* Bop = sm + 4 * AB;              // Qrh, Qrl, Qih, Qil
+  c64* ring = reinterpret_cast<c64*>(Bop + 4 * BB);
+  c64* L11 = ring + ring_elems;                     // L11[j*16 + a] = L(k+a, k+j)
+  c64* dis = L11 + NB * NB;                   // 1/d_{k+j}
+  uint64_t* bar = reinterpret_cast<uint64_t*>(dis + NB);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  S* L = Lall + sd.l_off;
+  S* Lr = Lrev_all + sd.l_off;
+  c64* dv = dinv_all + sd.v_off;
+  const c64 zero = mk(0.f, 0.f);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  // rows 0..R-1, eight threads per row
+  for (int r0 = 0; r0 < R; r0 += kTcM / 8) {
+    const int r = r0 + (tid >> 3);
+    if (r < R) {
+      c64 v[4];
+      aloc_row<float>(Aloc, sd, r, v);
+      tc_fill_row(ring, LDW, r, r, b, v, tid & 7, 8);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  float dmin2 = 3e38f, dmax2 = 0.f;   // lane j of warp 0: pivots k+j
+  bool bad = false;
+  if (warp == 0) tc_diag_block<NB>(0, lane, ring, R, LDW, b, L11, dis, dmin2, dmax2, bad);
+  __syncthreads();
+  const uint32_t lba = kTcM * 16, lbb = (uint32_t)N * 16;
+  const uint64_t adesc0 = smem_desc(smem_u32(Aop), lba, 128), bdesc0 = smem_desc(smem_u32(Bop), lbb, 128);
+  const uint32_t id = idesc_tf32(kTcM, N), idn = id | (1u << 13);   // bit 13: negate A
+
+  bool failed = false;
+  uint32_t phase = 0;
+  const int t = tid;
+  // step 4's rows, read one panel ahead (warps 1-3, 96/NB threads per row)
+  constexpr int TPR = 96 / NB;
+  const int fq = (tid - 32) / TPR, fsub = (tid - 32) - TPR * ((tid - 32) / TPR);
+  c64 vnext[4];
+  if (warp > 0) aloc_row<float>(Aloc, sd, NB + b + fq, vnext);
+  for (int k = 0; k < npad; k += NB) {
+    const bool more = k + NB < npad;
+    const int i = k + NB + t;   // this thread's trailing row
+    c64 vcur[4];
+    if (warp > 0) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) vcur[e] = vnext[e];
+      if (k + 2 * NB < npad) aloc_row<float>(Aloc, sd, k + 2 * NB + b + fq, vnext);
+    }
+    tc_diag_out<S, NB>(k, tid, b, bp, npad, L11, dis, dv, L, Lr);
+    // 2. the panel part of the trailing rows
+    c64 cv[NB], lv[NB];
+    if (t < b) {
+      const c64* row = ring + (i % R) * LDW;
+      c64 y[NB];
+#pragma unroll
+      for (int jj = 0; jj < NB; ++jj) {
+        const int p = jj - NB - t + b;
+        y[jj] = p >= 0 ? row[p] : zero;
+      }
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        cv[j] = y[j];
+        lv[j] = y[j] * dis[j];
+#pragma unroll
+        for (int jj = j + 1; jj < NB; ++jj) y[jj] = fms(y[jj], cv[j], L11[j * NB + jj]);
+      }
+      // L(i, k+j) at entry o-1 of column k+j and of reversed row i, o = i-(k+j)
+      S* Lc = L + (long long)k * bp + (NB - 1 + t);
+      S* Lrr = Lr + (long long)(npad - 1 - i) * bp + (NB - 1 + t);
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        if (NB + t - j <= b) {
+          const S ls = st_entry<S, float>(lv[j]);
+          Lc[j * (bp - 1)] = ls;
+          if (i < npad) Lrr[-j] = ls;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NB; ++j) cv[j] = lv[j] = zero;
+    }
+    if (more) {
+      tc_put_split<NB>(Aop, AB, kTcM, t, cv);
+      if (t < N) tc_put_split<NB>(Bop, BB, N, t, lv);
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (!more) break;
+    tc_fence_after();
+    // 3. trailing update on the tensor cores (descriptors: the start address
+    //    field, bits 0-13 in 16-byte units, advances with the operand offset)
+    if (tid == 0) {
+      // (A array, B array, negate): Re += Prh Qrh + Prh Qrl + Prl Qrh - (Pih Qih + Pih Qil + Pil Qih)
+      //                             Im += Prh Qih + Prh Qil + Prl Qih + Pih Qrh + Pih Qrl + Pil Qrh
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        const uint32_t ta = (0x322100u >> (4 * u)) & 0xFu;    // 0, 0, 1, 2, 2, 3
+        const uint32_t tre = (0x232010u >> (4 * u)) & 0xFu;   // 0, 1, 0, 2, 3, 2
+        const uint32_t tim = (0x010232u >> (4 * u)) & 0xFu;   // 2, 3, 2, 0, 1, 0
+#pragma unroll
+        for (int s = 0; s < NB / 8; ++s) {
+          const uint64_t ad = adesc0 + ((ta * AB + 2 * s * lba) >> 4);
+          tc_mma_tf32(tmem, ad, bdesc0 + ((tre * BB + 2 * s * lbb) >> 4), u >= 3 ? idn : id, (u | s) ? 1u : 0u);
+          tc_mma_tf32(tmem + (uint32_t)N, ad, bdesc0 + ((tim * BB + 2 * s * lbb) >> 4), id, (u | s) ? 1u : 0u);
+        }
+      }
+      tc_commit(bar);
+    }
+    // 4. entering rows k+NB+b.. into the slots of rows k..k+NB-1 (warps 1-3,
+    //    while warp 0 issues the MMAs)
+    if (warp > 0) {
+      const int r = k + NB + b + fq;
+      tc_fill_row(ring, LDW, r % R, r, b, vcur, fsub, TPR);
+    }
+    // 5. accumulators back into the ring
+    const bool ok = mbar_wait_bounded(bar, phase);
+    phase ^= 1u;
+    if (!__syncthreads_and(ok)) {
+      // a bounded wait gave up: record it, wait once more (bounded) for the MMAs in flight, leave
+      if (tid == 0) atomicExch(&status->timeout, 1);
+      mbar_wait_bounded(bar, phase ^ 1u);
+      failed = true;
+      break;
+    }
+    tc_fence_after();
+    {
+      const int nch = min(N / 16, 2 * warp + 2);
+      c64* row = ring + (i % R) * LDW;
+      for (int h = 0; h < nch; ++h) {
+        float re[16], im[16];
+        const uint32_t ta0 = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * h);
+        tc_ld16x2(ta0, ta0 + (uint32_t)N, re, im);
+        if (t < b) {
+          // all loads first, then the stores (entries c <= t of row i)
+          c64* w = row + (16 * h - t + b);
+          c64 cur[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            if (16 * h + u <= t) cur[u] = w[u];
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            if (16 * h + u <= t) w[u] = mk(cur[u].re - re[u], cur[u].im - im[u]);
+        }
+      }
+    }
+    tc_fence_before();
+    if (warp == 0) {
+      __syncwarp();
+      tc_diag_block<NB>(k + NB, lane, ring, R, LDW, b, L11, dis, dmin2, dmax2, bad);
+    }
+    __syncthreads();
+  }
+  (void)failed;
+  if (warp == 0) {
+    // pivot statistics of the lanes that held pivots
+    float mn = lane < NB ? dmin2 : 3e38f, mx = lane < NB ? dmax2 : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const bool anybad = __any_sync(0xffffffffu, lane < NB && bad);
+    if (lane == 0) {
+      pivstats[2 * blockIdx.x] = sqrt((double)mn);
+      pivstats[2 * blockIdx.x + 1] = sqrt((double)mx);
+      if (anybad) atomicCAS(&status->pivot_bad_sub, -1, (int)blockIdx.x);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+  }
+}
+
 }  // namespace
 
 int max_band(int prec) { return prec == 0 ? kMaxBandC128 : kMaxBandC64; }
@@ -421,15 +793,65 @@ cudaError_t launch_factor_s(int threads, int rank, size_t smem, const SubDesc* s
 
 }  // namespace
 
-bool factor_shape_valid(int threads, int rank) {
+bool factor_tc_ok(int prec, int max_b) { return prec >= 1 && max_b >= 1 && max_b <= kMaxBandTc; }
+
+bool factor_shape_valid(int prec, int max_b, int threads, int rank) {
+  if (is_tc_rank(rank)) return threads == kTcM && factor_tc_ok(prec, max_b);
   return ((threads == 128 || threads == 256 || threads == 512) && (rank == 1 || rank == 2)) ||
          (threads == 1024 && rank == 2);
 }
 
+namespace {
+
+// shared memory of k_factor_tc<., NB> for half-bandwidths up to max_b, and
+// its TMEM columns (a power of two >= 2N); the request is raised where
+// needed so that the CTAs resident on one SM never ask for more than its 512
+// columns
+void tc_sizes(int max_b, int NB, size_t* smem, int* nmax, int* ring_elems, int* tcols) {
+  *nmax = tc_n(max_b);
+  *ring_elems = (NB + max_b) * (max_b + 2);
+  int tc = 32;
+  while (tc < 2 * *nmax) tc *= 2;
+  *tcols = tc;
+  size_t s = 4 * (size_t)tc_ab(NB) + 4 * (size_t)(*nmax) * NB * 4 + (size_t)(*ring_elems) * sizeof(c64) +
+             (size_t)(NB * NB + NB) * sizeof(c64) + 16;
+  const size_t per_sm = 228 * 1024, per_cta_reserved = 1024;
+  while (per_sm / (s + per_cta_reserved) > (size_t)(512 / tc)) s += 1024;
+  *smem = s;
+}
+
+template <typename S, int NB>
+cudaError_t launch_factor_tc(const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L, void* Lrev,
+                             void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
+  size_t smem;
+  int nmax, ring_elems, tcols;
+  tc_sizes(max_b, NB, &smem, &nmax, &ring_elems, &tcols);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_factor_tc<S, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_factor_tc<S, NB><<<nsub, kTcM, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (c64*)dinv, pivstats, status, nmax,
+                                               ring_elems, tcols);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_factor_tc_nb(int rank, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
+                                void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
+  if (rank == 8) return launch_factor_tc<S, 8>(subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status, st);
+  return launch_factor_tc<S, 16>(subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status, st);
+}
+
+}  // namespace
+
 cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, int nsub, int max_b,
                           const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status,
                           cudaStream_t st) {
-  if (!factor_shape_valid(threads, rank)) return cudaErrorInvalidValue;
+  if (!factor_shape_valid(prec, max_b, threads, rank)) return cudaErrorInvalidValue;
+  if (is_tc_rank(rank)) {
+    if (prec == 1) return launch_factor_tc_nb<c64>(rank, subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status, st);
+    return launch_factor_tc_nb<h2c>(rank, subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status, st);
+  }
   const size_t smem = factor_smem_bytes(max_b, prec, rank);
   if (prec == 0)
     return launch_factor_s<double, c128>(threads, rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);

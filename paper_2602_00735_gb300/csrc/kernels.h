@@ -39,7 +39,13 @@ struct Tune {
   int factor_rank = 2;        // pivots per pass over the window: 1 or 2
   int apply_cols = 8;         // band columns per bulk copy: 8 (4 or 16 with complex64 storage)
 };
-bool factor_shape_valid(int threads, int rank);
+// factor_rank 8 or 16 (with 128 threads): the blocked form on the tensor
+// cores with that many pivots per panel, complex64 arithmetic (prec 1 and 2)
+// and b <= kMaxBandTc
+inline bool is_tc_rank(int rank) { return rank == 8 || rank == 16; }
+constexpr int kMaxBandTc = 127;
+bool factor_tc_ok(int prec, int max_b);
+bool factor_shape_valid(int prec, int max_b, int threads, int rank);
 bool apply_cols_valid(int prec, int cols);
 
 // assembly.cu

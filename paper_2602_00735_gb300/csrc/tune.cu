@@ -1,6 +1,6 @@
 // Tile-shape tuner: times each candidate shape of the factor launch (threads
-// per CTA, pivots per pass) and of the local-solve launch (band columns per
-// bulk copy) on the caller's own subdomains with CUDA events on its stream,
+// per CTA, pivots per pass; the blocked tensor-core form where it applies)
+// and of the local-solve launch (band columns per bulk copy) on the caller's own subdomains with CUDA events on its stream,
 // and returns the fastest. The factor runs last with the chosen shape, so
 // the factors left behind are that shape's.
 #include <algorithm>
@@ -28,9 +28,10 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
     return RASPML_ECUDA;
   }
   cudaError_t e = cudaSuccess;
-  const int fthreads[6] = {128, 256, 512, 256, 512, 1024};
-  const int franks[6] = {1, 1, 1, 2, 2, 2};
-  for (int c = 0; c < 6 && e == cudaSuccess; ++c) {
+  const int fthreads[8] = {128, 256, 512, 256, 512, 1024, 128, 128};
+  const int franks[8] = {1, 1, 1, 2, 2, 2, 8, 16};
+  const int nfc = factor_tc_ok(t.prec, t.max_b) ? 8 : 6;   // the tensor-core forms where they apply
+  for (int c = 0; c < nfc && e == cudaSuccess; ++c) {
     std::vector<float> ms;
     for (int r = 0; r < reps && e == cudaSuccess; ++r) {
       e = cudaEventRecord(e0, t.st);

@@ -110,7 +110,8 @@ def test_restarted_and_tuned_solve(pkg, probs):
     with pkg.BatchRasPml([w.params() for w in probs], factor_prec=1) as B:
         rep = B.tune()
         assert rep["factor_threads"] in (128, 256, 512, 1024) and rep["apply_cols"] in (4, 8, 16)
-        assert set(rep["factor_ms"]) == {"128x1", "256x1", "512x1", "256x2", "512x2", "1024x2"}
+        # the tensor-core forms (128 x 8, 128 x 16) are candidates: complex64, every b <= 127
+        assert set(rep["factor_ms"]) == {"128x1", "256x1", "512x1", "256x2", "512x2", "1024x2", "128x8", "128x16"}
         assert all(v > 0 for v in rep["factor_ms"].values())
         inf = B.info()
         assert (inf["factor_threads"], inf["factor_rank"], inf["apply_cols"]) == \
@@ -141,3 +142,44 @@ def test_not_converged_and_errors(pkg, probs):
         bn[int(B.offsets[1]) + 5] = float("nan")
         with pytest.raises(RasPmlError):
             B.solve(bn, rtol=1e-6, maxit=10)
+
+
+def test_mixed_variants_in_one_batch(pkg):
+    """Problems that differ in closure (impedance / Dirichlet), local PML
+    (present / absent), boxes and stretching profile (the paper's g = 10k x^3
+    set-up) share the launches; each matches its own oracle."""
+    from gpu_util import variant
+    probs = [variant("tiny3", local_bc=1), variant("tiny3", pml_cells=0), variant("small", px=3, py=5),
+             workloads.paper_setup(160, 40)]
+    for prec, tol in ((0, 1e-10), (2, 2e-2)):
+        with pkg.BatchRasPml([w.params() for w in probs], factor_prec=prec) as B:
+            B.factor()
+            rs = [random_vector(int(n), 40 + q) for q, n in enumerate(B.sizes)]
+            z = B.apply(B.join(rs))
+            for q, (w, zq) in enumerate(zip(probs, B.split(z))):
+                _, _, R = oracle_problem(w)
+                assert rel(zq.cpu().numpy(), R.apply(rs[q])) <= tol, (prec, q)
+            if prec == 0:
+                b = B.assemble_rhs(_sources(probs))
+                x, it, relres, st = B.solve(b, rtol=1e-10, maxit=400)
+                assert st == 0
+                for q, (w, xq) in enumerate(zip(probs, B.split(x))):
+                    grid, A, _ = oracle_problem(w)
+                    u = fem.direct_solve(A, fem.assemble_rhs(w.params(), w.centres, w.amps, w.width))
+                    assert rel(xq.cpu().numpy(), u) <= 1e-8, q
+
+
+@pytest.mark.parametrize("rank", [8, 16])
+@pytest.mark.parametrize("prec,tol", [(1, 1e-4), (2, 2e-2)])
+def test_tensor_core_factor_in_a_batch(pkg, probs, prec, tol, rank):
+    """The blocked tensor-core factorisation over the union of the problems'
+    subdomains (uneven bands, LPT order) gives each problem's oracle B^-1."""
+    with pkg.BatchRasPml([w.params() for w in probs], factor_prec=prec) as B:
+        B.set_shapes(128, rank, 8)
+        B.factor()
+        assert (B.info()["factor_threads"], B.info()["factor_rank"]) == (128, rank)
+        rs = [random_vector(int(n), 60 + q) for q, n in enumerate(B.sizes)]
+        z = B.apply(B.join(rs))
+        for q, (w, zq) in enumerate(zip(probs, B.split(z))):
+            _, _, R = oracle_problem(w)
+            assert rel(zq.cpu().numpy(), R.apply(rs[q])) <= tol, q

@@ -252,6 +252,57 @@ def test_factor_shapes_match_oracle(solver_cls, name, kw, prec, tol, threads, ra
         assert rel(s.apply(to_dev(r)).cpu().numpy(), R.apply(r)) <= tol
 
 
+# ------------------------------------------------ tensor-core factor form --
+# The blocked factorisation on the tensor cores (8 or 16 pivots per panel,
+# the trailing update as TF32 MMAs with a three-term split of each FP32 operand)
+# gives the oracle's B^-1 about as closely as the complex64 CUDA-core form on
+# the same input: each TF32 product pair carries ~2^-21 relative rounding
+# against FP32's 2^-24, so its error may exceed that form's by a small factor
+# only. Half-bandwidths from below one panel (b < 16) to the form's limit
+# (127), odd and even, mixed within one handle.
+
+TC_CASES = [("tiny3", {}), ("small", {"px": 3, "py": 5}),
+            ("tiny", {"px": 6, "py": 5, "ovlp_cells": 1, "pml_cells": 1}),
+            ("c0", {"px": 2, "py": 3}), ("c0", {"px": 2, "py": 2, "ovlp_cells": 15, "pml_cells": 15})]
+
+
+@pytest.mark.parametrize("rank", [8, 16])
+@pytest.mark.parametrize("prec,cap", [(1, 1e-3), (2, 2e-2)])
+@pytest.mark.parametrize("name,kw", TC_CASES)
+def test_tensor_core_factor_matches_oracle(solver_cls, name, kw, prec, cap, rank):
+    w = variant(name, **kw)
+    grid, A, R = oracle_problem(w)
+    r = random_vector(grid.n, 4)
+    ref = R.apply(r)
+    errs = {}
+    with solver_cls(w.params(), factor_prec=prec) as s:
+        for shape in ((256, 2), (128, rank)):
+            s.set_shapes(*shape, 8)
+            s.factor()
+            errs[shape] = rel(s.apply(to_dev(r)).cpu().numpy(), ref)
+    e32, etc = errs[(256, 2)], errs[(128, rank)]
+    print(f"{name} {kw} prec {prec} panel {rank}: CUDA-core {e32:.2e}, tensor-core {etc:.2e}")
+    assert etc <= max(16 * e32, 1e-6) and etc <= cap, (e32, etc)
+
+
+def test_tensor_core_factor_solve_reaches_fp64_solution(solver_cls):
+    """FGMRES with the tensor-core factors converges to the FP64 solution in
+    the iterations of the CUDA-core factors (within one)."""
+    w = variant("c0", px=2, py=3)
+    p = w.params()
+    grid, A, _ = oracle_problem(w)
+    u = fem.direct_solve(A, fem.assemble_rhs(p, w.centres, w.amps, w.width))
+    its = {}
+    for shape in ((256, 2), (128, 8), (128, 16)):
+        with solver_cls(p, factor_prec=1) as s:
+            s.set_shapes(*shape, 8)
+            b = s.assemble_rhs(w.centres, w.amps, w.width)
+            x, its[shape], relres, st = s.solve(b, rtol=1e-10, maxit=400)
+            assert st == 0 and relres <= 1e-10
+            assert rel(x.cpu().numpy(), u) <= 1e-8
+    assert abs(its[(128, 8)] - its[(256, 2)]) <= 1 and abs(its[(128, 16)] - its[(256, 2)]) <= 1, its
+
+
 @pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
 def test_residual_after_one_sweep_lives_in_the_overlaps(solver_cls, prec, tol):
     """Section 3, practical point (i), on the GPU: b - A B^-1 b vanishes away
