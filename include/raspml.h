@@ -250,7 +250,9 @@ void ras_pml_destroy(ras_pml_handle* h);
  * shapes): times each candidate shape of the factor launch (threads per CTA
  * and pivots per pass over the window) and of the apply launch (band columns
  * per bulk copy) on the handle's own subdomains with CUDA events, keeps the
- * fastest for later calls, and leaves the handle factored (every shape
+ * fastest for later calls (the default, 256 threads x 2 pivots and 8
+ * columns, unless another shape beats it by 2%), and leaves the handle
+ * factored (every shape
  * computes the same factors up to the rounding order of the rank-2 update).
  * Factor candidates: 128, 256, 512 threads with one pivot per pass, 256,
  * 512 and 1024 threads with two, and, when factor_prec >= 1 and every

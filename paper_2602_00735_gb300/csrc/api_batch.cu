@@ -27,6 +27,7 @@ struct ras_pml_batch {
   std::vector<Geo> geos_h;
   std::vector<SubDesc> subs_h;      // launch order (decreasing factor cost)
   std::vector<int> sub_index_h;     // natural index -> launch position
+  rp::BandSplit split;              // wide subdomains first in the launch order
   std::vector<int> tile_prob_h, tile0_h, tile1_h;
   long long ntot = 0, sum_n = 0, sum_npad = 0, sum_l = 0, sum_bn = 0;
   int nsub = 0, max_b = 0, max_bp = 0, max_npad = 0, ntiles = 0;
@@ -227,12 +228,22 @@ int ras_pml_batch_setup(const ras_pml_params* params, int nprob, void* stream, r
   h->ntot = goff;
   h->ntiles = (int)h->tile_prob_h.size();
   h->nsub = (int)nat.size();
-  // launch order: decreasing factor cost npad * b^2 (ties: natural order)
+  // launch order: the subdomains wider than the tensor-core factor's limit
+  // first, then the others, each part by decreasing factor cost npad * b^2
+  // (ties: natural order)
   std::vector<int> order(h->nsub);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const bool wa = nat[a].b > rp::kMaxBandTc, wb = nat[b].b > rp::kMaxBandTc;
+    if (wa != wb) return wa;
     return (double)nat[a].npad * nat[a].b * nat[a].b > (double)nat[b].npad * nat[b].b * nat[b].b;
   });
+  h->split.nwide = 0;
+  h->split.max_b_tc = 0;
+  for (int i = 0; i < h->nsub; ++i) {
+    if (nat[i].b > rp::kMaxBandTc) ++h->split.nwide;
+    else h->split.max_b_tc = std::max(h->split.max_b_tc, nat[i].b);
+  }
   h->sub_index_h.assign(h->nsub, 0);
   long long l_off = 0, v_off = 0;
   for (int pos = 0; pos < h->nsub; ++pos) {
@@ -426,7 +437,7 @@ int ras_pml_batch_factor(ras_pml_batch* h) {
   s = batch_local_rows(h, &Aloc);
   if (s != RASPML_OK) { dfree(Aloc); return s; }
   cudaError_t e = rp::launch_factor(h->prec, h->tune.factor_threads, h->tune.factor_rank, h->subs_d, h->nsub, h->max_b, Aloc, h->L,
-                                    h->Lrev, h->dinv, h->pivstats, h->status, h->st);
+                                    h->Lrev, h->dinv, h->pivstats, h->status, h->st, h->split);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   dfree(Aloc);
   if (e != cudaSuccess) {
@@ -463,7 +474,7 @@ int ras_pml_batch_tune(ras_pml_batch* h, ras_pml_tune_t* report) {
   if (s == RASPML_OK && cudaMemsetAsync(r, 0, sizeof(c128) * h->ntot, h->st) != cudaSuccess) s = RASPML_ECUDA;
   if (s == RASPML_OK) {
     rp::TuneTarget t{h->prec, h->geos_d, h->subs_d, h->nsub, h->max_b, h->max_bp, h->max_npad, h->sum_npad,
-                     h->sum_l, Aloc, h->L, h->Lrev, h->dinv, h->Y, h->pivstats, h->status, r, h->st};
+                     h->sum_l, Aloc, h->L, h->Lrev, h->dinv, h->Y, h->pivstats, h->status, r, h->st, h->split};
     s = rp::tune_shapes(t, 3, &h->tune, report);
   }
   cudaStreamSynchronize(h->st);
@@ -473,7 +484,7 @@ int ras_pml_batch_tune(ras_pml_batch* h, ras_pml_tune_t* report) {
 }
 
 int ras_pml_batch_set_shapes(ras_pml_batch* h, int factor_threads, int factor_rank, int apply_cols) {
-  if (!h || !rp::factor_shape_valid(h->prec, h->max_b, factor_threads, factor_rank) || !rp::apply_cols_valid(h->prec, apply_cols))
+  if (!h || !rp::factor_shape_valid(h->prec, h->max_b, factor_threads, factor_rank, h->split) || !rp::apply_cols_valid(h->prec, apply_cols))
     return RASPML_EBADARG;
   h->tune.factor_threads = factor_threads;
   h->tune.factor_rank = factor_rank;

@@ -548,10 +548,11 @@ template <typename S, int NB>
 __global__ void __launch_bounds__(kTcM)
     k_factor_tc(const SubDesc* __restrict__ subs, const c128* __restrict__ Aloc, S* __restrict__ Lall,
                 S* __restrict__ Lrev_all, c64* __restrict__ dinv_all, double* __restrict__ pivstats,
-                DevStatus* status, int Nmax, int ring_elems, int tcols) {
+                DevStatus* status, int Nmax, int ring_elems, int tcols, int sub_base) {
   extern __shared__ __align__(1024) unsigned char smt[];
   unsigned char* sm = smt;
-  const SubDesc sd = subs[blockIdx.x];
+  const int sub = sub_base + (int)blockIdx.x;   // launch position of this subdomain
+  const SubDesc sd = subs[sub];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b = sd.b, bp = sd.bp, npad = sd.npad;
   const int R = NB + b, LDW = tc_ldw(b), N = tc_n(b);
@@ -734,9 +735,9 @@ __global__ void __launch_bounds__(kTcM)
     }
     const bool anybad = __any_sync(0xffffffffu, lane < NB && bad);
     if (lane == 0) {
-      pivstats[2 * blockIdx.x] = sqrt((double)mn);
-      pivstats[2 * blockIdx.x + 1] = sqrt((double)mx);
-      if (anybad) atomicCAS(&status->pivot_bad_sub, -1, (int)blockIdx.x);
+      pivstats[2 * sub] = sqrt((double)mn);
+      pivstats[2 * sub + 1] = sqrt((double)mx);
+      if (anybad) atomicCAS(&status->pivot_bad_sub, -1, sub);
     }
   }
   tc_fence_before();
@@ -795,8 +796,11 @@ cudaError_t launch_factor_s(int threads, int rank, size_t smem, const SubDesc* s
 
 bool factor_tc_ok(int prec, int max_b) { return prec >= 1 && max_b >= 1 && max_b <= kMaxBandTc; }
 
-bool factor_shape_valid(int prec, int max_b, int threads, int rank) {
-  if (is_tc_rank(rank)) return threads == kTcM && factor_tc_ok(prec, max_b);
+bool factor_shape_valid(int prec, int max_b, int threads, int rank, BandSplit split) {
+  if (is_tc_rank(rank)) {
+    if (threads == kTcM) return factor_tc_ok(prec, max_b);
+    return prec >= 1 && split.nwide >= 0 && (threads == 256 || threads == 512 || threads == 1024);
+  }
   return ((threads == 128 || threads == 256 || threads == 512) && (rank == 1 || rank == 2)) ||
          (threads == 1024 && rank == 2);
 }
@@ -822,7 +826,7 @@ void tc_sizes(int max_b, int NB, size_t* smem, int* nmax, int* ring_elems, int* 
 
 template <typename S, int NB>
 cudaError_t launch_factor_tc(const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L, void* Lrev,
-                             void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
+                             void* dinv, double* pivstats, DevStatus* status, cudaStream_t st, int sub_base) {
   size_t smem;
   int nmax, ring_elems, tcols;
   tc_sizes(max_b, NB, &smem, &nmax, &ring_elems, &tcols);
@@ -831,23 +835,49 @@ cudaError_t launch_factor_tc(const SubDesc* subs, int nsub, int max_b, const c12
       cudaFuncSetAttribute(k_factor_tc<S, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_factor_tc<S, NB><<<nsub, kTcM, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (c64*)dinv, pivstats, status, nmax,
-                                               ring_elems, tcols);
+                                               ring_elems, tcols, sub_base);
   return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t launch_factor_tc_nb(int rank, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
-                                void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
-  if (rank == 8) return launch_factor_tc<S, 8>(subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status, st);
-  return launch_factor_tc<S, 16>(subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status, st);
+                                void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st,
+                                int sub_base = 0) {
+  if (rank == 8) return launch_factor_tc<S, 8>(subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status, st, sub_base);
+  return launch_factor_tc<S, 16>(subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status, st, sub_base);
+}
+
+// mixed shape: the wide subdomains (launch positions 0..nwide-1) on the CUDA
+// cores with two pivots per pass, the others on the tensor cores, one launch
+// after the other on the stream
+template <typename S>
+cudaError_t launch_factor_mixed(int threads, int rank, const SubDesc* subs, int nsub, int max_b, BandSplit sp,
+                                const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats,
+                                DevStatus* status, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  const int nw = sp.nwide < nsub ? sp.nwide : nsub;
+  if (nw > 0)
+    e = launch_factor_s<float, S>(threads, 2, factor_smem_bytes(max_b, 1, 2), subs, nw, Aloc, L, Lrev, dinv, pivstats,
+                                  status, st);
+  if (e == cudaSuccess && nsub > nw) {
+    const int mb = nw > 0 ? sp.max_b_tc : max_b;
+    if (!factor_tc_ok(1, mb)) return cudaErrorInvalidValue;
+    e = launch_factor_tc_nb<S>(rank, subs, nsub - nw, mb, Aloc, L, Lrev, dinv, pivstats, status, st, nw);
+  }
+  return e;
 }
 
 }  // namespace
 
 cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, int nsub, int max_b,
                           const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status,
-                          cudaStream_t st) {
-  if (!factor_shape_valid(prec, max_b, threads, rank)) return cudaErrorInvalidValue;
+                          cudaStream_t st, BandSplit split) {
+  if (!factor_shape_valid(prec, max_b, threads, rank, split)) return cudaErrorInvalidValue;
+  if (is_tc_rank(rank) && threads != kTcM) {
+    if (prec == 1)
+      return launch_factor_mixed<c64>(threads, rank, subs, nsub, max_b, split, Aloc, L, Lrev, dinv, pivstats, status, st);
+    return launch_factor_mixed<h2c>(threads, rank, subs, nsub, max_b, split, Aloc, L, Lrev, dinv, pivstats, status, st);
+  }
   if (is_tc_rank(rank)) {
     if (prec == 1) return launch_factor_tc_nb<c64>(rank, subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status, st);
     return launch_factor_tc_nb<h2c>(rank, subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status, st);

@@ -68,6 +68,7 @@ struct TuneTarget {
   DevStatus* status;
   const c128* r;       // any input vector of the problems' layout
   cudaStream_t st;
+  BandSplit split;     // the batched form's order by band (nwide < 0: none)
 };
 int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* report);
 

@@ -44,8 +44,18 @@ struct Tune {
 // and b <= kMaxBandTc
 inline bool is_tc_rank(int rank) { return rank == 8 || rank == 16; }
 constexpr int kMaxBandTc = 127;
+// Subdomains split by half-bandwidth for the mixed factor shape (factor_rank
+// 8 or 16 with 256, 512 or 1024 threads): the first nwide entries of the
+// launch order have b > kMaxBandTc and go to the CUDA-core kernel (two
+// pivots per pass, that many threads), the others (largest band max_b_tc)
+// to the tensor-core kernel. nwide < 0: no such order (the one-problem
+// handle), and the mixed shape is not available.
+struct BandSplit {
+  int nwide = -1;
+  int max_b_tc = 0;
+};
 bool factor_tc_ok(int prec, int max_b);
-bool factor_shape_valid(int prec, int max_b, int threads, int rank);
+bool factor_shape_valid(int prec, int max_b, int threads, int rank, BandSplit split = BandSplit{});
 bool apply_cols_valid(int prec, int cols);
 
 // assembly.cu
@@ -61,7 +71,7 @@ cudaError_t launch_rhs(const Geo& g, const double* cen, const double* amp, int n
 size_t factor_smem_bytes(int b, int prec, int rank);
 cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, int nsub, int max_b,
                           const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status,
-                          cudaStream_t st);
+                          cudaStream_t st, BandSplit split = BandSplit{});
 
 // apply.cu
 size_t apply_smem_bytes(int max_bp, int prec, int cols);

@@ -1,8 +1,9 @@
 // Tile-shape tuner: times each candidate shape of the factor launch (threads
 // per CTA, pivots per pass; the blocked tensor-core form where it applies)
-// and of the local-solve launch (band columns per bulk copy) on the caller's own subdomains with CUDA events on its stream,
-// and returns the fastest. The factor runs last with the chosen shape, so
-// the factors left behind are that shape's.
+// and of the local-solve launch (band columns per bulk copy) on the caller's
+// own subdomains with CUDA events on its stream, and returns the fastest (the
+// default shape unless another beats it by 2%). The factor runs last with
+// the chosen shape, so the factors left behind are that shape's.
 #include <algorithm>
 
 #include "host.h"
@@ -28,16 +29,27 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
     return RASPML_ECUDA;
   }
   cudaError_t e = cudaSuccess;
-  const int fthreads[8] = {128, 256, 512, 256, 512, 1024, 128, 128};
+  // the CUDA-core shapes, then the tensor-core forms: alone where every
+  // band allows it, else mixed with the fastest two-pivot CUDA-core shape
+  // on the wide subdomains (the batched form's order by band)
+  int fthreads[8] = {128, 256, 512, 256, 512, 1024, 128, 128};
   const int franks[8] = {1, 1, 1, 2, 2, 2, 8, 16};
-  const int nfc = factor_tc_ok(t.prec, t.max_b) ? 8 : 6;   // the tensor-core forms where they apply
+  const bool tc_all = factor_tc_ok(t.prec, t.max_b);
+  const bool tc_mixed = !tc_all && t.prec >= 1 && t.split.nwide >= 0 && t.split.nwide < t.nsub;
+  const int nfc = (tc_all || tc_mixed) ? 8 : 6;
   for (int c = 0; c < nfc && e == cudaSuccess; ++c) {
+    if (c == 6 && tc_mixed) {
+      int b2 = 3;
+      for (int i = 4; i < 6; ++i)
+        if (rep.factor_ms[i] < rep.factor_ms[b2]) b2 = i;
+      fthreads[6] = fthreads[7] = fthreads[b2];
+    }
     std::vector<float> ms;
     for (int r = 0; r < reps && e == cudaSuccess; ++r) {
       e = cudaEventRecord(e0, t.st);
       if (e == cudaSuccess)
         e = launch_factor(t.prec, fthreads[c], franks[c], t.subs, t.nsub, t.max_b, t.Aloc, t.L, t.Lrev, t.dinv,
-                          t.pivstats, t.status, t.st);
+                          t.pivstats, t.status, t.st, t.split);
       if (e == cudaSuccess) e = cudaEventRecord(e1, t.st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       if (e == cudaSuccess) ms.push_back(ev_ms(e0, e1));
@@ -70,14 +82,23 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
     std::fprintf(stderr, "raspml: tune: %s\n", cudaGetErrorString(e));
     return RASPML_ECUDA;
   }
-  int bf = 0, ba = 0;
-  for (int i = 1; i < rep.n_factor; ++i)
-    if (rep.factor_ms[i] < rep.factor_ms[bf]) bf = i;
-  for (int i = 1; i < rep.n_apply; ++i)
-    if (rep.apply_ms[i] < rep.apply_ms[ba]) ba = i;
+  // the fastest shape, but the default (256 x 2, 8 columns) unless another
+  // beats it by 2%: near-ties are decided by timing noise, and the default
+  // apply shape holds up better in the solves, where stopped problems drop out
+  auto pick = [](const float* ms, int n, int def) {
+    int b = def;
+    for (int i = 0; i < n; ++i)
+      if (ms[i] < ms[b] && ms[i] < 0.98f * ms[def]) b = i;
+    return b;
+  };
+  int fdef = 0;
+  for (int i = 0; i < rep.n_factor; ++i)
+    if (rep.factor_cand_threads[i] == 256 && rep.factor_cand_rank[i] == 2) fdef = i;
+  const int bf = pick(rep.factor_ms, rep.n_factor, fdef);
+  const int ba = rep.n_apply > 0 ? pick(rep.apply_ms, rep.n_apply, 0) : 0;
   // leave the factors of the chosen shape
   cudaError_t e3 = launch_factor(t.prec, rep.factor_cand_threads[bf], rep.factor_cand_rank[bf], t.subs, t.nsub,
-                                 t.max_b, t.Aloc, t.L, t.Lrev, t.dinv, t.pivstats, t.status, t.st);
+                                 t.max_b, t.Aloc, t.L, t.Lrev, t.dinv, t.pivstats, t.status, t.st, t.split);
   if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(t.st);
   if (e3 != cudaSuccess) {
     std::fprintf(stderr, "raspml: tune: %s\n", cudaGetErrorString(e3));

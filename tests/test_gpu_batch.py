@@ -183,3 +183,34 @@ def test_tensor_core_factor_in_a_batch(pkg, probs, prec, tol, rank):
         for q, (w, zq) in enumerate(zip(probs, B.split(z))):
             _, _, R = oracle_problem(w)
             assert rel(zq.cpu().numpy(), R.apply(rs[q])) <= tol, q
+
+
+def test_mixed_band_factor_shape(pkg):
+    """A batch whose subdomains straddle the tensor-core form's band limit
+    (b = 193 in c0 with one box across, b <= 127 elsewhere): the mixed shape
+    factors the wide ones on the CUDA cores and the rest on the tensor cores,
+    and gives every problem its oracle B^-1 and the CUDA-core shape's
+    iteration counts."""
+    from gpu_util import variant
+    from paper_2602_00735_gb300 import RasPmlError
+    probs = [variant("c0", px=1, py=2), variant("tiny3"), variant("small", px=3, py=5)]
+    with pkg.BatchRasPml([w.params() for w in probs], factor_prec=1) as B:
+        assert B.info()["max_band"] > 127
+        with pytest.raises(RasPmlError):
+            B.set_shapes(128, 8, 8)            # the tensor-core form alone cannot take b > 127
+        rs = [random_vector(int(n), 70 + q) for q, n in enumerate(B.sizes)]
+        b = B.assemble_rhs(_sources(probs))
+        its = {}
+        for shape in ((1024, 2), (1024, 8), (512, 16)):
+            B.set_shapes(*shape, 8)
+            B.factor()
+            z = B.apply(B.join(rs))
+            for q, (w, zq) in enumerate(zip(probs, B.split(z))):
+                _, _, R = oracle_problem(w)
+                assert rel(zq.cpu().numpy(), R.apply(rs[q])) <= 1e-4, (shape, q)
+            _, its[shape], _, st = B.solve(b, rtol=1e-8, maxit=400)
+            assert st == 0
+        for shape in ((1024, 8), (512, 16)):
+            assert np.all(np.abs(np.asarray(its[shape]) - np.asarray(its[(1024, 2)])) <= 1), its
+        rep = B.tune()
+        assert {"1024x2", "512x2"} <= set(rep["factor_ms"]) and len(rep["factor_ms"]) == 8
