@@ -258,11 +258,12 @@ def test_factor_shapes_match_oracle(solver_cls, name, kw, prec, tol, threads, ra
 # gives the oracle's B^-1 about as closely as the complex64 CUDA-core form on
 # the same input: each TF32 product pair carries ~2^-21 relative rounding
 # against FP32's 2^-24, so its error may exceed that form's by a small factor
-# only. Half-bandwidths from below one panel (b < 16) to the form's limit
-# (127), odd and even, mixed within one handle.
+# only. Half-bandwidths from below one panel (b = 5, 6 and 10, 12) to the
+# form's limit (127), odd and even, mixed within one handle.
 
 TC_CASES = [("tiny3", {}), ("small", {"px": 3, "py": 5}),
             ("tiny", {"px": 6, "py": 5, "ovlp_cells": 1, "pml_cells": 1}),
+            ("tiny", {"px": 12, "py": 12, "ovlp_cells": 1, "pml_cells": 0}),
             ("c0", {"px": 2, "py": 3}), ("c0", {"px": 2, "py": 2, "ovlp_cells": 15, "pml_cells": 15})]
 
 
