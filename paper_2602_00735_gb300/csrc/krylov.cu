@@ -101,21 +101,42 @@ __device__ __forceinline__ void cmac_df(float& rh, float& rl, float& ih, float& 
   df_acc(ih, il, p, t);
 }
 
-__global__ void __launch_bounds__(kThreads)
-    k_spmv_df(long long n, int nx, const dfc* __restrict__ D, const dfc* __restrict__ CW,
-              const dfc* __restrict__ CS, const dfc* __restrict__ CSW, const c128* __restrict__ x,
-              c128* __restrict__ y, const KState* __restrict__ kst) {
+// y = A x in double-float arithmetic on split coefficients, tiled: a CTA
+// takes kSpTX x kSpTY grid points, splits the x values of the tile and its
+// one-point halo into shared memory once (1.3 splits per row instead of 7),
+// and each thread sums its row's seven products in the fixed order D, W, E,
+// S, N, SW, NE. Couplings to points outside the grid are zero in the stored
+// coefficients and are skipped.
+constexpr int kSpTX = 32, kSpTY = 8;
+
+__global__ void __launch_bounds__(kSpTX * kSpTY)
+    k_spmv_df(int nx, int ny, const dfc* __restrict__ D, const dfc* __restrict__ CW, const dfc* __restrict__ CS,
+              const dfc* __restrict__ CSW, const c128* __restrict__ x, c128* __restrict__ y,
+              const KState* __restrict__ kst) {
   if (kst != nullptr && kst->stop) return;
-  const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (r >= n) return;
+  __shared__ dfc xs[kSpTY + 2][kSpTX + 2];
+  const int i0 = blockIdx.x * kSpTX, j0 = blockIdx.y * kSpTY;
+  for (int e = threadIdx.x; e < (kSpTX + 2) * (kSpTY + 2); e += kSpTX * kSpTY) {
+    const int li = e % (kSpTX + 2), lj = e / (kSpTX + 2);
+    const int gi = i0 + li - 1, gj = j0 + lj - 1;
+    dfc v = {0.f, 0.f, 0.f, 0.f};
+    if (gi >= 0 && gi < nx && gj >= 0 && gj < ny) v = split_c(x[(long long)gj * nx + gi]);
+    xs[lj][li] = v;
+  }
+  __syncthreads();
+  const int ti = threadIdx.x % kSpTX, tj = threadIdx.x / kSpTX;
+  const int i = i0 + ti, j = j0 + tj;
+  if (i >= nx || j >= ny) return;
+  const long long r = (long long)j * nx + i;
+  const bool e_ok = i + 1 < nx, n_ok = j + 1 < ny;
   float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-  cmac_df(rh, rl, ih, il, D[r], split_c(x[r]));
-  if (r >= 1) cmac_df(rh, rl, ih, il, CW[r], split_c(x[r - 1]));
-  if (r + 1 < n) cmac_df(rh, rl, ih, il, CW[r + 1], split_c(x[r + 1]));
-  if (r >= nx) cmac_df(rh, rl, ih, il, CS[r], split_c(x[r - nx]));
-  if (r + nx < n) cmac_df(rh, rl, ih, il, CS[r + nx], split_c(x[r + nx]));
-  if (r >= nx + 1) cmac_df(rh, rl, ih, il, CSW[r], split_c(x[r - nx - 1]));
-  if (r + nx + 1 < n) cmac_df(rh, rl, ih, il, CSW[r + nx + 1], split_c(x[r + nx + 1]));
+  cmac_df(rh, rl, ih, il, D[r], xs[tj + 1][ti + 1]);
+  if (i >= 1) cmac_df(rh, rl, ih, il, CW[r], xs[tj + 1][ti]);
+  if (e_ok) cmac_df(rh, rl, ih, il, CW[r + 1], xs[tj + 1][ti + 2]);
+  if (j >= 1) cmac_df(rh, rl, ih, il, CS[r], xs[tj][ti + 1]);
+  if (n_ok) cmac_df(rh, rl, ih, il, CS[r + nx], xs[tj + 2][ti + 1]);
+  if (i >= 1 && j >= 1) cmac_df(rh, rl, ih, il, CSW[r], xs[tj][ti]);
+  if (e_ok && n_ok) cmac_df(rh, rl, ih, il, CSW[r + nx + 1], xs[tj + 2][ti + 2]);
   y[r] = mk(df_to_d(rh, rl), df_to_d(ih, il));
 }
 
@@ -602,9 +623,10 @@ cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, cons
 
 cudaError_t launch_spmv_df(long long n, int nx, const void* D, const void* CW, const void* CS, const void* CSW,
                            const c128* x, c128* y, const KState* kst, cudaStream_t st) {
-  unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
-  k_spmv_df<<<blocks, kThreads, 0, st>>>(n, nx, (const dfc*)D, (const dfc*)CW, (const dfc*)CS, (const dfc*)CSW, x, y,
-                                         kst);
+  const int ny = (int)(n / nx);
+  dim3 grid((nx + kSpTX - 1) / kSpTX, (ny + kSpTY - 1) / kSpTY);
+  k_spmv_df<<<grid, kSpTX * kSpTY, 0, st>>>(nx, ny, (const dfc*)D, (const dfc*)CW, (const dfc*)CS, (const dfc*)CSW,
+                                            x, y, kst);
   return cudaGetLastError();
 }
 
