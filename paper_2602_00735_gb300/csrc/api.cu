@@ -126,7 +126,8 @@ int ensure_krylov(ras_pml_handle* h, int m, int maxit) {
     RP_ALLOC(h->yv, (size_t)m);
     RP_ALLOC(h->hbuf, (size_t)m + 1);
     RP_ALLOC(h->cs, (size_t)m);
-    RP_ALLOC(h->partial, (size_t)(m + 1) * rp::dot_blocks());
+    // projections: (m + 1) x dot_blocks(); norms from the update: up to 16 per SM
+    RP_ALLOC(h->partial, (size_t)std::max(m + 1, 8) * rp::dot_blocks());
     h->kcap = m;
   }
   if (h->hist_cap < maxit + 1) {
@@ -629,8 +630,9 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
           RP_CUDA(rp::launch_mr_axpy(zj, h->lc, h->lhv, n, h->kst, st));
         }
         if (h->timing) RP_CUDA(cudaEventRecord(evj[1], st));
-        if (h->Ddf)
-          RP_CUDA(rp::launch_spmv_df(n, h->geo.nx, h->Ddf, h->CWdf, h->CSdf, h->CSWdf, zj, w, h->kst, st));
+        if (h->Ddf)   // with the complex64 basis, w stays in double-float form through the step
+          RP_CUDA(rp::launch_spmv_df(n, h->geo.nx, h->Ddf, h->CWdf, h->CSdf, h->CSWdf, zj, w, h->kst, st,
+                                     c64basis ? 1 : 0));
         else
           RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, nullptr, w, h->kst, st));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[2], st));
@@ -645,11 +647,13 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
           RP_CUDA(rp::launch_add(hcol, h->hbuf, jj + 1, h->kst, 0, st));
           if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst))) return s;
         } else if (c64basis) {
-          // one pass against the complex64 basis, double-float products and sums
-          RP_CUDA(rp::launch_dots_c64b(V64, n, jj + 1, w, n, h->partial, h->kst, st));
+          // one pass against the complex64 basis, double-float products and sums;
+          // the update also leaves the partial sums of ||w||^2
+          int nparts = 0;
+          RP_CUDA(rp::launch_dots_c64b(V64, n, jj + 1, w, n, h->partial, h->kst, st, 1));
           RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, hcol, 0, h->kst, 0, st));
-          RP_CUDA(rp::launch_axpys_c64b(V64, n, jj + 1, hcol, -1.0, w, n, h->kst, st));
-          if ((s = dev_norm(h, w, &h->kst->hnorm, hcol + jj + 1, h->kst))) return s;
+          RP_CUDA(rp::launch_axpys_c64b(V64, n, jj + 1, hcol, -1.0, w, n, h->kst, st, 1, h->partial, &nparts));
+          RP_CUDA(rp::launch_norm_finish(h->partial, &h->kst->hnorm, hcol + jj + 1, h->kst, 0, st, nparts));
         } else if (h->p.ortho == 3) {
           // one pass against the double-float basis, products and sums on the FP32 pipe
           RP_CUDA(rp::launch_split(w, h->wdf, n, h->kst, st));
@@ -676,7 +680,7 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
         if (dfbasis)
           RP_CUDA(rp::launch_scale_to_df(w, n, &h->kst->hnorm, h->kst, st));
         else if (c64basis)
-          RP_CUDA(rp::launch_scale_to_c64(w, V64 + (size_t)(jj + 1) * n, n, &h->kst->hnorm, h->kst, st));
+          RP_CUDA(rp::launch_scale_df_to_c64(w, V64 + (size_t)(jj + 1) * n, n, &h->kst->hnorm, h->kst, st));
         else
           RP_CUDA(rp::launch_scale_inv(w, n, &h->kst->hnorm, h->kst, st));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[3], st));

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kBT)
     k_bdots_df(const int* __restrict__ tile_prob, const c64* __restrict__ V, long long ldv,
                const c128* __restrict__ w, const int* __restrict__ jptr, c128* __restrict__ partial, int ntiles,
                const KState* __restrict__ kst) {
-  extern __shared__ c128 wsum[];   // [ncols][kBT / 32]
+  extern __shared__ float4 wsum[];   // [ncols][kBT / 32] double-float sums (rh, rl, ih, il)
   const int t = blockIdx.x;
   const int q = tile_prob[t];
   if (kst[q].stop) return;
@@ -260,19 +260,32 @@ __global__ void __launch_bounds__(kBT)
         df_acc(ih[u], il[u], -p, -e);
       }
     }
+    // warp sums in double-float on the FP32 pipe (an FP64 sum per thread
+    // and column cost more than the products here)
 #pragma unroll
     for (int u = 0; u < kBCols; ++u) {
       if (c0 + u >= ncols) break;
-      const c128 v = warp_sum(mk(df_to_d(rh[u], rl[u]), df_to_d(ih[u], il[u])));
-      if (lane == 0) wsum[(c0 + u) * (kBT / 32) + wid] = v;
+      float a = rh[u], b = rl[u], c = ih[u], d = il[u];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float a2 = __shfl_xor_sync(0xffffffffu, a, o), b2 = __shfl_xor_sync(0xffffffffu, b, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, c, o), d2 = __shfl_xor_sync(0xffffffffu, d, o);
+        df_acc(a, b, a2, b2);
+        df_acc(c, d, c2, d2);
+      }
+      if (lane == 0) wsum[(c0 + u) * (kBT / 32) + wid] = make_float4(a, b, c, d);
     }
   }
   __syncthreads();
   for (int c = threadIdx.x; c < ncols; c += kBT) {
-    c128 s = mk(0.0, 0.0);
+    float4 s4 = wsum[c * (kBT / 32)];
 #pragma unroll
-    for (int u = 0; u < kBT / 32; ++u) s = s + wsum[c * (kBT / 32) + u];
-    partial[(long long)c * ntiles + t] = s;
+    for (int u = 1; u < kBT / 32; ++u) {
+      const float4 v = wsum[c * (kBT / 32) + u];
+      df_acc(s4.x, s4.y, v.x, v.y);
+      df_acc(s4.z, s4.w, v.z, v.w);
+    }
+    partial[(long long)c * ntiles + t] = mk(df_to_d(s4.x, s4.y), df_to_d(s4.z, s4.w));
   }
 }
 

@@ -94,9 +94,10 @@ cudaError_t launch_apply(int prec, int cols, const Geo& g, const Geo* geos, cons
 cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, const c128* CS, const c128* CSW,
                         const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st,
                         int bsub_kind = RK_C128);
-// y = A x with double-float coefficients (dfc arrays from launch_split)
+// y = A x with double-float coefficients (dfc arrays from launch_split); y
+// written as dfc (double-float form) when out_df is set
 cudaError_t launch_spmv_df(long long n, int nx, const void* D, const void* CW, const void* CS, const void* CSW,
-                           const c128* x, c128* y, const KState* kst, cudaStream_t st);
+                           const c128* x, c128* y, const KState* kst, cudaStream_t st, int out_df = 0);
 int dot_blocks();
 cudaError_t launch_dots(const c128* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
                         const KState* kst, int gate, cudaStream_t st);
@@ -113,15 +114,22 @@ cudaError_t launch_axpys_df(const void* V, long long ldv, int ncols, const c128*
                             long long n, const KState* kst, int gate, cudaStream_t st);
 cudaError_t launch_add(c128* dst, const c128* src, int cnt, const KState* kst, int gate, cudaStream_t st);
 // complex64 Krylov basis (ortho = 4): v = fl32(w / nrm); projections of w
-// (complex128, split in the kernel) on the basis and the update, double-float
+// on the basis and the update, double-float. w is complex128 (split in the
+// kernels) or, with wdf, held in double-float form (dfc); the update can
+// also leave the per-block sums of |w|^2 in pnorm (*nblocks of them) for
+// launch_norm_finish.
 cudaError_t launch_scale_to_c64(const c128* w, void* v, long long n, const double* nrm, const KState* kst,
                                 cudaStream_t st);
+cudaError_t launch_scale_df_to_c64(const void* w, void* v, long long n, const double* nrm, const KState* kst,
+                                   cudaStream_t st);
 cudaError_t launch_dots_c64b(const void* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
-                             const KState* kst, cudaStream_t st);
+                             const KState* kst, cudaStream_t st, int wdf = 0);
 cudaError_t launch_axpys_c64b(const void* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
-                              long long n, const KState* kst, cudaStream_t st);
+                              long long n, const KState* kst, cudaStream_t st, int wdf = 0, c128* pnorm = nullptr,
+                              int* nblocks = nullptr);
+// ||.|| from nparts partial sums (default: dot_blocks() of them)
 cudaError_t launch_norm_finish(const c128* partial, double* out, c128* hslot, const KState* kst, int gate,
-                               cudaStream_t st);
+                               cudaStream_t st, int nparts = 0);
 cudaError_t launch_scale_inv(c128* v, long long n, const double* nrm, const KState* kst, cudaStream_t st);
 cudaError_t launch_cycle_init(KState* kst, c128* gvec, int m, double rtol, double* hist, cudaStream_t st);
 // the cycle also ends (without convergence) once |g_{j+1}| <= cfloor * beta0

@@ -111,7 +111,7 @@ constexpr int kSpTX = 32, kSpTY = 8;
 
 __global__ void __launch_bounds__(kSpTX * kSpTY)
     k_spmv_df(int nx, int ny, const dfc* __restrict__ D, const dfc* __restrict__ CW, const dfc* __restrict__ CS,
-              const dfc* __restrict__ CSW, const c128* __restrict__ x, c128* __restrict__ y,
+              const dfc* __restrict__ CSW, const c128* __restrict__ x, c128* __restrict__ y, int out_df,
               const KState* __restrict__ kst) {
   if (kst != nullptr && kst->stop) return;
   __shared__ dfc xs[kSpTY + 2][kSpTX + 2];
@@ -137,7 +137,16 @@ __global__ void __launch_bounds__(kSpTX * kSpTY)
   if (n_ok) cmac_df(rh, rl, ih, il, CS[r + nx], xs[tj + 2][ti + 1]);
   if (i >= 1 && j >= 1) cmac_df(rh, rl, ih, il, CSW[r], xs[tj][ti]);
   if (e_ok && n_ok) cmac_df(rh, rl, ih, il, CSW[r + nx + 1], xs[tj + 2][ti + 2]);
-  y[r] = mk(df_to_d(rh, rl), df_to_d(ih, il));
+  if (out_df) {
+    dfc o;
+    o.rh = rh;
+    o.rl = rl;
+    o.ih = ih;
+    o.il = il;
+    reinterpret_cast<dfc*>(y)[r] = o;
+  } else {
+    y[r] = mk(df_to_d(rh, rl), df_to_d(ih, il));
+  }
 }
 
 // partial[c * gridDim.x + blk] = sum over the block's rows of conj(V_c) w
@@ -345,7 +354,7 @@ __global__ void k_scale_to_c64(const c128* __restrict__ w, c64* __restrict__ v, 
 constexpr int kC64Cols = 4;
 
 __global__ void __launch_bounds__(kThreads)
-    k_dots_c64b(const c64* __restrict__ V, long long ldv, int ncols, const c128* __restrict__ w, long long n,
+    k_dots_c64b(const c64* __restrict__ V, long long ldv, int ncols, const c128* __restrict__ w, int wdf, long long n,
                 c128* __restrict__ partial, const KState* __restrict__ kst) {
   if (skip(kst, 0)) return;
   constexpr int kDfCols = kC64Cols;
@@ -371,7 +380,8 @@ __global__ void __launch_bounds__(kThreads)
         a[u][q] = (q < nc && (u == 0 || two)) ? V[(long long)(c0 + q) * ldv + r + u * kThreads] : mk(0.f, 0.f);
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const dfc b = split_c(wv[u]);
+      // w held in double-float form already (wdf), or complex128 split here
+      const dfc b = wdf ? *reinterpret_cast<const dfc*>(&wv[u]) : split_c(wv[u]);
       const dfl br = dfl_of(b.rh, b.rl), bi = dfl_of(b.ih, b.il);
 #pragma unroll
       for (int q = 0; q < kDfCols; ++q) {
@@ -389,36 +399,55 @@ __global__ void __launch_bounds__(kThreads)
       }
     }
   }
-  // the kDfCols sums of the block in one pass: shuffles within each warp,
-  // one barrier, then the first warp adds the warps' values
-  __shared__ c128 red[kThreads / 32][kDfCols];
+  // the kDfCols sums of the block in one pass, in double-float on the FP32
+  // pipe (FP64 runs at a small fraction of it here: summing in FP64 per
+  // thread cost as much as the main loop): shuffles within each warp, one
+  // barrier, the first warp adds the warps' values, one conversion per column
+  __shared__ float4 red[kThreads / 32][kDfCols];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < kDfCols; ++q) {
-    const c128 v = warp_sum(mk(df_to_d(rh[q], rl[q]), df_to_d(ih[q], il[q])));
-    if (lane == 0) red[wid][q] = v;
+    float a = rh[q], b = rl[q], c = ih[q], d = il[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float a2 = __shfl_xor_sync(0xffffffffu, a, o), b2 = __shfl_xor_sync(0xffffffffu, b, o);
+      const float c2 = __shfl_xor_sync(0xffffffffu, c, o), d2 = __shfl_xor_sync(0xffffffffu, d, o);
+      df_acc(a, b, a2, b2);
+      df_acc(c, d, c2, d2);
+    }
+    if (lane == 0) red[wid][q] = make_float4(a, b, c, d);
   }
   __syncthreads();
   if (threadIdx.x < nc) {
-    c128 s = mk(0.0, 0.0);
+    float4 t = red[0][threadIdx.x];
 #pragma unroll
-    for (int u = 0; u < kThreads / 32; ++u) s = s + red[u][threadIdx.x];
-    partial[(long long)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+    for (int u = 1; u < kThreads / 32; ++u) {
+      const float4 v = red[u][threadIdx.x];
+      df_acc(t.x, t.y, v.x, v.y);
+      df_acc(t.z, t.w, v.z, v.w);
+    }
+    partial[(long long)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = mk(df_to_d(t.x, t.y), df_to_d(t.z, t.w));
   }
 }
 
-// w += sign * sum_c V_c h_c, double-float accumulation
+// w += sign * sum_c V_c h_c, double-float accumulation. With wdf, w is held
+// in double-float form (read and written as dfc); with pnorm, the block's
+// sum of |w|^2 (double-float, FP64 at the end) goes to pnorm[blockIdx.x].re.
 __global__ void __launch_bounds__(kThreads)
     k_axpys_c64b(const c64* __restrict__ V, long long ldv, int ncols, const c128* __restrict__ h, double sign,
-                 c128* __restrict__ w, long long n, const KState* __restrict__ kst) {
+                 c128* __restrict__ w, int wdf, c128* __restrict__ pnorm, long long n,
+                 const KState* __restrict__ kst) {
   if (skip(kst, 0)) return;
   extern __shared__ dfc hsc[];
   for (int c = threadIdx.x; c < ncols; c += blockDim.x) hsc[c] = split_c(mk(sign * h[c].re, sign * h[c].im));
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
+  float nh = 0.f, nl = 0.f;   // sum of |w|^2 of this thread's rows
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
-    const dfc w0 = split_c(w[r]);
-    float rh = w0.rh, rl = w0.rl, ih = w0.ih, il = w0.il;
+    const dfc w0 = wdf ? reinterpret_cast<const dfc*>(w)[r] : split_c(w[r]);
+    // two accumulator sets (even and odd columns) for two independent
+    // dependency chains per part; added together at the end
+    float rh[2] = {w0.rh, 0.f}, rl[2] = {w0.rl, 0.f}, ih[2] = {w0.ih, 0.f}, il[2] = {w0.il, 0.f};
     constexpr int kU = 2 * kDfCols;   // basis entries loaded ahead of the arithmetic
     for (int c0 = 0; c0 < ncols; c0 += kU) {
       c64 a[kU];
@@ -428,21 +457,91 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
       for (int q = 0; q < kU; ++q) {
         if (c0 + q >= ncols) continue;
+        const int u = q & 1;
         const dfc hc = hsc[c0 + q];
         const dfl hr = dfl_of(hc.rh, hc.rl), hi_ = dfl_of(hc.ih, hc.il);
         float p, t;
         // a h = (ar hr - ai hi) + i (ar hi + ai hr)
         fdf_prod(a[q].re, hr, p, t);
-        df_acc(rh, rl, p, t);
+        df_acc(rh[u], rl[u], p, t);
         fdf_prod(a[q].im, hi_, p, t);
-        df_acc(rh, rl, -p, -t);
+        df_acc(rh[u], rl[u], -p, -t);
         fdf_prod(a[q].re, hi_, p, t);
-        df_acc(ih, il, p, t);
+        df_acc(ih[u], il[u], p, t);
         fdf_prod(a[q].im, hr, p, t);
-        df_acc(ih, il, p, t);
+        df_acc(ih[u], il[u], p, t);
       }
     }
-    w[r] = mk(df_to_d(rh, rl), df_to_d(ih, il));
+    df_acc(rh[0], rl[0], rh[1], rl[1]);
+    df_acc(ih[0], il[0], ih[1], il[1]);
+    if (wdf) {
+      dfc o;
+      o.rh = rh[0];
+      o.rl = rl[0];
+      o.ih = ih[0];
+      o.il = il[0];
+      reinterpret_cast<dfc*>(w)[r] = o;
+    } else {
+      w[r] = mk(df_to_d(rh[0], rl[0]), df_to_d(ih[0], il[0]));
+    }
+    if (pnorm != nullptr) {
+      // |w|^2 = rh^2 + 2 rh rl + ih^2 + 2 ih il (+ terms below 2^-46 relative)
+      float p = rh[0] * rh[0];
+      float t = fmaf(rh[0], rh[0], -p) + 2.f * rh[0] * rl[0];
+      df_acc(nh, nl, p, t);
+      p = ih[0] * ih[0];
+      t = fmaf(ih[0], ih[0], -p) + 2.f * ih[0] * il[0];
+      df_acc(nh, nl, p, t);
+    }
+  }
+  if (pnorm != nullptr) {
+    __shared__ float2 red[kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float a2 = __shfl_xor_sync(0xffffffffu, nh, o), b2 = __shfl_xor_sync(0xffffffffu, nl, o);
+      df_acc(nh, nl, a2, b2);
+    }
+    if (lane == 0) red[wid] = make_float2(nh, nl);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float a = red[0].x, b = red[0].y;
+      for (int u = 1; u < kThreads / 32; ++u) df_acc(a, b, red[u].x, red[u].y);
+      pnorm[blockIdx.x] = mk(df_to_d(a, b), 0.0);
+    }
+  }
+}
+
+// v = fl32(w / nrm) for w in double-float form: 1/nrm as a double-float
+// pair from an FP32 reciprocal and one Newton step, products as FMA
+// residual pairs (FP32 pipe only)
+__global__ void k_scale_df_to_c64(const dfc* __restrict__ w, c64* __restrict__ v, long long n,
+                                  const double* __restrict__ nrm, const KState* __restrict__ kst) {
+  if (skip(kst, 0)) return;
+  const double d = *nrm;
+  if (!(d > 0.0)) return;
+  const dfl dd = split_d(d);
+  const float s0 = 1.f / dd.hi;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (!(dd.hi > 0.f) || !(s0 < 3e38f)) {
+    // nrm outside the FP32 range: FP64 (never on a regular step)
+    const double sd = 1.0 / d;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
+      const dfc x = w[r];
+      v[r] = mk((float)(sd * ((double)x.rh + (double)x.rl)), (float)(sd * ((double)x.ih + (double)x.il)));
+    }
+    return;
+  }
+  // 1 - d s0 in double-float, then s = s0 + s0 (1 - d s0)
+  const float r0 = fmaf(-dd.hi, s0, 1.f) - dd.lo * s0;
+  const float sh = s0, sl = s0 * r0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
+    const dfc x = w[r];
+    float p = x.rh * sh;
+    const float vr = p + (fmaf(x.rh, sh, -p) + fmaf(x.rh, sl, x.rl * sh));
+    p = x.ih * sh;
+    const float vi = p + (fmaf(x.ih, sh, -p) + fmaf(x.ih, sl, x.il * sh));
+    v[r] = mk(vr, vi);
   }
 }
 
@@ -622,11 +721,11 @@ cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, cons
 }
 
 cudaError_t launch_spmv_df(long long n, int nx, const void* D, const void* CW, const void* CS, const void* CSW,
-                           const c128* x, c128* y, const KState* kst, cudaStream_t st) {
+                           const c128* x, c128* y, const KState* kst, cudaStream_t st, int out_df) {
   const int ny = (int)(n / nx);
   dim3 grid((nx + kSpTX - 1) / kSpTX, (ny + kSpTY - 1) / kSpTY);
   k_spmv_df<<<grid, kSpTX * kSpTY, 0, st>>>(nx, ny, (const dfc*)D, (const dfc*)CW, (const dfc*)CS, (const dfc*)CSW,
-                                            x, y, kst);
+                                            x, y, out_df, kst);
   return cudaGetLastError();
 }
 
@@ -694,8 +793,15 @@ cudaError_t launch_add(c128* dst, const c128* src, int cnt, const KState* kst, i
 }
 
 cudaError_t launch_norm_finish(const c128* partial, double* out, c128* hslot, const KState* kst, int gate,
-                               cudaStream_t st) {
-  k_norm_finish<<<1, 32, 0, st>>>(partial, dot_blocks(), out, hslot, kst, gate);
+                               cudaStream_t st, int nparts) {
+  k_norm_finish<<<1, 32, 0, st>>>(partial, nparts > 0 ? nparts : dot_blocks(), out, hslot, kst, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_df_to_c64(const void* w, void* v, long long n, const double* nrm, const KState* kst,
+                                   cudaStream_t st) {
+  dot_blocks();
+  k_scale_df_to_c64<<<grid_for(n, kThreads), kThreads, 0, st>>>((const dfc*)w, (c64*)v, n, nrm, kst);
   return cudaGetLastError();
 }
 
@@ -735,21 +841,24 @@ cudaError_t launch_scale_to_c64(const c128* w, void* v, long long n, const doubl
 }
 
 cudaError_t launch_dots_c64b(const void* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
-                             const KState* kst, cudaStream_t st) {
+                             const KState* kst, cudaStream_t st, int wdf) {
   dim3 grid(dot_blocks(), (ncols + kC64Cols - 1) / kC64Cols);
-  k_dots_c64b<<<grid, kThreads, 0, st>>>((const c64*)V, ldv, ncols, w, n, partial, kst);
+  k_dots_c64b<<<grid, kThreads, 0, st>>>((const c64*)V, ldv, ncols, w, wdf, n, partial, kst);
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpys_c64b(const void* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
-                              long long n, const KState* kst, cudaStream_t st) {
+                              long long n, const KState* kst, cudaStream_t st, int wdf, c128* pnorm,
+                              int* nblocks) {
   dot_blocks();
   const size_t smem = (size_t)ncols * sizeof(dfc);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_axpys_c64b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_axpys_c64b<<<grid_for(n, kThreads), kThreads, smem, st>>>((const c64*)V, ldv, ncols, h, sign, w, n, kst);
+  const unsigned g = grid_for(n, kThreads);
+  if (nblocks) *nblocks = (int)g;
+  k_axpys_c64b<<<g, kThreads, smem, st>>>((const c64*)V, ldv, ncols, h, sign, w, wdf, pnorm, n, kst);
   return cudaGetLastError();
 }
 
