@@ -571,6 +571,9 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
   double rel = NAN;
   const bool dfbasis = h->p.ortho == 3;   // V stored in double-float form
   const bool c64basis = h->p.ortho == 4;  // V stored as complex64, w in its own buffer
+  // z_j in double-float form (prolongation to SpMV and to x += Z y); not with
+  // the learned stage, which updates z_j in complex128
+  const int zdf = (c64basis && h->Ddf && !h->net && h->p.factor_prec >= 1) ? 1 : 0;
   const int bkind = dfbasis ? rp::RK_DF : c64basis ? rp::RK_C64 : rp::RK_C128;
   c64* V64 = reinterpret_cast<c64*>(h->V);
   for (;;) {
@@ -614,7 +617,7 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
         ++issued;
         if (h->timing) RP_CUDA(cudaEventRecord(evj[0], st));
         RP_CUDA(rp::launch_apply(h->p.factor_prec, h->tune.apply_cols, h->geo, h->geo_d, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev,
-                                 h->dinv, vj, h->Y, zj, h->kst, h->status, st, bkind));
+                                 h->dinv, vj, h->Y, zj, h->kst, h->status, st, bkind, zdf));
         if (h->net) {
           // learned stage: c = correction of r1 = v_j - A z_j (r1 held in w), then
           // z_j += alpha c with the alpha minimising ||r1 - alpha A c||
@@ -632,7 +635,7 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
         if (h->timing) RP_CUDA(cudaEventRecord(evj[1], st));
         if (h->Ddf)   // with the complex64 basis, w stays in double-float form through the step
           RP_CUDA(rp::launch_spmv_df(n, h->geo.nx, h->Ddf, h->CWdf, h->CSdf, h->CSWdf, zj, w, h->kst, st,
-                                     c64basis ? 1 : 0));
+                                     c64basis ? 1 : 0, zdf));
         else
           RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, nullptr, w, h->kst, st));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[2], st));
@@ -702,7 +705,10 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
     // x += Z y with y = H^-1 g
     if (ks.jdone > 0) {
       RP_CUDA(rp::launch_backsolve(h->H, ldh, h->gvec, h->kst, h->yv, st));
-      RP_CUDA(rp::launch_axpys(h->Z, n, ks.jdone, h->yv, 1.0, x, n, nullptr, 0, st));
+      if (zdf)
+        RP_CUDA(rp::launch_axpys_df(h->Z, n, ks.jdone, h->yv, 1.0, x, n, nullptr, 0, st));
+      else
+        RP_CUDA(rp::launch_axpys(h->Z, n, ks.jdone, h->yv, 1.0, x, n, nullptr, 0, st));
     }
     // true residual
     RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, x, b, h->V, nullptr, st));

@@ -21,7 +21,9 @@
 //   Subdomains may belong to different problems of a batch: each reads its
 //   problem's geometry (geos[prob]) and skips when that problem has stopped.
 // k_prolong: one thread per global unknown sums the (at most four) weighted
-//   local values that cover it, in a fixed order (bit-reproducible).
+//   local values that cover it, in a fixed order (bit-reproducible): in FP64
+//   into complex128, or, for complex64 local values, in double-float on the
+//   FP32 pipe into the double-float form (dfc) the Arnoldi SpMV reads.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(32)
 
 template <typename R>
 __global__ void k_prolong(Geo g, const SubDesc* __restrict__ subs, const cx<R>* __restrict__ Y,
-                          c128* __restrict__ z, const KState* __restrict__ kst) {
+                          c128* __restrict__ z, int out_df, const KState* __restrict__ kst) {
   if (kst != nullptr && kst->stop) return;
   // n < 2^31 (checked at set-up): 32-bit index arithmetic
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -254,6 +256,28 @@ __global__ void k_prolong(Geo g, const SubDesc* __restrict__ subs, const cx<R>* 
   if (bx + 1 < g.px && i > box_start(bx + 1, g.Mx, g.px) - o) qx1 = bx + 1;
   if (by > 0 && j < box_start(by, g.My, g.py) + o) qy0 = by - 1;
   if (by + 1 < g.py && j > box_start(by + 1, g.My, g.py) - o) qy1 = by + 1;
+  if constexpr (sizeof(R) == sizeof(float)) {
+    if (out_df) {
+      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+      for (int qy = qy0; qy <= qy1; ++qy) {
+        for (int qx = qx0; qx <= qx1; ++qx) {
+          const SubDesc& sd = subs[qy * g.px + qx];
+          const int li = i - sd.ix0, lj = j - sd.iy0;
+          if (li < 0 || li >= sd.nlx || lj < 0 || lj >= sd.nly) continue;
+          const cx<R> v = Y[sd.v_off + (long long)lj * sd.nlx + li];
+          df_acc(rh, rl, v.re, 0.f);
+          df_acc(ih, il, v.im, 0.f);
+        }
+      }
+      dfc o;
+      o.rh = rh;
+      o.rl = rl;
+      o.ih = ih;
+      o.il = il;
+      reinterpret_cast<dfc*>(z)[r] = o;
+      return;
+    }
+  }
   double re = 0.0, im = 0.0;
   for (int qy = qy0; qy <= qy1; ++qy) {
     for (int qx = qx0; qx <= qx1; ++qx) {
@@ -310,24 +334,26 @@ cudaError_t launch_local_solves(int prec, int cols, const Geo* geos, const SubDe
 #undef RP_APPLY_ARGS
 
 cudaError_t launch_prolong(int prec, const Geo& g, const SubDesc* subs, const void* Y, c128* z, const KState* kst,
-                           cudaStream_t st) {
+                           cudaStream_t st, int out_df) {
   long long n = (long long)g.nx * g.ny;
   int threads = 256;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
-  if (prec == 0)
-    k_prolong<double><<<blocks, threads, 0, st>>>(g, subs, (const c128*)Y, z, kst);
-  else
-    k_prolong<float><<<blocks, threads, 0, st>>>(g, subs, (const c64*)Y, z, kst);
+  if (prec == 0) {
+    if (out_df) return cudaErrorInvalidValue;
+    k_prolong<double><<<blocks, threads, 0, st>>>(g, subs, (const c128*)Y, z, 0, kst);
+  } else {
+    k_prolong<float><<<blocks, threads, 0, st>>>(g, subs, (const c64*)Y, z, out_df, kst);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply(int prec, int cols, const Geo& g, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
                          int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r, void* Y,
-                         c128* z, const KState* kst, DevStatus* status, cudaStream_t st, int rkind) {
+                         c128* z, const KState* kst, DevStatus* status, cudaStream_t st, int rkind, int out_df) {
   cudaError_t e = launch_local_solves(prec, cols, geos, subs, nsub, max_b, max_bp, Lf, Lb, dinv, r, 0, nullptr, Y,
                                       kst, status, st, rkind);
   if (e != cudaSuccess) return e;
-  return launch_prolong(prec, g, subs, Y, z, kst, st);
+  return launch_prolong(prec, g, subs, Y, z, kst, st, out_df);
 }
 
 }  // namespace rp

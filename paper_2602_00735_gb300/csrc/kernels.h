@@ -83,21 +83,26 @@ cudaError_t launch_local_solves(int prec, int cols, const Geo* geos, const SubDe
                                 int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r,
                                 long long r_ld, const int* jptr, void* Y, const KState* kst, DevStatus* status,
                                 cudaStream_t st, int rkind);
+// z = sum_j R_j^T Y_j; with out_df (complex64 Y only) z is written in
+// double-float form (dfc)
 cudaError_t launch_prolong(int prec, const Geo& g, const SubDesc* subs, const void* Y, c128* z, const KState* kst,
-                           cudaStream_t st);
+                           cudaStream_t st, int out_df = 0);
 // one problem: local solves + prolongation
 cudaError_t launch_apply(int prec, int cols, const Geo& g, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
                          int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r, void* Y,
-                         c128* z, const KState* kst, DevStatus* status, cudaStream_t st, int rkind = RK_C128);
+                         c128* z, const KState* kst, DevStatus* status, cudaStream_t st, int rkind = RK_C128,
+                         int out_df = 0);
 
 // krylov.cu
 cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, const c128* CS, const c128* CSW,
                         const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st,
                         int bsub_kind = RK_C128);
 // y = A x with double-float coefficients (dfc arrays from launch_split); y
-// written as dfc (double-float form) when out_df is set
+// written as dfc (double-float form) when out_df is set, x read as dfc when
+// in_df is set
 cudaError_t launch_spmv_df(long long n, int nx, const void* D, const void* CW, const void* CS, const void* CSW,
-                           const c128* x, c128* y, const KState* kst, cudaStream_t st, int out_df = 0);
+                           const c128* x, c128* y, const KState* kst, cudaStream_t st, int out_df = 0,
+                           int in_df = 0);
 int dot_blocks();
 cudaError_t launch_dots(const c128* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
                         const KState* kst, int gate, cudaStream_t st);

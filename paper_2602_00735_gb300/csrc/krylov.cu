@@ -112,7 +112,7 @@ constexpr int kSpTX = 32, kSpTY = 8;
 __global__ void __launch_bounds__(kSpTX * kSpTY)
     k_spmv_df(int nx, int ny, const dfc* __restrict__ D, const dfc* __restrict__ CW, const dfc* __restrict__ CS,
               const dfc* __restrict__ CSW, const c128* __restrict__ x, c128* __restrict__ y, int out_df,
-              const KState* __restrict__ kst) {
+              int in_df, const KState* __restrict__ kst) {
   if (kst != nullptr && kst->stop) return;
   __shared__ dfc xs[kSpTY + 2][kSpTX + 2];
   const int i0 = blockIdx.x * kSpTX, j0 = blockIdx.y * kSpTY;
@@ -120,7 +120,10 @@ __global__ void __launch_bounds__(kSpTX * kSpTY)
     const int li = e % (kSpTX + 2), lj = e / (kSpTX + 2);
     const int gi = i0 + li - 1, gj = j0 + lj - 1;
     dfc v = {0.f, 0.f, 0.f, 0.f};
-    if (gi >= 0 && gi < nx && gj >= 0 && gj < ny) v = split_c(x[(long long)gj * nx + gi]);
+    if (gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
+      const long long idx = (long long)gj * nx + gi;
+      v = in_df ? reinterpret_cast<const dfc*>(x)[idx] : split_c(x[idx]);
+    }
     xs[lj][li] = v;
   }
   __syncthreads();
@@ -721,11 +724,11 @@ cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, cons
 }
 
 cudaError_t launch_spmv_df(long long n, int nx, const void* D, const void* CW, const void* CS, const void* CSW,
-                           const c128* x, c128* y, const KState* kst, cudaStream_t st, int out_df) {
+                           const c128* x, c128* y, const KState* kst, cudaStream_t st, int out_df, int in_df) {
   const int ny = (int)(n / nx);
   dim3 grid((nx + kSpTX - 1) / kSpTX, (ny + kSpTY - 1) / kSpTY);
   k_spmv_df<<<grid, kSpTX * kSpTY, 0, st>>>(nx, ny, (const dfc*)D, (const dfc*)CW, (const dfc*)CS, (const dfc*)CSW,
-                                            x, y, out_df, kst);
+                                            x, y, out_df, in_df, kst);
   return cudaGetLastError();
 }
 
