@@ -66,7 +66,7 @@ template <typename R>
 __global__ void __launch_bounds__(kBT)
     k_bprolong(const int* __restrict__ tile_prob, const Geo* __restrict__ geos, const SubDesc* __restrict__ subs,
                const int* __restrict__ sub_index, const cx<R>* __restrict__ Y, c128* __restrict__ zbase,
-               long long ldz, const int* __restrict__ jptr, const KState* __restrict__ kst, int gate) {
+               long long ldz, const int* __restrict__ jptr, const KState* __restrict__ kst, int gate, int zdf) {
   const int t = blockIdx.x;
   const int q = tile_prob[t];
   if (gated(kst, q, gate)) return;
@@ -89,6 +89,29 @@ __global__ void __launch_bounds__(kBT)
     if (bx + 1 < px && i > box_start(bx + 1, Mx, px) - o) qx1 = bx + 1;
     if (by > 0 && j < box_start(by, My, py) + o) qy0 = by - 1;
     if (by + 1 < py && j > box_start(by + 1, My, py) - o) qy1 = by + 1;
+    if constexpr (sizeof(R) == sizeof(float)) {
+      if (zdf) {
+        // complex64 local values summed in double-float into the dfc form
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        for (int qy = qy0; qy <= qy1; ++qy) {
+          for (int qx = qx0; qx <= qx1; ++qx) {
+            const SubDesc& sd = subs[sub_index[sub0 + qy * px + qx]];
+            const int li = i - sd.ix0, lj = j - sd.iy0;
+            if (li < 0 || li >= sd.nlx || lj < 0 || lj >= sd.nly) continue;
+            const cx<R> v = Y[sd.v_off + (long long)lj * sd.nlx + li];
+            df_acc(rh, rl, v.re, 0.f);
+            df_acc(ih, il, v.im, 0.f);
+          }
+        }
+        dfc o;
+        o.rh = rh;
+        o.rl = rl;
+        o.ih = ih;
+        o.il = il;
+        reinterpret_cast<dfc*>(z)[r] = o;
+        continue;
+      }
+    }
     double re = 0.0, im = 0.0;
     for (int qy = qy0; qy <= qy1; ++qy) {
       for (int qx = qx0; qx <= qx1; ++qx) {
@@ -152,8 +175,7 @@ __global__ void __launch_bounds__(kBT)
 // The Arnoldi product w = A z_j of step j with the coefficients in
 // double-float form (split once at set-up) and double-float products and
 // sums; the cycle-start residual b - A x keeps the FP64 k_bspmv.
-__device__ __forceinline__ void bcmac_df(float& rh, float& rl, float& ih, float& il, const dfc& a, const c128& xv) {
-  const dfc x = split_c(xv);
+__device__ __forceinline__ void bcmac_df(float& rh, float& rl, float& ih, float& il, const dfc& a, const dfc& x) {
   const dfl ar = dfl_of(a.rh, a.rl), ai = dfl_of(a.ih, a.il);
   const dfl xr = dfl_of(x.rh, x.rl), xi = dfl_of(x.ih, x.il);
   float p, t;
@@ -171,30 +193,38 @@ __global__ void __launch_bounds__(kBT)
     k_bspmv_df(const int* __restrict__ tile_prob, const Geo* __restrict__ geos, const dfc* __restrict__ D,
                const dfc* __restrict__ CW, const dfc* __restrict__ CS, const dfc* __restrict__ CSW,
                const c128* __restrict__ xbase, long long ldx, const int* __restrict__ jptr, c128* __restrict__ y,
-               const KState* __restrict__ kst) {
+               int xdf, const KState* __restrict__ kst) {
   const int t = blockIdx.x;
   const int q = tile_prob[t];
   if (kst[q].stop) return;
   const long long goff = geos[q].goff;
   const int nx = geos[q].nx, n = geos[q].n;
   const c128* x = xbase + (long long)(*jptr) * ldx;
+  // x in double-float form (xdf) or complex128 split here; y written as dfc
+  auto X = [&](long long k) -> dfc { return xdf ? reinterpret_cast<const dfc*>(x)[k] : split_c(x[k]); };
+  dfc* yd = reinterpret_cast<dfc*>(y);
 #pragma unroll 2
   for (int s = 0; s < kRows; ++s) {
     const long long r = (long long)t * kBatchTile + s * kBT + threadIdx.x;
     const int lr = (int)(r - goff);
+    dfc o = {0.f, 0.f, 0.f, 0.f};
     if (lr >= n) {
-      y[r] = mk(0.0, 0.0);
+      yd[r] = o;
       continue;
     }
     float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-    bcmac_df(rh, rl, ih, il, D[r], x[r]);
-    if (lr >= 1) bcmac_df(rh, rl, ih, il, CW[r], x[r - 1]);
-    if (lr + 1 < n) bcmac_df(rh, rl, ih, il, CW[r + 1], x[r + 1]);
-    if (lr >= nx) bcmac_df(rh, rl, ih, il, CS[r], x[r - nx]);
-    if (lr + nx < n) bcmac_df(rh, rl, ih, il, CS[r + nx], x[r + nx]);
-    if (lr >= nx + 1) bcmac_df(rh, rl, ih, il, CSW[r], x[r - nx - 1]);
-    if (lr + nx + 1 < n) bcmac_df(rh, rl, ih, il, CSW[r + nx + 1], x[r + nx + 1]);
-    y[r] = mk(df_to_d(rh, rl), df_to_d(ih, il));
+    bcmac_df(rh, rl, ih, il, D[r], X(r));
+    if (lr >= 1) bcmac_df(rh, rl, ih, il, CW[r], X(r - 1));
+    if (lr + 1 < n) bcmac_df(rh, rl, ih, il, CW[r + 1], X(r + 1));
+    if (lr >= nx) bcmac_df(rh, rl, ih, il, CS[r], X(r - nx));
+    if (lr + nx < n) bcmac_df(rh, rl, ih, il, CS[r + nx], X(r + nx));
+    if (lr >= nx + 1) bcmac_df(rh, rl, ih, il, CSW[r], X(r - nx - 1));
+    if (lr + nx + 1 < n) bcmac_df(rh, rl, ih, il, CSW[r + nx + 1], X(r + nx + 1));
+    o.rh = rh;
+    o.rl = rl;
+    o.ih = ih;
+    o.il = il;
+    yd[r] = o;
   }
 }
 
@@ -231,7 +261,7 @@ __global__ void __launch_bounds__(kBT)
   dfl wr[kRows], wi[kRows];
 #pragma unroll
   for (int s = 0; s < kRows; ++s) {
-    const dfc b = split_c(w[r0 + s * kBT]);
+    const dfc b = reinterpret_cast<const dfc*>(w)[r0 + s * kBT];   // w in double-float form
     wr[s] = dfl_of(b.rh, b.rl);
     wi[s] = dfl_of(b.ih, b.il);
   }
@@ -324,11 +354,12 @@ __global__ void __launch_bounds__(kBT)
   for (int c = threadIdx.x; c < ncols; c += kBT) hsd[c] = split_c(mk(-col[c].re, -col[c].im));
   __syncthreads();
   const long long r0 = (long long)t * kBatchTile + threadIdx.x;
-  double nrm = 0.0;
+  dfc* wd = reinterpret_cast<dfc*>(w);   // w in double-float form
+  float nh = 0.f, nl = 0.f;               // this thread's sum of |w|^2, double-float
 #pragma unroll 1
   for (int s = 0; s < kRows; ++s) {
     const long long r = r0 + s * kBT;
-    const dfc w0 = split_c(w[r]);
+    const dfc w0 = wd[r];
     float rh = w0.rh, rl = w0.rl, ih = w0.ih, il = w0.il;
     for (int c0 = 0; c0 < ncols; c0 += 2 * kBCols) {
       c64 a[2 * kBCols];
@@ -352,12 +383,35 @@ __global__ void __launch_bounds__(kBT)
         df_acc(ih, il, p, e);
       }
     }
-    const c128 v = mk(df_to_d(rh, rl), df_to_d(ih, il));
-    w[r] = v;
-    nrm = fma(v.re, v.re, fma(v.im, v.im, nrm));
+    dfc o;
+    o.rh = rh;
+    o.rl = rl;
+    o.ih = ih;
+    o.il = il;
+    wd[r] = o;
+    // |w|^2 = rh^2 + 2 rh rl + ih^2 + 2 ih il (+ terms below 2^-46 relative)
+    float p = rh * rh;
+    float e = fmaf(rh, rh, -p) + 2.f * rh * rl;
+    df_acc(nh, nl, p, e);
+    p = ih * ih;
+    e = fmaf(ih, ih, -p) + 2.f * ih * il;
+    df_acc(nh, nl, p, e);
   }
-  const double s = block_sumd(nrm);
-  if (threadIdx.x == 0) pnorm[t] = s;
+  // block sum in double-float, one conversion
+  __shared__ float2 red[kBT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float a2 = __shfl_xor_sync(0xffffffffu, nh, o), b2 = __shfl_xor_sync(0xffffffffu, nl, o);
+    df_acc(nh, nl, a2, b2);
+  }
+  if (lane == 0) red[wid] = make_float2(nh, nl);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = red[0].x, b = red[0].y;
+    for (int u = 1; u < kBT / 32; ++u) df_acc(a, b, red[u].x, red[u].y);
+    pnorm[t] = df_to_d(a, b);
+  }
 }
 
 // Step j, one warp per problem: h_{j+1,j} = ||w|| from the tile partials,
@@ -430,8 +484,10 @@ __global__ void k_bnorm_givens(const int* __restrict__ tile0, const int* __restr
   }
 }
 
-// v_{j+1} = fl32(w / h_{j+1,j}) for problems whose cycle continues; with
-// jptr == nullptr, v_0 = fl32(w / beta) at a cycle start (beta in hnorm).
+// v_{j+1} = fl32(w / h_{j+1,j}) for problems whose cycle continues, w in
+// double-float form, 1/h as a double-float pair from an FP32 reciprocal and
+// one Newton step (FP32 pipe only); with jptr == nullptr, v_0 = fl32(w / beta)
+// at a cycle start (w complex128, beta in hnorm, FP64).
 __global__ void __launch_bounds__(kBT)
     k_bscale_df(const int* __restrict__ tile_prob, const c128* __restrict__ w, c64* __restrict__ V, long long ldv,
                 const int* __restrict__ jptr, const KState* __restrict__ kst) {
@@ -440,13 +496,35 @@ __global__ void __launch_bounds__(kBT)
   if (kst[q].stop) return;
   const double d = kst[q].hnorm;
   if (!(d > 0.0)) return;
-  const double sc = 1.0 / d;
   c64* v = V + (jptr ? (long long)(*jptr + 1) * ldv : 0);
+  const dfl dd = split_d(d);
+  const float s0 = 1.f / dd.hi;
+  if (jptr == nullptr || !(dd.hi > 0.f) || !(s0 < 3e38f)) {
+    const double sc = 1.0 / d;
+#pragma unroll 2
+    for (int s = 0; s < kRows; ++s) {
+      const long long r = (long long)t * kBatchTile + s * kBT + threadIdx.x;
+      if (jptr == nullptr) {
+        const c128 x = w[r];
+        v[r] = mk((float)(sc * x.re), (float)(sc * x.im));
+      } else {
+        const dfc x = reinterpret_cast<const dfc*>(w)[r];
+        v[r] = mk((float)(sc * ((double)x.rh + (double)x.rl)), (float)(sc * ((double)x.ih + (double)x.il)));
+      }
+    }
+    return;
+  }
+  const float r0 = fmaf(-dd.hi, s0, 1.f) - dd.lo * s0;
+  const float sh = s0, sl = s0 * r0;
 #pragma unroll 2
   for (int s = 0; s < kRows; ++s) {
     const long long r = (long long)t * kBatchTile + s * kBT + threadIdx.x;
-    const c128 x = w[r];
-    v[r] = mk((float)(sc * x.re), (float)(sc * x.im));
+    const dfc x = reinterpret_cast<const dfc*>(w)[r];
+    float p = x.rh * sh;
+    const float vr = p + (fmaf(x.rh, sh, -p) + fmaf(x.rh, sl, x.rl * sh));
+    p = x.ih * sh;
+    const float vi = p + (fmaf(x.ih, sh, -p) + fmaf(x.ih, sl, x.il * sh));
+    v[r] = mk(vr, vi);
   }
 }
 
@@ -512,17 +590,50 @@ __global__ void k_bbacksolve(const c128* __restrict__ H, int ldh, long long hstr
   }
 }
 
-// x += sum_{c < jdone_q} Z_c y_q[c] (FP64) for problems still being solved.
+// x += sum_{c < jdone_q} Z_c y_q[c] for problems still being solved: in
+// FP64 for complex128 columns of Z, in double-float on the FP32 pipe (y split
+// once per column, x once per row) when Z holds double-float pairs (zdf).
 __global__ void __launch_bounds__(kBT)
     k_bupdate(const int* __restrict__ tile_prob, const c128* __restrict__ Z, long long ldz,
-              const c128* __restrict__ y, int m, const KState* __restrict__ kst, c128* __restrict__ x) {
+              const c128* __restrict__ y, int m, const KState* __restrict__ kst, c128* __restrict__ x, int zdf) {
   extern __shared__ c128 ys[];
   const int t = blockIdx.x;
   const int q = tile_prob[t];
   if (!kst[q].live) return;
   const int nj = kst[q].jdone;
-  for (int c = threadIdx.x; c < nj; c += kBT) ys[c] = y[(long long)q * m + c];
+  for (int c = threadIdx.x; c < nj; c += kBT) {
+    const c128 yc = y[(long long)q * m + c];
+    if (zdf) reinterpret_cast<dfc*>(ys)[c] = split_c(yc);
+    else ys[c] = yc;
+  }
   __syncthreads();
+  if (zdf) {
+    const dfc* Zd = reinterpret_cast<const dfc*>(Z);
+    const dfc* yd = reinterpret_cast<const dfc*>(ys);
+#pragma unroll 1
+    for (int s = 0; s < kRows; ++s) {
+      const long long r = (long long)t * kBatchTile + s * kBT + threadIdx.x;
+      const dfc x0 = split_c(x[r]);
+      float rh = x0.rh, rl = x0.rl, ih = x0.ih, il = x0.il;
+      for (int c = 0; c < nj; ++c) {
+        const dfc a = Zd[(long long)c * ldz + r], h = yd[c];
+        const dfl ar = dfl_of(a.rh, a.rl), ai = dfl_of(a.ih, a.il);
+        const dfl hr = dfl_of(h.rh, h.rl), hi_ = dfl_of(h.ih, h.il);
+        float p, e;
+        // a h = (ar hr - ai hi) + i (ar hi + ai hr)
+        df_prod(ar, hr, p, e);
+        df_acc(rh, rl, p, e);
+        df_prod(ai, hi_, p, e);
+        df_acc(rh, rl, -p, -e);
+        df_prod(ar, hi_, p, e);
+        df_acc(ih, il, p, e);
+        df_prod(ai, hr, p, e);
+        df_acc(ih, il, p, e);
+      }
+      x[r] = mk(df_to_d(rh, rl), df_to_d(ih, il));
+    }
+    return;
+  }
 #pragma unroll 1
   for (int s = 0; s < kRows; ++s) {
     const long long r = (long long)t * kBatchTile + s * kBT + threadIdx.x;
@@ -541,13 +652,13 @@ __global__ void __launch_bounds__(kBT)
 
 cudaError_t launch_bprolong(int prec, int ntiles, const int* tile_prob, const Geo* geos, const SubDesc* subs,
                             const int* sub_index, const void* Y, c128* z, long long ldz, const int* jptr,
-                            const KState* kst, int gate, cudaStream_t st) {
+                            const KState* kst, int gate, cudaStream_t st, int zdf) {
   if (prec == 0)
     k_bprolong<double><<<ntiles, kBT, 0, st>>>(tile_prob, geos, subs, sub_index, (const c128*)Y, z, ldz, jptr, kst,
-                                               gate);
+                                               gate, 0);
   else
     k_bprolong<float><<<ntiles, kBT, 0, st>>>(tile_prob, geos, subs, sub_index, (const c64*)Y, z, ldz, jptr, kst,
-                                              gate);
+                                              gate, zdf);
   return cudaGetLastError();
 }
 
@@ -574,10 +685,13 @@ cudaError_t launch_bstep(const BStep& a, cudaStream_t st) {
   e = launch_local_solves(a.prec, a.cols, a.geos, a.subs, a.nsub, a.max_b, a.max_bp, a.L, a.Lrev, a.dinv,
                           (const c128*)a.V, a.ld, jp, a.Y, a.kst, a.status, st, RK_C64);
   if (e != cudaSuccess) return e;
-  e = launch_bprolong(a.prec, a.ntiles, a.tile_prob, a.geos, a.subs, a.sub_index, a.Y, a.Z, a.ld, jp, a.kst, 1, st);
+  // z_j in double-float form with complex64 local values; w always in that form
+  const int zdf = a.prec >= 1 ? 1 : 0;
+  e = launch_bprolong(a.prec, a.ntiles, a.tile_prob, a.geos, a.subs, a.sub_index, a.Y, a.Z, a.ld, jp, a.kst, 1, st,
+                      zdf);
   if (e != cudaSuccess) return e;
   k_bspmv_df<<<a.ntiles, kBT, 0, st>>>(a.tile_prob, a.geos, (const dfc*)a.Ddf, (const dfc*)a.CWdf,
-                                       (const dfc*)a.CSdf, (const dfc*)a.CSWdf, a.Z, a.ld, jp, a.w, a.kst);
+                                       (const dfc*)a.CSdf, (const dfc*)a.CSWdf, a.Z, a.ld, jp, a.w, zdf, a.kst);
   k_bdots_df<<<a.ntiles, kBT, dsm, st>>>(a.tile_prob, (const c64*)a.V, a.ld, a.w, jp, a.partial, a.ntiles, a.kst);
   k_bdots_finish<<<a.nprob, kBT, 0, st>>>(a.tile0, a.tile1, a.partial, a.ntiles, jp, a.H, a.m + 1, a.hstride,
                                           a.kst);
@@ -606,7 +720,7 @@ cudaError_t launch_bcycle_end(const BStep& a, c128* x, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_bupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysm);
     if (e != cudaSuccess) return e;
   }
-  k_bupdate<<<a.ntiles, kBT, ysm, st>>>(a.tile_prob, a.Z, a.ld, a.yv, a.m, a.kst, x);
+  k_bupdate<<<a.ntiles, kBT, ysm, st>>>(a.tile_prob, a.Z, a.ld, a.yv, a.m, a.kst, x, a.prec >= 1 ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -194,9 +194,10 @@ struct BStep {
   DevStatus* status;
 };
 
+// with zdf (complex64 Y only) z is written in double-float form (dfc)
 cudaError_t launch_bprolong(int prec, int ntiles, const int* tile_prob, const Geo* geos, const SubDesc* subs,
                             const int* sub_index, const void* Y, c128* z, long long ldz, const int* jptr,
-                            const KState* kst, int gate, cudaStream_t st);
+                            const KState* kst, int gate, cudaStream_t st, int zdf = 0);
 cudaError_t launch_bspmv(int ntiles, const int* tile_prob, const Geo* geos, const c128* D, const c128* CW,
                          const c128* CS, const c128* CSW, const c128* x, long long ldx, const int* jptr,
                          const c128* bsub, c128* y, double* pnorm, const KState* kst, int gate, cudaStream_t st);
