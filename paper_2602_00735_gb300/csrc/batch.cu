@@ -429,21 +429,18 @@ __global__ void k_bnorm_givens(const int* __restrict__ tile0, const int* __restr
   const int j = *jptr;
   double s = 0.0;
   for (int u = tile0[q] + threadIdx.x; u < tile1[q]; u += 32) s += pnorm[u];
-  s = warp_sumd(s);
-  if (threadIdx.x != 0) return;
+  s = warp_sumd(s);   // in every lane
   const double hn = sqrt(s);
-  k.hnorm = hn;
   c128* col = H + q * hstride + (long long)j * ldh;
-  col[j + 1] = mk(hn, 0.0);
   double* csq = cs + (long long)q * m;
   c128* snq = sn + (long long)q * m;
   c128* gq = gvec + (long long)q * (m + 1);
-  for (int i = 0; i < j; ++i) {
-    const c128 a = col[i], b = col[i + 1];
-    const c128 tt = csq[i] * a + snq[i] * b;
-    col[i + 1] = csq[i] * b - conj(snq[i]) * a;
-    col[i] = tt;
-  }
+  // the previous rotations on column j (one warp), then lane 0 continues
+  const c128 cj = givens_prev_warp(col, csq, snq, j, threadIdx.x);
+  if (threadIdx.x != 0) return;
+  k.hnorm = hn;
+  col[j] = cj;
+  col[j + 1] = mk(hn, 0.0);
   const c128 a = col[j], b = col[j + 1];
   const double aa = sqrt(abs2(a)), bb = sqrt(abs2(b));
   double c;

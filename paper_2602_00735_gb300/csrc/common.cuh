@@ -291,6 +291,59 @@ __device__ __forceinline__ dfl dfl_of(float hi, float lo) {
   return r;
 }
 
+
+// Complex Givens rotations (Section 4.1's least-squares update): applies the
+// previous rotations i = 0..j-1 (cosine cs[i], sine sn[i]) to column j of the
+// Hessenberg matrix, one warp, all lanes calling. The sweep is the recurrence
+// carry_0 = col[0]; col'[i] = c_i carry_i + s_i col[i+1], carry_{i+1} =
+// -conj(s_i) carry_i + c_i col[i+1]; each lane takes a chunk of consecutive
+// i, composes its chunk's affine maps carry -> A carry + B, a warp scan
+// composes the chunks (log2(32) + 2 j/32 dependent steps instead of j), and
+// each lane replays its chunk from its incoming carry, writing col'[0..j-1].
+// Returns carry_j (the new col[j]) in every lane; col[j] is not written.
+__device__ __forceinline__ c128 shfl_c128(c128 v, int src) {
+  return {__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
+}
+__device__ __forceinline__ c128 shfl_up_c128(c128 v, int d) {
+  return {__shfl_up_sync(0xffffffffu, v.re, d), __shfl_up_sync(0xffffffffu, v.im, d)};
+}
+__device__ __forceinline__ c128 givens_prev_warp(c128* col, const double* cs, const c128* sn, int j, int lane) {
+  const int K = (j + 31) / 32;
+  const int i0 = min(lane * K, j), i1 = min(i0 + K, j);
+  const c128 one = {1.0, 0.0}, zero = {0.0, 0.0};
+  c128 A = one, B = zero;
+  for (int i = i0; i < i1; ++i) {
+    const c128 ai = {-sn[i].re, sn[i].im};   // -conj(s_i)
+    const c128 bi = cs[i] * col[i + 1];
+    A = ai * A;
+    B = ai * B + bi;
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const c128 Ap = shfl_up_c128(A, d), Bp = shfl_up_c128(B, d);
+    if (lane >= d) {
+      B = A * Bp + B;
+      A = A * Ap;
+    }
+  }
+  const c128 c0 = col[0];
+  const c128 Ae = shfl_up_c128(A, 1), Be = shfl_up_c128(B, 1);
+  c128 carry = lane == 0 ? c0 : Ae * c0 + Be;
+  // col[i1] is the next lane's first output: read it before any lane writes
+  const c128 bnd = i1 > i0 ? col[i1] : zero;
+  __syncwarp();
+  for (int i = i0; i < i1; ++i) {
+    const c128 b = i + 1 == i1 ? bnd : col[i + 1];
+    const c128 t = cs[i] * carry + sn[i] * b;
+    carry = cs[i] * b - conj(sn[i]) * carry;
+    col[i] = t;
+  }
+  const int last = j > 0 ? (j - 1) / K : 0;
+  const c128 cj = shfl_c128(carry, last);
+  __syncwarp();
+  return cj;
+}
+
 // Device status words shared by the kernels of one handle.
 struct DevStatus {
   int pivot_bad_sub;    // first subdomain with a zero / non-finite pivot, else -1

@@ -619,67 +619,16 @@ __global__ void k_cycle_init(KState* kst, c128* gvec, int m, double rtol, double
 
 // Givens step j of the cycle (one thread): rotate the new Hessenberg column,
 // build the new rotation, update g and the residual estimate, decide stop.
-// shuffle of a complex128 value
-__device__ __forceinline__ c128 shfl_c(c128 v, int src) {
-  return mk(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
-}
-__device__ __forceinline__ c128 shfl_up_c(c128 v, int d) {
-  return mk(__shfl_up_sync(0xffffffffu, v.re, d), __shfl_up_sync(0xffffffffu, v.im, d));
-}
-
-// One warp. The previous rotations i = 0..j-1 act on column j of H as the
-// recurrence carry_0 = H(0, j); H'(i, j) = c_i carry_i + s_i H(i+1, j),
-// carry_{i+1} = -conj(s_i) carry_i + c_i H(i+1, j), and carry_j is the new
-// H(j, j). Each lane takes a chunk of consecutive i: it composes its chunk's
-// affine maps carry -> A carry + B, a warp scan composes the chunks (so the
-// j sequential steps become log2(32) + 2 j/32), and each lane then replays
-// its chunk from its incoming carry. Lane 0 forms the new rotation.
+// One warp applies the previous rotations to column j of H (givens_prev_warp)
+// and lane 0 forms the new rotation.
 __global__ void k_givens(KState* kst, c128* H, int ldh, double* cs, c128* sn, c128* gvec, int j, double rtol,
                          int mcycle, int maxit, double* hist, double cfloor) {
   if (kst->stop) return;
   const int lane = threadIdx.x;
   c128* col = H + (long long)j * ldh;
-  const int K = (j + 31) / 32;
-  const int i0 = min(lane * K, j), i1 = min(i0 + K, j);
-  const c128 one = mk(1.0, 0.0), zero = mk(0.0, 0.0);
-  // this chunk's composed map
-  c128 A = one, B = zero;
-  for (int i = i0; i < i1; ++i) {
-    const c128 ai = mk(-sn[i].re, sn[i].im);   // -conj(s_i)
-    const c128 bi = cs[i] * col[i + 1];
-    A = ai * A;
-    B = ai * B + bi;
-  }
-  // inclusive scan of the maps over the lanes (later lanes applied after)
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const c128 Ap = shfl_up_c(A, d), Bp = shfl_up_c(B, d);
-    if (lane >= d) {
-      B = A * Bp + B;
-      A = A * Ap;
-    }
-  }
-  // the carry entering this lane's chunk: the previous lane's composed map
-  // applied to carry_0 = H(0, j)
-  const c128 c0 = col[0];
-  const c128 Ae = shfl_up_c(A, 1), Be = shfl_up_c(B, 1);
-  c128 carry = lane == 0 ? c0 : Ae * c0 + Be;
-  // H(i1, j) is the next lane's first output: read it before any lane writes
-  const c128 bnd = i1 > i0 ? col[i1] : zero;
-  __syncwarp();
-  for (int i = i0; i < i1; ++i) {
-    const c128 b = i + 1 == i1 ? bnd : col[i + 1];
-    const c128 t = cs[i] * carry + sn[i] * b;
-    carry = cs[i] * b - conj(sn[i]) * carry;
-    col[i] = t;
-  }
-  // carry_j: the lane whose chunk ends at j (a lane with an empty chunk
-  // passes the carry it received)
-  const int last = j > 0 ? (j - 1) / K : 0;
-  const c128 cj = shfl_c(carry, last);
-  __syncwarp();
+  const c128 cj = givens_prev_warp(col, cs, sn, j, lane);
   if (lane != 0) return;
-  if (j > 0) col[j] = cj;
+  col[j] = cj;
   c128 a = col[j], b = col[j + 1];
   double aa = sqrt(abs2(a)), bb = sqrt(abs2(b));
   double c;
