@@ -395,13 +395,15 @@ __global__ void __launch_bounds__(NT)
 //      k+NB+b, is the product P Q^T of P = (c_ij) and Q = (l_cj), both
 //      b x NB. It runs as tcgen05.mma kind::tf32 (M = 128 rows, N = b
 //      rounded up to 16, FP32 accumulators in TMEM): complex products as
-//      real ones (Re = Pr Qr^T - Pi Qi^T, Im = Pr Qi^T + Pi Qr^T) and every
+//      real ones (Re = Pr Qr^T - Pi Qi^T through the instruction
+//      descriptor's negate-A bit, Im = Pr Qi^T + Pi Qr^T) and every
 //      FP32 operand as a TF32 head plus tail (x = xh + xl, xh = x with the 13
 //      low mantissa bits cleared, exact in TF32), of which the three products
 //      xh yh + xh yl + xl yh are kept: about 2^-21 relative rounding per
 //      product, next to FP32's 2^-24;
-//   4. while the MMAs run, the NB rows entering the window (read from global
-//      memory during step 2) fill the slots of rows k..k+NB-1;
+//   4. while one thread issues the MMAs, warps 1-3 write the NB rows entering
+//      the window (read from global memory a panel ahead) into the slots of
+//      rows k..k+NB-1;
 //   5. each warp reads its 32 accumulator rows back (tcgen05.ld) and
 //      subtracts them from the ring; warp 0 then factors the next diagonal
 //      block (its rows are the first NB of this trailing block), while the
