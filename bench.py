@@ -80,19 +80,22 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def traffic_from_profile(kernel_src: str):
-    """DRAM bytes per launch of k_apply from the committed ncu summary, or None
-    when the summary is missing or was taken on a different apply.cu."""
+def traffic_from_profile(kernel_src: str, algorithmic_bytes: float):
+    """DRAM bytes per launch of k_apply for a launch of `algorithmic_bytes`,
+    from the committed ncu summary (its measured ratio of DRAM traffic to
+    algorithmic bytes: every factor entry is read once per sweep, so traffic
+    grows in proportion), or None when the summary is missing or was taken
+    on a different apply.cu."""
     path = os.path.join(ROOT, "profiles", "k_apply_sweep_c1.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m_h = re.search(r"apply\.cu sha256: ([0-9a-f]{16})", txt)
-    m_t = re.search(r"dram bytes per full c2 launch: ([0-9.eE+]+)", txt)
-    if not m_h or not m_t:
+    m_r = re.search(r"traffic / algorithmic = ([0-9.]+)", txt)
+    if not m_h or not m_r:
         return None
     cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-    return float(m_t.group(1)) if cur == m_h.group(1) else None
+    return float(f"{float(m_r.group(1)) * algorithmic_bytes:.4g}") if cur == m_h.group(1) else None
 
 
 class ClockSampler:
@@ -436,7 +439,8 @@ def run_ours(args, rank, world, local_rank):
     avg_apply_s = apply_ms / max(1, applies) / 1e3
     achieved = info["apply_bytes"] / avg_apply_s / 1e9
     peak, peak_kind = peaks()
-    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2602_00735_gb300", "csrc", "apply.cu"))
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2602_00735_gb300", "csrc", "apply.cu"),
+                                   info["apply_bytes"])
     launches_per_step = [q["launches"] + 4 for q in per_c64]   # + setup stencil, rhs, local rows, factor
     out = {
         "metric": METRIC, "value": round(mean_t, 4), "unit": "s", "n_gpus": world, "steps": args.steps,
