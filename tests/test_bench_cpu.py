@@ -73,3 +73,22 @@ def test_max_over_ranks_with_two_gloo_ranks():
     assert all(p.exitcode == 0 for p in procs)
     got = dict(q.get(timeout=5) for _ in range(2))
     assert got == {0: 2.5, 1: 2.5}
+
+
+def test_apply_traffic_scales_with_the_workload(tmp_path):
+    """The roofline's traffic figure comes from the committed ncu summary of
+    k_apply: its captured DRAM-to-algorithmic ratio times the workload's own
+    algorithmic bytes, and None once apply.cu differs from the captured one."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    src = os.path.join(ROOT, "paper_2602_00735_gb300", "csrc", "apply.cu")
+    a = bench.traffic_from_profile(src, 1.0e9)
+    b = bench.traffic_from_profile(src, 4.0e9)
+    assert a is not None and b is not None
+    assert 1.0 <= a / 1.0e9 <= 1.2                  # a little above the algorithmic bytes
+    assert abs(b / a - 4.0) < 1e-3                   # in proportion to the work
+    other = tmp_path / "apply.cu"
+    other.write_text(open(src).read() + "\n// changed\n")
+    assert bench.traffic_from_profile(str(other), 1.0e9) is None
