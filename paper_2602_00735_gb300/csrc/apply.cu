@@ -249,13 +249,8 @@ __global__ void k_prolong(Geo g, const SubDesc* __restrict__ subs, const cx<R>* 
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= g.nx * g.ny) return;
   const int j = r / g.nx + 1, i = r - (j - 1) * g.nx + 1;
-  const int o = g.ovlp;
-  int bx = box_of_node(i, g.Mx, g.px), by = box_of_node(j, g.My, g.py);
-  int qx0 = bx, qx1 = bx, qy0 = by, qy1 = by;
-  if (bx > 0 && i < box_start(bx, g.Mx, g.px) + o) qx0 = bx - 1;
-  if (bx + 1 < g.px && i > box_start(bx + 1, g.Mx, g.px) - o) qx1 = bx + 1;
-  if (by > 0 && j < box_start(by, g.My, g.py) + o) qy0 = by - 1;
-  if (by + 1 < g.py && j > box_start(by + 1, g.My, g.py) - o) qy1 = by + 1;
+  const int2 cxr = cover_range(boxes_of(g.Mx, g.px), i, g.ovlp), cyr = cover_range(boxes_of(g.My, g.py), j, g.ovlp);
+  const int qx0 = cxr.x, qx1 = cxr.y, qy0 = cyr.x, qy1 = cyr.y;
   if constexpr (sizeof(R) == sizeof(float)) {
     if (out_df) {
       float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;

@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(kBT)
   const int nx = g.nx, n = g.n, o = g.ovlp, Mx = g.Mx, My = g.My, px = g.px, py = g.py, sub0 = g.sub0;
   const long long goff = g.goff;
   c128* z = zbase + (jptr ? (long long)(*jptr) * ldz : 0);
+  const Boxes bxs = boxes_of(Mx, px), bys = boxes_of(My, py);
 #pragma unroll 1
   for (int s = 0; s < kRows; ++s) {
     const long long r = (long long)t * kBatchTile + s * kBT + threadIdx.x;
@@ -83,12 +84,8 @@ __global__ void __launch_bounds__(kBT)
       continue;
     }
     const int j = lr / nx + 1, i = lr - (j - 1) * nx + 1;
-    const int bx = box_of_node(i, Mx, px), by = box_of_node(j, My, py);
-    int qx0 = bx, qx1 = bx, qy0 = by, qy1 = by;
-    if (bx > 0 && i < box_start(bx, Mx, px) + o) qx0 = bx - 1;
-    if (bx + 1 < px && i > box_start(bx + 1, Mx, px) - o) qx1 = bx + 1;
-    if (by > 0 && j < box_start(by, My, py) + o) qy0 = by - 1;
-    if (by + 1 < py && j > box_start(by + 1, My, py) - o) qy1 = by + 1;
+    const int2 cxr = cover_range(bxs, i, o), cyr = cover_range(bys, j, o);
+    const int qx0 = cxr.x, qx1 = cxr.y, qy0 = cyr.x, qy1 = cyr.y;
     if constexpr (sizeof(R) == sizeof(float)) {
       if (zdf) {
         // complex64 local values summed in double-float into the dfc form

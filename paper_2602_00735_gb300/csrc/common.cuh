@@ -208,6 +208,30 @@ __host__ __device__ __forceinline__ int box_start(int p, int M, int P) {
   return p * base + (p < extra ? p : extra);
 }
 
+// The same box arithmetic with the divisions by P done once (per thread,
+// not per query): cover_range gives the boxes whose subdomains hold node i,
+// its own box and the neighbours whose overlap of o cells reaches it.
+struct Boxes {
+  int base, extra, split, P;
+};
+__device__ __forceinline__ Boxes boxes_of(int M, int P) {
+  Boxes b;
+  b.base = M / P;
+  b.extra = M % P;
+  b.split = b.extra * (b.base + 1);
+  b.P = P;
+  return b;
+}
+__device__ __forceinline__ int box_first(const Boxes& b, int p) { return p * b.base + (p < b.extra ? p : b.extra); }
+__device__ __forceinline__ int2 cover_range(const Boxes& b, int i, int o) {
+  int p = (i < b.split) ? i / (b.base + 1) : b.extra + (i - b.split) / b.base;
+  p = p < b.P ? p : b.P - 1;
+  int q0 = p, q1 = p;
+  if (p > 0 && i < box_first(b, p) + o) q0 = p - 1;
+  if (p + 1 < b.P && i > box_first(b, p + 1) - o) q1 = p + 1;
+  return make_int2(q0, q1);
+}
+
 // ---------------------------------------------------------------------------
 // Double-float numbers: a double x held as floats hi + lo, split with integer
 // operations and one exact float subtraction. hi keeps the sign, exponent and
