@@ -12,7 +12,8 @@ Contents, each following the paper (Xie, Gong, Graham, Spence, Zhang,
 equation"):
 
   fem.py     Section 1: PML stretching, the truncated weak form on P1
-             triangles, global matrix and load vector, direct solve.
+             triangles (the complex-symmetric gamma_1 gamma_2 form, or
+             eq. weak as printed), global matrix and load vector, direct solve.
   ras.py     Section 2 and Section 3 (ii): Cartesian covering, local PML
              stretching, local operators A_j with impedance closure,
              partition of unity chi_j, and the preconditioner

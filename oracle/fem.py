@@ -8,12 +8,17 @@ Cartesian PML of Section 1: gamma_i = 1 + i g_i'(x^i), where g_i is the
 stretching g shifted to the side of Omega_int that x^i lies beyond and zero
 inside Omega_int, and u = 0 on the outer boundary (u in H^1_0(Omega)).
 
-The weak form used is the paper's eq. (weak) multiplied through by
+The default weak form (form 0) is the paper's eq. (weak) multiplied through by
 gamma_1 gamma_2, which turns it into a complex-symmetric bilinear form with the
 same solution (gamma = 1 in Omega_int, where f lives):
 
     a(u, v) = int (gamma_2/gamma_1) u_x v_x + (gamma_1/gamma_2) u_y v_y
               - k^2 gamma_1 gamma_2 u v,          F(v) = int f v.
+
+Form 1 is eq. (weak) as printed, int (D grad u).grad v - (beta.grad u) v
+- k^2 u v with D_ii = gamma_i^-2 and beta_i = gamma_i'/gamma_i^3 (not
+symmetric); at the continuous level it is form 0 tested with v/(gamma_1
+gamma_2), so both discretise the same problem.
 
 Discretisation: uniform cells of size h, each split along its
 (i,j)-(i+1,j+1) diagonal into two right triangles; P1 elements; every element
@@ -52,6 +57,19 @@ def gprime(d, amp: float, ramp: float, profile: int = 0):
         return np.where(d > 0.0, 3.0 * amp * d * d, 0.0)
     t = np.clip(d / ramp, 0.0, 1.0)
     return np.where(d > 0.0, amp * (3.0 * t * t - 2.0 * t ** 3), 0.0)
+
+
+def gsecond(d, amp: float, ramp: float, profile: int = 0):
+    """Second derivative g''(d) of the same stretching (enters beta of eq. weak).
+
+    profile 0: amp*6t(1-t)/ramp for 0 < d < ramp, 0 beyond; profile 1: 6 amp d.
+    Both are 0 for d <= 0 and continuous.
+    """
+    d = np.asarray(d, dtype=np.float64)
+    if profile == 1:
+        return np.where(d > 0.0, 6.0 * amp * d, 0.0)
+    t = np.clip(d / ramp, 0.0, 1.0)
+    return np.where(d > 0.0, amp * 6.0 * t * (1.0 - t) / ramp, 0.0)
 
 
 def g_integral(d, amp: float, ramp: float):
@@ -126,6 +144,21 @@ def global_gamma_y(grid: Grid, s, amp, ramp, profile: int = 0):
     return 1.0 + 1j * gprime(d, amp, ramp, profile)
 
 
+def _dgamma(c, lo, hi, amp, ramp, profile):
+    """gamma_i' = i g_i'' at coordinate c: g_i(c) = g(c - hi) beyond hi, -g(lo - c)
+    below lo (Section 1), so g_i'' = g''(c - hi) there and -g''(lo - c) below."""
+    return 1j * (gsecond(c - hi, amp, ramp, profile) - gsecond(lo - c, amp, ramp, profile))
+
+
+def global_dgamma_x(grid: Grid, s, amp, ramp, profile: int = 0):
+    """gamma_1'(x) = i g_1''(x) of the global PML at half-index s."""
+    return _dgamma(grid.xs(s), grid.x0, grid.x1, amp, ramp, profile)
+
+
+def global_dgamma_y(grid: Grid, s, amp, ramp, profile: int = 0):
+    return _dgamma(grid.ys(s), grid.y0, grid.y1, amp, ramp, profile)
+
+
 # ----------------------------------------------------------------------------
 # Element assembly
 # ----------------------------------------------------------------------------
@@ -184,6 +217,46 @@ def assemble_cells(grid: Grid, ci, cj, gx_fn, gy_fn, k: float):
     return (np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
 
 
+def assemble_cells_weak(grid: Grid, ci, cj, gx_fn, gy_fn, dgx_fn, dgy_fn, k: float):
+    """Element contributions of the paper's eq. weak itself over cells (ci, cj).
+
+        a(u, v) = int (D grad u) . grad v - (beta . grad u) v - k^2 u v,
+        D = diag(gamma_1^-2, gamma_2^-2), beta_i = gamma_i' / gamma_i^3,
+
+    which is not symmetric (the beta term). Row a is the test function phi_a,
+    column b the trial function phi_b; on triangle T
+        int_T D11 dxphi_b dxphi_a + D22 dyphi_b dyphi_a
+              - (beta_1 dxphi_b + beta_2 dyphi_b) phi_a - k^2 phi_b phi_a,
+    every integral by the edge-midpoint rule (weight h^2/6 per midpoint).
+    dgx_fn(s), dgy_fn(s): gamma_1' and gamma_2' at half-index positions.
+    """
+    ci = np.asarray(ci).ravel()
+    cj = np.asarray(cj).ravel()
+    h = grid.h
+    rows, cols, vals = [], [], []
+    for tri in _TRI:
+        sx = [2 * ci + m[0][0] for m in tri["mids"]]
+        sy = [2 * cj + m[0][1] for m in tri["mids"]]
+        g1 = [gx_fn(s) for s in sx]
+        g2 = [gy_fn(s) for s in sy]
+        b1 = [dgx_fn(s) / g ** 3 for s, g in zip(sx, g1)]
+        b2 = [dgy_fn(s) / g ** 3 for s, g in zip(sy, g2)]
+        dx = sum(1.0 / (g1[m] * g1[m]) for m in range(3)) / 6.0   # (1/h^2) int_T D11
+        dy = sum(1.0 / (g2[m] * g2[m]) for m in range(3)) / 6.0
+        nodes = [(cj + dj) * (grid.Mx + 1) + (ci + di) for (di, dj) in tri["verts"]]
+        for a in range(3):
+            for b in range(3):
+                ga, gb = tri["grads"][a], tri["grads"][b]
+                stiff = dx * (gb[0] * ga[0]) + dy * (gb[1] * ga[1])
+                adv = sum((b1[m] * gb[0] + b2[m] * gb[1]) * tri["mids"][m][1][a]
+                          for m in range(3)) * (h / 6.0)
+                mass = sum(tri["mids"][m][1][a] * tri["mids"][m][1][b] for m in range(3)) * (h * h / 6.0)
+                rows.append(nodes[a])
+                cols.append(nodes[b])
+                vals.append(stiff - adv - k * k * mass)
+    return (np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
 def load_cells(grid: Grid, ci, cj, f_fn):
     """Load contributions int_T f phi_a over cells, by the same edge-midpoint rule."""
     ci = np.asarray(ci).ravel()
@@ -216,10 +289,13 @@ def _to_matrix(rows, cols, vals, numbering, n):
     return A
 
 
-def assemble_global(p: dict, gx_fn=None, gy_fn=None):
+def assemble_global(p: dict, gx_fn=None, gy_fn=None, dgx_fn=None, dgy_fn=None):
     """Global matrix A of a(.,.) on V_h subset H^1_0(Omega) (Section 1, eq. weak).
 
-    gx_fn/gy_fn override the stretching (tests); default: the global PML.
+    p["form"] (default 0) selects the bilinear form: 0 the gamma_1 gamma_2
+    multiplied, complex-symmetric one; 1 eq. weak as printed (not symmetric).
+    gx_fn/gy_fn (and dgx_fn/dgy_fn, the derivatives, for form 1) override the
+    stretching (tests); default: the global PML.
     Returns (grid, A) with A a CSR complex128 matrix of size n x n.
     """
     grid = make_grid(p)
@@ -228,8 +304,15 @@ def assemble_global(p: dict, gx_fn=None, gy_fn=None):
         gx_fn = lambda s: global_gamma_x(grid, s, amp, ramp, prof)  # noqa: E731
     if gy_fn is None:
         gy_fn = lambda s: global_gamma_y(grid, s, amp, ramp, prof)  # noqa: E731
+    if dgx_fn is None:
+        dgx_fn = lambda s: global_dgamma_x(grid, s, amp, ramp, prof)  # noqa: E731
+    if dgy_fn is None:
+        dgy_fn = lambda s: global_dgamma_y(grid, s, amp, ramp, prof)  # noqa: E731
     cj, ci = np.meshgrid(np.arange(grid.My), np.arange(grid.Mx), indexing="ij")
-    r, c, v = assemble_cells(grid, ci, cj, gx_fn, gy_fn, p["k"])
+    if p.get("form", 0) == 1:
+        r, c, v = assemble_cells_weak(grid, ci, cj, gx_fn, gy_fn, dgx_fn, dgy_fn, p["k"])
+    else:
+        r, c, v = assemble_cells(grid, ci, cj, gx_fn, gy_fn, p["k"])
     return grid, _to_matrix(r, c, v, interior_numbering(grid), grid.n)
 
 

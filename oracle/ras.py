@@ -21,6 +21,12 @@ condition d_nu u - i k u = 0 (eq. impedance) enters as the natural term
 integral by 2-point Gauss. With local_bc = 1 (RAS-PML-Drch) those nodes are
 dropped (Dirichlet). Nodes on the outer boundary are always Dirichlet.
 
+With form = 1 (eq. weak as printed, not symmetric) the element terms carry
+D = diag(gamma^-2) and the beta term with the local gamma_j and its
+derivative, and the impedance condition, read in the stretched normal
+coordinate (gamma_n^-1 d_nu u = i k u), enters as -i k int gamma_n^-1 u v ds:
+the same local problem as form 0's, tested with v/(gamma_1 gamma_2).
+
 Partition of unity (Section 2, Section 4): chi_j is the tensor product of 1D
 weights that are 1 on the box away from the overlaps and vary linearly across
 every overlap strip (2*ovlp cells centred on the box edge), reaching 0 on the
@@ -121,6 +127,29 @@ def local_gamma_fn(grid: fem.Grid, r: Range1D, axis: int, amp: float, ramp: floa
     return fn
 
 
+def local_dgamma_fn(grid: fem.Grid, r: Range1D, axis: int, amp: float, ramp: float, profile: int = 0):
+    """gamma_j' along one axis (derivative of local_gamma_fn; eq. weak's beta, form 1).
+
+    Beyond an interior side hi of Omega_j,int g_j = g(x - hi), so gamma_j' =
+    i g''(x - hi); below an interior side lo g_j = -g(lo - x), so gamma_j' =
+    -i g''(lo - x); otherwise the global derivative.
+    """
+    glob = fem.global_dgamma_x if axis == 0 else fem.global_dgamma_y
+    hh = 0.5 * grid.h
+
+    def fn(s):
+        s = np.asarray(s, dtype=np.float64)
+        val = glob(grid, s, amp, ramp, profile)
+        if r.hi_interior:
+            d = (s - 2 * r.int_hi) * hh
+            val = np.where(s >= 2 * r.int_hi, 1j * fem.gsecond(d, amp, ramp, profile), val)
+        if r.lo_interior:
+            d = (2 * r.int_lo - s) * hh
+            val = np.where(s <= 2 * r.int_lo, -1j * fem.gsecond(d, amp, ramp, profile), val)
+        return val
+    return fn
+
+
 _GAUSS2 = (0.5 - 0.5 / math.sqrt(3.0), 0.5 + 0.5 / math.sqrt(3.0))
 
 
@@ -141,11 +170,17 @@ def local_operator(p: dict, grid: fem.Grid, rx: Range1D, ry: Range1D):
     amp, ramp, k = p["g_amp"], p["g_ramp"], p["k"]
     prof = p.get("g_profile", 0)
     imp = p.get("local_bc", 0) == 0
+    weak = p.get("form", 0) == 1
     gx = local_gamma_fn(grid, rx, 0, amp, ramp, prof)
     gy = local_gamma_fn(grid, ry, 1, amp, ramp, prof)
     cj, ci = np.meshgrid(np.arange(ry.ext_lo, ry.ext_hi),
                          np.arange(rx.ext_lo, rx.ext_hi), indexing="ij")
-    rows, cols, vals = fem.assemble_cells(grid, ci, cj, gx, gy, k)
+    if weak:
+        dgx = local_dgamma_fn(grid, rx, 0, amp, ramp, prof)
+        dgy = local_dgamma_fn(grid, ry, 1, amp, ramp, prof)
+        rows, cols, vals = fem.assemble_cells_weak(grid, ci, cj, gx, gy, dgx, dgy, k)
+    else:
+        rows, cols, vals = fem.assemble_cells(grid, ci, cj, gx, gy, k)
 
     # which nodes of Omega_j are local unknowns
     def keep_1d(lo, hi, M):
@@ -162,6 +197,8 @@ def local_operator(p: dict, grid: fem.Grid, rx: Range1D, ry: Range1D):
     numbering[nodes] = np.arange(nodes.size)
 
     # impedance term on the artificial boundary: -i k int gamma_t phi_a phi_b ds
+    # (form 0); with form 1 the weight is 1/gamma_n, the reciprocal of the
+    # stretch normal to the edge (constant along it)
     if imp:
         er, ec, ev = [], [], []
         h = grid.h
@@ -177,21 +214,27 @@ def local_operator(p: dict, grid: fem.Grid, rx: Range1D, ry: Range1D):
                 ec.append((n0, n1)[b])
                 ev.append(-1j * k * s)
 
-        # vertical sides x = const (tangential stretch: gamma_2)
+        # vertical sides x = const (tangential stretch: gamma_2; normal: gamma_1)
         for side_ok, ii in ((rx.lo_interior and rx.ext_lo > 0, rx.ext_lo),
                             (rx.hi_interior and rx.ext_hi < grid.Mx, rx.ext_hi)):
             if not side_ok:
                 continue
             for jc in range(ry.ext_lo, ry.ext_hi):
-                gam = [gy(2.0 * (jc + q)) for q in _GAUSS2]
+                if weak:
+                    gam = [1.0 / gx(2.0 * ii)] * 2
+                else:
+                    gam = [gy(2.0 * (jc + q)) for q in _GAUSS2]
                 edge_terms(jc * (grid.Mx + 1) + ii, (jc + 1) * (grid.Mx + 1) + ii, gam)
-        # horizontal sides y = const (tangential stretch: gamma_1)
+        # horizontal sides y = const (tangential stretch: gamma_1; normal: gamma_2)
         for side_ok, jj in ((ry.lo_interior and ry.ext_lo > 0, ry.ext_lo),
                             (ry.hi_interior and ry.ext_hi < grid.My, ry.ext_hi)):
             if not side_ok:
                 continue
             for ic in range(rx.ext_lo, rx.ext_hi):
-                gam = [gx(2.0 * (ic + q)) for q in _GAUSS2]
+                if weak:
+                    gam = [1.0 / gy(2.0 * jj)] * 2
+                else:
+                    gam = [gx(2.0 * (ic + q)) for q in _GAUSS2]
                 edge_terms(jj * (grid.Mx + 1) + ic, jj * (grid.Mx + 1) + ic + 1, gam)
         if er:
             rows = np.concatenate([rows, np.array(er, dtype=np.int64)])

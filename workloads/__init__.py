@@ -65,6 +65,7 @@ class Workload:
     g_ramp: float = 0.05
     local_bc: int = 0          # 0 impedance (RAS-PML-Imp), 1 Dirichlet
     g_profile: int = 0         # 0 smoothstep ramp; 1 g(d) = g_amp d^3
+    form: int = 0              # 0 gamma_1 gamma_2 (symmetric) form; 1 eq. weak as printed
     centres: np.ndarray = field(default_factory=lambda: np.zeros((0, 2)))
     amps: np.ndarray = field(default_factory=lambda: np.zeros(0))
     width: float = 0.02
@@ -88,7 +89,7 @@ class Workload:
                     kappa_g=self.kappa_g, h=self.h, px=self.px, py=self.py,
                     ovlp_cells=self.ovlp_cells, pml_cells=self.pml_cells,
                     g_amp=self.g_amp, g_ramp=self.g_ramp, local_bc=self.local_bc,
-                    g_profile=self.g_profile)
+                    g_profile=self.g_profile, form=self.form)
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
