@@ -104,6 +104,20 @@ typedef struct {
   int    g_profile;       /* stretching: 0 g'(d) as above; 1 g(d) = g_amp d^3,
                              i.e. g'(d) = 3 g_amp d^2 (the paper's experiments
                              use g_amp = 10k, Section 4); g_ramp unused        */
+  int    form;            /* bilinear form (Section 1, eq. weak):
+                             0 eq. weak multiplied by gamma_1 gamma_2, complex
+                               symmetric; local factors L D L^T (default);
+                             1 eq. weak as printed, int (D grad u).grad v
+                               - (beta.grad u) v - k^2 u v with D_ii =
+                               gamma_i^-2, beta_i = gamma_i'/gamma_i^3: not
+                               symmetric; local factors L D U without pivoting,
+                               impedance closure -i k int gamma_n^-1 u v ds
+                               (gamma_n: the stretch normal to the edge).
+                               Needs ortho 0..2 and a local half-bandwidth of
+                               at most 112 (factor_prec 0) or 160 (1 and 2);
+                               not accepted by ras_pml_batch_setup.
+                             Both discretise the same problem; their solutions
+                             differ by the discretisation error.              */
 } ras_pml_params;
 
 /* Sizes and statistics of a handle (filled by ras_pml_info). */
@@ -131,7 +145,7 @@ typedef struct ras_pml_handle ras_pml_handle;
  * eq. weak on the current device, on `cuda_stream` (a cudaStream_t, may be
  * NULL for the legacy default stream). Validates params (RASPML_EBADARG when
  * Omega is not whole cells, 2*ovlp exceeds a box, or a local half-bandwidth nlx+1 exceeds
- * 160 for factor_prec 0 or 232 for factor_prec 1 and 2).
+ * 160 for factor_prec 0 or 232 for factor_prec 1 and 2; with form 1, 112 and 160).
  * On success *out owns all device memory of the handle. */
 int ras_pml_setup(const ras_pml_params* params, void* cuda_stream,
                   ras_pml_handle** out);
@@ -172,7 +186,8 @@ int ras_pml_assemble_rhs_noalloc(ras_pml_handle* h, const double* centres_host,
 
 /* Assembles every local operator A_j (Section 2; impedance term of
  * Section 3 (ii) when local_bc = 0) and factors it as A_j = L_j D_j L_j^T
- * (no pivoting; A_j is complex symmetric) in the handle's factor precision.
+ * (no pivoting; A_j is complex symmetric) in the handle's factor precision;
+ * with form 1 as A_j = L_j D_j U_j (no pivoting, one CUDA-core shape).
  * Returns RASPML_EPIVOT if a pivot is zero or non-finite (see info.bad_subdomain),
  * RASPML_ETIMEOUT if the tensor-core form's bounded wait for its MMAs gave up.
  * Synchronises the stream. */
@@ -260,7 +275,8 @@ void ras_pml_destroy(ras_pml_handle* h);
  * threads, factor_rank 8 or 16: that many pivots per panel, the trailing
  * update as TF32 MMAs with a three-term split of each FP32 operand); apply
  * columns 8, plus 4 and 16 when factor_prec = 1.
- * Synchronises the stream.
+ * Synchronises the stream. With form 1 it factors once and times nothing
+ * (one factor shape; the apply shape stays as set; n_factor = n_apply = 0).
  * ------------------------------------------------------------------------- */
 typedef struct {
   int32_t factor_threads;    /* chosen threads per factor CTA                 */
@@ -336,7 +352,8 @@ typedef struct {
 } ras_pml_batch_info_t;
 
 /* Builds every problem (params[q], q < nprob; RASPML_EBADARG if one is
- * invalid, as ras_pml_setup) on the current device and stream. */
+ * invalid, as ras_pml_setup, or has form != 0) on the current device and
+ * stream. */
 int ras_pml_batch_setup(const ras_pml_params* params, int nprob, void* cuda_stream,
                         ras_pml_batch** out);
 

@@ -33,7 +33,7 @@ class Params(ctypes.Structure):
                 ("kappa_g", c_double), ("h", c_double), ("px", c_int), ("py", c_int),
                 ("ovlp_cells", c_int), ("pml_cells", c_int), ("g_amp", c_double), ("g_ramp", c_double),
                 ("local_bc", c_int), ("factor_prec", c_int), ("ortho", c_int),
-                ("g_profile", c_int)]
+                ("g_profile", c_int), ("form", c_int)]
 
 
 class Info(ctypes.Structure):

@@ -30,6 +30,7 @@ struct ras_pml_handle {
   int nsub = 0, max_b = 0, max_bp = 0, max_npad = 0, max_n = 0;
   long long n = 0, sum_npad = 0, sum_l = 0, sum_n = 0, sum_bn = 0;
   c128 *D = nullptr, *CW = nullptr, *CS = nullptr, *CSW = nullptr;
+  c128 *CE = nullptr, *CN = nullptr, *CNE = nullptr;   // form 1: the couplings symmetry no longer gives
   c128 *Ddf = nullptr, *CWdf = nullptr, *CSdf = nullptr, *CSWdf = nullptr;   // the same, split (ortho >= 3)
   void *L = nullptr, *Lrev = nullptr, *dinv = nullptr, *Y = nullptr;
   double* pivstats = nullptr;
@@ -71,6 +72,16 @@ constexpr double kC64BasisFloor = 1e-6;
     int s_ = dalloc(&(ptr), (cnt));   \
     if (s_ != RASPML_OK) return s_;   \
   } while (0)
+
+// y = A x, or y = bsub - A x: the four-array product of the symmetric form
+// (form 0) or the seven-array one of eq. weak as printed (form 1)
+cudaError_t spmv_A(const ras_pml_handle* h, const c128* x, const c128* bsub, c128* y, const rp::KState* kst,
+                   cudaStream_t st, int bkind = rp::RK_C128) {
+  if (h->p.form == 1)
+    return rp::launch_spmv7(h->n, h->geo.nx, rp::Stencil7{h->D, h->CW, h->CE, h->CS, h->CN, h->CSW, h->CNE}, x,
+                            bsub, y, kst, st, bkind);
+  return rp::launch_spmv(h->n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, x, bsub, y, kst, st, bkind);
+}
 
 int ensure_events(ras_pml_handle* h, int count) {
   while ((int)h->ev.size() < count) {
@@ -165,8 +176,10 @@ namespace rp {
 int build_problem(const ras_pml_params& p, int prob, Geo& g, std::vector<SubDesc>& subs) {
   if (!(p.k >= 0.0) || !(p.h > 0.0) || !(p.kappa_g >= 0.0) || !(p.x1 > p.x0) || !(p.y1 > p.y0) || p.px < 1 ||
       p.py < 1 || !(p.g_ramp > 0.0) || !(p.g_amp >= 0.0) || (p.local_bc != 0 && p.local_bc != 1) ||
-      (p.factor_prec < 0 || p.factor_prec > 2) || (p.ortho < 0 || p.ortho > 4) || (p.g_profile != 0 && p.g_profile != 1))
+      (p.factor_prec < 0 || p.factor_prec > 2) || (p.ortho < 0 || p.ortho > 4) || (p.g_profile != 0 && p.g_profile != 1) ||
+      (p.form != 0 && p.form != 1) || (p.form == 1 && p.ortho > 2))
     return RASPML_EBADARG;
+  const int band_limit = p.form == 1 ? max_band_lu(p.factor_prec) : max_band(p.factor_prec);
   const double lx = p.x1 - p.x0 + 2 * p.kappa_g, ly = p.y1 - p.y0 + 2 * p.kappa_g;
   const long long Mx = std::llround(lx / p.h), My = std::llround(ly / p.h);
   if (Mx < 2 || My < 2 || std::fabs(Mx * p.h - lx) > 1e-9 * lx || std::fabs(My * p.h - ly) > 1e-9 * ly ||
@@ -208,7 +221,7 @@ int build_problem(const ras_pml_params& p, int prob, Geo& g, std::vector<SubDesc
       int iy0 = imp ? Yr.ext_lo : Yr.ext_lo + 1, iy1 = imp ? Yr.ext_hi : Yr.ext_hi - 1;
       ix0 = std::max(ix0, 1); iy0 = std::max(iy0, 1);
       ix1 = std::min(ix1, g.Mx - 1); iy1 = std::min(iy1, g.My - 1);
-      if (ix1 < ix0 || iy1 < iy0 || (d.b = ix1 - ix0 + 2) > max_band(p.factor_prec)) {
+      if (ix1 < ix0 || iy1 < iy0 || (d.b = ix1 - ix0 + 2) > band_limit) {
         subs.resize(first);
         return RASPML_EBADARG;
       }
@@ -249,6 +262,7 @@ void ras_pml_destroy(ras_pml_handle* h) {
   if (h->st) cudaStreamSynchronize(h->st);
   dfree(h->Ddf); dfree(h->CWdf); dfree(h->CSdf); dfree(h->CSWdf);
   dfree(h->subs_d); dfree(h->geo_d); dfree(h->D); dfree(h->CW); dfree(h->CS); dfree(h->CSW);
+  dfree(h->CE); dfree(h->CN); dfree(h->CNE);
   dfree(h->L); dfree(h->Lrev); dfree(h->dinv); dfree(h->Y); dfree(h->pivstats); dfree(h->status);
   dfree(h->V); dfree(h->Z); dfree(h->H); dfree(h->sn); dfree(h->gvec); dfree(h->yv);
   dfree(h->partial); dfree(h->hbuf); dfree(h->cs); dfree(h->hist); dfree(h->scal); dfree(h->kst);
@@ -300,6 +314,11 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   SETUP_ALLOC(h->CW, (size_t)h->n);
   SETUP_ALLOC(h->CS, (size_t)h->n);
   SETUP_ALLOC(h->CSW, (size_t)h->n);
+  if (h->p.form == 1) {
+    SETUP_ALLOC(h->CE, (size_t)h->n);
+    SETUP_ALLOC(h->CN, (size_t)h->n);
+    SETUP_ALLOC(h->CNE, (size_t)h->n);
+  }
   SETUP_ALLOC(h->pivstats, (size_t)2 * h->nsub);
   SETUP_ALLOC(h->status, (size_t)1);
   cudaError_t e = cudaMemcpyAsync(h->subs_d, h->subs_h.data(), sizeof(SubDesc) * h->nsub, cudaMemcpyHostToDevice,
@@ -310,7 +329,12 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
     e = cudaMemcpyAsync(h->status, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->st);
   c128* tab = nullptr;
   if (e == cudaSuccess) e = cudaMalloc((void**)&tab, sizeof(c128) * rp::stretch_table_elems(g));
-  if (e == cudaSuccess) e = rp::launch_global_stencil(g, tab, h->D, h->CW, h->CS, h->CSW, h->st);
+  if (e == cudaSuccess) {
+    if (h->p.form == 1)
+      e = rp::launch_global_stencil_w(g, rp::Stencil7W{h->D, h->CW, h->CE, h->CS, h->CN, h->CSW, h->CNE}, h->st);
+    else
+      e = rp::launch_global_stencil(g, tab, h->D, h->CW, h->CS, h->CSW, h->st);
+  }
   if (e == cudaSuccess && h->p.ortho >= 3) {
     // the Arnoldi products of the double-float forms use the split coefficients
     c128* src[4] = {h->D, h->CW, h->CS, h->CSW};
@@ -396,8 +420,9 @@ int ras_pml_factor(ras_pml_handle* h) {
     if (e != cudaSuccess) return RASPML_ENOMEM;
     h->Y = p;
   }
+  const bool weak = h->p.form == 1;   // seven couplings per local row, L D U factors
   c128* Aloc = nullptr;
-  RP_ALLOC(Aloc, (size_t)4 * h->sum_npad);
+  RP_ALLOC(Aloc, (size_t)(weak ? 7 : 4) * h->sum_npad);
   if (h->timing) {
     int es_ = ensure_events(h, 2);
     if (es_) return es_;
@@ -406,8 +431,15 @@ int ras_pml_factor(ras_pml_handle* h) {
   cudaError_t e = cudaMemcpyAsync(h->status, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[0], h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->Lrev, 0, (size_t)h->sum_l * esl, h->st);
-  if (e == cudaSuccess) e = rp::launch_local_rows(h->p.factor_prec, h->geo_d, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && weak) {
+    e = rp::launch_local_rows_w(h->p.factor_prec, h->geo_d, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
+    if (e == cudaSuccess)
+      e = rp::launch_factor_lu(h->p.factor_prec, h->subs_d, h->nsub, h->max_b, Aloc, h->L, h->Lrev, h->dinv,
+                               h->pivstats, h->status, h->st);
+  }
+  if (e == cudaSuccess && !weak)
+    e = rp::launch_local_rows(h->p.factor_prec, h->geo_d, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
+  if (e == cudaSuccess && !weak)
     e = rp::launch_factor(h->p.factor_prec, h->tune.factor_threads, h->tune.factor_rank, h->subs_d, h->nsub, h->max_b, Aloc, h->L, h->Lrev, h->dinv,
                           h->pivstats, h->status, h->st);
   if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[1], h->st);
@@ -443,6 +475,16 @@ int ras_pml_tune(ras_pml_handle* h, ras_pml_tune_t* report) {
   cudaSetDevice(h->dev);
   int s = ras_pml_factor(h);
   if (s != RASPML_OK) return s;
+  if (h->p.form == 1) {
+    // one factor shape (the L D U kernel); the apply shape stays as set
+    if (report) {
+      std::memset(report, 0, sizeof(*report));
+      report->factor_threads = h->tune.factor_threads;
+      report->factor_rank = h->tune.factor_rank;
+      report->apply_cols = h->tune.apply_cols;
+    }
+    return RASPML_OK;
+  }
   c128 *Aloc = nullptr, *r = nullptr;
   RP_ALLOC(Aloc, (size_t)4 * h->sum_npad);
   if ((s = dalloc(&r, (size_t)h->n)) != RASPML_OK) { dfree(Aloc); return s; }
@@ -511,7 +553,7 @@ int ras_pml_apply(ras_pml_handle* h, const rp_c128* r, rp_c128* z) {
 int ras_pml_matvec(ras_pml_handle* h, const rp_c128* x, rp_c128* y) {
   if (!h || !x || !y || (const void*)x == (const void*)y) return RASPML_EBADARG;
   cudaSetDevice(h->dev);
-  RP_CUDA(rp::launch_spmv(h->n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, (const c128*)x, nullptr, (c128*)y,
+  RP_CUDA(spmv_A(h, (const c128*)x, nullptr, (c128*)y,
                           nullptr, h->st));
   return RASPML_OK;
 }
@@ -580,7 +622,7 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
     // new cycle: V0 = b - A x, beta = ||V0||, g = beta e1, V0 /= beta
     c128* V0 = c64basis ? h->wdf : h->V;
     ++cycles;
-    RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, x, b, V0, nullptr, st));
+    RP_CUDA(spmv_A(h, x, b, V0, nullptr, st));
     if ((s = dev_norm(h, V0, &h->kst->hnorm, nullptr, nullptr))) return s;
     RP_CUDA(rp::launch_cycle_init(h->kst, h->gvec, m, rtol, h->hist, st));
     if (dfbasis)
@@ -621,11 +663,11 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
         if (h->net) {
           // learned stage: c = correction of r1 = v_j - A z_j (r1 held in w), then
           // z_j += alpha c with the alpha minimising ||r1 - alpha A c||
-          RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, vj, w, h->kst, st, bkind));
+          RP_CUDA(spmv_A(h, zj, vj, w, h->kst, st, bkind));
           RP_CUDA(cudaMemsetAsync(h->lc, 0, sizeof(c128) * n, st));
           const int cs = rp::net_correct(h->net, w, h->lc, h->geo.nx, h->geo.ny, h->kst, st);
           if (cs != RASPML_OK) return cs;
-          RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, h->lc, nullptr, h->lac, h->kst, st));
+          RP_CUDA(spmv_A(h, h->lc, nullptr, h->lac, h->kst, st));
           RP_CUDA(rp::launch_dots(h->lac, n, 1, w, n, h->partial, h->kst, 0, st));
           RP_CUDA(rp::launch_dots_finish(h->partial, 1, h->lhv, 0, h->kst, 0, st));
           RP_CUDA(rp::launch_dots(h->lac, n, 1, h->lac, n, h->partial, h->kst, 0, st));
@@ -637,7 +679,7 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
           RP_CUDA(rp::launch_spmv_df(n, h->geo.nx, h->Ddf, h->CWdf, h->CSdf, h->CSWdf, zj, w, h->kst, st,
                                      c64basis ? 1 : 0, zdf));
         else
-          RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, zj, nullptr, w, h->kst, st));
+          RP_CUDA(spmv_A(h, zj, nullptr, w, h->kst, st));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[2], st));
         if (h->p.ortho == 0) {
           // classical Gram-Schmidt, twice
@@ -711,7 +753,7 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
         RP_CUDA(rp::launch_axpys(h->Z, n, ks.jdone, h->yv, 1.0, x, n, nullptr, 0, st));
     }
     // true residual
-    RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, x, b, h->V, nullptr, st));
+    RP_CUDA(spmv_A(h, x, b, h->V, nullptr, st));
     if ((s = dev_norm(h, h->V, h->scal, nullptr, nullptr))) return s;
     double rn = 0.0;
     RP_CUDA(cudaMemcpyAsync(&rn, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -789,7 +831,7 @@ int ras_pml_richardson(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, 
   double rel = 0.0;
   int status = RASPML_NOT_CONVERGED;
   for (;; ++it) {
-    RP_CUDA(rp::launch_spmv(n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, x, b, h->tmp_r, nullptr, h->st));
+    RP_CUDA(spmv_A(h, x, b, h->tmp_r, nullptr, h->st));
     if ((s = dev_norm(h, h->tmp_r, h->scal, nullptr, nullptr))) return s;
     double rn = 0.0;
     RP_CUDA(cudaMemcpyAsync(&rn, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));

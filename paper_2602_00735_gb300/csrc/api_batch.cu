@@ -211,7 +211,8 @@ int ras_pml_batch_setup(const ras_pml_params* params, int nprob, void* stream, r
   std::vector<SubDesc> nat;   // natural order: problem by problem, x fastest
   long long goff = 0;
   for (int q = 0; q < nprob; ++q) {
-    if (params[q].factor_prec != h->prec) { delete h; return RASPML_EBADARG; }
+    // the batched kernels take the symmetric form only
+    if (params[q].factor_prec != h->prec || params[q].form != 0) { delete h; return RASPML_EBADARG; }
     Geo g{};
     const int s = rp::build_problem(params[q], q, g, nat);
     if (s != RASPML_OK) { delete h; return s; }

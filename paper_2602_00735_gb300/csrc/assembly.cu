@@ -361,6 +361,213 @@ __global__ void k_rhs(Geo g, const double* __restrict__ cen, const double* __res
   b[r] = mk(f * (g.h * g.h / 6.0), 0.0);
 }
 
+// ---------------------------------------------------------------------------
+// Form 1: eq. weak as printed (Section 1),
+//   a(u,v) = int (D grad u).grad v - (beta.grad u) v - k^2 u v,
+//   D = diag(gamma_1^-2, gamma_2^-2), beta_i = gamma_i' / gamma_i^3,
+// which is not symmetric, so every row keeps all seven couplings
+// {D, W, E, S, N, SW, NE}. Each node's row is summed from the element
+// matrices of the (up to six) triangles around it, in a fixed order, every
+// integral by the edge-midpoint rule (weight h^2/6 per midpoint).
+// ---------------------------------------------------------------------------
+
+// g''(d) in arithmetic type T (zero for d <= 0; continuous).
+template <typename T>
+__device__ __forceinline__ T gsecond_t(double d, double amp, double ramp, int profile) {
+  if (!(d > 0.0)) return (T)0;
+  if (profile == 1) return (T)6 * (T)amp * (T)d;
+  const T t = fmin((T)d / (T)ramp, (T)1);
+  return (T)6 * (T)amp * t * ((T)1 - t) / (T)ramp;
+}
+
+// The two triangles of cell (ci, cj): vertex offsets, hat gradients (units
+// 1/h), edge-midpoint half-index offsets from (2ci, 2cj) and the hat values
+// there (phi[t][m][a]: hat of vertex a at midpoint m).
+struct TriTab {
+  int vx[2][3], vy[2][3];
+  double gx[2][3], gy[2][3];
+  int mx[2][3], my[2][3];
+  double phi[2][3][3];
+};
+__constant__ TriTab kTri = {
+    {{0, 1, 1}, {0, 1, 0}},
+    {{0, 0, 1}, {0, 1, 1}},
+    {{-1.0, 1.0, 0.0}, {0.0, 1.0, -1.0}},
+    {{0.0, -1.0, 1.0}, {-1.0, 0.0, 1.0}},
+    {{1, 2, 1}, {1, 1, 0}},
+    {{0, 1, 1}, {1, 2, 1}},
+    {{{0.5, 0.5, 0.0}, {0.0, 0.5, 0.5}, {0.5, 0.0, 0.5}}, {{0.5, 0.5, 0.0}, {0.0, 0.5, 0.5}, {0.5, 0.0, 0.5}}}};
+
+// coupling slot of a neighbour offset: D, W, E, S, N, SW, NE
+__device__ __forceinline__ int slot7(int dx, int dy) {
+  return dy == 0 ? (dx == 0 ? 0 : dx < 0 ? 1 : 2) : (dx == 0 ? (dy < 0 ? 3 : 4) : (dy < 0 ? 5 : 6));
+}
+
+// Global stretching and its derivative: gamma_1' = i (g''(x - x1) - g''(x0 - x)).
+struct GlobalStretchW {
+  Geo g;
+  __device__ c128 gx(double s) const { return gam_global_x(g, s); }
+  __device__ c128 gy(double s) const { return gam_global_y(g, s); }
+  __device__ c128 dgx(double s) const {
+    const double x = xpos(g, s);
+    return mk(0.0, gsecond_t<double>(x - g.x1, g.g_amp, g.g_ramp, g.g_profile) -
+                       gsecond_t<double>(g.x0 - x, g.g_amp, g.g_ramp, g.g_profile));
+  }
+  __device__ c128 dgy(double s) const {
+    const double y = ypos(g, s);
+    return mk(0.0, gsecond_t<double>(y - g.y1, g.g_amp, g.g_ramp, g.g_profile) -
+                       gsecond_t<double>(g.y0 - y, g.g_amp, g.g_ramp, g.g_profile));
+  }
+  __device__ bool cell_ok(int ci, int cj) const { return ci >= 0 && ci < g.Mx && cj >= 0 && cj < g.My; }
+};
+
+// Local stretching g_j (Section 2) and its derivative: beyond an interior
+// side hi of Omega_j,int gamma' = i g''(x - hi), below an interior side lo
+// gamma' = -i g''(lo - x), the global derivative elsewhere.
+template <typename T>
+struct LocalStretchW {
+  LocalStretch<T> ls;
+  __device__ cx<T> dg(double s, double c0, double c1, int lo, int hi, int flo, int fhi, double X0) const {
+    const Geo& g = ls.g;
+    if ((ls.sd.flags & fhi) && s >= 2.0 * hi)
+      return mk((T)0, gsecond_t<T>((s - 2.0 * hi) * g.hh, g.g_amp, g.g_ramp, g.g_profile));
+    if ((ls.sd.flags & flo) && s <= 2.0 * lo)
+      return mk((T)0, -gsecond_t<T>((2.0 * lo - s) * g.hh, g.g_amp, g.g_ramp, g.g_profile));
+    const double x = __dadd_rn(X0, __dmul_rn(s, g.hh));
+    return mk((T)0, gsecond_t<T>(x - c1, g.g_amp, g.g_ramp, g.g_profile) -
+                        gsecond_t<T>(c0 - x, g.g_amp, g.g_ramp, g.g_profile));
+  }
+  __device__ cx<T> gx(double s) const { return ls.gx(s); }
+  __device__ cx<T> gy(double s) const { return ls.gy(s); }
+  __device__ cx<T> dgx(double s) const {
+    return dg(s, ls.g.x0, ls.g.x1, ls.sd.int_lo_x, ls.sd.int_hi_x, LO_X, HI_X, ls.g.X0);
+  }
+  __device__ cx<T> dgy(double s) const {
+    return dg(s, ls.g.y0, ls.g.y1, ls.sd.int_lo_y, ls.sd.int_hi_y, LO_Y, HI_Y, ls.g.Y0);
+  }
+  __device__ bool cell_ok(int ci, int cj) const { return ls.cell_ok(ci, cj); }
+};
+
+// Row of node (i, j): c[slot7(dx, dy)] += a(phi_(i+dx, j+dy), phi_(i,j)) over
+// the cells around the node that S admits.
+template <typename T, class S>
+__device__ void node_row_w(const Geo& g, const S& st, int i, int j, cx<T> (&c)[7]) {
+  const T sixth = (T)(1.0 / 6.0), hs = (T)(g.h / 6.0), k2m = (T)(g.k * g.k * g.h * g.h / 6.0);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) c[q] = mk((T)0, (T)0);
+  for (int q = 0; q < 4; ++q) {
+    const int ci = i - 1 + (q & 1), cj = j - 1 + (q >> 1);
+    if (!st.cell_ok(ci, cj)) continue;
+    for (int t = 0; t < 2; ++t) {
+      int a = -1;
+      for (int v = 0; v < 3; ++v)
+        if (ci + kTri.vx[t][v] == i && cj + kTri.vy[t][v] == j) a = v;
+      if (a < 0) continue;
+      cx<T> d1 = mk((T)0, (T)0), d2 = d1, b1[3], b2[3];
+      for (int m = 0; m < 3; ++m) {
+        const double sx = 2.0 * ci + kTri.mx[t][m], sy = 2.0 * cj + kTri.my[t][m];
+        const cx<T> r1 = crecip(st.gx(sx)), r2 = crecip(st.gy(sy));
+        const cx<T> r1s = r1 * r1, r2s = r2 * r2;
+        d1 = d1 + r1s;
+        d2 = d2 + r2s;
+        b1[m] = st.dgx(sx) * (r1s * r1);
+        b2[m] = st.dgy(sy) * (r2s * r2);
+      }
+      d1 = sixth * d1;
+      d2 = sixth * d2;
+      const T gax = (T)kTri.gx[t][a], gay = (T)kTri.gy[t][a];
+      for (int b = 0; b < 3; ++b) {
+        const T gbx = (T)kTri.gx[t][b], gby = (T)kTri.gy[t][b];
+        cx<T> adv = mk((T)0, (T)0);
+        T mass = (T)0;
+        for (int m = 0; m < 3; ++m) {
+          const T pa = (T)kTri.phi[t][m][a];
+          adv = adv + pa * (gbx * b1[m] + gby * b2[m]);
+          mass += pa * (T)kTri.phi[t][m][b];
+        }
+        const cx<T> v = (gbx * gax) * d1 + (gby * gay) * d2 - hs * adv - mk(k2m * mass, (T)0);
+        const int sl = slot7(ci + kTri.vx[t][b] - i, cj + kTri.vy[t][b] - j);
+        c[sl] = c[sl] + v;
+      }
+    }
+  }
+}
+
+// Impedance closure of form 1 (Section 3 (ii), read in the stretched normal
+// coordinate): -i k int gamma_n^-1 phi_a phi_b ds on the edges of the
+// artificial boundary of Omega_j; gamma_n is constant along a side, so an
+// edge of length h contributes h/3 on the diagonal and h/6 to the coupling.
+template <typename T>
+__device__ void impedance_terms_w(const Geo& g, const SubDesc& sd, const LocalStretch<T>& st, int i, int j,
+                                  cx<T> (&c)[7]) {
+  const cx<T> mik = mk((T)0, (T)(-g.k * g.h));
+  const T third = (T)(1.0 / 3.0), sixth = (T)(1.0 / 6.0);
+  const bool left = sd.ext_lo_x > 0 && i == sd.ext_lo_x;
+  const bool right = sd.ext_hi_x < g.Mx && i == sd.ext_hi_x;
+  if (left || right) {
+    const cx<T> w = mik * crecip(st.gx(2.0 * i));
+    if (j - 1 >= sd.ext_lo_y) { c[0] = c[0] + third * w; c[3] = c[3] + sixth * w; }
+    if (j < sd.ext_hi_y) { c[0] = c[0] + third * w; c[4] = c[4] + sixth * w; }
+  }
+  const bool bottom = sd.ext_lo_y > 0 && j == sd.ext_lo_y;
+  const bool top = sd.ext_hi_y < g.My && j == sd.ext_hi_y;
+  if (bottom || top) {
+    const cx<T> w = mik * crecip(st.gy(2.0 * j));
+    if (i - 1 >= sd.ext_lo_x) { c[0] = c[0] + third * w; c[1] = c[1] + sixth * w; }
+    if (i < sd.ext_hi_x) { c[0] = c[0] + third * w; c[2] = c[2] + sixth * w; }
+  }
+}
+
+// one thread per global row; couplings to outer-boundary nodes are zero
+__global__ void k_global_stencil_w(Geo g, Stencil7W A) {
+  const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n = (long long)g.nx * g.ny;
+  if (r >= n) return;
+  const int jq = (int)r / g.nx, i = (int)r - jq * g.nx + 1, j = jq + 1;   // n < 2^31
+  c128 c[7];
+  node_row_w<double>(g, GlobalStretchW{g}, i, j, c);
+  const c128 z = mk(0.0, 0.0);
+  A.D[r] = c[0];
+  A.W[r] = i > 1 ? c[1] : z;
+  A.E[r] = i < g.nx ? c[2] : z;
+  A.S[r] = j > 1 ? c[3] : z;
+  A.N[r] = j < g.ny ? c[4] : z;
+  A.SW[r] = (i > 1 && j > 1) ? c[5] : z;
+  A.NE[r] = (i < g.nx && j < g.ny) ? c[6] : z;
+}
+
+// one thread per local row: Aw[7 (v_off + r) + q] = coupling q of row r of
+// A_j; couplings to nodes that are not local unknowns are zero; padding
+// rows (r >= n) are identity rows
+template <typename T>
+__global__ void __launch_bounds__(kLrThreads)
+    k_local_rows_w(const Geo* __restrict__ geos, const SubDesc* __restrict__ subs, c128* __restrict__ Aw) {
+  const SubDesc sd = subs[blockIdx.y];
+  const int r = blockIdx.x * kLrThreads + threadIdx.x;
+  if (r >= sd.npad) return;
+  c128* out = Aw + 7 * (sd.v_off + r);
+  const c128 z = mk(0.0, 0.0);
+  if (r >= sd.n) {
+    out[0] = mk(1.0, 0.0);
+    for (int q = 1; q < 7; ++q) out[q] = z;
+    return;
+  }
+  const Geo g = geos[sd.prob];
+  const LocalStretch<T> ls{g, sd};
+  const int i = sd.ix0 + r % sd.nlx, j = sd.iy0 + r / sd.nlx;
+  cx<T> c[7];
+  node_row_w<T>(g, LocalStretchW<T>{ls}, i, j, c);
+  if (g.local_bc == 0) impedance_terms_w<T>(g, sd, ls, i, j, c);
+  const bool w = i > sd.ix0, e = i < sd.ix0 + sd.nlx - 1, s = j > sd.iy0, nn = j < sd.iy0 + sd.nly - 1;
+  out[0] = cvt<double>(c[0]);
+  out[1] = w ? cvt<double>(c[1]) : z;
+  out[2] = e ? cvt<double>(c[2]) : z;
+  out[3] = s ? cvt<double>(c[3]) : z;
+  out[4] = nn ? cvt<double>(c[4]) : z;
+  out[5] = (w && s) ? cvt<double>(c[5]) : z;
+  out[6] = (e && nn) ? cvt<double>(c[6]) : z;
+}
+
 }  // namespace
 
 size_t stretch_table_elems(const Geo& g) { return (size_t)2 * (2 * g.Mx + 1 + 2 * g.My + 1); }
@@ -392,6 +599,23 @@ cudaError_t launch_rhs(const Geo& g, const double* cen, const double* amp, int n
   int threads = 256;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
   k_rhs<<<blocks, threads, 0, st>>>(g, cen, amp, ns, width, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_global_stencil_w(const Geo& g, const Stencil7W& A, cudaStream_t st) {
+  const long long n = (long long)g.nx * g.ny;
+  const int threads = 256;
+  k_global_stencil_w<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(g, A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_local_rows_w(int prec, const Geo* geos, const SubDesc* subs, int nsub, int max_npad, c128* Aw,
+                                cudaStream_t st) {
+  dim3 grid((max_npad + kLrThreads - 1) / kLrThreads, nsub);
+  if (prec == 0)
+    k_local_rows_w<double><<<grid, kLrThreads, 0, st>>>(geos, subs, Aw);
+  else
+    k_local_rows_w<float><<<grid, kLrThreads, 0, st>>>(geos, subs, Aw);
   return cudaGetLastError();
 }
 

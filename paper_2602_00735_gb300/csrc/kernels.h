@@ -67,6 +67,34 @@ cudaError_t launch_local_rows(int prec, const Geo* geos, const SubDesc* subs, in
 cudaError_t launch_rhs(const Geo& g, const double* cen, const double* amp, int ns, double width, c128* b,
                        cudaStream_t st);
 
+// Form 1, eq. weak as printed (not symmetric): the seven couplings of every
+// global row, as stored (assembly.cu, written) and as read (weak.cu).
+struct Stencil7W {
+  c128 *D, *W, *E, *S, *N, *SW, *NE;
+};
+struct Stencil7 {
+  const c128 *D, *W, *E, *S, *N, *SW, *NE;
+};
+// largest local half-bandwidth of the form-1 factor: its square window,
+// (b+1)^2 entries in the arithmetic type, must fit in shared memory
+constexpr int kMaxBandLuC128 = 112;
+constexpr int kMaxBandLuC64 = 160;
+int max_band_lu(int prec);
+size_t factor_lu_smem_bytes(int b, int prec);
+// assembly.cu
+cudaError_t launch_global_stencil_w(const Geo& g, const Stencil7W& A, cudaStream_t st);
+// Aw: 7 complex128 couplings per local row (D, W, E, S, N, SW, NE)
+cudaError_t launch_local_rows_w(int prec, const Geo* geos, const SubDesc* subs, int nsub, int max_npad, c128* Aw,
+                                cudaStream_t st);
+// weak.cu: y = A x, or y = bsub - A x (bsub of kind bsub_kind)
+cudaError_t launch_spmv7(long long n, int nx, const Stencil7& A, const c128* x, const c128* bsub, c128* y,
+                         const KState* kst, cudaStream_t st, int bsub_kind);
+// A_j = L D U without pivoting; writes L, the reversed band of U (the
+// backward sweep's input, zero-filled by the caller) and D^-1 in the
+// layout of launch_factor
+cudaError_t launch_factor_lu(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aw, void* L, void* Urev,
+                             void* dinv, double* pivstats, DevStatus* status, cudaStream_t st);
+
 // factor.cu
 size_t factor_smem_bytes(int b, int prec, int rank);
 cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, int nsub, int max_b,

@@ -24,6 +24,7 @@ def make_params(params: dict, factor_prec: int = 0, ortho: int = 0) -> _lib.Para
     p.factor_prec = int(factor_prec)
     p.ortho = int(ortho)
     p.g_profile = int(params.get("g_profile", 0))
+    p.form = int(params.get("form", 0))
     return p
 
 

@@ -89,6 +89,23 @@ def test_error_strings_and_null_handling(lib):
     assert lib.ras_pml_setup(ctypes.byref(p), None, ctypes.byref(h)) == -1   # not whole cells
 
 
+def test_form_validation_before_any_device_call(lib):
+    """form 1 (eq. weak as printed) accepts ortho 0..2 and local half-bandwidths
+    up to 112 with complex128 factors; other forms are refused."""
+    import ctypes
+    from paper_2602_00735_gb300 import _lib
+    base = dict(k=10.0, x0=0, y0=0, x1=1, y1=1, kappa_g=0.1, h=0.0125, px=2, py=2, ovlp_cells=2,
+                pml_cells=2, g_amp=20, g_ramp=0.05, local_bc=0, factor_prec=0)
+    h = ctypes.c_void_p()
+    for kw in (dict(form=2), dict(form=-1), dict(form=1, ortho=3), dict(form=1, ortho=4),
+               dict(form=1, h=1 / 120, px=1, py=1)):        # b = 144 > 112
+        p = _lib.Params(**{**base, **kw})
+        assert lib.ras_pml_setup(ctypes.byref(p), None, ctypes.byref(h)) == -1, kw
+    p = _lib.Params(**{**base, "form": 1})
+    arr = (_lib.Params * 1)(p)
+    assert lib.ras_pml_batch_setup(arr, 1, None, ctypes.byref(h)) == -1
+
+
 def test_product_path_has_no_oracle_import():
     pkgdir = os.path.join(ROOT, "paper_2602_00735_gb300")
     for dirpath, _, files in os.walk(pkgdir):
