@@ -267,7 +267,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w = workloads.get(args.workload)
-    p = w.params()
+    p = dict(w.params(), form=args.form)
     stream = torch.cuda.current_stream(dev)
 
     shapes = {}   # tile shapes per factor precision, tuned once on a warm-up handle
@@ -451,6 +451,7 @@ def run_ours(args, rank, world, local_rank):
                                f"{p['px']}x{p['py']} subdomains, ovlp={p['ovlp_cells']} pml={p['pml_cells']} cells, "
                                f"{len(w.amps)} Gaussians width {w.width}",
                    "n_unknowns": info["n"], "rtol": RTOL, "parallelism": f"replicas x{world}",
+                   "form": args.form,
                    "l2": "inputs larger than L2 (complex64 factors %.1f GB)" % (info["factor_bytes"] / 1e9)},
         "iters": last["iters"], "relres": last["relres"], "ortho": args.ortho, "reorths": last["reorths"],
         "phases_ms": {"factor": round(last["factor_ms"], 2), "solve": round(last["solve_ms"], 2),
@@ -459,8 +460,9 @@ def run_ours(args, rank, world, local_rank):
                       "setup_and_rest": round(mean_t * 1e3 - last["factor_ms"] - last["solve_ms"], 2)},
         "apply_gbs": round(achieved, 1),
         "applies_per_s": round(1.0 / avg_apply_s, 1),
-        # one timed SpMV per direction: 4 coefficient arrays, x and y (96 bytes per row)
-        "spmv_gbs": round(96.0 * info["n"] * sum(q["applies"] for q in per_c64)
+        # one timed SpMV per direction: 4 coefficient arrays, x and y (96 bytes per row);
+        # 7 arrays with form 1 (144 bytes per row)
+        "spmv_gbs": round((96.0 if args.form == 0 else 144.0) * info["n"] * sum(q["applies"] for q in per_c64)
                           / max(1e-9, sum(q["spmv_ms"] for q in per_c64) / 1e3) / 1e9, 1),
         "roofline": {"kernel": "ras_pml_apply (k_apply + k_prolong), complex64", "bound": "hbm",
                      "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -749,6 +751,9 @@ def main():
                          "2: once; 3: once in double-float arithmetic; 4: as 3 on a complex64 basis")
     ap.add_argument("--prec", type=int, default=1, choices=[1, 2],
                     help="local factors of the headline form: 1 complex64, 2 complex64 with half-precision storage")
+    ap.add_argument("--form", type=int, default=0, choices=[0, 1],
+                    help="bilinear form: 0 the complex-symmetric gamma_1 gamma_2 form (L D L^T factors), "
+                         "1 eq. weak as printed (L D U factors; needs --ortho 0..2, no learned stage)")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-learned", action="store_true")
@@ -756,6 +761,10 @@ def main():
     ap.add_argument("--shapes", default="",
                     help="fixed tile shapes 'threads,rank,cols' instead of tuning (profiling runs)")
     args = ap.parse_args()
+    if args.form == 1:
+        if args.ortho > 2 or args.workload in ("c3", "net"):
+            ap.error("--form 1 takes --ortho 0..2 and a one-problem workload")
+        args.skip_learned = True
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -12,7 +12,9 @@
 //     1. reads the pivot column c_t = W(k+t, k) and row r_t = W(k, k+t),
 //        d = c_0, writes L(k+t, k) = c_t / d, U(k, k+t) = u_t = r_t / d and
 //        D^-1(k) = 1/d;
-//     2. applies W(k+i, k+j) -= c_i u_j, 1 <= i, j <= b, and at the same time
+//     2. applies W(k+i, k+j) -= c_i u_j, 1 <= i, j <= b (a thread keeps one
+//        column j and steps through rows i with a fixed stride, so the
+//        circular slots advance by additions), and at the same time
 //        moves row k+b+1 and column k+b+1 of A_j into the slots of row k and
 //        column k (disjoint from the update's slots; neither has been touched
 //        by an earlier pivot, since they lie outside its band).
@@ -101,6 +103,11 @@ __global__ void __launch_bounds__(kLuThreads)
   R dmin2 = (R)3e38, dmax2 = (R)0;
   bool bad = false;
   int ks = 0;   // k mod Wc
+  // update mapping: G = NT / b row groups; thread tid < G*b owns column
+  // j = 1 + tid mod b and rows i = 1 + tid / b, 1 + tid / b + G, ...
+  const int G = kLuThreads / b;
+  const int uj = 1 + tid % b, ui0 = 1 + tid / b;
+  const bool upd = tid < G * b;
   for (int k = 0; k < npad; ++k) {
     // 1. pivot column and row
     if (tid <= b) {
@@ -127,13 +134,17 @@ __global__ void __launch_bounds__(kLuThreads)
     __syncthreads();
     // 2. update of rows and columns k+1..k+b; row and column k+b+1 enter the
     //    slots of row k and column k
-    for (int e = tid; e < b * b; e += kLuThreads) {
-      const int i = e / b + 1, j = e - (i - 1) * b + 1;
-      int ri = ks + i, cj = ks + j;
-      if (ri >= Wc) ri -= Wc;
+    if (upd) {
+      int cj = ks + uj, ri = ks + ui0;
       if (cj >= Wc) cj -= Wc;
-      cx<R>* w = &W[ri * Wc + cj];
-      *w = fms(*w, cbuf[i], ubuf[j]);
+      if (ri >= Wc) ri -= Wc;
+      const cx<R> u = ubuf[uj];
+      for (int i = ui0; i <= b; i += G) {   // i + G <= b implies ri + G < 2 Wc
+        cx<R>* w = &W[ri * Wc + cj];
+        *w = fms(*w, cbuf[i], u);
+        ri += G;
+        if (ri >= Wc) ri -= Wc;
+      }
     }
     if (tid <= b) {
       const int rn = k + b + 1;
