@@ -151,7 +151,7 @@ class ClockSampler:
 # CPU oracle baseline on a bounded sample
 # ---------------------------------------------------------------------------
 
-def cpu_sample(w, iters: int, n_local: int = 8):
+def cpu_sample(w, iters: int, n_local: int = 64):
     """Times the oracle on a bounded sample of workload w and scales it to a
     full solve of `iters` FGMRES directions, with the oracle's own code:
       full:   global assembly, load vector, one global SpMV, one norm, and one
@@ -180,7 +180,7 @@ def cpu_sample(w, iters: int, n_local: int = 8):
     t5 = time.perf_counter()
     grid, rxs, rys = ras.covering(p)
     nsub = len(rxs) * len(rys)
-    picks = np.linspace(0, nsub - 1, n_local).astype(int)
+    picks = np.unique(np.linspace(0, nsub - 1, min(n_local, nsub)).astype(int))
     tf = ta = 0.0
     z = np.zeros(grid.n, dtype=np.complex128)
     for j in picks:
@@ -201,12 +201,13 @@ def cpu_sample(w, iters: int, n_local: int = 8):
     return est, sample_s, nsub, nrm
 
 
-def cpu_baseline_obj(w, iters):
-    est, sample_s, nsub, _ = cpu_sample(w, iters)
+def cpu_baseline_obj(w, iters, n_local: int = 64):
+    n_local = min(n_local, w.px * w.py)
+    est, sample_s, nsub, _ = cpu_sample(w, iters, n_local)
     return {"value": round(est, 3), "unit": "s", "cores": 1, "kind": "oracle",
             "sample": (f"oracle on {w.name}: global assembly, load vector, one SpMV, one norm and one modified "
                        f"Gram-Schmidt step on the full mesh; local assembly + SuperLU factor + one local apply "
-                       f"(gather, solve, weighted scatter) on 8 of {nsub} subdomains (scaled x{nsub / 8:g}); "
+                       f"(gather, solve, weighted scatter) on {n_local} of {nsub} subdomains (scaled x{nsub / n_local:g}); "
                        f"scaled to {iters} FGMRES directions; {sample_s:.1f} s of CPU work, one thread")}
 
 
