@@ -405,20 +405,10 @@ int ras_pml_factor(ras_pml_handle* h) {
   cudaSetDevice(h->dev);
   const size_t es = h->p.factor_prec == 0 ? sizeof(c128) : sizeof(c64);
   const size_t esl = h->p.factor_prec == 0 ? 16 : h->p.factor_prec == 1 ? 8 : 4;   // L entry storage
-  if (!h->L) {
-    void* p;
-    cudaError_t e = cudaMalloc(&p, (size_t)h->sum_l * esl);
-    if (e != cudaSuccess) return RASPML_ENOMEM;
-    h->L = p;
-    e = cudaMalloc(&p, (size_t)h->sum_l * esl);
-    if (e != cudaSuccess) return RASPML_ENOMEM;
-    h->Lrev = p;
-    e = cudaMalloc(&p, (size_t)h->sum_npad * es);
-    if (e != cudaSuccess) return RASPML_ENOMEM;
-    h->dinv = p;
-    e = cudaMalloc(&p, (size_t)h->sum_npad * es);
-    if (e != cudaSuccess) return RASPML_ENOMEM;
-    h->Y = p;
+  {
+    const int sa = rp::alloc_factor_buffers(&h->L, &h->Lrev, &h->dinv, &h->Y, (size_t)h->sum_l * esl,
+                                            (size_t)h->sum_npad * es);
+    if (sa != RASPML_OK) return sa;
   }
   const bool weak = h->p.form == 1;   // seven couplings per local row, L D U factors
   c128* Aloc = nullptr;

@@ -401,18 +401,9 @@ int ras_pml_batch_assemble_rhs(ras_pml_batch* h, const int32_t* ns, const double
 namespace {
 
 int batch_alloc_factors(ras_pml_batch* h) {
-  if (h->L) return RASPML_OK;
   const size_t esl = l_bytes(h->prec), es = entry_bytes(h->prec);
-  void* p;
-  if (cudaMalloc(&p, (size_t)h->sum_l * esl) != cudaSuccess) return RASPML_ENOMEM;
-  h->L = p;
-  if (cudaMalloc(&p, (size_t)h->sum_l * esl) != cudaSuccess) return RASPML_ENOMEM;
-  h->Lrev = p;
-  if (cudaMalloc(&p, (size_t)h->sum_npad * es) != cudaSuccess) return RASPML_ENOMEM;
-  h->dinv = p;
-  if (cudaMalloc(&p, (size_t)h->sum_npad * es) != cudaSuccess) return RASPML_ENOMEM;
-  h->Y = p;
-  return RASPML_OK;
+  return rp::alloc_factor_buffers(&h->L, &h->Lrev, &h->dinv, &h->Y, (size_t)h->sum_l * esl,
+                                  (size_t)h->sum_npad * es);
 }
 
 // local rows of every subdomain into a fresh Aloc (caller frees)

@@ -29,7 +29,28 @@ int dalloc(T** p, size_t count) {
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
   if (e != cudaSuccess) {
     *p = nullptr;
+    cudaGetLastError();   // an allocation failure is not sticky: keep it out of later launch checks
     return e == cudaErrorMemoryAllocation ? RASPML_ENOMEM : RASPML_ECUDA;
+  }
+  return RASPML_OK;
+}
+
+// Allocates whichever of a handle's factor buffers are still missing (L, its
+// reversed band copy, D^-1, the work vector Y). After a failure the buffers
+// already held stay with the handle, so a later call completes the set and
+// ras_pml_destroy frees them; no buffer is ever left half-set.
+inline int alloc_factor_buffers(void** L, void** Lrev, void** dinv, void** Y, size_t l_bytes, size_t v_bytes) {
+  struct {
+    void** p;
+    size_t n;
+  } bufs[4] = {{L, l_bytes}, {Lrev, l_bytes}, {dinv, v_bytes}, {Y, v_bytes}};
+  for (auto& b : bufs) {
+    if (*b.p) continue;
+    if (cudaMalloc(b.p, b.n ? b.n : 1) != cudaSuccess) {
+      *b.p = nullptr;
+      cudaGetLastError();
+      return RASPML_ENOMEM;
+    }
   }
   return RASPML_OK;
 }
