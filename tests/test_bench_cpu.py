@@ -29,6 +29,15 @@ def test_reference_arm_prints_one_json_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0
 
 
+def test_form_option_is_validated_before_any_device_work():
+    """--form 1 (eq. weak as printed) takes the FP64 Gram-Schmidt variants and a
+    one-problem workload only; argparse refuses the rest with status 2."""
+    for args in (["--form", "1", "--ortho", "4"], ["--form", "1", "--ortho", "2", "--workload", "c3"],
+                 ["--form", "2"]):
+        r = _run(args, {})
+        assert r.returncode == 2 and "form" in r.stderr, (args, r.stderr)
+
+
 def test_reference_arm_for_the_batched_workload():
     """--workload c3: the oracle's bounded sample on the median problem, scaled
     by the oracle's own per-problem iteration counts (tests/golden)."""
