@@ -201,10 +201,16 @@ def cpu_sample(w, iters: int, n_local: int = 64):
     return est, sample_s, nsub, nrm
 
 
+def host_cpus() -> dict:
+    """The host's logical CPUs and the ones this process may run on."""
+    aff = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else None
+    return {"host_cpus": os.cpu_count(), "affinity_cpus": aff}
+
+
 def cpu_baseline_obj(w, iters, n_local: int = 64):
     n_local = min(n_local, w.px * w.py)
     est, sample_s, nsub, _ = cpu_sample(w, iters, n_local)
-    return {"value": round(est, 3), "unit": "s", "cores": 1, "kind": "oracle",
+    return {"value": round(est, 3), "unit": "s", "cores": 1, "kind": "oracle", **host_cpus(),
             "sample": (f"oracle on {w.name}: global assembly, load vector, one SpMV, one norm and one modified "
                        f"Gram-Schmidt step on the full mesh; local assembly + SuperLU factor + one local apply "
                        f"(gather, solve, weighted scatter) on {n_local} of {nsub} subdomains (scaled x{nsub / n_local:g}); "
@@ -220,7 +226,7 @@ def cpu_batch_baseline(probs, iters):
     q = int(np.argsort(n)[len(n) // 2])
     est_q, sample_s, nsub, _ = cpu_sample(probs[q], int(it[q]))
     est = est_q * float(np.sum(n * (it + 1)) / (n[q] * (it[q] + 1)))
-    return {"value": round(est, 3), "unit": "s", "cores": 1, "kind": "oracle",
+    return {"value": round(est, 3), "unit": "s", "cores": 1, "kind": "oracle", **host_cpus(),
             "sample": (f"oracle cpu_sample on {probs[q].name} ({int(n[q])} unknowns, {nsub} subdomains, "
                        f"{int(it[q])} directions; {sample_s:.1f} s of CPU work, one thread), scaled to all "
                        f"{len(probs)} problems by unknowns x (directions + 1)")}
