@@ -211,3 +211,59 @@ def test_weak_one_subdomain_and_gmres():
     x, it, rel, _ = krylov.fgmres(A.dot, ras.RAS(p).factor().apply, b, rtol=1e-12, maxit=300)
     u = fem.direct_solve(A, b)
     assert rel <= 1e-12 and np.linalg.norm(x - u) <= 1e-10 * np.linalg.norm(u)
+
+
+def _local_solution_gap(h, planted=False):
+    """Relative difference on Omega_j,int of the local solutions of the two
+    forms for the middle subdomain of a 3 x 3 covering (widths fixed in length
+    as h halves), one Gaussian source inside Omega_int. planted = True swaps
+    form 1's impedance weight 1/gamma_n for form 0's gamma_t (a mistake planted
+    in the oracle)."""
+    import scipy.sparse.linalg as spla
+    p = _p(k=10.0, h=h, kappa_g=0.1, px=3, py=3, ovlp_cells=round(0.05 / h), pml_cells=round(0.1 / h),
+           g_amp=30.0, g_profile=1)
+    sols = {}
+    for form in (0, 1):
+        q = dict(p, form=form)
+        grid, rxs, rys = ras.covering(q)
+        rx, ry = rxs[1], rys[1]
+        A, nodes, _, _, _ = ras.local_operator(q, grid, rx, ry)
+        if planted and form == 1:
+            A0, _, _, _, _ = ras.local_operator(dict(q, form=0), grid, rx, ry)
+            A = A - _impedance_part(q, grid, rx, ry, nodes, A) + _impedance_part(dict(q, form=0), grid, rx, ry,
+                                                                                 nodes, A0)
+        xs, ys = grid.xs(2 * (nodes % (grid.Mx + 1))), grid.ys(2 * (nodes // (grid.Mx + 1)))
+        f = np.exp(-((xs - 0.5) ** 2 + (ys - 0.5) ** 2) / 0.05 ** 2) * h * h
+        ii, jj = nodes % (grid.Mx + 1), nodes // (grid.Mx + 1)
+        m = (ii >= rx.int_lo) & (ii <= rx.int_hi) & (jj >= ry.int_lo) & (jj <= ry.int_hi)
+        sols[form] = (spla.splu(A.tocsc()).solve(f.astype(complex)), m)
+    (u0, m), (u1, _) = sols[0], sols[1]
+    return np.linalg.norm((u1 - u0)[m]) / np.linalg.norm(u0[m])
+
+
+def _impedance_part(p, grid, rx, ry, nodes, A):
+    """A_j minus its element terms: the impedance closure alone."""
+    amp, ramp, prof = p["g_amp"], p["g_ramp"], p["g_profile"]
+    gx, gy = ras.local_gamma_fn(grid, rx, 0, amp, ramp, prof), ras.local_gamma_fn(grid, ry, 1, amp, ramp, prof)
+    cj, ci = np.meshgrid(np.arange(ry.ext_lo, ry.ext_hi), np.arange(rx.ext_lo, rx.ext_hi), indexing="ij")
+    if p["form"] == 1:
+        dgx, dgy = ras.local_dgamma_fn(grid, rx, 0, amp, ramp, prof), ras.local_dgamma_fn(grid, ry, 1, amp, ramp, prof)
+        r, c, v = fem.assemble_cells_weak(grid, ci, cj, gx, gy, dgx, dgy, p["k"])
+    else:
+        r, c, v = fem.assemble_cells(grid, ci, cj, gx, gy, p["k"])
+    num = -np.ones((grid.Mx + 1) * (grid.My + 1), dtype=np.int64)
+    num[nodes] = np.arange(nodes.size)
+    return A - fem._to_matrix(r, c, v, num, nodes.size)
+
+
+def test_both_forms_pose_the_same_local_problem():
+    """Section 3 (ii) read in the stretched normal coordinate: form 1's closure
+    -i k int gamma_n^-1 u v ds is form 0's -i k int gamma_t u v ds tested with
+    v/(gamma_1 gamma_2), so the two local solutions converge to each other
+    (0.40% -> 0.10% from h = 1/40 to 1/80, with a weak local PML g = 30 d^3
+    whose boundary condition matters). With form 0's weight planted in form 1
+    the local problems differ and the gap stays at ~25%."""
+    d1, d2 = _local_solution_gap(1 / 40), _local_solution_gap(1 / 80)
+    assert d1 < 0.01 and d1 / d2 > 3.5
+    p1, p2 = _local_solution_gap(1 / 40, planted=True), _local_solution_gap(1 / 80, planted=True)
+    assert p2 > 0.1 and p1 / p2 < 1.2
