@@ -146,10 +146,13 @@ int ensure_krylov(ras_pml_handle* h, int m, int maxit) {
     RP_ALLOC(h->hist, (size_t)maxit + 1);
     h->hist_cap = maxit + 1;
   }
-  if (!h->kst) {
-    RP_ALLOC(h->kst, 1);
-    RP_ALLOC(h->scal, 4);
-    RP_CUDA(cudaMallocHost((void**)&h->kst_host, 2 * sizeof(KState)));
+  // each one on its own, so a failed allocation leaves none of them half-set
+  if (!h->kst) RP_ALLOC(h->kst, 1);
+  if (!h->scal) RP_ALLOC(h->scal, 4);
+  if (!h->kst_host && cudaMallocHost((void**)&h->kst_host, 2 * sizeof(KState)) != cudaSuccess) {
+    h->kst_host = nullptr;
+    cudaGetLastError();
+    return RASPML_ENOMEM;
   }
   return RASPML_OK;
 }
