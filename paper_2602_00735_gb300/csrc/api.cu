@@ -508,11 +508,11 @@ int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, i
 int ras_pml_attach_net(ras_pml_handle* h, ras_pml_net* net) {
   if (!h) return RASPML_EBADARG;
   if (net && (rp::net_grid(net) > h->geo.nx || rp::net_grid(net) > h->geo.ny)) return RASPML_EBADARG;
-  if (net && !h->lc) {
+  if (net) {   // each buffer on its own: a failed allocation leaves none half-set
     cudaSetDevice(h->dev);
-    RP_ALLOC(h->lc, (size_t)h->n);
-    RP_ALLOC(h->lac, (size_t)h->n);
-    RP_ALLOC(h->lhv, (size_t)2);
+    if (!h->lc) RP_ALLOC(h->lc, (size_t)h->n);
+    if (!h->lac) RP_ALLOC(h->lac, (size_t)h->n);
+    if (!h->lhv) RP_ALLOC(h->lhv, (size_t)2);
   }
   h->net = net;
   return RASPML_OK;
@@ -787,10 +787,8 @@ int helmholtz_solve_host(ras_pml_handle* h, const rp_c128* b_host, rp_c128* x_ho
                          int restart, int* iters, double* relres) {
   if (!h || !b_host || !x_host) return RASPML_EBADARG;
   cudaSetDevice(h->dev);
-  if (!h->tmp_b) {
-    RP_ALLOC(h->tmp_b, (size_t)h->n);
-    RP_ALLOC(h->tmp_x, (size_t)h->n);
-  }
+  if (!h->tmp_b) RP_ALLOC(h->tmp_b, (size_t)h->n);
+  if (!h->tmp_x) RP_ALLOC(h->tmp_x, (size_t)h->n);
   const size_t bytes = sizeof(c128) * h->n;
   RP_CUDA(cudaMemcpyAsync(h->tmp_b, b_host, bytes, cudaMemcpyHostToDevice, h->st));
   RP_CUDA(cudaMemcpyAsync(h->tmp_x, x_host, bytes, cudaMemcpyHostToDevice, h->st));
