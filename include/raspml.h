@@ -237,7 +237,7 @@ int ras_pml_history(const ras_pml_handle* h, double* hist_host, int cap, int* co
  * CUDA events recorded on the handle's stream (recorded only while timing is
  * enabled with ras_pml_set_timing; disabled by default). */
 typedef struct {
-  double factor_ms;       /* local assembly + LDL^T factorisation              */
+  double factor_ms;       /* local assembly + factorisation (L D L^T; L D U with form 1) */
   double solve_ms;        /* whole helmholtz_solve, first launch to last       */
   double apply_ms;        /* sum over the solve's applies of B^-1              */
   double spmv_ms;         /* sum over the solve's A z products                 */
