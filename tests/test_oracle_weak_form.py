@@ -267,3 +267,20 @@ def test_both_forms_pose_the_same_local_problem():
     assert d1 < 0.01 and d1 / d2 > 3.5
     p1, p2 = _local_solution_gap(1 / 40, planted=True), _local_solution_gap(1 / 80, planted=True)
     assert p2 > 0.1 and p1 / p2 < 1.2
+
+
+def test_tables_1_2_ordering_in_the_papers_own_form():
+    """Section 4, Tables 1-2, on the paper's set-up (g = 10 k x^3, a
+    three-wavelength global PML, h = 1/(2k), the smoothed delta) in eq. weak as
+    printed: RAS-PML-Imp needs no more iterations than RAS-PML-Drch, and both
+    fewer than RAS-Imp (k = 160, 5 x 5 boxes of 64 cells: 28, 29, 44)."""
+    its = {}
+    for name, kw in (("imp", dict(local_bc=0)), ("drch", dict(local_bc=1)),
+                     ("ras_imp", dict(local_bc=0, pml=False))):
+        w = workloads.paper_setup(160, 64, C_delta=1 / 6, C_kappa=3 / 8, **kw).with_(form=1)
+        p = w.params()
+        grid, A = fem.assemble_global(p)
+        b = fem.assemble_rhs(p, w.centres, w.amps, w.width)
+        x, its[name], rel, _ = krylov.fgmres(A.dot, ras.RAS(p).factor().apply, b, rtol=1e-10, maxit=300)
+        assert rel <= 1e-10
+    assert its["imp"] <= its["drch"] < its["ras_imp"], its
