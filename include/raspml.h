@@ -153,6 +153,11 @@ int ras_pml_setup(const ras_pml_params* params, void* cuda_stream,
 /* Fills *info (host struct). */
 int ras_pml_info(const ras_pml_handle* h, ras_pml_info_t* info);
 
+/* *n = number of global unknowns, (Mx-1)*(My-1): the interior nodes of the
+ * mesh of Omega (Section 1, u in H^1_0), x fastest; the length of every
+ * _dev vector of the handle. Host-only; RASPML_EBADARG on NULL arguments. */
+int ras_pml_num_unknowns(const ras_pml_handle* h, int64_t* n);
+
 /* Load vector F_i = int f phi_i (Section 1) of
  *   f(x) = sum_s amps[s] * exp(-|x - c_s|^2 / width^2) cut to Omega_int,
  * with c_s = (centres[2s], centres[2s+1]); centres and amps are host arrays of

@@ -12,7 +12,7 @@ OK, NOT_CONVERGED = 0, 1
 ERRORS = {-1: "EBADARG", -2: "ENOMEM", -3: "ECUDA", -4: "EPIVOT", -5: "ENAN", -6: "ETIMEOUT", -7: "ESTATE"}
 
 #: every entry point declared in include/raspml.h
-SYMBOLS = ("ras_pml_setup", "ras_pml_info", "ras_pml_assemble_rhs", "ras_pml_assemble_rhs_noalloc",
+SYMBOLS = ("ras_pml_setup", "ras_pml_info", "ras_pml_num_unknowns", "ras_pml_assemble_rhs", "ras_pml_assemble_rhs_noalloc",
            "ras_pml_factor", "ras_pml_apply",
            "ras_pml_matvec", "helmholtz_solve", "helmholtz_solve_host", "ras_pml_richardson",
            "ras_pml_history", "ras_pml_set_timing", "ras_pml_get_timing", "ras_pml_error_string",
@@ -83,6 +83,7 @@ def load() -> ctypes.CDLL:
     H = c_void_p
     lib.ras_pml_setup.argtypes = [POINTER(Params), c_void_p, POINTER(c_void_p)]
     lib.ras_pml_info.argtypes = [H, POINTER(Info)]
+    lib.ras_pml_num_unknowns.argtypes = [H, POINTER(c_int64)]
     lib.ras_pml_assemble_rhs.argtypes = [H, c_void_p, c_void_p, c_int, c_double, c_void_p]
     lib.ras_pml_assemble_rhs_noalloc.argtypes = [H, c_void_p, c_void_p, c_int, c_double, c_void_p]
     lib.ras_pml_factor.argtypes = [H]

@@ -358,6 +358,12 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   return RASPML_OK;
 }
 
+int ras_pml_num_unknowns(const ras_pml_handle* h, int64_t* n) {
+  if (!h || !n) return RASPML_EBADARG;
+  *n = h->n;
+  return RASPML_OK;
+}
+
 int ras_pml_info(const ras_pml_handle* h, ras_pml_info_t* info) {
   if (!h || !info) return RASPML_EBADARG;
   std::memset(info, 0, sizeof(*info));

@@ -77,6 +77,7 @@ def test_error_strings_and_null_handling(lib):
     assert lib.ras_pml_setup(None, None, None) == -1
     assert lib.ras_pml_apply(None, None, None) == -1
     assert lib.ras_pml_tune(None, None) == -1
+    assert lib.ras_pml_num_unknowns(None, None) == -1
     assert lib.ras_pml_batch_setup(None, 1, None, None) == -1
     assert lib.ras_pml_batch_solve(None, None, None, 1e-6, 10, 0, None, None) == -1
     assert lib.ras_pml_batch_apply(None, None, None) == -1
