@@ -284,3 +284,26 @@ def test_tables_1_2_ordering_in_the_papers_own_form():
         x, its[name], rel, _ = krylov.fgmres(A.dot, ras.RAS(p).factor().apply, b, rtol=1e-10, maxit=300)
         assert rel <= 1e-10
     assert its["imp"] <= its["drch"] < its["ras_imp"], its
+
+
+@pytest.mark.parametrize("profile,amp", [(0, 20.0), (1, 30.0)])
+def test_local_dgamma_is_the_derivative_of_the_local_stretch(profile, amp):
+    """Section 2's local stretching restarts beyond an interior side of
+    Omega_j,int (g(x - b_j) above, -g(a_j - x) below): a central difference of
+    gamma_j along each axis matches gamma_j', below, inside and above."""
+    p = _w("tiny3", g_profile=profile, g_amp=amp).params()
+    grid, rxs, rys = ras.covering(p)
+    rx, ry = rxs[1], rys[1]
+    hh, e = 0.5 * grid.h, 1e-4
+    for axis, r in ((0, rx), (1, ry)):
+        gam = ras.local_gamma_fn(grid, r, axis, p["g_amp"], p["g_ramp"], profile)
+        dgam = ras.local_dgamma_fn(grid, r, axis, p["g_amp"], p["g_ramp"], profile)
+        pts = [2 * r.int_lo - 1.3, 2 * r.int_lo - 0.4, r.int_lo + r.int_hi + 0.5, 2 * r.int_hi + 0.4,
+               2 * r.int_hi + 1.3]
+        checked = 0
+        for s in pts:
+            fd = (gam(s + e) - gam(s - e)) / (2 * e * hh)
+            d = dgam(s)
+            assert abs(fd - d) <= 1e-5 * max(1.0, abs(d)), (axis, s, fd, d)
+            checked += abs(d) > 0
+        assert checked >= 4     # the points beyond both sides carry a nonzero derivative
