@@ -27,10 +27,14 @@ batch(name) returns a list of independent problems for the batched form:
        with s uniform in [0.5, 1.5] and the same PML of width 0.1; about 16
        points per wavelength (h = (s + 0.2)/M, M = round((s + 0.2) 16 k / 2 pi));
        overlap and local PML width 0.5*ln(k)/k in cells; px and py drawn
-       independently from 2..12, within the range where a subdomain's
-       half-bandwidth stays <= 232 and a box holds at least two overlaps;
-       1..8 Gaussian sources (width 0.4*pi/k, amplitude 1) uniform in
-       Omega_int. All draws from numpy's default_rng(seed).
+       independently and uniformly from 2..12; 1..8 Gaussian sources (width
+       0.4*pi/k, amplitude 1) uniform in Omega_int. All draws from numpy's
+       default_rng(seed). A drawn grid whose boxes could not hold the two
+       overlap strips (fewer than 2*overlap cells) raises instead of being
+       redrawn; seed 3 draws none.
+  c3small  8 problems of the same construction at k in [8*pi, 24*pi] (test
+       size); there px, py are drawn from 2 up to the largest count whose
+       boxes hold the two overlap strips.
 """
 from __future__ import annotations
 
@@ -165,23 +169,16 @@ def get(name: str) -> Workload:
 
 NAMES = ("c0", "c1", "c2", "c4", "tiny", "tiny3", "small", "mid")
 
-#: largest local half-bandwidth of the complex64 factor window
-BAND_LIMIT = 232
-
-
-def _grid_range(M: int, w: int) -> tuple[int, int]:
-    """Subdomain counts P in 2..12 for M cells with overlap and PML width w:
-    every box holds at least 2w cells (floor(M/P) >= 2w) and the widest
-    subdomain, ceil(M/P) + 4w + 1 nodes, keeps b <= BAND_LIMIT."""
-    lo = 2
-    while lo <= 12 and -(-M // lo) + 4 * w + 2 > BAND_LIMIT:
-        lo += 1
-    hi = 12
+def _max_boxes(M: int, w: int, cap: int = 12) -> int:
+    """The largest box count P <= cap whose boxes (floor(M/P) cells or more)
+    hold the two overlap strips of w cells each: the covering's own
+    requirement, independent of any kernel."""
+    hi = cap
     while hi >= 2 and M // hi < 2 * w:
         hi -= 1
-    if lo > hi:
-        raise ValueError(f"no subdomain grid in 2..12 fits M={M}, w={w}")
-    return lo, hi
+    if hi < 2:
+        raise ValueError(f"no subdomain grid of 2 or more boxes fits M={M}, w={w}")
+    return hi
 
 
 def _batch_c3(count=64, seed=3, name="c3") -> list:
@@ -194,8 +191,9 @@ def _batch_c3(count=64, seed=3, name="c3") -> list:
         M = int(round(L * 16 * k / (2 * math.pi)))
         h = L / M
         w = width_cells(k, h)
-        lo, hi = _grid_range(M, w)
-        px, py = (int(v) for v in rng.integers(lo, hi + 1, size=2))
+        px, py = (int(v) for v in rng.integers(2, 13, size=2))
+        if M // max(px, py) < 2 * w:
+            raise ValueError(f"{name}-{q}: {px}x{py} boxes of {M} cells cannot hold two overlaps of {w} cells")
         ns = int(rng.integers(1, 9))
         centres = rng.uniform(0.0, side, size=(ns, 2))
         out.append(Workload(name=f"{name}-{q}", k=k, x0=0.0, y0=0.0, x1=side, y1=side, kappa_g=0.1, h=h,
@@ -220,8 +218,8 @@ def batch(name: str) -> list:
             M = int(round(L * 16 * k / (2 * math.pi)))
             h = L / M
             w = width_cells(k, h)
-            lo, hi = _grid_range(M, w)
-            px, py = (int(v) for v in rng.integers(lo, hi + 1, size=2))
+            hi = _max_boxes(M, w)
+            px, py = (int(v) for v in rng.integers(2, hi + 1, size=2))
             ns = int(rng.integers(1, 9))
             out.append(Workload(name=f"c3small-{q}", k=k, x0=0.0, y0=0.0, x1=side, y1=side, kappa_g=0.1, h=h,
                                 px=px, py=py, ovlp_cells=w, pml_cells=w,
