@@ -251,6 +251,11 @@ typedef struct {
   int32_t reorths;        /* second Gram-Schmidt passes taken (ortho = 1)      */
   int32_t launches;       /* kernels the solve launched, including those that
                              returned at once after convergence               */
+  int32_t learned_dirs;   /* directions the learned stage corrected before its
+                             gate closed (0 without a network); filled whether
+                             or not timing is enabled                         */
+  double learned_gain;    /* largest fraction of a residual's squared norm one
+                             learned correction removed                       */
 } ras_pml_timing_t;
 
 /* Enables (1) or disables (0) event timing on the handle. */
@@ -258,6 +263,26 @@ int ras_pml_set_timing(ras_pml_handle* h, int enable);
 
 /* Fills *t (host struct) for the last factor and solve. */
 int ras_pml_get_timing(const ras_pml_handle* h, ras_pml_timing_t* t);
+
+/* Failure injection for the device-side time-out path (failure detection;
+ * the paper has no counterpart). Sets, for the current
+ * device and every later launch on it, the limit in SM clock cycles of the
+ * apply kernels' waits for their bulk copies of factor columns; cycles <= 0
+ * restores the default (2^31 cycles, about a second); cycles = 1 makes every
+ * such wait give up at its first check. With a limit shorter than a copy
+ * takes, a warp's wait gives up: the warp records the time-out,
+ * waits for its own copies still in flight with the default limit, and
+ * returns, and the solve or apply reports RASPML_ETIMEOUT; the context stays
+ * usable. A later ras_pml_factor clears the recorded time-out. Not for
+ * production use; -3 if the device variable cannot be written. */
+int ras_pml_set_copy_wait_limit(long long cycles);
+
+/* Throughput of the FP64 (fp64 = 1) or FP32 (fp64 = 0) fused multiply-add
+ * pipes of the current device, in TFLOP/s (2 flops per FMA), from a
+ * microbenchmark of independent FMA chains on every SM timed with CUDA events:
+ * the ALU roofline of the kernels whose arithmetic, not memory, bounds them.
+ * The paper has no counterpart. Synchronises the device; -3 on a CUDA error. */
+int ras_pml_fma_peak(int fp64, double* tflops);
 
 /* Human-readable text for a status code (static storage). */
 const char* ras_pml_error_string(int status);
@@ -461,8 +486,13 @@ void ras_pml_net_destroy(ras_pml_net* net);
  * residual r1 = v_j - A z1 described above, and alpha = <A c, r1> / ||A c||^2
  * the step that minimises ||r1 - alpha A c|| (so the stage never increases
  * that residual); the flexible GMRES absorbs the nonlinearity. Costs two
- * more SpMVs and two inner products per direction. The net must live as long as it is attached; Nc must not
- * exceed the unknowns per grid row or column. */
+ * more SpMVs and three inner products per direction. The stage is gated:
+ * once it has corrected 4 directions of a solve without removing 5% of
+ * ||r1||^2 in any of them, the solve stops issuing it (the host sees this one
+ * batch of four directions late), so a stage that does not help costs about
+ * eight directions' worth of its kernels; ras_pml_get_timing reports the
+ * directions it corrected and its largest gain. The net must live as long
+ * as it is attached; Nc must not exceed the unknowns per grid row or column. */
 int ras_pml_attach_net(ras_pml_handle* h, ras_pml_net* net);
 /* z += c(r): the learned correction of a fine residual r on the handle's
  * grid (n complex128 each, device, not overlapping). Synchronises. */

@@ -23,7 +23,8 @@ SYMBOLS = ("ras_pml_setup", "ras_pml_info", "ras_pml_num_unknowns", "ras_pml_ass
            "ras_pml_net_create", "ras_pml_net_param_count", "ras_pml_net_set_params", "ras_pml_net_get_params",
            "ras_pml_net_forward", "ras_pml_net_loss_grad", "ras_pml_net_adam_step", "ras_pml_net_set_gamma",
            "ras_pml_net_get_gamma", "ras_pml_net_train", "ras_pml_net_destroy", "ras_pml_attach_net",
-           "ras_pml_get_params", "ras_pml_net_correct")
+           "ras_pml_get_params", "ras_pml_net_correct", "ras_pml_set_copy_wait_limit",
+           "ras_pml_fma_peak")
 VOID_SYMBOLS = ("ras_pml_error_string", "ras_pml_destroy", "ras_pml_batch_destroy", "ras_pml_net_destroy",
                 "ras_pml_net_get_gamma")
 
@@ -48,7 +49,7 @@ class Info(ctypes.Structure):
 class Timing(ctypes.Structure):
     _fields_ = [("factor_ms", c_double), ("solve_ms", c_double), ("apply_ms", c_double),
                 ("spmv_ms", c_double), ("ortho_ms", c_double), ("applies", c_int32), ("reorths", c_int32),
-                ("launches", c_int32)]
+                ("launches", c_int32), ("learned_dirs", c_int32), ("learned_gain", c_double)]
 
 
 class TuneReport(ctypes.Structure):
@@ -95,6 +96,8 @@ def load() -> ctypes.CDLL:
     lib.ras_pml_richardson.argtypes = [H, c_void_p, c_void_p, c_double, c_int, POINTER(c_int), POINTER(c_double)]
     lib.ras_pml_history.argtypes = [H, c_void_p, c_int, POINTER(c_int)]
     lib.ras_pml_set_timing.argtypes = [H, c_int]
+    lib.ras_pml_set_copy_wait_limit.argtypes = [ctypes.c_longlong]
+    lib.ras_pml_fma_peak.argtypes = [c_int, POINTER(c_double)]
     lib.ras_pml_get_timing.argtypes = [H, POINTER(Timing)]
     lib.ras_pml_error_string.argtypes = [c_int]
     lib.ras_pml_error_string.restype = ctypes.c_char_p

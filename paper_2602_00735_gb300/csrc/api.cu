@@ -28,6 +28,8 @@ struct ras_pml_handle {
   std::vector<SubDesc> subs_h;
   SubDesc* subs_d = nullptr;
   int nsub = 0, max_b = 0, max_bp = 0, max_npad = 0, max_n = 0;
+  int nwslot = 0;                // subdomains of the wide-band factor (b > max_band)
+  rp::BandSplit split{};         // the widest of the other subdomains (no band order here)
   long long n = 0, sum_npad = 0, sum_l = 0, sum_n = 0, sum_bn = 0;
   c128 *D = nullptr, *CW = nullptr, *CS = nullptr, *CSW = nullptr;
   c128 *CE = nullptr, *CN = nullptr, *CNE = nullptr;   // form 1: the couplings symmetry no longer gives
@@ -75,12 +77,15 @@ constexpr double kC64BasisFloor = 1e-6;
 
 // y = A x, or y = bsub - A x: the four-array product of the symmetric form
 // (form 0) or the seven-array one of eq. weak as printed (form 1)
+// y = A x or bsub - A x in FP64; x in double-float form with xdf (form 0)
 cudaError_t spmv_A(const ras_pml_handle* h, const c128* x, const c128* bsub, c128* y, const rp::KState* kst,
-                   cudaStream_t st, int bkind = rp::RK_C128) {
-  if (h->p.form == 1)
+                   cudaStream_t st, int bkind = rp::RK_C128, int xdf = 0) {
+  if (h->p.form == 1) {
+    if (xdf) return cudaErrorInvalidValue;
     return rp::launch_spmv7(h->n, h->geo.nx, rp::Stencil7{h->D, h->CW, h->CE, h->CS, h->CN, h->CSW, h->CNE}, x,
                             bsub, y, kst, st, bkind);
-  return rp::launch_spmv(h->n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, x, bsub, y, kst, st, bkind);
+  }
+  return rp::launch_spmv(h->n, h->geo.nx, h->D, h->CW, h->CS, h->CSW, x, bsub, y, kst, st, bkind, xdf);
 }
 
 int ensure_events(ras_pml_handle* h, int count) {
@@ -182,7 +187,8 @@ int build_problem(const ras_pml_params& p, int prob, Geo& g, std::vector<SubDesc
       (p.factor_prec < 0 || p.factor_prec > 2) || (p.ortho < 0 || p.ortho > 4) || (p.g_profile != 0 && p.g_profile != 1) ||
       (p.form != 0 && p.form != 1) || (p.form == 1 && p.ortho > 2))
     return RASPML_EBADARG;
-  const int band_limit = p.form == 1 ? max_band_lu(p.factor_prec) : max_band(p.factor_prec);
+  // form 0: shared-memory window up to max_band, blocked wide kernel beyond
+  const int band_limit = p.form == 1 ? max_band_lu(p.factor_prec) : kMaxBandWide;
   const double lx = p.x1 - p.x0 + 2 * p.kappa_g, ly = p.y1 - p.y0 + 2 * p.kappa_g;
   const long long Mx = std::llround(lx / p.h), My = std::llround(ly / p.h);
   if (Mx < 2 || My < 2 || std::fabs(Mx * p.h - lx) > 1e-9 * lx || std::fabs(My * p.h - ly) > 1e-9 * ly ||
@@ -306,6 +312,7 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   h->nsub = (int)h->subs_h.size();
   h->sum_npad = v_off;
   h->sum_l = l_off;
+  h->nwslot = rp::assign_wide_slots(h->subs_h, h->p.factor_prec, &h->split.max_b_narrow);
 
   int s;
 #define SETUP_ALLOC(ptr, cnt) \
@@ -422,6 +429,11 @@ int ras_pml_factor(ras_pml_handle* h) {
   const bool weak = h->p.form == 1;   // seven couplings per local row, L D U factors
   c128* Aloc = nullptr;
   RP_ALLOC(Aloc, (size_t)(weak ? 7 : 4) * h->sum_npad);
+  void* wscratch = nullptr;
+  if (const int sw = rp::alloc_wide_scratch(&wscratch, h->nwslot, h->p.factor_prec, h->max_b); sw != RASPML_OK) {
+    cudaFree(Aloc);
+    return sw;
+  }
   if (h->timing) {
     int es_ = ensure_events(h, 2);
     if (es_) return es_;
@@ -437,14 +449,15 @@ int ras_pml_factor(ras_pml_handle* h) {
                                h->pivstats, h->status, h->st);
   }
   if (e == cudaSuccess && !weak)
-    e = rp::launch_local_rows(h->p.factor_prec, h->geo_d, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
+    e = rp::launch_local_rows(h->p.factor_prec, h->geo_d, h->subs_d, h->nsub, h->max_npad, h->max_b, Aloc, h->st);
   if (e == cudaSuccess && !weak)
     e = rp::launch_factor(h->p.factor_prec, h->tune.factor_threads, h->tune.factor_rank, h->subs_d, h->nsub, h->max_b, Aloc, h->L, h->Lrev, h->dinv,
-                          h->pivstats, h->status, h->st);
+                          h->pivstats, h->status, h->st, h->split, wscratch);
   if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[1], h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e == cudaSuccess && h->timing) h->tm.factor_ms = ev_ms(h->ev[0], h->ev[1]);
   cudaFree(Aloc);
+  if (wscratch) cudaFree(wscratch);
   if (e != cudaSuccess) {
     std::fprintf(stderr, "raspml: factor: %s\n", cudaGetErrorString(e));
     return RASPML_ECUDA;
@@ -489,21 +502,31 @@ int ras_pml_tune(ras_pml_handle* h, ras_pml_tune_t* report) {
   if ((s = dalloc(&r, (size_t)h->n)) != RASPML_OK) { dfree(Aloc); return s; }
   cudaError_t e = cudaMemsetAsync(r, 0, sizeof(c128) * h->n, h->st);
   if (e == cudaSuccess)
-    e = rp::launch_local_rows(h->p.factor_prec, h->geo_d, h->subs_d, h->nsub, h->max_npad, Aloc, h->st);
+    e = rp::launch_local_rows(h->p.factor_prec, h->geo_d, h->subs_d, h->nsub, h->max_npad, h->max_b, Aloc, h->st);
   if (e != cudaSuccess) {
     dfree(Aloc); dfree(r);
     return RASPML_ECUDA;
   }
+  void* wscratch = nullptr;
+  if ((s = rp::alloc_wide_scratch(&wscratch, h->nwslot, h->p.factor_prec, h->max_b)) != RASPML_OK) {
+    dfree(Aloc); dfree(r);
+    return s;
+  }
   rp::TuneTarget t{h->p.factor_prec, h->geo_d, h->subs_d, h->nsub, h->max_b, h->max_bp, h->max_npad, h->sum_npad,
-                   h->sum_l, Aloc, h->L, h->Lrev, h->dinv, h->Y, h->pivstats, h->status, r, h->st};
+                   h->sum_l, Aloc, h->L, h->Lrev, h->dinv, h->Y, h->pivstats, h->status, r, h->st, h->split,
+                   wscratch};
   s = rp::tune_shapes(t, 3, &h->tune, report);
   cudaStreamSynchronize(h->st);
   dfree(Aloc); dfree(r);
+  if (wscratch) cudaFree(wscratch);
   return s;
 }
 
 int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, int apply_cols) {
-  if (!h || !rp::factor_shape_valid(h->p.factor_prec, h->max_b, factor_threads, factor_rank) || !rp::apply_cols_valid(h->p.factor_prec, apply_cols))
+  if (!h ||
+      !rp::factor_shape_valid(h->p.factor_prec, rp::narrow_band(h->p.factor_prec, h->max_b, h->split), factor_threads,
+                              factor_rank) ||
+      !rp::apply_cols_valid(h->p.factor_prec, apply_cols))
     return RASPML_EBADARG;
   h->tune.factor_threads = factor_threads;
   h->tune.factor_rank = factor_rank;
@@ -518,7 +541,7 @@ int ras_pml_attach_net(ras_pml_handle* h, ras_pml_net* net) {
     cudaSetDevice(h->dev);
     if (!h->lc) RP_ALLOC(h->lc, (size_t)h->n);
     if (!h->lac) RP_ALLOC(h->lac, (size_t)h->n);
-    if (!h->lhv) RP_ALLOC(h->lhv, (size_t)2);
+    if (!h->lhv) RP_ALLOC(h->lhv, (size_t)3);
   }
   h->net = net;
   return RASPML_OK;
@@ -531,6 +554,11 @@ int ras_pml_net_correct(ras_pml_handle* h, ras_pml_net* net, const rp_c128* r, r
   const int s = rp::net_correct(net, (const c128*)r, (c128*)z, h->geo.nx, h->geo.ny, nullptr, h->st);
   if (s != RASPML_OK) return s;
   RP_CUDA(cudaStreamSynchronize(h->st));
+  return RASPML_OK;
+}
+
+int ras_pml_set_copy_wait_limit(long long cycles) {
+  RP_CUDA(rp::set_copy_wait_limit(cycles));
   return RASPML_OK;
 }
 
@@ -612,9 +640,18 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
   double rel = NAN;
   const bool dfbasis = h->p.ortho == 3;   // V stored in double-float form
   const bool c64basis = h->p.ortho == 4;  // V stored as complex64, w in its own buffer
-  // z_j in double-float form (prolongation to SpMV and to x += Z y); not with
-  // the learned stage, which updates z_j in complex128
-  const int zdf = (c64basis && h->Ddf && !h->net && h->p.factor_prec >= 1) ? 1 : 0;
+  // z_j in double-float form (prolongation to SpMV and to x += Z y), and w
+  // with it through the step
+  const int zdf = ((c64basis && h->p.factor_prec >= 1) || dfbasis) && h->Ddf ? 1 : 0;
+  // The learned stage is gated: once it has corrected kGateDirs directions
+  // without removing kGateGain of a residual's squared norm in any of them,
+  // the host stops issuing it for the rest of the solve (read one batch late,
+  // like the stop flag), so a stage that does not help costs a few
+  // directions' worth of its kernels.
+  constexpr int kGateDirs = 4;
+  constexpr double kGateGain = 0.05;
+  bool stage_on = h->net != nullptr;
+  long long staged = 0;   // directions the stage corrected (about 20 launches each)
   const int bkind = dfbasis ? rp::RK_DF : c64basis ? rp::RK_C64 : rp::RK_C128;
   c64* V64 = reinterpret_cast<c64*>(h->V);
   for (;;) {
@@ -659,10 +696,11 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
         if (h->timing) RP_CUDA(cudaEventRecord(evj[0], st));
         RP_CUDA(rp::launch_apply(h->p.factor_prec, h->tune.apply_cols, h->geo, h->geo_d, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev,
                                  h->dinv, vj, h->Y, zj, h->kst, h->status, st, bkind, zdf));
-        if (h->net) {
+        if (stage_on) {
+          ++staged;
           // learned stage: c = correction of r1 = v_j - A z_j (r1 held in w), then
           // z_j += alpha c with the alpha minimising ||r1 - alpha A c||
-          RP_CUDA(spmv_A(h, zj, vj, w, h->kst, st, bkind));
+          RP_CUDA(spmv_A(h, zj, vj, w, h->kst, st, bkind, zdf));
           RP_CUDA(cudaMemsetAsync(h->lc, 0, sizeof(c128) * n, st));
           const int cs = rp::net_correct(h->net, w, h->lc, h->geo.nx, h->geo.ny, h->kst, st);
           if (cs != RASPML_OK) return cs;
@@ -671,12 +709,14 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
           RP_CUDA(rp::launch_dots_finish(h->partial, 1, h->lhv, 0, h->kst, 0, st));
           RP_CUDA(rp::launch_dots(h->lac, n, 1, h->lac, n, h->partial, h->kst, 0, st));
           RP_CUDA(rp::launch_dots_finish(h->partial, 1, h->lhv + 1, 0, h->kst, 0, st));
-          RP_CUDA(rp::launch_mr_axpy(zj, h->lc, h->lhv, n, h->kst, st));
+          RP_CUDA(rp::launch_dots(w, n, 1, w, n, h->partial, h->kst, 0, st));
+          RP_CUDA(rp::launch_dots_finish(h->partial, 1, h->lhv + 2, 0, h->kst, 0, st));
+          RP_CUDA(rp::launch_mr_axpy(zj, h->lc, h->lhv, n, h->kst, st, zdf));
         }
         if (h->timing) RP_CUDA(cudaEventRecord(evj[1], st));
-        if (h->Ddf)   // with the complex64 basis, w stays in double-float form through the step
+        if (h->Ddf)   // with the complex64 basis or zdf, w stays in double-float form through the step
           RP_CUDA(rp::launch_spmv_df(n, h->geo.nx, h->Ddf, h->CWdf, h->CSdf, h->CSWdf, zj, w, h->kst, st,
-                                     c64basis ? 1 : 0, zdf));
+                                     (c64basis || zdf) ? 1 : 0, zdf));
         else
           RP_CUDA(spmv_A(h, zj, nullptr, w, h->kst, st));
         if (h->timing) RP_CUDA(cudaEventRecord(evj[2], st));
@@ -697,6 +737,15 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
           RP_CUDA(rp::launch_dots_c64b(V64, n, jj + 1, w, n, h->partial, h->kst, st, 1));
           RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, hcol, 0, h->kst, 0, st));
           RP_CUDA(rp::launch_axpys_c64b(V64, n, jj + 1, hcol, -1.0, w, n, h->kst, st, 1, h->partial, &nparts));
+          RP_CUDA(rp::launch_norm_finish(h->partial, &h->kst->hnorm, hcol + jj + 1, h->kst, 0, st, nparts));
+        } else if (dfbasis && zdf) {
+          // one pass against the double-float basis with w in double-float form
+          // (written so by the SpMV); the update also leaves the partial sums
+          // of ||w||^2; no FP64 per element
+          int nparts = 0;
+          RP_CUDA(rp::launch_dots_dfb(h->V, n, jj + 1, w, n, h->partial, h->kst, st));
+          RP_CUDA(rp::launch_dots_finish(h->partial, jj + 1, hcol, 0, h->kst, 0, st));
+          RP_CUDA(rp::launch_axpys_dfb(h->V, n, jj + 1, hcol, -1.0, w, n, h->kst, st, h->partial, &nparts));
           RP_CUDA(rp::launch_norm_finish(h->partial, &h->kst->hnorm, hcol + jj + 1, h->kst, 0, st, nparts));
         } else if (h->p.ortho == 3) {
           // one pass against the double-float basis, products and sums on the FP32 pipe
@@ -721,7 +770,9 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
         }
         RP_CUDA(rp::launch_givens(h->kst, h->H, ldh, h->cs, h->sn, h->gvec, jj, rtol, m, maxit, h->hist, st,
                                   c64basis ? kC64BasisFloor : 0.0));
-        if (dfbasis)
+        if (dfbasis && zdf)
+          RP_CUDA(rp::launch_scale_df_to_df(w, w, n, &h->kst->hnorm, h->kst, st));
+        else if (dfbasis)
           RP_CUDA(rp::launch_scale_to_df(w, n, &h->kst->hnorm, h->kst, st));
         else if (c64basis)
           RP_CUDA(rp::launch_scale_df_to_c64(w, V64 + (size_t)(jj + 1) * n, n, &h->kst->hnorm, h->kst, st));
@@ -734,6 +785,8 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
       if (pending >= 0) {
         if ((s = drain(pending, pending_nb))) return s;
         if (h->kst_host[pending].stop) stopped = true;
+        if (stage_on && h->kst_host[pending].ldirs >= kGateDirs && h->kst_host[pending].lgain < kGateGain)
+          stage_on = false;
       }
       pending = slot;
       pending_nb = nb;
@@ -768,8 +821,11 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
   // launches: ||b|| (2); per cycle: residual, norm (2), init, scale, backsolve,
   // update, true residual, norm (2) = 10; per issued direction: 13 (CGS twice)
   // or 17 (one pass, test, gated second pass)
-  launches += 10 * cycles + (h->p.ortho == 0 ? 13 : h->p.ortho == 3 ? 12 : h->p.ortho == 4 ? 11 : 17) * issued;
+  launches += 10 * cycles + (h->p.ortho == 0 ? 13 : h->p.ortho == 3 ? (zdf ? 11 : 12) : h->p.ortho == 4 ? 11 : 17) * issued;
+  launches += 20 * staged;
   h->tm.launches = (int32_t)launches;
+  h->tm.learned_dirs = h->kst_host->ldirs;
+  h->tm.learned_gain = h->kst_host->lgain;
   h->tm.applies = total;
   h->tm.reorths = h->p.ortho == 0 ? total : (h->p.ortho >= 3 ? 0 : h->kst_host->reorths);
   if (h->timing) {
@@ -921,7 +977,7 @@ extern "C" int ras_pml_assemble_rhs_noalloc(ras_pml_handle* h, const double* cen
                  kNoAllocMaxSources, ns);
     return RASPML_EBADARG;
   }
-  cudaSetDevice(h->dev);
+  RP_CUDA(cudaSetDevice(h->dev));
   double* table = nullptr;
   int s = noalloc_table(h->dev, &table);
   if (s != RASPML_OK) return s;

@@ -31,6 +31,7 @@ struct ras_pml_batch {
   std::vector<int> tile_prob_h, tile0_h, tile1_h;
   long long ntot = 0, sum_n = 0, sum_npad = 0, sum_l = 0, sum_bn = 0;
   int nsub = 0, max_b = 0, max_bp = 0, max_npad = 0, ntiles = 0;
+  int nwslot = 0;                   // subdomains of the wide-band factor (b > max_band)
   Geo* geos_d = nullptr;
   SubDesc* subs_d = nullptr;
   int *sub_index_d = nullptr, *tile_prob_d = nullptr, *tile0_d = nullptr, *tile1_d = nullptr;
@@ -262,6 +263,7 @@ int ras_pml_batch_setup(const ras_pml_params* params, int nprob, void* stream, r
   }
   h->sum_npad = v_off;
   h->sum_l = l_off;
+  h->nwslot = rp::assign_wide_slots(h->subs_h, h->prec, &h->split.max_b_narrow);
 
   int s;
 #define BS_ALLOC(ptr, cnt) \
@@ -410,7 +412,7 @@ int batch_alloc_factors(ras_pml_batch* h) {
 int batch_local_rows(ras_pml_batch* h, c128** Aloc) {
   int s = dalloc(Aloc, (size_t)4 * h->sum_npad);
   if (s != RASPML_OK) return s;
-  RP_CUDA(rp::launch_local_rows(h->prec, h->geos_d, h->subs_d, h->nsub, h->max_npad, *Aloc, h->st));
+  RP_CUDA(rp::launch_local_rows(h->prec, h->geos_d, h->subs_d, h->nsub, h->max_npad, h->max_b, *Aloc, h->st));
   return RASPML_OK;
 }
 
@@ -428,10 +430,16 @@ int ras_pml_batch_factor(ras_pml_batch* h) {
   c128* Aloc = nullptr;
   s = batch_local_rows(h, &Aloc);
   if (s != RASPML_OK) { dfree(Aloc); return s; }
+  void* wscratch = nullptr;
+  if ((s = rp::alloc_wide_scratch(&wscratch, h->nwslot, h->prec, h->max_b)) != RASPML_OK) {
+    dfree(Aloc);
+    return s;
+  }
   cudaError_t e = rp::launch_factor(h->prec, h->tune.factor_threads, h->tune.factor_rank, h->subs_d, h->nsub, h->max_b, Aloc, h->L,
-                                    h->Lrev, h->dinv, h->pivstats, h->status, h->st, h->split);
+                                    h->Lrev, h->dinv, h->pivstats, h->status, h->st, h->split, wscratch);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   dfree(Aloc);
+  if (wscratch) cudaFree(wscratch);
   if (e != cudaSuccess) {
     std::fprintf(stderr, "raspml: batch factor: %s\n", cudaGetErrorString(e));
     return RASPML_ECUDA;
@@ -465,9 +473,13 @@ int ras_pml_batch_tune(ras_pml_batch* h, ras_pml_tune_t* report) {
   if (s == RASPML_OK) s = dalloc(&r, (size_t)h->ntot);
   if (s == RASPML_OK && cudaMemsetAsync(r, 0, sizeof(c128) * h->ntot, h->st) != cudaSuccess) s = RASPML_ECUDA;
   if (s == RASPML_OK) {
+    void* wscratch = nullptr;
+    s = rp::alloc_wide_scratch(&wscratch, h->nwslot, h->prec, h->max_b);
     rp::TuneTarget t{h->prec, h->geos_d, h->subs_d, h->nsub, h->max_b, h->max_bp, h->max_npad, h->sum_npad,
-                     h->sum_l, Aloc, h->L, h->Lrev, h->dinv, h->Y, h->pivstats, h->status, r, h->st, h->split};
-    s = rp::tune_shapes(t, 3, &h->tune, report);
+                     h->sum_l, Aloc, h->L, h->Lrev, h->dinv, h->Y, h->pivstats, h->status, r, h->st, h->split,
+                     wscratch};
+    if (s == RASPML_OK) s = rp::tune_shapes(t, 3, &h->tune, report);
+    if (wscratch) cudaFree(wscratch);
   }
   cudaStreamSynchronize(h->st);
   dfree(Aloc);
@@ -476,7 +488,10 @@ int ras_pml_batch_tune(ras_pml_batch* h, ras_pml_tune_t* report) {
 }
 
 int ras_pml_batch_set_shapes(ras_pml_batch* h, int factor_threads, int factor_rank, int apply_cols) {
-  if (!h || !rp::factor_shape_valid(h->prec, h->max_b, factor_threads, factor_rank, h->split) || !rp::apply_cols_valid(h->prec, apply_cols))
+  if (!h ||
+      !rp::factor_shape_valid(h->prec, rp::narrow_band(h->prec, h->max_b, h->split), factor_threads, factor_rank,
+                              h->split) ||
+      !rp::apply_cols_valid(h->prec, apply_cols))
     return RASPML_EBADARG;
   h->tune.factor_threads = factor_threads;
   h->tune.factor_rank = factor_rank;

@@ -22,14 +22,23 @@
 //   problem's geometry (geos[prob]) and skips when that problem has stopped.
 // k_prolong: one thread per global unknown sums the (at most four) weighted
 //   local values that cover it, in a fixed order (bit-reproducible): in FP64
-//   into complex128, or, for complex64 local values, in double-float on the
-//   FP32 pipe into the double-float form (dfc) the Arnoldi SpMV reads.
+//   into complex128 (or split into the double-float form), or, for complex64
+//   local values, in double-float on the FP32 pipe into the double-float form
+//   (dfc) the Arnoldi SpMV reads.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace rp {
 
 namespace {
+
+// Limit of the waits for the ring's bulk copies, in SM clock cycles: the
+// default bound (about a second), or a smaller one set from the host to
+// inject a time-out (ras_pml_set_copy_wait_limit). The drain after a time-out
+// always waits with the default bound.
+__device__ long long g_copy_wait_limit = kWaitLimitCycles;
 
 // ring depth: 4 stages of 8 columns (a deeper ring for half-pair entries was
 // measured: no gain on c2, slower on c4)
@@ -60,6 +69,7 @@ struct Pipe {
   const S* src1;       // reversed row band of L
   int stage_elems, Q, bp;
   uint32_t bytes;
+  long long limit;     // wait limit of the copies (g_copy_wait_limit)
   __device__ void issue(int s) const {
     const S* src = s < Q ? src0 + (long long)s * KC * bp : src1 + (long long)(s - Q) * KC * bp;
     const int st = s % stages_for<S>();
@@ -68,7 +78,9 @@ struct Pipe {
   }
   __device__ const S* wait(int s, bool& ok) const {
     const int st = s % stages_for<S>();
-    ok = mbar_wait_bounded(&bar[st], (uint32_t)((s / stages_for<S>()) & 1));
+    // limit 1: every wait gives up at once (the deterministic form of the
+    // failure injection); otherwise a bounded wait
+    ok = limit > 1 && mbar_wait_limited(&bar[st], (uint32_t)((s / stages_for<S>()) & 1), limit);
     return stg + st * stage_elems;
   }
 };
@@ -126,9 +138,57 @@ __device__ __forceinline__ bool group_dispatch(int ph, const Pipe<ST, KC>& pp, i
   return false;
 }
 
-// The two sweeps of one subdomain with an S-slot register window (S >= the
-// subdomain's ceil((b+1)/32)); the bulk-copy ring is already started.
+// The 32 steps of one row group for a wide window (S > 8 slots): slot 0
+// always holds the group being finished, and after the group the window is
+// rotated by one slot (S - 1 register moves per 32 steps), so there is one
+// copy of the step code per S instead of one per phase.
 template <typename R, typename ST, int S, int KC>
+__device__ __forceinline__ bool group_steps_rot(const Pipe<ST, KC>& pp, int s0, int b, int lane, cx<R> (&win)[S],
+                                                const cx<R>& nxt, cx<R>& outv) {
+  const int bp = pp.bp;
+#pragma unroll 1
+  for (int c4 = 0; c4 < 32 / KC; ++c4) {
+    const int s = s0 + c4;
+    bool ok;
+    const ST* Lc = pp.wait(s, ok);
+    if (!__all_sync(0xffffffffu, ok)) return false;
+#pragma unroll 2
+    for (int ii = 0; ii < KC; ++ii) {
+      const int i = c4 * KC + ii;
+      const ST* col = Lc + ii * bp;
+      const cx<R> y = shfl(win[0], i);
+      if (lane == i) {
+        outv = y;
+        win[0] = nxt;
+      }
+      const int base = lane - i - 1;
+      {
+        const int t = (lane > i) ? base : base + 32 * S;
+        if (t < b) win[0] = fms(win[0], ld_entry(col[t]), y);
+      }
+#pragma unroll
+      for (int sl = 1; sl < S; ++sl) {
+        const int t = base + 32 * sl;
+        if (t < b) win[sl] = fms(win[sl], ld_entry(col[t]), y);
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && s + stages_for<ST>() < 2 * pp.Q) {
+      fence_proxy_async_smem();
+      pp.issue(s + stages_for<ST>());
+    }
+  }
+  const cx<R> f = win[0];   // refilled with the rows 32 S ahead: the last slot now
+#pragma unroll
+  for (int sl = 0; sl + 1 < S; ++sl) win[sl] = win[sl + 1];
+  win[S - 1] = f;
+  return true;
+}
+
+// The two sweeps of one subdomain with an S-slot register window (S >= the
+// subdomain's ceil((b+1)/32)); the bulk-copy ring is already started. ROT:
+// the rotating window of the wide kernel.
+template <typename R, typename ST, int S, int KC, bool ROT>
 __device__ __forceinline__ void sweeps(const SubDesc& sd, const Pipe<ST, KC>& pp, int nx, long long goff, int o,
                                        const c128* __restrict__ rglob, int rdf, const cx<R>* __restrict__ dv,
                                        cx<R>* __restrict__ Yj, DevStatus* status) {
@@ -154,7 +214,9 @@ __device__ __forceinline__ void sweeps(const SubDesc& sd, const Pipe<ST, KC>& pp
     const cx<R> nxt2 = gather_row<R>(sd, nx, goff, rglob, rdf, 32 * (gi + S + 1) + lane);
     const cx<R> d = dv[32 * gi + lane];
     cx<R> outv;
-    if (!group_dispatch<R, ST, S, KC>(gi % S, pp, (32 / KC) * gi, b, lane, win, nxt, outv)) {
+    const bool ok = ROT ? group_steps_rot<R, ST, S, KC>(pp, (32 / KC) * gi, b, lane, win, nxt, outv)
+                        : group_dispatch<R, ST, S, KC>(gi % S, pp, (32 / KC) * gi, b, lane, win, nxt, outv);
+    if (!ok) {
       fail((32 / KC) * gi);
       return;
     }
@@ -172,7 +234,9 @@ __device__ __forceinline__ void sweeps(const SubDesc& sd, const Pipe<ST, KC>& pp
   for (int gi = 0; gi < G; ++gi) {
     const cx<R> nxt2 = zrow(32 * (gi + S + 1) + lane);
     cx<R> outv;
-    if (!group_dispatch<R, ST, S, KC>(gi % S, pp, pp.Q + (32 / KC) * gi, b, lane, win, nxt, outv)) {
+    const bool ok = ROT ? group_steps_rot<R, ST, S, KC>(pp, pp.Q + (32 / KC) * gi, b, lane, win, nxt, outv)
+                        : group_dispatch<R, ST, S, KC>(gi % S, pp, pp.Q + (32 / KC) * gi, b, lane, win, nxt, outv);
+    if (!ok) {
       fail(pp.Q + (32 / KC) * gi);
       return;
     }
@@ -188,11 +252,14 @@ __device__ __forceinline__ void sweeps(const SubDesc& sd, const Pipe<ST, KC>& pp
 }
 
 // One warp per subdomain; the register window is sized per subdomain
-// (S = ceil((b+1)/32), at most SMAX), so subdomains of different bands share
-// one launch without the small ones paying for the largest window.
+// (S = ceil((b+1)/32)), so subdomains of different bands share one launch
+// without the small ones paying for the largest window. WIDE = false: the
+// subdomains with S <= SMAX (phase-dispatched window); WIDE = true: those
+// with SMAX < S <= kApplyWideSlots (rotating window). Each launch returns at
+// once for the subdomains of the other kind, before it issues any copy.
 // rbase + (*jptr) * r_ld is the input vector when jptr is set (a step of a
 // captured Arnoldi graph reads its column index from device memory).
-template <typename R, typename ST, int SMAX, int KC>
+template <typename R, typename ST, int SMAX, int KC, bool WIDE>
 __global__ void __launch_bounds__(32)
     k_apply(const Geo* __restrict__ geos, const SubDesc* __restrict__ subs, const ST* __restrict__ Lf,
             const ST* __restrict__ Lb, const cx<R>* __restrict__ dinv_all, const c128* __restrict__ rbase,
@@ -200,6 +267,8 @@ __global__ void __launch_bounds__(32)
             const KState* __restrict__ kst, DevStatus* status) {
   extern __shared__ __align__(128) unsigned char sm[];
   const SubDesc sd = subs[blockIdx.x];
+  const int S = (sd.b + 32) / 32;
+  if (WIDE ? (S <= SMAX || S > kApplyWideSlots) : S > SMAX) return;
   if (kst != nullptr && kst[sd.prob].stop) return;
   const int nx = geos[sd.prob].nx, o = geos[sd.prob].ovlp;
   const long long goff = geos[sd.prob].goff;
@@ -217,6 +286,7 @@ __global__ void __launch_bounds__(32)
   pp.Q = sd.npad / KC;
   pp.bp = sd.bp;
   pp.bytes = (uint32_t)(KC * sd.bp * sizeof(ST));
+  pp.limit = g_copy_wait_limit;
   const int nseq = 2 * pp.Q;
   constexpr int NST = stages_for<ST>();
   if (lane == 0) {
@@ -227,17 +297,19 @@ __global__ void __launch_bounds__(32)
   __syncwarp();
   const cx<R>* dv = dinv_all + sd.v_off;
   cx<R>* Yj = Y + sd.v_off;
-#define RP_SWEEPS(S_) sweeps<R, ST, S_, KC>(sd, pp, nx, goff, o, rglob, rdf, dv, Yj, status)
-  switch ((sd.b + 32) / 32) {
-    case 1: RP_SWEEPS(1); break;
-    case 2: if constexpr (SMAX >= 2) RP_SWEEPS(2); break;
-    case 3: if constexpr (SMAX >= 3) RP_SWEEPS(3); break;
-    case 4: if constexpr (SMAX >= 4) RP_SWEEPS(4); break;
-    case 5: if constexpr (SMAX >= 5) RP_SWEEPS(5); break;
-    case 6: if constexpr (SMAX >= 6) RP_SWEEPS(6); break;
-    case 7: if constexpr (SMAX >= 7) RP_SWEEPS(7); break;
-    case 8: if constexpr (SMAX >= 8) RP_SWEEPS(8); break;
+#define RP_SWEEPS(S_) sweeps<R, ST, S_, KC, WIDE>(sd, pp, nx, goff, o, rglob, rdf, dv, Yj, status)
+#define RP_CASE(S_) \
+  case S_:          \
+    if constexpr ((WIDE && S_ > SMAX) || (!WIDE && S_ <= SMAX)) RP_SWEEPS(S_); \
+    break;
+  switch (S) {
+    RP_CASE(1) RP_CASE(2) RP_CASE(3) RP_CASE(4) RP_CASE(5) RP_CASE(6) RP_CASE(7) RP_CASE(8)
+    RP_CASE(9) RP_CASE(10) RP_CASE(11) RP_CASE(12) RP_CASE(13) RP_CASE(14) RP_CASE(15) RP_CASE(16)
+    RP_CASE(17) RP_CASE(18) RP_CASE(19) RP_CASE(20) RP_CASE(21) RP_CASE(22) RP_CASE(23) RP_CASE(24)
+    RP_CASE(25) RP_CASE(26) RP_CASE(27) RP_CASE(28) RP_CASE(29)
   }
+  static_assert(kApplyWideSlots == 29, "the case list covers S = 1..29");
+#undef RP_CASE
 #undef RP_SWEEPS
 }
 
@@ -264,6 +336,8 @@ __global__ void k_prolong(Geo g, const SubDesc* __restrict__ subs, const cx<R>* 
           df_acc(ih, il, v.im, 0.f);
         }
       }
+      df_norm(rh, rl);
+      df_norm(ih, il);
       dfc o;
       o.rh = rh;
       o.rl = rl;
@@ -284,33 +358,69 @@ __global__ void k_prolong(Geo g, const SubDesc* __restrict__ subs, const cx<R>* 
       im += (double)v.im;
     }
   }
-  z[r] = mk(re, im);
+  if (out_df)
+    reinterpret_cast<dfc*>(z)[r] = split_c(mk(re, im));
+  else
+    z[r] = mk(re, im);
 }
 
-// SMAX: 6 slots for complex128 (b <= 160), 8 for complex64 (b <= 232)
+// SMAX: the narrow kernel's window, 6 slots for complex128, 8 for complex64
+// storage. The narrow launch takes the subdomains with b < 32 SMAX, the wide
+// one (4 columns per bulk copy for complex128, 8 otherwise, so that its ring
+// fits in shared memory up to b = kMaxBandWide) the others; both are launched
+// over all subdomains, each skipping the other kind, wide first.
+template <typename R>
+constexpr int smax_for() { return sizeof(R) == 8 ? 6 : 8; }
+
+template <typename R, typename ST, int KC, bool WIDE>
+cudaError_t launch_apply_k(int max_bp, const Geo* geos, const SubDesc* subs, int nsub, const void* Lf, const void* Lb,
+                           const void* dinv, const c128* r, long long r_ld, const int* jptr, int rdf, void* Y,
+                           const KState* kst, DevStatus* status, cudaStream_t st) {
+  constexpr int SMAX = smax_for<R>();
+  const int stage_elems = KC * max_bp;
+  const size_t smem = 128 + (size_t)stages_for<ST>() * KC * max_bp * sizeof(ST);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_apply<R, ST, SMAX, KC, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_apply<R, ST, SMAX, KC, WIDE><<<nsub, 32, smem, st>>>(geos, subs, (const ST*)Lf, (const ST*)Lb, (const cx<R>*)dinv,
+                                                         r, r_ld, jptr, rdf, (cx<R>*)Y, stage_elems, kst, status);
+  return cudaGetLastError();
+}
+
 template <typename R, typename ST, int KC>
 cudaError_t launch_apply_t(int max_b, const Geo* geos, const SubDesc* subs, int nsub, int max_bp, const void* Lf,
                            const void* Lb, const void* dinv, const c128* r, long long r_ld, const int* jptr, int rdf,
                            void* Y, const KState* kst, DevStatus* status, cudaStream_t st) {
-  constexpr int SMAX = sizeof(R) == 8 ? 6 : 8;
-  if ((max_b + 32) / 32 > SMAX) return cudaErrorInvalidValue;
-  const int stage_elems = KC * max_bp;
-  const size_t smem = 128 + (size_t)stages_for<ST>() * KC * max_bp * sizeof(ST);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_apply<R, ST, SMAX, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_apply<R, ST, SMAX, KC><<<nsub, 32, smem, st>>>(geos, subs, (const ST*)Lf, (const ST*)Lb, (const cx<R>*)dinv, r,
-                                                   r_ld, jptr, rdf, (cx<R>*)Y, stage_elems, kst, status);
-  return cudaGetLastError();
+  constexpr int SMAX = smax_for<R>();
+  if (max_b > kMaxBandWide) return cudaErrorInvalidValue;
+  cudaError_t e = cudaSuccess;
+  int narrow_bp = max_bp;
+  if ((max_b + 32) / 32 > SMAX) {
+    constexpr int KW = sizeof(ST) == 16 ? 4 : 8;
+    e = launch_apply_k<R, ST, KW, true>(max_bp, geos, subs, nsub, Lf, Lb, dinv, r, r_ld, jptr, rdf, Y, kst, status,
+                                        st);
+    narrow_bp = std::min(max_bp, 32 * SMAX);
+  }
+  if (e == cudaSuccess)
+    e = launch_apply_k<R, ST, KC, false>(narrow_bp, geos, subs, nsub, Lf, Lb, dinv, r, r_ld, jptr, rdf, Y, kst,
+                                         status, st);
+  return e;
 }
 
 }  // namespace
+
+cudaError_t set_copy_wait_limit(long long cycles) {
+  const long long v = cycles > 0 ? cycles : kWaitLimitCycles;
+  return cudaMemcpyToSymbol(g_copy_wait_limit, &v, sizeof(v));
+}
 
 bool apply_cols_valid(int prec, int cols) { return cols == 8 || (prec == 1 && (cols == 4 || cols == 16)); }
 
 size_t apply_smem_bytes(int max_bp, int prec, int cols) {
   const size_t es = prec == 0 ? sizeof(c128) : prec == 1 ? sizeof(c64) : sizeof(h2c);
-  return 128 + (size_t)4 * cols * max_bp * es;
+  const int narrow_bp = std::min(max_bp, 32 * (prec == 0 ? 6 : 8));   // the wide launch has its own ring
+  return 128 + (size_t)4 * cols * narrow_bp * es;
 }
 
 cudaError_t launch_local_solves(int prec, int cols, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
@@ -334,8 +444,7 @@ cudaError_t launch_prolong(int prec, const Geo& g, const SubDesc* subs, const vo
   int threads = 256;
   unsigned blocks = (unsigned)((n + threads - 1) / threads);
   if (prec == 0) {
-    if (out_df) return cudaErrorInvalidValue;
-    k_prolong<double><<<blocks, threads, 0, st>>>(g, subs, (const c128*)Y, z, 0, kst);
+    k_prolong<double><<<blocks, threads, 0, st>>>(g, subs, (const c128*)Y, z, out_df, kst);
   } else {
     k_prolong<float><<<blocks, threads, 0, st>>>(g, subs, (const c64*)Y, z, out_df, kst);
   }

@@ -261,11 +261,13 @@ __device__ __forceinline__ CellTerms<T> cell_of(const Geo& g, const LocalTab<T>&
   return t;
 }
 
-// table sizes of k_local_rows: x half-indices of a subdomain of up to
-// kMaxBandC64 + 1 nodes per line, y half-indices of the lines of 128 rows
+// table sizes of k_local_rows: the x half-indices of a subdomain (2 nlx + 3
+// of them, nlx = b - 1) in dynamic shared memory sized per launch by the
+// widest band, tab_x(max_b) entries; the y half-indices of the lines of 128
+// rows in a fixed array
 constexpr int kLrThreads = 128;
-constexpr int kLrTabX = 2 * (kMaxBandC64 + 1) + 4;
 constexpr int kLrTabY = 2 * (kLrThreads + 1) + 4;
+inline int lr_tab_x(int max_b) { return 2 * max_b + 4; }
 
 // kLrThreads local rows per CTA; blockIdx.y = subdomain. Output
 // Aloc[v_off + r] = {D, W, S, SW}; padding rows (r >= n) are identity rows.
@@ -275,11 +277,15 @@ constexpr int kLrTabY = 2 * (kLrThreads + 1) + 4;
 // first (one evaluation per half-index instead of six per cell).
 template <typename T>
 __global__ void __launch_bounds__(kLrThreads)
-    k_local_rows(const Geo* __restrict__ geos, const SubDesc* __restrict__ subs, c128* __restrict__ Aloc) {
-  __shared__ cx<T> tabx[2 * kLrTabX], taby[2 * kLrTabY];
+    k_local_rows(const Geo* __restrict__ geos, const SubDesc* __restrict__ subs, c128* __restrict__ Aloc,
+                 int tab_x) {
+  extern __shared__ __align__(16) unsigned char lr_sm[];
+  cx<T>* tabx = reinterpret_cast<cx<T>*>(lr_sm);   // 2 tab_x values
+  __shared__ cx<T> taby[2 * kLrTabY];
   const SubDesc sd = subs[blockIdx.y];
   const int r0 = blockIdx.x * kLrThreads;
   if (r0 >= sd.npad) return;   // whole CTA
+  if (2 * sd.nlx + 3 > tab_x) return;   // never: the launch sizes the table by the widest band
   const int r = r0 + threadIdx.x;
   const Geo g = geos[sd.prob];
   const LocalStretch<T> ls{g, sd};
@@ -582,14 +588,23 @@ cudaError_t launch_global_stencil(const Geo& g, c128* tab, c128* D, c128* CW, c1
   return cudaGetLastError();
 }
 
-cudaError_t launch_local_rows(int prec, const Geo* geos, const SubDesc* subs, int nsub, int max_npad, c128* Aloc,
-                              cudaStream_t st) {
+cudaError_t launch_local_rows(int prec, const Geo* geos, const SubDesc* subs, int nsub, int max_npad, int max_b,
+                              c128* Aloc, cudaStream_t st) {
   const int threads = kLrThreads;
   dim3 grid((max_npad + threads - 1) / threads, nsub);
-  if (prec == 0)
-    k_local_rows<double><<<grid, threads, 0, st>>>(geos, subs, Aloc);
-  else
-    k_local_rows<float><<<grid, threads, 0, st>>>(geos, subs, Aloc);
+  const int tx = lr_tab_x(max_b);
+  cudaError_t e;
+  if (prec == 0) {
+    const size_t smem = (size_t)2 * tx * sizeof(c128);
+    e = cudaFuncSetAttribute(k_local_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_local_rows<double><<<grid, threads, smem, st>>>(geos, subs, Aloc, tx);
+  } else {
+    const size_t smem = (size_t)2 * tx * sizeof(c64);
+    e = cudaFuncSetAttribute(k_local_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_local_rows<float><<<grid, threads, smem, st>>>(geos, subs, Aloc, tx);
+  }
   return cudaGetLastError();
 }
 

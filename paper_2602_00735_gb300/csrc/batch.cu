@@ -100,6 +100,8 @@ __global__ void __launch_bounds__(kBT)
             df_acc(ih, il, v.im, 0.f);
           }
         }
+        df_norm(rh, rl);
+        df_norm(ih, il);
         dfc o;
         o.rh = rh;
         o.rl = rl;
@@ -217,6 +219,8 @@ __global__ void __launch_bounds__(kBT)
     if (lr + nx < n) bcmac_df(rh, rl, ih, il, CS[r + nx], X(r + nx));
     if (lr >= nx + 1) bcmac_df(rh, rl, ih, il, CSW[r], X(r - nx - 1));
     if (lr + nx + 1 < n) bcmac_df(rh, rl, ih, il, CSW[r + nx + 1], X(r + nx + 1));
+    df_norm(rh, rl);
+    df_norm(ih, il);
     o.rh = rh;
     o.rl = rl;
     o.ih = ih;
@@ -380,6 +384,8 @@ __global__ void __launch_bounds__(kBT)
         df_acc(ih, il, p, e);
       }
     }
+    df_norm(rh, rl);
+    df_norm(ih, il);
     dfc o;
     o.rh = rh;
     o.rl = rl;

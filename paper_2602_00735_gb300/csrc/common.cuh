@@ -133,7 +133,7 @@ struct SubDesc {
   long long l_off;                              // element offset of L_j
   long long v_off;                              // element offset of per-row arrays
   int prob;                                     // problem of a batch (0 for one problem)
-  int pad0;
+  int wslot;                                    // scratch slot of the wide-band factor, -1: none
 };
 
 __device__ __forceinline__ double xpos(const Geo& g, double s) {
@@ -308,6 +308,19 @@ __device__ __forceinline__ void df_acc(float& hi, float& lo, float p, float t) {
 
 __device__ __forceinline__ double df_to_d(float hi, float lo) { return (double)hi + (double)lo; }
 
+// Renormalise a double-float pair in place (TwoSum of its two parts):
+// afterwards |lo| <= ulp(hi)/2 and hi + lo is unchanged. Sums kept in
+// double-float form (df_acc) leave lo as a running total of rounding errors,
+// which after cancellation in hi can be as large as hi itself; a product of
+// two double-float values (df_prod) drops the lo * lo term, so every pair that
+// later enters such a product is renormalised where it is produced.
+__device__ __forceinline__ void df_norm(float& hi, float& lo) {
+  const float s = hi + lo;
+  const float bb = s - hi;
+  lo = (hi - (s - bb)) + (lo - bb);
+  hi = s;
+}
+
 __device__ __forceinline__ dfl dfl_of(float hi, float lo) {
   dfl r;
   r.hi = hi;
@@ -403,14 +416,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: gives up after ~2^31 SM clock cycles (about a second at the
-// GB300 clock); returns false on time-out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Bounded wait: gives up after `limit` SM clock cycles; returns false on
+// time-out.
+__device__ __forceinline__ bool mbar_wait_limited(uint64_t* bar, uint32_t parity, long long limit) {
   long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
+}
+constexpr long long kWaitLimitCycles = 1ll << 31;   // about a second at the GB300 clock
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_limited(bar, parity, kWaitLimitCycles);
 }
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -67,9 +67,10 @@ template <typename R, typename S, int NT>
 __global__ void __launch_bounds__(NT)
     k_factor_ldlt(const SubDesc* __restrict__ subs, const c128* __restrict__ Aloc, S* __restrict__ Lall,
                   S* __restrict__ Lrev_all, cx<R>* __restrict__ dinv_all, double* __restrict__ pivstats,
-                  DevStatus* status) {
+                  DevStatus* status, int bcap) {
   extern __shared__ __align__(16) unsigned char sm[];
   const SubDesc sd = subs[blockIdx.x];
+  if (sd.b > bcap) return;   // wider than this launch's window: the wide kernel takes it
   const int tid = threadIdx.x;
   const int b = sd.b, bp = sd.bp, Wc = b + 1;
   const int nwin = Wc * (b + 2) / 2;
@@ -209,9 +210,10 @@ template <typename R, typename S, int NT>
 __global__ void __launch_bounds__(NT)
     k_factor_ldlt2(const SubDesc* __restrict__ subs, const c128* __restrict__ Aloc, S* __restrict__ Lall,
                    S* __restrict__ Lrev_all, cx<R>* __restrict__ dinv_all, double* __restrict__ pivstats,
-                   DevStatus* status) {
+                   DevStatus* status, int bcap) {
   extern __shared__ __align__(16) unsigned char sm[];
   const SubDesc sd = subs[blockIdx.x];
+  if (sd.b > bcap) return;   // wider than this launch's window: the wide kernel takes it
   const int tid = threadIdx.x;
   const int b = sd.b, bp = sd.bp, Wc = b + 1, npad = sd.npad;
   const int nwin = Wc * (b + 2) / 2;
@@ -550,11 +552,12 @@ template <typename S, int NB>
 __global__ void __launch_bounds__(kTcM)
     k_factor_tc(const SubDesc* __restrict__ subs, const c128* __restrict__ Aloc, S* __restrict__ Lall,
                 S* __restrict__ Lrev_all, c64* __restrict__ dinv_all, double* __restrict__ pivstats,
-                DevStatus* status, int Nmax, int ring_elems, int tcols, int sub_base) {
+                DevStatus* status, int Nmax, int ring_elems, int tcols, int sub_base, int bcap) {
   extern __shared__ __align__(1024) unsigned char smt[];
   unsigned char* sm = smt;
   const int sub = sub_base + (int)blockIdx.x;   // launch position of this subdomain
   const SubDesc sd = subs[sub];
+  if (sd.b > bcap) return;   // wider than this launch's ring (before any TMEM allocation)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b = sd.b, bp = sd.bp, npad = sd.npad;
   const int R = NB + b, LDW = tc_ldw(b), N = tc_n(b);
@@ -765,30 +768,33 @@ namespace {
 
 template <typename R, typename S, int NT>
 cudaError_t launch_factor_t(int rank, size_t smem, const SubDesc* subs, int nsub, const c128* Aloc, void* L,
-                            void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
+                            void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st, int bcap) {
   cudaError_t e;
   if (NT == 1024 || rank == 2) {
     e = cudaFuncSetAttribute(k_factor_ldlt2<R, S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_factor_ldlt2<R, S, NT><<<nsub, NT, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (cx<R>*)dinv, pivstats, status);
+    k_factor_ldlt2<R, S, NT><<<nsub, NT, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (cx<R>*)dinv, pivstats, status,
+                                                     bcap);
   } else if constexpr (NT < 1024) {
     e = cudaFuncSetAttribute(k_factor_ldlt<R, S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_factor_ldlt<R, S, NT><<<nsub, NT, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (cx<R>*)dinv, pivstats, status);
+    k_factor_ldlt<R, S, NT><<<nsub, NT, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (cx<R>*)dinv, pivstats, status,
+                                                    bcap);
   }
   return cudaGetLastError();
 }
 
 template <typename R, typename S>
 cudaError_t launch_factor_s(int threads, int rank, size_t smem, const SubDesc* subs, int nsub, const c128* Aloc,
-                            void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st) {
+                            void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status, cudaStream_t st,
+                            int bcap) {
   switch (threads) {
-    case 128: return launch_factor_t<R, S, 128>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
-    case 256: return launch_factor_t<R, S, 256>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
-    case 512: return launch_factor_t<R, S, 512>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+    case 128: return launch_factor_t<R, S, 128>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st, bcap);
+    case 256: return launch_factor_t<R, S, 256>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st, bcap);
+    case 512: return launch_factor_t<R, S, 512>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st, bcap);
     case 1024:
       if (rank == 2)
-        return launch_factor_t<R, S, 1024>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+        return launch_factor_t<R, S, 1024>(rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st, bcap);
       break;
   }
   return cudaErrorInvalidValue;
@@ -798,13 +804,22 @@ cudaError_t launch_factor_s(int threads, int rank, size_t smem, const SubDesc* s
 
 bool factor_tc_ok(int prec, int max_b) { return prec >= 1 && max_b >= 1 && max_b <= kMaxBandTc; }
 
+// max_b: the widest subdomain the shared-memory kernels take. Their steps give
+// one thread to each of the b + 1 window diagonals (and the entering row), so
+// a CUDA-core shape needs at least b + 2 threads.
 bool factor_shape_valid(int prec, int max_b, int threads, int rank, BandSplit split) {
   if (is_tc_rank(rank)) {
     if (threads == kTcM) return factor_tc_ok(prec, max_b);
-    return prec >= 1 && split.nwide >= 0 && (threads == 256 || threads == 512 || threads == 1024);
+    return prec >= 1 && split.nwide >= 0 && (threads == 256 || threads == 512 || threads == 1024) &&
+           threads >= max_b + 2;
   }
-  return ((threads == 128 || threads == 256 || threads == 512) && (rank == 1 || rank == 2)) ||
-         (threads == 1024 && rank == 2);
+  return (((threads == 128 || threads == 256 || threads == 512) && (rank == 1 || rank == 2)) ||
+          (threads == 1024 && rank == 2)) &&
+         threads >= max_b + 2;
+}
+
+int narrow_band(int prec, int max_b, BandSplit split) {
+  return max_b > max_band(prec) ? split.max_b_narrow : max_b;
 }
 
 namespace {
@@ -837,7 +852,7 @@ cudaError_t launch_factor_tc(const SubDesc* subs, int nsub, int max_b, const c12
       cudaFuncSetAttribute(k_factor_tc<S, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_factor_tc<S, NB><<<nsub, kTcM, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (c64*)dinv, pivstats, status, nmax,
-                                               ring_elems, tcols, sub_base);
+                                               ring_elems, tcols, sub_base, max_b);
   return cudaGetLastError();
 }
 
@@ -860,7 +875,7 @@ cudaError_t launch_factor_mixed(int threads, int rank, const SubDesc* subs, int 
   const int nw = sp.nwide < nsub ? sp.nwide : nsub;
   if (nw > 0)
     e = launch_factor_s<float, S>(threads, 2, factor_smem_bytes(max_b, 1, 2), subs, nw, Aloc, L, Lrev, dinv, pivstats,
-                                  status, st);
+                                  status, st, max_b);
   if (e == cudaSuccess && nsub > nw) {
     const int mb = nw > 0 ? sp.max_b_tc : max_b;
     if (!factor_tc_ok(1, mb)) return cudaErrorInvalidValue;
@@ -873,7 +888,17 @@ cudaError_t launch_factor_mixed(int threads, int rank, const SubDesc* subs, int 
 
 cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, int nsub, int max_b,
                           const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status,
-                          cudaStream_t st, BandSplit split) {
+                          cudaStream_t st, BandSplit split, void* wscratch, bool skip_wide) {
+  if (max_b > max_band(prec)) {
+    // the subdomains wider than the shared-memory window first (blocked
+    // kernel, window in scratch), then the others with the chosen shape,
+    // sized for the widest of them; each launch skips the other kind
+    cudaError_t e = skip_wide ? cudaSuccess
+                              : launch_factor_wide(prec, subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status,
+                                                   wscratch, st);
+    if (e != cudaSuccess || split.max_b_narrow <= 0) return e;
+    max_b = split.max_b_narrow;
+  }
   if (!factor_shape_valid(prec, max_b, threads, rank, split)) return cudaErrorInvalidValue;
   if (is_tc_rank(rank) && threads != kTcM) {
     if (prec == 1)
@@ -886,10 +911,13 @@ cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, 
   }
   const size_t smem = factor_smem_bytes(max_b, prec, rank);
   if (prec == 0)
-    return launch_factor_s<double, c128>(threads, rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+    return launch_factor_s<double, c128>(threads, rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st,
+                                         max_b);
   if (prec == 1)
-    return launch_factor_s<float, c64>(threads, rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
-  return launch_factor_s<float, h2c>(threads, rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st);
+    return launch_factor_s<float, c64>(threads, rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st,
+                                       max_b);
+  return launch_factor_s<float, h2c>(threads, rank, smem, subs, nsub, Aloc, L, Lrev, dinv, pivstats, status, st,
+                                     max_b);
 }
 
 }  // namespace rp

@@ -1,0 +1,272 @@
+// Band LDL^T of the subdomains whose window does not fit in shared memory
+// (Section 2: the local solves A_j^-1 of B^-1), kMaxBandC64 / kMaxBandC128 <
+// b <= kMaxBandWide: A_j = L_j D_j L_j^T without pivoting, blocked.
+//
+// One CTA of kWideThreads threads per subdomain, right-looking, panels of NB
+// pivots. The active rows k..k+NB+b-1 of the lower band live in a window in
+// device scratch (one slot per wide subdomain, SubDesc::wslot, set aside by
+// the caller): row r in row slot r mod (NB+b), its entries A(r, r-b..r) at
+// positions 0..b (position q holds column r-b+q), in the arithmetic type.
+// Panel at k:
+//   1. the panel's NB columns, rows k..k+NB+b-1, are copied to shared memory,
+//      column-major (Pn[j][i] = W(k+i, k+j));
+//   2. they are factored there pivot by pivot: the multipliers of the pivot
+//      column, then c_i l_j' subtracted from the later panel columns (two
+//      barriers per pivot), and the pivot column scaled to L;
+//   3. L(k+i, k+j) goes to both output copies and 1/d to D^-1 (the layout of
+//      factor.cu), and the rows k+NB+b..k+2NB+b-1 of A_j enter the slots of
+//      the finished rows k..k+NB-1 (zero except their four stored couplings);
+//   4. the trailing window, rows and columns k+NB..k+NB+b-1, takes the rank-NB
+//      update W(r, c) -= sum_j L(r, k+j) d_j L(c, k+j) for c <= r: each warp
+//      takes tiles of 8 rows x 64 columns, each thread 4 x 4 entries kept in
+//      registers over the NB terms, the panel read from shared memory; the
+//      window is read and written once per panel.
+// Rows n..npad-1 are identity padding. Zero or non-finite pivots are reported
+// like the narrow kernels do (status->pivot_bad_sub); there is no device-side
+// wait besides the block barriers.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rp {
+
+namespace {
+
+constexpr int kWideThreads = 256;
+constexpr int kWideOverhang = 64;   // zero rows after the panel: the tile overhang of step 4
+
+// the four stored couplings of row r (D, W, S, SW), identity for padding rows
+template <typename R>
+__device__ __forceinline__ void stored_row(const c128* __restrict__ A, const SubDesc& sd, int r, cx<R> (&v)[4]) {
+  if (r >= sd.n) {
+    v[0] = mk((R)1, (R)0);
+    v[1] = v[2] = v[3] = mk((R)0, (R)0);
+    return;
+  }
+  const c128* a = A + 4 * (sd.v_off + r);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) v[e] = cvt<R>(a[e]);
+}
+
+// window entry at position q of row r (column r - b + q) from its couplings
+template <typename R>
+__device__ __forceinline__ cx<R> band_entry(const cx<R> (&v)[4], int r, int q, int b) {
+  if (r - b + q < 0) return mk((R)0, (R)0);
+  const int t = b - q;   // distance below the diagonal
+  cx<R> x = mk((R)0, (R)0);
+  if (t == 0) x = v[0];
+  if (t == 1) x = x + v[1];
+  if (t == b - 1) x = x + v[2];
+  if (t == b) x = x + v[3];
+  return x;
+}
+
+// rows r0 <= r < r1 (and < npad) of A_j into their window slots
+template <typename R>
+__device__ __forceinline__ void fill_rows(cx<R>* Wn, const c128* __restrict__ Aloc, const SubDesc& sd, int r0,
+                                          int r1, int RS, int LDW) {
+  const int b = sd.b;
+  r1 = min(r1, sd.npad);
+  const long long cnt = (long long)max(0, r1 - r0) * LDW;
+  for (long long e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int r = r0 + (int)(e / LDW), q = (int)(e % LDW);
+    cx<R> v[4];
+    stored_row<R>(Aloc, sd, r, v);
+    Wn[(long long)(r % RS) * LDW + q] = q <= b ? band_entry<R>(v, r, q, b) : mk((R)0, (R)0);
+  }
+}
+
+template <typename R, typename S, int NB>
+__global__ void __launch_bounds__(kWideThreads)
+    k_factor_wide(const SubDesc* __restrict__ subs, const c128* __restrict__ Aloc, S* __restrict__ Lall,
+                  S* __restrict__ Lrev_all, cx<R>* __restrict__ dinv_all, double* __restrict__ pivstats,
+                  DevStatus* status, cx<R>* __restrict__ scratch, long long slot_elems, int bmin, int pld) {
+  extern __shared__ __align__(16) unsigned char smw[];
+  const SubDesc sd = subs[blockIdx.x];
+  if (sd.b <= bmin || sd.wslot < 0) return;   // the shared-memory kernels take it
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = sd.b, bp = sd.bp, npad = sd.npad;
+  const int RS = NB + b, LDW = b + 1;
+  cx<R>* Wn = scratch + (long long)sd.wslot * slot_elems;
+  cx<R>* Pn = reinterpret_cast<cx<R>*>(smw);   // Pn[j * pld + i], i < NB + b + kWideOverhang
+  cx<R>* dsh = Pn + (long long)NB * pld;        // 1/d of the panel's pivots
+  cx<R>* dpv = dsh + NB;                        // the pivots d
+  cx<R>* lb = dpv + NB;                         // multipliers of the panel rows
+  S* L = Lall + sd.l_off;
+  S* Lr = Lrev_all + sd.l_off;
+  cx<R>* dv = dinv_all + sd.v_off;
+  const cx<R> zero = mk((R)0, (R)0);
+
+  fill_rows<R>(Wn, Aloc, sd, 0, RS, RS, LDW);
+  for (int e = tid; e < NB * pld; e += kWideThreads) Pn[e] = zero;
+  R dmin2 = (R)3e38, dmax2 = (R)0;
+  bool bad = false;
+  __syncthreads();
+
+  for (int k = 0; k < npad; k += NB) {
+    const int nbk = min(NB, npad - k);           // pivots in this panel
+    const int rows = min(NB + b, npad - k);      // panel rows present
+    // 1. panel columns into shared memory (rows of the window read along q)
+    for (int e = tid; e < rows * NB; e += kWideThreads) {
+      const int i = e / NB, j = e % NB;
+      const int q = j - i + b;
+      cx<R> x = zero;
+      if (j < nbk && q >= 0 && q <= b) x = Wn[(long long)((k + i) % RS) * LDW + q];
+      Pn[j * pld + i] = x;
+    }
+    for (int e = tid; e < NB * (NB + b - rows); e += kWideThreads) {
+      const int j = e / (NB + b - rows), i = rows + e % (NB + b - rows);
+      Pn[j * pld + i] = zero;
+    }
+    __syncthreads();
+    // 2. factor the panel
+    for (int j = 0; j < nbk; ++j) {
+      const cx<R> d = Pn[j * pld + j];
+      const R ad2 = abs2(d);
+      const cx<R> di = crecip(d);
+      if (tid == 0) {
+        dsh[j] = di;
+        dpv[j] = d;
+        if (!(ad2 > (R)0) || !isfinite(ad2) || !isfinite(di.re) || !isfinite(di.im)) bad = true;
+        dmin2 = fmin(dmin2, ad2);
+        dmax2 = fmax(dmax2, ad2);
+      }
+      for (int i = j + 1 + tid; i < NB; i += kWideThreads) lb[i] = Pn[j * pld + i] * di;
+      __syncthreads();
+      for (int i = j + 1 + tid; i < rows; i += kWideThreads) {
+        const cx<R> c = Pn[j * pld + i];
+        const int jmax = min(NB - 1, i);
+        for (int jj = j + 1; jj <= jmax; ++jj) Pn[jj * pld + i] = fms(Pn[jj * pld + i], c, lb[jj]);
+        Pn[j * pld + i] = c * di;
+      }
+      __syncthreads();
+    }
+    // 3. outputs, and the rows entering the window
+    for (int e = tid; e < nbk; e += kWideThreads) dv[k + e] = dsh[e];
+    for (int e = tid; e < nbk * bp; e += kWideThreads) {
+      const int j = e / bp, t = e % bp;   // L column k+j, entry t: row k+j+1+t
+      const int i = j + 1 + t;
+      L[(long long)(k + j) * bp + t] = st_entry<S, R>((t < b && i < rows) ? Pn[j * pld + i] : zero);
+    }
+    for (int e = tid; e < (rows - 1) * NB; e += kWideThreads) {
+      const int i = 1 + e / NB, j = e % NB;   // reversed row k+i, entry i-j-1
+      if (j < i && j < nbk && i - j <= b)
+        Lr[(long long)(npad - 1 - (k + i)) * bp + (i - j - 1)] = st_entry<S, R>(Pn[j * pld + i]);
+    }
+    fill_rows<R>(Wn, Aloc, sd, k + RS, k + RS + NB, RS, LDW);
+    // 4. trailing update of rows and columns k+NB..k+NB+b-1
+    if (k + NB < npad) {
+      const int nt = rows - NB;                 // trailing rows present
+      const int ng = (nt + 7) / 8;              // row groups of 8
+      const int ur = 4 * (lane >> 4), uc = 4 * (lane & 15);
+      for (int g = warp; g < ng; g += kWideThreads / 32) {
+        const int ii0 = 8 * g + ur;             // this thread's first trailing row
+        const int nct = (8 * g + 7) / 64 + 1;   // column tiles reaching the diagonal
+        for (int ct = 0; ct < nct; ++ct) {
+          const int jj0 = 64 * ct + uc;
+          if (jj0 > ii0 + 3) continue;          // the tile lies above the diagonal
+          cx<R> acc[4][4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int ii = ii0 + u;
+            const int r = k + NB + ii;
+            cx<R>* wr = Wn + (long long)(r % RS) * LDW + (b - ii);   // position of column k+NB
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const int jj = jj0 + v;
+              acc[u][v] = (ii < nt && jj <= ii) ? wr[jj] : zero;
+            }
+          }
+#pragma unroll 2
+          for (int j = 0; j < nbk; ++j) {
+            const cx<R>* pj = Pn + j * pld + NB;
+            const cx<R> d = dpv[j];
+            cx<R> a[4], q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              a[u] = pj[ii0 + u] * d;   // L(r, k+j) d_j
+              q[u] = pj[jj0 + u];       // L(c, k+j)
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) acc[u][v] = fms(acc[u][v], a[u], q[v]);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int ii = ii0 + u;
+            if (ii >= nt) continue;
+            const int r = k + NB + ii;
+            cx<R>* wr = Wn + (long long)(r % RS) * LDW + (b - ii);
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              if (jj0 + v <= ii) wr[jj0 + v] = acc[u][v];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    pivstats[2 * blockIdx.x] = sqrt((double)dmin2);
+    pivstats[2 * blockIdx.x + 1] = sqrt((double)dmax2);
+    if (bad) atomicCAS(&status->pivot_bad_sub, -1, (int)blockIdx.x);
+  }
+}
+
+// the panel width for bands up to max_b: the largest NB whose panel fits in
+// shared memory; 0 when none does
+template <typename R>
+int wide_nb(int max_b) {
+  for (int nb : {32, 16, 8}) {
+    const size_t bytes = ((size_t)nb * (nb + max_b + kWideOverhang) + 3 * nb) * sizeof(cx<R>);
+    if (bytes <= 220 * 1024) return nb;
+  }
+  return 0;
+}
+
+template <typename R, typename S, int NB>
+cudaError_t launch_wide_t(const SubDesc* subs, int nsub, int bmin, int max_b, const c128* Aloc, void* L, void* Lrev,
+                          void* dinv, double* pivstats, DevStatus* status, void* scratch, cudaStream_t st) {
+  const int pld = NB + max_b + kWideOverhang;
+  const size_t smem = ((size_t)NB * pld + 3 * NB) * sizeof(cx<R>);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_factor_wide<R, S, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long slot = (long long)(NB + max_b) * (max_b + 1);
+  k_factor_wide<R, S, NB><<<nsub, kWideThreads, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (cx<R>*)dinv, pivstats,
+                                                            status, (cx<R>*)scratch, slot, bmin, pld);
+  return cudaGetLastError();
+}
+
+template <typename R, typename S>
+cudaError_t launch_wide_s(const SubDesc* subs, int nsub, int bmin, int max_b, const c128* Aloc, void* L, void* Lrev,
+                          void* dinv, double* pivstats, DevStatus* status, void* scratch, cudaStream_t st) {
+  switch (wide_nb<R>(max_b)) {
+    case 32: return launch_wide_t<R, S, 32>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+    case 16: return launch_wide_t<R, S, 16>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+    case 8: return launch_wide_t<R, S, 8>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+size_t factor_wide_slot_bytes(int prec, int max_b) {
+  if (max_b <= max_band(prec) || max_b > kMaxBandWide) return 0;
+  const size_t es = prec == 0 ? sizeof(c128) : sizeof(c64);
+  const int nb = prec == 0 ? wide_nb<double>(max_b) : wide_nb<float>(max_b);
+  return (size_t)(nb + max_b) * (max_b + 1) * es;
+}
+
+cudaError_t launch_factor_wide(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
+                               void* Lrev, void* dinv, double* pivstats, DevStatus* status, void* scratch,
+                               cudaStream_t st) {
+  const int bmin = max_band(prec);
+  if (max_b <= bmin) return cudaSuccess;
+  if (max_b > kMaxBandWide || scratch == nullptr) return cudaErrorInvalidValue;
+  if (prec == 0) return launch_wide_s<double, c128>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+  if (prec == 1) return launch_wide_s<float, c64>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+  return launch_wide_s<float, h2c>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+}
+
+}  // namespace rp

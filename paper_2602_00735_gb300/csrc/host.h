@@ -3,6 +3,7 @@
 // problem's geometry and covering (Section 2).
 #pragma once
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -75,6 +76,38 @@ int build_problem(const ras_pml_params& p, int prob, Geo& g, std::vector<SubDesc
 // Entry counts of one subdomain's factor (L: npad*bp) and per-row arrays (npad).
 inline long long sub_l_entries(const SubDesc& d) { return (long long)d.npad * d.bp; }
 
+// Scratch slots of the wide-band factor: SubDesc::wslot numbers the
+// subdomains with b > max_band(prec) in order, -1 elsewhere. Returns the
+// number of slots; *max_b_narrow is the widest of the other subdomains.
+inline int assign_wide_slots(std::vector<SubDesc>& subs, int prec, int* max_b_narrow) {
+  int slots = 0, nb = 0;
+  for (SubDesc& d : subs) {
+    if (d.b > max_band(prec)) {
+      d.wslot = slots++;
+    } else {
+      d.wslot = -1;
+      nb = std::max(nb, d.b);
+    }
+  }
+  *max_b_narrow = nb;
+  return slots;
+}
+
+// Device scratch for the windows of the wide-band factor (nullptr and OK
+// when there is no slot); the caller frees it after the factor has run.
+inline int alloc_wide_scratch(void** p, int slots, int prec, int max_b) {
+  *p = nullptr;
+  if (slots <= 0) return RASPML_OK;
+  const size_t bytes = (size_t)slots * factor_wide_slot_bytes(prec, max_b);
+  if (bytes == 0) return RASPML_EBADARG;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return RASPML_ENOMEM;
+  }
+  return RASPML_OK;
+}
+
 // Times each tile shape of the factor and the apply on the given problem
 // set (CUDA events, median of `reps`) and returns the fastest in *best.
 struct TuneTarget {
@@ -90,6 +123,7 @@ struct TuneTarget {
   const c128* r;       // any input vector of the problems' layout
   cudaStream_t st;
   BandSplit split;     // the batched form's order by band (nwide < 0: none)
+  void* wscratch;      // windows of the wide-band factor (nullptr: no wide subdomain)
 };
 int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* report);
 

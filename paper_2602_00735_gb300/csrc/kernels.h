@@ -12,6 +12,12 @@ namespace rp {
 constexpr int kMaxBandC128 = 160;
 constexpr int kMaxBandC64 = 232;
 int max_band(int prec);
+// Wider subdomains (b up to kMaxBandWide, both precisions) are factored by
+// the blocked kernel of factor_wide.cu, with its window in device scratch,
+// and solved by the wide apply kernel (rotating register window of up to
+// kApplyWideSlots = ceil((kMaxBandWide + 1) / 32) slots).
+constexpr int kMaxBandWide = 900;
+constexpr int kApplyWideSlots = 29;
 constexpr int kDotBlocksPerSM = 2;
 
 // Krylov control block in device memory.
@@ -30,7 +36,8 @@ struct KState {
   double relres;   // true relative residual at the last cycle start (batch)
   double beta0;    // ||r|| at the start of the current cycle
   int live;        // batch: not yet finished (converged or out of iterations)
-  int pad;
+  int ldirs;       // directions the learned stage has corrected
+  double lgain;    // largest fraction of ||r1||^2 one learned correction removed
 };
 
 // Tile shapes of the factor and apply launches (chosen by the tuner).
@@ -50,20 +57,28 @@ constexpr int kMaxBandTc = 127;
 // pivots per pass, that many threads), the others (largest band max_b_tc)
 // to the tensor-core kernel. nwide < 0: no such order (the one-problem
 // handle), and the mixed shape is not available.
+// max_b_narrow: the widest subdomain at or below max_band(prec) (0: none),
+// for the launch of the shared-memory kernels when wider subdomains exist.
 struct BandSplit {
   int nwide = -1;
   int max_b_tc = 0;
+  int max_b_narrow = 0;
 };
 bool factor_tc_ok(int prec, int max_b);
 bool factor_shape_valid(int prec, int max_b, int threads, int rank, BandSplit split = BandSplit{});
+// the widest subdomain of the shared-memory factor kernels: max_b, or, when
+// wider subdomains go to the blocked kernel, split.max_b_narrow
+int narrow_band(int prec, int max_b, BandSplit split);
 bool apply_cols_valid(int prec, int cols);
 
 // assembly.cu
 // tab: scratch of stretch_table_elems(g) complex128 values (stretching tables)
 size_t stretch_table_elems(const Geo& g);
 cudaError_t launch_global_stencil(const Geo& g, c128* tab, c128* D, c128* CW, c128* CS, c128* CSW, cudaStream_t st);
-cudaError_t launch_local_rows(int prec, const Geo* geos, const SubDesc* subs, int nsub, int max_npad, c128* Aloc,
-                              cudaStream_t st);
+// Aloc: 4 couplings per local row; max_b: the widest subdomain of the launch
+// (sizes the kernel's stretching table)
+cudaError_t launch_local_rows(int prec, const Geo* geos, const SubDesc* subs, int nsub, int max_npad, int max_b,
+                              c128* Aloc, cudaStream_t st);
 cudaError_t launch_rhs(const Geo& g, const double* cen, const double* amp, int ns, double width, c128* b,
                        cudaStream_t st);
 
@@ -95,14 +110,28 @@ cudaError_t launch_spmv7(long long n, int nx, const Stencil7& A, const c128* x, 
 cudaError_t launch_factor_lu(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aw, void* L, void* Urev,
                              void* dinv, double* pivstats, DevStatus* status, cudaStream_t st);
 
+// factor_wide.cu: the subdomains with max_band(prec) < b <= kMaxBandWide,
+// each CTA in its own scratch slot (SubDesc::wslot) of factor_wide_slot_bytes
+// (prec, max_b) bytes; the other subdomains of the launch return at once.
+size_t factor_wide_slot_bytes(int prec, int max_b);
+cudaError_t launch_factor_wide(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
+                               void* Lrev, void* dinv, double* pivstats, DevStatus* status, void* scratch,
+                               cudaStream_t st);
+
 // factor.cu
 size_t factor_smem_bytes(int b, int prec, int rank);
+// Subdomains with b > max_band(prec) (up to kMaxBandWide) need wscratch of
+// (slots) x factor_wide_slot_bytes(prec, max_b) bytes, SubDesc::wslot < slots;
+// skip_wide leaves them out (the tuner times the other kernels' shapes).
 cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, int nsub, int max_b,
                           const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status,
-                          cudaStream_t st, BandSplit split = BandSplit{});
+                          cudaStream_t st, BandSplit split = BandSplit{}, void* wscratch = nullptr,
+                          bool skip_wide = false);
 
 // apply.cu
 size_t apply_smem_bytes(int max_bp, int prec, int cols);
+// wait limit of the apply's bulk copies on the current device (<= 0: default)
+cudaError_t set_copy_wait_limit(long long cycles);
 // Input kinds of r: complex128, double-float (dfc) or complex64
 enum : int { RK_C128 = 0, RK_DF = 1, RK_C64 = 2 };
 // Local solves of all subdomains into Y. The input is r of kind rkind, or
@@ -124,7 +153,7 @@ cudaError_t launch_apply(int prec, int cols, const Geo& g, const Geo* geos, cons
 // krylov.cu
 cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, const c128* CS, const c128* CSW,
                         const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st,
-                        int bsub_kind = RK_C128);
+                        int bsub_kind = RK_C128, int xdf = 0);
 // y = A x with double-float coefficients (dfc arrays from launch_split); y
 // written as dfc (double-float form) when out_df is set, x read as dfc when
 // in_df is set
@@ -160,6 +189,16 @@ cudaError_t launch_dots_c64b(const void* V, long long ldv, int ncols, const c128
 cudaError_t launch_axpys_c64b(const void* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
                               long long n, const KState* kst, cudaStream_t st, int wdf = 0, c128* pnorm = nullptr,
                               int* nblocks = nullptr);
+// The same projection and update on a basis in double-float form (dfc, the
+// split complex128 basis of ortho = 3), w held in double-float form; the
+// update leaves the per-block sums of |w|^2 in pnorm
+cudaError_t launch_dots_dfb(const void* V, long long ldv, int ncols, const void* wdf, long long n, c128* partial,
+                            const KState* kst, cudaStream_t st);
+cudaError_t launch_axpys_dfb(const void* V, long long ldv, int ncols, const c128* h, double sign, void* wdf,
+                             long long n, const KState* kst, cudaStream_t st, c128* pnorm, int* nblocks);
+// v = w / nrm, both in double-float form (in place allowed), on the FP32 pipe
+cudaError_t launch_scale_df_to_df(const void* w, void* v, long long n, const double* nrm, const KState* kst,
+                                  cudaStream_t st);
 // ||.|| from nparts partial sums (default: dot_blocks() of them)
 cudaError_t launch_norm_finish(const c128* partial, double* out, c128* hslot, const KState* kst, int gate,
                                cudaStream_t st, int nparts = 0);
@@ -173,7 +212,11 @@ cudaError_t launch_backsolve(const c128* H, int ldh, const c128* gvec, const KSt
                              cudaStream_t st);
 cudaError_t launch_axpy_state(c128* x, const c128* v, long long n, cudaStream_t st);
 // z += (hv[0] / hv[1]) c, skipped when hv[1] = 0 or kst->stop
-cudaError_t launch_mr_axpy(c128* z, const c128* c, const c128* hv, long long n, const KState* kst, cudaStream_t st);
+// z += alpha c (the learned stage's minimal-residual step, hv: <Ac, r1>,
+// ||Ac||^2, ||r1||^2); records the stage's gain in kst; z in double-float
+// form with zdf
+cudaError_t launch_mr_axpy(c128* z, const c128* c, const c128* hv, long long n, KState* kst, cudaStream_t st,
+                           int zdf = 0);
 
 }  // namespace rp
 

@@ -53,18 +53,25 @@ __device__ __forceinline__ c128 block_sum(c128 v) {
 // complex64 (2))
 __global__ void k_spmv(long long n, int nx, const c128* __restrict__ D, const c128* __restrict__ CW,
                        const c128* __restrict__ CS, const c128* __restrict__ CSW, const c128* __restrict__ x,
-                       const c128* __restrict__ bsub, int bdf, c128* __restrict__ y, const KState* __restrict__ kst) {
+                       const c128* __restrict__ bsub, int bdf, c128* __restrict__ y, const KState* __restrict__ kst,
+                       int xdf) {
   if (kst != nullptr && kst->stop) return;
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (r >= n) return;
+  // x in complex128, or in double-float form (xdf: the FGMRES directions z_j)
+  auto X = [&](long long q) -> c128 {
+    if (!xdf) return x[q];
+    const dfc v = reinterpret_cast<const dfc*>(x)[q];
+    return mk(df_to_d(v.rh, v.rl), df_to_d(v.ih, v.il));
+  };
   c128 a0 = mk(0.0, 0.0), a1 = mk(0.0, 0.0);
-  a0 = fmac(a0, D[r], x[r]);
-  if (r >= 1) a1 = fmac(a1, CW[r], x[r - 1]);
-  if (r + 1 < n) a0 = fmac(a0, CW[r + 1], x[r + 1]);
-  if (r >= nx) a1 = fmac(a1, CS[r], x[r - nx]);
-  if (r + nx < n) a0 = fmac(a0, CS[r + nx], x[r + nx]);
-  if (r >= nx + 1) a1 = fmac(a1, CSW[r], x[r - nx - 1]);
-  if (r + nx + 1 < n) a0 = fmac(a0, CSW[r + nx + 1], x[r + nx + 1]);
+  a0 = fmac(a0, D[r], X(r));
+  if (r >= 1) a1 = fmac(a1, CW[r], X(r - 1));
+  if (r + 1 < n) a0 = fmac(a0, CW[r + 1], X(r + 1));
+  if (r >= nx) a1 = fmac(a1, CS[r], X(r - nx));
+  if (r + nx < n) a0 = fmac(a0, CS[r + nx], X(r + nx));
+  if (r >= nx + 1) a1 = fmac(a1, CSW[r], X(r - nx - 1));
+  if (r + nx + 1 < n) a0 = fmac(a0, CSW[r + nx + 1], X(r + nx + 1));
   const c128 acc = a0 + a1;
   if (bsub) {
     c128 bv;
@@ -141,6 +148,8 @@ __global__ void __launch_bounds__(kSpTX * kSpTY)
   if (i >= 1 && j >= 1) cmac_df(rh, rl, ih, il, CSW[r], xs[tj][ti]);
   if (e_ok && n_ok) cmac_df(rh, rl, ih, il, CSW[r + nx + 1], xs[tj + 2][ti + 2]);
   if (out_df) {
+    df_norm(rh, rl);
+    df_norm(ih, il);
     dfc o;
     o.rh = rh;
     o.rl = rl;
@@ -351,14 +360,35 @@ __global__ void k_scale_to_c64(const c128* __restrict__ w, c64* __restrict__ v, 
   }
 }
 
+// Basis entries of the two stored forms: complex64 roundings (ortho = 4) or
+// double-float pairs (ortho = 3). bprod_* gives the real or imaginary part of
+// the entry times a double-float b as p + t (exact FMA residual of the
+// leading product).
+__device__ __forceinline__ void bprod_re(const c64& a, const dfl& b, float& p, float& t) { fdf_prod(a.re, b, p, t); }
+__device__ __forceinline__ void bprod_im(const c64& a, const dfl& b, float& p, float& t) { fdf_prod(a.im, b, p, t); }
+__device__ __forceinline__ void bprod_re(const dfc& a, const dfl& b, float& p, float& t) {
+  df_prod(dfl_of(a.rh, a.rl), b, p, t);
+}
+__device__ __forceinline__ void bprod_im(const dfc& a, const dfl& b, float& p, float& t) {
+  df_prod(dfl_of(a.ih, a.il), b, p, t);
+}
+template <typename B>
+__device__ __forceinline__ B bzero();
+template <>
+__device__ __forceinline__ c64 bzero<c64>() { return mk(0.f, 0.f); }
+template <>
+__device__ __forceinline__ dfc bzero<dfc>() { return dfc{0.f, 0.f, 0.f, 0.f}; }
+
 // partial[c * gridDim.x + blk] = sum over the block's rows of conj(V_c) w,
 // four columns per block, w read and split once per row of the block (eight
-// columns were measured: 105 registers per thread, slower on c2 and c4)
+// columns were measured on the complex64 basis: 105 registers per thread,
+// slower on c2 and c4)
 constexpr int kC64Cols = 4;
 
+template <typename B>
 __global__ void __launch_bounds__(kThreads)
-    k_dots_c64b(const c64* __restrict__ V, long long ldv, int ncols, const c128* __restrict__ w, int wdf, long long n,
-                c128* __restrict__ partial, const KState* __restrict__ kst) {
+    k_dots_b(const B* __restrict__ V, long long ldv, int ncols, const c128* __restrict__ w, int wdf, long long n,
+             c128* __restrict__ partial, const KState* __restrict__ kst) {
   if (skip(kst, 0)) return;
   constexpr int kDfCols = kC64Cols;
   const int c0 = blockIdx.y * kDfCols;
@@ -373,14 +403,14 @@ __global__ void __launch_bounds__(kThreads)
   for (long long r = r0 + threadIdx.x; r < r1; r += 2 * kThreads) {
     const bool two = r + kThreads < r1;
     c128 wv[2];
-    c64 a[2][kDfCols];
+    B a[2][kDfCols];
     wv[0] = w[r];
     wv[1] = two ? w[r + kThreads] : mk(0.0, 0.0);
 #pragma unroll
     for (int u = 0; u < 2; ++u)
 #pragma unroll
       for (int q = 0; q < kDfCols; ++q)
-        a[u][q] = (q < nc && (u == 0 || two)) ? V[(long long)(c0 + q) * ldv + r + u * kThreads] : mk(0.f, 0.f);
+        a[u][q] = (q < nc && (u == 0 || two)) ? V[(long long)(c0 + q) * ldv + r + u * kThreads] : bzero<B>();
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       // w held in double-float form already (wdf), or complex128 split here
@@ -391,13 +421,13 @@ __global__ void __launch_bounds__(kThreads)
         if (q >= nc) continue;
         float p, t;
         // conj(a) w = (ar wr + ai wi) + i (ar wi - ai wr)
-        fdf_prod(a[u][q].re, br, p, t);
+        bprod_re(a[u][q], br, p, t);
         df_acc(rh[q], rl[q], p, t);
-        fdf_prod(a[u][q].im, bi, p, t);
+        bprod_im(a[u][q], bi, p, t);
         df_acc(rh[q], rl[q], p, t);
-        fdf_prod(a[u][q].re, bi, p, t);
+        bprod_re(a[u][q], bi, p, t);
         df_acc(ih[q], il[q], p, t);
-        fdf_prod(a[u][q].im, br, p, t);
+        bprod_im(a[u][q], br, p, t);
         df_acc(ih[q], il[q], -p, -t);
       }
     }
@@ -436,10 +466,10 @@ __global__ void __launch_bounds__(kThreads)
 // w += sign * sum_c V_c h_c, double-float accumulation. With wdf, w is held
 // in double-float form (read and written as dfc); with pnorm, the block's
 // sum of |w|^2 (double-float, FP64 at the end) goes to pnorm[blockIdx.x].re.
+template <typename B>
 __global__ void __launch_bounds__(kThreads)
-    k_axpys_c64b(const c64* __restrict__ V, long long ldv, int ncols, const c128* __restrict__ h, double sign,
-                 c128* __restrict__ w, int wdf, c128* __restrict__ pnorm, long long n,
-                 const KState* __restrict__ kst) {
+    k_axpys_b(const B* __restrict__ V, long long ldv, int ncols, const c128* __restrict__ h, double sign,
+              c128* __restrict__ w, int wdf, c128* __restrict__ pnorm, long long n, const KState* __restrict__ kst) {
   if (skip(kst, 0)) return;
   extern __shared__ dfc hsc[];
   for (int c = threadIdx.x; c < ncols; c += blockDim.x) hsc[c] = split_c(mk(sign * h[c].re, sign * h[c].im));
@@ -451,9 +481,9 @@ __global__ void __launch_bounds__(kThreads)
     // two accumulator sets (even and odd columns) for two independent
     // dependency chains per part; added together at the end
     float rh[2] = {w0.rh, 0.f}, rl[2] = {w0.rl, 0.f}, ih[2] = {w0.ih, 0.f}, il[2] = {w0.il, 0.f};
-    constexpr int kU = 2 * kDfCols;   // basis entries loaded ahead of the arithmetic
+    constexpr int kU = 2 * kC64Cols;   // basis entries loaded ahead of the arithmetic
     for (int c0 = 0; c0 < ncols; c0 += kU) {
-      c64 a[kU];
+      B a[kU];
 #pragma unroll
       for (int q = 0; q < kU; ++q)
         if (c0 + q < ncols) a[q] = V[(long long)(c0 + q) * ldv + r];   // loads first
@@ -465,18 +495,20 @@ __global__ void __launch_bounds__(kThreads)
         const dfl hr = dfl_of(hc.rh, hc.rl), hi_ = dfl_of(hc.ih, hc.il);
         float p, t;
         // a h = (ar hr - ai hi) + i (ar hi + ai hr)
-        fdf_prod(a[q].re, hr, p, t);
+        bprod_re(a[q], hr, p, t);
         df_acc(rh[u], rl[u], p, t);
-        fdf_prod(a[q].im, hi_, p, t);
+        bprod_im(a[q], hi_, p, t);
         df_acc(rh[u], rl[u], -p, -t);
-        fdf_prod(a[q].re, hi_, p, t);
+        bprod_re(a[q], hi_, p, t);
         df_acc(ih[u], il[u], p, t);
-        fdf_prod(a[q].im, hr, p, t);
+        bprod_im(a[q], hr, p, t);
         df_acc(ih[u], il[u], p, t);
       }
     }
     df_acc(rh[0], rl[0], rh[1], rl[1]);
     df_acc(ih[0], il[0], ih[1], il[1]);
+    df_norm(rh[0], rl[0]);
+    df_norm(ih[0], il[0]);
     if (wdf) {
       dfc o;
       o.rh = rh[0];
@@ -512,6 +544,43 @@ __global__ void __launch_bounds__(kThreads)
       for (int u = 1; u < kThreads / 32; ++u) df_acc(a, b, red[u].x, red[u].y);
       pnorm[blockIdx.x] = mk(df_to_d(a, b), 0.0);
     }
+  }
+}
+
+// v = w / nrm in double-float form, both in double-float form (in place
+// allowed): 1/nrm as a double-float pair from an FP32 reciprocal and one
+// Newton step, products as FMA residual pairs, each part renormalised
+// (|lo| <= ulp(hi)/2) so that the stored basis is a valid split
+__global__ void k_scale_df_to_df(const dfc* w, dfc* v, long long n, const double* __restrict__ nrm,
+                                 const KState* __restrict__ kst) {
+  if (skip(kst, 0)) return;
+  const double d = *nrm;
+  if (!(d > 0.0)) return;
+  const dfl dd = split_d(d);
+  const float s0 = 1.f / dd.hi;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (!(dd.hi > 0.f) || !(s0 < 3e38f)) {
+    // nrm outside the FP32 range: FP64 (never on a regular step)
+    const double sd = 1.0 / d;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
+      const dfc x = w[r];
+      v[r] = split_c(mk(sd * ((double)x.rh + (double)x.rl), sd * ((double)x.ih + (double)x.il)));
+    }
+    return;
+  }
+  const float r0 = fmaf(-dd.hi, s0, 1.f) - dd.lo * s0;
+  const dfl s = dfl_of(s0, s0 * r0);
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
+    const dfc x = w[r];
+    float p, t;
+    dfc o;
+    df_prod(dfl_of(x.rh, x.rl), s, p, t);
+    o.rh = p + t;
+    o.rl = t - (o.rh - p);
+    df_prod(dfl_of(x.ih, x.il), s, p, t);
+    o.ih = p + t;
+    o.il = t - (o.ih - p);
+    v[r] = o;
   }
 }
 
@@ -688,14 +757,33 @@ __global__ void k_axpy(c128* __restrict__ x, const c128* __restrict__ v, long lo
 
 // z += alpha c with alpha = hv[0] / hv[1] (the minimal-residual step of a
 // correction c: hv[0] = <A c, r1>, hv[1] = <A c, A c>); nothing when hv[1] = 0
+// z += alpha c, alpha = <Ac, r1> / ||Ac||^2 (hv[0], hv[1]; hv[2] = ||r1||^2):
+// the minimal-residual step of the learned stage. Block 0 also records the
+// fraction of ||r1||^2 the step removes, |<Ac, r1>|^2 / (||Ac||^2 ||r1||^2),
+// as the stage's gain (largest over the solve, KState::lgain). z in
+// complex128, or in double-float form (zdf).
 __global__ void k_mr_axpy(c128* __restrict__ z, const c128* __restrict__ c, const c128* __restrict__ hv,
-                          long long n, const KState* __restrict__ kst) {
+                          long long n, KState* __restrict__ kst, int zdf) {
   if (kst != nullptr && kst->stop) return;
   const double d = hv[1].re;
   if (!(d > 0.0)) return;
   const c128 a = mk(hv[0].re / d, hv[0].im / d);
+  if (kst != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+    const double rr = hv[2].re;
+    const double gain = rr > 0.0 ? abs2(hv[0]) / (d * rr) : 0.0;
+    kst->lgain = fmax(kst->lgain, gain);
+    kst->ldirs += 1;
+  }
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) z[r] = fmac(z[r], a, c[r]);
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) {
+    if (zdf) {
+      dfc* zd = reinterpret_cast<dfc*>(z);
+      const dfc v = zd[r];
+      zd[r] = split_c(fmac(mk(df_to_d(v.rh, v.rl), df_to_d(v.ih, v.il)), a, c[r]));
+    } else {
+      z[r] = fmac(z[r], a, c[r]);
+    }
+  }
 }
 
 unsigned grid_for(long long n, int threads) {
@@ -717,9 +805,10 @@ int dot_blocks() {
 }
 
 cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, const c128* CS, const c128* CSW,
-                        const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st, int bsub_kind) {
+                        const c128* x, const c128* bsub, c128* y, const KState* kst, cudaStream_t st, int bsub_kind,
+                        int xdf) {
   unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
-  k_spmv<<<blocks, kThreads, 0, st>>>(n, nx, D, CW, CS, CSW, x, bsub, bsub_kind, y, kst);
+  k_spmv<<<blocks, kThreads, 0, st>>>(n, nx, D, CW, CS, CSW, x, bsub, bsub_kind, y, kst, xdf);
   return cudaGetLastError();
 }
 
@@ -843,31 +932,61 @@ cudaError_t launch_scale_to_c64(const c128* w, void* v, long long n, const doubl
   return cudaGetLastError();
 }
 
+template <typename B>
+cudaError_t launch_dots_bt(const void* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
+                           const KState* kst, cudaStream_t st, int wdf) {
+  dim3 grid(dot_blocks(), (ncols + kC64Cols - 1) / kC64Cols);
+  k_dots_b<B><<<grid, kThreads, 0, st>>>((const B*)V, ldv, ncols, w, wdf, n, partial, kst);
+  return cudaGetLastError();
+}
+
+template <typename B>
+cudaError_t launch_axpys_bt(const void* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
+                            long long n, const KState* kst, cudaStream_t st, int wdf, c128* pnorm, int* nblocks) {
+  dot_blocks();
+  const size_t smem = (size_t)ncols * sizeof(dfc);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_axpys_b<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned g = grid_for(n, kThreads);
+  if (nblocks) *nblocks = (int)g;
+  k_axpys_b<B><<<g, kThreads, smem, st>>>((const B*)V, ldv, ncols, h, sign, w, wdf, pnorm, n, kst);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dots_c64b(const void* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
                              const KState* kst, cudaStream_t st, int wdf) {
-  dim3 grid(dot_blocks(), (ncols + kC64Cols - 1) / kC64Cols);
-  k_dots_c64b<<<grid, kThreads, 0, st>>>((const c64*)V, ldv, ncols, w, wdf, n, partial, kst);
-  return cudaGetLastError();
+  return launch_dots_bt<c64>(V, ldv, ncols, w, n, partial, kst, st, wdf);
 }
 
 cudaError_t launch_axpys_c64b(const void* V, long long ldv, int ncols, const c128* h, double sign, c128* w,
                               long long n, const KState* kst, cudaStream_t st, int wdf, c128* pnorm,
                               int* nblocks) {
+  return launch_axpys_bt<c64>(V, ldv, ncols, h, sign, w, n, kst, st, wdf, pnorm, nblocks);
+}
+
+cudaError_t launch_dots_dfb(const void* V, long long ldv, int ncols, const void* wdf, long long n, c128* partial,
+                            const KState* kst, cudaStream_t st) {
+  return launch_dots_bt<dfc>(V, ldv, ncols, (const c128*)wdf, n, partial, kst, st, 1);
+}
+
+cudaError_t launch_axpys_dfb(const void* V, long long ldv, int ncols, const c128* h, double sign, void* wdf,
+                             long long n, const KState* kst, cudaStream_t st, c128* pnorm, int* nblocks) {
+  return launch_axpys_bt<dfc>(V, ldv, ncols, h, sign, (c128*)wdf, n, kst, st, 1, pnorm, nblocks);
+}
+
+cudaError_t launch_scale_df_to_df(const void* w, void* v, long long n, const double* nrm, const KState* kst,
+                                  cudaStream_t st) {
   dot_blocks();
-  const size_t smem = (size_t)ncols * sizeof(dfc);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_axpys_c64b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  const unsigned g = grid_for(n, kThreads);
-  if (nblocks) *nblocks = (int)g;
-  k_axpys_c64b<<<g, kThreads, smem, st>>>((const c64*)V, ldv, ncols, h, sign, w, wdf, pnorm, n, kst);
+  k_scale_df_to_df<<<grid_for(n, kThreads), kThreads, 0, st>>>((const dfc*)w, (dfc*)v, n, nrm, kst);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mr_axpy(c128* z, const c128* c, const c128* hv, long long n, const KState* kst, cudaStream_t st) {
+cudaError_t launch_mr_axpy(c128* z, const c128* c, const c128* hv, long long n, KState* kst, cudaStream_t st,
+                           int zdf) {
   dot_blocks();
-  k_mr_axpy<<<grid_for(n, kThreads), kThreads, 0, st>>>(z, c, hv, n, kst);
+  k_mr_axpy<<<grid_for(n, kThreads), kThreads, 0, st>>>(z, c, hv, n, kst, zdf);
   return cudaGetLastError();
 }
 

@@ -34,22 +34,29 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
   // on the wide subdomains (the batched form's order by band)
   int fthreads[8] = {128, 256, 512, 256, 512, 1024, 128, 128};
   const int franks[8] = {1, 1, 1, 2, 2, 2, 8, 16};
-  const bool tc_all = factor_tc_ok(t.prec, t.max_b);
-  const bool tc_mixed = !tc_all && t.prec >= 1 && t.split.nwide >= 0 && t.split.nwide < t.nsub;
-  const int nfc = (tc_all || tc_mixed) ? 8 : 6;
+  // shapes are judged and timed on the subdomains of the shared-memory
+  // kernels (the blocked wide-band kernel, the same in every candidate, runs
+  // only in the final factor); a CUDA-core shape with fewer threads than the
+  // widest window needs is skipped
+  const int nb = narrow_band(t.prec, t.max_b, t.split);
+  const bool tc_all = t.max_b <= max_band(t.prec) && factor_tc_ok(t.prec, t.max_b);
+  const bool tc_mixed = !tc_all && t.prec >= 1 && t.split.nwide >= 0 && t.split.nwide < t.nsub && nb > 0;
+  const int nfc = nb == 0 ? 0 : (tc_all || tc_mixed) ? 8 : 6;   // nb == 0: every subdomain is wide
   for (int c = 0; c < nfc && e == cudaSuccess; ++c) {
     if (c == 6 && tc_mixed) {
-      int b2 = 3;
-      for (int i = 4; i < 6; ++i)
-        if (rep.factor_ms[i] < rep.factor_ms[b2]) b2 = i;
-      fthreads[6] = fthreads[7] = fthreads[b2];
+      int b2 = -1;   // the fastest two-pivot shape timed so far
+      for (int i = 0; i < rep.n_factor; ++i)
+        if (rep.factor_cand_rank[i] == 2 && (b2 < 0 || rep.factor_ms[i] < rep.factor_ms[b2])) b2 = i;
+      if (b2 < 0) break;
+      fthreads[6] = fthreads[7] = rep.factor_cand_threads[b2];
     }
+    if (!factor_shape_valid(t.prec, nb, fthreads[c], franks[c], t.split)) continue;
     std::vector<float> ms;
     for (int r = 0; r < reps && e == cudaSuccess; ++r) {
       e = cudaEventRecord(e0, t.st);
       if (e == cudaSuccess)
         e = launch_factor(t.prec, fthreads[c], franks[c], t.subs, t.nsub, t.max_b, t.Aloc, t.L, t.Lrev, t.dinv,
-                          t.pivstats, t.status, t.st, t.split);
+                          t.pivstats, t.status, t.st, t.split, t.wscratch, /*skip_wide=*/true);
       if (e == cudaSuccess) e = cudaEventRecord(e1, t.st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       if (e == cudaSuccess) ms.push_back(ev_ms(e0, e1));
@@ -94,11 +101,18 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
   int fdef = 0;
   for (int i = 0; i < rep.n_factor; ++i)
     if (rep.factor_cand_threads[i] == 256 && rep.factor_cand_rank[i] == 2) fdef = i;
+  if (rep.n_factor == 0) {   // only wide subdomains: the shape does not matter
+    rep.factor_cand_threads[0] = 256;
+    rep.factor_cand_rank[0] = 2;
+    rep.factor_ms[0] = 0.f;
+    rep.n_factor = 1;
+  }
   const int bf = pick(rep.factor_ms, rep.n_factor, fdef);
   const int ba = rep.n_apply > 0 ? pick(rep.apply_ms, rep.n_apply, 0) : 0;
   // leave the factors of the chosen shape
   cudaError_t e3 = launch_factor(t.prec, rep.factor_cand_threads[bf], rep.factor_cand_rank[bf], t.subs, t.nsub,
-                                 t.max_b, t.Aloc, t.L, t.Lrev, t.dinv, t.pivstats, t.status, t.st, t.split);
+                                 t.max_b, t.Aloc, t.L, t.Lrev, t.dinv, t.pivstats, t.status, t.st, t.split,
+                                 t.wscratch);
   if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(t.st);
   if (e3 != cudaSuccess) {
     std::fprintf(stderr, "raspml: tune: %s\n", cudaGetErrorString(e3));

@@ -25,8 +25,16 @@ def test_reference_arm_prints_one_json_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "s"
     assert d["higher_is_better"] is False
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == min(cores, 9)
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+    # the same config object as the GPU arm's line
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads
+    assert d["config"] == bench.bench_config(workloads.get("tiny3"), 0, 1)
+    sp = d["cpu_baseline"]["split"]
+    assert abs(sp["total_s"] - (sp["setup_s"] + sp["factor_s"] + sp["solve_s"])) < 2e-3
 
 
 def test_form_option_is_validated_before_any_device_work():
@@ -39,7 +47,7 @@ def test_form_option_is_validated_before_any_device_work():
 
 
 def test_reference_arm_for_the_batched_workload():
-    """--workload c3: the oracle's bounded sample on the median problem, scaled
+    """--workload c3: the oracle's median problem solved on all cores, scaled
     by the oracle's own per-problem iteration counts (tests/golden)."""
     r = _run(["--impl", "reference", "--workload", "c3", "--steps", "1", "--warmup", "0"], {})
     assert r.returncode == 0, r.stderr

@@ -213,4 +213,7 @@ def test_mixed_band_factor_shape(pkg):
         for shape in ((1024, 8), (512, 16)):
             assert np.all(np.abs(np.asarray(its[shape]) - np.asarray(its[(1024, 2)])) <= 1), its
         rep = B.tune()
-        assert {"1024x2", "512x2"} <= set(rep["factor_ms"]) and len(rep["factor_ms"]) == 8
+        # 128 threads cannot hold the 194 diagonals of the b = 193 window:
+        # that shape is skipped, the other seven are timed
+        assert {"1024x2", "512x2"} <= set(rep["factor_ms"]) and len(rep["factor_ms"]) == 7
+        assert "128x1" not in rep["factor_ms"]
