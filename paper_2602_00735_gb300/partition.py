@@ -22,6 +22,14 @@ One apply z = B^-1 r = sum_j R_j^T (chi_j * A_j^-1 R_j r):
   the overlaps (Section 3 (i); Section 4 runs one process per subdomain).
 One product y = A x needs x one node beyond the owned ones (the 1-cell
 halo of the seven-point stencil).
+
+Algorithm 1 (u <- u + B^-1 (F - A u)) after its first sweep: the new
+residual vanishes at every node whose stencil lies where a single chi_j is 1
+(there A B^-1 r reproduces r exactly), so it lives on the nodes within ovlp
+of an interior box edge in either direction (Section 3 (i)). The restriction
+halo of those sweeps shrinks to its part in that support
+(restrict_recv_sparse): the local PML extension beyond the overlap is no
+longer exchanged.
 """
 from __future__ import annotations
 
@@ -87,6 +95,8 @@ class Plan:
       subdomains[r]          its subdomains (natural index qy px + qx)
       owned[r]               its unknowns, sorted
       restrict_recv[r][s]    unknowns it receives from rank s before an apply
+      restrict_recv_sparse[r][s]  the same within the residual's support (the
+                             later sweeps of Algorithm 1)
       prolong_send[r][s]     (subdomain, unknown) pairs whose contribution it
                              sends to rank s after its local solves
       spmv_recv[r][s]        unknowns it receives from rank s before a product
@@ -104,6 +114,7 @@ class Plan:
     subdomains: list = field(default_factory=list)
     owned: list = field(default_factory=list)
     restrict_recv: list = field(default_factory=list)
+    restrict_recv_sparse: list = field(default_factory=list)
     prolong_send: list = field(default_factory=list)
     spmv_recv: list = field(default_factory=list)
 
@@ -125,6 +136,7 @@ class Plan:
         owner = (rank_y[:, None] * Rx + rank_x[None, :]).ravel()   # index (j-1) nx + (i-1)
         plan = cls(Mx, My, px, py, ovlp, pml, local_bc, Rx, Ry)
         R = Rx * Ry
+        support = plan.residual_support()
 
         def nodes(lo, hi):
             return np.arange(lo, hi + 1)
@@ -151,6 +163,8 @@ class Plan:
                         contrib[int(s)].extend((q, int(v)) for v in gc[owner[gc] == s])
             need = np.array(sorted(need), dtype=np.int64)
             plan.restrict_recv.append({int(s): need[owner[need] == s] for s in np.unique(owner[need])})
+            sparse = need[support[need]]
+            plan.restrict_recv_sparse.append({int(s): sparse[owner[sparse] == s] for s in np.unique(owner[sparse])})
             plan.prolong_send.append({s: v for s, v in contrib.items() if v})
             # SpMV halo: the W, E, S, N, SW, NE neighbours of owned nodes
             o = plan.owned[r]
@@ -164,6 +178,25 @@ class Plan:
             halo = np.array(sorted(halo), dtype=np.int64)
             plan.spmv_recv.append({int(s): halo[owner[halo] == s] for s in np.unique(owner[halo])})
         return plan
+
+    def residual_support(self) -> np.ndarray:
+        """Mask over the unknowns of where a residual b - A u can be non-zero
+        after a sweep of Algorithm 1: nodes within ovlp of an interior box
+        edge in x or in y (their stencil touches a node covered by two
+        subdomains' chi > 0)."""
+        def near(M, P):
+            c = box_edges(M, P)[1:-1]
+            i = np.arange(1, M)
+            if c.size == 0:
+                return np.zeros(M - 1, dtype=bool)
+            return np.min(np.abs(i[:, None] - c[None, :]), axis=1) <= self.ovlp
+        sx, sy = near(self.Mx, self.px), near(self.My, self.py)
+        return (sy[:, None] | sx[None, :]).ravel()
+
+    def restrict_send_sparse(self, r: int) -> dict:
+        """Unknowns rank r sends to each other rank before a later sweep of
+        Algorithm 1 (the residual's support only)."""
+        return {s: self.restrict_recv_sparse[s][r] for s in range(self.nranks) if r in self.restrict_recv_sparse[s]}
 
     def restrict_send(self, r: int) -> dict:
         """Unknowns rank r sends to each other rank before an apply."""
@@ -181,5 +214,6 @@ class Plan:
         """Bytes rank r receives per apply and per product (complex128
         entries): restriction halo, prolongation contributions, SpMV halo."""
         return {"restrict": entry_bytes * sum(len(v) for v in self.restrict_recv[r].values()),
+                "restrict_sparse": entry_bytes * sum(len(v) for v in self.restrict_recv_sparse[r].values()),
                 "prolong": entry_bytes * sum(len(v) for v in self.prolong_recv(r).values()),
                 "spmv": entry_bytes * sum(len(v) for v in self.spmv_recv[r].values())}

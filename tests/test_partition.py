@@ -184,3 +184,131 @@ def test_plan_covers_every_unknown_once_and_exchanges_only_overlaps(name, Rx, Ry
             assert dist(idx) <= 1
         b = plan.exchange_bytes(r)
         assert b["restrict"] > 0 and b["prolong"] > 0 and b["spmv"] > 0
+
+
+def test_residual_after_a_sweep_lives_on_the_plans_support():
+    """One sweep of Algorithm 1 in the oracle (u = B^-1 F): b - A u vanishes,
+    to rounding, outside the plan's residual support (Section 3 (i))."""
+    from oracle import fem, ras
+    for name, kw in (("tiny3", {}), ("small", {"px": 3, "py": 5}), ("small", {"local_bc": 1})):
+        w = workloads.get(name).with_(**kw)
+        p = w.params()
+        grid, A = fem.assemble_global(p)
+        b = fem.assemble_rhs(p, w.centres, w.amps, w.width)
+        u = ras.RAS(p).factor().apply(b)
+        res = b - A @ u
+        sup = _plan(w, 1, 1).residual_support()
+        assert np.max(np.abs(res[~sup])) <= 1e-12 * np.max(np.abs(res))
+        assert np.max(np.abs(res[sup])) > 1e-3 * np.linalg.norm(b)     # and does not vanish on it
+        assert sup.mean() < 0.9
+
+
+def _richardson_rank(rank, world, port, case, sweeps, q):
+    import scipy.sparse.linalg as spla
+    import torch.distributed as dist
+
+    from oracle import fem, ras
+    name, Rx, Ry, kw = CASES[case]
+    w = workloads.get(name).with_(**kw)
+    p = w.params()
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        plan = _plan(w, Rx, Ry)
+        grid, rxs, rys = ras.covering(p)
+        grid, A = fem.assemble_global(p)
+        A = A.tocsr()
+        n = grid.n
+        b_full = fem.assemble_rhs(p, w.centres, w.amps, w.width)
+        own = plan.owned[rank]
+        owner = np.empty(n, dtype=np.int64)
+        for s in range(world):
+            owner[plan.owned[s]] = s
+        subs = []
+        for qd in plan.subdomains[rank]:
+            sd = ras.build_subdomain(p, grid, rxs[qd % p["px"]], rys[qd // p["px"]])
+            subs.append((qd, sd, spla.splu(sd.A.tocsc())))
+        u = np.zeros(n, dtype=complex)          # owned entries meaningful
+        sent = 0
+        for it in range(sweeps):
+            # r = F - A u on owned rows, with the SpMV halo of u
+            uh = np.full(n, np.nan + 0j)
+            uh[own] = u[own]
+            got = _xchg(dist, plan.spmv_send(rank), {s: len(v) for s, v in plan.spmv_recv[rank].items()},
+                        lambda d, idx: uh[idx], lambda c: c)
+            for s, vals in got.items():
+                uh[plan.spmv_recv[rank][s]] = vals
+            r = np.full(n, np.nan + 0j)
+            r[own] = b_full[own] - A[own] @ uh
+            # restriction halo: full before the first sweep, the residual's
+            # support after it (zero is taken elsewhere)
+            recv = plan.restrict_recv[rank] if it == 0 else plan.restrict_recv_sparse[rank]
+            send = plan.restrict_send(rank) if it == 0 else plan.restrict_send_sparse(rank)
+            if it > 0:
+                full = np.concatenate([v for v in plan.restrict_recv[rank].values()])
+                r[full] = 0.0
+            got = _xchg(dist, send, {s: len(v) for s, v in recv.items()}, lambda d, idx: r[idx], lambda c: c)
+            for s, vals in got.items():
+                r[recv[s]] = vals
+                sent += len(vals)
+            contrib = []
+            for qd, sd, lu in subs:
+                c = sd.chi * lu.solve(r[sd.glob])
+                m = sd.chi > 0
+                contrib.extend(zip([qd] * int(m.sum()), sd.glob[m].tolist(), c[m].tolist()))
+            mine = [t for t in contrib if owner[t[1]] == rank]
+            away = {}
+            for t in contrib:
+                if owner[t[1]] != rank:
+                    away.setdefault(int(owner[t[1]]), []).append(t)
+            recv_pairs = plan.prolong_recv(rank)
+            got = _xchg(dist, {s: [v for _, _, v in away[s]] for s in away},
+                        {s: len(v) for s, v in recv_pairs.items()}, lambda d, vals: np.array(vals, dtype=complex),
+                        lambda c: c)
+            for s, vals in got.items():
+                mine.extend((int(a), int(b), v) for (a, b), v in zip(recv_pairs[s], vals))
+            z = np.zeros(n, dtype=complex)
+            for qd, node, v in sorted(mine, key=lambda t: (t[1], t[0])):
+                z[node] = z[node] + v
+            u[own] = u[own] + z[own]
+        q.put((rank, own, u[own], sent))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("case", [0, 1, 4], ids=["tiny3-2x1", "small-2x1", "small-2x1-px3-py5"])
+def test_algorithm_1_with_the_reduced_restriction_halo(case):
+    """Algorithm 1 on two gloo ranks: the first sweep exchanges the full
+    restriction halo, the later ones only its part in the residual's support;
+    after 4 sweeps the iterate equals the one-rank oracle's to rounding, with
+    fewer values exchanged than with the full halo every sweep."""
+    import torch.multiprocessing as mp
+
+    from oracle import fem, krylov, ras
+    name, Rx, Ry, kw = CASES[case]
+    w = workloads.get(name).with_(**kw)
+    p = w.params()
+    sweeps = 4
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_richardson_rank, args=(r, 2, port, case, sweeps, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    res = [q.get(timeout=300) for _ in range(2)]
+    for pr in procs:
+        pr.join(timeout=120)
+    assert all(pr.exitcode == 0 for pr in procs)
+    grid, A = fem.assemble_global(p)
+    b = fem.assemble_rhs(p, w.centres, w.amps, w.width)
+    u_ref, it, _, _ = krylov.richardson(A.dot, ras.RAS(p).factor().apply, b, rtol=0.0, maxit=sweeps)
+    assert it == sweeps
+    u = np.full(grid.n, np.nan + 0j)
+    plan = _plan(w, Rx, Ry)
+    full = 0
+    for rank, own, uo, sent in res:
+        u[own] = uo
+        full += sweeps * sum(len(v) for v in plan.restrict_recv[rank].values())
+    assert np.linalg.norm(u - u_ref) <= 1e-12 * np.linalg.norm(u_ref)
+    assert sum(t[3] for t in res) < 0.9 * full
