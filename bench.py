@@ -481,6 +481,10 @@ def run_ours(args, rank, world, local_rank):
                               stream, dev, x_c64)
     del x_c64
 
+    richardson = None
+    if not args.skip_extra and args.form == 0:
+        richardson = run_richardson(args, p, w, shapes[(w.name, args.prec)], stream)
+
     # config 4 (k = 320*pi) and the batched config 3 in the same run
     extra = {}
     # the FP64 step of config 4 runs once, with the default tile shapes (its
@@ -529,7 +533,7 @@ def run_ours(args, rank, world, local_rank):
         "fp64": fp64, "error_vs_fp64": err, "error_vs_oracle": err_oracle, "c64_basis": c64b,
         "alu_peaks_measured": alu,
         "tune": shapes[(w.name, args.prec)][3],
-        "learned": learned, **extra,
+        "learned": learned, "richardson": richardson, **extra,
         "gpu_launches": int(sum(launches_per_step)),
         "gpu_launches_per_step": int(launches_per_step[-1]),
         "clocks": clk, "e2e": e2e,
@@ -611,6 +615,37 @@ def run_learned(args, p, w, shp, iters_plain, t_plain, stream, dev, x_ref):
                     "after 4 directions that each removed < 5% of the residual's squared norm (stage_directions: "
                     "directions it corrected; stage_largest_gain: the best fraction it removed); time excludes "
                     "training"}
+
+
+def run_richardson(args, p, w, shp, stream):
+    """Algorithm 1 (u <- u + B^-1 (F - A u)) on the same workload with the
+    headline's local factors: set-up, factor and sweeps to rtol 1e-6, 1 warm-up
+    and 2 timed steps, split as the paper's Table 4 (set-up + factor, solve)."""
+    import torch
+
+    from paper_2602_00735_gb300 import RasPml
+    times, its, rels, fac = [], None, None, None
+    for k in range(3):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        s = RasPml(p, factor_prec=args.prec, ortho=args.ortho)
+        s.set_shapes(*shp[:3])
+        b = s.assemble_rhs(w.centres, w.amps, w.width)
+        s.factor()
+        e1.record(stream)
+        x, its, rels, st = s.richardson(b, rtol=RTOL, maxit=2000)
+        e2.record(stream)
+        e2.synchronize()
+        if k > 0:
+            times.append(e0.elapsed_time(e2) / 1e3)
+            fac = e0.elapsed_time(e1) / 1e3
+        s.close()
+        del x, b
+    t = float(np.mean(times))
+    return {"time_s": round(t, 4), "steps": len(times), "sweeps": int(its), "relres": float(rels),
+            "setup_factor_s": round(fac, 4), "solve_s": round(t - fac, 4),
+            "note": "Algorithm 1 with the headline's complex64 local factors; sweeps enqueued four at a time, "
+                    "the host reads the device stop flag one batch late"}
 
 
 def summary_c4(args, timed, rel_err):

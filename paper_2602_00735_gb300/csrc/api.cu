@@ -871,39 +871,61 @@ int ras_pml_richardson(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, 
   }
   int s = ensure_krylov(h, 1, maxit);
   if (s) return s;
+  if ((s = ensure_events(h, 2)) != RASPML_OK) return s;
   if (!h->tmp_r) RP_ALLOC(h->tmp_r, (size_t)h->n);
   const long long n = h->n;
   const c128* b = (const c128*)b_dev;
   c128* x = (c128*)x_dev;
-  if ((s = dev_norm(h, b, h->scal, nullptr, nullptr))) return s;
-  double bn = 0.0;
-  RP_CUDA(cudaMemcpyAsync(&bn, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-  RP_CUDA(cudaStreamSynchronize(h->st));
-  h->hist_host.clear();
-  int it = 0;
-  double rel = 0.0;
-  int status = RASPML_NOT_CONVERGED;
-  for (;; ++it) {
-    RP_CUDA(spmv_A(h, x, b, h->tmp_r, nullptr, h->st));
-    if ((s = dev_norm(h, h->tmp_r, h->scal, nullptr, nullptr))) return s;
-    double rn = 0.0;
-    RP_CUDA(cudaMemcpyAsync(&rn, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    RP_CUDA(cudaStreamSynchronize(h->st));
-    rel = bn > 0.0 ? rn / bn : 0.0;
-    h->hist_host.push_back(rel);
-    if (!std::isfinite(rel)) { status = RASPML_ENAN; break; }
-    if (rel <= rtol) { status = RASPML_OK; break; }
-    if (it >= maxit) break;
-    RP_CUDA(rp::launch_apply(h->p.factor_prec, h->tune.apply_cols, h->geo, h->geo_d, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev, h->dinv,
-                             h->tmp_r, h->Y, h->V, nullptr, h->status, h->st));
-    RP_CUDA(rp::launch_axpy_state(x, h->V, n, h->st));
+  cudaStream_t st = h->st;
+  // Sweeps in batches of four: each sweep is r = b - A x, ||r||, the check
+  // (stop flag once rel <= rtol or after maxit sweeps), z = B^-1 r, x += z;
+  // every kernel reads the stop flag first, and the host reads it one batch
+  // late, so it synchronises once per four sweeps.
+  KState k0{};
+  RP_CUDA(cudaMemcpyAsync(h->kst, &k0, sizeof(k0), cudaMemcpyHostToDevice, st));
+  if ((s = dev_norm(h, b, &h->kst->bnorm, nullptr, nullptr))) return s;
+  const int batch = 4;
+  int slot = 0, pending = -1;
+  bool stopped = false;
+  for (int it0 = 0; !stopped; it0 += batch) {
+    for (int it = it0; it < it0 + batch && it <= maxit; ++it) {
+      RP_CUDA(spmv_A(h, x, b, h->tmp_r, h->kst, st));
+      if ((s = dev_norm(h, h->tmp_r, &h->kst->hnorm, nullptr, h->kst))) return s;
+      RP_CUDA(rp::launch_rich_check(h->kst, rtol, maxit, it, h->hist, st));
+      RP_CUDA(rp::launch_apply(h->p.factor_prec, h->tune.apply_cols, h->geo, h->geo_d, h->subs_d, h->nsub, h->max_b,
+                               h->max_bp, h->L, h->Lrev, h->dinv, h->tmp_r, h->Y, h->V, h->kst, h->status, st));
+      RP_CUDA(rp::launch_axpy_state(x, h->V, n, st, h->kst));
+    }
+    RP_CUDA(cudaMemcpyAsync(h->kst_host + slot, h->kst, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    RP_CUDA(cudaEventRecord(h->ev[slot], st));
+    if (pending >= 0) {
+      RP_CUDA(cudaEventSynchronize(h->ev[pending]));
+      if (h->kst_host[pending].stop) stopped = true;
+    }
+    if (it0 + batch > maxit) {   // every sweep is enqueued: wait for the last batch
+      RP_CUDA(cudaEventSynchronize(h->ev[slot]));
+      stopped = true;
+      pending = slot;
+    }
+    if (!stopped) {
+      pending = slot;
+      slot ^= 1;
+    }
   }
+  RP_CUDA(cudaStreamSynchronize(st));
+  RP_CUDA(cudaMemcpy(h->kst_host, h->kst, sizeof(KState), cudaMemcpyDeviceToHost));
+  const KState ks = *h->kst_host;
+  const int it = ks.total;
+  const double rel = ks.est;
+  h->hist_host.resize(it + 1);
+  RP_CUDA(cudaMemcpy(h->hist_host.data(), h->hist, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost));
   h->last_iters = it;
   if (iters) *iters = it;
   if (relres) *relres = rel;
   int ts = check_status(h);
   if (ts != RASPML_OK) return ts;
-  return status;
+  if (ks.nan) return RASPML_ENAN;
+  return ks.conv ? RASPML_OK : RASPML_NOT_CONVERGED;
 }
 
 int ras_pml_set_timing(ras_pml_handle* h, int enable) {

@@ -210,7 +210,10 @@ cudaError_t launch_givens(KState* kst, c128* H, int ldh, double* cs, c128* sn, c
 cudaError_t launch_reorth_decide(KState* kst, c128* hcol, int j, double eta2, cudaStream_t st);
 cudaError_t launch_backsolve(const c128* H, int ldh, const c128* gvec, const KState* kst, c128* y,
                              cudaStream_t st);
-cudaError_t launch_axpy_state(c128* x, const c128* v, long long n, cudaStream_t st);
+// x += v; nothing once kst->stop is set (kst may be null)
+cudaError_t launch_axpy_state(c128* x, const c128* v, long long n, cudaStream_t st, const KState* kst = nullptr);
+// the residual check of a sweep of Algorithm 1 (sets the stop flag)
+cudaError_t launch_rich_check(KState* kst, double rtol, int maxit, int it, double* hist, cudaStream_t st);
 // z += (hv[0] / hv[1]) c, skipped when hv[1] = 0 or kst->stop
 // z += alpha c (the learned stage's minimal-residual step, hv: <Ac, r1>,
 // ||Ac||^2, ||r1||^2); records the stage's gain in kst; z in double-float

@@ -750,7 +750,8 @@ __global__ void k_backsolve(const c128* __restrict__ H, int ldh, const c128* __r
   }
 }
 
-__global__ void k_axpy(c128* __restrict__ x, const c128* __restrict__ v, long long n) {
+__global__ void k_axpy(c128* __restrict__ x, const c128* __restrict__ v, long long n, const KState* __restrict__ kst) {
+  if (kst != nullptr && kst->stop) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += stride) x[r] = x[r] + v[r];
 }
@@ -990,9 +991,35 @@ cudaError_t launch_mr_axpy(c128* z, const c128* c, const c128* hv, long long n, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_axpy_state(c128* x, const c128* v, long long n, cudaStream_t st) {
+// The residual check of a sweep of Algorithm 1: rel = ||r|| / ||b|| from
+// kst->hnorm and kst->bnorm, into hist[it]; the stop flag once rel <= rtol,
+// it reaches maxit, or rel is not finite (every later kernel of the loop
+// returns at once).
+__global__ void k_rich_check(KState* kst, double rtol, int maxit, int it, double* hist) {
+  if (kst->stop) return;
+  const double rel = kst->bnorm > 0.0 ? kst->hnorm / kst->bnorm : 0.0;
+  hist[it] = rel;
+  kst->est = rel;
+  kst->total = it;
+  if (!isfinite(rel)) {
+    kst->nan = 1;
+    kst->stop = 1;
+  } else if (rel <= rtol) {
+    kst->conv = 1;
+    kst->stop = 1;
+  } else if (it >= maxit) {
+    kst->stop = 1;
+  }
+}
+
+cudaError_t launch_rich_check(KState* kst, double rtol, int maxit, int it, double* hist, cudaStream_t st) {
+  k_rich_check<<<1, 1, 0, st>>>(kst, rtol, maxit, it, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_state(c128* x, const c128* v, long long n, cudaStream_t st, const KState* kst) {
   dot_blocks();
-  k_axpy<<<grid_for(n, kThreads), kThreads, 0, st>>>(x, v, n);
+  k_axpy<<<grid_for(n, kThreads), kThreads, 0, st>>>(x, v, n, kst);
   return cudaGetLastError();
 }
 
