@@ -687,7 +687,7 @@ def summary_c3(args, stream):
         srcs = [(v.centres, v.amps, v.width) for v in probs]
         B0 = BatchRasPml(params, factor_prec=args.prec)
         tune = B0.tune()
-        shp = (tune["factor_threads"], tune["factor_rank"], tune["apply_cols"])
+        shp = (tune["factor_threads"], tune["factor_rank"], tune["apply_cols"], tune["wide_cluster"])
         B0.close()
         times = []
         for k in range(3):
@@ -759,7 +759,7 @@ def run_batch(args, rank, world, local_rank):
     else:
         B0 = BatchRasPml(params, factor_prec=args.prec)
         tune = B0.tune()
-        shapes = (tune["factor_threads"], tune["factor_rank"], tune["apply_cols"])
+        shapes = (tune["factor_threads"], tune["factor_rank"], tune["apply_cols"], tune["wide_cluster"])
         B0.close()
     for _ in range(args.warmup):
         B, b, x, it, rel, st = one_step()

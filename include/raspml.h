@@ -304,7 +304,11 @@ void ras_pml_destroy(ras_pml_handle* h);
  * half-bandwidth is <= 127, the blocked form on the tensor cores (128
  * threads, factor_rank 8 or 16: that many pivots per panel, the trailing
  * update as TF32 MMAs with a three-term split of each FP32 operand); apply
- * columns 8, plus 4 and 16 when factor_prec = 1.
+ * columns 8, plus 4 and 16 when factor_prec = 1; where subdomains are wider
+ * than the shared-memory window, the wide-band factor's cluster size (1, 2
+ * or 4 CTAs per subdomain; kept: the automatic choice, the largest size for
+ * which all wide subdomains' clusters are resident at once, unless another
+ * beats it by 2%).
  * Synchronises the stream. With form 1 it factors once and times nothing
  * (one factor shape; the apply shape stays as set; n_factor = n_apply = 0).
  * ------------------------------------------------------------------------- */
@@ -320,6 +324,13 @@ typedef struct {
   int32_t apply_cand[4];
   float   apply_ms[4];       /* median time of each apply candidate (local
                                 solves of all subdomains)                     */
+  int32_t wide_cluster;      /* CTAs per subdomain of the wide-band factor in
+                                use (0: no wide subdomain)                    */
+  int32_t n_wide;            /* cluster sizes timed (entries below; 0 when no
+                                subdomain is wider than the shared-memory
+                                window)                                       */
+  int32_t wide_cand[4];
+  float   wide_ms[4];        /* time of the wide-band factor's launch        */
 } ras_pml_tune_t;
 
 int ras_pml_tune(ras_pml_handle* h, ras_pml_tune_t* report);
@@ -329,9 +340,10 @@ int ras_pml_tune(ras_pml_handle* h, ras_pml_tune_t* report);
  * factor_rank 1 or 2, 1024 with factor_rank 2, or 128 with factor_rank 8
  * or 16 (the tensor-core form: factor_prec >= 1 and every half-bandwidth
  * <= 127);
- * apply_cols 8, or 4 or 16 with factor_prec = 1. RASPML_EBADARG for other
- * values. */
-int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, int apply_cols);
+ * apply_cols 8, or 4 or 16 with factor_prec = 1; wide_cluster 1, 2 or 4
+ * CTAs per subdomain of the wide-band factor, or 0 for the automatic choice.
+ * RASPML_EBADARG for other values. */
+int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, int apply_cols, int wide_cluster);
 
 /* ---------------------------------------------------------------------------
  * Batched form: many independent problems in the same launches. The paper
@@ -404,7 +416,8 @@ int ras_pml_batch_factor(ras_pml_batch* h);
 
 /* ras_pml_tune and ras_pml_set_shapes on the batch's subdomains. */
 int ras_pml_batch_tune(ras_pml_batch* h, ras_pml_tune_t* report);
-int ras_pml_batch_set_shapes(ras_pml_batch* h, int factor_threads, int factor_rank, int apply_cols);
+int ras_pml_batch_set_shapes(ras_pml_batch* h, int factor_threads, int factor_rank, int apply_cols,
+                             int wide_cluster);
 
 /* z = B_q^-1 r for every problem q (batch vectors, must not overlap). */
 int ras_pml_batch_apply(ras_pml_batch* h, const rp_c128* r_dev, rp_c128* z_dev);

@@ -56,7 +56,8 @@ class TuneReport(ctypes.Structure):
     _fields_ = [("factor_threads", c_int32), ("factor_rank", c_int32), ("apply_cols", c_int32),
                 ("n_factor", c_int32), ("n_apply", c_int32), ("factor_cand_threads", c_int32 * 8),
                 ("factor_cand_rank", c_int32 * 8), ("factor_ms", ctypes.c_float * 8),
-                ("apply_cand", c_int32 * 4), ("apply_ms", ctypes.c_float * 4)]
+                ("apply_cand", c_int32 * 4), ("apply_ms", ctypes.c_float * 4), ("wide_cluster", c_int32),
+                ("n_wide", c_int32), ("wide_cand", c_int32 * 4), ("wide_ms", ctypes.c_float * 4)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -104,8 +105,8 @@ def load() -> ctypes.CDLL:
     lib.ras_pml_destroy.argtypes = [H]
     lib.ras_pml_destroy.restype = None
     lib.ras_pml_tune.argtypes = [H, POINTER(TuneReport)]
-    lib.ras_pml_set_shapes.argtypes = [H, c_int, c_int, c_int]
-    lib.ras_pml_batch_set_shapes.argtypes = [H, c_int, c_int, c_int]
+    lib.ras_pml_set_shapes.argtypes = [H, c_int, c_int, c_int, c_int]
+    lib.ras_pml_batch_set_shapes.argtypes = [H, c_int, c_int, c_int, c_int]
     lib.ras_pml_batch_setup.argtypes = [POINTER(Params), c_int, c_void_p, POINTER(c_void_p)]
     lib.ras_pml_batch_info.argtypes = [H, POINTER(BatchInfo)]
     lib.ras_pml_batch_layout.argtypes = [H, c_void_p, c_void_p]

@@ -82,9 +82,11 @@ class BatchRasPml:
         _lib.check("ras_pml_batch_tune", self.lib.ras_pml_batch_tune(self._h, byref(rep)))
         return tune_dict(rep)
 
-    def set_shapes(self, factor_threads: int, factor_rank: int, apply_cols: int) -> None:
+    def set_shapes(self, factor_threads: int, factor_rank: int, apply_cols: int, wide_cluster: int = 0) -> None:
+        """Tile shapes (e.g. another batch's tuning); wide_cluster 0: automatic."""
         _lib.check("ras_pml_batch_set_shapes",
-                   self.lib.ras_pml_batch_set_shapes(self._h, int(factor_threads), int(factor_rank), int(apply_cols)))
+                   self.lib.ras_pml_batch_set_shapes(self._h, int(factor_threads), int(factor_rank), int(apply_cols),
+                                                     int(wide_cluster)))
 
     # -- operators and solver ----------------------------------------------------
     def apply(self, r: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:

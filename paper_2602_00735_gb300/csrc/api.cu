@@ -313,6 +313,7 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   h->sum_npad = v_off;
   h->sum_l = l_off;
   h->nwslot = rp::assign_wide_slots(h->subs_h, h->p.factor_prec, &h->split.max_b_narrow);
+  h->split.nblocked = h->nwslot;
 
   int s;
 #define SETUP_ALLOC(ptr, cnt) \
@@ -452,7 +453,7 @@ int ras_pml_factor(ras_pml_handle* h) {
     e = rp::launch_local_rows(h->p.factor_prec, h->geo_d, h->subs_d, h->nsub, h->max_npad, h->max_b, Aloc, h->st);
   if (e == cudaSuccess && !weak)
     e = rp::launch_factor(h->p.factor_prec, h->tune.factor_threads, h->tune.factor_rank, h->subs_d, h->nsub, h->max_b, Aloc, h->L, h->Lrev, h->dinv,
-                          h->pivstats, h->status, h->st, h->split, wscratch);
+                          h->pivstats, h->status, h->st, h->split, wscratch, false, h->tune.wide_cluster);
   if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[1], h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e == cudaSuccess && h->timing) h->tm.factor_ms = ev_ms(h->ev[0], h->ev[1]);
@@ -522,15 +523,17 @@ int ras_pml_tune(ras_pml_handle* h, ras_pml_tune_t* report) {
   return s;
 }
 
-int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, int apply_cols) {
+int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, int apply_cols, int wide_cluster) {
   if (!h ||
       !rp::factor_shape_valid(h->p.factor_prec, rp::narrow_band(h->p.factor_prec, h->max_b, h->split), factor_threads,
                               factor_rank) ||
-      !rp::apply_cols_valid(h->p.factor_prec, apply_cols))
+      !rp::apply_cols_valid(h->p.factor_prec, apply_cols) ||
+      !(wide_cluster == 0 || wide_cluster == 1 || wide_cluster == 2 || wide_cluster == 4))
     return RASPML_EBADARG;
   h->tune.factor_threads = factor_threads;
   h->tune.factor_rank = factor_rank;
   h->tune.apply_cols = apply_cols;
+  h->tune.wide_cluster = wide_cluster;
   return RASPML_OK;
 }
 

@@ -264,6 +264,7 @@ int ras_pml_batch_setup(const ras_pml_params* params, int nprob, void* stream, r
   h->sum_npad = v_off;
   h->sum_l = l_off;
   h->nwslot = rp::assign_wide_slots(h->subs_h, h->prec, &h->split.max_b_narrow);
+  h->split.nblocked = h->nwslot;
 
   int s;
 #define BS_ALLOC(ptr, cnt) \
@@ -436,7 +437,8 @@ int ras_pml_batch_factor(ras_pml_batch* h) {
     return s;
   }
   cudaError_t e = rp::launch_factor(h->prec, h->tune.factor_threads, h->tune.factor_rank, h->subs_d, h->nsub, h->max_b, Aloc, h->L,
-                                    h->Lrev, h->dinv, h->pivstats, h->status, h->st, h->split, wscratch);
+                                    h->Lrev, h->dinv, h->pivstats, h->status, h->st, h->split, wscratch, false,
+                                    h->tune.wide_cluster);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   dfree(Aloc);
   if (wscratch) cudaFree(wscratch);
@@ -487,15 +489,17 @@ int ras_pml_batch_tune(ras_pml_batch* h, ras_pml_tune_t* report) {
   return s;
 }
 
-int ras_pml_batch_set_shapes(ras_pml_batch* h, int factor_threads, int factor_rank, int apply_cols) {
+int ras_pml_batch_set_shapes(ras_pml_batch* h, int factor_threads, int factor_rank, int apply_cols, int wide_cluster) {
   if (!h ||
       !rp::factor_shape_valid(h->prec, rp::narrow_band(h->prec, h->max_b, h->split), factor_threads, factor_rank,
                               h->split) ||
-      !rp::apply_cols_valid(h->prec, apply_cols))
+      !rp::apply_cols_valid(h->prec, apply_cols) ||
+      !(wide_cluster == 0 || wide_cluster == 1 || wide_cluster == 2 || wide_cluster == 4))
     return RASPML_EBADARG;
   h->tune.factor_threads = factor_threads;
   h->tune.factor_rank = factor_rank;
   h->tune.apply_cols = apply_cols;
+  h->tune.wide_cluster = wide_cluster;
   return RASPML_OK;
 }
 

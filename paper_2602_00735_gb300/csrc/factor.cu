@@ -888,14 +888,15 @@ cudaError_t launch_factor_mixed(int threads, int rank, const SubDesc* subs, int 
 
 cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, int nsub, int max_b,
                           const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status,
-                          cudaStream_t st, BandSplit split, void* wscratch, bool skip_wide) {
+                          cudaStream_t st, BandSplit split, void* wscratch, bool skip_wide, int wide_cluster) {
   if (max_b > max_band(prec)) {
     // the subdomains wider than the shared-memory window first (blocked
     // kernel, window in scratch), then the others with the chosen shape,
     // sized for the widest of them; each launch skips the other kind
+    const int cl = wide_cluster > 0 ? wide_cluster : wide_cluster_auto(split.nblocked);
     cudaError_t e = skip_wide ? cudaSuccess
                               : launch_factor_wide(prec, subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status,
-                                                   wscratch, st);
+                                                   wscratch, st, cl);
     if (e != cudaSuccess || split.max_b_narrow <= 0) return e;
     max_b = split.max_b_narrow;
   }

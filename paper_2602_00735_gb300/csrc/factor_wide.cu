@@ -2,28 +2,35 @@
 // (Section 2: the local solves A_j^-1 of B^-1), kMaxBandC64 / kMaxBandC128 <
 // b <= kMaxBandWide: A_j = L_j D_j L_j^T without pivoting, blocked.
 //
-// One CTA of kWideThreads threads per subdomain, right-looking, panels of NB
-// pivots. The active rows k..k+NB+b-1 of the lower band live in a window in
-// device scratch (one slot per wide subdomain, SubDesc::wslot, set aside by
-// the caller): row r in row slot r mod (NB+b), its entries A(r, r-b..r) at
+// A thread-block cluster of CL CTAs (1, 2 or 4) of kWideThreads threads per
+// subdomain, right-looking, panels of NB pivots. The active rows
+// k..k+NB+b-1 of the lower band live in a window in device scratch (one slot
+// per wide subdomain, SubDesc::wslot, set aside by the caller), shared by the
+// cluster: row r in row slot r mod (NB+b), its entries A(r, r-b..r) at
 // positions 0..b (position q holds column r-b+q), in the arithmetic type.
 // Panel at k:
-//   1. the panel's NB columns, rows k..k+NB+b-1, are copied to shared memory,
-//      column-major (Pn[j][i] = W(k+i, k+j));
-//   2. they are factored there pivot by pivot: the multipliers of the pivot
-//      column, then c_i l_j' subtracted from the later panel columns (two
+//   1. every CTA copies the panel's NB columns, rows k..k+NB+b-1, to its
+//      shared memory, column-major (Pn[j][i] = W(k+i, k+j)); cluster barrier;
+//   2. every CTA factors them pivot by pivot (the same arithmetic in each, so
+//      the copies agree bit for bit): the multipliers of the pivot column,
+//      then c_i l_j' subtracted from the later panel columns (two block
 //      barriers per pivot), and the pivot column scaled to L;
-//   3. L(k+i, k+j) goes to both output copies and 1/d to D^-1 (the layout of
-//      factor.cu), and the rows k+NB+b..k+2NB+b-1 of A_j enter the slots of
-//      the finished rows k..k+NB-1 (zero except their four stored couplings);
+//   3. CTA 0 writes L(k+i, k+j) to both output copies and 1/d to D^-1 (the
+//      layout of factor.cu); the rows k+NB+b..k+2NB+b-1 of A_j enter the
+//      slots of the finished rows k..k+NB-1 (zero except their four stored
+//      couplings), rows shared out over the cluster;
 //   4. the trailing window, rows and columns k+NB..k+NB+b-1, takes the rank-NB
-//      update W(r, c) -= sum_j L(r, k+j) d_j L(c, k+j) for c <= r: each warp
-//      takes tiles of 8 rows x 64 columns, each thread 4 x 4 entries kept in
-//      registers over the NB terms, the panel read from shared memory; the
-//      window is read and written once per panel.
+//      update W(r, c) -= sum_j (L(r, k+j) d_j) L(c, k+j) for c <= r: groups
+//      of 8 rows go round-robin to the warps of the cluster, a warp takes
+//      them in tiles of 8 rows x 64 columns, each thread 4 x 4 entries kept
+//      in registers over the NB terms, the panel read from shared memory; the
+//      window is read and written once per panel; cluster barrier.
 // Rows n..npad-1 are identity padding. Zero or non-finite pivots are reported
-// like the narrow kernels do (status->pivot_bad_sub); there is no device-side
-// wait besides the block barriers.
+// like the narrow kernels do (status->pivot_bad_sub). The only waits are the
+// block and cluster barriers, which every CTA of a cluster reaches the same
+// number of times (one subdomain, one loop).
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -31,7 +38,10 @@ namespace rp {
 
 namespace {
 
-constexpr int kWideThreads = 256;
+namespace cg = cooperative_groups;
+
+constexpr int kWideThreads = 512;
+constexpr int kWideWarps = kWideThreads / 32;
 constexpr int kWideOverhang = 64;   // zero rows after the panel: the tile overhang of step 4
 
 // the four stored couplings of row r (D, W, S, SW), identity for padding rows
@@ -60,14 +70,15 @@ __device__ __forceinline__ cx<R> band_entry(const cx<R> (&v)[4], int r, int q, i
   return x;
 }
 
-// rows r0 <= r < r1 (and < npad) of A_j into their window slots
+// rows r0 <= r < r1 (and < npad) of A_j into their window slots; the
+// entries are shared out over the `parts` CTAs of the cluster (this one: part)
 template <typename R>
 __device__ __forceinline__ void fill_rows(cx<R>* Wn, const c128* __restrict__ Aloc, const SubDesc& sd, int r0,
-                                          int r1, int RS, int LDW) {
+                                          int r1, int RS, int LDW, int part, int parts) {
   const int b = sd.b;
   r1 = min(r1, sd.npad);
   const long long cnt = (long long)max(0, r1 - r0) * LDW;
-  for (long long e = threadIdx.x; e < cnt; e += blockDim.x) {
+  for (long long e = (long long)part * blockDim.x + threadIdx.x; e < cnt; e += (long long)parts * blockDim.x) {
     const int r = r0 + (int)(e / LDW), q = (int)(e % LDW);
     cx<R> v[4];
     stored_row<R>(Aloc, sd, r, v);
@@ -81,8 +92,11 @@ __global__ void __launch_bounds__(kWideThreads)
                   S* __restrict__ Lrev_all, cx<R>* __restrict__ dinv_all, double* __restrict__ pivstats,
                   DevStatus* status, cx<R>* __restrict__ scratch, long long slot_elems, int bmin, int pld) {
   extern __shared__ __align__(16) unsigned char smw[];
-  const SubDesc sd = subs[blockIdx.x];
-  if (sd.b <= bmin || sd.wslot < 0) return;   // the shared-memory kernels take it
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks();
+  const int sub = blockIdx.x / CL, crank = (int)cluster.block_rank();   // the cluster's CTAs are consecutive
+  const SubDesc sd = subs[sub];
+  if (sd.b <= bmin || sd.wslot < 0) return;   // the whole cluster: the shared-memory kernels take it
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int b = sd.b, bp = sd.bp, npad = sd.npad;
   const int RS = NB + b, LDW = b + 1;
@@ -96,11 +110,12 @@ __global__ void __launch_bounds__(kWideThreads)
   cx<R>* dv = dinv_all + sd.v_off;
   const cx<R> zero = mk((R)0, (R)0);
 
-  fill_rows<R>(Wn, Aloc, sd, 0, RS, RS, LDW);
+  fill_rows<R>(Wn, Aloc, sd, 0, RS, RS, LDW, crank, CL);
   for (int e = tid; e < NB * pld; e += kWideThreads) Pn[e] = zero;
   R dmin2 = (R)3e38, dmax2 = (R)0;
   bool bad = false;
-  __syncthreads();
+  __threadfence();
+  cluster.sync();
 
   for (int k = 0; k < npad; k += NB) {
     const int nbk = min(NB, npad - k);           // pivots in this panel
@@ -117,7 +132,8 @@ __global__ void __launch_bounds__(kWideThreads)
       const int j = e / (NB + b - rows), i = rows + e % (NB + b - rows);
       Pn[j * pld + i] = zero;
     }
-    __syncthreads();
+    // every CTA has read the panel rows before any refills their slots (step 3)
+    cluster.sync();
     // 2. factor the panel
     for (int j = 0; j < nbk; ++j) {
       const cx<R> d = Pn[j * pld + j];
@@ -140,25 +156,28 @@ __global__ void __launch_bounds__(kWideThreads)
       }
       __syncthreads();
     }
-    // 3. outputs, and the rows entering the window
-    for (int e = tid; e < nbk; e += kWideThreads) dv[k + e] = dsh[e];
-    for (int e = tid; e < nbk * bp; e += kWideThreads) {
-      const int j = e / bp, t = e % bp;   // L column k+j, entry t: row k+j+1+t
-      const int i = j + 1 + t;
-      L[(long long)(k + j) * bp + t] = st_entry<S, R>((t < b && i < rows) ? Pn[j * pld + i] : zero);
+    // 3. outputs (CTA 0) and the rows entering the window
+    if (crank == 0) {
+      for (int e = tid; e < nbk; e += kWideThreads) dv[k + e] = dsh[e];
+      for (int e = tid; e < nbk * bp; e += kWideThreads) {
+        const int j = e / bp, t = e % bp;   // L column k+j, entry t: row k+j+1+t
+        const int i = j + 1 + t;
+        L[(long long)(k + j) * bp + t] = st_entry<S, R>((t < b && i < rows) ? Pn[j * pld + i] : zero);
+      }
+      for (int e = tid; e < (rows - 1) * NB; e += kWideThreads) {
+        const int i = 1 + e / NB, j = e % NB;   // reversed row k+i, entry i-j-1
+        if (j < i && j < nbk && i - j <= b)
+          Lr[(long long)(npad - 1 - (k + i)) * bp + (i - j - 1)] = st_entry<S, R>(Pn[j * pld + i]);
+      }
     }
-    for (int e = tid; e < (rows - 1) * NB; e += kWideThreads) {
-      const int i = 1 + e / NB, j = e % NB;   // reversed row k+i, entry i-j-1
-      if (j < i && j < nbk && i - j <= b)
-        Lr[(long long)(npad - 1 - (k + i)) * bp + (i - j - 1)] = st_entry<S, R>(Pn[j * pld + i]);
-    }
-    fill_rows<R>(Wn, Aloc, sd, k + RS, k + RS + NB, RS, LDW);
+    fill_rows<R>(Wn, Aloc, sd, k + RS, k + RS + NB, RS, LDW, crank, CL);
+    __syncthreads();
     // 4. trailing update of rows and columns k+NB..k+NB+b-1
     if (k + NB < npad) {
       const int nt = rows - NB;                 // trailing rows present
       const int ng = (nt + 7) / 8;              // row groups of 8
       const int ur = 4 * (lane >> 4), uc = 4 * (lane & 15);
-      for (int g = warp; g < ng; g += kWideThreads / 32) {
+      for (int g = crank * kWideWarps + warp; g < ng; g += CL * kWideWarps) {
         const int ii0 = 8 * g + ur;             // this thread's first trailing row
         const int nct = (8 * g + 7) / 64 + 1;   // column tiles reaching the diagonal
         for (int ct = 0; ct < nct; ++ct) {
@@ -204,12 +223,13 @@ __global__ void __launch_bounds__(kWideThreads)
         }
       }
     }
-    __syncthreads();
+    __threadfence();
+    cluster.sync();   // the window is complete for the next panel
   }
-  if (tid == 0) {
-    pivstats[2 * blockIdx.x] = sqrt((double)dmin2);
-    pivstats[2 * blockIdx.x + 1] = sqrt((double)dmax2);
-    if (bad) atomicCAS(&status->pivot_bad_sub, -1, (int)blockIdx.x);
+  if (crank == 0 && tid == 0) {
+    pivstats[2 * sub] = sqrt((double)dmin2);
+    pivstats[2 * sub + 1] = sqrt((double)dmax2);
+    if (bad) atomicCAS(&status->pivot_bad_sub, -1, sub);
   }
 }
 
@@ -225,26 +245,41 @@ int wide_nb(int max_b) {
 }
 
 template <typename R, typename S, int NB>
-cudaError_t launch_wide_t(const SubDesc* subs, int nsub, int bmin, int max_b, const c128* Aloc, void* L, void* Lrev,
-                          void* dinv, double* pivstats, DevStatus* status, void* scratch, cudaStream_t st) {
+cudaError_t launch_wide_t(const SubDesc* subs, int nsub, int bmin, int max_b, int cl, const c128* Aloc, void* L,
+                          void* Lrev, void* dinv, double* pivstats, DevStatus* status, void* scratch,
+                          cudaStream_t st) {
   const int pld = NB + max_b + kWideOverhang;
   const size_t smem = ((size_t)NB * pld + 3 * NB) * sizeof(cx<R>);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_factor_wide<R, S, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = k_factor_wide<R, S, NB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long slot = (long long)(NB + max_b) * (max_b + 1);
-  k_factor_wide<R, S, NB><<<nsub, kWideThreads, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (cx<R>*)dinv, pivstats,
-                                                            status, (cx<R>*)scratch, slot, bmin, pld);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nsub * cl);
+  cfg.blockDim = dim3(kWideThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, subs, Aloc, (S*)L, (S*)Lrev, (cx<R>*)dinv, pivstats, status, (cx<R>*)scratch,
+                         slot, bmin, pld);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 template <typename R, typename S>
-cudaError_t launch_wide_s(const SubDesc* subs, int nsub, int bmin, int max_b, const c128* Aloc, void* L, void* Lrev,
-                          void* dinv, double* pivstats, DevStatus* status, void* scratch, cudaStream_t st) {
+cudaError_t launch_wide_s(const SubDesc* subs, int nsub, int bmin, int max_b, int cl, const c128* Aloc, void* L,
+                          void* Lrev, void* dinv, double* pivstats, DevStatus* status, void* scratch,
+                          cudaStream_t st) {
   switch (wide_nb<R>(max_b)) {
-    case 32: return launch_wide_t<R, S, 32>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
-    case 16: return launch_wide_t<R, S, 16>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
-    case 8: return launch_wide_t<R, S, 8>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+    case 32: return launch_wide_t<R, S, 32>(subs, nsub, bmin, max_b, cl, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+    case 16: return launch_wide_t<R, S, 16>(subs, nsub, bmin, max_b, cl, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+    case 8: return launch_wide_t<R, S, 8>(subs, nsub, bmin, max_b, cl, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -258,15 +293,26 @@ size_t factor_wide_slot_bytes(int prec, int max_b) {
   return (size_t)(nb + max_b) * (max_b + 1) * es;
 }
 
+int wide_cluster_auto(int nblocked) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 1;
+  for (int cl : {4, 2})
+    if ((long long)nblocked * cl <= sms) return cl;
+  return 1;
+}
+
 cudaError_t launch_factor_wide(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
                                void* Lrev, void* dinv, double* pivstats, DevStatus* status, void* scratch,
-                               cudaStream_t st) {
+                               cudaStream_t st, int cl) {
   const int bmin = max_band(prec);
   if (max_b <= bmin) return cudaSuccess;
-  if (max_b > kMaxBandWide || scratch == nullptr) return cudaErrorInvalidValue;
-  if (prec == 0) return launch_wide_s<double, c128>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
-  if (prec == 1) return launch_wide_s<float, c64>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
-  return launch_wide_s<float, h2c>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+  if (max_b > kMaxBandWide || scratch == nullptr || !(cl == 1 || cl == 2 || cl == 4)) return cudaErrorInvalidValue;
+  if (prec == 0)
+    return launch_wide_s<double, c128>(subs, nsub, bmin, max_b, cl, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+  if (prec == 1)
+    return launch_wide_s<float, c64>(subs, nsub, bmin, max_b, cl, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+  return launch_wide_s<float, h2c>(subs, nsub, bmin, max_b, cl, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
 }
 
 }  // namespace rp

@@ -45,6 +45,7 @@ struct Tune {
   int factor_threads = 256;   // threads per factor CTA: 128, 256, 512 (1024 with rank 2)
   int factor_rank = 2;        // pivots per pass over the window: 1 or 2
   int apply_cols = 8;         // band columns per bulk copy: 8 (4 or 16 with complex64 storage)
+  int wide_cluster = 0;       // CTAs per subdomain of the wide-band factor: 1, 2, 4; 0: wide_cluster_auto
 };
 // factor_rank 8 or 16 (with 128 threads): the blocked form on the tensor
 // cores with that many pivots per panel, complex64 arithmetic (prec 1 and 2)
@@ -58,11 +59,13 @@ constexpr int kMaxBandTc = 127;
 // to the tensor-core kernel. nwide < 0: no such order (the one-problem
 // handle), and the mixed shape is not available.
 // max_b_narrow: the widest subdomain at or below max_band(prec) (0: none),
-// for the launch of the shared-memory kernels when wider subdomains exist.
+// for the launch of the shared-memory kernels when wider subdomains exist;
+// nblocked: the number of wider ones (the blocked kernel's subdomains).
 struct BandSplit {
   int nwide = -1;
   int max_b_tc = 0;
   int max_b_narrow = 0;
+  int nblocked = 0;
 };
 bool factor_tc_ok(int prec, int max_b);
 bool factor_shape_valid(int prec, int max_b, int threads, int rank, BandSplit split = BandSplit{});
@@ -111,22 +114,27 @@ cudaError_t launch_factor_lu(int prec, const SubDesc* subs, int nsub, int max_b,
                              void* dinv, double* pivstats, DevStatus* status, cudaStream_t st);
 
 // factor_wide.cu: the subdomains with max_band(prec) < b <= kMaxBandWide,
-// each CTA in its own scratch slot (SubDesc::wslot) of factor_wide_slot_bytes
-// (prec, max_b) bytes; the other subdomains of the launch return at once.
+// each factored by a cluster of cl CTAs (1, 2 or 4) in its own scratch slot
+// (SubDesc::wslot) of factor_wide_slot_bytes(prec, max_b) bytes; the other
+// subdomains of the launch return at once. wide_cluster_auto: the largest
+// cl in {4, 2} for which all nblocked clusters are resident at once (one CTA
+// per SM), else 1.
 size_t factor_wide_slot_bytes(int prec, int max_b);
+int wide_cluster_auto(int nblocked);
 cudaError_t launch_factor_wide(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
                                void* Lrev, void* dinv, double* pivstats, DevStatus* status, void* scratch,
-                               cudaStream_t st);
+                               cudaStream_t st, int cl);
 
 // factor.cu
 size_t factor_smem_bytes(int b, int prec, int rank);
 // Subdomains with b > max_band(prec) (up to kMaxBandWide) need wscratch of
 // (slots) x factor_wide_slot_bytes(prec, max_b) bytes, SubDesc::wslot < slots;
-// skip_wide leaves them out (the tuner times the other kernels' shapes).
+// skip_wide leaves them out (the tuner times the other kernels' shapes);
+// wide_cluster: CTAs per wide subdomain (0: wide_cluster_auto(split.nblocked)).
 cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, int nsub, int max_b,
                           const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status,
                           cudaStream_t st, BandSplit split = BandSplit{}, void* wscratch = nullptr,
-                          bool skip_wide = false);
+                          bool skip_wide = false, int wide_cluster = 0);
 
 // apply.cu
 size_t apply_smem_bytes(int max_bp, int prec, int cols);

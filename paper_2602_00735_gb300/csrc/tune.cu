@@ -1,6 +1,7 @@
 // Tile-shape tuner: times each candidate shape of the factor launch (threads
-// per CTA, pivots per pass; the blocked tensor-core form where it applies)
-// and of the local-solve launch (band columns per bulk copy) on the caller's
+// per CTA, pivots per pass; the blocked tensor-core form where it applies),
+// the wide-band factor's cluster size (CTAs per subdomain) where there are
+// wide subdomains, and the local-solve launch (band columns per bulk copy) on the caller's
 // own subdomains with CUDA events on its stream, and returns the fastest (the
 // default shape unless another beats it by 2%). The factor runs last with
 // the chosen shape, so the factors left behind are that shape's.
@@ -65,6 +66,23 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
     rep.factor_cand_rank[rep.n_factor] = franks[c];
     rep.factor_ms[rep.n_factor++] = median(ms);
   }
+  // the wide-band factor's cluster size: its launch alone, one run per
+  // candidate (each run takes tens to hundreds of milliseconds)
+  if (t.split.nblocked > 0 && t.wscratch != nullptr) {
+    for (int cl : {1, 2, 4}) {
+      if (e != cudaSuccess) break;
+      e = cudaEventRecord(e0, t.st);
+      if (e == cudaSuccess)
+        e = launch_factor_wide(t.prec, t.subs, t.nsub, t.max_b, t.Aloc, t.L, t.Lrev, t.dinv, t.pivstats, t.status,
+                               t.wscratch, t.st, cl);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, t.st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) {
+        rep.wide_cand[rep.n_wide] = cl;
+        rep.wide_ms[rep.n_wide++] = ev_ms(e0, e1);
+      }
+    }
+  }
   std::vector<int> acand{8};
   if (t.prec == 1) { acand.push_back(4); acand.push_back(16); }
   for (int cols : acand) {
@@ -109,10 +127,18 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
   }
   const int bf = pick(rep.factor_ms, rep.n_factor, fdef);
   const int ba = rep.n_apply > 0 ? pick(rep.apply_ms, rep.n_apply, 0) : 0;
+  int wcl = 0;   // the automatic choice unless another cluster size beats it by 2%
+  if (rep.n_wide > 0) {
+    const int cauto = wide_cluster_auto(t.split.nblocked);
+    int wdef = 0;
+    for (int i = 0; i < rep.n_wide; ++i)
+      if (rep.wide_cand[i] == cauto) wdef = i;
+    wcl = rep.wide_cand[pick(rep.wide_ms, rep.n_wide, wdef)];
+  }
   // leave the factors of the chosen shape
   cudaError_t e3 = launch_factor(t.prec, rep.factor_cand_threads[bf], rep.factor_cand_rank[bf], t.subs, t.nsub,
                                  t.max_b, t.Aloc, t.L, t.Lrev, t.dinv, t.pivstats, t.status, t.st, t.split,
-                                 t.wscratch);
+                                 t.wscratch, false, wcl);
   if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(t.st);
   if (e3 != cudaSuccess) {
     std::fprintf(stderr, "raspml: tune: %s\n", cudaGetErrorString(e3));
@@ -121,9 +147,11 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
   best->factor_threads = rep.factor_cand_threads[bf];
   best->factor_rank = rep.factor_cand_rank[bf];
   best->apply_cols = rep.n_apply > 0 ? rep.apply_cand[ba] : 8;
+  best->wide_cluster = wcl;
   rep.factor_threads = best->factor_threads;
   rep.factor_rank = best->factor_rank;
   rep.apply_cols = best->apply_cols;
+  rep.wide_cluster = wcl > 0 ? wcl : (t.split.nblocked > 0 ? wide_cluster_auto(t.split.nblocked) : 0);
   if (report) *report = rep;
   return RASPML_OK;
 }

@@ -33,7 +33,9 @@ def tune_dict(rep: _lib.TuneReport) -> dict:
     return {"factor_threads": rep.factor_threads, "factor_rank": rep.factor_rank, "apply_cols": rep.apply_cols,
             "factor_ms": {f"{rep.factor_cand_threads[i]}x{rep.factor_cand_rank[i]}": rep.factor_ms[i]
                           for i in range(rep.n_factor)},
-            "apply_ms": {rep.apply_cand[i]: rep.apply_ms[i] for i in range(rep.n_apply)}}
+            "apply_ms": {rep.apply_cand[i]: rep.apply_ms[i] for i in range(rep.n_apply)},
+            "wide_cluster": rep.wide_cluster,
+            "wide_ms": {rep.wide_cand[i]: rep.wide_ms[i] for i in range(rep.n_wide)}}
 
 
 def _dev_ptr(t: torch.Tensor, n: int) -> int:
@@ -113,9 +115,10 @@ class RasPml:
             self._h, net._h, c_void_p(_dev_ptr(r, self.n)), c_void_p(_dev_ptr(z, self.n))))
         return z
 
-    def set_shapes(self, factor_threads: int, factor_rank: int, apply_cols: int) -> None:
+    def set_shapes(self, factor_threads: int, factor_rank: int, apply_cols: int, wide_cluster: int = 0) -> None:
+        """Tile shapes (e.g. another handle's tuning); wide_cluster 0: automatic."""
         _lib.check("ras_pml_set_shapes", self.lib.ras_pml_set_shapes(self._h, int(factor_threads), int(factor_rank),
-                                                                     int(apply_cols)))
+                                                                     int(apply_cols), int(wide_cluster)))
 
     # -- operators -------------------------------------------------------------
     def apply(self, r: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:

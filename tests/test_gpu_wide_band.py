@@ -127,3 +127,25 @@ def test_band_above_900_is_refused(solver_cls):
         assert s.info()["max_band"] == 900
     with pytest.raises(RasPmlError):
         solver_cls(strip(901).params(), factor_prec=1)
+
+
+def test_cluster_sizes_factor_bit_for_bit_alike(solver_cls):
+    """The wide-band factor with 1, 2 and 4 CTAs per subdomain: every CTA of
+    a cluster repeats the panel factorisation and the trailing rows are
+    only shared out, so the factors, and the applies, agree bit for bit; the
+    tuner times the three sizes and keeps one of them."""
+    w = strip(300)
+    grid, A, R = oracle_problem(w)
+    r = random_vector(grid.n, 3)
+    outs = {}
+    for cl in (1, 2, 4):
+        with solver_cls(w.params(), factor_prec=1) as s:
+            s.set_shapes(256, 2, 8, cl)
+            s.factor()
+            outs[cl] = s.apply(to_dev(r)).cpu().numpy()
+    assert np.array_equal(outs[1], outs[2]) and np.array_equal(outs[1], outs[4])
+    assert rel(outs[1], R.apply(r)) <= 1e-4
+    with solver_cls(w.params(), factor_prec=1) as s:
+        rep = s.tune()
+    assert set(rep["wide_ms"]) == {1, 2, 4} and all(v > 0 for v in rep["wide_ms"].values())
+    assert rep["wide_cluster"] in (1, 2, 4)
