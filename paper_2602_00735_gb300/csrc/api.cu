@@ -30,6 +30,7 @@ struct ras_pml_handle {
   int nsub = 0, max_b = 0, max_bp = 0, max_npad = 0, max_n = 0;
   int nwslot = 0;                // subdomains of the wide-band factor (b > max_band)
   rp::BandSplit split{};         // the widest of the other subdomains (no band order here)
+  rp::ApplyStreams as{};         // band classes of the local solves, run concurrently
   long long n = 0, sum_npad = 0, sum_l = 0, sum_n = 0, sum_bn = 0;
   c128 *D = nullptr, *CW = nullptr, *CS = nullptr, *CSW = nullptr;
   c128 *CE = nullptr, *CN = nullptr, *CNE = nullptr;   // form 1: the couplings symmetry no longer gives
@@ -280,6 +281,7 @@ void ras_pml_destroy(ras_pml_handle* h) {
   dfree(h->lc); dfree(h->lac); dfree(h->lhv);
   if (h->kst_host) cudaFreeHost(h->kst_host);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  rp::destroy_apply_streams(&h->as);
   delete h;
 }
 
@@ -314,6 +316,10 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   h->sum_l = l_off;
   h->nwslot = rp::assign_wide_slots(h->subs_h, h->p.factor_prec, &h->split.max_b_narrow);
   h->split.nblocked = h->nwslot;
+  if (const int sa = rp::make_apply_streams(&h->as, h->subs_h, h->p.factor_prec); sa != RASPML_OK) {
+    ras_pml_destroy(h);
+    return sa;
+  }
 
   int s;
 #define SETUP_ALLOC(ptr, cnt) \
@@ -576,7 +582,7 @@ int ras_pml_apply(ras_pml_handle* h, const rp_c128* r, rp_c128* z) {
   if (!h->factored) return RASPML_ESTATE;
   cudaSetDevice(h->dev);
   RP_CUDA(rp::launch_apply(h->p.factor_prec, h->tune.apply_cols, h->geo, h->geo_d, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev, h->dinv,
-                           (const c128*)r, h->Y, (c128*)z, nullptr, h->status, h->st));
+                           (const c128*)r, h->Y, (c128*)z, nullptr, h->status, h->st, rp::RK_C128, 0, &h->as));
   return RASPML_OK;
 }
 
@@ -698,7 +704,7 @@ int helmholtz_solve(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, dou
         ++issued;
         if (h->timing) RP_CUDA(cudaEventRecord(evj[0], st));
         RP_CUDA(rp::launch_apply(h->p.factor_prec, h->tune.apply_cols, h->geo, h->geo_d, h->subs_d, h->nsub, h->max_b, h->max_bp, h->L, h->Lrev,
-                                 h->dinv, vj, h->Y, zj, h->kst, h->status, st, bkind, zdf));
+                                 h->dinv, vj, h->Y, zj, h->kst, h->status, st, bkind, zdf, &h->as));
         if (stage_on) {
           ++staged;
           // learned stage: c = correction of r1 = v_j - A z_j (r1 held in w), then
@@ -896,7 +902,8 @@ int ras_pml_richardson(ras_pml_handle* h, const rp_c128* b_dev, rp_c128* x_dev, 
       if ((s = dev_norm(h, h->tmp_r, &h->kst->hnorm, nullptr, h->kst))) return s;
       RP_CUDA(rp::launch_rich_check(h->kst, rtol, maxit, it, h->hist, st));
       RP_CUDA(rp::launch_apply(h->p.factor_prec, h->tune.apply_cols, h->geo, h->geo_d, h->subs_d, h->nsub, h->max_b,
-                               h->max_bp, h->L, h->Lrev, h->dinv, h->tmp_r, h->Y, h->V, h->kst, h->status, st));
+                               h->max_bp, h->L, h->Lrev, h->dinv, h->tmp_r, h->Y, h->V, h->kst, h->status, st,
+                               rp::RK_C128, 0, &h->as));
       RP_CUDA(rp::launch_axpy_state(x, h->V, n, st, h->kst));
     }
     RP_CUDA(cudaMemcpyAsync(h->kst_host + slot, h->kst, sizeof(KState), cudaMemcpyDeviceToHost, st));

@@ -28,6 +28,7 @@ struct ras_pml_batch {
   std::vector<SubDesc> subs_h;      // launch order (decreasing factor cost)
   std::vector<int> sub_index_h;     // natural index -> launch position
   rp::BandSplit split;              // wide subdomains first in the launch order
+  rp::ApplyStreams as{};            // band classes of the local solves, run concurrently
   std::vector<int> tile_prob_h, tile0_h, tile1_h;
   long long ntot = 0, sum_n = 0, sum_npad = 0, sum_l = 0, sum_bn = 0;
   int nsub = 0, max_b = 0, max_bp = 0, max_npad = 0, ntiles = 0;
@@ -145,6 +146,7 @@ rp::BStep step_args(ras_pml_batch* h, int m, double rtol, int maxit) {
   a.kst = h->kst;
   a.ctl = h->ctl;
   a.status = h->status;
+  a.as = &h->as;
   return a;
 }
 
@@ -198,6 +200,7 @@ void ras_pml_batch_destroy(ras_pml_batch* h) {
   for (cudaEvent_t e : h->ev)
     if (e) cudaEventDestroy(e);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  rp::destroy_apply_streams(&h->as);
   delete h;
 }
 
@@ -265,6 +268,10 @@ int ras_pml_batch_setup(const ras_pml_params* params, int nprob, void* stream, r
   h->sum_l = l_off;
   h->nwslot = rp::assign_wide_slots(h->subs_h, h->prec, &h->split.max_b_narrow);
   h->split.nblocked = h->nwslot;
+  if (const int sa = rp::make_apply_streams(&h->as, h->subs_h, h->prec); sa != RASPML_OK) {
+    ras_pml_batch_destroy(h);
+    return sa;
+  }
 
   int s;
 #define BS_ALLOC(ptr, cnt) \
@@ -509,7 +516,7 @@ int ras_pml_batch_apply(ras_pml_batch* h, const rp_c128* r, rp_c128* z) {
   cudaSetDevice(h->dev);
   RP_CUDA(rp::launch_local_solves(h->prec, h->tune.apply_cols, h->geos_d, h->subs_d, h->nsub, h->max_b, h->max_bp,
                                   h->L, h->Lrev, h->dinv, (const c128*)r, 0, nullptr, h->Y, nullptr, h->status,
-                                  h->st, rp::RK_C128));
+                                  h->st, rp::RK_C128, &h->as));
   RP_CUDA(rp::launch_bprolong(h->prec, h->ntiles, h->tile_prob_d, h->geos_d, h->subs_d, h->sub_index_d, h->Y,
                               (c128*)z, 0, nullptr, nullptr, 0, h->st));
   return RASPML_OK;

@@ -256,7 +256,7 @@ __device__ __forceinline__ void sweeps(const SubDesc& sd, const Pipe<ST, KC>& pp
 // without the small ones paying for the largest window. WIDE = false: the
 // subdomains with S <= SMAX (phase-dispatched window); WIDE = true: those
 // with SMAX < S <= kApplyWideSlots (rotating window). Each launch returns at
-// once for the subdomains of the other kind, before it issues any copy.
+// once for the subdomains outside its band class, before it issues any copy.
 // rbase + (*jptr) * r_ld is the input vector when jptr is set (a step of a
 // captured Arnoldi graph reads its column index from device memory).
 template <typename R, typename ST, int SMAX, int KC, bool WIDE>
@@ -264,11 +264,13 @@ __global__ void __launch_bounds__(32)
     k_apply(const Geo* __restrict__ geos, const SubDesc* __restrict__ subs, const ST* __restrict__ Lf,
             const ST* __restrict__ Lb, const cx<R>* __restrict__ dinv_all, const c128* __restrict__ rbase,
             long long r_ld, const int* __restrict__ jptr, int rdf, cx<R>* __restrict__ Y, int stage_elems,
-            const KState* __restrict__ kst, DevStatus* status) {
+            const KState* __restrict__ kst, DevStatus* status, int smin, int smax) {
   extern __shared__ __align__(128) unsigned char sm[];
   const SubDesc sd = subs[blockIdx.x];
   const int S = (sd.b + 32) / 32;
-  if (WIDE ? (S <= SMAX || S > kApplyWideSlots) : S > SMAX) return;
+  // this launch's band class (smin..smax register slots; the host keeps
+  // smax <= SMAX for the narrow kernel and smin > SMAX for the wide one)
+  if (S < smin || S > smax) return;
   if (kst != nullptr && kst[sd.prob].stop) return;
   const int nx = geos[sd.prob].nx, o = geos[sd.prob].ovlp;
   const long long goff = geos[sd.prob].goff;
@@ -365,46 +367,95 @@ __global__ void k_prolong(Geo g, const SubDesc* __restrict__ subs, const cx<R>* 
 }
 
 // SMAX: the narrow kernel's window, 6 slots for complex128, 8 for complex64
-// storage. The narrow launch takes the subdomains with b < 32 SMAX, the wide
-// one (4 columns per bulk copy for complex128, 8 otherwise, so that its ring
-// fits in shared memory up to b = kMaxBandWide) the others; both are launched
-// over all subdomains, each skipping the other kind, wide first.
+// storage. The subdomains are launched in band classes by register slots
+// S = (b + 32) / 32: 1..4 and 5..SMAX on the narrow kernel, SMAX+1..29 on the
+// wide one; each launch covers all subdomains, skips those of the other
+// classes, and sizes its ring for its own class, so that a few wide
+// subdomains do not shrink every warp's share of shared memory. The wide
+// class copies 16 columns per bulk copy (8 for complex128 storage), halved
+// where the ring would not fit, so that one warp keeps up to about 200 KB of
+// copies in flight. With side streams the classes run concurrently (the
+// widest first, on the side streams), else one after the other.
 template <typename R>
 constexpr int smax_for() { return sizeof(R) == 8 ? 6 : 8; }
 
 template <typename R, typename ST, int KC, bool WIDE>
-cudaError_t launch_apply_k(int max_bp, const Geo* geos, const SubDesc* subs, int nsub, const void* Lf, const void* Lb,
-                           const void* dinv, const c128* r, long long r_ld, const int* jptr, int rdf, void* Y,
-                           const KState* kst, DevStatus* status, cudaStream_t st) {
-  constexpr int SMAX = smax_for<R>();
-  const int stage_elems = KC * max_bp;
-  const size_t smem = 128 + (size_t)stages_for<ST>() * KC * max_bp * sizeof(ST);
+cudaError_t launch_apply_k(int bp_max, int smin, int smax, const Geo* geos, const SubDesc* subs, int nsub,
+                           const void* Lf, const void* Lb, const void* dinv, const c128* r, long long r_ld,
+                           const int* jptr, int rdf, void* Y, const KState* kst, DevStatus* status,
+                           cudaStream_t st) {
+  const int stage_elems = KC * bp_max;
+  const size_t smem = 128 + (size_t)stages_for<ST>() * KC * bp_max * sizeof(ST);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_apply<R, ST, SMAX, KC, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_apply<R, ST, smax_for<R>(), KC, WIDE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_apply<R, ST, SMAX, KC, WIDE><<<nsub, 32, smem, st>>>(geos, subs, (const ST*)Lf, (const ST*)Lb, (const cx<R>*)dinv,
-                                                         r, r_ld, jptr, rdf, (cx<R>*)Y, stage_elems, kst, status);
+  k_apply<R, ST, smax_for<R>(), KC, WIDE><<<nsub, 32, smem, st>>>(geos, subs, (const ST*)Lf, (const ST*)Lb,
+                                                                  (const cx<R>*)dinv, r, r_ld, jptr, rdf, (cx<R>*)Y,
+                                                                  stage_elems, kst, status, smin, smax);
   return cudaGetLastError();
+}
+
+// the wide class: the widest chunk (columns per copy) whose ring fits
+template <typename R, typename ST>
+cudaError_t launch_apply_wide(int bp_max, int smin, int smax, const Geo* geos, const SubDesc* subs, int nsub,
+                              const void* Lf, const void* Lb, const void* dinv, const c128* r, long long r_ld,
+                              const int* jptr, int rdf, void* Y, const KState* kst, DevStatus* status,
+                              cudaStream_t st) {
+  auto fits = [&](int kc) { return 128 + (size_t)stages_for<ST>() * kc * bp_max * sizeof(ST) <= 227 * 1024; };
+#define RP_WIDE_ARGS bp_max, smin, smax, geos, subs, nsub, Lf, Lb, dinv, r, r_ld, jptr, rdf, Y, kst, status, st
+  if constexpr (sizeof(ST) < 16) {
+    if (fits(16)) return launch_apply_k<R, ST, 16, true>(RP_WIDE_ARGS);
+  }
+  if (fits(8)) return launch_apply_k<R, ST, 8, true>(RP_WIDE_ARGS);
+  return launch_apply_k<R, ST, 4, true>(RP_WIDE_ARGS);
+#undef RP_WIDE_ARGS
 }
 
 template <typename R, typename ST, int KC>
 cudaError_t launch_apply_t(int max_b, const Geo* geos, const SubDesc* subs, int nsub, int max_bp, const void* Lf,
                            const void* Lb, const void* dinv, const c128* r, long long r_ld, const int* jptr, int rdf,
-                           void* Y, const KState* kst, DevStatus* status, cudaStream_t st) {
+                           void* Y, const KState* kst, DevStatus* status, cudaStream_t st,
+                           const ApplyStreams* as) {
   constexpr int SMAX = smax_for<R>();
   if (max_b > kMaxBandWide) return cudaErrorInvalidValue;
-  cudaError_t e = cudaSuccess;
-  int narrow_bp = max_bp;
-  if ((max_b + 32) / 32 > SMAX) {
-    constexpr int KW = sizeof(ST) == 16 ? 4 : 8;
-    e = launch_apply_k<R, ST, KW, true>(max_bp, geos, subs, nsub, Lf, Lb, dinv, r, r_ld, jptr, rdf, Y, kst, status,
-                                        st);
-    narrow_bp = std::min(max_bp, 32 * SMAX);
+  const int stop = (max_b + 32) / 32;   // the most slots any subdomain needs
+  // classes, widest first: {smin, smax}
+  int cls[3][2] = {{SMAX + 1, kApplyWideSlots}, {5, SMAX}, {1, 4}};
+  int use[3], nuse = 0;
+  for (int c = 0; c < 3; ++c) {
+    const int lo = cls[c][0], hi = std::min(cls[c][1], stop);
+    if (lo > hi) continue;
+    if (as != nullptr && as->slot_mask != 0) {
+      const uint32_t bits = ((1u << hi) - 1u) & ~((1u << (lo - 1)) - 1u);
+      if ((as->slot_mask & bits) == 0) continue;   // no subdomain in this class
+    }
+    cls[c][1] = hi;
+    use[nuse++] = c;
   }
-  if (e == cudaSuccess)
-    e = launch_apply_k<R, ST, KC, false>(narrow_bp, geos, subs, nsub, Lf, Lb, dinv, r, r_ld, jptr, rdf, Y, kst,
-                                         status, st);
+  auto launch = [&](int c, cudaStream_t s) {
+    const int bp = std::min(max_bp, 32 * cls[c][1]);
+    if (c == 0)
+      return launch_apply_wide<R, ST>(bp, cls[c][0], cls[c][1], geos, subs, nsub, Lf, Lb, dinv, r, r_ld, jptr, rdf, Y,
+                                      kst, status, s);
+    return launch_apply_k<R, ST, KC, false>(bp, cls[c][0], cls[c][1], geos, subs, nsub, Lf, Lb, dinv, r, r_ld, jptr,
+                                           rdf, Y, kst, status, s);
+  };
+  cudaError_t e = cudaSuccess;
+  const bool concurrent = as != nullptr && as->side[0] != nullptr && as->side[1] != nullptr && nuse > 1;
+  if (!concurrent) {
+    for (int i = 0; i < nuse && e == cudaSuccess; ++i) e = launch(use[i], st);
+    return e;
+  }
+  // fork: the wider classes on the side streams, the narrowest on st; join
+  e = cudaEventRecord(as->fork, st);
+  for (int i = 0; i + 1 < nuse && e == cudaSuccess; ++i) {
+    e = cudaStreamWaitEvent(as->side[i], as->fork, 0);
+    if (e == cudaSuccess) e = launch(use[i], as->side[i]);
+    if (e == cudaSuccess) e = cudaEventRecord(as->join[i], as->side[i]);
+  }
+  if (e == cudaSuccess) e = launch(use[nuse - 1], st);
+  for (int i = 0; i + 1 < nuse && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(st, as->join[i], 0);
   return e;
 }
 
@@ -413,6 +464,15 @@ cudaError_t launch_apply_t(int max_b, const Geo* geos, const SubDesc* subs, int 
 cudaError_t set_copy_wait_limit(long long cycles) {
   const long long v = cycles > 0 ? cycles : kWaitLimitCycles;
   return cudaMemcpyToSymbol(g_copy_wait_limit, &v, sizeof(v));
+}
+
+uint32_t apply_slot_mask(const SubDesc* subs_host, int nsub) {
+  uint32_t m = 0;
+  for (int j = 0; j < nsub; ++j) {
+    const int S = (subs_host[j].b + 32) / 32;
+    if (S >= 1 && S <= 32) m |= 1u << (S - 1);
+  }
+  return m;
 }
 
 bool apply_cols_valid(int prec, int cols) { return cols == 8 || (prec == 1 && (cols == 4 || cols == 16)); }
@@ -426,10 +486,10 @@ size_t apply_smem_bytes(int max_bp, int prec, int cols) {
 cudaError_t launch_local_solves(int prec, int cols, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
                                 int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r,
                                 long long r_ld, const int* jptr, void* Y, const KState* kst, DevStatus* status,
-                                cudaStream_t st, int rkind) {
+                                cudaStream_t st, int rkind, const ApplyStreams* as) {
   const int rdf = rkind;
   if (!apply_cols_valid(prec, cols)) return cudaErrorInvalidValue;
-#define RP_APPLY_ARGS max_b, geos, subs, nsub, max_bp, Lf, Lb, dinv, r, r_ld, jptr, rdf, Y, kst, status, st
+#define RP_APPLY_ARGS max_b, geos, subs, nsub, max_bp, Lf, Lb, dinv, r, r_ld, jptr, rdf, Y, kst, status, st, as
   if (prec == 0) return launch_apply_t<double, c128, 8>(RP_APPLY_ARGS);
   if (prec == 2) return launch_apply_t<float, h2c, 8>(RP_APPLY_ARGS);
   if (cols == 4) return launch_apply_t<float, c64, 4>(RP_APPLY_ARGS);
@@ -453,9 +513,10 @@ cudaError_t launch_prolong(int prec, const Geo& g, const SubDesc* subs, const vo
 
 cudaError_t launch_apply(int prec, int cols, const Geo& g, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
                          int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r, void* Y,
-                         c128* z, const KState* kst, DevStatus* status, cudaStream_t st, int rkind, int out_df) {
+                         c128* z, const KState* kst, DevStatus* status, cudaStream_t st, int rkind, int out_df,
+                         const ApplyStreams* as) {
   cudaError_t e = launch_local_solves(prec, cols, geos, subs, nsub, max_b, max_bp, Lf, Lb, dinv, r, 0, nullptr, Y,
-                                      kst, status, st, rkind);
+                                      kst, status, st, rkind, as);
   if (e != cudaSuccess) return e;
   return launch_prolong(prec, g, subs, Y, z, kst, st, out_df);
 }

@@ -683,7 +683,7 @@ cudaError_t launch_bstep(const BStep& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
   }
   e = launch_local_solves(a.prec, a.cols, a.geos, a.subs, a.nsub, a.max_b, a.max_bp, a.L, a.Lrev, a.dinv,
-                          (const c128*)a.V, a.ld, jp, a.Y, a.kst, a.status, st, RK_C64);
+                          (const c128*)a.V, a.ld, jp, a.Y, a.kst, a.status, st, RK_C64, a.as);
   if (e != cudaSuccess) return e;
   // z_j in double-float form with complex64 local values; w always in that form
   const int zdf = a.prec >= 1 ? 1 : 0;

@@ -93,6 +93,32 @@ inline int assign_wide_slots(std::vector<SubDesc>& subs, int prec, int* max_b_na
   return slots;
 }
 
+// The local solves' band classes (see ApplyStreams): the slot mask of the
+// subdomains and, when they fall in more than one class, two non-blocking
+// side streams and the fork/join events that run the classes concurrently.
+inline int make_apply_streams(ApplyStreams* as, const std::vector<SubDesc>& subs, int prec) {
+  *as = ApplyStreams{};
+  as->slot_mask = apply_slot_mask(subs.data(), (int)subs.size());
+  const int smax = prec == 0 ? 6 : 8;
+  const uint32_t lo4 = 0xFu, mid = ((1u << smax) - 1u) & ~lo4, hi = ~((1u << smax) - 1u);
+  const int classes = ((as->slot_mask & lo4) != 0) + ((as->slot_mask & mid) != 0) + ((as->slot_mask & hi) != 0);
+  if (classes < 2) return RASPML_OK;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&as->side[i], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&as->fork, cudaEventDisableTiming);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&as->join[i], cudaEventDisableTiming);
+  return e == cudaSuccess ? RASPML_OK : RASPML_ECUDA;
+}
+
+inline void destroy_apply_streams(ApplyStreams* as) {
+  for (int i = 0; i < 2; ++i) {
+    if (as->side[i]) cudaStreamDestroy(as->side[i]);
+    if (as->join[i]) cudaEventDestroy(as->join[i]);
+  }
+  if (as->fork) cudaEventDestroy(as->fork);
+  *as = ApplyStreams{};
+}
+
 // Device scratch for the windows of the wide-band factor (nullptr and OK
 // when there is no slot); the caller frees it after the factor has run.
 inline int alloc_wide_scratch(void** p, int slots, int prec, int max_b) {

@@ -144,10 +144,23 @@ cudaError_t set_copy_wait_limit(long long cycles);
 enum : int { RK_C128 = 0, RK_DF = 1, RK_C64 = 2 };
 // Local solves of all subdomains into Y. The input is r of kind rkind, or
 // r + (*jptr) * r_ld when jptr is set.
+// Band classes of the local solves (register slots S = (b + 32) / 32):
+// slot_mask bit S-1 is set when some subdomain needs S slots (0: unknown,
+// every class up to max_b is launched); with both side streams set, the
+// classes run concurrently, forked from and joined back to the caller's
+// stream by the events (timing disabled), which also works under stream
+// capture.
+struct ApplyStreams {
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[2] = {nullptr, nullptr};
+  uint32_t slot_mask = 0;
+};
+uint32_t apply_slot_mask(const SubDesc* subs_host, int nsub);
 cudaError_t launch_local_solves(int prec, int cols, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
                                 int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r,
                                 long long r_ld, const int* jptr, void* Y, const KState* kst, DevStatus* status,
-                                cudaStream_t st, int rkind);
+                                cudaStream_t st, int rkind, const ApplyStreams* as = nullptr);
 // z = sum_j R_j^T Y_j; with out_df (complex64 Y only) z is written in
 // double-float form (dfc)
 cudaError_t launch_prolong(int prec, const Geo& g, const SubDesc* subs, const void* Y, c128* z, const KState* kst,
@@ -156,7 +169,7 @@ cudaError_t launch_prolong(int prec, const Geo& g, const SubDesc* subs, const vo
 cudaError_t launch_apply(int prec, int cols, const Geo& g, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
                          int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r, void* Y,
                          c128* z, const KState* kst, DevStatus* status, cudaStream_t st, int rkind = RK_C128,
-                         int out_df = 0);
+                         int out_df = 0, const ApplyStreams* as = nullptr);
 
 // krylov.cu
 cudaError_t launch_spmv(long long n, int nx, const c128* D, const c128* CW, const c128* CS, const c128* CSW,
@@ -274,6 +287,7 @@ struct BStep {
   KState* kst;            // per problem
   BCtl* ctl;
   DevStatus* status;
+  const ApplyStreams* as;   // band classes of the local solves (may be null)
 };
 
 // with zdf (complex64 Y only) z is written in double-float form (dfc)
