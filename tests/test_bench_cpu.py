@@ -105,7 +105,7 @@ def test_apply_traffic_scales_with_the_workload(tmp_path):
     b = bench.traffic_from_profile(src, 4.0e9)
     assert a is not None and b is not None
     assert 1.0 <= a / 1.0e9 <= 1.2                  # a little above the algorithmic bytes
-    assert abs(b / a - 4.0) < 1e-3                   # in proportion to the work
+    assert abs(b / a / 4.0 - 1.0) < 1e-3             # in proportion (both rounded to 4 digits)
     other = tmp_path / "apply.cu"
     other.write_text(open(src).read() + "\n// changed\n")
     assert bench.traffic_from_profile(str(other), 1.0e9) is None
