@@ -22,9 +22,10 @@
 //   4. the trailing window, rows and columns k+NB..k+NB+b-1, takes the rank-NB
 //      update W(r, c) -= sum_j (L(r, k+j) d_j) L(c, k+j) for c <= r: groups
 //      of 8 rows go round-robin to the warps of the cluster, a warp takes
-//      them in tiles of 8 rows x 64 columns, each thread 4 x 4 entries kept
-//      in registers over the NB terms, the panel read from shared memory; the
-//      window is read and written once per panel; cluster barrier.
+//      them in tiles of 8 rows x 64 columns, each thread 4 rows x 4 columns
+//      (16 apart) kept in registers over the NB terms, the panel read from
+//      shared memory; the window is read and written once per panel;
+//      cluster barrier.
 // Rows n..npad-1 are identity padding. Zero or non-finite pivots are reported
 // like the narrow kernels do (status->pivot_bad_sub). The only waits are the
 // block and cluster barriers, which every CTA of a cluster reaches the same
@@ -176,13 +177,16 @@ __global__ void __launch_bounds__(kWideThreads)
     if (k + NB < npad) {
       const int nt = rows - NB;                 // trailing rows present
       const int ng = (nt + 7) / 8;              // row groups of 8
-      const int ur = 4 * (lane >> 4), uc = 4 * (lane & 15);
+      // rows ii0..ii0+3, columns jj0 + 16 v: a half-warp reads 16 consecutive
+      // panel entries per load (four consecutive columns per thread read
+      // them 32 bytes apart, a 4-way bank conflict)
+      const int ur = 4 * (lane >> 4), uc = lane & 15;
       for (int g = crank * kWideWarps + warp; g < ng; g += CL * kWideWarps) {
         const int ii0 = 8 * g + ur;             // this thread's first trailing row
         const int nct = (8 * g + 7) / 64 + 1;   // column tiles reaching the diagonal
         for (int ct = 0; ct < nct; ++ct) {
           const int jj0 = 64 * ct + uc;
-          if (jj0 > ii0 + 3) continue;          // the tile lies above the diagonal
+          if (jj0 > ii0 + 3) continue;          // this thread's part lies above the diagonal
           cx<R> acc[4][4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(kWideThreads)
             cx<R>* wr = Wn + (long long)(r % RS) * LDW + (b - ii);   // position of column k+NB
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-              const int jj = jj0 + v;
+              const int jj = jj0 + 16 * v;
               acc[u][v] = (ii < nt && jj <= ii) ? wr[jj] : zero;
             }
           }
@@ -202,8 +206,8 @@ __global__ void __launch_bounds__(kWideThreads)
             cx<R> a[4], q[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              a[u] = pj[ii0 + u] * d;   // L(r, k+j) d_j
-              q[u] = pj[jj0 + u];       // L(c, k+j)
+              a[u] = pj[ii0 + u] * d;         // L(r, k+j) d_j
+              q[u] = pj[jj0 + 16 * u];        // L(c, k+j)
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(kWideThreads)
             cx<R>* wr = Wn + (long long)(r % RS) * LDW + (b - ii);
 #pragma unroll
             for (int v = 0; v < 4; ++v)
-              if (jj0 + v <= ii) wr[jj0 + v] = acc[u][v];
+              if (jj0 + 16 * v <= ii) wr[jj0 + 16 * v] = acc[u][v];
           }
         }
       }
