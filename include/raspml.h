@@ -305,10 +305,11 @@ void ras_pml_destroy(ras_pml_handle* h);
  * threads, factor_rank 8 or 16: that many pivots per panel, the trailing
  * update as TF32 MMAs with a three-term split of each FP32 operand); apply
  * columns 8, plus 4 and 16 when factor_prec = 1; where subdomains are wider
- * than the shared-memory window, the wide-band factor's cluster size (1, 2
- * or 4 CTAs per subdomain; kept: the automatic choice, the largest size for
- * which all wide subdomains' clusters are resident at once, unless another
- * beats it by 2%).
+ * than the shared-memory window, the wide-band factor's shape: 1, 2 or 4
+ * CTAs per subdomain on the CUDA cores, or (factor_prec >= 1) 16, the
+ * trailing update on the tensor cores (kept: the automatic choice, the
+ * largest cluster for which all wide subdomains' clusters are resident at
+ * once, unless another shape beats it by 2%).
  * Synchronises the stream. With form 1 it factors once and times nothing
  * (one factor shape; the apply shape stays as set; n_factor = n_apply = 0).
  * ------------------------------------------------------------------------- */
@@ -324,9 +325,10 @@ typedef struct {
   int32_t apply_cand[4];
   float   apply_ms[4];       /* median time of each apply candidate (local
                                 solves of all subdomains)                     */
-  int32_t wide_cluster;      /* CTAs per subdomain of the wide-band factor in
-                                use (0: no wide subdomain)                    */
-  int32_t n_wide;            /* cluster sizes timed (entries below; 0 when no
+  int32_t wide_cluster;      /* wide-band factor shape in use: 1, 2, 4 CTAs
+                                per subdomain, 16 tensor cores (0: no wide
+                                subdomain)                                    */
+  int32_t n_wide;            /* wide shapes timed (entries below; 0 when no
                                 subdomain is wider than the shared-memory
                                 window)                                       */
   int32_t wide_cand[4];
@@ -341,7 +343,8 @@ int ras_pml_tune(ras_pml_handle* h, ras_pml_tune_t* report);
  * or 16 (the tensor-core form: factor_prec >= 1 and every half-bandwidth
  * <= 127);
  * apply_cols 8, or 4 or 16 with factor_prec = 1; wide_cluster 1, 2 or 4
- * CTAs per subdomain of the wide-band factor, or 0 for the automatic choice.
+ * CTAs per subdomain of the wide-band factor on the CUDA cores, 16 for its
+ * tensor-core form (factor_prec >= 1), or 0 for the automatic choice.
  * RASPML_EBADARG for other values. */
 int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, int apply_cols, int wide_cluster);
 

@@ -534,7 +534,8 @@ int ras_pml_set_shapes(ras_pml_handle* h, int factor_threads, int factor_rank, i
       !rp::factor_shape_valid(h->p.factor_prec, rp::narrow_band(h->p.factor_prec, h->max_b, h->split), factor_threads,
                               factor_rank) ||
       !rp::apply_cols_valid(h->p.factor_prec, apply_cols) ||
-      !(wide_cluster == 0 || wide_cluster == 1 || wide_cluster == 2 || wide_cluster == 4))
+      !(wide_cluster == 0 || wide_cluster == 1 || wide_cluster == 2 || wide_cluster == 4 ||
+        (wide_cluster == rp::kWideTensorCores && h->p.factor_prec >= 1)))
     return RASPML_EBADARG;
   h->tune.factor_threads = factor_threads;
   h->tune.factor_rank = factor_rank;

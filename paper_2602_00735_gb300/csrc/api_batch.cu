@@ -501,7 +501,8 @@ int ras_pml_batch_set_shapes(ras_pml_batch* h, int factor_threads, int factor_ra
       !rp::factor_shape_valid(h->prec, rp::narrow_band(h->prec, h->max_b, h->split), factor_threads, factor_rank,
                               h->split) ||
       !rp::apply_cols_valid(h->prec, apply_cols) ||
-      !(wide_cluster == 0 || wide_cluster == 1 || wide_cluster == 2 || wide_cluster == 4))
+      !(wide_cluster == 0 || wide_cluster == 1 || wide_cluster == 2 || wide_cluster == 4 ||
+        (wide_cluster == rp::kWideTensorCores && h->prec >= 1)))
     return RASPML_EBADARG;
   h->tune.factor_threads = factor_threads;
   h->tune.factor_rank = factor_rank;

@@ -34,6 +34,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tc.cuh"
 
 namespace rp {
 
@@ -237,6 +238,219 @@ __global__ void __launch_bounds__(kWideThreads)
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same factorisation with the trailing update on the tensor cores
+// (complex64 arithmetic; the tuner's wide shape 16). One CTA of
+// kWideTcThreads threads per subdomain, panels of kWideTcNB pivots; steps 1-3
+// as above (one CTA, block barriers). Step 4: the trailing window is cut into
+// 128 x 128 tiles (row block I, column block J <= I), and tile (I, J) takes
+// D = (L D)_I L_J^T from tcgen05.mma kind::tf32 (M = N = 128, K = 8, two K
+// steps): complex products as four real ones (the negate-A bit of the
+// instruction descriptor for -Li Li^T), each FP32 operand as a TF32 head
+// plus tail with the three products head head, head tail, tail head kept
+// (about 2^-21 relative rounding per product), the scheme of k_factor_tc.
+// The accumulators (Re and Im, 256 TMEM columns) are read back by eight warps
+// (32 rows and 64 columns each) and subtracted from the window's entries
+// with c <= r. A_I is staged in shared memory once per row block, B_J once per
+// tile, both in the no-swizzle K-major core-matrix layout. The one wait, for
+// the MMAs' completion, is bounded: on time-out the kernel records it, waits
+// once more (bounded), frees its TMEM and returns.
+constexpr int kWideTcThreads = 256;
+constexpr int kWideTcNB = 16;
+constexpr int kWideTcTile = 128;
+constexpr uint32_t kWideTcArr = kWideTcTile * kWideTcNB * 4;   // bytes of one operand array
+constexpr uint32_t kWideTcCols = 2 * kWideTcTile;              // TMEM columns: Re and Im
+
+template <typename S>
+__global__ void __launch_bounds__(kWideTcThreads)
+    k_factor_wide_tc(const SubDesc* __restrict__ subs, const c128* __restrict__ Aloc, S* __restrict__ Lall,
+                     S* __restrict__ Lrev_all, c64* __restrict__ dinv_all, double* __restrict__ pivstats,
+                     DevStatus* status, c64* __restrict__ scratch, long long slot_elems, int bmin, int pld) {
+  constexpr int NB = kWideTcNB, T = kWideTcTile;
+  constexpr uint32_t AB = kWideTcArr;
+  extern __shared__ __align__(1024) unsigned char smt[];
+  const int sub = blockIdx.x;
+  const SubDesc sd = subs[sub];
+  if (sd.b <= bmin || sd.wslot < 0) return;   // before any TMEM allocation
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = sd.b, bp = sd.bp, npad = sd.npad;
+  const int RS = NB + b, LDW = b + 1;
+  c64* Wn = scratch + (long long)sd.wslot * slot_elems;
+  unsigned char* Aop = smt;            // (L D)_I: Re head, Re tail, Im head, Im tail
+  unsigned char* Bop = smt + 4 * AB;   // L_J, the same four arrays
+  c64* Pn = reinterpret_cast<c64*>(smt + 8 * AB);   // Pn[j * pld + i]
+  c64* dsh = Pn + (long long)NB * pld;              // 1/d of the panel's pivots
+  c64* dpv = dsh + NB;                              // the pivots d
+  c64* lb = dpv + NB;                               // multipliers of the panel rows
+  uint64_t* bar = reinterpret_cast<uint64_t*>(lb + NB);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  S* L = Lall + sd.l_off;
+  S* Lr = Lrev_all + sd.l_off;
+  c64* dv = dinv_all + sd.v_off;
+  const c64 zero = mk(0.f, 0.f);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kWideTcCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  fill_rows<float>(Wn, Aloc, sd, 0, RS, RS, LDW, 0, 1);
+  for (int e = tid; e < NB * pld; e += kWideTcThreads) Pn[e] = zero;
+  float dmin2 = 3e38f, dmax2 = 0.f;
+  bool bad = false, failed = false;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t lbo = T * 16;   // both operands have T rows
+  const uint64_t adesc0 = smem_desc(smem_u32(Aop), lbo, 128), bdesc0 = smem_desc(smem_u32(Bop), lbo, 128);
+  const uint32_t id = idesc_tf32(T, T), idn = id | (1u << 13);   // bit 13: negate A
+  uint32_t phase = 0;
+
+  for (int k = 0; k < npad && !failed; k += NB) {
+    const int rows = min(NB + b, npad - k);   // panel rows present (npad is a multiple of 32)
+    // 1. panel columns into shared memory
+    for (int e = tid; e < rows * NB; e += kWideTcThreads) {
+      const int i = e / NB, j = e % NB;
+      const int q = j - i + b;
+      Pn[j * pld + i] = (q >= 0 && q <= b) ? Wn[(long long)((k + i) % RS) * LDW + q] : zero;
+    }
+    for (int e = tid; e < NB * (NB + b - rows); e += kWideTcThreads) {
+      const int j = e / (NB + b - rows), i = rows + e % (NB + b - rows);
+      Pn[j * pld + i] = zero;
+    }
+    __syncthreads();
+    // 2. factor the panel
+    for (int j = 0; j < NB; ++j) {
+      const c64 d = Pn[j * pld + j];
+      const float ad2 = abs2(d);
+      const c64 di = crecip(d);
+      if (tid == 0) {
+        dsh[j] = di;
+        dpv[j] = d;
+        if (!(ad2 > 0.f) || !isfinite(ad2) || !isfinite(di.re) || !isfinite(di.im)) bad = true;
+        dmin2 = fminf(dmin2, ad2);
+        dmax2 = fmaxf(dmax2, ad2);
+      }
+      for (int i = j + 1 + tid; i < NB; i += kWideTcThreads) lb[i] = Pn[j * pld + i] * di;
+      __syncthreads();
+      for (int i = j + 1 + tid; i < rows; i += kWideTcThreads) {
+        const c64 c = Pn[j * pld + i];
+        const int jmax = min(NB - 1, i);
+        for (int jj = j + 1; jj <= jmax; ++jj) Pn[jj * pld + i] = fms(Pn[jj * pld + i], c, lb[jj]);
+        Pn[j * pld + i] = c * di;
+      }
+      __syncthreads();
+    }
+    // 3. outputs and the rows entering the window
+    for (int e = tid; e < NB; e += kWideTcThreads) dv[k + e] = dsh[e];
+    for (int e = tid; e < NB * bp; e += kWideTcThreads) {
+      const int j = e / bp, t = e % bp;   // L column k+j, entry t: row k+j+1+t
+      const int i = j + 1 + t;
+      L[(long long)(k + j) * bp + t] = st_entry<S, float>((t < b && i < rows) ? Pn[j * pld + i] : zero);
+    }
+    for (int e = tid; e < (rows - 1) * NB; e += kWideTcThreads) {
+      const int i = 1 + e / NB, j = e % NB;   // reversed row k+i, entry i-j-1
+      if (j < i && i - j <= b)
+        Lr[(long long)(npad - 1 - (k + i)) * bp + (i - j - 1)] = st_entry<S, float>(Pn[j * pld + i]);
+    }
+    fill_rows<float>(Wn, Aloc, sd, k + RS, k + RS + NB, RS, LDW, 0, 1);
+    __syncthreads();
+    // 4. trailing update of rows and columns k+NB..k+NB+b-1, tile by tile
+    if (k + NB >= npad) continue;
+    const int nt = rows - NB;               // trailing rows present
+    const int nbl = (nt + T - 1) / T;       // row blocks
+    for (int I = 0; I < nbl && !failed; ++I) {
+      for (int J = 0; J <= I && !failed; ++J) {
+        // operands: A_I (rows T I.., L d) when a row block starts, B_J (L)
+        for (int e = tid; e < (J == 0 ? 2 : 1) * T; e += kWideTcThreads) {
+          const bool isa = J == 0 && e < T;
+          const int rr = isa ? e : e - (J == 0 ? T : 0);
+          const int t = T * (isa ? I : J) + rr;
+          c64 z[NB];
+#pragma unroll
+          for (int j = 0; j < NB; ++j) {
+            const c64 l = t < nt ? Pn[j * pld + NB + t] : zero;
+            z[j] = isa ? l * dpv[j] : l;
+          }
+          tc_put_split<NB>(isa ? Aop : Bop, AB, T, rr, z);
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+          // (A array, B array, negate): Re += Arh Brh + Arh Brl + Arl Brh - (Aih Bih + Aih Bil + Ail Bih)
+          //                             Im += Arh Bih + Arh Bil + Arl Bih + Aih Brh + Aih Brl + Ail Brh
+#pragma unroll
+          for (int u = 0; u < 6; ++u) {
+            const uint32_t ta = (0x322100u >> (4 * u)) & 0xFu;    // 0, 0, 1, 2, 2, 3
+            const uint32_t tre = (0x232010u >> (4 * u)) & 0xFu;   // 0, 1, 0, 2, 3, 2
+            const uint32_t tim = (0x010232u >> (4 * u)) & 0xFu;   // 2, 3, 2, 0, 1, 0
+#pragma unroll
+            for (int s = 0; s < NB / 8; ++s) {
+              const uint64_t ad = adesc0 + ((ta * AB + 2 * s * lbo) >> 4);
+              tc_mma_tf32(tmem, ad, bdesc0 + ((tre * AB + 2 * s * lbo) >> 4), u >= 3 ? idn : id, (u | s) ? 1u : 0u);
+              tc_mma_tf32(tmem + (uint32_t)T, ad, bdesc0 + ((tim * AB + 2 * s * lbo) >> 4), id, (u | s) ? 1u : 0u);
+            }
+          }
+          tc_commit(bar);
+        }
+        const bool ok = mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) {
+          // a bounded wait gave up: record it, wait once more (bounded) for the MMAs in flight, leave
+          if (tid == 0) atomicExch(&status->timeout, 1);
+          mbar_wait_bounded(bar, phase ^ 1u);
+          failed = true;
+          break;
+        }
+        tc_fence_after();
+        {
+          // warp w: tile rows 32 (w mod 4).., columns 64 (w div 4)..
+          const int rr = 32 * (warp & 3) + lane;
+          const int t = T * I + rr;
+          const int r = k + NB + t;
+          c64* wrow = Wn + (long long)(r % RS) * LDW + (b - t);   // position of column k+NB
+#pragma unroll 1
+          for (int h = 0; h < 4; ++h) {
+            const int c0 = 64 * (warp >> 2) + 16 * h;
+            float re[16], im[16];
+            const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
+            tc_ld16x2(ta, ta + (uint32_t)T, re, im);
+            if (t < nt) {
+#pragma unroll
+              for (int u = 0; u < 16; ++u) {
+                const int col = T * J + c0 + u;
+                if (col <= t) wrow[col] = mk(wrow[col].re - re[u], wrow[col].im - im[u]);
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncthreads();
+      }
+    }
+  }
+  if (tid == 0) {
+    pivstats[2 * sub] = sqrt((double)dmin2);
+    pivstats[2 * sub + 1] = sqrt((double)dmax2);
+    if (bad) atomicCAS(&status->pivot_bad_sub, -1, sub);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWideTcCols)
+                 : "memory");
+  }
+}
+
 // the panel width for bands up to max_b: the largest NB whose panel fits in
 // shared memory; 0 when none does
 template <typename R>
@@ -288,6 +502,21 @@ cudaError_t launch_wide_s(const SubDesc* subs, int nsub, int bmin, int max_b, in
   return cudaErrorInvalidValue;
 }
 
+template <typename S>
+cudaError_t launch_wide_tc(const SubDesc* subs, int nsub, int bmin, int max_b, const c128* Aloc, void* L, void* Lrev,
+                           void* dinv, double* pivstats, DevStatus* status, void* scratch, cudaStream_t st) {
+  constexpr int NB = kWideTcNB;
+  const int pld = NB + max_b + kWideOverhang;
+  const size_t smem = 8 * (size_t)kWideTcArr + ((size_t)NB * pld + 3 * NB) * sizeof(c64) + 16;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_factor_wide_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long slot = (long long)(NB + max_b) * (max_b + 1);
+  k_factor_wide_tc<S><<<nsub, kWideTcThreads, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (c64*)dinv, pivstats, status,
+                                                          (c64*)scratch, slot, bmin, pld);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t factor_wide_slot_bytes(int prec, int max_b) {
@@ -311,7 +540,15 @@ cudaError_t launch_factor_wide(int prec, const SubDesc* subs, int nsub, int max_
                                cudaStream_t st, int cl) {
   const int bmin = max_band(prec);
   if (max_b <= bmin) return cudaSuccess;
-  if (max_b > kMaxBandWide || scratch == nullptr || !(cl == 1 || cl == 2 || cl == 4)) return cudaErrorInvalidValue;
+  if (max_b > kMaxBandWide || scratch == nullptr) return cudaErrorInvalidValue;
+  if (cl == kWideTensorCores) {
+    // the tensor-core form: complex64 arithmetic; its panel (16 pivots) is
+    // never wider than the CUDA-core form's, so the scratch slot holds it
+    if (prec == 1) return launch_wide_tc<c64>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+    if (prec == 2) return launch_wide_tc<h2c>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+    return cudaErrorInvalidValue;
+  }
+  if (!(cl == 1 || cl == 2 || cl == 4)) return cudaErrorInvalidValue;
   if (prec == 0)
     return launch_wide_s<double, c128>(subs, nsub, bmin, max_b, cl, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
   if (prec == 1)

@@ -45,7 +45,7 @@ struct Tune {
   int factor_threads = 256;   // threads per factor CTA: 128, 256, 512 (1024 with rank 2)
   int factor_rank = 2;        // pivots per pass over the window: 1 or 2
   int apply_cols = 8;         // band columns per bulk copy: 8 (4 or 16 with complex64 storage)
-  int wide_cluster = 0;       // CTAs per subdomain of the wide-band factor: 1, 2, 4; 0: wide_cluster_auto
+  int wide_cluster = 0;       // wide-band factor: 1, 2, 4 CTAs per subdomain, 16 tensor cores; 0: wide_cluster_auto
 };
 // factor_rank 8 or 16 (with 128 threads): the blocked form on the tensor
 // cores with that many pivots per panel, complex64 arithmetic (prec 1 and 2)
@@ -114,11 +114,14 @@ cudaError_t launch_factor_lu(int prec, const SubDesc* subs, int nsub, int max_b,
                              void* dinv, double* pivstats, DevStatus* status, cudaStream_t st);
 
 // factor_wide.cu: the subdomains with max_band(prec) < b <= kMaxBandWide,
-// each factored by a cluster of cl CTAs (1, 2 or 4) in its own scratch slot
+// each factored by a cluster of cl CTAs (1, 2 or 4) on the CUDA cores, or,
+// with cl = kWideTensorCores (complex64 arithmetic, prec 1 and 2), by one CTA
+// with the trailing update on the tensor cores, in its own scratch slot
 // (SubDesc::wslot) of factor_wide_slot_bytes(prec, max_b) bytes; the other
 // subdomains of the launch return at once. wide_cluster_auto: the largest
 // cl in {4, 2} for which all nblocked clusters are resident at once (one CTA
 // per SM), else 1.
+constexpr int kWideTensorCores = 16;
 size_t factor_wide_slot_bytes(int prec, int max_b);
 int wide_cluster_auto(int nblocked);
 cudaError_t launch_factor_wide(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,

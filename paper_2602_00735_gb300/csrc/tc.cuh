@@ -73,5 +73,63 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// TF32 head of an FP32 value: the 13 low mantissa bits cleared (exact in
+// TF32); the tail x - head is the second term of the three-product split.
+__device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// Row `r` (K = NB values) of an operand array with `rows` rows in the
+// no-swizzle K-major core-matrix layout (LBO = rows * 16 bytes, SBO = 128):
+// element (r, k) at (k/4)*rows*16 + (r/8)*128 + (r%8)*16 + (k%4)*4.
+template <int NB>
+__device__ __forceinline__ void tc_put_row(unsigned char* arr, int rows, int r, const float (&v)[NB]) {
+#pragma unroll
+  for (int q = 0; q < NB / 4; ++q)
+    *reinterpret_cast<float4*>(arr + q * rows * 16 + (r >> 3) * 128 + (r & 7) * 16) =
+        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+// head and tail arrays of the real and imaginary parts of z[0..NB-1], at
+// base, base + stride, base + 2 stride, base + 3 stride
+template <int NB>
+__device__ __forceinline__ void tc_put_split(unsigned char* base, uint32_t stride, int rows, int r,
+                                             const c64 (&z)[NB]) {
+  float h[NB], l[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    h[j] = tf32_head(z[j].re);
+    l[j] = z[j].re - h[j];
+  }
+  tc_put_row<NB>(base, rows, r, h);
+  tc_put_row<NB>(base + stride, rows, r, l);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    h[j] = tf32_head(z[j].im);
+    l[j] = z[j].im - h[j];
+  }
+  tc_put_row<NB>(base + 2 * stride, rows, r, h);
+  tc_put_row<NB>(base + 3 * stride, rows, r, l);
+}
+
+// 32 lanes x 16 columns from each of two TMEM addresses, one wait
+__device__ __forceinline__ void tc_ld16x2(uint32_t ta, uint32_t tb, float (&va)[16], float (&vb)[16]) {
+  uint32_t a[16], c[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
+        "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15])
+      : "r"(ta));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7]),
+        "=r"(c[8]), "=r"(c[9]), "=r"(c[10]), "=r"(c[11]), "=r"(c[12]), "=r"(c[13]), "=r"(c[14]), "=r"(c[15])
+      : "r"(tb));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    va[i] = __uint_as_float(a[i]);
+    vb[i] = __uint_as_float(c[i]);
+  }
+}
+
 }  // namespace
 }  // namespace rp

@@ -66,11 +66,13 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
     rep.factor_cand_rank[rep.n_factor] = franks[c];
     rep.factor_ms[rep.n_factor++] = median(ms);
   }
-  // the wide-band factor's cluster size: its launch alone, one run per
-  // candidate (each run takes tens to hundreds of milliseconds)
+  // the wide-band factor's shape (cluster size on the CUDA cores, or the
+  // tensor-core form): its launch alone, one run per candidate (each run
+  // takes tens to hundreds of milliseconds)
   if (t.split.nblocked > 0 && t.wscratch != nullptr) {
-    for (int cl : {1, 2, 4}) {
+    for (int cl : {1, 2, 4, kWideTensorCores}) {
       if (e != cudaSuccess) break;
+      if (cl == kWideTensorCores && t.prec == 0) continue;   // complex64 arithmetic only
       e = cudaEventRecord(e0, t.st);
       if (e == cudaSuccess)
         e = launch_factor_wide(t.prec, t.subs, t.nsub, t.max_b, t.Aloc, t.L, t.Lrev, t.dinv, t.pivstats, t.status,

@@ -133,7 +133,7 @@ def test_cluster_sizes_factor_bit_for_bit_alike(solver_cls):
     """The wide-band factor with 1, 2 and 4 CTAs per subdomain: every CTA of
     a cluster repeats the panel factorisation and the trailing rows are
     only shared out, so the factors, and the applies, agree bit for bit; the
-    tuner times the three sizes and keeps one of them."""
+    tuner times the three sizes and the tensor-core form and keeps one."""
     w = strip(300)
     grid, A, R = oracle_problem(w)
     r = random_vector(grid.n, 3)
@@ -147,5 +147,41 @@ def test_cluster_sizes_factor_bit_for_bit_alike(solver_cls):
     assert rel(outs[1], R.apply(r)) <= 1e-4
     with solver_cls(w.params(), factor_prec=1) as s:
         rep = s.tune()
-    assert set(rep["wide_ms"]) == {1, 2, 4} and all(v > 0 for v in rep["wide_ms"].values())
-    assert rep["wide_cluster"] in (1, 2, 4)
+    assert set(rep["wide_ms"]) == {1, 2, 4, 16} and all(v > 0 for v in rep["wide_ms"].values())
+    assert rep["wide_cluster"] in (1, 2, 4, 16)
+
+
+@pytest.mark.parametrize("b", [300, 600, 850])
+def test_tensor_core_wide_factor_matches_oracle(solver_cls, b):
+    """The wide-band factor's tensor-core form (shape 16: the trailing update
+    as TF32 MMAs, each FP32 operand split into a TF32 head and tail with three
+    products kept, about 2^-21 relative rounding per product against FP32's
+    2^-24) against the oracle's B^-1; its bound is the CUDA-core form's,
+    widened for that rounding (measured values are printed)."""
+    w = strip(b, My=20)
+    grid, A, R = oracle_problem(w)
+    r = random_vector(grid.n, 8)
+    with solver_cls(w.params(), factor_prec=1) as s:
+        s.set_shapes(256, 2, 8, 16)
+        s.factor()
+        z = s.apply(to_dev(r)).cpu().numpy()
+        assert s.info()["min_pivot_ratio"] > 0
+    e = rel(z, R.apply(r))
+    print(f"b={b} tensor-core wide factor: apply error {e:.2e}")
+    assert e <= (3e-4 if b <= 300 else 2e-3)
+
+
+def test_tensor_core_wide_factor_solve_matches_direct_solve(solver_cls):
+    """The headline form with the tensor-core wide factor on a b = 600 strip,
+    converged to rtol 1e-11: the outer FGMRES corrects the factor's rounding,
+    and the solution is the direct solve's."""
+    w = strip(600)
+    p = w.params()
+    grid, A, _ = oracle_problem(w)
+    u = fem.direct_solve(A, fem.assemble_rhs(p, w.centres, w.amps, w.width))
+    with solver_cls(p, factor_prec=1, ortho=3) as s:
+        s.set_shapes(256, 2, 8, 16)
+        b = s.assemble_rhs(w.centres, w.amps, w.width)
+        x, it, relres, st = s.solve(b, rtol=1e-11, maxit=300)
+        assert st == 0 and relres <= 1e-11
+        assert rel(x.cpu().numpy(), u) <= 1e-9
