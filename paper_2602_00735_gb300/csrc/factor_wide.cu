@@ -249,13 +249,13 @@ __global__ void __launch_bounds__(kWideThreads)
 // instruction descriptor for -Li Li^T), each FP32 operand as a TF32 head
 // plus tail with the three products head head, head tail, tail head kept
 // (about 2^-21 relative rounding per product), the scheme of k_factor_tc.
-// The accumulators (Re and Im, 256 TMEM columns) are read back by eight warps
-// (32 rows and 64 columns each) and subtracted from the window's entries
-// with c <= r. A_I is staged in shared memory once per row block, B_J once per
+// The accumulators (Re and Im, 256 TMEM columns) are read back by sixteen
+// warps (32 rows and 32 columns each) and subtracted from the window's
+// entries with c <= r. A_I is staged in shared memory once per row block, B_J once per
 // tile, both in the no-swizzle K-major core-matrix layout. The one wait, for
 // the MMAs' completion, is bounded: on time-out the kernel records it, waits
 // once more (bounded), frees its TMEM and returns.
-constexpr int kWideTcThreads = 256;
+constexpr int kWideTcThreads = 512;
 constexpr int kWideTcNB = 16;
 constexpr int kWideTcTile = 128;
 constexpr uint32_t kWideTcArr = kWideTcTile * kWideTcNB * 4;   // bytes of one operand array
@@ -315,6 +315,7 @@ __global__ void __launch_bounds__(kWideTcThreads)
   for (int k = 0; k < npad && !failed; k += NB) {
     const int rows = min(NB + b, npad - k);   // panel rows present (npad is a multiple of 32)
     // 1. panel columns into shared memory
+#pragma unroll 4
     for (int e = tid; e < rows * NB; e += kWideTcThreads) {
       const int i = e / NB, j = e % NB;
       const int q = j - i + b;
@@ -401,6 +402,20 @@ __global__ void __launch_bounds__(kWideTcThreads)
           }
           tc_commit(bar);
         }
+        // this thread's window entries (tile row 32 (w mod 4) + lane, columns
+        // 32 (w div 4) + 16 h + u), loaded a chunk ahead: the first chunk while
+        // the MMAs run, the next one while the current is read back
+        const int rr = 32 * (warp & 3) + lane;
+        const int t = T * I + rr;
+        const int r = k + NB + t;
+        c64* wrow = Wn + (long long)(r % RS) * LDW + (b - t);   // position of column k+NB
+        auto load_chunk = [&](int h, c64 (&v)[16]) {
+          const int c0 = T * J + 32 * (warp >> 2) + 16 * h;
+#pragma unroll
+          for (int u = 0; u < 16; ++u) v[u] = (t < nt && c0 + u <= t) ? wrow[c0 + u] : zero;
+        };
+        c64 cur[16];
+        load_chunk(0, cur);
         const bool ok = mbar_wait_bounded(bar, phase);
         phase ^= 1u;
         if (!__syncthreads_and(ok)) {
@@ -411,25 +426,24 @@ __global__ void __launch_bounds__(kWideTcThreads)
           break;
         }
         tc_fence_after();
-        {
-          // warp w: tile rows 32 (w mod 4).., columns 64 (w div 4)..
-          const int rr = 32 * (warp & 3) + lane;
-          const int t = T * I + rr;
-          const int r = k + NB + t;
-          c64* wrow = Wn + (long long)(r % RS) * LDW + (b - t);   // position of column k+NB
 #pragma unroll 1
-          for (int h = 0; h < 4; ++h) {
-            const int c0 = 64 * (warp >> 2) + 16 * h;
-            float re[16], im[16];
-            const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
-            tc_ld16x2(ta, ta + (uint32_t)T, re, im);
-            if (t < nt) {
+        for (int h = 0; h < 2; ++h) {
+          c64 nxt[16];
+          if (h < 1) load_chunk(h + 1, nxt);
+          const int c0 = 32 * (warp >> 2) + 16 * h;
+          float re[16], im[16];
+          const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
+          tc_ld16x2(ta, ta + (uint32_t)T, re, im);
+          if (t < nt) {
 #pragma unroll
-              for (int u = 0; u < 16; ++u) {
-                const int col = T * J + c0 + u;
-                if (col <= t) wrow[col] = mk(wrow[col].re - re[u], wrow[col].im - im[u]);
-              }
+            for (int u = 0; u < 16; ++u) {
+              const int col = T * J + c0 + u;
+              if (col <= t) wrow[col] = mk(cur[u].re - re[u], cur[u].im - im[u]);
             }
+          }
+          if (h < 1) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) cur[u] = nxt[u];
           }
         }
         tc_fence_before();
