@@ -46,29 +46,21 @@ constexpr int kWideThreads = 512;
 constexpr int kWideWarps = kWideThreads / 32;
 constexpr int kWideOverhang = 64;   // zero rows after the panel: the tile overhang of step 4
 
-// the four stored couplings of row r (D, W, S, SW), identity for padding rows
+// window entry at position q of row r (column r - b + q): the stored
+// couplings D, W, S, SW of row r sit at distances 0, 1, b-1 and b below the
+// diagonal, every other entry of the band is zero, and padding rows are
+// identity; only the coupling an entry needs is read
 template <typename R>
-__device__ __forceinline__ void stored_row(const c128* __restrict__ A, const SubDesc& sd, int r, cx<R> (&v)[4]) {
-  if (r >= sd.n) {
-    v[0] = mk((R)1, (R)0);
-    v[1] = v[2] = v[3] = mk((R)0, (R)0);
-    return;
-  }
-  const c128* a = A + 4 * (sd.v_off + r);
-#pragma unroll
-  for (int e = 0; e < 4; ++e) v[e] = cvt<R>(a[e]);
-}
-
-// window entry at position q of row r (column r - b + q) from its couplings
-template <typename R>
-__device__ __forceinline__ cx<R> band_entry(const cx<R> (&v)[4], int r, int q, int b) {
-  if (r - b + q < 0) return mk((R)0, (R)0);
+__device__ __forceinline__ cx<R> band_entry(const c128* __restrict__ A, const SubDesc& sd, int r, int q, int b) {
   const int t = b - q;   // distance below the diagonal
   cx<R> x = mk((R)0, (R)0);
-  if (t == 0) x = v[0];
-  if (t == 1) x = x + v[1];
-  if (t == b - 1) x = x + v[2];
-  if (t == b) x = x + v[3];
+  if (q > b || r - t < 0 || (t != 0 && t != 1 && t != b - 1 && t != b)) return x;
+  if (r >= sd.n) return t == 0 ? mk((R)1, (R)0) : x;
+  const c128* a = A + 4 * (sd.v_off + r);
+  if (t == 0) x = cvt<R>(a[0]);
+  if (t == 1) x = x + cvt<R>(a[1]);
+  if (t == b - 1) x = x + cvt<R>(a[2]);
+  if (t == b) x = x + cvt<R>(a[3]);
   return x;
 }
 
@@ -82,9 +74,7 @@ __device__ __forceinline__ void fill_rows(cx<R>* Wn, const c128* __restrict__ Al
   const long long cnt = (long long)max(0, r1 - r0) * LDW;
   for (long long e = (long long)part * blockDim.x + threadIdx.x; e < cnt; e += (long long)parts * blockDim.x) {
     const int r = r0 + (int)(e / LDW), q = (int)(e % LDW);
-    cx<R> v[4];
-    stored_row<R>(Aloc, sd, r, v);
-    Wn[(long long)(r % RS) * LDW + q] = q <= b ? band_entry<R>(v, r, q, b) : mk((R)0, (R)0);
+    Wn[(long long)(r % RS) * LDW + q] = band_entry<R>(Aloc, sd, r, q, b);
   }
 }
 
@@ -250,8 +240,9 @@ __global__ void __launch_bounds__(kWideThreads)
 // plus tail with the three products head head, head tail, tail head kept
 // (about 2^-21 relative rounding per product), the scheme of k_factor_tc.
 // The accumulators (Re and Im, 256 TMEM columns) are read back by sixteen
-// warps (32 rows and 32 columns each) and subtracted from the window's
-// entries with c <= r. A_I is staged in shared memory once per row block, B_J once per
+// warps (32 rows and 32 columns each), transposed through shared memory in
+// 8-column slices, and subtracted from the window's entries with c <= r along
+// rows. A_I is staged in shared memory once per row block, B_J once per
 // tile, both in the no-swizzle K-major core-matrix layout. The one wait, for
 // the MMAs' completion, is bounded: on time-out the kernel records it, waits
 // once more (bounded), frees its TMEM and returns.
@@ -402,20 +393,6 @@ __global__ void __launch_bounds__(kWideTcThreads)
           }
           tc_commit(bar);
         }
-        // this thread's window entries (tile row 32 (w mod 4) + lane, columns
-        // 32 (w div 4) + 16 h + u), loaded a chunk ahead: the first chunk while
-        // the MMAs run, the next one while the current is read back
-        const int rr = 32 * (warp & 3) + lane;
-        const int t = T * I + rr;
-        const int r = k + NB + t;
-        c64* wrow = Wn + (long long)(r % RS) * LDW + (b - t);   // position of column k+NB
-        auto load_chunk = [&](int h, c64 (&v)[16]) {
-          const int c0 = T * J + 32 * (warp >> 2) + 16 * h;
-#pragma unroll
-          for (int u = 0; u < 16; ++u) v[u] = (t < nt && c0 + u <= t) ? wrow[c0 + u] : zero;
-        };
-        c64 cur[16];
-        load_chunk(0, cur);
         const bool ok = mbar_wait_bounded(bar, phase);
         phase ^= 1u;
         if (!__syncthreads_and(ok)) {
@@ -426,24 +403,45 @@ __global__ void __launch_bounds__(kWideTcThreads)
           break;
         }
         tc_fence_after();
+        // read back: warp w holds tile rows 32 (w mod 4).. (one per lane, as
+        // TMEM gives them) and columns 32 (w div 4)..; each 8-column slice goes
+        // through the warp's 2 KB of the B operand area (free once the MMAs
+        // have completed) so that the window's read-modify-write runs along
+        // rows, eight lanes per row, instead of one lane per row
+        {
+          c64* sc = reinterpret_cast<c64*>(Bop) + warp * 256;   // 32 rows x 8 columns; column XOR (row/2) mod 8
+          // keeps both the row-wise writes and the column-wise reads free of bank conflicts
+          const int row0 = T * I + 32 * (warp & 3);             // first trailing row of the warp
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-          c64 nxt[16];
-          if (h < 1) load_chunk(h + 1, nxt);
-          const int c0 = 32 * (warp >> 2) + 16 * h;
-          float re[16], im[16];
-          const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
-          tc_ld16x2(ta, ta + (uint32_t)T, re, im);
-          if (t < nt) {
+          for (int h = 0; h < 2; ++h) {
+            const int c0 = 32 * (warp >> 2) + 16 * h;
+            float re[16], im[16];
+            const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
+            tc_ld16x2(ta, ta + (uint32_t)T, re, im);
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-              const int col = T * J + c0 + u;
-              if (col <= t) wrow[col] = mk(cur[u].re - re[u], cur[u].im - im[u]);
+            for (int half = 0; half < 2; ++half) {
+              __syncwarp();
+#pragma unroll
+              for (int u = 0; u < 8; ++u) sc[lane * 8 + (u ^ ((lane >> 1) & 7))] = mk(re[8 * half + u], im[8 * half + u]);
+              __syncwarp();
+              const int u = lane & 7, col = T * J + c0 + 8 * half + u;
+              c64 cur[8];
+#pragma unroll
+              for (int it = 0; it < 8; ++it) {
+                const int rho = 4 * it + (lane >> 3), t = row0 + rho;
+                cur[it] = (t < nt && col <= t)
+                              ? Wn[(long long)((k + NB + t) % RS) * LDW + (b - t) + col]
+                              : zero;
+              }
+#pragma unroll
+              for (int it = 0; it < 8; ++it) {
+                const int rho = 4 * it + (lane >> 3), t = row0 + rho;
+                if (t < nt && col <= t) {
+                  const c64 d = sc[rho * 8 + (u ^ ((rho >> 1) & 7))];
+                  Wn[(long long)((k + NB + t) % RS) * LDW + (b - t) + col] = mk(cur[it].re - d.re, cur[it].im - d.im);
+                }
+              }
             }
-          }
-          if (h < 1) {
-#pragma unroll
-            for (int u = 0; u < 16; ++u) cur[u] = nxt[u];
           }
         }
         tc_fence_before();
