@@ -393,6 +393,31 @@ __global__ void __launch_bounds__(kWideTcThreads)
           }
           tc_commit(bar);
         }
+        // read back: warp w holds tile rows 32 (w mod 4).. (one per lane, as
+        // TMEM gives them) and columns 32 (w div 4)..; each 8-column slice
+        // (chunk q = 0..3) goes through the warp's 2 KB of the B operand area
+        // (free once the MMAs have completed) so that the window's
+        // read-modify-write runs along rows, eight lanes per row. The lane's
+        // window entries (rows row0 + 4 it + lane/8, column col0 + 8 q) are
+        // loaded two chunks ahead, the first two while the MMAs run.
+        const int row0 = T * I + 32 * (warp & 3);
+        const int col0 = T * J + 32 * (warp >> 2) + (lane & 7);
+        int off[8];   // window offset of column 0 in each of the lane's rows
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int t = row0 + 4 * it + (lane >> 3);
+          off[it] = ((k + NB + t) % RS) * LDW + (b - t);
+        }
+        auto load_chunk = [&](int q, c64 (&v)[8]) {
+#pragma unroll
+          for (int it = 0; it < 8; ++it) {
+            const int t = row0 + 4 * it + (lane >> 3), col = col0 + 8 * q;
+            v[it] = (t < nt && col <= t) ? Wn[off[it] + col] : zero;
+          }
+        };
+        c64 w0[8], w1[8], w2[8];
+        load_chunk(0, w0);
+        load_chunk(1, w1);
         const bool ok = mbar_wait_bounded(bar, phase);
         phase ^= 1u;
         if (!__syncthreads_and(ok)) {
@@ -403,46 +428,36 @@ __global__ void __launch_bounds__(kWideTcThreads)
           break;
         }
         tc_fence_after();
-        // read back: warp w holds tile rows 32 (w mod 4).. (one per lane, as
-        // TMEM gives them) and columns 32 (w div 4)..; each 8-column slice goes
-        // through the warp's 2 KB of the B operand area (free once the MMAs
-        // have completed) so that the window's read-modify-write runs along
-        // rows, eight lanes per row, instead of one lane per row
         {
-          c64* sc = reinterpret_cast<c64*>(Bop) + warp * 256;   // 32 rows x 8 columns; column XOR (row/2) mod 8
-          // keeps both the row-wise writes and the column-wise reads free of bank conflicts
-          const int row0 = T * I + 32 * (warp & 3);             // first trailing row of the warp
-#pragma unroll 1
-          for (int h = 0; h < 2; ++h) {
-            const int c0 = 32 * (warp >> 2) + 16 * h;
-            float re[16], im[16];
-            const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
-            tc_ld16x2(ta, ta + (uint32_t)T, re, im);
+          // 32 rows x 8 columns; column XOR (row/2) mod 8 keeps both the
+          // row-wise writes and the column-wise reads free of bank conflicts
+          c64* sc = reinterpret_cast<c64*>(Bop) + warp * 256;
+          float re[16], im[16];
+          auto slice = [&](int q, const c64 (&v)[8]) {
+            const int half = q & 1;
+            __syncwarp();
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-              __syncwarp();
+            for (int u = 0; u < 8; ++u) sc[lane * 8 + (u ^ ((lane >> 1) & 7))] = mk(re[8 * half + u], im[8 * half + u]);
+            __syncwarp();
+            const int u = lane & 7, col = col0 + 8 * q;
 #pragma unroll
-              for (int u = 0; u < 8; ++u) sc[lane * 8 + (u ^ ((lane >> 1) & 7))] = mk(re[8 * half + u], im[8 * half + u]);
-              __syncwarp();
-              const int u = lane & 7, col = T * J + c0 + 8 * half + u;
-              c64 cur[8];
-#pragma unroll
-              for (int it = 0; it < 8; ++it) {
-                const int rho = 4 * it + (lane >> 3), t = row0 + rho;
-                cur[it] = (t < nt && col <= t)
-                              ? Wn[(long long)((k + NB + t) % RS) * LDW + (b - t) + col]
-                              : zero;
-              }
-#pragma unroll
-              for (int it = 0; it < 8; ++it) {
-                const int rho = 4 * it + (lane >> 3), t = row0 + rho;
-                if (t < nt && col <= t) {
-                  const c64 d = sc[rho * 8 + (u ^ ((rho >> 1) & 7))];
-                  Wn[(long long)((k + NB + t) % RS) * LDW + (b - t) + col] = mk(cur[it].re - d.re, cur[it].im - d.im);
-                }
+            for (int it = 0; it < 8; ++it) {
+              const int rho = 4 * it + (lane >> 3), t = row0 + rho;
+              if (t < nt && col <= t) {
+                const c64 d = sc[rho * 8 + (u ^ ((rho >> 1) & 7))];
+                Wn[off[it] + col] = mk(v[it].re - d.re, v[it].im - d.im);
               }
             }
-          }
+          };
+          const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
+          tc_ld16x2(ta, ta + (uint32_t)T, re, im);
+          load_chunk(2, w2);
+          slice(0, w0);
+          load_chunk(3, w0);
+          slice(1, w1);
+          tc_ld16x2(ta + 16u, ta + (uint32_t)T + 16u, re, im);
+          slice(2, w2);
+          slice(3, w0);
         }
         tc_fence_before();
         __syncthreads();
