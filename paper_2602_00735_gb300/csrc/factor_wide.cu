@@ -272,8 +272,7 @@ __global__ void __launch_bounds__(kWideTcThreads)
   c64* Pn = reinterpret_cast<c64*>(smt + 8 * AB);   // Pn[j * pld + i]
   c64* dsh = Pn + (long long)NB * pld;              // 1/d of the panel's pivots
   c64* dpv = dsh + NB;                              // the pivots d
-  c64* lb = dpv + NB;                               // multipliers of the panel rows
-  uint64_t* bar = reinterpret_cast<uint64_t*>(lb + NB);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(dpv + NB);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
   S* L = Lall + sd.l_off;
   S* Lr = Lrev_all + sd.l_off;
@@ -317,28 +316,54 @@ __global__ void __launch_bounds__(kWideTcThreads)
       Pn[j * pld + i] = zero;
     }
     __syncthreads();
-    // 2. factor the panel
-    for (int j = 0; j < NB; ++j) {
-      const c64 d = Pn[j * pld + j];
-      const float ad2 = abs2(d);
-      const c64 di = crecip(d);
-      if (tid == 0) {
-        dsh[j] = di;
-        dpv[j] = d;
-        if (!(ad2 > 0.f) || !isfinite(ad2) || !isfinite(di.re) || !isfinite(di.im)) bad = true;
+    // 2. factor the panel: its NB x NB diagonal block on warp 0 (row a in
+    //    lane a, multipliers passed by shuffles; L(k+a, k+j) into Pn[j][a]),
+    //    then every trailing row forward-substituted against it in registers
+    if (warp == 0) {
+      const int a = lane & (NB - 1);
+      c64 x[NB];
+#pragma unroll
+      for (int jj = 0; jj < NB; ++jj) x[jj] = jj <= a ? Pn[jj * pld + a] : zero;
+      c64 myd = zero, mydi = zero;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const c64 d = shfl(x[j], j);
+        const c64 di = crecip(d);
+        const c64 l = x[j] * di;
+        if (a == j) {
+          myd = d;
+          mydi = di;
+        }
+        // entries jj > a of a row are never read back: updated without a predicate
+#pragma unroll
+        for (int jj = j + 1; jj < NB; ++jj) x[jj] = fms(x[jj], x[j], shfl(l, jj));
+        if (lane < NB && a > j) Pn[j * pld + a] = l;
+      }
+      if (lane < NB) {
+        const float ad2 = abs2(myd);
+        dsh[a] = mydi;
+        dpv[a] = myd;
+        if (!(ad2 > 0.f) || !isfinite(ad2) || !isfinite(mydi.re) || !isfinite(mydi.im)) bad = true;
         dmin2 = fminf(dmin2, ad2);
         dmax2 = fmaxf(dmax2, ad2);
       }
-      for (int i = j + 1 + tid; i < NB; i += kWideTcThreads) lb[i] = Pn[j * pld + i] * di;
-      __syncthreads();
-      for (int i = j + 1 + tid; i < rows; i += kWideTcThreads) {
-        const c64 c = Pn[j * pld + i];
-        const int jmax = min(NB - 1, i);
-        for (int jj = j + 1; jj <= jmax; ++jj) Pn[jj * pld + i] = fms(Pn[jj * pld + i], c, lb[jj]);
-        Pn[j * pld + i] = c * di;
-      }
-      __syncthreads();
     }
+    __syncthreads();
+    for (int i = NB + tid; i < rows; i += kWideTcThreads) {
+      c64 y[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) y[j] = Pn[j * pld + i];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const c64 c = y[j];
+#pragma unroll
+        for (int jj = j + 1; jj < NB; ++jj) y[jj] = fms(y[jj], c, Pn[j * pld + jj]);
+        y[j] = c * dsh[j];
+      }
+#pragma unroll
+      for (int j = 0; j < NB; ++j) Pn[j * pld + i] = y[j];
+    }
+    __syncthreads();
     // 3. outputs and the rows entering the window
     for (int e = tid; e < NB; e += kWideTcThreads) dv[k + e] = dsh[e];
     for (int e = tid; e < NB * bp; e += kWideTcThreads) {
@@ -359,18 +384,21 @@ __global__ void __launch_bounds__(kWideTcThreads)
     const int nbl = (nt + T - 1) / T;       // row blocks
     for (int I = 0; I < nbl && !failed; ++I) {
       for (int J = 0; J <= I && !failed; ++J) {
-        // operands: A_I (rows T I.., L d) when a row block starts, B_J (L)
-        for (int e = tid; e < (J == 0 ? 2 : 1) * T; e += kWideTcThreads) {
-          const bool isa = J == 0 && e < T;
-          const int rr = isa ? e : e - (J == 0 ? T : 0);
+        // operands: A_I (rows T I.., L d) when a row block starts, B_J (L);
+        // four threads per row, each with four of the NB columns (one 16-byte
+        // core-matrix row of each split array), a warp on 32 consecutive rows
+        for (int e = tid; e < (J == 0 ? 2 : 1) * 4 * T; e += kWideTcThreads) {
+          const bool isa = J == 0 && e < 4 * T;
+          const int ee = isa ? e : e - (J == 0 ? 4 * T : 0);
+          const int qq = (ee >> 5) & 3, rr = (ee & 31) + 32 * (ee >> 7);
           const int t = T * (isa ? I : J) + rr;
-          c64 z[NB];
+          c64 z[4];
 #pragma unroll
-          for (int j = 0; j < NB; ++j) {
-            const c64 l = t < nt ? Pn[j * pld + NB + t] : zero;
-            z[j] = isa ? l * dpv[j] : l;
+          for (int j = 0; j < 4; ++j) {
+            const c64 l = t < nt ? Pn[(4 * qq + j) * pld + NB + t] : zero;
+            z[j] = isa ? l * dpv[4 * qq + j] : l;
           }
-          tc_put_split<NB>(isa ? Aop : Bop, AB, T, rr, z);
+          tc_put_split_quad(isa ? Aop : Bop, AB, T, rr, qq, z);
         }
         fence_proxy_async_smem();
         tc_fence_before();
@@ -464,10 +492,20 @@ __global__ void __launch_bounds__(kWideTcThreads)
       }
     }
   }
-  if (tid == 0) {
-    pivstats[2 * sub] = sqrt((double)dmin2);
-    pivstats[2 * sub + 1] = sqrt((double)dmax2);
-    if (bad) atomicCAS(&status->pivot_bad_sub, -1, sub);
+  if (warp == 0) {
+    // pivot statistics of the lanes that held pivots
+    float mn = dmin2, mx = dmax2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const bool anybad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+      pivstats[2 * sub] = sqrt((double)mn);
+      pivstats[2 * sub + 1] = sqrt((double)mx);
+      if (anybad) atomicCAS(&status->pivot_bad_sub, -1, sub);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -534,7 +572,7 @@ cudaError_t launch_wide_tc(const SubDesc* subs, int nsub, int bmin, int max_b, c
                            void* dinv, double* pivstats, DevStatus* status, void* scratch, cudaStream_t st) {
   constexpr int NB = kWideTcNB;
   const int pld = NB + max_b + kWideOverhang;
-  const size_t smem = 8 * (size_t)kWideTcArr + ((size_t)NB * pld + 3 * NB) * sizeof(c64) + 16;
+  const size_t smem = 8 * (size_t)kWideTcArr + ((size_t)NB * pld + 2 * NB) * sizeof(c64) + 16;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_factor_wide_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

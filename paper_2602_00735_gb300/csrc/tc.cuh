@@ -110,6 +110,28 @@ __device__ __forceinline__ void tc_put_split(unsigned char* base, uint32_t strid
   tc_put_row<NB>(base + 3 * stride, rows, r, l);
 }
 
+// columns 4 qq .. 4 qq + 3 of row r (z[0..3]) in the four split arrays of
+// tc_put_split: one 16-byte core-matrix row in each
+__device__ __forceinline__ void tc_put_split_quad(unsigned char* base, uint32_t stride, int rows, int r, int qq,
+                                                  const c64 (&z)[4]) {
+  unsigned char* p = base + qq * rows * 16 + (r >> 3) * 128 + (r & 7) * 16;
+  float h[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    h[j] = tf32_head(z[j].re);
+    l[j] = z[j].re - h[j];
+  }
+  *reinterpret_cast<float4*>(p) = make_float4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<float4*>(p + stride) = make_float4(l[0], l[1], l[2], l[3]);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    h[j] = tf32_head(z[j].im);
+    l[j] = z[j].im - h[j];
+  }
+  *reinterpret_cast<float4*>(p + 2 * stride) = make_float4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<float4*>(p + 3 * stride) = make_float4(l[0], l[1], l[2], l[3]);
+}
+
 // 32 lanes x 16 columns from each of two TMEM addresses, one wait
 __device__ __forceinline__ void tc_ld16x2(uint32_t ta, uint32_t tb, float (&va)[16], float (&vb)[16]) {
   uint32_t a[16], c[16];
