@@ -20,6 +20,11 @@
 //   bulk-copy (TMA) engine; both sweeps use one continuous chunk sequence.
 //   Subdomains may belong to different problems of a batch: each reads its
 //   problem's geometry (geos[prob]) and skips when that problem has stopped.
+// k_apply_mw: the same sweeps for the wide band classes (more register slots
+//   than one warp's phase-dispatched window holds) on several warps per
+//   subdomain, each holding the row group being finished and a share of the
+//   slots below it, with the same arithmetic in the same order (results bit
+//   for bit independent of the number of warps).
 // k_prolong: one thread per global unknown sums the (at most four) weighted
 //   local values that cover it, in a fixed order (bit-reproducible): in FP64
 //   into complex128 (or split into the double-float form), or, for complex64
@@ -138,57 +143,9 @@ __device__ __forceinline__ bool group_dispatch(int ph, const Pipe<ST, KC>& pp, i
   return false;
 }
 
-// The 32 steps of one row group for a wide window (S > 8 slots): slot 0
-// always holds the group being finished, and after the group the window is
-// rotated by one slot (S - 1 register moves per 32 steps), so there is one
-// copy of the step code per S instead of one per phase.
-template <typename R, typename ST, int S, int KC>
-__device__ __forceinline__ bool group_steps_rot(const Pipe<ST, KC>& pp, int s0, int b, int lane, cx<R> (&win)[S],
-                                                const cx<R>& nxt, cx<R>& outv) {
-  const int bp = pp.bp;
-#pragma unroll 1
-  for (int c4 = 0; c4 < 32 / KC; ++c4) {
-    const int s = s0 + c4;
-    bool ok;
-    const ST* Lc = pp.wait(s, ok);
-    if (!__all_sync(0xffffffffu, ok)) return false;
-#pragma unroll 2
-    for (int ii = 0; ii < KC; ++ii) {
-      const int i = c4 * KC + ii;
-      const ST* col = Lc + ii * bp;
-      const cx<R> y = shfl(win[0], i);
-      if (lane == i) {
-        outv = y;
-        win[0] = nxt;
-      }
-      const int base = lane - i - 1;
-      {
-        const int t = (lane > i) ? base : base + 32 * S;
-        if (t < b) win[0] = fms(win[0], ld_entry(col[t]), y);
-      }
-#pragma unroll
-      for (int sl = 1; sl < S; ++sl) {
-        const int t = base + 32 * sl;
-        if (t < b) win[sl] = fms(win[sl], ld_entry(col[t]), y);
-      }
-    }
-    __syncwarp();
-    if (lane == 0 && s + stages_for<ST>() < 2 * pp.Q) {
-      fence_proxy_async_smem();
-      pp.issue(s + stages_for<ST>());
-    }
-  }
-  const cx<R> f = win[0];   // refilled with the rows 32 S ahead: the last slot now
-#pragma unroll
-  for (int sl = 0; sl + 1 < S; ++sl) win[sl] = win[sl + 1];
-  win[S - 1] = f;
-  return true;
-}
-
 // The two sweeps of one subdomain with an S-slot register window (S >= the
-// subdomain's ceil((b+1)/32)); the bulk-copy ring is already started. ROT:
-// the rotating window of the wide kernel.
-template <typename R, typename ST, int S, int KC, bool ROT>
+// subdomain's ceil((b+1)/32)); the bulk-copy ring is already started.
+template <typename R, typename ST, int S, int KC>
 __device__ __forceinline__ void sweeps(const SubDesc& sd, const Pipe<ST, KC>& pp, int nx, long long goff, int o,
                                        const c128* __restrict__ rglob, int rdf, const cx<R>* __restrict__ dv,
                                        cx<R>* __restrict__ Yj, DevStatus* status) {
@@ -214,8 +171,7 @@ __device__ __forceinline__ void sweeps(const SubDesc& sd, const Pipe<ST, KC>& pp
     const cx<R> nxt2 = gather_row<R>(sd, nx, goff, rglob, rdf, 32 * (gi + S + 1) + lane);
     const cx<R> d = dv[32 * gi + lane];
     cx<R> outv;
-    const bool ok = ROT ? group_steps_rot<R, ST, S, KC>(pp, (32 / KC) * gi, b, lane, win, nxt, outv)
-                        : group_dispatch<R, ST, S, KC>(gi % S, pp, (32 / KC) * gi, b, lane, win, nxt, outv);
+    const bool ok = group_dispatch<R, ST, S, KC>(gi % S, pp, (32 / KC) * gi, b, lane, win, nxt, outv);
     if (!ok) {
       fail((32 / KC) * gi);
       return;
@@ -234,8 +190,7 @@ __device__ __forceinline__ void sweeps(const SubDesc& sd, const Pipe<ST, KC>& pp
   for (int gi = 0; gi < G; ++gi) {
     const cx<R> nxt2 = zrow(32 * (gi + S + 1) + lane);
     cx<R> outv;
-    const bool ok = ROT ? group_steps_rot<R, ST, S, KC>(pp, pp.Q + (32 / KC) * gi, b, lane, win, nxt, outv)
-                        : group_dispatch<R, ST, S, KC>(gi % S, pp, pp.Q + (32 / KC) * gi, b, lane, win, nxt, outv);
+    const bool ok = group_dispatch<R, ST, S, KC>(gi % S, pp, pp.Q + (32 / KC) * gi, b, lane, win, nxt, outv);
     if (!ok) {
       fail(pp.Q + (32 / KC) * gi);
       return;
@@ -253,13 +208,12 @@ __device__ __forceinline__ void sweeps(const SubDesc& sd, const Pipe<ST, KC>& pp
 
 // One warp per subdomain; the register window is sized per subdomain
 // (S = ceil((b+1)/32)), so subdomains of different bands share one launch
-// without the small ones paying for the largest window. WIDE = false: the
-// subdomains with S <= SMAX (phase-dispatched window); WIDE = true: those
-// with SMAX < S <= kApplyWideSlots (rotating window). Each launch returns at
-// once for the subdomains outside its band class, before it issues any copy.
-// rbase + (*jptr) * r_ld is the input vector when jptr is set (a step of a
-// captured Arnoldi graph reads its column index from device memory).
-template <typename R, typename ST, int SMAX, int KC, bool WIDE>
+// without the small ones paying for the largest window: the subdomains with
+// smin <= S <= smax (<= SMAX, the phase-dispatched window). Each launch
+// returns at once for the subdomains outside its band class, before it issues
+// any copy. rbase + (*jptr) * r_ld is the input vector when jptr is set (a
+// step of a captured Arnoldi graph reads its column index from device memory).
+template <typename R, typename ST, int SMAX, int KC>
 __global__ void __launch_bounds__(32)
     k_apply(const Geo* __restrict__ geos, const SubDesc* __restrict__ subs, const ST* __restrict__ Lf,
             const ST* __restrict__ Lb, const cx<R>* __restrict__ dinv_all, const c128* __restrict__ rbase,
@@ -268,8 +222,7 @@ __global__ void __launch_bounds__(32)
   extern __shared__ __align__(128) unsigned char sm[];
   const SubDesc sd = subs[blockIdx.x];
   const int S = (sd.b + 32) / 32;
-  // this launch's band class (smin..smax register slots; the host keeps
-  // smax <= SMAX for the narrow kernel and smin > SMAX for the wide one)
+  // this launch's band class (smin..smax register slots, smax <= SMAX)
   if (S < smin || S > smax) return;
   if (kst != nullptr && kst[sd.prob].stop) return;
   const int nx = geos[sd.prob].nx, o = geos[sd.prob].ovlp;
@@ -299,20 +252,208 @@ __global__ void __launch_bounds__(32)
   __syncwarp();
   const cx<R>* dv = dinv_all + sd.v_off;
   cx<R>* Yj = Y + sd.v_off;
-#define RP_SWEEPS(S_) sweeps<R, ST, S_, KC, WIDE>(sd, pp, nx, goff, o, rglob, rdf, dv, Yj, status)
 #define RP_CASE(S_) \
   case S_:          \
-    if constexpr ((WIDE && S_ > SMAX) || (!WIDE && S_ <= SMAX)) RP_SWEEPS(S_); \
+    if constexpr (S_ <= SMAX) sweeps<R, ST, S_, KC>(sd, pp, nx, goff, o, rglob, rdf, dv, Yj, status); \
+    break;
+  switch (S) { RP_CASE(1) RP_CASE(2) RP_CASE(3) RP_CASE(4) RP_CASE(5) RP_CASE(6) RP_CASE(7) RP_CASE(8) }
+  static_assert(SMAX <= 8, "the case list covers S = 1..SMAX");
+#undef RP_CASE
+}
+
+// The wide class on W warps per subdomain (a CTA of 32 W threads). Every
+// warp keeps the row group being finished (slot 0) and performs its 32 steps
+// itself, so the multiplier y_k of each step comes from a shuffle inside the
+// warp, bit for bit the same in every warp; the other S - 1 slots are shared
+// out, warp w holding slots 1 + w SPW .. (SPW = ceil((S - 1) / W)). After
+// each group the window moves up one slot: warp 0's first slot becomes every
+// warp's slot 0, warp w's first slot becomes warp w-1's last, and the rows
+// entering at the bottom (collected in slot 0, whose lanes take them as they
+// finish their rows) go to the warp holding slot S - 1; one block barrier and
+// 32 W entries through shared memory per group. The copy ring is shared: one
+// block barrier per stage combines the warps' wait results and frees the
+// previous stage, whose refill thread 0 then issues. Two warps measured
+// fastest on a batch of 64 problems with 208 wide subdomains (b up to 408;
+// four warps: more barriers per slot).
+template <typename R, typename ST, int S, int KC, int W>
+__device__ __forceinline__ bool group_steps_mw(const Pipe<ST, KC>& pp, int s0, int b, int lane, int w,
+                                               cx<R>& win0, cx<R> (&own)[(S - 1 + W - 1) / W], const cx<R>& nxt,
+                                               cx<R>& outv, cx<R>* xch, int& sfail) {
+  constexpr int SPW = (S - 1 + W - 1) / W;
+  constexpr int NST = stages_for<ST>();
+  const int bp = pp.bp, g0 = 1 + w * SPW;
+#pragma unroll 1
+  for (int c4 = 0; c4 < 32 / KC; ++c4) {
+    const int s = s0 + c4;
+    bool ok;
+    const ST* Lc = pp.wait(s, ok);
+    if (!__syncthreads_and(ok)) {
+      sfail = s;
+      return false;
+    }
+    // every warp is past stage s - 1: its buffer takes stage s - 1 + NST
+    if (threadIdx.x == 0 && s > 0 && s - 1 + NST < 2 * pp.Q) {
+      fence_proxy_async_smem();
+      pp.issue(s - 1 + NST);
+    }
+#pragma unroll 2
+    for (int ii = 0; ii < KC; ++ii) {
+      const int i = c4 * KC + ii;
+      const ST* col = Lc + ii * bp;
+      const cx<R> y = shfl(win0, i);
+      if (lane == i) {
+        outv = y;
+        win0 = nxt;
+      }
+      const int base = lane - i - 1;
+      {
+        const int t = (lane > i) ? base : base + 32 * S;
+        if (t < b) win0 = fms(win0, ld_entry(col[t]), y);
+      }
+#pragma unroll
+      for (int m = 0; m < SPW; ++m) {
+        const int t = base + 32 * (g0 + m);
+        if (g0 + m < S && t < b) own[m] = fms(own[m], ld_entry(col[t]), y);
+      }
+    }
+  }
+  // move the window up one slot
+  xch[w * 32 + lane] = own[0];
+  __syncthreads();
+  const cx<R> f = win0;   // the rows entering at the bottom: slot S - 1
+  win0 = xch[lane];
+#pragma unroll
+  for (int m = 0; m + 1 < SPW; ++m) own[m] = own[m + 1];
+  if (w + 1 < W) own[SPW - 1] = xch[(w + 1) * 32 + lane];
+  if (S - 1 >= g0 && S - 1 < g0 + SPW) {
+#pragma unroll
+    for (int m = 0; m < SPW; ++m)
+      if (g0 + m == S - 1) own[m] = f;
+  }
+  return true;
+}
+
+template <typename R, typename ST, int S, int KC, int W>
+__device__ __forceinline__ void sweeps_mw(const SubDesc& sd, const Pipe<ST, KC>& pp, int nx, long long goff, int o,
+                                          const c128* __restrict__ rglob, int rdf, const cx<R>* __restrict__ dv,
+                                          cx<R>* __restrict__ Yj, cx<R>* xch, DevStatus* status) {
+  constexpr int SPW = (S - 1 + W - 1) / W;
+  constexpr int NST = stages_for<ST>();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = sd.b, npad = sd.npad, G = npad / 32;
+  const int nseq = 2 * pp.Q, g0 = 1 + w * SPW;
+  const cx<R> zero = mk((R)0, (R)0);
+  auto fail = [&](int s) {
+    // a bounded wait gave up: record it, drain the copies in flight (stages
+    // s .. s + NST - 1 issued before the first stage's barrier, s .. s + NST - 2
+    // after it), leave
+    if (threadIdx.x == 0) {
+      atomicExch(&status->timeout, 1);
+      const int hi = s + (s == 0 ? NST : NST - 1);
+      for (int t = s; t < hi && t < nseq; ++t) mbar_wait_bounded(&pp.bar[t % NST], (t / NST) & 1);
+    }
+  };
+  int sfail = 0;
+
+  // ---------------- forward: L y = R_j r, z = D^-1 y ----------------
+  cx<R> win0 = gather_row<R>(sd, nx, goff, rglob, rdf, lane);
+  cx<R> own[SPW];
+#pragma unroll
+  for (int m = 0; m < SPW; ++m)
+    own[m] = g0 + m < S ? gather_row<R>(sd, nx, goff, rglob, rdf, 32 * (g0 + m) + lane) : zero;
+  cx<R> nxt = gather_row<R>(sd, nx, goff, rglob, rdf, 32 * S + lane);
+  for (int gi = 0; gi < G; ++gi) {
+    const cx<R> nxt2 = gather_row<R>(sd, nx, goff, rglob, rdf, 32 * (gi + S + 1) + lane);
+    const cx<R> d = dv[32 * gi + lane];
+    cx<R> outv;
+    if (!group_steps_mw<R, ST, S, KC, W>(pp, (32 / KC) * gi, b, lane, w, win0, own, nxt, outv, xch, sfail)) {
+      fail(sfail);
+      return;
+    }
+    if (w == 0) Yj[32 * gi + lane] = outv * d;
+    nxt = nxt2;
+  }
+  __syncthreads();   // warp 0's z visible to every warp
+
+  // ---------------- backward: L^T x = z on reversed rows ----------------
+  auto zrow = [&](int q) -> cx<R> { return q < npad ? Yj[npad - 1 - q] : zero; };
+  win0 = zrow(lane);
+#pragma unroll
+  for (int m = 0; m < SPW; ++m) own[m] = g0 + m < S ? zrow(32 * (g0 + m) + lane) : zero;
+  nxt = zrow(32 * S + lane);
+  for (int gi = 0; gi < G; ++gi) {
+    const cx<R> nxt2 = zrow(32 * (gi + S + 1) + lane);
+    cx<R> outv;
+    if (!group_steps_mw<R, ST, S, KC, W>(pp, pp.Q + (32 / KC) * gi, b, lane, w, win0, own, nxt, outv, xch,
+                                         sfail)) {
+      fail(sfail);
+      return;
+    }
+    if (w == 0) {
+      const int row = npad - 1 - (32 * gi + lane);
+      cx<R> v = zero;
+      if (row < sd.n) {
+        const int i = sd.ix0 + row % sd.nlx, j = sd.iy0 + row / sd.nlx;
+        v = (R)pou_weight(sd, i, j, o) * outv;
+      }
+      Yj[row] = v;
+    }
+    nxt = nxt2;
+  }
+}
+
+// The wide class (SMAX < S <= kApplyWideSlots) on kApplyWideWarps warps per
+// subdomain; arguments and band-class skipping as k_apply.
+template <typename R, typename ST, int SMAX, int KC, int W>
+__global__ void __launch_bounds__(32 * W)
+    k_apply_mw(const Geo* __restrict__ geos, const SubDesc* __restrict__ subs, const ST* __restrict__ Lf,
+               const ST* __restrict__ Lb, const cx<R>* __restrict__ dinv_all, const c128* __restrict__ rbase,
+               long long r_ld, const int* __restrict__ jptr, int rdf, cx<R>* __restrict__ Y, int stage_elems,
+               const KState* __restrict__ kst, DevStatus* status, int smin, int smax) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const SubDesc sd = subs[blockIdx.x];
+  const int S = (sd.b + 32) / 32;
+  if (S < smin || S > smax) return;
+  if (kst != nullptr && kst[sd.prob].stop) return;
+  const int nx = geos[sd.prob].nx, o = geos[sd.prob].ovlp;
+  const long long goff = geos[sd.prob].goff;
+  const c128* rglob = rbase;
+  if (jptr != nullptr)
+    rglob = rdf == 2 ? (const c128*)((const c64*)rbase + (long long)(*jptr) * r_ld)
+                     : (const c128*)((const dfc*)rbase + (long long)(*jptr) * r_ld);
+  constexpr int NST = stages_for<ST>();
+  Pipe<ST, KC> pp;
+  pp.bar = reinterpret_cast<uint64_t*>(sm);
+  pp.stg = reinterpret_cast<ST*>(sm + 128);
+  pp.src0 = Lf + sd.l_off;
+  pp.src1 = Lb + sd.l_off;
+  pp.stage_elems = stage_elems;
+  pp.Q = sd.npad / KC;
+  pp.bp = sd.bp;
+  pp.bytes = (uint32_t)(KC * sd.bp * sizeof(ST));
+  pp.limit = g_copy_wait_limit;
+  cx<R>* xch = reinterpret_cast<cx<R>*>(sm + 128 + (size_t)NST * stage_elems * sizeof(ST));
+  const int nseq = 2 * pp.Q;
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < NST; ++t) mbar_init(&pp.bar[t], 1);
+    mbar_fence_init();
+    for (int t = 0; t < NST && t < nseq; ++t) pp.issue(t);
+  }
+  __syncthreads();
+  const cx<R>* dv = dinv_all + sd.v_off;
+  cx<R>* Yj = Y + sd.v_off;
+#define RP_CASE(S_) \
+  case S_:          \
+    if constexpr (S_ > SMAX) sweeps_mw<R, ST, S_, KC, W>(sd, pp, nx, goff, o, rglob, rdf, dv, Yj, xch, status); \
     break;
   switch (S) {
-    RP_CASE(1) RP_CASE(2) RP_CASE(3) RP_CASE(4) RP_CASE(5) RP_CASE(6) RP_CASE(7) RP_CASE(8)
+    RP_CASE(5) RP_CASE(6) RP_CASE(7) RP_CASE(8)
     RP_CASE(9) RP_CASE(10) RP_CASE(11) RP_CASE(12) RP_CASE(13) RP_CASE(14) RP_CASE(15) RP_CASE(16)
     RP_CASE(17) RP_CASE(18) RP_CASE(19) RP_CASE(20) RP_CASE(21) RP_CASE(22) RP_CASE(23) RP_CASE(24)
     RP_CASE(25) RP_CASE(26) RP_CASE(27) RP_CASE(28) RP_CASE(29)
   }
   static_assert(kApplyWideSlots == 29, "the case list covers S = 1..29");
 #undef RP_CASE
-#undef RP_SWEEPS
 }
 
 template <typename R>
@@ -368,18 +509,18 @@ __global__ void k_prolong(Geo g, const SubDesc* __restrict__ subs, const cx<R>* 
 
 // SMAX: the narrow kernel's window, 6 slots for complex128, 8 for complex64
 // storage. The subdomains are launched in band classes by register slots
-// S = (b + 32) / 32: 1..4 and 5..SMAX on the narrow kernel, SMAX+1..29 on the
-// wide one; each launch covers all subdomains, skips those of the other
+// S = (b + 32) / 32: 1..4 and 5..SMAX on the narrow kernel, SMAX+1..29 on
+// k_apply_mw; each launch covers all subdomains, skips those of the other
 // classes, and sizes its ring for its own class, so that a few wide
 // subdomains do not shrink every warp's share of shared memory. The wide
-// class copies 16 columns per bulk copy (8 for complex128 storage), halved
-// where the ring would not fit, so that one warp keeps up to about 200 KB of
-// copies in flight. With side streams the classes run concurrently (the
-// widest first, on the side streams), else one after the other.
+// class copies the most columns per bulk copy (16, 8 or 4) for which two of
+// its CTAs share an SM, else the most for which its ring fits. With side
+// streams the classes run concurrently (the widest first, on the side
+// streams), else one after the other.
 template <typename R>
 constexpr int smax_for() { return sizeof(R) == 8 ? 6 : 8; }
 
-template <typename R, typename ST, int KC, bool WIDE>
+template <typename R, typename ST, int KC>
 cudaError_t launch_apply_k(int bp_max, int smin, int smax, const Geo* geos, const SubDesc* subs, int nsub,
                            const void* Lf, const void* Lb, const void* dinv, const c128* r, long long r_ld,
                            const int* jptr, int rdf, void* Y, const KState* kst, DevStatus* status,
@@ -387,28 +528,52 @@ cudaError_t launch_apply_k(int bp_max, int smin, int smax, const Geo* geos, cons
   const int stage_elems = KC * bp_max;
   const size_t smem = 128 + (size_t)stages_for<ST>() * KC * bp_max * sizeof(ST);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_apply<R, ST, smax_for<R>(), KC, WIDE>,
+  cudaError_t e = cudaFuncSetAttribute(k_apply<R, ST, smax_for<R>(), KC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_apply<R, ST, smax_for<R>(), KC, WIDE><<<nsub, 32, smem, st>>>(geos, subs, (const ST*)Lf, (const ST*)Lb,
-                                                                  (const cx<R>*)dinv, r, r_ld, jptr, rdf, (cx<R>*)Y,
-                                                                  stage_elems, kst, status, smin, smax);
+  k_apply<R, ST, smax_for<R>(), KC><<<nsub, 32, smem, st>>>(geos, subs, (const ST*)Lf, (const ST*)Lb,
+                                                            (const cx<R>*)dinv, r, r_ld, jptr, rdf, (cx<R>*)Y,
+                                                            stage_elems, kst, status, smin, smax);
   return cudaGetLastError();
 }
 
-// the wide class: the widest chunk (columns per copy) whose ring fits
+template <typename R, typename ST, int KC>
+cudaError_t launch_apply_mw(int bp_max, int smin, int smax, const Geo* geos, const SubDesc* subs, int nsub,
+                            const void* Lf, const void* Lb, const void* dinv, const c128* r, long long r_ld,
+                            const int* jptr, int rdf, void* Y, const KState* kst, DevStatus* status,
+                            cudaStream_t st) {
+  constexpr int W = kApplyWideWarps;
+  const int stage_elems = KC * bp_max;
+  const size_t smem = 128 + (size_t)stages_for<ST>() * KC * bp_max * sizeof(ST) + (size_t)W * 32 * sizeof(cx<R>);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  auto kern = k_apply_mw<R, ST, smax_for<R>(), KC, W>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<nsub, 32 * W, smem, st>>>(geos, subs, (const ST*)Lf, (const ST*)Lb, (const cx<R>*)dinv, r, r_ld, jptr, rdf,
+                                   (cx<R>*)Y, stage_elems, kst, status, smin, smax);
+  return cudaGetLastError();
+}
+
+// the wide class: the widest chunk (columns per copy) whose ring lets two
+// CTAs share an SM, else the widest whose ring fits
 template <typename R, typename ST>
 cudaError_t launch_apply_wide(int bp_max, int smin, int smax, const Geo* geos, const SubDesc* subs, int nsub,
                               const void* Lf, const void* Lb, const void* dinv, const c128* r, long long r_ld,
                               const int* jptr, int rdf, void* Y, const KState* kst, DevStatus* status,
                               cudaStream_t st) {
-  auto fits = [&](int kc) { return 128 + (size_t)stages_for<ST>() * kc * bp_max * sizeof(ST) <= 227 * 1024; };
+  auto bytes = [&](int kc) {
+    return 128 + (size_t)stages_for<ST>() * kc * bp_max * sizeof(ST) + (size_t)kApplyWideWarps * 32 * sizeof(cx<R>);
+  };
+  auto fits = [&](int kc, int per_sm) { return per_sm * (bytes(kc) + 1024) <= 228 * 1024; };
 #define RP_WIDE_ARGS bp_max, smin, smax, geos, subs, nsub, Lf, Lb, dinv, r, r_ld, jptr, rdf, Y, kst, status, st
-  if constexpr (sizeof(ST) < 16) {
-    if (fits(16)) return launch_apply_k<R, ST, 16, true>(RP_WIDE_ARGS);
+  for (int per_sm : {2, 1}) {
+    if constexpr (sizeof(ST) < 16) {
+      if (fits(16, per_sm)) return launch_apply_mw<R, ST, 16>(RP_WIDE_ARGS);
+    }
+    if (fits(8, per_sm)) return launch_apply_mw<R, ST, 8>(RP_WIDE_ARGS);
+    if (fits(4, per_sm)) return launch_apply_mw<R, ST, 4>(RP_WIDE_ARGS);
   }
-  if (fits(8)) return launch_apply_k<R, ST, 8, true>(RP_WIDE_ARGS);
-  return launch_apply_k<R, ST, 4, true>(RP_WIDE_ARGS);
+  return cudaErrorInvalidValue;
 #undef RP_WIDE_ARGS
 }
 
@@ -438,7 +603,7 @@ cudaError_t launch_apply_t(int max_b, const Geo* geos, const SubDesc* subs, int 
     if (c == 0)
       return launch_apply_wide<R, ST>(bp, cls[c][0], cls[c][1], geos, subs, nsub, Lf, Lb, dinv, r, r_ld, jptr, rdf, Y,
                                       kst, status, s);
-    return launch_apply_k<R, ST, KC, false>(bp, cls[c][0], cls[c][1], geos, subs, nsub, Lf, Lb, dinv, r, r_ld, jptr,
+    return launch_apply_k<R, ST, KC>(bp, cls[c][0], cls[c][1], geos, subs, nsub, Lf, Lb, dinv, r, r_ld, jptr,
                                            rdf, Y, kst, status, s);
   };
   cudaError_t e = cudaSuccess;

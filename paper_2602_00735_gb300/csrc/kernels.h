@@ -13,11 +13,16 @@ constexpr int kMaxBandC128 = 160;
 constexpr int kMaxBandC64 = 232;
 int max_band(int prec);
 // Wider subdomains (b up to kMaxBandWide, both precisions) are factored by
-// the blocked kernel of factor_wide.cu, with its window in device scratch,
-// and solved by the wide apply kernel (rotating register window of up to
-// kApplyWideSlots = ceil((kMaxBandWide + 1) / 32) slots).
+// the blocked kernels of factor_wide.cu, with their window in device scratch,
+// and solved by k_apply_mw (a register window of up to kApplyWideSlots =
+// ceil((kMaxBandWide + 1) / 32) slots shared over kApplyWideWarps warps).
 constexpr int kMaxBandWide = 900;
 constexpr int kApplyWideSlots = 29;
+// warps per subdomain of the wide-class sweep (k_apply_mw)
+#ifndef RP_APPLY_WIDE_WARPS
+#define RP_APPLY_WIDE_WARPS 2
+#endif
+constexpr int kApplyWideWarps = RP_APPLY_WIDE_WARPS;
 constexpr int kDotBlocksPerSM = 2;
 
 // Krylov control block in device memory.
