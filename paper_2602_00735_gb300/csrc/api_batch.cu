@@ -445,7 +445,7 @@ int ras_pml_batch_factor(ras_pml_batch* h) {
   }
   cudaError_t e = rp::launch_factor(h->prec, h->tune.factor_threads, h->tune.factor_rank, h->subs_d, h->nsub, h->max_b, Aloc, h->L,
                                     h->Lrev, h->dinv, h->pivstats, h->status, h->st, h->split, wscratch, false,
-                                    h->tune.wide_cluster);
+                                    h->tune.wide_cluster, &h->as);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   dfree(Aloc);
   if (wscratch) cudaFree(wscratch);

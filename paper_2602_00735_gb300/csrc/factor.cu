@@ -811,17 +811,17 @@ cudaError_t launch_factor_tc_nb(int rank, const SubDesc* subs, int nsub, int max
 }
 
 // mixed shape: the wide subdomains (launch positions 0..nwide-1) on the CUDA
-// cores with two pivots per pass, the others on the tensor cores, one launch
-// after the other on the stream
+// cores with two pivots per pass (on st_cuda), the others on the tensor cores
+// (on st)
 template <typename S>
 cudaError_t launch_factor_mixed(int threads, int rank, const SubDesc* subs, int nsub, int max_b, BandSplit sp,
                                 const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats,
-                                DevStatus* status, cudaStream_t st) {
+                                DevStatus* status, cudaStream_t st, cudaStream_t st_cuda) {
   cudaError_t e = cudaSuccess;
   const int nw = sp.nwide < nsub ? sp.nwide : nsub;
   if (nw > 0)
     e = launch_factor_s<float, S>(threads, 2, factor_smem_bytes(max_b, 1, 2), subs, nw, Aloc, L, Lrev, dinv, pivstats,
-                                  status, st, max_b);
+                                  status, st_cuda, max_b);
   if (e == cudaSuccess && nsub > nw) {
     const int mb = nw > 0 ? sp.max_b_tc : max_b;
     if (!factor_tc_ok(1, mb)) return cudaErrorInvalidValue;
@@ -834,23 +834,47 @@ cudaError_t launch_factor_mixed(int threads, int rank, const SubDesc* subs, int 
 
 cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, int nsub, int max_b,
                           const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status,
-                          cudaStream_t st, BandSplit split, void* wscratch, bool skip_wide, int wide_cluster) {
+                          cudaStream_t st, BandSplit split, void* wscratch, bool skip_wide, int wide_cluster,
+                          const ApplyStreams* as) {
   if (max_b > max_band(prec)) {
     // the subdomains wider than the shared-memory window first (blocked
     // kernel, window in scratch), then the others with the chosen shape,
     // sized for the widest of them; each launch skips the other kind
     const int cl = wide_cluster > 0 ? wide_cluster : wide_cluster_auto(split.nblocked);
-    cudaError_t e = skip_wide ? cudaSuccess
-                              : launch_factor_wide(prec, subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status,
-                                                   wscratch, st, cl);
+    const bool conc = as != nullptr && as->side[0] != nullptr && as->side[1] != nullptr && !skip_wide &&
+                      split.max_b_narrow > 0 && factor_shape_valid(prec, split.max_b_narrow, threads, rank, split);
+    cudaError_t e = cudaSuccess;
+    if (conc) {
+      e = cudaEventRecord(as->fork, st);
+      for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(as->side[i], as->fork, 0);
+    }
+    if (e == cudaSuccess && !skip_wide)
+      e = launch_factor_wide(prec, subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status, wscratch,
+                             conc ? as->side[0] : st, cl);
     if (e != cudaSuccess || split.max_b_narrow <= 0) return e;
+    if (conc) {
+      const int mn = split.max_b_narrow;
+      if (is_tc_rank(rank) && threads != kTcM)
+        e = prec == 1 ? launch_factor_mixed<c64>(threads, rank, subs, nsub, mn, split, Aloc, L, Lrev, dinv, pivstats,
+                                                 status, st, as->side[1])
+                      : launch_factor_mixed<h2c>(threads, rank, subs, nsub, mn, split, Aloc, L, Lrev, dinv, pivstats,
+                                                 status, st, as->side[1]);
+      else
+        e = launch_factor(prec, threads, rank, subs, nsub, mn, Aloc, L, Lrev, dinv, pivstats, status, as->side[1],
+                          split, nullptr, true, 0, nullptr);
+      for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventRecord(as->join[i], as->side[i]);
+      for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(st, as->join[i], 0);
+      return e;
+    }
     max_b = split.max_b_narrow;
   }
   if (!factor_shape_valid(prec, max_b, threads, rank, split)) return cudaErrorInvalidValue;
   if (is_tc_rank(rank) && threads != kTcM) {
     if (prec == 1)
-      return launch_factor_mixed<c64>(threads, rank, subs, nsub, max_b, split, Aloc, L, Lrev, dinv, pivstats, status, st);
-    return launch_factor_mixed<h2c>(threads, rank, subs, nsub, max_b, split, Aloc, L, Lrev, dinv, pivstats, status, st);
+      return launch_factor_mixed<c64>(threads, rank, subs, nsub, max_b, split, Aloc, L, Lrev, dinv, pivstats, status, st,
+                                      st);
+    return launch_factor_mixed<h2c>(threads, rank, subs, nsub, max_b, split, Aloc, L, Lrev, dinv, pivstats, status, st,
+                                    st);
   }
   if (is_tc_rank(rank)) {
     if (prec == 1) return launch_factor_tc_nb<c64>(rank, subs, nsub, max_b, Aloc, L, Lrev, dinv, pivstats, status, st);

@@ -139,10 +139,6 @@ size_t factor_smem_bytes(int b, int prec, int rank);
 // (slots) x factor_wide_slot_bytes(prec, max_b) bytes, SubDesc::wslot < slots;
 // skip_wide leaves them out (the tuner times the other kernels' shapes);
 // wide_cluster: CTAs per wide subdomain (0: wide_cluster_auto(split.nblocked)).
-cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, int nsub, int max_b,
-                          const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status,
-                          cudaStream_t st, BandSplit split = BandSplit{}, void* wscratch = nullptr,
-                          bool skip_wide = false, int wide_cluster = 0);
 
 // apply.cu
 size_t apply_smem_bytes(int max_bp, int prec, int cols);
@@ -165,6 +161,15 @@ struct ApplyStreams {
   uint32_t slot_mask = 0;
 };
 uint32_t apply_slot_mask(const SubDesc* subs_host, int nsub);
+// All local factors. With side streams (as, both set) and subdomains wider
+// than the shared-memory window, the wide launch, the narrow CUDA-core launch
+// and the narrow tensor-core launch run concurrently (forked from st, joined
+// back into it), so that SMs the wide kernel's last CTAs leave idle take
+// narrow subdomains; else one after the other on st.
+cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, int nsub, int max_b,
+                          const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status,
+                          cudaStream_t st, BandSplit split = BandSplit{}, void* wscratch = nullptr,
+                          bool skip_wide = false, int wide_cluster = 0, const ApplyStreams* as = nullptr);
 cudaError_t launch_local_solves(int prec, int cols, const Geo* geos, const SubDesc* subs, int nsub, int max_b,
                                 int max_bp, const void* Lf, const void* Lb, const void* dinv, const c128* r,
                                 long long r_ld, const int* jptr, void* Y, const KState* kst, DevStatus* status,
