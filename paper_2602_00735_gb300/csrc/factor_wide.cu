@@ -516,12 +516,17 @@ __global__ void __launch_bounds__(kWideTcThreads)
   }
 }
 
+// entries between the panel's columns in shared memory: odd, so that the 16
+// or 32 columns of one row fall in different banks (the panel copy and the
+// reversed-row outputs walk a row across the columns)
+inline int wide_pld(int nb, int max_b) { return (nb + max_b + kWideOverhang) | 1; }
+
 // the panel width for bands up to max_b: the largest NB whose panel fits in
 // shared memory; 0 when none does
 template <typename R>
 int wide_nb(int max_b) {
   for (int nb : {32, 16, 8}) {
-    const size_t bytes = ((size_t)nb * (nb + max_b + kWideOverhang) + 3 * nb) * sizeof(cx<R>);
+    const size_t bytes = ((size_t)nb * wide_pld(nb, max_b) + 3 * nb) * sizeof(cx<R>);
     if (bytes <= 220 * 1024) return nb;
   }
   return 0;
@@ -531,7 +536,7 @@ template <typename R, typename S, int NB>
 cudaError_t launch_wide_t(const SubDesc* subs, int nsub, int bmin, int max_b, int cl, const c128* Aloc, void* L,
                           void* Lrev, void* dinv, double* pivstats, DevStatus* status, void* scratch,
                           cudaStream_t st) {
-  const int pld = NB + max_b + kWideOverhang;
+  const int pld = wide_pld(NB, max_b);
   const size_t smem = ((size_t)NB * pld + 3 * NB) * sizeof(cx<R>);
   auto kern = k_factor_wide<R, S, NB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -571,7 +576,7 @@ template <typename S>
 cudaError_t launch_wide_tc(const SubDesc* subs, int nsub, int bmin, int max_b, const c128* Aloc, void* L, void* Lrev,
                            void* dinv, double* pivstats, DevStatus* status, void* scratch, cudaStream_t st) {
   constexpr int NB = kWideTcNB;
-  const int pld = NB + max_b + kWideOverhang;
+  const int pld = wide_pld(NB, max_b);
   const size_t smem = 8 * (size_t)kWideTcArr + ((size_t)NB * pld + 2 * NB) * sizeof(c64) + 16;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_factor_wide_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
