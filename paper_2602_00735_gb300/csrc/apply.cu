@@ -275,13 +275,63 @@ __global__ void __launch_bounds__(32)
 // previous stage, whose refill thread 0 then issues. Two warps measured
 // fastest on a batch of 64 problems with 208 wide subdomains (b up to 408;
 // four warps: more barriers per slot).
+// The KC steps of one ring stage for warp WI: slot 0 and the warp's SPW
+// slots. Slots 1..S-2 lie inside the band for every lane and step (their
+// entry t = lane - i - 1 + 32 g is at most 32 S - 34 < b, since S =
+// floor((b + 32) / 32)); only slot 0 (rows entering at the bottom) and slot
+// S - 1 are checked against b. WI is a template argument so that each slot's
+// offset in the column is an immediate.
+template <typename R, typename ST, int S, int KC, int W, int WI>
+__device__ __forceinline__ void stage_steps_mw(const ST* __restrict__ Lc, int bp, int c4, int b, int lane,
+                                               cx<R>& win0, cx<R> (&own)[(S - 1 + W - 1) / W], const cx<R>& nxt,
+                                               cx<R>& outv) {
+  constexpr int SPW = (S - 1 + W - 1) / W;
+  constexpr int G0 = 1 + WI * SPW;
+#pragma unroll 4
+  for (int ii = 0; ii < KC; ++ii) {
+    const int i = c4 * KC + ii;
+    const int base = lane - i - 1;
+    const ST* col = Lc + ii * bp + base;   // entry t of the column at col[t - base]
+    const cx<R> y = shfl(win0, i);
+    if (lane == i) {
+      outv = y;
+      win0 = nxt;
+    }
+    {
+      const int off = (lane > i) ? 0 : 32 * S;
+      if (base + off < b) win0 = fms(win0, ld_entry(col[off]), y);
+    }
+#pragma unroll
+    for (int m = 0; m < SPW; ++m) {
+      if (G0 + m < S - 1) {
+        own[m] = fms(own[m], ld_entry(col[32 * (G0 + m)]), y);
+      } else if (G0 + m == S - 1) {
+        if (base + 32 * (S - 1) < b) own[m] = fms(own[m], ld_entry(col[32 * (S - 1)]), y);
+      }
+    }
+  }
+}
+
+template <typename R, typename ST, int S, int KC, int W, int WI>
+__device__ __forceinline__ void stage_dispatch_mw(int w, const ST* Lc, int bp, int c4, int b, int lane, cx<R>& win0,
+                                                  cx<R> (&own)[(S - 1 + W - 1) / W], const cx<R>& nxt,
+                                                  cx<R>& outv) {
+  if constexpr (WI < W) {
+    if (w == WI) {
+      stage_steps_mw<R, ST, S, KC, W, WI>(Lc, bp, c4, b, lane, win0, own, nxt, outv);
+      return;
+    }
+    stage_dispatch_mw<R, ST, S, KC, W, WI + 1>(w, Lc, bp, c4, b, lane, win0, own, nxt, outv);
+  }
+}
+
 template <typename R, typename ST, int S, int KC, int W>
 __device__ __forceinline__ bool group_steps_mw(const Pipe<ST, KC>& pp, int s0, int b, int lane, int w,
                                                cx<R>& win0, cx<R> (&own)[(S - 1 + W - 1) / W], const cx<R>& nxt,
                                                cx<R>& outv, cx<R>* xch, int& sfail) {
   constexpr int SPW = (S - 1 + W - 1) / W;
   constexpr int NST = stages_for<ST>();
-  const int bp = pp.bp, g0 = 1 + w * SPW;
+  const int g0 = 1 + w * SPW;
 #pragma unroll 1
   for (int c4 = 0; c4 < 32 / KC; ++c4) {
     const int s = s0 + c4;
@@ -296,26 +346,8 @@ __device__ __forceinline__ bool group_steps_mw(const Pipe<ST, KC>& pp, int s0, i
       fence_proxy_async_smem();
       pp.issue(s - 1 + NST);
     }
-#pragma unroll 2
-    for (int ii = 0; ii < KC; ++ii) {
-      const int i = c4 * KC + ii;
-      const ST* col = Lc + ii * bp;
-      const cx<R> y = shfl(win0, i);
-      if (lane == i) {
-        outv = y;
-        win0 = nxt;
-      }
-      const int base = lane - i - 1;
-      {
-        const int t = (lane > i) ? base : base + 32 * S;
-        if (t < b) win0 = fms(win0, ld_entry(col[t]), y);
-      }
-#pragma unroll
-      for (int m = 0; m < SPW; ++m) {
-        const int t = base + 32 * (g0 + m);
-        if (g0 + m < S && t < b) own[m] = fms(own[m], ld_entry(col[t]), y);
-      }
-    }
+    // the steps themselves have no barrier: the warps take their own code
+    stage_dispatch_mw<R, ST, S, KC, W, 0>(w, Lc, pp.bp, c4, b, lane, win0, own, nxt, outv);
   }
   // move the window up one slot
   xch[w * 32 + lane] = own[0];
@@ -405,7 +437,7 @@ __device__ __forceinline__ void sweeps_mw(const SubDesc& sd, const Pipe<ST, KC>&
 // The wide class (SMAX < S <= kApplyWideSlots) on kApplyWideWarps warps per
 // subdomain; arguments and band-class skipping as k_apply.
 template <typename R, typename ST, int SMAX, int KC, int W>
-__global__ void __launch_bounds__(32 * W)
+__global__ void __launch_bounds__(32 * W, 1)
     k_apply_mw(const Geo* __restrict__ geos, const SubDesc* __restrict__ subs, const ST* __restrict__ Lf,
                const ST* __restrict__ Lb, const cx<R>* __restrict__ dinv_all, const c128* __restrict__ rbase,
                long long r_ld, const int* __restrict__ jptr, int rdf, cx<R>* __restrict__ Y, int stage_elems,
