@@ -303,7 +303,13 @@ void ras_pml_destroy(ras_pml_handle* h);
  * 512 and 1024 threads with two, and, when factor_prec >= 1 and every
  * half-bandwidth is <= 127, the blocked form on the tensor cores (128
  * threads, factor_rank 8 or 16: that many pivots per panel, the trailing
- * update as TF32 MMAs with a three-term split of each FP32 operand); apply
+ * update as TF32 MMAs with a three-term split of each FP32 operand); in
+ * the batched form with factor_prec >= 1 also the tensor-core form mixed
+ * with two-pivot CUDA-core shapes for the half-bandwidths above 127, and
+ * factor_rank 24 (128 threads): those half-bandwidths (up to the
+ * shared-memory window's limit) on the blocked tensor-core kernel of the
+ * wide bands, window in device scratch, the rest with 16 pivots per panel;
+ * apply
  * columns 8, plus 4 and 16 when factor_prec = 1; where subdomains are wider
  * than the shared-memory window, the wide-band factor's shape: 1, 2 or 4
  * CTAs per subdomain on the CUDA cores, or (factor_prec >= 1) 16, the
@@ -315,13 +321,14 @@ void ras_pml_destroy(ras_pml_handle* h);
  * ------------------------------------------------------------------------- */
 typedef struct {
   int32_t factor_threads;    /* chosen threads per factor CTA                 */
-  int32_t factor_rank;       /* chosen pivots per pass (1, 2; 8, 16: tensor cores) */
+  int32_t factor_rank;       /* chosen pivots per pass (1, 2; 8, 16: tensor cores;
+                                24: blocked tensor-core form, batched) */
   int32_t apply_cols;        /* chosen band columns per bulk copy             */
   int32_t n_factor;          /* factor candidates timed (entries below)       */
   int32_t n_apply;           /* apply candidates timed                        */
-  int32_t factor_cand_threads[8];
-  int32_t factor_cand_rank[8];
-  float   factor_ms[8];      /* median time of each factor candidate          */
+  int32_t factor_cand_threads[10];
+  int32_t factor_cand_rank[10];
+  float   factor_ms[10];     /* median time of each factor candidate          */
   int32_t apply_cand[4];
   float   apply_ms[4];       /* median time of each apply candidate (local
                                 solves of all subdomains)                     */
@@ -341,7 +348,9 @@ int ras_pml_tune(ras_pml_handle* h, ras_pml_tune_t* report);
  * handle of the same sizes): factor_threads 128, 256 or 512 with
  * factor_rank 1 or 2, 1024 with factor_rank 2, or 128 with factor_rank 8
  * or 16 (the tensor-core form: factor_prec >= 1 and every half-bandwidth
- * <= 127);
+ * <= 127; in the batched form also 256, 512 or 1024 threads, mixed with
+ * the CUDA-core kernel for half-bandwidths above 127, or 128 threads with
+ * factor_rank 24, the blocked tensor-core kernel for those);
  * apply_cols 8, or 4 or 16 with factor_prec = 1; wide_cluster 1, 2 or 4
  * CTAs per subdomain of the wide-band factor on the CUDA cores, 16 for its
  * tensor-core form (factor_prec >= 1), or 0 for the automatic choice.

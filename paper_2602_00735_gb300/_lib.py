@@ -54,8 +54,8 @@ class Timing(ctypes.Structure):
 
 class TuneReport(ctypes.Structure):
     _fields_ = [("factor_threads", c_int32), ("factor_rank", c_int32), ("apply_cols", c_int32),
-                ("n_factor", c_int32), ("n_apply", c_int32), ("factor_cand_threads", c_int32 * 8),
-                ("factor_cand_rank", c_int32 * 8), ("factor_ms", ctypes.c_float * 8),
+                ("n_factor", c_int32), ("n_apply", c_int32), ("factor_cand_threads", c_int32 * 10),
+                ("factor_cand_rank", c_int32 * 10), ("factor_ms", ctypes.c_float * 10),
                 ("apply_cand", c_int32 * 4), ("apply_ms", ctypes.c_float * 4), ("wide_cluster", c_int32),
                 ("n_wide", c_int32), ("wide_cand", c_int32 * 4), ("wide_ms", ctypes.c_float * 4)]
 

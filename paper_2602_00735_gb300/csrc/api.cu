@@ -314,8 +314,7 @@ int ras_pml_setup(const ras_pml_params* pp, void* stream, ras_pml_handle** out) 
   h->nsub = (int)h->subs_h.size();
   h->sum_npad = v_off;
   h->sum_l = l_off;
-  h->nwslot = rp::assign_wide_slots(h->subs_h, h->p.factor_prec, &h->split.max_b_narrow);
-  h->split.nblocked = h->nwslot;
+  h->nwslot = rp::assign_wide_slots(h->subs_h, h->p.factor_prec, &h->split.max_b_narrow, &h->split.nblocked);
   if (const int sa = rp::make_apply_streams(&h->as, h->subs_h, h->p.factor_prec); sa != RASPML_OK) {
     ras_pml_destroy(h);
     return sa;

@@ -32,7 +32,7 @@ struct ras_pml_batch {
   std::vector<int> tile_prob_h, tile0_h, tile1_h;
   long long ntot = 0, sum_n = 0, sum_npad = 0, sum_l = 0, sum_bn = 0;
   int nsub = 0, max_b = 0, max_bp = 0, max_npad = 0, ntiles = 0;
-  int nwslot = 0;                   // subdomains of the wide-band factor (b > max_band)
+  int nwslot = 0;                   // scratch slots (split.nblocked of them for b > max_band)
   Geo* geos_d = nullptr;
   SubDesc* subs_d = nullptr;
   int *sub_index_d = nullptr, *tile_prob_d = nullptr, *tile0_d = nullptr, *tile1_d = nullptr;
@@ -266,8 +266,11 @@ int ras_pml_batch_setup(const ras_pml_params* params, int nprob, void* stream, r
   }
   h->sum_npad = v_off;
   h->sum_l = l_off;
-  h->nwslot = rp::assign_wide_slots(h->subs_h, h->prec, &h->split.max_b_narrow);
-  h->split.nblocked = h->nwslot;
+  // scratch slots: the subdomains wider than the shared-memory window, then
+  // (complex64 arithmetic) those with kMaxBandTc < b <= max_band for the
+  // blocked tensor-core shape (factor_rank kRankTcBlocked)
+  h->nwslot = rp::assign_wide_slots(h->subs_h, h->prec, &h->split.max_b_narrow, &h->split.nblocked,
+                                    h->prec >= 1 ? rp::kMaxBandTc : -1);
   if (const int sa = rp::make_apply_streams(&h->as, h->subs_h, h->prec); sa != RASPML_OK) {
     ras_pml_batch_destroy(h);
     return sa;
@@ -439,7 +442,8 @@ int ras_pml_batch_factor(ras_pml_batch* h) {
   s = batch_local_rows(h, &Aloc);
   if (s != RASPML_OK) { dfree(Aloc); return s; }
   void* wscratch = nullptr;
-  if ((s = rp::alloc_wide_scratch(&wscratch, h->nwslot, h->prec, h->max_b)) != RASPML_OK) {
+  const int slots = h->tune.factor_rank == rp::kRankTcBlocked ? h->nwslot : h->split.nblocked;
+  if ((s = rp::alloc_wide_scratch(&wscratch, slots, h->prec, h->max_b)) != RASPML_OK) {
     dfree(Aloc);
     return s;
   }

@@ -28,6 +28,8 @@
 // at l_off + (npad-1-i)*bp; this is the column band of L^T in reversed
 // index order, which the backward sweep of the apply streams. The caller
 // zero-fills that copy first (entries left of column 0 stay zero).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "tc.cuh"
@@ -754,6 +756,8 @@ bool factor_tc_ok(int prec, int max_b) { return prec >= 1 && max_b >= 1 && max_b
 // one thread to each of the b + 1 window diagonals (and the entering row), so
 // a CUDA-core shape needs at least b + 2 threads.
 bool factor_shape_valid(int prec, int max_b, int threads, int rank, BandSplit split) {
+  if (rank == kRankTcBlocked)
+    return prec >= 1 && split.nwide >= 0 && threads == kTcM && (split.max_b_tc == 0 || factor_tc_ok(prec, split.max_b_tc));
   if (is_tc_rank(rank)) {
     if (threads == kTcM) return factor_tc_ok(prec, max_b);
     return prec >= 1 && split.nwide >= 0 && (threads == 256 || threads == 512 || threads == 1024) &&
@@ -836,6 +840,40 @@ cudaError_t launch_factor(int prec, int threads, int rank, const SubDesc* subs, 
                           const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status,
                           cudaStream_t st, BandSplit split, void* wscratch, bool skip_wide, int wide_cluster,
                           const ApplyStreams* as) {
+  if (rank == kRankTcBlocked) {
+    // launch positions 0..nw-1 hold the subdomains with b > kMaxBandTc: the
+    // blocked tensor-core kernel takes them up to max_band(prec) (all of
+    // them when the wide-band shape is the tensor-core form too: one launch),
+    // the wide-band shape those above; the rest go to the tensor-core kernel
+    if (!factor_shape_valid(prec, max_b, threads, rank, split)) return cudaErrorInvalidValue;
+    const int nw = std::min(split.nwide, nsub);
+    const bool has_wide = max_b > max_band(prec) && !skip_wide;
+    const int cl = wide_cluster > 0 ? wide_cluster : wide_cluster_auto(split.nblocked);
+    const bool merged = has_wide && cl == kWideTensorCores;
+    const bool conc = as != nullptr && as->side[0] != nullptr && as->side[1] != nullptr;
+    cudaError_t e = cudaSuccess;
+    if (conc) {
+      e = cudaEventRecord(as->fork, st);
+      for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(as->side[i], as->fork, 0);
+    }
+    cudaStream_t s_wide = conc ? as->side[0] : st, s_mid = conc ? as->side[1] : st;
+    if (e == cudaSuccess && has_wide && !merged)
+      e = launch_factor_wide(prec, subs, nw, max_b, Aloc, L, Lrev, dinv, pivstats, status, wscratch, s_wide, cl);
+    if (e == cudaSuccess && nw > 0)
+      e = launch_factor_wide(prec, subs, nw, max_b, Aloc, L, Lrev, dinv, pivstats, status, wscratch,
+                             merged ? s_wide : s_mid, kWideTensorCores, kMaxBandTc,
+                             merged ? kMaxBandWide : max_band(prec));
+    if (e == cudaSuccess && nsub > nw)
+      e = prec == 1 ? launch_factor_tc_nb<c64>(16, subs, nsub - nw, split.max_b_tc, Aloc, L, Lrev, dinv, pivstats,
+                                              status, st, nw)
+                    : launch_factor_tc_nb<h2c>(16, subs, nsub - nw, split.max_b_tc, Aloc, L, Lrev, dinv, pivstats,
+                                              status, st, nw);
+    if (conc) {
+      for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventRecord(as->join[i], as->side[i]);
+      for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(st, as->join[i], 0);
+    }
+    return e;
+  }
   if (max_b > max_band(prec)) {
     // the subdomains wider than the shared-memory window first (blocked
     // kernel, window in scratch), then the others with the chosen shape,

@@ -32,6 +32,8 @@
 // number of times (one subdomain, one loop).
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "tc.cuh"
@@ -256,13 +258,14 @@ template <typename S>
 __global__ void __launch_bounds__(kWideTcThreads)
     k_factor_wide_tc(const SubDesc* __restrict__ subs, const c128* __restrict__ Aloc, S* __restrict__ Lall,
                      S* __restrict__ Lrev_all, c64* __restrict__ dinv_all, double* __restrict__ pivstats,
-                     DevStatus* status, c64* __restrict__ scratch, long long slot_elems, int bmin, int pld) {
+                     DevStatus* status, c64* __restrict__ scratch, long long slot_elems, int bmin, int bmax,
+                     int pld) {
   constexpr int NB = kWideTcNB, T = kWideTcTile;
   constexpr uint32_t AB = kWideTcArr;
   extern __shared__ __align__(1024) unsigned char smt[];
   const int sub = blockIdx.x;
   const SubDesc sd = subs[sub];
-  if (sd.b <= bmin || sd.wslot < 0) return;   // before any TMEM allocation
+  if (sd.b <= bmin || sd.b > bmax || sd.wslot < 0) return;   // before any TMEM allocation
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int b = sd.b, bp = sd.bp, npad = sd.npad;
   const int RS = NB + b, LDW = b + 1;
@@ -573,24 +576,32 @@ cudaError_t launch_wide_s(const SubDesc* subs, int nsub, int bmin, int max_b, in
 }
 
 template <typename S>
-cudaError_t launch_wide_tc(const SubDesc* subs, int nsub, int bmin, int max_b, const c128* Aloc, void* L, void* Lrev,
-                           void* dinv, double* pivstats, DevStatus* status, void* scratch, cudaStream_t st) {
+cudaError_t launch_wide_tc(const SubDesc* subs, int nsub, int bmin, int bmax, int max_b, long long slot,
+                           const c128* Aloc, void* L, void* Lrev, void* dinv, double* pivstats, DevStatus* status,
+                           void* scratch, cudaStream_t st) {
   constexpr int NB = kWideTcNB;
-  const int pld = wide_pld(NB, max_b);
+  const int bl = std::min(max_b, bmax);   // the widest band this launch factors
+  const int pld = wide_pld(NB, bl);
   const size_t smem = 8 * (size_t)kWideTcArr + ((size_t)NB * pld + 2 * NB) * sizeof(c64) + 16;
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  if (smem > 227 * 1024 || (long long)(NB + bl) * (bl + 1) > slot) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_factor_wide_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long slot = (long long)(NB + max_b) * (max_b + 1);
   k_factor_wide_tc<S><<<nsub, kWideTcThreads, smem, st>>>(subs, Aloc, (S*)L, (S*)Lrev, (c64*)dinv, pivstats, status,
-                                                          (c64*)scratch, slot, bmin, pld);
+                                                          (c64*)scratch, slot, bmin, bmax, pld);
   return cudaGetLastError();
 }
 
 }  // namespace
 
+// one slot: the window of the widest CUDA-core panel for max_b, or, below
+// the shared-memory window's limit (where only the tensor-core form runs,
+// complex64), of its 16-pivot panel
 size_t factor_wide_slot_bytes(int prec, int max_b) {
-  if (max_b <= max_band(prec) || max_b > kMaxBandWide) return 0;
+  if (max_b > kMaxBandWide) return 0;
+  if (max_b <= max_band(prec)) {
+    if (prec == 0 || max_b <= kMaxBandTc) return 0;
+    return (size_t)(kWideTcNB + max_b) * (max_b + 1) * sizeof(c64);
+  }
   const size_t es = prec == 0 ? sizeof(c128) : sizeof(c64);
   const int nb = prec == 0 ? wide_nb<double>(max_b) : wide_nb<float>(max_b);
   return (size_t)(nb + max_b) * (max_b + 1) * es;
@@ -607,18 +618,24 @@ int wide_cluster_auto(int nblocked) {
 
 cudaError_t launch_factor_wide(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
                                void* Lrev, void* dinv, double* pivstats, DevStatus* status, void* scratch,
-                               cudaStream_t st, int cl) {
-  const int bmin = max_band(prec);
-  if (max_b <= bmin) return cudaSuccess;
+                               cudaStream_t st, int cl, int bmin, int bmax) {
+  if (bmin < 0) bmin = max_band(prec);
+  if (max_b <= bmin || bmax <= bmin) return cudaSuccess;
   if (max_b > kMaxBandWide || scratch == nullptr) return cudaErrorInvalidValue;
   if (cl == kWideTensorCores) {
     // the tensor-core form: complex64 arithmetic; its panel (16 pivots) is
-    // never wider than the CUDA-core form's, so the scratch slot holds it
-    if (prec == 1) return launch_wide_tc<c64>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
-    if (prec == 2) return launch_wide_tc<h2c>(subs, nsub, bmin, max_b, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
+    // never wider than the CUDA-core form's, so the slot of max_b holds it
+    if (bmin < kMaxBandTc) return cudaErrorInvalidValue;
+    const long long slot = (long long)(factor_wide_slot_bytes(prec, max_b) / sizeof(c64));
+    if (prec == 1)
+      return launch_wide_tc<c64>(subs, nsub, bmin, bmax, max_b, slot, Aloc, L, Lrev, dinv, pivstats, status, scratch,
+                                 st);
+    if (prec == 2)
+      return launch_wide_tc<h2c>(subs, nsub, bmin, bmax, max_b, slot, Aloc, L, Lrev, dinv, pivstats, status, scratch,
+                                 st);
     return cudaErrorInvalidValue;
   }
-  if (!(cl == 1 || cl == 2 || cl == 4)) return cudaErrorInvalidValue;
+  if (!(cl == 1 || cl == 2 || cl == 4) || bmin != max_band(prec) || bmax < max_b) return cudaErrorInvalidValue;
   if (prec == 0)
     return launch_wide_s<double, c128>(subs, nsub, bmin, max_b, cl, Aloc, L, Lrev, dinv, pivstats, status, scratch, st);
   if (prec == 1)

@@ -77,18 +77,23 @@ int build_problem(const ras_pml_params& p, int prob, Geo& g, std::vector<SubDesc
 inline long long sub_l_entries(const SubDesc& d) { return (long long)d.npad * d.bp; }
 
 // Scratch slots of the wide-band factor: SubDesc::wslot numbers the
-// subdomains with b > max_band(prec) in order, -1 elsewhere. Returns the
-// number of slots; *max_b_narrow is the widest of the other subdomains.
-inline int assign_wide_slots(std::vector<SubDesc>& subs, int prec, int* max_b_narrow) {
+// subdomains with b > max_band(prec) in order (slots 0 .. *nblocked - 1),
+// then, when slot_bmin >= 0, those with slot_bmin < b <= max_band(prec) (the
+// blocked tensor-core form of factor_rank kRankTcBlocked), -1 elsewhere.
+// Returns the number of slots; *max_b_narrow is the widest subdomain at or
+// below max_band(prec).
+inline int assign_wide_slots(std::vector<SubDesc>& subs, int prec, int* max_b_narrow, int* nblocked,
+                             int slot_bmin = -1) {
   int slots = 0, nb = 0;
   for (SubDesc& d : subs) {
-    if (d.b > max_band(prec)) {
-      d.wslot = slots++;
-    } else {
-      d.wslot = -1;
-      nb = std::max(nb, d.b);
-    }
+    d.wslot = -1;
+    if (d.b > max_band(prec)) d.wslot = slots++;
+    else nb = std::max(nb, d.b);
   }
+  *nblocked = slots;
+  if (slot_bmin >= 0)
+    for (SubDesc& d : subs)
+      if (d.b > slot_bmin && d.b <= max_band(prec)) d.wslot = slots++;
   *max_b_narrow = nb;
   return slots;
 }

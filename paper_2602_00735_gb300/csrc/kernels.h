@@ -57,6 +57,12 @@ struct Tune {
 // and b <= kMaxBandTc
 inline bool is_tc_rank(int rank) { return rank == 8 || rank == 16; }
 constexpr int kMaxBandTc = 127;
+// factor_rank kRankTcBlocked (with 128 threads; the batched form, complex64
+// arithmetic): the subdomains with kMaxBandTc < b <= max_band(prec) on the
+// blocked tensor-core kernel of factor_wide.cu (window in a scratch slot),
+// those with b <= kMaxBandTc on the tensor-core kernel with 16 pivots per
+// panel; wider ones as always on the wide-band factor's own shape.
+constexpr int kRankTcBlocked = 24;
 // Subdomains split by half-bandwidth for the mixed factor shape (factor_rank
 // 8 or 16 with 256, 512 or 1024 threads): the first nwide entries of the
 // launch order have b > kMaxBandTc and go to the CUDA-core kernel (two
@@ -118,20 +124,22 @@ cudaError_t launch_spmv7(long long n, int nx, const Stencil7& A, const c128* x, 
 cudaError_t launch_factor_lu(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aw, void* L, void* Urev,
                              void* dinv, double* pivstats, DevStatus* status, cudaStream_t st);
 
-// factor_wide.cu: the subdomains with max_band(prec) < b <= kMaxBandWide,
-// each factored by a cluster of cl CTAs (1, 2 or 4) on the CUDA cores, or,
-// with cl = kWideTensorCores (complex64 arithmetic, prec 1 and 2), by one CTA
-// with the trailing update on the tensor cores, in its own scratch slot
-// (SubDesc::wslot) of factor_wide_slot_bytes(prec, max_b) bytes; the other
-// subdomains of the launch return at once. wide_cluster_auto: the largest
-// cl in {4, 2} for which all nblocked clusters are resident at once (one CTA
-// per SM), else 1.
+// factor_wide.cu: the subdomains with bmin < b <= bmax (bmin < 0: from
+// max_band(prec); b up to kMaxBandWide), each factored by a cluster of cl
+// CTAs (1, 2 or 4; only from max_band(prec)) on the CUDA cores, or, with
+// cl = kWideTensorCores (complex64 arithmetic, prec 1 and 2; bmin down to
+// kMaxBandTc), by one CTA with the trailing update on the tensor cores, in
+// its own scratch slot (SubDesc::wslot) of factor_wide_slot_bytes(prec,
+// max_b) bytes, max_b the widest band of all slots (one slot stride for every
+// launch); the other subdomains of the launch return at once.
+// wide_cluster_auto: the largest cl in {4, 2} for which all nblocked clusters
+// are resident at once (one CTA per SM), else 1.
 constexpr int kWideTensorCores = 16;
 size_t factor_wide_slot_bytes(int prec, int max_b);
 int wide_cluster_auto(int nblocked);
 cudaError_t launch_factor_wide(int prec, const SubDesc* subs, int nsub, int max_b, const c128* Aloc, void* L,
                                void* Lrev, void* dinv, double* pivstats, DevStatus* status, void* scratch,
-                               cudaStream_t st, int cl);
+                               cudaStream_t st, int cl, int bmin = -1, int bmax = kMaxBandWide);
 
 // factor.cu
 size_t factor_smem_bytes(int b, int prec, int rank);

@@ -33,8 +33,10 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
   // the CUDA-core shapes, then the tensor-core forms: alone where every
   // band allows it, else mixed with the fastest two-pivot CUDA-core shape
   // on the wide subdomains (the batched form's order by band)
-  int fthreads[8] = {128, 256, 512, 256, 512, 1024, 128, 128};
-  const int franks[8] = {1, 1, 1, 2, 2, 2, 8, 16};
+  // (the batched form, complex64: also the blocked tensor-core kernel for
+  // kMaxBandTc < b <= max_band with the tensor-core kernel for the rest)
+  int fthreads[9] = {128, 256, 512, 256, 512, 1024, 128, 128, 128};
+  const int franks[9] = {1, 1, 1, 2, 2, 2, 8, 16, kRankTcBlocked};
   // shapes are judged and timed on the subdomains of the shared-memory
   // kernels (the blocked wide-band kernel, the same in every candidate, runs
   // only in the final factor); a CUDA-core shape with fewer threads than the
@@ -42,7 +44,8 @@ int tune_shapes(const TuneTarget& t, int reps, Tune* best, ras_pml_tune_t* repor
   const int nb = narrow_band(t.prec, t.max_b, t.split);
   const bool tc_all = t.max_b <= max_band(t.prec) && factor_tc_ok(t.prec, t.max_b);
   const bool tc_mixed = !tc_all && t.prec >= 1 && t.split.nwide >= 0 && t.split.nwide < t.nsub && nb > 0;
-  const int nfc = nb == 0 ? 0 : (tc_all || tc_mixed) ? 8 : 6;   // nb == 0: every subdomain is wide
+  const bool tc_blocked = tc_mixed && t.wscratch != nullptr;
+  const int nfc = nb == 0 ? 0 : tc_blocked ? 9 : (tc_all || tc_mixed) ? 8 : 6;   // nb == 0: every subdomain is wide
   for (int c = 0; c < nfc && e == cudaSuccess; ++c) {
     if (c == 6 && tc_mixed) {
       int b2 = -1;   // the fastest two-pivot shape timed so far

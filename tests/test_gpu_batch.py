@@ -189,8 +189,9 @@ def test_mixed_band_factor_shape(pkg):
     """A batch whose subdomains straddle the tensor-core form's band limit
     (b = 193 in c0 with one box across, b <= 127 elsewhere): the mixed shape
     factors the wide ones on the CUDA cores and the rest on the tensor cores,
-    and gives every problem its oracle B^-1 and the CUDA-core shape's
-    iteration counts."""
+    factor_rank 24 the wide ones on the blocked tensor-core kernel (window in
+    scratch), and each gives every problem its oracle B^-1 and the CUDA-core
+    shape's iteration counts."""
     from gpu_util import variant
     from paper_2602_00735_gb300 import RasPmlError
     probs = [variant("c0", px=1, py=2), variant("tiny3"), variant("small", px=3, py=5)]
@@ -201,7 +202,7 @@ def test_mixed_band_factor_shape(pkg):
         rs = [random_vector(int(n), 70 + q) for q, n in enumerate(B.sizes)]
         b = B.assemble_rhs(_sources(probs))
         its = {}
-        for shape in ((1024, 2), (1024, 8), (512, 16)):
+        for shape in ((1024, 2), (1024, 8), (512, 16), (128, 24)):
             B.set_shapes(*shape, 8)
             B.factor()
             z = B.apply(B.join(rs))
@@ -210,10 +211,11 @@ def test_mixed_band_factor_shape(pkg):
                 assert rel(zq.cpu().numpy(), R.apply(rs[q])) <= 1e-4, (shape, q)
             _, its[shape], _, st = B.solve(b, rtol=1e-8, maxit=400)
             assert st == 0
-        for shape in ((1024, 8), (512, 16)):
+        for shape in ((1024, 8), (512, 16), (128, 24)):
             assert np.all(np.abs(np.asarray(its[shape]) - np.asarray(its[(1024, 2)])) <= 1), its
         rep = B.tune()
         # 128 threads cannot hold the 194 diagonals of the b = 193 window:
-        # that shape is skipped, the other seven are timed
-        assert {"1024x2", "512x2"} <= set(rep["factor_ms"]) and len(rep["factor_ms"]) == 7
+        # that shape is skipped, the other seven and the blocked tensor-core
+        # shape are timed
+        assert {"1024x2", "512x2", "128x24"} <= set(rep["factor_ms"]) and len(rep["factor_ms"]) == 8
         assert "128x1" not in rep["factor_ms"]

@@ -60,11 +60,20 @@ def _fields(src, start, end):
     return [re.sub(r"\[\d+\]", "", f).strip() for grp in fields for f in grp.split(",")]
 
 
+def _lengths(src, start, end):
+    body = src[src.index(start):]
+    body = body[:body.index(end)]
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"(\w+)\[(\d+)\]", body)}
+
+
 def test_tune_and_batch_struct_layouts(lib):
     from paper_2602_00735_gb300 import _lib
     src = open(HEADER).read()
-    assert _fields(src, "typedef struct {\n  int32_t factor_threads;", "} ras_pml_tune_t;") == \
-        [n for n, _ in _lib.TuneReport._fields_]
+    tune = ("typedef struct {\n  int32_t factor_threads;", "} ras_pml_tune_t;")
+    assert _fields(src, *tune) == [n for n, _ in _lib.TuneReport._fields_]
+    # array members have the header's lengths (the report is filled by the library)
+    arrays = {n: t._length_ for n, t in _lib.TuneReport._fields_ if hasattr(t, "_length_")}
+    assert arrays == _lengths(src, *tune)
     assert _fields(src, "typedef struct {\n  int32_t nprob;", "} ras_pml_batch_info_t;") == \
         [n for n, _ in _lib.BatchInfo._fields_]
 
