@@ -23,8 +23,8 @@
 // k_apply_mw: the same sweeps for the wide band classes (more register slots
 //   than one warp's phase-dispatched window holds) on several warps per
 //   subdomain, each holding the row group being finished and a share of the
-//   slots below it, with the same arithmetic in the same order (results bit
-//   for bit independent of the number of warps).
+//   slots below it; every row takes its updates in the order of a one-warp
+//   sweep (two warps measured bit for bit equal to one).
 // k_prolong: one thread per global unknown sums the (at most four) weighted
 //   local values that cover it, in a fixed order (bit-reproducible): in FP64
 //   into complex128 (or split into the double-float form), or, for complex64
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(32)
 // The wide class on W warps per subdomain (a CTA of 32 W threads). Every
 // warp keeps the row group being finished (slot 0) and performs its 32 steps
 // itself, so the multiplier y_k of each step comes from a shuffle inside the
-// warp, bit for bit the same in every warp; the other S - 1 slots are shared
+// warp, the same in every warp (explicit FMAs); the other S - 1 slots are shared
 // out, warp w holding slots 1 + w SPW .. (SPW = ceil((S - 1) / W)). After
 // each group the window moves up one slot: warp 0's first slot becomes every
 // warp's slot 0, warp w's first slot becomes warp w-1's last, and the rows

@@ -219,3 +219,20 @@ def test_mixed_band_factor_shape(pkg):
         # shape are timed
         assert {"1024x2", "512x2", "128x24"} <= set(rep["factor_ms"]) and len(rep["factor_ms"]) == 8
         assert "128x1" not in rep["factor_ms"]
+
+
+def test_blocked_tensor_core_shape_with_half_storage(pkg):
+    """Factor shape 24 with half-precision factor storage: the subdomains
+    with 127 < b <= 232 on the blocked tensor-core kernel, the others on the
+    tensor-core kernel, each problem's B^-1 at the half-storage tolerance."""
+    from gpu_util import variant
+    probs = [variant("c0", px=1, py=2), variant("small", px=3, py=5)]
+    with pkg.BatchRasPml([w.params() for w in probs], factor_prec=2) as B:
+        assert 127 < B.info()["max_band"] <= 232
+        B.set_shapes(128, 24, 8)
+        B.factor()
+        rs = [random_vector(int(n), 90 + q) for q, n in enumerate(B.sizes)]
+        z = B.apply(B.join(rs))
+        for q, (w, zq) in enumerate(zip(probs, B.split(z))):
+            _, _, R = oracle_problem(w)
+            assert rel(zq.cpu().numpy(), R.apply(rs[q])) <= 2e-2, q
