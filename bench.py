@@ -8,7 +8,7 @@ load vector, local assembly and LDL^T factorisation of all 1024 PML-extended
 subdomains, and flexible GMRES with the RAS-PML preconditioner to a relative
 residual of 1e-6.
 
-  value      time per step of the precision form of config 2: local factors
+  value      time per step of the precision form on c2 (k = 160*pi): local factors
              and solves in complex64; SpMV, Arnoldi (Gram-Schmidt in
              double-float arithmetic on a split complex128 basis, --ortho 3,
              complex128-accurate), Givens and true residual in complex128
@@ -24,8 +24,8 @@ residual of 1e-6.
   roofline   the apply of B^-1 (k_apply + k_prolong), timed with CUDA events
              inside the timed steps on the handle's stream
   learned    the same step with the learned coarse correction attached
-  c4, c3     summaries of the headline form on config 4 (k = 320*pi, 9.4M
-             unknowns) and of the batched form on config 3 (64 problems)
+  c4, c3     summaries of the headline form on c4 (k = 320*pi, 9.4M
+             unknowns) and of the batched form on c3 (64 problems)
   cpu_baseline  the CPU oracle on all host cores (SuperLU local factors and
              solves in a process pool): c0 and c1 timed in full, c2 from a
              bounded sample, with the model checked against the full c1 run
@@ -64,7 +64,7 @@ import numpy as np  # noqa: E402
 
 import workloads  # noqa: E402
 
-METRIC = ("RAS-PML time to rtol 1e-6 at k=160*pi (config 2), complex64 local factors + FGMRES with "
+METRIC = ("RAS-PML time to rtol 1e-6 at k=160*pi (c2), complex64 local factors + FGMRES with "
           "complex128-accurate Arnoldi/Givens/residual (s)")
 BATCH_METRIC = ("RAS-PML batched form: 64 independent problems (k 20*pi..120*pi, 19.5M unknowns) to rtol 1e-6, "
                 "complex64 local factors + complex128 lockstep FGMRES (s)")
@@ -485,9 +485,9 @@ def run_ours(args, rank, world, local_rank):
     if not args.skip_extra and args.form == 0:
         richardson = run_richardson(args, p, w, shapes[(w.name, args.prec)], stream)
 
-    # config 4 (k = 320*pi) and the batched config 3 in the same run
+    # c4 (k = 320*pi) and the batched c3 in the same run
     extra = {}
-    # the FP64 step of config 4 runs once, with the default tile shapes (its
+    # the FP64 step of c4 runs once, with the default tile shapes (its
     # tuning would cost more than the step and is not part of the comparison)
     shapes.setdefault(("c4", 0), (256, 2, 8, {"fixed": "256,2,8 (defaults, not tuned)"}))
     if not args.skip_extra and args.form == 0 and args.workload == "c2":
@@ -545,7 +545,7 @@ def run_ours(args, rank, world, local_rank):
 
 
 def run_learned(args, p, w, shp, iters_plain, t_plain, stream, dev, x_ref):
-    """The learned coarse correction (config 4's network): trained on this
+    """The learned coarse correction (a CNN coarse stage): trained on this
     problem's own residual/error pairs (training time reported apart), then
     the headline step with the stage attached; the network's own timings."""
     import torch
@@ -649,7 +649,7 @@ def run_richardson(args, p, w, shp, stream):
 
 
 def summary_c4(args, timed, rel_err):
-    """Config 4 (k = 320*pi, h = 1/2560, 64 x 64 subdomains, 9.4M unknowns):
+    """c4 (k = 320*pi, h = 1/2560, 64 x 64 subdomains, 9.4M unknowns):
     the headline form, 1 warm-up and 2 timed steps, against one plain FP64
     step (default tile shapes); the apply's fraction of the HBM peak."""
     try:
@@ -676,7 +676,7 @@ def summary_c4(args, timed, rel_err):
 
 
 def summary_c3(args, stream):
-    """Config 3 (64 independent problems in the same launches): 1 warm-up and
+    """c3 (64 independent problems in the same launches): 1 warm-up and
     2 timed steps of the batched form with tuned tile shapes."""
     import torch
 

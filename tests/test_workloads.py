@@ -36,7 +36,7 @@ def test_batch_recipe(name):
 
 
 def test_c3_grids_are_drawn_uniformly_without_a_band_filter():
-    """Config 3: px and py independent and uniform in 2..12. The draws are
+    """c3: px and py independent and uniform in 2..12. The draws are
     the generator's own: the same integers as rng.integers(2, 13, size=2) at
     that point of the sequence, so nothing narrows them to what a kernel can
     hold; the widest local band follows from them (408 with seed 3)."""
