@@ -30,6 +30,13 @@
 // like the narrow kernels do (status->pivot_bad_sub). The only waits are the
 // block and cluster barriers, which every CTA of a cluster reaches the same
 // number of times (one subdomain, one loop).
+//
+// k_factor_wide_tc (below) is the same factorisation in complex64 with the
+// trailing update on the tensor cores, one CTA per subdomain; it also takes
+// the bands from kMaxBandTc up to the shared-memory window's limit (factor
+// shape kRankTcBlocked of the batched form). Every launch addresses the
+// scratch slots with one stride, factor_wide_slot_bytes(prec, max_b), so
+// launches that run concurrently never share memory.
 #include <cooperative_groups.h>
 
 #include <algorithm>
