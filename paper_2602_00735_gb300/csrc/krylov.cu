@@ -379,10 +379,12 @@ __device__ __forceinline__ c64 bzero<c64>() { return mk(0.f, 0.f); }
 template <>
 __device__ __forceinline__ dfc bzero<dfc>() { return dfc{0.f, 0.f, 0.f, 0.f}; }
 
-// partial[c * gridDim.x + blk] = sum over the block's rows of conj(V_c) w,
-// four columns per block, w read and split once per row of the block (eight
+// partial[c * nrb + rb] = sum over row block rb's rows of conj(V_c) w, four
+// columns per block, w read and split once per row of the block (eight
 // columns were measured on the complex64 basis: 105 registers per thread,
-// slower on c2 and c4)
+// slower on c2 and c4). The blocks of one row block (its column groups) are
+// consecutive in the grid, so they run together and their reads of the same
+// rows of w after the first come from L2.
 constexpr int kC64Cols = 4;
 
 template <typename B>
@@ -391,10 +393,12 @@ __global__ void __launch_bounds__(kThreads)
              c128* __restrict__ partial, const KState* __restrict__ kst) {
   if (skip(kst, 0)) return;
   constexpr int kDfCols = kC64Cols;
-  const int c0 = blockIdx.y * kDfCols;
+  const int ncg = (ncols + kDfCols - 1) / kDfCols;   // column groups
+  const int cg = blockIdx.x % ncg, rb = blockIdx.x / ncg, nrb = gridDim.x / ncg;
+  const int c0 = cg * kDfCols;
   const int nc = min(kDfCols, ncols - c0);
-  const long long per = (n + gridDim.x - 1) / gridDim.x;
-  const long long r0 = blockIdx.x * per;
+  const long long per = (n + nrb - 1) / nrb;
+  const long long r0 = rb * per;
   const long long r1 = min(n, r0 + per);
   float rh[kDfCols], rl[kDfCols], ih[kDfCols], il[kDfCols];
 #pragma unroll
@@ -459,7 +463,7 @@ __global__ void __launch_bounds__(kThreads)
       df_acc(t.x, t.y, v.x, v.y);
       df_acc(t.z, t.w, v.z, v.w);
     }
-    partial[(long long)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = mk(df_to_d(t.x, t.y), df_to_d(t.z, t.w));
+    partial[(long long)(c0 + threadIdx.x) * nrb + rb] = mk(df_to_d(t.x, t.y), df_to_d(t.z, t.w));
   }
 }
 
@@ -936,7 +940,8 @@ cudaError_t launch_scale_to_c64(const c128* w, void* v, long long n, const doubl
 template <typename B>
 cudaError_t launch_dots_bt(const void* V, long long ldv, int ncols, const c128* w, long long n, c128* partial,
                            const KState* kst, cudaStream_t st, int wdf) {
-  dim3 grid(dot_blocks(), (ncols + kC64Cols - 1) / kC64Cols);
+  // row blocks x column groups, the column group varying fastest
+  const unsigned grid = (unsigned)dot_blocks() * (unsigned)((ncols + kC64Cols - 1) / kC64Cols);
   k_dots_b<B><<<grid, kThreads, 0, st>>>((const B*)V, ldv, ncols, w, wdf, n, partial, kst);
   return cudaGetLastError();
 }
